@@ -1,0 +1,417 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test is chosen so that a plausible mistake in the oracle (a dropped
+term, a wrong sign, a transposed index or operand, a wrong normalisation)
+fails at least one of them.  None of them compares the oracle with itself
+under a re-typed formula: they use closed forms, exact reproductions,
+invariants, brute force and the golden values under tests/golden/.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_39443_b300 import workloads as W
+from paper_2609_39443_b300.workloads import BeamSpec, GridSpec, StepInput, Workload
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    for line in open(os.path.join(GOLD, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def _beams(line_off, cv_len, **kw):
+    n = len(line_off) - 1
+    base = dict(d=0.01, cdn=1.2, cdt=0.01, eps=0.02, ell_s=0.07, alpha_f=1.0)
+    base.update(kw.pop("per_line", {}))
+    arrs = {k: np.full(n, float(v)) if np.ndim(v) == 0 else np.asarray(v, float) for k, v in base.items()}
+    return BeamSpec(line_off=np.asarray(line_off, np.int32), cv_len=np.asarray(cv_len, float), **arrs, **kw)
+
+
+def _uniform(grid, u):
+    U = np.zeros((3, grid.n_cells))
+    for a in range(3):
+        U[a] = u[a]
+    return U
+
+
+# ----------------------------------------------------------------------------
+# sampling (Eqs. almPreliminaryVelocity, almRelativeVelocity; trilinear reading)
+# ----------------------------------------------------------------------------
+
+def test_trilinear_reproduces_affine_fields():
+    rng = np.random.default_rng(1)
+    g = GridSpec(7, 5, 6, 0.1, origin=(0.3, -0.2, 1.0))
+    idx = np.arange(g.n_cells)
+    i, j, k = idx % g.nx, (idx // g.nx) % g.ny, idx // (g.nx * g.ny)
+    xc = np.stack([g.origin[0] + (i + .5) * g.h, g.origin[1] + (j + .5) * g.h, g.origin[2] + (k + .5) * g.h])
+    A = rng.normal(size=(3, 3))
+    b = rng.normal(size=3)
+    U = A @ xc + b[:, None]
+    for _ in range(200):
+        # interior points (at least half a cell from the walls): exact
+        p = np.array(g.origin) + (0.5 + rng.uniform(0, 1, 3) * (np.array([g.nx, g.ny, g.nz]) - 1)) * g.h
+        ok, v = oracle.sample(g, U, 0, p)
+        assert ok
+        np.testing.assert_allclose(v, A @ p + b, rtol=0, atol=1e-12)
+
+
+def test_trilinear_cell_centres_and_wall_extension():
+    rng = np.random.default_rng(2)
+    g = GridSpec(4, 3, 5, 0.5)
+    f = rng.normal(size=(1, g.n_cells))
+    for c in [(0, 0, 0), (3, 2, 4), (1, 2, 3)]:
+        p = (np.array(c) + 0.5) * g.h
+        ok, v = oracle.sample(g, f, 0, p)
+        assert ok and v[0] == pytest.approx(f[0, c[0] + g.nx * (c[1] + g.ny * c[2])], abs=1e-14)
+    # in the half cell next to the x = 0 wall the wall cell's value is extended
+    fx = np.tile(np.arange(g.nx, dtype=float) * 3.0 + 1.0, g.ny * g.nz)[None]
+    ok, v = oracle.sample(g, fx, 0, np.array([0.1, 0.7, 1.3]) * g.h + np.array([0, 0, 0]))
+    assert ok and v[0] == pytest.approx(1.0, abs=1e-14)
+
+
+def test_cell_mode_returns_the_containing_cell():
+    rng = np.random.default_rng(3)
+    g = GridSpec(6, 4, 5, 0.25, origin=(1.0, 2.0, -1.0))
+    f = rng.normal(size=(3, g.n_cells))
+    for _ in range(100):
+        c = rng.integers([0, 0, 0], [g.nx, g.ny, g.nz])
+        frac = rng.uniform(0.05, 0.95, 3)
+        p = np.array(g.origin) + (c + frac) * g.h
+        ok, v = oracle.sample(g, f, 1, p)
+        assert ok
+        np.testing.assert_array_equal(v, f[:, c[0] + g.nx * (c[1] + g.ny * c[2])])
+    # a point on a face goes to the upper cell (floor rule)
+    ok, v = oracle.sample(g, f, 1, np.array(g.origin) + np.array([2.0, 1.5, 3.25]) * g.h)
+    np.testing.assert_array_equal(v, f[:, 2 + g.nx * (1 + g.ny * 3)])
+
+
+def test_outside_points_are_reported():
+    g = GridSpec(4, 4, 4, 1.0)
+    f = np.ones((1, g.n_cells))
+    assert not oracle.sample(g, f, 0, [-1e-9, 1, 1])[0]
+    assert not oracle.sample(g, f, 0, [4.0, 1, 1])[0]
+    assert oracle.sample(g, f, 0, [0.0, 1, 3.999999])[0]
+
+
+# ----------------------------------------------------------------------------
+# tangent, sampling point and fallback (Sec. 3.2.2, Eq. almSamplingPoint)
+# ----------------------------------------------------------------------------
+
+def _line_workload(P, U, Pdot=None, grid=None, **beamkw):
+    grid = grid or GridSpec(40, 40, 40, 0.01)
+    n = P.shape[1]
+    b = _beams([0, n], np.full(n, beamkw.pop("cv", 0.01)), **beamkw)
+    return Workload("pin", grid, b, StepInput(U=U, P=P, Pdot=np.zeros_like(P) if Pdot is None else Pdot))
+
+
+def test_tangent_straight_line_and_circle():
+    g = GridSpec(40, 40, 40, 0.01)
+    d = np.array([0.3, -0.4, 0.866])
+    d /= np.linalg.norm(d)
+    P = np.array([0.2, 0.2, 0.05])[:, None] + 0.01 * np.arange(9)[None] * d[:, None]
+    r = oracle.point_step(g, _line_workload(P, _uniform(g, (0.5, 0, 0))).beams,
+                          _line_workload(P, _uniform(g, (0.5, 0, 0))).step)
+    np.testing.assert_allclose(r["e_t"], np.repeat(d[:, None], 9, axis=1), atol=1e-14)
+    # equally spaced points on a circle: interior tangents are perpendicular to the radius
+    th = np.linspace(0.2, 2.0, 12)
+    c0 = np.array([0.2, 0.2, 0.2])
+    P = c0[:, None] + 0.05 * np.stack([np.cos(th), np.sin(th), 0 * th])
+    wl = _line_workload(P, _uniform(g, (0.5, 0, 0)))
+    et = oracle.point_step(g, wl.beams, wl.step)["e_t"]
+    radial = P - c0[:, None]
+    np.testing.assert_allclose((et[:, 1:-1] * radial[:, 1:-1]).sum(0), 0, atol=1e-15)
+    np.testing.assert_allclose(np.linalg.norm(et, axis=0), 1, atol=1e-14)
+    np.testing.assert_allclose(et[:, 0], (P[:, 1] - P[:, 0]) / np.linalg.norm(P[:, 1] - P[:, 0]), atol=1e-15)
+
+
+def test_sampling_point_in_uniform_flow_is_straight_upstream():
+    g = GridSpec(40, 40, 40, 0.01)
+    P = np.stack([np.full(10, 0.2), np.full(10, 0.2), 0.05 + 0.01 * np.arange(10)])
+    wl = _line_workload(P, _uniform(g, (0.5, 0.0, 0.0)), per_line=dict(ell_s=0.07))
+    r = oracle.point_step(g, wl.beams, wl.step)
+    np.testing.assert_allclose(r["P_s"], P - np.array([0.07, 0, 0])[:, None], atol=1e-15)
+    assert r["status"][oracle.ST_FALLBACK] == 0
+
+
+def test_sampling_plane_projection_bounds_the_offset():
+    rng = np.random.default_rng(4)
+    g = GridSpec(40, 40, 40, 0.01)
+    U = _uniform(g, (0.4, 0.3, 0.0)) + rng.normal(0, 0.01, size=(3, g.n_cells))
+    P = np.stack([np.full(10, 0.2), np.full(10, 0.2), 0.05 + 0.01 * np.arange(10)])
+    wl = _line_workload(P, U, per_line=dict(ell_s=0.07), n_p=(0.0, 1.0, 0.0))
+    r = oracle.point_step(g, wl.beams, wl.step)
+    off = r["P_s"] - P
+    np.testing.assert_allclose(off[1], 0.0, atol=1e-16)
+    assert (np.linalg.norm(off, axis=0) <= 0.07 + 1e-15).all()
+    assert (np.linalg.norm(off, axis=0) < 0.07 - 1e-3).all()     # y part removed, not renormalised
+
+
+def test_fallback_direction():
+    g = GridSpec(40, 40, 40, 0.01)
+    P = np.stack([np.full(6, 0.2), np.full(6, 0.2), 0.1 + 0.01 * np.arange(6)])
+    U = _uniform(g, (0.3, 0.1, 0.2))
+    Pdot = np.repeat(np.array([0.3, 0.1, 0.2])[:, None], 6, axis=1)   # no relative flow
+    wl = _line_workload(P, U, Pdot, per_line=dict(ell_s=0.05), g_up=(-1.0, 0.0, 1.0))
+    r = oracle.point_step(g, wl.beams, wl.step)
+    assert r["status"][oracle.ST_FALLBACK] == 6
+    # g_up projected on the cross-section plane (perpendicular to z) and renormalised
+    np.testing.assert_allclose(r["P_s"] - P, np.repeat(np.array([-0.05, 0, 0])[:, None], 6, 1), atol=1e-15)
+    np.testing.assert_allclose(r["F"], 0.0, atol=1e-30)
+    wl = _line_workload(P, U, Pdot, per_line=dict(ell_s=0.05), g_up=(0.0, 0.0, 1.0))
+    r = oracle.point_step(g, wl.beams, wl.step)
+    assert r["status"][oracle.ST_FALLBACK_ZERO] == 6
+    np.testing.assert_allclose(r["P_s"], P, atol=0)
+
+
+# ----------------------------------------------------------------------------
+# line force (Eqs. almLineForce, fext_drag, almForceRelaxation)
+# ----------------------------------------------------------------------------
+
+def test_cylinder_drag_golden():
+    gd = _golden("cylinder_drag.txt")
+    n = int(gd["n_cv"])
+    g = GridSpec(64, 32, 32, 0.01, rho_const=gd["rho"])
+    P = np.stack([np.full(n, 0.2), np.full(n, 0.16), (np.arange(n) + 0.5) * gd["length"] / n])
+    wl = _line_workload(P, _uniform(g, (gd["U0"], 0, 0)), grid=g, cv=gd["length"] / n,
+                        per_line=dict(d=gd["d"], cdn=gd["cdn"], cdt=0.37))
+    r = oracle.point_step(g, wl.beams, wl.step)
+    np.testing.assert_allclose(r["F"][0], gd["F_per_cv"], rtol=1e-14)
+    np.testing.assert_allclose(r["F"][1:], 0.0, atol=1e-18)
+    np.testing.assert_allclose(r["f"][0], gd["f_per_length"], rtol=1e-14)
+    assert r["F"][0].sum() == pytest.approx(gd["F_total"], rel=1e-14)
+
+
+@pytest.mark.parametrize("drag_mode", [W.DRAG_DISCRETE, W.DRAG_SPLIT])
+def test_inclined_cylinder_closed_form(drag_mode):
+    theta = 0.6                                     # angle between line and flow
+    U0, rho, d, cdn, cdt = 0.7, 1000.0, 0.01, 1.3, 0.05
+    g = GridSpec(60, 20, 60, 0.01, rho_const=rho)
+    t = np.array([np.cos(theta), 0.0, np.sin(theta)])
+    P = np.array([0.2, 0.1, 0.2])[:, None] + 0.01 * np.arange(8)[None] * t[:, None]
+    wl = _line_workload(P, _uniform(g, (U0, 0, 0)), grid=g, cv=0.01,
+                        per_line=dict(d=d, cdn=cdn, cdt=cdt), drag_mode=drag_mode)
+    F = oracle.point_step(g, wl.beams, wl.step)["F"] / 0.01
+    Ut = U0 * np.cos(theta) * t
+    Un = np.array([U0, 0, 0]) - Ut
+    if drag_mode == W.DRAG_DISCRETE:      # |U_r| (C_dn U_n + C_dt U_t)
+        f = 0.5 * rho * d * U0 * (cdn * Un + cdt * Ut)
+    else:                                 # C_dn |U_n| U_n + C_dt |U_t| U_t
+        f = 0.5 * rho * d * (cdn * np.linalg.norm(Un) * Un + cdt * np.linalg.norm(Ut) * Ut)
+    np.testing.assert_allclose(F, np.repeat(f[:, None], 8, 1), rtol=1e-13, atol=1e-15)
+    # normal magnitude: 1/2 rho d C_dn U0^2 sin(theta) vs ... sin^2(theta)
+    p = 1 if drag_mode == W.DRAG_DISCRETE else 2
+    assert np.linalg.norm(F[:, 3] - (F[:, 3] @ t) * t) == pytest.approx(0.5 * rho * d * cdn * U0 ** 2 * np.sin(theta) ** p, rel=1e-13)
+
+
+def test_relative_velocity_is_galilean():
+    rng = np.random.default_rng(5)
+    wl = W.make_random(11, 24, 20, 22, n_lines=3, kinds=("stem",))
+    c = np.array([0.13, -0.07, 0.05])
+    wl2 = Workload("s", wl.grid, wl.beams, StepInput(U=wl.step.U + c[:, None], P=wl.step.P,
+                                                      Pdot=wl.step.Pdot + c[:, None]))
+    # upstream direction and forces depend on U - Pdot only (field noise is the same)
+    r1 = oracle.point_step(wl.grid, wl.beams, wl.step)
+    r2 = oracle.point_step(wl2.grid, wl2.beams, wl2.step)
+    np.testing.assert_allclose(r2["F"], r1["F"], rtol=1e-9, atol=1e-12)
+    # moving the beam with the flow reduces the load; a sign error would increase it
+    wl3 = Workload("s", wl.grid, wl.beams, StepInput(U=wl.step.U, P=wl.step.P,
+                                                      Pdot=wl.step.Pdot + np.array([0.2, 0, 0])[:, None]))
+    r3 = oracle.point_step(wl3.grid, wl3.beams, wl3.step)
+    assert r3["F"][0].sum() < r1["F"][0].sum()
+    del rng
+
+
+def test_relaxation_blend():
+    wl = W.make_random(12, 24, 20, 22, n_lines=2, kinds=("stem",))
+    r0 = oracle.point_step(wl.grid, wl.beams, wl.step)
+    f_prev = np.random.default_rng(6).normal(size=r0["f"].shape)
+    r1 = oracle.point_step(wl.grid, wl.beams, wl.step, f_prev=f_prev)
+    af = np.repeat(wl.beams.alpha_f, np.diff(wl.beams.line_off))
+    np.testing.assert_allclose(r1["f"], af * r0["f"] + (1 - af) * f_prev, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(r1["F"], r1["f"] * wl.beams.cv_len, rtol=1e-14)
+
+
+def test_mixture_density():
+    g = GridSpec(40, 40, 40, 0.01, has_alpha=True, rho1=1000.0, rho2=1.2)
+    P = np.stack([np.full(5, 0.2), np.full(5, 0.2), 0.1 + 0.01 * np.arange(5)])
+    out = {}
+    for a in (1.0, 0.0, 0.3):
+        wl = _line_workload(P, _uniform(g, (0.5, 0, 0)), grid=g)
+        wl.step.alpha = np.full(g.n_cells, a)
+        out[a] = oracle.point_step(g, wl.beams, wl.step)["F"][0]
+    np.testing.assert_allclose(out[0.0] / out[1.0], 1.2 / 1000.0, rtol=1e-13)
+    np.testing.assert_allclose(out[0.3] / out[1.0], (0.3 * 1000 + 0.7 * 1.2) / 1000.0, rtol=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# projection (Eqs. almProjectionPoint, almGaussian, almMomentumSource)
+# ----------------------------------------------------------------------------
+
+def test_closest_segment_against_dense_polyline_sampling():
+    rng = np.random.default_rng(7)
+    for trial in range(30):
+        n = int(rng.integers(2, 12))
+        X = np.cumsum(rng.normal(size=(3, n)), axis=1)
+        c = rng.normal(size=3) * 2 + X.mean(axis=1)
+        k, s, r = oracle.closest_segment(X, c)
+        # brute force: 20001 points on every segment
+        tt = np.linspace(0, 1, 20001)
+        best = np.inf
+        for j in range(n - 1):
+            pts = X[:, j, None] + tt[None] * (X[:, j + 1] - X[:, j])[:, None]
+            dd = np.linalg.norm(pts - c[:, None], axis=0)
+            best = min(best, dd.min())
+        assert r <= best + 1e-12
+        assert r == pytest.approx(best, abs=1e-3 * np.linalg.norm(np.diff(X, axis=1), axis=0).max())
+        foot = X[:, k] + s * (X[:, k + 1] - X[:, k])
+        assert np.linalg.norm(foot - c) == pytest.approx(r, rel=1e-12)
+        assert 0.0 <= s <= 1.0
+
+
+def _straight_z_line(g, x, y, z0, dz, n, F):
+    P = np.stack([np.full(n, x), np.full(n, y), z0 + dz * np.arange(n)])
+    b = _beams([0, n], np.full(n, dz), per_line=dict(eps=2 * g.h))
+    return b, P, np.asarray(F, float)
+
+
+def test_gaussian_shape_between_cells_of_one_segment():
+    g = GridSpec(24, 24, 24, 1.0)
+    # line along z through cell centres (x, y) = (12.5, 12.5); nodes every 2 cells
+    n = 6
+    F = np.zeros((3, n)); F[0] = 1.0
+    b, P, F = _straight_z_line(g, 12.5, 12.5, 4.5, 2.0, n, F)
+    S = oracle.project(g, b, P, F)["S"][0].reshape(g.nz, g.ny, g.nx)
+    eps = 2.0
+    # cells at the same height (same segment and s) at r = 1 and r = sqrt(5), 2
+    s0 = S[9, 12, 12]
+    np.testing.assert_allclose(S[9, 12, 13] / s0, np.exp(-(1.0 ** 2) / eps ** 2), rtol=1e-13)
+    np.testing.assert_allclose(S[9, 13, 14] / s0, np.exp(-5.0 / eps ** 2), rtol=1e-13)
+    np.testing.assert_allclose(S[9, 12, 10] / s0, np.exp(-4.0 / eps ** 2), rtol=1e-13)
+    # cut-off at r = 3 eps = 6 is inclusive: (6, 0) kept, (6, 1) dropped
+    assert S[9, 12, 18] != 0.0 and S[9, 13, 18] == 0.0
+    np.testing.assert_allclose(S[9, 12, 18] / s0, np.exp(-9.0), rtol=1e-12)
+    # the source opposes the load (minus sign of Eq. almMomentumSource)
+    assert s0 < 0
+
+
+def test_nodal_interpolation_weights():
+    g = GridSpec(24, 24, 24, 1.0)
+    n = 4
+    F = np.zeros((3, n)); F[0] = [1.0, 3.0, -2.0, 5.0]; F[2] = [0.5, 0.0, 1.5, -1.0]
+    b, P, F = _straight_z_line(g, 12.5, 12.5, 6.5, 4.0, n, F)
+    r = oracle.project(g, b, P, F)
+    S, w = r["S"], r["w"]
+    fhat = F / w
+    eps = 2.0
+    for z, seg, s in [(7, 0, 0.25), (9, 0, 0.75), (12, 1, 0.5), (17, 2, 0.75)]:
+        for (x, y) in [(12, 12), (13, 12), (12, 10)]:
+            rr2 = (x - 12) ** 2 + (y - 12) ** 2
+            eta = np.exp(-rr2 / eps ** 2) / (np.pi * eps ** 2)
+            want = -eta * ((1 - s) * fhat[:, seg] + s * fhat[:, seg + 1])
+            np.testing.assert_allclose(S[:, x + 24 * (y + 24 * z)], want, rtol=1e-12, atol=1e-15)
+
+
+def test_gaussian_normalisation_converges_to_truncated_integral():
+    gd = _golden("gaussian_truncation.txt")
+    g = GridSpec(40, 40, 30, 1.0)
+    n = 11
+    eps = 4.0
+    P = np.stack([np.full(n, 20.0), np.full(n, 20.0), 4.5 + 2.0 * np.arange(n)])
+    b = _beams([0, n], np.full(n, 2.0), per_line=dict(eps=eps))
+    F = np.ones((3, n))
+    w = oracle.project(g, b, P, F)["w"]
+    # interior nodes: w_k -> L_k (1 - e^-9) for a well-resolved kernel
+    np.testing.assert_allclose(w[3:-3] / 2.0, gd["retained_fraction"], rtol=2e-4)
+    assert np.exp(-9.0) == pytest.approx(gd["discarded_fraction"], rel=1e-15)
+
+
+def test_conservation_on_random_lines():
+    for seed in range(6):
+        wl = W.make_random(100 + seed, 26, 22, 20, n_lines=5, precision="fp64",
+                           kinds=("stem", "arc", "random", "flat", "point", "dup"))
+        r = oracle.sample_drag_spread(wl)
+        F, SV = r["totals"][:3], r["totals"][3:]
+        scale = np.abs(r["F"]).sum()
+        lost = r["status"][oracle.ST_DEPOSIT_LOST]
+        if lost == 0:
+            assert np.abs(F + SV).max() <= 1e-12 * scale
+
+
+def test_cull_has_no_effect_bitwise():
+    for seed in range(4):
+        wl = W.make_random(200 + seed, 16, 14, 12, n_lines=3, precision="fp64",
+                           kinds=("stem", "arc", "random", "point"))
+        ps = oracle.point_step(wl.grid, wl.beams, wl.step)
+        a = oracle.project(wl.grid, wl.beams, wl.step.P, ps["F"], cull=True)
+        b = oracle.project(wl.grid, wl.beams, wl.step.P, ps["F"], cull=False)
+        np.testing.assert_array_equal(a["S"], b["S"])
+        np.testing.assert_array_equal(a["w"], b["w"])
+
+
+def test_superposition_over_lines_and_linearity():
+    wl = W.make_random(300, 26, 22, 20, n_lines=4, precision="fp64", kinds=("stem", "arc"))
+    ps = oracle.point_step(wl.grid, wl.beams, wl.step)
+    full = oracle.project(wl.grid, wl.beams, wl.step.P, ps["F"])["S"]
+    acc = np.zeros_like(full)
+    for l in range(wl.beams.n_lines):
+        m = np.zeros(wl.beams.n_lines, np.uint8); m[l] = 1
+        acc += oracle.project(wl.grid, wl.beams, wl.step.P, ps["F"], line_mask=m)["S"]
+    np.testing.assert_allclose(acc, full, rtol=1e-13, atol=1e-13 * np.abs(full).max())
+    s2 = oracle.project(wl.grid, wl.beams, wl.step.P, -2.5 * ps["F"])["S"]
+    np.testing.assert_allclose(s2, -2.5 * full, rtol=1e-14, atol=1e-14 * np.abs(full).max())
+
+
+def test_integer_translation_and_mirror():
+    g = GridSpec(20, 20, 20, 0.25)
+    rng = np.random.default_rng(8)
+    n = 7
+    # dyadic coordinates so the translated set-up is represented exactly
+    P = np.stack([2.5 + np.round(rng.uniform(-0.5, 0.5, n) * 64) / 64,
+                  2.0 + np.round(rng.uniform(-0.5, 0.5, n) * 64) / 64,
+                  1.75 + 0.25 * np.arange(n)])
+    F = rng.normal(size=(3, n))
+    b = _beams([0, n], np.full(n, 0.25), per_line=dict(eps=0.5))
+    S = oracle.project(g, b, P, F)["S"].reshape(3, 20, 20, 20)
+    # shift by (+2, +1, -1) cells; the support stays inside the grid in both positions
+    S2 = oracle.project(g, b, P + np.array([0.5, 0.25, -0.25])[:, None], F)["S"].reshape(3, 20, 20, 20)
+    np.testing.assert_allclose(S2[:, :-1, 1:, 2:], S[:, 1:, :-1, :-2], rtol=1e-12, atol=1e-12 * np.abs(S).max())
+    # mirror y -> 5 - y (the grid spans [0, 5]): S_y flips, x and z are mirrored copies
+    Pm = P.copy(); Pm[1] = 5.0 - P[1]
+    Fm = F.copy(); Fm[1] = -F[1]
+    Sm = oracle.project(g, b, Pm, Fm)["S"].reshape(3, 20, 20, 20)
+    np.testing.assert_allclose(Sm[0], S[0][:, ::-1, :], rtol=1e-12, atol=1e-12 * np.abs(S).max())
+    np.testing.assert_allclose(Sm[1], -S[1][:, ::-1, :], rtol=1e-12, atol=1e-12 * np.abs(S).max())
+    np.testing.assert_allclose(Sm[2], S[2][:, ::-1, :], rtol=1e-12, atol=1e-12 * np.abs(S).max())
+
+
+def test_zero_weight_nodes_are_deposited():
+    g = GridSpec(12, 12, 12, 1.0)
+    # kernel much narrower than a cell, nodes away from cell centres: no cell within 3 eps
+    P = np.array([[3.2, 5.7, 8.9], [4.1, 4.3, 6.6], [2.2, 6.9, 9.3]])
+    F = np.array([[1.0, -2.0, 0.5], [0.3, 0.2, 0.1], [-1.0, 0.0, 2.0]])
+    b = _beams([0, 3], np.ones(3), per_line=dict(eps=0.05))
+    r = oracle.project(g, b, P, F)
+    assert r["status"][oracle.ST_ZERO_WEIGHT] == 3
+    np.testing.assert_array_equal(r["w"], 0.0)
+    for k in range(3):
+        c = np.floor(P[:, k]).astype(int)
+        np.testing.assert_allclose(r["S"][:, c[0] + 12 * (c[1] + 12 * c[2])], -F[:, k], rtol=1e-15)
+    np.testing.assert_allclose(r["S"].sum(axis=1), -F.sum(axis=1), rtol=1e-14)
+
+
+def test_plain_config_totals():
+    wl = W.make_plain(0)
+    r = oracle.sample_drag_spread(wl)
+    assert np.abs(r["totals"][:3] + r["totals"][3:]).max() < 1e-14
+    # near-uniform flow of 0.5 m/s normal to a near-vertical 0.2 m cylinder: ~0.3 N
+    assert r["totals"][0] == pytest.approx(0.3, rel=0.1)
+    assert (r["status"][:2] == 0).all()
