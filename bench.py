@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of one coupling step of the actuator-line transfer operators.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload canopy|flume|plain]
+                    [--eps 2.0] [--impl ours|reference]
+
+A step is one call of al_sample_drag_spread (sampling, Morison line force,
+relaxation, normalised Gaussian projection of every line) on one instance
+whose fields and points are resident in HBM.  Under torchrun every rank runs
+its own independent instance (seed = rank) with no collective on the data
+path (weak scaling); timing is the max over ranks.
+
+Prints ONE JSON line (rank 0).  Throughput `value` is coupling steps/s over
+all ranks, device-timed with CUDA events; L2 is flushed (256 MiB write)
+between timed steps, outside the events.  `e2e` is the same metric through
+the public API with pinned host buffers, host<->device copies inside the
+timed region.  `roofline` reports the projection kernel (k_spread): its
+algorithmic bytes (the dense S write plus the staged per-node data) over
+its event-timed duration, against the measured HBM copy bandwidth.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KERNELS_PER_STEP = 9     # k_points k_segments k_lines k_mask k_weights k_normalise k_spread k_deposit k_totals
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="canopy", choices=["canopy", "flume", "plain"])
+    ap.add_argument("--eps", type=float, default=2.0, help="canopy kernel width in cells")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def _workload(name, seed, eps):
+    from paper_2609_39443_b300 import workloads as W
+    if name == "canopy":
+        return W.make_canopy(seed, eps)
+    if name == "flume":
+        return W.make_flume(seed)
+    return W.make_plain(seed)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("paper_2609_39443_b300/csrc/al_kernels.cuh", "paper_2609_39443_b300/csrc/al_api.cu"):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(workload_name):
+    """dram bytes per k_spread launch from a committed ncu summary, if it was
+    taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "spread_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(workload_name)
+    if not e or e.get("kernel_hash") != _kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for n, v in zip(names, r[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _algorithmic_bytes(wl):
+    """Bytes the projection kernel must move per launch: the dense S write
+    (3 components of every cell) plus, per actuator point, its position and
+    normalised force (staged once per brick that needs it; counted once)."""
+    es = 8 if wl.grid.precision == "fp64" else 4
+    return 3 * es * wl.grid.n_cells + wl.beams.n_points * (3 * es + 3 * es)
+
+
+def _cpu_baseline(wl, budget_s=12.0):
+    """The FP64 oracle as it stands, on this host's cores, on a bounded
+    sample of the same workload.  Returns (steps/s, cores, sample text)."""
+    import oracle
+    nl = wl.beams.n_lines
+    # sample: every m-th line's projection plus all points' sampling; the
+    # step rate is scaled by the fraction of lines projected
+    t0 = time.perf_counter()
+    oracle.point_step(wl.grid, wl.beams, wl.step)
+    t_point = time.perf_counter() - t0
+    m = 1
+    mask = np.ones(nl, np.uint8)
+    est = None
+    while True:
+        t0 = time.perf_counter()
+        ps = oracle.point_step(wl.grid, wl.beams, wl.step)
+        Psp = wl.step.P if wl.step.P_spread is None else wl.step.P_spread
+        oracle.project(wl.grid, wl.beams, Psp, ps["F"], line_mask=mask)
+        dt = time.perf_counter() - t0
+        frac = mask.sum() / max(nl, 1)
+        est = dt - t_point
+        if dt > 2.0 and m == 1 and nl > 1:
+            m = int(np.ceil(dt / 2.0))
+            mask = np.zeros(nl, np.uint8)
+            mask[::m] = 1
+            continue
+        break
+    reps, tot = 0, 0.0
+    while tot < budget_s and reps < 50:
+        t0 = time.perf_counter()
+        ps = oracle.point_step(wl.grid, wl.beams, wl.step)
+        oracle.project(wl.grid, wl.beams, Psp, ps["F"], line_mask=mask)
+        tot += time.perf_counter() - t0
+        reps += 1
+    per = tot / reps
+    t_full = t_point + (per - t_point) / frac if frac < 1 else per
+    cores = os.cpu_count()
+    sample = (f"{reps} oracle steps of {wl.name}" if frac >= 1 else
+              f"{reps} oracle steps of {wl.name} projecting every {m}-th line ({int(mask.sum())}/{nl}); "
+              f"step time scaled by the projected-line fraction")
+    del est
+    return 1.0 / t_full, cores, sample
+
+
+def run_reference(a):
+    """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = _workload(a.workload, 0, a.eps)
+    v, cores, sample = _cpu_baseline(wl, budget_s=max(5.0, min(60.0, 2.0 * (a.steps + a.warmup))))
+    line = {"impl": "reference", "metric": "coupling steps/s", "value": v, "unit": "steps/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2609_39443_b300 import build as B
+    if B.stale():
+        if rank == 0:
+            B.build()
+        if dist:
+            dist.barrier()
+    from paper_2609_39443_b300.al import Instance, PHASES, ST_SUPPORT
+
+    wl = _workload(a.workload, rank, a.eps)
+    inst = Instance(wl, device=f"cuda:{local}")
+    inst.grid.trace(True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    for _ in range(a.warmup):
+        inst.status.zero_()
+        inst.step()
+    torch.cuda.synchronize()
+    supp = int(inst.status[ST_SUPPORT].item())
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    phases = np.zeros(len(PHASES))
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(a.steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        inst.step()
+        ev1[k].record(stream)
+        phases += np.array(inst.grid.trace_last())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1)]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * a.steps / total_s
+    ph = phases / a.steps
+    spread_s = ph[PHASES.index("spread")] / 1e3
+
+    # ---- end to end through the public API with host buffers -----------------
+    e2e = None
+    if not a.no_e2e:
+        def pin(x):
+            return None if x is None else torch.as_tensor(np.ascontiguousarray(x)).pin_memory()
+        hU, hP, hPd, hal = pin(wl.step.U), pin(wl.step.P), pin(wl.step.Pdot), pin(wl.step.alpha)
+        hS = torch.empty(inst.S.shape, dtype=inst.S.dtype).pin_memory()
+        hF = torch.empty(inst.F.shape, dtype=inst.F.dtype).pin_memory()
+        h2d = sum(int(t.numel() * t.element_size()) for t in (hU, hP, hPd, hal) if t is not None)
+        d2h = int(hS.numel() * hS.element_size() + hF.numel() * hF.element_size())
+        n_e2e = max(3, min(a.steps, 10))
+
+        def e2e_step():
+            inst.U.copy_(hU, non_blocking=True)
+            inst.P.copy_(hP, non_blocking=True)
+            inst.Pdot.copy_(hPd, non_blocking=True)
+            if hal is not None:
+                inst.alpha.copy_(hal, non_blocking=True)
+            inst.step()
+            hS.copy_(inst.S, non_blocking=True)
+            hF.copy_(inst.F, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], dtype=torch.float64, device=f"cuda:{local}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * n_e2e / te, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    peak, peak_kind = _peaks()
+    alg = _algorithmic_bytes(wl)
+    achieved = alg / spread_s / 1e9
+    traffic = _traffic(wl.name)
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        v, cores, sample = _cpu_baseline(wl)
+        cpu = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        line = {"metric": "coupling steps/s", "value": value, "unit": "steps/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total_s / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if wl.grid.precision == "fp64" else "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "cells": wl.grid.n_cells, "points": wl.beams.n_points,
+                           "lines": wl.beams.n_lines, "parallelism": f"{world} independent instances",
+                           "l2": "flushed between timed steps (256 MiB write)"},
+                "kernel_cell_updates_per_s": supp * value,
+                "support_pairs_per_step": supp,
+                "phases_ms": {k: float(v) for k, v in zip(PHASES, ph)},
+                "roofline": {"bound": "hbm", "kernel": "k_spread", "achieved": achieved, "peak": peak,
+                             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                             "algorithmic_bytes": alg, "traffic": traffic},
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": KERNELS_PER_STEP * a.steps}
+        print(json.dumps(line), flush=True)
+    inst.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

@@ -1,0 +1,222 @@
+/*
+ * al.h -- C ABI of the B300 actuator-line transfer operators.
+ *
+ * One coupling step of the two-way actuator-line method of arXiv 2609.39443
+ * (Sec. 3.2, Algorithm 1 steps 1-5 and 7-8) on a uniform Cartesian fluid
+ * grid:
+ *   1. actuator points P_a and their velocities are given (Eqs.
+ *      almKinematicCoupling, almActuatorPoint);
+ *   2. the fluid velocity is sampled at P_a (Eq. almPreliminaryVelocity),
+ *      the upstream sampling point P_s is built (Eq. almSamplingPoint) and
+ *      the velocity (and, for free-surface flow, the volume fraction and
+ *      mixture density rho = alpha rho1 + (1-alpha) rho2, Sec. 2.1) is
+ *      sampled there (Eq. almRelativeVelocity);
+ *   3. the Morison line force is evaluated and under-relaxed (Eqs.
+ *      almLineForce, almForceRelaxation) and returned per CV as F_i = f_i L_i;
+ *   4. the equal and opposite reaction is projected onto the grid with the
+ *      truncated 2-D Gaussian, nearest-segment interpolation and per-node
+ *      normalisation (Eqs. almProjectionPoint, almGaussian,
+ *      almMomentumSource), so that sum_j S_j V = -sum_i F_i (Sec. 3.2.4).
+ *
+ * All functions return an int status: AL_OK (0) or a negative AL_ERR_*.
+ * No function exits the process, throws, or traps the device.  Argument
+ * errors are detected on the host before anything is enqueued.  Device-side
+ * anomalies (points outside the grid, zero weights, ...) are counted in the
+ * caller's status array and never stop the step.
+ *
+ * Memory: the caller owns every field, point and output buffer (device
+ * memory, passed as plain pointers).  The library owns only its scratch
+ * (per-point state, geometry, weights, bin masks), allocated by
+ * al_create_grid / al_load_beams and freed by al_destroy.
+ *
+ * Streams: a `stream` argument is a cudaStream_t passed as void*; NULL is
+ * the legacy default stream.  al_sample_drag_spread is asynchronous and
+ * stream-ordered; it performs no allocation and no host synchronisation.
+ */
+#ifndef AL_H
+#define AL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define AL_OK              0
+#define AL_ERR_ARG        -1   /* null pointer, bad size, inconsistent descriptor */
+#define AL_ERR_CUDA       -2   /* a CUDA runtime call failed (message via al_last_cuda_error) */
+#define AL_ERR_OOM        -3   /* device allocation failed */
+#define AL_ERR_STATE      -4   /* call out of order (e.g. step before al_load_beams) */
+#define AL_ERR_TIMEOUT    -5   /* a bounded wait ran out */
+#define AL_ERR_CAPACITY   -6   /* request larger than a fixed capacity */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define AL_FP32 0              /* fields, points, S and F stored as float  */
+#define AL_FP64 1              /* ... stored as double                     */
+
+#define AL_SAMPLE_TRILINEAR 0  /* trilinear interpolation of cell values   */
+#define AL_SAMPLE_CELL      1  /* value of the single containing cell (the paper's operator) */
+
+#define AL_DRAG_DISCRETE 0     /* Eq. almLineForce: |U_r| (C_dn U_n + C_dt U_t)        */
+#define AL_DRAG_SPLIT    1     /* Eq. fext_drag: C_dn |U_n| U_n + C_dt |U_t| U_t        */
+
+/* ---- device status counters (int[AL_STATUS_N], caller-owned, device) --- */
+#define AL_ST_PA_OUTSIDE     0 /* actuator point outside the grid: no load this step   */
+#define AL_ST_PS_OUTSIDE     1 /* sampling point outside the grid: no load (Sec. 3.2.5) */
+#define AL_ST_FALLBACK       2 /* |u0_n| < tau: fallback upstream direction used       */
+#define AL_ST_FALLBACK_ZERO  3 /* fallback direction parallel to the tangent: P_s = P_a */
+#define AL_ST_ZERO_WEIGHT    4 /* node with w_k = 0: load deposited in its cell        */
+#define AL_ST_DEPOSIT_LOST   5 /* zero-weight node outside the grid: load lost         */
+#define AL_ST_REFINED        6 /* geometric decisions re-taken in FP64 (near ties)     */
+#define AL_ST_IRREGULAR      7 /* lines projected by exhaustive segment search         */
+#define AL_ST_SUPPORT        8 /* (cell, line) pairs within 3 eps: kernel-cell updates   */
+#define AL_STATUS_N         16
+
+/* ---- descriptors ------------------------------------------------------- */
+typedef struct al_grid_s *al_grid;    /* opaque instance handle */
+
+/* Uniform Cartesian grid.  Cell (i,j,k) has centre
+ * origin + ((i+1/2) dx, (j+1/2) dx, (k+1/2) dx), volume dx^3, and linear
+ * index i + nx*(j + ny*k) (x fastest) in every field array. */
+typedef struct {
+    int nx, ny, nz;            /* cells per axis, each >= 1 */
+    double dx;                 /* cell size (m), > 0 */
+    double origin[3];          /* grid corner (m) */
+    int precision;             /* AL_FP32 or AL_FP64 */
+    int has_alpha;             /* 1: a volume-fraction field is sampled and rho = alpha rho1 + (1-alpha) rho2 */
+    double rho1, rho2;         /* phase densities (kg/m^3) */
+    double rho_const;          /* density when has_alpha = 0 */
+} al_grid_desc;
+
+/* Actuator lines (one per beam).  Line l owns points line_off[l] ..
+ * line_off[l+1]-1, ordered root to tip.  All arrays are HOST memory, read
+ * during the call and copied; the caller may free them afterwards. */
+typedef struct {
+    int n_lines;               /* >= 0 */
+    const int *line_off;       /* [n_lines + 1], non-decreasing, line_off[0] = 0 */
+    const double *d;           /* [n_lines] drag reference length (m) */
+    const double *cdn, *cdt;   /* [n_lines] normal / tangential drag coefficients */
+    const double *eps;         /* [n_lines] Gaussian width (m), > 0; cut-off at 3 eps */
+    const double *ell_s;       /* [n_lines] sampling distance (m), >= 0 */
+    const double *alpha_f;     /* [n_lines] relaxation factor in (0, 1] */
+    const double *cv_len;      /* [n_points] CV length L_i (m), the Delta s_i of Eq. almMomentumSource */
+    double n_p[3];             /* sampling-plane normal: unit vector or 0 (no projection) */
+    double g_up[3];            /* global upstream direction for the fallback */
+    double tau;                /* fallback threshold on |u0_n| (m/s) */
+    int sample_mode;           /* AL_SAMPLE_* (both samples use the same operator) */
+    int drag_mode;             /* AL_DRAG_* */
+    int tangents_given;        /* 1: al_step_in.tangent is used instead of the centreline tangent */
+} al_beam_desc;
+
+/* Inputs of one step: DEVICE pointers, element type per grid precision,
+ * SoA (component c of the vector field is the array [c]).  Unused optional
+ * pointers are NULL. */
+typedef struct {
+    const void *U[3];          /* [N_c] fluid velocity */
+    const void *alpha;         /* [N_c] volume fraction (required iff has_alpha) */
+    const void *P[3];          /* [N_p] actuator points (m) */
+    const void *Pdot[3];       /* [N_p] actuator-point velocities (m/s) */
+    const void *P_spread[3];   /* [N_p] optional positions for the projection (Algorithm 1,
+                                  step 7: positions after the beam update); NULL: P */
+    const void *tangent[3];    /* [N_p] optional tangents (used iff tangents_given) */
+} al_step_in;
+
+/* Outputs of one step: DEVICE pointers. */
+typedef struct {
+    void *S[3];                /* [N_c] momentum source (N/m^3), every cell overwritten */
+    void *F[3];                /* [N_p] per-CV line load on the beam F_i = f_i L_i (N) */
+    double *totals;            /* [6] or NULL: sum F (3), sum S V (3), FP64 */
+    int *status;               /* [AL_STATUS_N] or NULL: counters, ADDED to (zero them first) */
+} al_step_out;
+
+/* ---- single-instance API ----------------------------------------------- */
+
+/* Create an instance on the current CUDA device.  Validates the grid
+ * descriptor (AL_ERR_ARG) and allocates the per-grid scratch. */
+int al_create_grid(const al_grid_desc *desc, al_grid *out);
+
+/* Copy the line table and per-line coefficients to the device, allocate the
+ * per-point scratch and reset the relaxation state (the next step is
+ * un-relaxed, f = f*).  May be called again to replace the lines.
+ * Synchronous with respect to the host. */
+int al_load_beams(al_grid g, const al_beam_desc *beams);
+
+/* One coupling step (sampling, line force, relaxation, projection) on
+ * `stream`.  S and F are fully overwritten; totals (if given) are
+ * overwritten; status counters (if given) are incremented.  Updates the
+ * instance's relaxation state f_prev.  Consecutive steps of one instance
+ * must be ordered (same stream or explicit dependencies). */
+int al_sample_drag_spread(al_grid g, const al_step_in *in, const al_step_out *out, void *stream);
+
+/* Free everything the instance owns.  Synchronises the device first. */
+int al_destroy(al_grid g);
+
+/* Relaxation state export / import (checkpoint, eviction): f_prev as
+ * 3 x N_p values of the grid precision in DEVICE memory, plus whether a
+ * previous force exists.  Stream-ordered on `stream`. */
+int al_get_state(al_grid g, void *f_prev_dev, int *has_prev, void *stream);
+int al_set_state(al_grid g, const void *f_prev_dev, int has_prev, void *stream);
+
+/* Phase timing (tracing).  When enabled, each step records CUDA events on
+ * its stream at the phase boundaries below; al_trace_last waits for the
+ * last step's final event and returns the elapsed milliseconds of each
+ * phase.  Off by default; enabling creates AL_TRACE_N + 1 events. */
+#define AL_PH_POINTS    0      /* sampling, line force, segment geometry, line certificates */
+#define AL_PH_MASK      1      /* brick masks */
+#define AL_PH_WEIGHTS   2      /* nodal weights w_k */
+#define AL_PH_NORMALISE 3      /* f^_k = F_k / w_k */
+#define AL_PH_SPREAD    4      /* momentum source S (every cell) */
+#define AL_PH_TOTALS    5      /* zero-weight deposits, FP64 totals */
+#define AL_TRACE_N      6
+int al_trace_enable(al_grid g, int on);
+int al_trace_last(al_grid g, float *ms /* [AL_TRACE_N] */);
+
+/* Sizes of an instance: cells and points. */
+int al_sizes(al_grid g, long long *n_cells, long long *n_points, int *n_lines);
+
+/* ---- batched form ------------------------------------------------------ */
+/* Many independent instances advanced together: every phase of the step is
+ * one launch over the work items of all instances (points, lines, bricks),
+ * each item mapped to its instance through a device work list, and the
+ * projection runs as a persistent kernel over the bricks of every instance.
+ * With graphs on, the launch sequence is captured once into a CUDA graph and
+ * replayed.  Results are bitwise those of al_sample_drag_spread on each
+ * instance alone. */
+typedef struct al_batch_s *al_batch;
+
+int al_batch_create(al_batch *out);
+/* Register an instance with the device buffers of its steps; the buffers and
+ * the instance must stay valid while the batch is used.  All instances of a
+ * batch share one precision.  The step descriptors are copied. */
+int al_batch_add(al_batch b, al_grid g, const al_step_in *in, const al_step_out *out);
+/* Reserve n_slots slots of the given precision (before commit); slots beyond
+ * the added instances start empty and are bound later with al_batch_assign. */
+int al_batch_reserve(al_batch b, int n_slots, int precision);
+/* Freeze the batch: upload the work list (synchronous).  use_graph: capture
+ * the step into a CUDA graph on the first al_batch_run.  spread_ctas_per_sm:
+ * persistent grid of the projection (0: occupancy maximum). */
+int al_batch_commit(al_batch b, int use_graph, int spread_ctas_per_sm);
+/* One coupling step of every instance, stream-ordered on `stream`. */
+int al_batch_run(al_batch b, void *stream);
+/* One coupling step of the n_idx instances idx[0..n_idx) (distinct indices
+ * in add order), without a graph: the selection's work list is copied from a
+ * ring of 8 pinned slots allocated at commit, so a call waits only when the
+ * slot it reuses is still being read by a step 8 calls back.  Instances with
+ * steps in flight on other streams must not be selected again until those
+ * steps complete (steps of one instance are ordered). */
+int al_batch_run_subset(al_batch b, const int *idx, int n_idx, void *stream);
+/* Bind (g non-NULL) or clear (g NULL) one slot of a committed batch without a
+ * graph; the slot's descriptor is copied on `stream`, so later runs on that
+ * stream see it.  The previous binding must not have steps in flight. */
+int al_batch_assign(al_batch b, int slot, al_grid g, const al_step_in *in, const al_step_out *out, void *stream);
+int al_batch_destroy(al_batch b);
+
+/* Human-readable text of a status code (static storage). */
+const char *al_error_string(int code);
+
+/* Text of the last CUDA error seen by this thread (static per thread). */
+const char *al_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AL_H */

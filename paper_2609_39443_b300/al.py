@@ -1,0 +1,296 @@
+"""Thin ctypes binding of the C ABI in include/al.h.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library ``libal.so``.  PyTorch provides device memory and streams.  The
+library must be built (``python -m paper_2609_39443_b300.build``); if it is
+missing this module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libal.so")
+
+AL_OK, AL_ERR_ARG, AL_ERR_CUDA, AL_ERR_OOM, AL_ERR_STATE, AL_ERR_TIMEOUT, AL_ERR_CAPACITY = 0, -1, -2, -3, -4, -5, -6
+AL_FP32, AL_FP64 = 0, 1
+AL_STATUS_N = 16
+(ST_PA_OUTSIDE, ST_PS_OUTSIDE, ST_FALLBACK, ST_FALLBACK_ZERO, ST_ZERO_WEIGHT, ST_DEPOSIT_LOST,
+ ST_REFINED, ST_IRREGULAR, ST_SUPPORT) = range(9)
+
+TRACE_N = 6
+PHASES = ("points", "mask", "weights", "normalise", "spread", "totals")
+
+_vp = C.c_void_p
+_dp = C.POINTER(C.c_double)
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double),
+                ("origin", C.c_double * 3), ("precision", C.c_int), ("has_alpha", C.c_int),
+                ("rho1", C.c_double), ("rho2", C.c_double), ("rho_const", C.c_double)]
+
+
+class BeamDesc(C.Structure):
+    _fields_ = [("n_lines", C.c_int), ("line_off", C.POINTER(C.c_int)), ("d", _dp), ("cdn", _dp),
+                ("cdt", _dp), ("eps", _dp), ("ell_s", _dp), ("alpha_f", _dp), ("cv_len", _dp),
+                ("n_p", C.c_double * 3), ("g_up", C.c_double * 3), ("tau", C.c_double),
+                ("sample_mode", C.c_int), ("drag_mode", C.c_int), ("tangents_given", C.c_int)]
+
+
+class StepIn(C.Structure):
+    _fields_ = [("U", _vp * 3), ("alpha", _vp), ("P", _vp * 3), ("Pdot", _vp * 3),
+                ("P_spread", _vp * 3), ("tangent", _vp * 3)]
+
+
+class StepOut(C.Structure):
+    _fields_ = [("S", _vp * 3), ("F", _vp * 3), ("totals", _dp), ("status", C.POINTER(C.c_int))]
+
+
+class ALError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib():
+    """Load libal.so (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ALError(f"CUDA library not built: {LIB_PATH} (python -m paper_2609_39443_b300.build)")
+        L = C.CDLL(LIB_PATH)
+        L.al_create_grid.argtypes = [C.POINTER(GridDesc), C.POINTER(_vp)]
+        L.al_load_beams.argtypes = [_vp, C.POINTER(BeamDesc)]
+        L.al_sample_drag_spread.argtypes = [_vp, C.POINTER(StepIn), C.POINTER(StepOut), _vp]
+        L.al_destroy.argtypes = [_vp]
+        L.al_get_state.argtypes = [_vp, _vp, C.POINTER(C.c_int), _vp]
+        L.al_set_state.argtypes = [_vp, _vp, C.c_int, _vp]
+        L.al_sizes.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
+        L.al_batch_create.argtypes = [C.POINTER(_vp)]
+        L.al_batch_add.argtypes = [_vp, _vp, C.POINTER(StepIn), C.POINTER(StepOut)]
+        L.al_batch_commit.argtypes = [_vp, C.c_int, C.c_int]
+        L.al_batch_run.argtypes = [_vp, _vp]
+        L.al_batch_destroy.argtypes = [_vp]
+        L.al_trace_enable.argtypes = [_vp, C.c_int]
+        L.al_trace_last.argtypes = [_vp, C.POINTER(C.c_float)]
+        L.al_error_string.restype = C.c_char_p
+        L.al_error_string.argtypes = [C.c_int]
+        L.al_last_cuda_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def check(rc: int, what: str = "") -> None:
+    if rc != AL_OK:
+        L = lib()
+        msg = L.al_error_string(rc).decode()
+        if rc == AL_ERR_CUDA or rc == AL_ERR_OOM:
+            msg += " (" + L.al_last_cuda_error().decode() + ")"
+        raise ALError(f"{what}: {msg} [{rc}]")
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+def _three(x) -> Sequence:
+    """(3, N) tensor or sequence of 3 tensors -> 3 tensors (no copy)."""
+    if x is None:
+        return (None, None, None)
+    return (x[0], x[1], x[2])
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class BeamArrays:
+    """Host copies of a beam descriptor's arrays, kept alive for the call."""
+
+    def __init__(self, beams):
+        self.off = np.ascontiguousarray(beams.line_off, dtype=np.int32)
+        self.arr = [np.ascontiguousarray(x, dtype=np.float64)
+                    for x in (beams.d, beams.cdn, beams.cdt, beams.eps, beams.ell_s, beams.alpha_f, beams.cv_len)]
+
+        def p(a, ct=C.c_double):
+            return a.ctypes.data_as(C.POINTER(ct))
+
+        self.desc = BeamDesc(int(beams.n_lines), p(self.off, C.c_int), *[p(a) for a in self.arr],
+                             (C.c_double * 3)(*map(float, beams.n_p)), (C.c_double * 3)(*map(float, beams.g_up)),
+                             float(beams.tau), int(beams.sample_mode), int(beams.drag_mode),
+                             int(bool(beams.tangents_given)))
+
+
+def step_descriptors(U, P, Pdot, S, F, *, alpha=None, P_spread=None, tangent=None, totals=None, status=None):
+    """al_step_in / al_step_out for the given device tensors."""
+    sin = StepIn()
+    for a, t in enumerate(_three(U)):
+        sin.U[a] = _ptr(t)
+    for a, t in enumerate(_three(P)):
+        sin.P[a] = _ptr(t)
+    for a, t in enumerate(_three(Pdot)):
+        sin.Pdot[a] = _ptr(t)
+    for a, t in enumerate(_three(P_spread)):
+        sin.P_spread[a] = _ptr(t)
+    for a, t in enumerate(_three(tangent)):
+        sin.tangent[a] = _ptr(t)
+    sin.alpha = _ptr(alpha)
+    sout = StepOut()
+    for a, t in enumerate(_three(S)):
+        sout.S[a] = _ptr(t)
+    for a, t in enumerate(_three(F)):
+        sout.F[a] = _ptr(t)
+    sout.totals = C.cast(_ptr(totals), _dp) if totals is not None else None
+    sout.status = C.cast(_ptr(status), C.POINTER(C.c_int)) if status is not None else None
+    return sin, sout
+
+
+class Grid:
+    """One actuator-line instance: al_create_grid / al_load_beams /
+    al_sample_drag_spread / al_destroy."""
+
+    def __init__(self, grid):
+        self.spec = grid
+        self.desc = GridDesc(int(grid.nx), int(grid.ny), int(grid.nz), float(grid.h),
+                             (C.c_double * 3)(*map(float, grid.origin)),
+                             AL_FP64 if grid.precision == "fp64" else AL_FP32, int(bool(grid.has_alpha)),
+                             float(grid.rho1), float(grid.rho2), float(grid.rho_const))
+        h = _vp()
+        check(lib().al_create_grid(C.byref(self.desc), C.byref(h)), "al_create_grid")
+        self.h = h
+        self.n_points = 0
+        self.n_lines = 0
+
+    def load_beams(self, beams) -> None:
+        ba = BeamArrays(beams)
+        check(lib().al_load_beams(self.h, C.byref(ba.desc)), "al_load_beams")
+        self.n_points = int(beams.n_points)
+        self.n_lines = int(beams.n_lines)
+
+    def step(self, U, P, Pdot, S, F, *, alpha=None, P_spread=None, tangent=None, totals=None,
+             status=None, stream=None) -> None:
+        """Enqueue one coupling step.  U, S: (3, N_c); P, Pdot, F, P_spread,
+        tangent: (3, N_p) CUDA tensors of the grid precision (or sequences
+        of three 1-D tensors); totals: float64[6]; status: int32[16]."""
+        sin, sout = step_descriptors(U, P, Pdot, S, F, alpha=alpha, P_spread=P_spread, tangent=tangent,
+                                     totals=totals, status=status)
+        check(lib().al_sample_drag_spread(self.h, C.byref(sin), C.byref(sout), _stream_ptr(stream)),
+              "al_sample_drag_spread")
+
+    def get_state(self, f_prev, stream=None) -> bool:
+        hp = C.c_int(0)
+        check(lib().al_get_state(self.h, _ptr(f_prev), C.byref(hp), _stream_ptr(stream)), "al_get_state")
+        return bool(hp.value)
+
+    def set_state(self, f_prev, has_prev: bool, stream=None) -> None:
+        check(lib().al_set_state(self.h, _ptr(f_prev), int(bool(has_prev)), _stream_ptr(stream)), "al_set_state")
+
+    def trace(self, on: bool = True) -> None:
+        check(lib().al_trace_enable(self.h, int(bool(on))), "al_trace_enable")
+
+    def trace_last(self):
+        """Per-phase milliseconds of the last step (points, mask, weights,
+        normalise, spread, totals); waits for that step."""
+        ms = (C.c_float * TRACE_N)()
+        check(lib().al_trace_last(self.h, ms), "al_trace_last")
+        return list(ms)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lib().al_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Instance:
+    """A Grid plus device-resident copies of one workload's inputs and its
+    output buffers (data movement only)."""
+
+    def __init__(self, wl, device="cuda"):
+        import torch
+        self.wl = wl
+        self.device = device
+        dt = torch.float64 if wl.grid.precision == "fp64" else torch.float32
+        self.dtype = dt
+        s = wl.step
+
+        def dev(a):
+            return None if a is None else torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(device)
+
+        self.U, self.P, self.Pdot = dev(s.U), dev(s.P), dev(s.Pdot)
+        self.alpha, self.P_spread, self.tangent = dev(s.alpha), dev(s.P_spread), dev(s.tangent)
+        self.S = torch.empty((3, wl.grid.n_cells), dtype=dt, device=device)
+        self.F = torch.empty((3, max(wl.beams.n_points, 1)), dtype=dt, device=device)
+        self.totals = torch.zeros(6, dtype=torch.float64, device=device)
+        self.status = torch.zeros(AL_STATUS_N, dtype=torch.int32, device=device)
+        self.grid = Grid(wl.grid)
+        self.grid.load_beams(wl.beams)
+
+    def step(self, stream=None):
+        self.grid.step(self.U, self.P, self.Pdot, self.S, self.F, alpha=self.alpha, P_spread=self.P_spread,
+                       tangent=self.tangent if self.wl.beams.tangents_given else None,
+                       totals=self.totals, status=self.status, stream=stream)
+
+    def set_points(self, P=None, Pdot=None, P_spread=None):
+        import torch
+        if P is not None:
+            self.P.copy_(torch.as_tensor(np.ascontiguousarray(P), dtype=self.dtype))
+        if Pdot is not None:
+            self.Pdot.copy_(torch.as_tensor(np.ascontiguousarray(Pdot), dtype=self.dtype))
+        if P_spread is not None:
+            self.P_spread.copy_(torch.as_tensor(np.ascontiguousarray(P_spread), dtype=self.dtype))
+
+    def descriptors(self):
+        return step_descriptors(self.U, self.P, self.Pdot, self.S, self.F, alpha=self.alpha,
+                                P_spread=self.P_spread,
+                                tangent=self.tangent if self.wl.beams.tangents_given else None,
+                                totals=self.totals, status=self.status)
+
+    def close(self):
+        self.grid.close()
+
+
+class Batch:
+    """al_batch_*: many instances advanced by one launch per phase."""
+
+    def __init__(self, instances, use_graph=True, spread_ctas_per_sm=0):
+        h = _vp()
+        check(lib().al_batch_create(C.byref(h)), "al_batch_create")
+        self.h = h
+        self.instances = list(instances)
+        self._desc = []
+        for inst in self.instances:
+            sin, sout = inst.descriptors()
+            self._desc.append((sin, sout))
+            check(lib().al_batch_add(self.h, inst.grid.h, C.byref(sin), C.byref(sout)), "al_batch_add")
+        check(lib().al_batch_commit(self.h, int(bool(use_graph)), int(spread_ctas_per_sm)), "al_batch_commit")
+
+    def run(self, stream=None):
+        check(lib().al_batch_run(self.h, _stream_ptr(stream)), "al_batch_run")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().al_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,703 @@
+// al_api.cu -- host side of the C ABI declared in include/al.h.
+//
+// Owns the per-instance device scratch, validates descriptors on the host,
+// and enqueues the kernels of al_kernels.cuh on the caller's stream.  No
+// allocation, no host synchronisation and no CPU arithmetic of the method
+// happens inside al_sample_drag_spread.
+#include "al.h"
+#include "al_kernels.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <algorithm>
+#include <vector>
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e, const char *what) {
+    snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? AL_ERR_OOM : AL_ERR_CUDA;
+}
+
+#define AL_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+template <typename P>
+cudaError_t dalloc(P **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc((void **)p, n * sizeof(P));
+}
+
+void split_ff(double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+}  // namespace
+
+struct al_grid_s {
+    al_grid_desc d{};
+    int device = 0;
+    al::GridC gc{};
+    size_t esize = 4;                 // bytes per field element
+
+    // lines
+    bool loaded = false;
+    int n_lines = 0, n_points = 0, mask_words = 0;
+    int *d_line_off = nullptr, *d_line_of = nullptr;
+    double *d_d = nullptr, *d_cdn = nullptr, *d_cdt = nullptr, *d_eps = nullptr, *d_ell = nullptr,
+           *d_af = nullptr, *d_cvl = nullptr;
+    al_beam_desc bd{};
+
+    // per-point scratch (element type per precision)
+    void *fprev = nullptr, *uhi = nullptr, *segD = nullptr, *segIl2 = nullptr, *nodeM = nullptr,
+         *fhat = nullptr;
+    float *ulo = nullptr, *nodeTau = nullptr;
+    double *segWa = nullptr, *segWb = nullptr, *w = nullptr, *lineF = nullptr;
+    al::LineG *lines = nullptr;
+    uint32_t *mask = nullptr;
+    int *zeroList = nullptr;
+
+    // per-grid scratch
+    double *brickSum = nullptr;
+    int *zeroCount = nullptr;
+    double *depSum = nullptr;
+    int *statusInt = nullptr;
+    double *totalsInt = nullptr;
+    int *hasPrev = nullptr;           // device flag: f_prev is valid
+
+    // tracing
+    bool trace = false;
+    cudaEvent_t ev[AL_TRACE_N + 1] = {};
+};
+
+static void trace_mark(al_grid g, int i, cudaStream_t st) {
+    if (g->trace) cudaEventRecord(g->ev[i], st);
+}
+
+static void free_beams(al_grid g) {
+    void *ptrs[] = {g->d_line_off, g->d_line_of, g->d_d, g->d_cdn, g->d_cdt, g->d_eps, g->d_ell, g->d_af,
+                    g->d_cvl, g->fprev, g->uhi, g->segD, g->segIl2, g->nodeM, g->fhat, g->ulo,
+                    g->nodeTau, g->segWa, g->segWb, g->w, g->lineF, g->lines, g->mask, g->zeroList};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    g->d_line_off = g->d_line_of = nullptr;
+    g->d_d = g->d_cdn = g->d_cdt = g->d_eps = g->d_ell = g->d_af = g->d_cvl = nullptr;
+    g->fprev = g->uhi = g->segD = g->segIl2 = g->nodeM = g->fhat = nullptr;
+    g->ulo = g->nodeTau = nullptr;
+    g->segWa = g->segWb = g->w = g->lineF = nullptr;
+    g->lines = nullptr;
+    g->mask = nullptr;
+    g->zeroList = nullptr;
+    g->loaded = false;
+    g->n_lines = g->n_points = g->mask_words = 0;
+}
+
+extern "C" const char *al_error_string(int code) {
+    switch (code) {
+    case AL_OK: return "ok";
+    case AL_ERR_ARG: return "invalid argument";
+    case AL_ERR_CUDA: return "CUDA runtime error";
+    case AL_ERR_OOM: return "out of device memory";
+    case AL_ERR_STATE: return "call out of order";
+    case AL_ERR_TIMEOUT: return "bounded wait expired";
+    case AL_ERR_CAPACITY: return "request exceeds a fixed capacity";
+    default: return "unknown status";
+    }
+}
+
+extern "C" const char *al_last_cuda_error(void) { return g_cuda_err; }
+
+extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
+    if (!desc || !out) return AL_ERR_ARG;
+    *out = nullptr;
+    const al_grid_desc &d = *desc;
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1) return AL_ERR_ARG;
+    if (!(d.dx > 0.0) || !std::isfinite(d.dx)) return AL_ERR_ARG;
+    if (d.precision != AL_FP32 && d.precision != AL_FP64) return AL_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(d.origin[a])) return AL_ERR_ARG;
+    if (d.has_alpha && (!(d.rho1 > 0.0) || !(d.rho2 > 0.0))) return AL_ERR_ARG;
+    if (!d.has_alpha && !(d.rho_const > 0.0)) return AL_ERR_ARG;
+    const long long ncell = (long long)d.nx * d.ny * d.nz;
+    if (ncell > (1LL << 40)) return AL_ERR_ARG;
+
+    al_grid g = new (std::nothrow) al_grid_s();
+    if (!g) return AL_ERR_OOM;
+    g->d = d;
+    cudaGetDevice(&g->device);
+    g->esize = d.precision == AL_FP64 ? 8 : 4;
+    al::GridC &c = g->gc;
+    c.nx = d.nx; c.ny = d.ny; c.nz = d.nz;
+    c.ncell = ncell;
+    c.nbx = (d.nx + al::BX - 1) / al::BX;
+    c.nby = (d.ny + al::BY - 1) / al::BY;
+    c.nbz = (d.nz + al::BZ - 1) / al::BZ;
+    c.nbrick = (long long)c.nbx * c.nby * c.nbz;
+    c.h = d.dx;
+    c.V = d.dx * d.dx * d.dx;
+    for (int a = 0; a < 3; ++a) {
+        c.o[a] = d.origin[a];
+        split_ff(d.origin[a], c.o_hi[a], c.o_lo[a]);
+    }
+    split_ff(1.0 / d.dx, c.ih_hi, c.ih_lo);
+    c.has_alpha = d.has_alpha ? 1 : 0;
+    c.rho1 = d.rho1; c.rho2 = d.rho2; c.rho_const = d.rho_const;
+
+    cudaError_t e;
+    if ((e = dalloc(&g->brickSum, 3 * (size_t)c.nbrick)) != cudaSuccess ||
+        (e = dalloc(&g->zeroCount, 1)) != cudaSuccess || (e = dalloc(&g->depSum, 3)) != cudaSuccess ||
+        (e = dalloc(&g->statusInt, AL_STATUS_N)) != cudaSuccess || (e = dalloc(&g->totalsInt, 6)) != cudaSuccess ||
+        (e = dalloc(&g->hasPrev, 1)) != cudaSuccess) {
+        int rc = cuda_fail(e, "cudaMalloc");
+        al_destroy(g);
+        return rc;
+    }
+    *out = g;
+    return AL_OK;
+}
+
+extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
+    if (!g || !bp) return AL_ERR_ARG;
+    const al_beam_desc &b = *bp;
+    if (b.n_lines < 0) return AL_ERR_ARG;
+    if (b.n_lines > 0 && (!b.line_off || !b.d || !b.cdn || !b.cdt || !b.eps || !b.ell_s || !b.alpha_f))
+        return AL_ERR_ARG;
+    if (b.sample_mode != AL_SAMPLE_TRILINEAR && b.sample_mode != AL_SAMPLE_CELL) return AL_ERR_ARG;
+    if (b.drag_mode != AL_DRAG_DISCRETE && b.drag_mode != AL_DRAG_SPLIT) return AL_ERR_ARG;
+    if (!(b.tau >= 0.0)) return AL_ERR_ARG;
+    const double npn = std::sqrt(b.n_p[0] * b.n_p[0] + b.n_p[1] * b.n_p[1] + b.n_p[2] * b.n_p[2]);
+    if (!(npn == 0.0 || std::fabs(npn - 1.0) < 1e-9)) return AL_ERR_ARG;
+    int np = 0;
+    if (b.n_lines > 0) {
+        if (b.line_off[0] != 0) return AL_ERR_ARG;
+        for (int l = 0; l < b.n_lines; ++l) {
+            if (b.line_off[l + 1] < b.line_off[l]) return AL_ERR_ARG;
+            if (!(b.eps[l] > 0.0) || !(b.ell_s[l] >= 0.0) || !(b.alpha_f[l] > 0.0 && b.alpha_f[l] <= 1.0) ||
+                !(b.d[l] >= 0.0) || !std::isfinite(b.cdn[l]) || !std::isfinite(b.cdt[l]))
+                return AL_ERR_ARG;
+            // the kernel support 3 eps must span fewer than 2^20 cells
+            if (3.0 * b.eps[l] / g->d.dx > 1048576.0) return AL_ERR_ARG;
+        }
+        np = b.line_off[b.n_lines];
+        if (np > 0 && !b.cv_len) return AL_ERR_ARG;
+        for (int i = 0; i < np; ++i)
+            if (!(b.cv_len[i] >= 0.0) || !std::isfinite(b.cv_len[i])) return AL_ERR_ARG;
+    }
+    AL_CUDA(cudaDeviceSynchronize());
+    free_beams(g);
+    g->n_lines = b.n_lines;
+    g->n_points = np;
+    g->mask_words = (b.n_lines + 31) / 32;
+    g->bd = b;
+    const size_t es = g->esize, n3 = 3 * (size_t)np;
+    const size_t nl = (size_t)b.n_lines;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto **p, size_t n) {
+        if (e == cudaSuccess) e = dalloc(p, n);
+    };
+    auto AB = [&](void **p, size_t n) {
+        if (e == cudaSuccess) e = cudaMalloc(p, (n ? n : 1) * es);
+    };
+    A(&g->d_line_off, nl + 1);
+    A(&g->d_line_of, (size_t)np);
+    A(&g->d_d, nl); A(&g->d_cdn, nl); A(&g->d_cdt, nl); A(&g->d_eps, nl); A(&g->d_ell, nl); A(&g->d_af, nl);
+    A(&g->d_cvl, (size_t)np);
+    AB(&g->fprev, n3); AB(&g->uhi, n3); AB(&g->segD, n3); AB(&g->segIl2, (size_t)np); AB(&g->nodeM, n3);
+    AB(&g->fhat, n3);
+    A(&g->ulo, n3); A(&g->nodeTau, (size_t)np);
+    A(&g->segWa, (size_t)np); A(&g->segWb, (size_t)np); A(&g->w, (size_t)np); A(&g->lineF, 3 * nl);
+    A(&g->lines, nl);
+    A(&g->mask, (size_t)g->gc.nbrick * g->mask_words);
+    A(&g->zeroList, (size_t)np);
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "cudaMalloc");
+        free_beams(g);
+        return rc;
+    }
+    std::vector<int> off(nl + 1, 0), of((size_t)np);
+    if (b.n_lines > 0) {
+        for (size_t l = 0; l <= nl; ++l) off[l] = b.line_off[l];
+        for (size_t l = 0; l < nl; ++l)
+            for (int i = off[l]; i < off[l + 1]; ++i) of[i] = (int)l;
+    }
+    AL_CUDA(cudaMemcpy(g->d_line_off, off.data(), (nl + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    if (np) {
+        AL_CUDA(cudaMemcpy(g->d_line_of, of.data(), np * sizeof(int), cudaMemcpyHostToDevice));
+        AL_CUDA(cudaMemcpy(g->d_cvl, b.cv_len, np * sizeof(double), cudaMemcpyHostToDevice));
+        AL_CUDA(cudaMemset(g->fprev, 0, n3 * es));
+        AL_CUDA(cudaMemset(g->ulo, 0, n3 * sizeof(float)));
+    }
+    if (nl) {
+        AL_CUDA(cudaMemcpy(g->d_d, b.d, nl * sizeof(double), cudaMemcpyHostToDevice));
+        AL_CUDA(cudaMemcpy(g->d_cdn, b.cdn, nl * sizeof(double), cudaMemcpyHostToDevice));
+        AL_CUDA(cudaMemcpy(g->d_cdt, b.cdt, nl * sizeof(double), cudaMemcpyHostToDevice));
+        AL_CUDA(cudaMemcpy(g->d_eps, b.eps, nl * sizeof(double), cudaMemcpyHostToDevice));
+        AL_CUDA(cudaMemcpy(g->d_ell, b.ell_s, nl * sizeof(double), cudaMemcpyHostToDevice));
+        AL_CUDA(cudaMemcpy(g->d_af, b.alpha_f, nl * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    AL_CUDA(cudaMemset(g->mask, 0, ((size_t)g->gc.nbrick * g->mask_words ? (size_t)g->gc.nbrick * g->mask_words : 1) * sizeof(uint32_t)));
+    AL_CUDA(cudaMemset(g->hasPrev, 0, sizeof(int)));
+    g->loaded = true;
+    return AL_OK;
+}
+
+template <typename T>
+static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out *out) {
+    using namespace al;
+    const int np = g->n_points;
+    Inst<T> I{};
+    StepPtrs<T> &p = I.p;
+    for (int a = 0; a < 3; ++a) {
+        p.U[a] = (const T *)in->U[a];
+        p.P[a] = (const T *)in->P[a];
+        p.Pdot[a] = (const T *)in->Pdot[a];
+        p.Ps[a] = (const T *)(in->P_spread[a] ? in->P_spread[a] : in->P[a]);
+        p.tan[a] = (const T *)in->tangent[a];
+        p.S[a] = (T *)out->S[a];
+        p.F[a] = (T *)out->F[a];
+    }
+    p.alpha = (const T *)in->alpha;
+    p.np = np;
+    Scratch<T> &sc = I.sc;
+    sc.fprev = (T *)g->fprev; sc.uhi = (T *)g->uhi; sc.ulo = g->ulo; sc.segD = (T *)g->segD;
+    sc.segIl2 = (T *)g->segIl2; sc.nodeM = (T *)g->nodeM; sc.nodeTau = g->nodeTau;
+    sc.segWa = g->segWa; sc.segWb = g->segWb; sc.w = g->w; sc.fhat = (T *)g->fhat; sc.lineF = g->lineF;
+    sc.lines = g->lines; sc.mask = g->mask; sc.brickSum = g->brickSum; sc.zeroList = g->zeroList;
+    sc.zeroCount = g->zeroCount; sc.depSum = g->depSum; sc.hasPrev = g->hasPrev;
+    BeamsC &bc = I.b;
+    bc.n_lines = g->n_lines; bc.n_points = np; bc.mask_words = g->mask_words;
+    bc.line_off = g->d_line_off; bc.line_of = g->d_line_of;
+    bc.d = g->d_d; bc.cdn = g->d_cdn; bc.cdt = g->d_cdt; bc.eps = g->d_eps; bc.ell_s = g->d_ell;
+    bc.alpha_f = g->d_af; bc.cv_len = g->d_cvl;
+    for (int a = 0; a < 3; ++a) { bc.n_p[a] = g->bd.n_p[a]; bc.g_up[a] = g->bd.g_up[a]; }
+    bc.tau = g->bd.tau; bc.sample_mode = g->bd.sample_mode; bc.drag_mode = g->bd.drag_mode;
+    bc.tangents_given = g->bd.tangents_given;
+    I.g = g->gc;
+    I.status = out->status ? out->status : g->statusInt;
+    I.totals = out->totals ? out->totals : g->totalsInt;
+    return I;
+}
+
+template <typename T>
+static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cudaStream_t st) {
+    using namespace al;
+    const al::Inst<T> I = make_inst<T>(g, in, out);
+    const GridC &gc = I.g;
+    const BeamsC &bc = I.b;
+    const Scratch<T> &sc = I.sc;
+    const StepPtrs<T> &p = I.p;
+    int *status = I.status;
+    const int np = g->n_points;
+
+    trace_mark(g, 0, st);
+    AL_CUDA(cudaMemsetAsync(g->zeroCount, 0, sizeof(int), st));
+    AL_CUDA(cudaMemsetAsync(g->depSum, 0, 3 * sizeof(double), st));
+    const int nb = (np + 255) / 256;
+    if (np > 0) {
+        k_points<T><<<nb, 256, 0, st>>>(gc, bc, p, sc, status);
+        k_segments<T><<<nb, 256, 0, st>>>(bc, sc);
+    }
+    if (g->n_lines > 0) k_lines<T><<<(g->n_lines + 7) / 8, 256, 0, st>>>(gc, bc, sc, p, status);
+    trace_mark(g, 1, st);
+    if (np > 0) k_mask<T><<<nb, 256, 0, st>>>(gc, bc, sc);
+    trace_mark(g, 2, st);
+    if (np > 0) k_weights<T><<<(unsigned)(((long long)np * 32 + 127) / 128), 128, 0, st>>>(gc, bc, sc, p, status);
+    trace_mark(g, 3, st);
+    if (np > 0) k_normalise<T><<<nb, 256, 0, st>>>(bc, sc, p, status);
+    trace_mark(g, 4, st);
+    const size_t smem = sizeof(SpreadSmem<T>);
+    k_spread<T><<<(unsigned)gc.nbrick, SPREAD_THREADS, smem, st>>>(gc, bc, sc, p, status);
+    trace_mark(g, 5, st);
+    if (np > 0) k_deposit<T><<<1, 1, 0, st>>>(gc, bc, sc, p, status);
+    k_totals<T><<<1, 256, 0, st>>>(gc, bc, sc, I.totals);
+    trace_mark(g, 6, st);
+    AL_CUDA(cudaGetLastError());
+    return AL_OK;
+}
+
+extern "C" int al_sample_drag_spread(al_grid g, const al_step_in *in, const al_step_out *out, void *stream) {
+    if (!g || !in || !out) return AL_ERR_ARG;
+    if (!g->loaded) return AL_ERR_STATE;
+    for (int a = 0; a < 3; ++a)
+        if (!in->U[a] || !out->S[a]) return AL_ERR_ARG;
+    if (g->d.has_alpha && !in->alpha) return AL_ERR_ARG;
+    if (g->n_points > 0) {
+        for (int a = 0; a < 3; ++a) {
+            if (!in->P[a] || !in->Pdot[a] || !out->F[a]) return AL_ERR_ARG;
+            if (g->bd.tangents_given && !in->tangent[a]) return AL_ERR_ARG;
+        }
+        const bool sp = in->P_spread[0] != nullptr;
+        if ((in->P_spread[1] != nullptr) != sp || (in->P_spread[2] != nullptr) != sp) return AL_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    return g->d.precision == AL_FP64 ? step_impl<double>(g, in, out, st) : step_impl<float>(g, in, out, st);
+}
+
+extern "C" int al_trace_enable(al_grid g, int on) {
+    if (!g) return AL_ERR_ARG;
+    if (on && !g->trace) {
+        for (int i = 0; i <= AL_TRACE_N; ++i) AL_CUDA(cudaEventCreate(&g->ev[i]));
+        g->trace = true;
+    } else if (!on && g->trace) {
+        cudaDeviceSynchronize();
+        for (int i = 0; i <= AL_TRACE_N; ++i) cudaEventDestroy(g->ev[i]);
+        g->trace = false;
+    }
+    return AL_OK;
+}
+
+extern "C" int al_trace_last(al_grid g, float *ms) {
+    if (!g || !ms) return AL_ERR_ARG;
+    if (!g->trace) return AL_ERR_STATE;
+    AL_CUDA(cudaEventSynchronize(g->ev[AL_TRACE_N]));
+    for (int i = 0; i < AL_TRACE_N; ++i) AL_CUDA(cudaEventElapsedTime(&ms[i], g->ev[i], g->ev[i + 1]));
+    return AL_OK;
+}
+
+extern "C" int al_destroy(al_grid g) {
+    if (!g) return AL_ERR_ARG;
+    cudaDeviceSynchronize();
+    if (g->trace) al_trace_enable(g, 0);
+    free_beams(g);
+    void *ptrs[] = {g->brickSum, g->zeroCount, g->depSum, g->statusInt, g->totalsInt, g->hasPrev};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete g;
+    return AL_OK;
+}
+
+extern "C" int al_get_state(al_grid g, void *f_prev_dev, int *has_prev, void *stream) {
+    if (!g || !has_prev) return AL_ERR_ARG;
+    if (!g->loaded) return AL_ERR_STATE;
+    if (g->n_points > 0 && !f_prev_dev) return AL_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (g->n_points > 0)
+        AL_CUDA(cudaMemcpyAsync(f_prev_dev, g->fprev, 3 * (size_t)g->n_points * g->esize, cudaMemcpyDeviceToDevice, st));
+    int hp = 0;
+    AL_CUDA(cudaMemcpyAsync(&hp, g->hasPrev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    AL_CUDA(cudaStreamSynchronize(st));
+    *has_prev = hp;
+    return AL_OK;
+}
+
+extern "C" int al_set_state(al_grid g, const void *f_prev_dev, int has_prev, void *stream) {
+    if (!g) return AL_ERR_ARG;
+    if (!g->loaded) return AL_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (g->n_points > 0 && has_prev) {
+        if (!f_prev_dev) return AL_ERR_ARG;
+        AL_CUDA(cudaMemcpyAsync(g->fprev, f_prev_dev, 3 * (size_t)g->n_points * g->esize,
+                                cudaMemcpyDeviceToDevice, st));
+    }
+    AL_CUDA(cudaMemsetAsync(g->hasPrev, has_prev ? 0x01 : 0, 1, st));
+    AL_CUDA(cudaMemsetAsync((char *)g->hasPrev + 1, 0, sizeof(int) - 1, st));
+    return AL_OK;
+}
+
+extern "C" int al_sizes(al_grid g, long long *n_cells, long long *n_points, int *n_lines) {
+    if (!g) return AL_ERR_ARG;
+    if (n_cells) *n_cells = g->gc.ncell;
+    if (n_points) *n_points = g->n_points;
+    if (n_lines) *n_lines = g->n_lines;
+    return AL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched form
+// ---------------------------------------------------------------------------
+
+struct al_batch_s {
+    std::vector<al_grid> grids;
+    std::vector<al_step_in> ins;
+    std::vector<al_step_out> outs;
+    int precision = -1;
+    int capacity = 0;                          // slots (>= added instances)
+    bool committed = false;
+    void *h_inst = nullptr;                    // pinned staging of slot descriptors
+    std::vector<cudaEvent_t> slot_ev;
+    bool use_graph = false;
+    int n = 0;
+    void *d_inst = nullptr;                   // Inst<T>[n]
+    long long *d_pre = nullptr;               // 4 prefix arrays of n + 1: points, lines, bricks, points(warps)
+    long long tot_pts = 0, tot_lines = 0, tot_bricks = 0;
+    int spread_grid = 0, pt_grid = 0;
+    // subset runs: a ring of pinned host / device work lists
+    static constexpr int RING = 8;
+    int maxn = 0;
+    void *h_ring = nullptr;                   // pinned: RING x (sel[maxn] + pre[3 (maxn+1)])
+    void *d_ring = nullptr;
+    cudaEvent_t ring_ev[RING] = {};
+    int ring_pos = 0;
+    std::vector<long long> cnt_pts, cnt_lines, cnt_bricks;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+
+    static size_t slot_bytes(int n) {
+        size_t a = ((size_t)n * sizeof(int) + 15) & ~(size_t)15;
+        return a + 3 * (size_t)(n + 1) * sizeof(long long);
+    }
+};
+
+extern "C" int al_batch_create(al_batch *out) {
+    if (!out) return AL_ERR_ARG;
+    *out = new (std::nothrow) al_batch_s();
+    return *out ? AL_OK : AL_ERR_OOM;
+}
+
+extern "C" int al_batch_add(al_batch b, al_grid g, const al_step_in *in, const al_step_out *out) {
+    if (!b || !g || !in || !out) return AL_ERR_ARG;
+    if (b->committed) return AL_ERR_STATE;
+    if (!g->loaded) return AL_ERR_STATE;
+    if (b->precision >= 0 && b->precision != g->d.precision) return AL_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!in->U[a] || !out->S[a]) return AL_ERR_ARG;
+    if (g->d.has_alpha && !in->alpha) return AL_ERR_ARG;
+    if (g->n_points > 0)
+        for (int a = 0; a < 3; ++a)
+            if (!in->P[a] || !in->Pdot[a] || !out->F[a] || (g->bd.tangents_given && !in->tangent[a]))
+                return AL_ERR_ARG;
+    b->precision = g->d.precision;
+    b->grids.push_back(g);
+    b->ins.push_back(*in);
+    b->outs.push_back(*out);
+    return AL_OK;
+}
+
+template <typename T>
+static int batch_commit_t(al_batch b, int spread_ctas_per_sm) {
+    using namespace al;
+    const int added = (int)b->grids.size();
+    const int n = std::max(added, b->capacity);
+    b->grids.resize(n, nullptr);
+    b->ins.resize(n, al_step_in{});
+    b->outs.resize(n, al_step_out{});
+    std::vector<Inst<T>> h(n);
+    std::vector<long long> pre(4 * (size_t)(n + 1), 0);
+    for (int q = 0; q < n; ++q) {
+        const bool used = b->grids[q] != nullptr;
+        if (used) h[q] = make_inst<T>(b->grids[q], &b->ins[q], &b->outs[q]);
+        else memset((void *)&h[q], 0, sizeof(Inst<T>));
+        pre[0 * (n + 1) + q + 1] = pre[0 * (n + 1) + q] + (used ? b->grids[q]->n_points : 0);
+        pre[1 * (n + 1) + q + 1] = pre[1 * (n + 1) + q] + (used ? b->grids[q]->n_lines : 0);
+        pre[2 * (n + 1) + q + 1] = pre[2 * (n + 1) + q] + (used ? b->grids[q]->gc.nbrick : 0);
+    }
+    AL_CUDA(cudaMallocHost(&b->h_inst, sizeof(Inst<T>) * n));
+    b->slot_ev.assign(n, nullptr);
+    for (int q = 0; q < n; ++q) AL_CUDA(cudaEventCreateWithFlags(&b->slot_ev[q], cudaEventDisableTiming));
+    b->tot_pts = pre[n];
+    b->tot_lines = pre[(n + 1) + n];
+    b->tot_bricks = pre[2 * (n + 1) + n];
+    b->cnt_pts.resize(n); b->cnt_lines.resize(n); b->cnt_bricks.resize(n);
+    for (int q = 0; q < n; ++q) {
+        const bool used = b->grids[q] != nullptr;
+        b->cnt_pts[q] = used ? b->grids[q]->n_points : 0;
+        b->cnt_lines[q] = used ? b->grids[q]->n_lines : 0;
+        b->cnt_bricks[q] = used ? b->grids[q]->gc.nbrick : 0;
+    }
+    b->maxn = n;
+    const size_t slot = al_batch_s::slot_bytes(n);
+    AL_CUDA(cudaMallocHost(&b->h_ring, slot * al_batch_s::RING));
+    AL_CUDA(cudaMalloc(&b->d_ring, slot * al_batch_s::RING));
+    for (int r = 0; r < al_batch_s::RING; ++r) AL_CUDA(cudaEventCreateWithFlags(&b->ring_ev[r], cudaEventDisableTiming));
+    AL_CUDA(cudaMalloc(&b->d_inst, sizeof(Inst<T>) * (n ? n : 1)));
+    AL_CUDA(cudaMalloc(&b->d_pre, sizeof(long long) * pre.size()));
+    AL_CUDA(cudaMemcpy(b->d_inst, h.data(), sizeof(Inst<T>) * n, cudaMemcpyHostToDevice));
+    AL_CUDA(cudaMemcpy(b->d_pre, pre.data(), sizeof(long long) * pre.size(), cudaMemcpyHostToDevice));
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    AL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_spread<T>, SPREAD_THREADS, sizeof(SpreadSmem<T>)));
+    if (occ < 1) occ = 1;
+    const int per = spread_ctas_per_sm > 0 ? (spread_ctas_per_sm < occ ? spread_ctas_per_sm : occ) : occ;
+    b->spread_grid = (int)std::min<long long>((long long)nsm * per, std::max<long long>(b->tot_bricks, 1));
+    b->pt_grid = nsm * 8;
+    return AL_OK;
+}
+
+// enqueue one step of n selected instances (sel NULL: all); pre: device
+// prefix arrays (points, lines, bricks) of the selection; totals: host copies
+template <typename T>
+static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const long long *pre, int n,
+                           long long tot_pts, long long tot_lines, long long tot_bricks) {
+    using namespace al;
+    const Inst<T> *I = (const Inst<T> *)b->d_inst;
+    const long long *pp = pre, *pl = pre + (n + 1), *pb = pre + 2 * (n + 1);
+    auto grid_for = [&](long long items, int per_block) {
+        long long g = (items + per_block - 1) / per_block;
+        return (unsigned)std::max<long long>(1, std::min<long long>(g, (long long)b->pt_grid * 4));
+    };
+    kb_reset<T><<<(n + 127) / 128, 128, 0, st>>>(I, sel, n);
+    if (tot_pts > 0) {
+        kb_points<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
+        kb_segments<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
+    }
+    if (tot_lines > 0) kb_lines<T><<<grid_for(tot_lines, 8), 256, 0, st>>>(I, sel, pl, n);
+    if (tot_pts > 0) {
+        kb_mask<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
+        kb_weights<T><<<grid_for(tot_pts, 4), 128, 0, st>>>(I, sel, pp, n);
+        kb_normalise<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
+    }
+    if (tot_bricks > 0) {
+        const int gs = (int)std::min<long long>(b->spread_grid, tot_bricks);
+        kb_spread<T><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T>), st>>>(I, sel, pb, n);
+    }
+    kb_deposit<T><<<(n + 127) / 128, 128, 0, st>>>(I, sel, n);
+    kb_totals<T><<<std::max(1, std::min(n, 1024)), 256, 0, st>>>(I, sel, n);
+    AL_CUDA(cudaGetLastError());
+    return AL_OK;
+}
+
+extern "C" int al_batch_reserve(al_batch b, int n_slots, int precision) {
+    if (!b || n_slots < 0 || (precision != AL_FP32 && precision != AL_FP64)) return AL_ERR_ARG;
+    if (b->committed) return AL_ERR_STATE;
+    if (b->precision >= 0 && b->precision != precision) return AL_ERR_ARG;
+    b->precision = precision;
+    b->capacity = n_slots;
+    return AL_OK;
+}
+
+template <typename T>
+static int batch_assign_t(al_batch b, int slot, al_grid g, const al_step_in *in, const al_step_out *out,
+                          cudaStream_t st) {
+    using namespace al;
+    AL_CUDA(cudaEventSynchronize(b->slot_ev[slot]));       // staging of this slot is free again
+    Inst<T> *h = (Inst<T> *)b->h_inst + slot;
+    if (g) *h = make_inst<T>(g, in, out);
+    else memset((void *)h, 0, sizeof(Inst<T>));
+    AL_CUDA(cudaMemcpyAsync((Inst<T> *)b->d_inst + slot, h, sizeof(Inst<T>), cudaMemcpyHostToDevice, st));
+    AL_CUDA(cudaEventRecord(b->slot_ev[slot], st));
+    b->grids[slot] = g;
+    if (g) { b->ins[slot] = *in; b->outs[slot] = *out; }
+    b->cnt_pts[slot] = g ? g->n_points : 0;
+    b->cnt_lines[slot] = g ? g->n_lines : 0;
+    b->cnt_bricks[slot] = g ? g->gc.nbrick : 0;
+    return AL_OK;
+}
+
+extern "C" int al_batch_assign(al_batch b, int slot, al_grid g, const al_step_in *in, const al_step_out *out,
+                               void *stream) {
+    if (!b) return AL_ERR_ARG;
+    if (!b->committed) return AL_ERR_STATE;
+    if (slot < 0 || slot >= b->n) return AL_ERR_ARG;
+    if (g) {
+        if (!in || !out || !g->loaded || g->d.precision != b->precision) return AL_ERR_ARG;
+        for (int a = 0; a < 3; ++a)
+            if (!in->U[a] || !out->S[a]) return AL_ERR_ARG;
+        if (g->d.has_alpha && !in->alpha) return AL_ERR_ARG;
+        if (g->n_points > 0)
+            for (int a = 0; a < 3; ++a)
+                if (!in->P[a] || !in->Pdot[a] || !out->F[a] || (g->bd.tangents_given && !in->tangent[a]))
+                    return AL_ERR_ARG;
+    }
+    if (b->use_graph && b->exec) return AL_ERR_STATE;         // a captured graph holds the old table
+    cudaStream_t st = (cudaStream_t)stream;
+    return b->precision == AL_FP64 ? batch_assign_t<double>(b, slot, g, in, out, st)
+                                   : batch_assign_t<float>(b, slot, g, in, out, st);
+}
+
+extern "C" int al_batch_commit(al_batch b, int use_graph, int spread_ctas_per_sm) {
+    if (!b) return AL_ERR_ARG;
+    if (b->committed) return AL_ERR_STATE;
+    if (b->grids.empty() && b->capacity == 0) return AL_ERR_ARG;
+    if (b->precision < 0) return AL_ERR_ARG;
+    b->n = std::max((int)b->grids.size(), b->capacity);
+    int rc = b->precision == AL_FP64 ? batch_commit_t<double>(b, spread_ctas_per_sm)
+                                     : batch_commit_t<float>(b, spread_ctas_per_sm);
+    if (rc != AL_OK) return rc;
+    b->use_graph = use_graph != 0;
+    b->committed = true;
+    return AL_OK;
+}
+
+extern "C" int al_batch_run(al_batch b, void *stream) {
+    if (!b) return AL_ERR_ARG;
+    if (!b->committed) return AL_ERR_STATE;
+    for (int q = 0; q < b->n; ++q)
+        if (!b->grids[q]) return AL_ERR_STATE;                // every slot must be bound
+    cudaStream_t st = (cudaStream_t)stream;
+    auto enqueue = [&](cudaStream_t s) {
+        return b->precision == AL_FP64
+                   ? batch_enqueue_t<double>(b, s, nullptr, b->d_pre, b->n, b->tot_pts, b->tot_lines, b->tot_bricks)
+                   : batch_enqueue_t<float>(b, s, nullptr, b->d_pre, b->n, b->tot_pts, b->tot_lines, b->tot_bricks);
+    };
+    if (!b->use_graph) return enqueue(st);
+    if (!b->exec) {
+        AL_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+        AL_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue(b->cap);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+        if (rc != AL_OK) return rc;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        b->graph = graph;
+        AL_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    }
+    AL_CUDA(cudaGraphLaunch(b->exec, st));
+    return AL_OK;
+}
+
+extern "C" int al_batch_run_subset(al_batch b, const int *idx, int n_idx, void *stream) {
+    if (!b || (n_idx > 0 && !idx) || n_idx < 0) return AL_ERR_ARG;
+    if (!b->committed) return AL_ERR_STATE;
+    if (n_idx > b->maxn) return AL_ERR_CAPACITY;
+    if (n_idx == 0) return AL_OK;
+    for (int k = 0; k < n_idx; ++k) {
+        if (idx[k] < 0 || idx[k] >= b->n || !b->grids[idx[k]]) return AL_ERR_ARG;
+        for (int j = 0; j < k; ++j)
+            if (idx[j] == idx[k]) return AL_ERR_ARG;     // one step per instance per run
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int r = b->ring_pos;
+    b->ring_pos = (b->ring_pos + 1) % al_batch_s::RING;
+    // the slot's previous work list must have been consumed
+    AL_CUDA(cudaEventSynchronize(b->ring_ev[r]));
+    const size_t slot = al_batch_s::slot_bytes(b->maxn);
+    char *h = (char *)b->h_ring + r * slot, *d = (char *)b->d_ring + r * slot;
+    const size_t off_pre = ((size_t)b->maxn * sizeof(int) + 15) & ~(size_t)15;
+    int *hs = (int *)h;
+    long long *hp = (long long *)(h + off_pre);
+    long long tp = 0, tl = 0, tb = 0;
+    hp[0] = hp[n_idx + 1] = hp[2 * (n_idx + 1)] = 0;
+    for (int k = 0; k < n_idx; ++k) {
+        hs[k] = idx[k];
+        tp += b->cnt_pts[idx[k]]; tl += b->cnt_lines[idx[k]]; tb += b->cnt_bricks[idx[k]];
+        hp[k + 1] = tp; hp[(n_idx + 1) + k + 1] = tl; hp[2 * (n_idx + 1) + k + 1] = tb;
+    }
+    AL_CUDA(cudaMemcpyAsync(d, h, off_pre + 3 * (size_t)(n_idx + 1) * sizeof(long long), cudaMemcpyHostToDevice, st));
+    const int *ds = (const int *)d;
+    const long long *dp = (const long long *)(d + off_pre);
+    int rc = b->precision == AL_FP64 ? batch_enqueue_t<double>(b, st, ds, dp, n_idx, tp, tl, tb)
+                                     : batch_enqueue_t<float>(b, st, ds, dp, n_idx, tp, tl, tb);
+    if (rc != AL_OK) return rc;
+    AL_CUDA(cudaEventRecord(b->ring_ev[r], st));
+    return AL_OK;
+}
+
+extern "C" int al_batch_destroy(al_batch b) {
+    if (!b) return AL_ERR_ARG;
+    cudaDeviceSynchronize();
+    for (int r = 0; r < al_batch_s::RING; ++r)
+        if (b->ring_ev[r]) cudaEventDestroy(b->ring_ev[r]);
+    if (b->h_ring) cudaFreeHost(b->h_ring);
+    if (b->h_inst) cudaFreeHost(b->h_inst);
+    for (cudaEvent_t e : b->slot_ev)
+        if (e) cudaEventDestroy(e);
+    if (b->d_ring) cudaFree(b->d_ring);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->d_inst) cudaFree(b->d_inst);
+    if (b->d_pre) cudaFree(b->d_pre);
+    delete b;
+    return AL_OK;
+}
