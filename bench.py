@@ -41,7 +41,12 @@ def _args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="canopy", choices=["canopy", "flume", "plain"])
+    ap.add_argument("--workload", default="canopy", choices=["canopy", "flume", "plain", "batched", "serve"])
+    ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
+    ap.add_argument("--sims", type=int, default=256, help="serve: number of simulations")
+    ap.add_argument("--sim-steps", type=int, default=100, help="serve: steps per simulation")
+    ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000", help="serve: arrival rates (1/s)")
+    ap.add_argument("--budget-gb", type=float, default=2.0, help="serve: HBM budget for resident simulations")
     ap.add_argument("--eps", type=float, default=2.0, help="canopy kernel width in cells")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -329,9 +334,117 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_batched(a):
+    """64 independent instances of uneven size: one batched launch sequence
+    (CUDA graph) per step vs one launch sequence per instance."""
+    import torch
+    from paper_2609_39443_b300 import workloads as W
+    from paper_2609_39443_b300.al import Batch, Instance
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wls = W.make_batched(rank, a.instances)
+    insts = [Instance(w, device=f"cuda:{local}") for w in wls]
+    batch = Batch(insts, use_graph=True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
+
+    def per_instance():
+        for i in insts:
+            i.step()
+
+    for _ in range(a.warmup):
+        batch.run()
+        per_instance()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    t_batch = timed(batch.run, a.steps)
+    t_plain = timed(per_instance, a.steps)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([t_batch, t_plain], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_batch, t_plain = (float(x) for x in t.tolist())
+    n = len(insts)
+    value = world * n * a.steps / t_batch
+    cells = sum(w.grid.n_cells for w in wls)
+    pts = sum(w.beams.n_points for w in wls)
+    if rank == 0:
+        line = {"metric": "coupling steps/s", "value": value, "unit": "instance-steps/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_batch / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"batched_{n}_instances", "cells": cells, "points": pts,
+                           "parallelism": f"{world} independent batches",
+                           "l2": "flushed between timed steps (256 MiB write)"},
+                "per_instance_launch_steps_per_s": world * n * a.steps / t_plain,
+                "batched_speedup": t_plain / t_batch, "clocks": clk,
+                "gpu_launches": 11 * a.steps}
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for i in insts:
+        i.close()
+
+
+def run_serve(a):
+    """Poisson-arriving coupling-step requests from many simulations:
+    continuous batching vs one request at a time."""
+    import torch
+    from paper_2609_39443_b300 import workloads as W
+    from paper_2609_39443_b300.serve import BatchServer, PlainServer, Sim, poisson_arrivals
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    wls = W.make_batched(1000 + rank, a.sims)
+    sims = [Sim(w, a.sim_steps) for w in wls]
+    budget = int(a.budget_gb * 2 ** 30)
+    rows = []
+    for rate in [float(x) for x in a.rates.split(",")]:
+        arr = poisson_arrivals(sims, rate, seed=rate_seed(rate))
+        sb = BatchServer(sims, budget, n_slots=128).run(arr).summary()
+        sp = PlainServer(sims, budget).run(arr).summary()
+        rows.append({"rate": rate, "batched": sb, "plain": sp})
+    if rank == 0:
+        best = max(rows, key=lambda r: r["batched"]["steps_per_s"])
+        line = {"metric": "coupling steps/s", "value": best["batched"]["steps_per_s"], "unit": "steps/s",
+                "n_gpus": 1, "steps": a.sims * a.sim_steps, "warmup": 0,
+                "ms_per_step": 1e3 / best["batched"]["steps_per_s"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"serve_{a.sims}_sims_x_{a.sim_steps}_steps", "budget_bytes": budget},
+                "p50_ms": best["batched"]["p50_ms"], "p99_ms": best["batched"]["p99_ms"],
+                "sweep": rows}
+        print(json.dumps(line), flush=True)
+
+
+def rate_seed(rate):
+    return int(rate) % 100003
+
+
 if __name__ == "__main__":
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)

@@ -75,6 +75,9 @@ def lib():
         L.al_batch_create.argtypes = [C.POINTER(_vp)]
         L.al_batch_add.argtypes = [_vp, _vp, C.POINTER(StepIn), C.POINTER(StepOut)]
         L.al_batch_commit.argtypes = [_vp, C.c_int, C.c_int]
+        L.al_batch_reserve.argtypes = [_vp, C.c_int, C.c_int]
+        L.al_batch_run_subset.argtypes = [_vp, C.POINTER(C.c_int), C.c_int, _vp]
+        L.al_batch_assign.argtypes = [_vp, C.c_int, _vp, C.POINTER(StepIn), C.POINTER(StepOut), _vp]
         L.al_batch_run.argtypes = [_vp, _vp]
         L.al_batch_destroy.argtypes = [_vp]
         L.al_trace_enable.argtypes = [_vp, C.c_int]
@@ -267,22 +270,41 @@ class Instance:
 
 
 class Batch:
-    """al_batch_*: many instances advanced by one launch per phase."""
+    """al_batch_*: many instances advanced by one launch per phase.
+    reserve=(n_slots, precision) adds empty slots for al_batch_assign."""
 
-    def __init__(self, instances, use_graph=True, spread_ctas_per_sm=0):
+    def __init__(self, instances, use_graph=True, spread_ctas_per_sm=0, reserve=None):
         h = _vp()
         check(lib().al_batch_create(C.byref(h)), "al_batch_create")
         self.h = h
         self.instances = list(instances)
-        self._desc = []
-        for inst in self.instances:
+        self._desc = {}
+        for q, inst in enumerate(self.instances):
             sin, sout = inst.descriptors()
-            self._desc.append((sin, sout))
+            self._desc[q] = (sin, sout)
             check(lib().al_batch_add(self.h, inst.grid.h, C.byref(sin), C.byref(sout)), "al_batch_add")
+        if reserve is not None:
+            n, prec = reserve
+            check(lib().al_batch_reserve(self.h, int(n), AL_FP64 if prec == "fp64" else AL_FP32),
+                  "al_batch_reserve")
         check(lib().al_batch_commit(self.h, int(bool(use_graph)), int(spread_ctas_per_sm)), "al_batch_commit")
 
     def run(self, stream=None):
         check(lib().al_batch_run(self.h, _stream_ptr(stream)), "al_batch_run")
+
+    def run_subset(self, idx, stream=None):
+        arr = (C.c_int * len(idx))(*[int(i) for i in idx])
+        check(lib().al_batch_run_subset(self.h, arr, len(idx), _stream_ptr(stream)), "al_batch_run_subset")
+
+    def assign(self, slot, inst, stream=None):
+        if inst is None:
+            check(lib().al_batch_assign(self.h, int(slot), None, None, None, _stream_ptr(stream)), "al_batch_assign")
+            self._desc.pop(slot, None)
+            return
+        sin, sout = inst.descriptors()
+        self._desc[slot] = (sin, sout)
+        check(lib().al_batch_assign(self.h, int(slot), inst.grid.h, C.byref(sin), C.byref(sout),
+                                    _stream_ptr(stream)), "al_batch_assign")
 
     def close(self):
         if getattr(self, "h", None):

@@ -185,6 +185,12 @@ __device__ __forceinline__ int ffloor(T uh, float ul) {
     return c;
 }
 
+// floor / ceil in the arithmetic type (no FP64 for FP32 instances)
+__device__ __forceinline__ int ifloor(float x) { return (int)floorf(x); }
+__device__ __forceinline__ int ifloor(double x) { return (int)floor(x); }
+__device__ __forceinline__ int iceil(float x) { return (int)ceilf(x); }
+__device__ __forceinline__ int iceil(double x) { return (int)ceil(x); }
+
 // ---------------------------------------------------------------------------
 // sampling: trilinear (default) or containing cell
 // ---------------------------------------------------------------------------
@@ -575,7 +581,7 @@ __device__ void d_mask(const GridC &g, const BeamsC &b, const Scratch<T> &sc, co
 // segment distance evaluated from the caller's original positions.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ double dist2_f64(const GridC &g, const StepPtrs<T> &p, int ka, int kb, int ci, int cj, int ck,
+__device__ __noinline__ double dist2_f64(const GridC &g, const StepPtrs<T> &p, int ka, int kb, int ci, int cj, int ck,
                             double *s_out) {
     const double c[3] = {__dadd_rn(g.o[0], __dmul_rn((double)ci + 0.5, g.h)),
                          __dadd_rn(g.o[1], __dmul_rn((double)cj + 0.5, g.h)),
@@ -617,7 +623,7 @@ __device__ bool within_f64(const GridC &g, const StepPtrs<T> &p, double eps, int
 }
 // argmin over segments [k0, k1] in FP64, lowest index on ties
 template <typename T>
-__device__ int argmin_f64(const GridC &g, const StepPtrs<T> &p, int k0, int k1, int n, int ci, int cj, int ck) {
+__device__ __noinline__ int argmin_f64(const GridC &g, const StepPtrs<T> &p, int k0, int k1, int n, int ci, int cj, int ck) {
     double best = INFINITY;
     int kb = k0;
     for (int k = k0; k <= k1; ++k) {
@@ -745,6 +751,42 @@ __device__ __forceinline__ double warp_total(const Acc<double> &a) {
     return v;
 }
 
+// the cells of segment c.k's slab, columns along the two axes other than
+// the march axis AX (compile-time, so coordinates stay in registers)
+template <typename T, int AX>
+__device__ __forceinline__ void w_columns(const WSeg<T> &c, const GridC &g, const Scratch<T> &sc,
+                                          const StepPtrs<T> &p, int *status, const int lane, Acc<T> &wa,
+                                          Acc<T> &wb) {
+    constexpr int PA = (AX + 1) % 3, PB = (AX + 2) % 3;
+    const int na = c.hi[PA] - c.lo[PA] + 1, nbb = c.hi[PB] - c.lo[PB] + 1;
+    const int ncol = na * nbb;
+    for (int col = lane; col < ncol; col += 32) {
+        const int ia = c.lo[PA] + col % na, ib = c.lo[PB] + col / na;
+        T C[3];
+        C[PA] = (T)(ia - c.O[PA]) + (T)0.5;
+        C[PB] = (T)(ib - c.O[PB]) + (T)0.5;
+        // march-axis interval between the two planes (pruning only; the
+        // membership test decides)
+        T clo = (T)(c.lo[AX] - c.O[AX]) + (T)0.5, chi = (T)(c.hi[AX] - c.O[AX]) + (T)0.5;
+        if (c.has_lo && c.m0[AX] != (T)0) {
+            T r = c.A[AX] - ((C[PA] - c.A[PA]) * c.m0[PA] + (C[PB] - c.A[PB]) * c.m0[PB]) / c.m0[AX];
+            if (c.m0[AX] > (T)0) clo = fmax(clo, r - (T)0.05); else chi = fmin(chi, r + (T)0.05);
+        }
+        if (c.has_hi && c.m1[AX] != (T)0) {
+            T r = c.Bn[AX] - ((C[PA] - c.Bn[PA]) * c.m1[PA] + (C[PB] - c.Bn[PB]) * c.m1[PB]) / c.m1[AX];
+            if (c.m1[AX] > (T)0) chi = fmin(chi, r + (T)0.05); else clo = fmax(clo, r - (T)0.05);
+        }
+        const int i0 = max(c.lo[AX], iceil(clo - (T)0.5) + c.O[AX]);
+        const int i1 = min(c.hi[AX], ifloor(chi - (T)0.5) + c.O[AX]);
+        for (int ic = i0; ic <= i1; ++ic) {
+            C[AX] = (T)(ic - c.O[AX]) + (T)0.5;
+            int cg[3];
+            cg[AX] = ic; cg[PA] = ia; cg[PB] = ib;
+            w_cell(c, C, cg, g, sc, p, true, status, wa, wb);
+        }
+    }
+}
+
 template <typename T>
 __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
                           const int k, const int lane) {
@@ -757,7 +799,7 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
     c.nseg = (c.n == 1) ? 1 : c.n - 1;
     c.kb = seg_end(k, c.n);
     c.eps = b.eps[l];
-    for (int a = 0; a < 3; ++a) c.O[a] = (int)floor((double)sc.uhi[a * np + k]);
+    for (int a = 0; a < 3; ++a) c.O[a] = ifloor(sc.uhi[a * np + k]);
     for (int a = 0; a < 3; ++a) {
         c.A[a] = rel(sc.uhi[a * np + k], sc.ulo[a * np + k], c.O[a]);
         c.Bn[a] = rel(sc.uhi[a * np + c.kb], sc.ulo[a * np + c.kb], c.O[a]);
@@ -769,8 +811,8 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
     bool empty = false;
     for (int a = 0; a < 3; ++a) {
         T l0 = fmin(c.A[a], c.Bn[a]) - (T)lg.Rc - (T)0.01, h0 = fmax(c.A[a], c.Bn[a]) + (T)lg.Rc + (T)0.01;
-        c.lo[a] = max(0, (int)ceil((double)l0 - 0.5) + c.O[a]);
-        c.hi[a] = min(nn[a] - 1, (int)floor((double)h0 - 0.5) + c.O[a]);
+        c.lo[a] = max(0, iceil(l0 - (T)0.5) + c.O[a]);
+        c.hi[a] = min(nn[a] - 1, ifloor(h0 - (T)0.5) + c.O[a]);
         if (c.lo[a] > c.hi[a]) empty = true;
     }
     Acc<T> wa, wb;
@@ -785,34 +827,9 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
         int ax = 0;
         if (fabs(c.D[1]) > fabs(c.D[ax])) ax = 1;
         if (fabs(c.D[2]) > fabs(c.D[ax])) ax = 2;
-        const int pa = (ax + 1) % 3, pb = (ax + 2) % 3;
-        const int na = c.hi[pa] - c.lo[pa] + 1, nbb = c.hi[pb] - c.lo[pb] + 1;
-        const int ncol = na * nbb;
-        for (int col = lane; col < ncol; col += 32) {
-            const int ia = c.lo[pa] + col % na, ib = c.lo[pb] + col / na;
-            T C[3];
-            C[pa] = (T)(ia - c.O[pa]) + (T)0.5;
-            C[pb] = (T)(ib - c.O[pb]) + (T)0.5;
-            // march-axis interval between the two planes (pruning only; the
-            // membership test decides)
-            T clo = (T)(c.lo[ax] - c.O[ax]) + (T)0.5, chi = (T)(c.hi[ax] - c.O[ax]) + (T)0.5;
-            if (c.has_lo && c.m0[ax] != (T)0) {
-                T r = c.A[ax] - ((C[pa] - c.A[pa]) * c.m0[pa] + (C[pb] - c.A[pb]) * c.m0[pb]) / c.m0[ax];
-                if (c.m0[ax] > (T)0) clo = fmax(clo, r - (T)0.05); else chi = fmin(chi, r + (T)0.05);
-            }
-            if (c.has_hi && c.m1[ax] != (T)0) {
-                T r = c.Bn[ax] - ((C[pa] - c.Bn[pa]) * c.m1[pa] + (C[pb] - c.Bn[pb]) * c.m1[pb]) / c.m1[ax];
-                if (c.m1[ax] > (T)0) chi = fmin(chi, r + (T)0.05); else clo = fmax(clo, r - (T)0.05);
-            }
-            const int i0 = max(c.lo[ax], (int)ceil((double)clo - 0.5) + c.O[ax]);
-            const int i1 = min(c.hi[ax], (int)floor((double)chi - 0.5) + c.O[ax]);
-            for (int ic = i0; ic <= i1; ++ic) {
-                C[ax] = (T)(ic - c.O[ax]) + (T)0.5;
-                int cg[3];
-                cg[ax] = ic; cg[pa] = ia; cg[pb] = ib;
-                w_cell(c, C, cg, g, sc, p, true, status, wa, wb);
-            }
-        }
+        if (ax == 0) w_columns<T, 0>(c, g, sc, p, status, lane, wa, wb);
+        else if (ax == 1) w_columns<T, 1>(c, g, sc, p, status, lane, wa, wb);
+        else w_columns<T, 2>(c, g, sc, p, status, lane, wa, wb);
     } else if (!empty) {
         const int n0 = c.hi[0] - c.lo[0] + 1, n1 = c.hi[1] - c.lo[1] + 1, n2 = c.hi[2] - c.lo[2] + 1;
         const long long ncell = (long long)n0 * n1 * n2;
@@ -846,7 +863,8 @@ __device__ void d_normalise(const BeamsC &b, const Scratch<T> &sc, const StepPtr
     }
     sc.w[k] = w;
     if (w > 0.0) {
-        for (int a = 0; a < 3; ++a) sc.fhat[a * np + k] = (T)((double)p.F[a][k] / w);
+        const T wt = (T)w;                         // FP64 sum, divided in the field precision
+        for (int a = 0; a < 3; ++a) sc.fhat[a * np + k] = p.F[a][k] / wt;
     } else {
         for (int a = 0; a < 3; ++a) sc.fhat[a * np + k] = (T)0;
         int slot = atomicAdd(sc.zeroCount, 1);
@@ -872,21 +890,67 @@ struct SpreadSmem {
     T Il2[NN];
     int list[LIST];              // candidate lines of this brick (line order)
     int nlist, nbatch;
-    int e_line[ENT], e_jlo[ENT], e_jhi[ENT], e_base[ENT], e_reg[ENT], e_n[ENT];
+    int e_line[ENT], e_jlo[ENT], e_jhi[ENT], e_base[ENT], e_reg[ENT], e_n[ENT], e_first[ENT];
     float e_lo[ENT][3], e_hi[ENT][3];
+    T e_R2[ENT], e_gr[ENT], e_ie2[ENT], e_eta0[ENT];
     double red[3][SPREAD_THREADS / 32];
 };
+
+// rare paths of the gather, kept out of line so the unrolled cell loop stays small
+
+// FP64 re-decision of "segment k closer than k-1" (walk inside the band)
+template <typename T>
+__device__ __noinline__ bool nl_later_closer(const GridC &g, const StepPtrs<T> &p, int k, int ci, int cj, int ck,
+                                             int *status) {
+    atomicAdd(&status[ST_REFINED], 1);
+    return later_closer_f64(g, p, k, ci, cj, ck);
+}
+template <typename T>
+__device__ __noinline__ bool nl_within(const GridC &g, const StepPtrs<T> &p, double eps, int k, int n, int ci,
+                                       int cj, int ck, int *status) {
+    atomicAdd(&status[ST_REFINED], 1);
+    return within_f64(g, p, eps, k, n, ci, cj, ck);
+}
+// closest segment over [first + jlo, first + jhi] by exhaustive search
+// (lines without a walk certificate, or longer than the shared-memory stage);
+// returns the line-local segment index
+template <typename T>
+__device__ __noinline__ int nl_exhaustive(const GridC &g, const Scratch<T> &sc, const StepPtrs<T> &p, int first,
+                                          int n, int jlo, int jhi, const T C[3], const int B[3], int ci, int cj,
+                                          int ck, int *status) {
+    const long long np = p.np;
+    T best = (T)INFINITY, second = (T)INFINITY;
+    int js = jlo;
+    for (int jj = jlo; jj <= jhi; ++jj) {
+        const int ka = first + jj;
+        T x[3], Dj[3];
+        for (int a = 0; a < 3; ++a) {
+            x[a] = C[a] - rel(sc.uhi[a * np + ka], sc.ulo[a * np + ka], B[a]);
+            Dj[a] = sc.segD[a * np + ka];
+        }
+        T t = (x[0] * Dj[0] + x[1] * Dj[1] + x[2] * Dj[2]) * sc.segIl2[ka];
+        t = t < (T)0 ? (T)0 : (t > (T)1 ? (T)1 : t);
+        T e0 = x[0] - t * Dj[0], e1 = x[1] - t * Dj[1], e2 = x[2] - t * Dj[2];
+        T d2 = e0 * e0 + e1 * e1 + e2 * e2;
+        if (d2 < best) { second = best; best = d2; js = jj; }
+        else if (d2 < second) second = d2;
+    }
+    if (!(second - best > Tr<T>::grr(best))) {
+        js = argmin_f64(g, p, first + jlo, first + jhi, n, ci, cj, ck) - first;
+        atomicAdd(&status[ST_REFINED], 1);
+    }
+    return js;
+}
 
 template <typename T>
 __device__ __forceinline__ bool sig_pos(const SpreadSmem<T> &sm, int s, const T C[3], const GridC &g,
                                         const StepPtrs<T> &p, int kglob, int ci, int cj, int ck, int *status) {
-    T x0 = C[0] - sm.P[0][s], x1 = C[1] - sm.P[1][s], x2 = C[2] - sm.P[2][s];
-    T sg = x0 * sm.M[0][s] + x1 * sm.M[1][s] + x2 * sm.M[2][s];
-    T gs = Tr<T>::gsig(sqrt(x0 * x0 + x1 * x1 + x2 * x2));
+    const T x0 = C[0] - sm.P[0][s], x1 = C[1] - sm.P[1][s], x2 = C[2] - sm.P[2][s];
+    const T sg = x0 * sm.M[0][s] + x1 * sm.M[1][s] + x2 * sm.M[2][s];
+    const T gs = Tr<T>::gsig(sqrt(x0 * x0 + x1 * x1 + x2 * x2));
     if (sg > gs) return true;
     if (sg < -gs) return false;
-    atomicAdd(&status[ST_REFINED], 1);
-    return later_closer_f64(g, p, kglob, ci, cj, ck);
+    return nl_later_closer(g, p, kglob, ci, cj, ck, status);
 }
 
 template <typename T>
@@ -895,9 +959,12 @@ __device__ void d_spread(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
     const long long np = b.n_points;
     const int bxi = (int)(br % g.nbx), byi = (int)((br / g.nbx) % g.nby), bzi = (int)(br / ((long long)g.nbx * g.nby));
     const int B0 = bxi * BX, B1 = byi * BY, B2 = bzi * BZ;
+    const int Bv[3] = {B0, B1, B2};
     const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gx = B0 + tx, gy = B1 + ty;
+    const bool col_in = gx < g.nx && gy < g.ny;
+    const float cx = tx + 0.5f, cy = ty + 0.5f;
 
     T acc[BZ][3];
 #pragma unroll
@@ -906,7 +973,6 @@ __device__ void d_spread(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
 
     const int W = b.mask_words;
     uint32_t *mrow = sc.mask + br * (long long)W;
-    // brick box in cell units (centres lie in [B + 0.5, B + size - 0.5])
     const float blo[3] = {(float)B0, (float)B1, (float)B2};
     const float bhi[3] = {(float)(B0 + BX), (float)(B1 + BY), (float)(B2 + BZ)};
 
@@ -928,8 +994,7 @@ __device__ void d_spread(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
             while (m) {
                 int bit = __ffs(m) - 1;
                 m &= m - 1;
-                if (pos < SpreadSmem<T>::LIST) sm.list[pos] = ((w0 + lane) << 5) + bit;
-                ++pos;
+                sm.list[pos++] = ((w0 + lane) << 5) + bit;
             }
             if (lane == 0) sm.nlist = total;                      // <= 32 * CH = LIST
         }
@@ -971,6 +1036,11 @@ __device__ void d_spread(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
                     sm.e_jhi[e] = jhi;
                     sm.e_reg[e] = lg.regular;
                     sm.e_n[e] = lg.n;
+                    sm.e_first[e] = lg.first;
+                    sm.e_R2[e] = (T)lg.R2c;
+                    sm.e_gr[e] = Tr<T>::grr((T)lg.R2c);
+                    sm.e_ie2[e] = (T)lg.inv_eps2c;
+                    sm.e_eta0[e] = (T)lg.eta0;
                     for (int a = 0; a < 3; ++a) { sm.e_lo[e][a] = lo[a] - blo[a]; sm.e_hi[e][a] = hi[a] - blo[a]; }
                 }
             }
@@ -993,16 +1063,14 @@ __device__ void d_spread(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
             for (int e = 0; e < ne; ++e) {
                 const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e], base = sm.e_base[e];
                 if (jhi < jlo || base < 0) continue;
-                const int l = sm.e_line[e];
-                const int first = sc.lines[l].first, n = sm.e_n[e];
+                const int first = sm.e_first[e], n = sm.e_n[e];
                 const int cnt = jhi - jlo + 2;
                 for (int t = threadIdx.x; t < cnt; t += SPREAD_THREADS) {
                     const int k = first + jlo + t;
                     const int kn = (n == 1) ? first : k;    // single-node line: copy the node
                     const int s = base + t;
                     for (int a = 0; a < 3; ++a) {
-                        const int B = a == 0 ? B0 : (a == 1 ? B1 : B2);
-                        sm.P[a][s] = rel(sc.uhi[a * np + kn], sc.ulo[a * np + kn], B);
+                        sm.P[a][s] = rel(sc.uhi[a * np + kn], sc.ulo[a * np + kn], Bv[a]);
                         sm.M[a][s] = sc.nodeM[a * np + kn];
                         sm.Fh[a][s] = sc.fhat[a * np + kn];
                         sm.D[a][s] = sc.segD[a * np + kn];
@@ -1011,109 +1079,71 @@ __device__ void d_spread(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
                 }
             }
             __syncthreads();
-            // ---- gather --------------------------------------------------------
-            for (int e = 0; e < ne; ++e) {
-                const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e], base = sm.e_base[e];
-                if (jhi < jlo) continue;
-                const int l = sm.e_line[e];
-                const LineG lg = sc.lines[l];
-                const int first = lg.first, n = lg.n;
-                const float cx = tx + 0.5f, cy = ty + 0.5f;
-                if (cx < sm.e_lo[e][0] || cx > sm.e_hi[e][0] || cy < sm.e_lo[e][1] || cy > sm.e_hi[e][1]) continue;
-                if (gx >= g.nx || gy >= g.ny) continue;
-                const T R2 = (T)lg.R2c, gr = Tr<T>::grr(R2), ie2 = (T)lg.inv_eps2c, eta0 = (T)lg.eta0;
-                const double eps = b.eps[l];
-                const int reg = sm.e_reg[e];
-                int j = jlo;                                    // walk state (segment, line-local)
+            // ---- gather: every thread walks only the lines near its column ----
+            if (col_in) {
+                uint64_t cm = 0;
+                for (int e = 0; e < ne; ++e)
+                    if (sm.e_jhi[e] >= sm.e_jlo[e] && cx >= sm.e_lo[e][0] && cx <= sm.e_hi[e][0] &&
+                        cy >= sm.e_lo[e][1] && cy <= sm.e_hi[e][1])
+                        cm |= 1ull << e;
+                while (cm) {                                     // increasing e = line order
+                    const int e = __ffsll((long long)cm) - 1;
+                    cm &= cm - 1;
+                    const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e], base = sm.e_base[e];
+                    const int first = sm.e_first[e], n = sm.e_n[e], reg = sm.e_reg[e];
+                    const T R2 = sm.e_R2[e], gr = sm.e_gr[e], ie2 = sm.e_ie2[e], eta0 = sm.e_eta0[e];
+                    const float zlo = sm.e_lo[e][2], zhi = sm.e_hi[e][2];
+                    int j = jlo;                                  // walk state (line-local segment)
 #pragma unroll
-                for (int z = 0; z < BZ; ++z) {
-                    const float cz = z + 0.5f;
-                    if (cz < sm.e_lo[e][2] || cz > sm.e_hi[e][2]) continue;
-                    const int gz = B2 + z;
-                    if (gz >= g.nz) continue;
-                    const T C[3] = {(T)cx, (T)cy, (T)cz};
-                    int js;                                     // closest segment (line-local)
-                    T s, r2;
-                    if (base >= 0) {
-                        if (reg) {
+                    for (int z = 0; z < BZ; ++z) {
+                        const float cz = z + 0.5f;
+                        if (cz < zlo || cz > zhi) continue;
+                        const int gz = B2 + z;
+                        if (gz >= g.nz) continue;
+                        const T C[3] = {(T)cx, (T)cy, (T)cz};
+                        int js;
+                        if (reg && base >= 0) {
                             while (j > jlo && !sig_pos(sm, base + (j - jlo), C, g, p, first + j, gx, gy, gz, status)) --j;
                             while (j < jhi && sig_pos(sm, base + (j + 1 - jlo), C, g, p, first + j + 1, gx, gy, gz, status)) ++j;
                             js = j;
                         } else {
-                            T best = (T)INFINITY, second = (T)INFINITY;
-                            js = jlo;
-                            for (int jj = jlo; jj <= jhi; ++jj) {
-                                const int ss = base + (jj - jlo);
-                                T x0 = C[0] - sm.P[0][ss], x1 = C[1] - sm.P[1][ss], x2 = C[2] - sm.P[2][ss];
-                                T t = (x0 * sm.D[0][ss] + x1 * sm.D[1][ss] + x2 * sm.D[2][ss]) * sm.Il2[ss];
-                                t = t < (T)0 ? (T)0 : (t > (T)1 ? (T)1 : t);
-                                T e0 = x0 - t * sm.D[0][ss], e1 = x1 - t * sm.D[1][ss], e2 = x2 - t * sm.D[2][ss];
-                                T d2 = e0 * e0 + e1 * e1 + e2 * e2;
-                                if (d2 < best) { second = best; best = d2; js = jj; }
-                                else if (d2 < second) second = d2;
-                            }
-                            if (!(second - best > Tr<T>::grr(best))) {
-                                js = argmin_f64(g, p, first + jlo, first + jhi, n, gx, gy, gz) - first;
-                                atomicAdd(&status[ST_REFINED], 1);
-                            }
+                            js = nl_exhaustive(g, sc, p, first, n, jlo, jhi, C, Bv, gx, gy, gz, status);
                         }
-                        const int ss = base + (js - jlo);
-                        T x0 = C[0] - sm.P[0][ss], x1 = C[1] - sm.P[1][ss], x2 = C[2] - sm.P[2][ss];
-                        s = (x0 * sm.D[0][ss] + x1 * sm.D[1][ss] + x2 * sm.D[2][ss]) * sm.Il2[ss];
-                        s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
-                        T e0 = x0 - s * sm.D[0][ss], e1 = x1 - s * sm.D[1][ss], e2 = x2 - s * sm.D[2][ss];
-                        r2 = e0 * e0 + e1 * e1 + e2 * e2;
-                    } else {
-                        // line too long for shared memory: exhaustive from global memory
-                        const int Bv[3] = {B0, B1, B2};
-                        T best = (T)INFINITY, second = (T)INFINITY;
-                        js = jlo;
-                        for (int jj = jlo; jj <= jhi; ++jj) {
-                            const int ka = first + jj;
+                        T s, r2, fa[3], fb[3];
+                        if (base >= 0) {
+                            const int ss = base + (js - jlo), sb = (n == 1) ? ss : ss + 1;
+                            const T x0 = C[0] - sm.P[0][ss], x1 = C[1] - sm.P[1][ss], x2 = C[2] - sm.P[2][ss];
+                            const T d0 = sm.D[0][ss], d1 = sm.D[1][ss], d2 = sm.D[2][ss];
+                            s = (x0 * d0 + x1 * d1 + x2 * d2) * sm.Il2[ss];
+                            s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
+                            const T e0 = x0 - s * d0, e1 = x1 - s * d1, e2 = x2 - s * d2;
+                            r2 = e0 * e0 + e1 * e1 + e2 * e2;
+                            for (int a = 0; a < 3; ++a) { fa[a] = sm.Fh[a][ss]; fb[a] = sm.Fh[a][sb]; }
+                        } else {
+                            const int ka = first + js, kb = seg_end(ka, n);
                             T x[3], Dj[3];
                             for (int a = 0; a < 3; ++a) {
                                 x[a] = C[a] - rel(sc.uhi[a * np + ka], sc.ulo[a * np + ka], Bv[a]);
                                 Dj[a] = sc.segD[a * np + ka];
+                                fa[a] = sc.fhat[a * np + ka];
+                                fb[a] = sc.fhat[a * np + kb];
                             }
-                            T t = (x[0] * Dj[0] + x[1] * Dj[1] + x[2] * Dj[2]) * sc.segIl2[ka];
-                            t = t < (T)0 ? (T)0 : (t > (T)1 ? (T)1 : t);
-                            T e0 = x[0] - t * Dj[0], e1 = x[1] - t * Dj[1], e2 = x[2] - t * Dj[2];
-                            T d2 = e0 * e0 + e1 * e1 + e2 * e2;
-                            if (d2 < best) { second = best; best = d2; js = jj; }
-                            else if (d2 < second) second = d2;
+                            s = (x[0] * Dj[0] + x[1] * Dj[1] + x[2] * Dj[2]) * sc.segIl2[ka];
+                            s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
+                            const T e0 = x[0] - s * Dj[0], e1 = x[1] - s * Dj[1], e2 = x[2] - s * Dj[2];
+                            r2 = e0 * e0 + e1 * e1 + e2 * e2;
                         }
-                        if (!(second - best > Tr<T>::grr(best))) {
-                            js = argmin_f64(g, p, first + jlo, first + jhi, n, gx, gy, gz) - first;
-                            atomicAdd(&status[ST_REFINED], 1);
-                        }
-                        const int ka = first + js;
-                        T x[3], Dj[3];
-                        for (int a = 0; a < 3; ++a) {
-                            x[a] = C[a] - rel(sc.uhi[a * np + ka], sc.ulo[a * np + ka], Bv[a]);
-                            Dj[a] = sc.segD[a * np + ka];
-                        }
-                        s = (x[0] * Dj[0] + x[1] * Dj[1] + x[2] * Dj[2]) * sc.segIl2[ka];
-                        s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
-                        T e0 = x[0] - s * Dj[0], e1 = x[1] - s * Dj[1], e2 = x[2] - s * Dj[2];
-                        r2 = e0 * e0 + e1 * e1 + e2 * e2;
-                    }
-                    bool in;
-                    if (r2 < R2 - gr) in = true;
-                    else if (r2 > R2 + gr) in = false;
-                    else { in = within_f64(g, p, eps, first + js, n, gx, gy, gz); atomicAdd(&status[ST_REFINED], 1); }
-                    if (!in) continue;
-                    ++nsupp;
-                    const T eta = eta0 * Tr<T>::ex(-r2 * ie2);
-                    const T wa = eta * ((T)1 - s), wb = eta * s;
-                    if (base >= 0) {
-                        const int sa = base + (js - jlo), sb = (n == 1) ? sa : sa + 1;
-                        acc[z][0] -= wa * sm.Fh[0][sa] + wb * sm.Fh[0][sb];
-                        acc[z][1] -= wa * sm.Fh[1][sa] + wb * sm.Fh[1][sb];
-                        acc[z][2] -= wa * sm.Fh[2][sa] + wb * sm.Fh[2][sb];
-                    } else {
-                        const int ka = first + js, kb = seg_end(ka, n);
-                        for (int a = 0; a < 3; ++a)
-                            acc[z][a] -= wa * sc.fhat[a * np + ka] + wb * sc.fhat[a * np + kb];
+                        bool in;
+                        if (r2 < R2 - gr) in = true;
+                        else if (r2 > R2 + gr) in = false;
+                        else in = nl_within(g, p, b.eps[sm.e_line[e]], first + js, n, gx, gy, gz, status);
+                        if (!in) continue;
+                        ++nsupp;
+                        const T eta = eta0 * Tr<T>::ex(-r2 * ie2);
+                        const T wa = eta * ((T)1 - s), wb = eta * s;
+                        acc[z][0] -= wa * fa[0] + wb * fb[0];
+                        acc[z][1] -= wa * fa[1] + wb * fb[1];
+                        acc[z][2] -= wa * fa[2] + wb * fb[2];
                     }
                 }
             }
@@ -1123,7 +1153,7 @@ __device__ void d_spread(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
     }
     // ---- write every cell of the brick once; brick sums of S ----------------
     T cs[3] = {(T)0, (T)0, (T)0};
-    if (gx < g.nx && gy < g.ny) {
+    if (col_in) {
 #pragma unroll
         for (int z = 0; z < BZ; ++z) {
             const int gz = B2 + z;
