@@ -210,6 +210,34 @@ int al_batch_run_subset(al_batch b, const int *idx, int n_idx, void *stream);
 int al_batch_assign(al_batch b, int slot, al_grid g, const al_step_in *in, const al_step_out *out, void *stream);
 int al_batch_destroy(al_batch b);
 
+/* ---- line forces without device allocation ----------------------------- */
+/* The paper has no counterpart of this entry point: it exists for callers
+ * that cannot allocate device memory where they need the line forces (host
+ * code running while a CUDA graph is captured, an application whose
+ * allocator forbids allocation after start-up, a plug-in whose host owns all
+ * device memory).  It computes F = f L for every actuator point exactly as
+ * al_sample_drag_spread does (sampling, upstream direction, Morison drag,
+ * F[3] overwritten), relaxed against f_prev (device, 3 arrays of N_p) when
+ * f_prev is non-NULL and un-relaxed (f = f*) when it is NULL, without an
+ * al_grid and without allocating: no cudaMalloc, no cudaFree, nothing else
+ * that allocates device memory.  All buffers are the caller's (DEVICE
+ * pointers as in al_step_in; P_spread and the projection are not used).
+ * The host arrays of `beams` are copied into one fixed __device__ array of
+ * about 1 MiB held by every GPU that loads the library until the process
+ * exits; lines beyond AL_NOALLOC_MAX_LINES or points beyond
+ * AL_NOALLOC_MAX_POINTS are rejected with AL_ERR_CAPACITY.  The first call
+ * on each device looks up that array's device address (once, with the
+ * device current), so make the first call on a device before any stream
+ * capture.  Every call shares the array and it keeps the last call's
+ * contents: calls whose work overlaps on the GPU (unordered streams) race,
+ * so order them.  status (device int[AL_STATUS_N], optional) is added to as
+ * in al_sample_drag_spread; when NULL, counters in the shared array are used
+ * (zeroed by the call).  Stream-ordered on `stream`. */
+#define AL_NOALLOC_MAX_POINTS 65536
+#define AL_NOALLOC_MAX_LINES  4096
+int al_line_forces_noalloc(const al_grid_desc *grid, const al_beam_desc *beams, const al_step_in *in,
+                           const void *const f_prev[3], void *const F[3], int *status, void *stream);
+
 /* Human-readable text of a status code (static storage). */
 const char *al_error_string(int code);
 

@@ -80,6 +80,8 @@ def lib():
         L.al_batch_assign.argtypes = [_vp, C.c_int, _vp, C.POINTER(StepIn), C.POINTER(StepOut), _vp]
         L.al_batch_run.argtypes = [_vp, _vp]
         L.al_batch_destroy.argtypes = [_vp]
+        L.al_line_forces_noalloc.argtypes = [C.POINTER(GridDesc), C.POINTER(BeamDesc), C.POINTER(StepIn),
+                                             C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_int), _vp]
         L.al_trace_enable.argtypes = [_vp, C.c_int]
         L.al_trace_last.argtypes = [_vp, C.POINTER(C.c_float)]
         L.al_error_string.restype = C.c_char_p
@@ -316,3 +318,19 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def line_forces_noalloc(grid, beams, U, P, Pdot, F, *, alpha=None, tangent=None, f_prev=None, status=None,
+                        stream=None) -> None:
+    """al_line_forces_noalloc: per-CV line loads F (3, N_p) without an
+    al_grid and without device allocation (tensors are the caller's)."""
+    gd = GridDesc(int(grid.nx), int(grid.ny), int(grid.nz), float(grid.h),
+                  (C.c_double * 3)(*map(float, grid.origin)), AL_FP64 if grid.precision == "fp64" else AL_FP32,
+                  int(bool(grid.has_alpha)), float(grid.rho1), float(grid.rho2), float(grid.rho_const))
+    ba = BeamArrays(beams)
+    sin, _ = step_descriptors(U, P, Pdot, U, F, alpha=alpha, tangent=tangent)
+    fp = (_vp * 3)(*[_ptr(t) for t in _three(f_prev)]) if f_prev is not None else None
+    fo = (_vp * 3)(*[_ptr(t) for t in _three(F)])
+    st = C.cast(_ptr(status), C.POINTER(C.c_int)) if status is not None else None
+    check(lib().al_line_forces_noalloc(C.byref(gd), C.byref(ba.desc), C.byref(sin), fp, fo, st,
+                                       _stream_ptr(stream)), "al_line_forces_noalloc")
