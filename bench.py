@@ -33,7 +33,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-KERNELS_PER_STEP = 9     # k_points k_segments k_lines k_mask k_weights k_normalise k_spread k_deposit k_totals
+KERNELS_PER_STEP = 8     # k_points k_segments k_lines k_mask k_bweights k_normalise k_spread k_totals
 
 
 def _args():
@@ -397,7 +397,7 @@ def run_batched(a):
                            "l2": "flushed between timed steps (256 MiB write)"},
                 "per_instance_launch_steps_per_s": world * n * a.steps / t_plain,
                 "batched_speedup": t_plain / t_batch, "clocks": clk,
-                "gpu_launches": 11 * a.steps}
+                "gpu_launches": 8 * a.steps}
         print(json.dumps(line), flush=True)
     batch.close()
     for i in insts:

@@ -164,11 +164,25 @@ int al_set_state(al_grid g, const void *f_prev_dev, int has_prev, void *stream);
 #define AL_PH_MASK      1      /* brick masks */
 #define AL_PH_WEIGHTS   2      /* nodal weights w_k */
 #define AL_PH_NORMALISE 3      /* f^_k = F_k / w_k */
-#define AL_PH_SPREAD    4      /* momentum source S (every cell) */
-#define AL_PH_TOTALS    5      /* zero-weight deposits, FP64 totals */
+#define AL_PH_SPREAD    4      /* momentum source S (every cell), zero-weight deposits */
+#define AL_PH_TOTALS    5      /* FP64 totals */
 #define AL_TRACE_N      6
 int al_trace_enable(al_grid g, int on);
 int al_trace_last(al_grid g, float *ms /* [AL_TRACE_N] */);
+
+/* Execution options of an instance (results agree within the parity
+ * tolerances whichever is chosen; the autotuner picks them per workload).
+ * AL_OPT_WEIGHTS selects how the nodal weights w_k (Sec. 3.2.4) are summed:
+ *   AL_WEIGHTS_BRICK (default): cell-centric over the projection bricks, every
+ *     (cell, line) pair once, as exact fixed-point integers (deterministic);
+ *   AL_WEIGHTS_SEGMENT: segment-centric (one warp per segment over the cells
+ *     between its bisector planes, compensated FP32) for lines with a walk
+ *     certificate, the brick pass for the others.
+ * Takes effect at the next step; AL_ERR_ARG for an unknown option or value. */
+#define AL_OPT_WEIGHTS      1
+#define AL_WEIGHTS_BRICK    0
+#define AL_WEIGHTS_SEGMENT  1
+int al_set_option(al_grid g, int option, int value);
 
 /* Sizes of an instance: cells and points. */
 int al_sizes(al_grid g, long long *n_cells, long long *n_points, int *n_lines);

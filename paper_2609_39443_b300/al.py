@@ -22,6 +22,9 @@ AL_STATUS_N = 16
 (ST_PA_OUTSIDE, ST_PS_OUTSIDE, ST_FALLBACK, ST_FALLBACK_ZERO, ST_ZERO_WEIGHT, ST_DEPOSIT_LOST,
  ST_REFINED, ST_IRREGULAR, ST_SUPPORT) = range(9)
 
+OPT_WEIGHTS = 1
+WEIGHTS_BRICK, WEIGHTS_SEGMENT = 0, 1
+
 TRACE_N = 6
 PHASES = ("points", "mask", "weights", "normalise", "spread", "totals")
 
@@ -83,6 +86,7 @@ def lib():
         L.al_line_forces_noalloc.argtypes = [C.POINTER(GridDesc), C.POINTER(BeamDesc), C.POINTER(StepIn),
                                              C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_int), _vp]
         L.al_trace_enable.argtypes = [_vp, C.c_int]
+        L.al_set_option.argtypes = [_vp, C.c_int, C.c_int]
         L.al_trace_last.argtypes = [_vp, C.POINTER(C.c_float)]
         L.al_error_string.restype = C.c_char_p
         L.al_error_string.argtypes = [C.c_int]
@@ -200,6 +204,11 @@ class Grid:
 
     def set_state(self, f_prev, has_prev: bool, stream=None) -> None:
         check(lib().al_set_state(self.h, _ptr(f_prev), int(bool(has_prev)), _stream_ptr(stream)), "al_set_state")
+
+    def set_option(self, option: int, value: int) -> None:
+        """al_set_option: execution choices that leave results within the
+        parity tolerances (e.g. OPT_WEIGHTS = WEIGHTS_BRICK | WEIGHTS_SEGMENT)."""
+        check(lib().al_set_option(self.h, int(option), int(value)), "al_set_option")
 
     def trace(self, on: bool = True) -> None:
         check(lib().al_trace_enable(self.h, int(bool(on))), "al_trace_enable")

@@ -62,14 +62,12 @@ struct al_grid_s {
          *fhat = nullptr;
     float *ulo = nullptr, *nodeTau = nullptr;
     double *segWa = nullptr, *segWb = nullptr, *w = nullptr, *lineF = nullptr;
+    unsigned long long *wfix = nullptr;
     al::LineG *lines = nullptr;
     uint32_t *mask = nullptr;
-    int *zeroList = nullptr;
 
     // per-grid scratch
     double *brickSum = nullptr;
-    int *zeroCount = nullptr;
-    double *depSum = nullptr;
     int *statusInt = nullptr;
     double *totalsInt = nullptr;
     int *hasPrev = nullptr;           // device flag: f_prev is valid
@@ -86,7 +84,7 @@ static void trace_mark(al_grid g, int i, cudaStream_t st) {
 static void free_beams(al_grid g) {
     void *ptrs[] = {g->d_line_off, g->d_line_of, g->d_d, g->d_cdn, g->d_cdt, g->d_eps, g->d_ell, g->d_af,
                     g->d_cvl, g->fprev, g->uhi, g->segD, g->segIl2, g->nodeM, g->fhat, g->ulo,
-                    g->nodeTau, g->segWa, g->segWb, g->w, g->lineF, g->lines, g->mask, g->zeroList};
+                    g->nodeTau, g->segWa, g->segWb, g->w, g->lineF, g->lines, g->mask, g->wfix};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     g->d_line_off = g->d_line_of = nullptr;
@@ -94,9 +92,9 @@ static void free_beams(al_grid g) {
     g->fprev = g->uhi = g->segD = g->segIl2 = g->nodeM = g->fhat = nullptr;
     g->ulo = g->nodeTau = nullptr;
     g->segWa = g->segWb = g->w = g->lineF = nullptr;
+    g->wfix = nullptr;
     g->lines = nullptr;
     g->mask = nullptr;
-    g->zeroList = nullptr;
     g->loaded = false;
     g->n_lines = g->n_points = g->mask_words = 0;
 }
@@ -154,7 +152,6 @@ extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
 
     cudaError_t e;
     if ((e = dalloc(&g->brickSum, 3 * (size_t)c.nbrick)) != cudaSuccess ||
-        (e = dalloc(&g->zeroCount, 1)) != cudaSuccess || (e = dalloc(&g->depSum, 3)) != cudaSuccess ||
         (e = dalloc(&g->statusInt, AL_STATUS_N)) != cudaSuccess || (e = dalloc(&g->totalsInt, 6)) != cudaSuccess ||
         (e = dalloc(&g->hasPrev, 1)) != cudaSuccess) {
         int rc = cuda_fail(e, "cudaMalloc");
@@ -214,10 +211,10 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     AB(&g->fprev, n3); AB(&g->uhi, n3); AB(&g->segD, n3); AB(&g->segIl2, (size_t)np); AB(&g->nodeM, n3);
     AB(&g->fhat, n3);
     A(&g->ulo, n3); A(&g->nodeTau, (size_t)np);
-    A(&g->segWa, (size_t)np); A(&g->segWb, (size_t)np); A(&g->w, (size_t)np); A(&g->lineF, 3 * nl);
+    A(&g->segWa, (size_t)np); A(&g->segWb, (size_t)np);
+    A(&g->wfix, (size_t)np); A(&g->w, (size_t)np); A(&g->lineF, 3 * nl);
     A(&g->lines, nl);
     A(&g->mask, (size_t)g->gc.nbrick * g->mask_words);
-    A(&g->zeroList, (size_t)np);
     if (e != cudaSuccess) {
         int rc = cuda_fail(e, "cudaMalloc");
         free_beams(g);
@@ -250,6 +247,32 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     return AL_OK;
 }
 
+// The projection kernels use more than 48 KB of dynamic shared memory.
+template <typename T>
+static cudaError_t spread_smem_attr() {
+    static cudaError_t done = cudaErrorNotReady;
+    if (done != cudaSuccess) {
+        const int bytes = (int)sizeof(al::SpreadSmem<T>);
+        done = cudaFuncSetAttribute(al::k_spread<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (done == cudaSuccess)
+            done = cudaFuncSetAttribute(al::kb_spread<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (done == cudaSuccess)
+            done = cudaFuncSetAttribute(al::k_bweights<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (done == cudaSuccess)
+            done = cudaFuncSetAttribute(al::kb_bweights<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        // prefer shared memory over L1 so that several bricks share an SM
+        if (done == cudaSuccess)
+            done = cudaFuncSetAttribute(al::k_spread<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (done == cudaSuccess)
+            done = cudaFuncSetAttribute(al::kb_spread<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (done == cudaSuccess)
+            done = cudaFuncSetAttribute(al::k_bweights<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (done == cudaSuccess)
+            done = cudaFuncSetAttribute(al::kb_bweights<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
+    return done;
+}
+
 template <typename T>
 static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out *out) {
     using namespace al;
@@ -270,9 +293,9 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     Scratch<T> &sc = I.sc;
     sc.fprev = (T *)g->fprev; sc.uhi = (T *)g->uhi; sc.ulo = g->ulo; sc.segD = (T *)g->segD;
     sc.segIl2 = (T *)g->segIl2; sc.nodeM = (T *)g->nodeM; sc.nodeTau = g->nodeTau;
-    sc.segWa = g->segWa; sc.segWb = g->segWb; sc.w = g->w; sc.fhat = (T *)g->fhat; sc.lineF = g->lineF;
-    sc.lines = g->lines; sc.mask = g->mask; sc.brickSum = g->brickSum; sc.zeroList = g->zeroList;
-    sc.zeroCount = g->zeroCount; sc.depSum = g->depSum; sc.hasPrev = g->hasPrev;
+    sc.segWa = g->segWa; sc.segWb = g->segWb; sc.wfix = g->wfix; sc.w = g->w; sc.fhat = (T *)g->fhat; sc.lineF = g->lineF;
+    sc.lines = g->lines; sc.mask = g->mask; sc.brickSum = g->brickSum;
+    sc.hasPrev = g->hasPrev;
     BeamsC &bc = I.b;
     bc.n_lines = g->n_lines; bc.n_points = np; bc.mask_words = g->mask_words;
     bc.line_off = g->d_line_off; bc.line_of = g->d_line_of;
@@ -298,9 +321,8 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
     int *status = I.status;
     const int np = g->n_points;
 
+    AL_CUDA(spread_smem_attr<T>());
     trace_mark(g, 0, st);
-    AL_CUDA(cudaMemsetAsync(g->zeroCount, 0, sizeof(int), st));
-    AL_CUDA(cudaMemsetAsync(g->depSum, 0, 3 * sizeof(double), st));
     const int nb = (np + 255) / 256;
     if (np > 0) {
         k_points<T><<<nb, 256, 0, st>>>(gc, bc, p, sc, status);
@@ -310,14 +332,17 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
     trace_mark(g, 1, st);
     if (np > 0) k_mask<T><<<nb, 256, 0, st>>>(gc, bc, sc);
     trace_mark(g, 2, st);
-    if (np > 0) k_weights<T><<<(unsigned)(((long long)np * 32 + 127) / 128), 128, 0, st>>>(gc, bc, sc, p, status);
-    trace_mark(g, 3, st);
-    if (np > 0) k_normalise<T><<<nb, 256, 0, st>>>(bc, sc, p, status);
-    trace_mark(g, 4, st);
     const size_t smem = sizeof(SpreadSmem<T>);
+    if (np > 0) {
+        if (gc.wmode != 0)
+            k_weights<T><<<(unsigned)(((long long)np * 32 + 127) / 128), 128, 0, st>>>(gc, bc, sc, p, status);
+        k_bweights<T><<<(unsigned)gc.nbrick, SPREAD_THREADS, smem, st>>>(gc, bc, sc, p, status);
+    }
+    trace_mark(g, 3, st);
+    if (np > 0) k_normalise<T><<<nb, 256, 0, st>>>(gc, bc, sc, p, status);
+    trace_mark(g, 4, st);
     k_spread<T><<<(unsigned)gc.nbrick, SPREAD_THREADS, smem, st>>>(gc, bc, sc, p, status);
     trace_mark(g, 5, st);
-    if (np > 0) k_deposit<T><<<1, 1, 0, st>>>(gc, bc, sc, p, status);
     k_totals<T><<<1, 256, 0, st>>>(gc, bc, sc, I.totals);
     trace_mark(g, 6, st);
     AL_CUDA(cudaGetLastError());
@@ -340,6 +365,18 @@ extern "C" int al_sample_drag_spread(al_grid g, const al_step_in *in, const al_s
     }
     cudaStream_t st = (cudaStream_t)stream;
     return g->d.precision == AL_FP64 ? step_impl<double>(g, in, out, st) : step_impl<float>(g, in, out, st);
+}
+
+extern "C" int al_set_option(al_grid g, int option, int value) {
+    if (!g) return AL_ERR_ARG;
+    switch (option) {
+    case AL_OPT_WEIGHTS:
+        if (value != AL_WEIGHTS_BRICK && value != AL_WEIGHTS_SEGMENT) return AL_ERR_ARG;
+        g->gc.wmode = value;
+        return AL_OK;
+    default:
+        return AL_ERR_ARG;
+    }
 }
 
 extern "C" int al_trace_enable(al_grid g, int on) {
@@ -368,7 +405,7 @@ extern "C" int al_destroy(al_grid g) {
     cudaDeviceSynchronize();
     if (g->trace) al_trace_enable(g, 0);
     free_beams(g);
-    void *ptrs[] = {g->brickSum, g->zeroCount, g->depSum, g->statusInt, g->totalsInt, g->hasPrev};
+    void *ptrs[] = {g->brickSum, g->statusInt, g->totalsInt, g->hasPrev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -430,6 +467,7 @@ struct al_batch_s {
     long long *d_pre = nullptr;               // 4 prefix arrays of n + 1: points, lines, bricks, points(warps)
     long long tot_pts = 0, tot_lines = 0, tot_bricks = 0;
     int spread_grid = 0, pt_grid = 0;
+    bool any_segment_weights = false;         // some instance sums weights per segment
     // subset runs: a ring of pinned host / device work lists
     static constexpr int RING = 8;
     int maxn = 0;
@@ -487,6 +525,7 @@ static int batch_commit_t(al_batch b, int spread_ctas_per_sm) {
         const bool used = b->grids[q] != nullptr;
         if (used) h[q] = make_inst<T>(b->grids[q], &b->ins[q], &b->outs[q]);
         else memset((void *)&h[q], 0, sizeof(Inst<T>));
+        if (used && b->grids[q]->gc.wmode != 0) b->any_segment_weights = true;
         pre[0 * (n + 1) + q + 1] = pre[0 * (n + 1) + q] + (used ? b->grids[q]->n_points : 0);
         pre[1 * (n + 1) + q + 1] = pre[1 * (n + 1) + q] + (used ? b->grids[q]->n_lines : 0);
         pre[2 * (n + 1) + q + 1] = pre[2 * (n + 1) + q] + (used ? b->grids[q]->gc.nbrick : 0);
@@ -513,6 +552,7 @@ static int batch_commit_t(al_batch b, int spread_ctas_per_sm) {
     AL_CUDA(cudaMalloc(&b->d_pre, sizeof(long long) * pre.size()));
     AL_CUDA(cudaMemcpy(b->d_inst, h.data(), sizeof(Inst<T>) * n, cudaMemcpyHostToDevice));
     AL_CUDA(cudaMemcpy(b->d_pre, pre.data(), sizeof(long long) * pre.size(), cudaMemcpyHostToDevice));
+    AL_CUDA(spread_smem_attr<T>());
     int dev = 0, nsm = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -536,7 +576,6 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
         long long g = (items + per_block - 1) / per_block;
         return (unsigned)std::max<long long>(1, std::min<long long>(g, (long long)b->pt_grid * 4));
     };
-    kb_reset<T><<<(n + 127) / 128, 128, 0, st>>>(I, sel, n);
     if (tot_pts > 0) {
         kb_points<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
         kb_segments<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
@@ -544,14 +583,17 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
     if (tot_lines > 0) kb_lines<T><<<grid_for(tot_lines, 8), 256, 0, st>>>(I, sel, pl, n);
     if (tot_pts > 0) {
         kb_mask<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
-        kb_weights<T><<<grid_for(tot_pts, 4), 128, 0, st>>>(I, sel, pp, n);
+        if (b->any_segment_weights) kb_weights<T><<<grid_for(tot_pts, 4), 128, 0, st>>>(I, sel, pp, n);
+        if (tot_bricks > 0) {
+            const int gs = (int)std::min<long long>(b->spread_grid, tot_bricks);
+            kb_bweights<T><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T>), st>>>(I, sel, pb, n);
+        }
         kb_normalise<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
     }
     if (tot_bricks > 0) {
         const int gs = (int)std::min<long long>(b->spread_grid, tot_bricks);
         kb_spread<T><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T>), st>>>(I, sel, pb, n);
     }
-    kb_deposit<T><<<(n + 127) / 128, 128, 0, st>>>(I, sel, n);
     kb_totals<T><<<std::max(1, std::min(n, 1024)), 256, 0, st>>>(I, sel, n);
     AL_CUDA(cudaGetLastError());
     return AL_OK;
@@ -578,6 +620,7 @@ static int batch_assign_t(al_batch b, int slot, al_grid g, const al_step_in *in,
     AL_CUDA(cudaEventRecord(b->slot_ev[slot], st));
     b->grids[slot] = g;
     if (g) { b->ins[slot] = *in; b->outs[slot] = *out; }
+    if (g && g->gc.wmode != 0) b->any_segment_weights = true;
     b->cnt_pts[slot] = g ? g->n_points : 0;
     b->cnt_lines[slot] = g ? g->n_lines : 0;
     b->cnt_bricks[slot] = g ? g->gc.nbrick : 0;

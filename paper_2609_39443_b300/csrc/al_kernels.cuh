@@ -36,7 +36,7 @@ namespace al {
 
 constexpr int BX = 16, BY = 16, BZ = 8;          // spread brick (cells)
 constexpr int SPREAD_THREADS = BX * BY;          // one thread per column
-constexpr float BRICK_DIAG = 24.0f;              // sqrt(16^2+16^2+8^2)
+constexpr float BRICK_DIAG = 24.0f;              // tsqrt(16^2+16^2+8^2)
 constexpr double PI_D = 3.14159265358979323846;
 
 enum { ST_PA_OUTSIDE = 0, ST_PS_OUTSIDE = 1, ST_FALLBACK = 2, ST_FALLBACK_ZERO = 3,
@@ -52,6 +52,7 @@ struct GridC {
     float ih_hi, ih_lo;          // float-float 1/h
     int has_alpha;
     double rho1, rho2, rho_const;
+    int wmode;                   // 0: all weights from the brick pass; 1: segment pass for certified lines
 };
 
 struct BeamsC {
@@ -65,9 +66,14 @@ struct BeamsC {
 struct LineG {                   // per line, rebuilt every step
     float Rc;                    // 3 eps in cell units (box slack only)
     double R2c, inv_eps2c;       // (3 eps)^2, 1/eps^2 in cell units
+    double inv_eps2c_l2;         // log2(e) / eps^2 in cell units (Gaussian as a power of 2)
     double eta0;                 // 1 / (pi eps^2) in 1/m^2
-    int regular;                 // closest segment by monotone bisector walk
+    int regular;                 // 0: exhaustive search; 1: walk from any candidate; 2: walk from near the foot
     int first, n;
+    float thmax;                 // largest turning angle at a node (rad)
+    float Lmin, Lmax;            // shortest / longest segment (cells)
+    float rho2;                  // regular == 2: a walk may start at a node within sqrt(rho2) cells
+    int wshift;                  // fixed-point weights: omega eta / eta0 in units of 2^-wshift
 };
 
 template <typename T>
@@ -80,15 +86,13 @@ struct Scratch {
     T *nodeM;                    // [3][np] unit bisector at interior nodes
     float *nodeTau;              // [np] tan(theta_k / 2) at interior nodes
     double *segWa, *segWb;       // [np] weight of segment k to its two nodes
+    unsigned long long *wfix;    // [np] w_k / (eta0 V) in units of 2^-wshift (brick weights pass)
     double *w;                   // [np] w_k
     T *fhat;                     // [3][np] normalised nodal force
     double *lineF;               // [3][n_lines] sum of F per line
     LineG *lines;                // [n_lines]
     uint32_t *mask;              // [nbrick][mask_words] lines touching a brick
     double *brickSum;            // [3][nbrick] sum of S per brick
-    int *zeroList;               // [np]
-    int *zeroCount;              // [1]
-    double *depSum;              // [3]
     int *hasPrev;                // [1] a previous relaxed force exists (set by k_totals)
 };
 
@@ -114,13 +118,33 @@ template <> struct Tr<float> {
     static __device__ __forceinline__ float gsig(float x) { return 4e-6f * (x + 8.0f); }
     // r^2 error <= ~1e-4 cells^2 at R = 9 cells; band 1e-5 R^2 + 1e-4
     static __device__ __forceinline__ float grr(float R2) { return 1e-5f * R2 + 1e-4f; }
-    static __device__ __forceinline__ float ex(float x) { return expf(x); }
+    // 2^y with the SFU's ex2 instruction (relative error below 2^-22 over the
+    // arguments used here, y in [-13, 0]); the Gaussian is evaluated as
+    // exp(-(r/eps)^2) = 2^(-(r/eps)^2 log2 e)
+    static __device__ __forceinline__ float ex2(float y) {
+        float r;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+        return r;
+    }
 };
 template <> struct Tr<double> {
     static __device__ __forceinline__ double gsig(double x) { return 1e-12 * (x + 8.0); }
     static __device__ __forceinline__ double grr(double R2) { return 1e-12 * R2 + 1e-12; }
-    static __device__ __forceinline__ double ex(double x) { return exp(x); }
+    static __device__ __forceinline__ double ex2(double y) { return exp2(y); }
 };
+
+// precision-dispatched math: float arguments always take the float
+// instructions (a double overload would route through the FP64 pipe)
+__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float tabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double tabs(double a) { return fabs(a); }
+__device__ __forceinline__ float tfloor(float a) { return floorf(a); }
+__device__ __forceinline__ double tfloor(double a) { return floor(a); }
 
 // ---------------------------------------------------------------------------
 // float-float helpers (error-free transformations, Knuth / Dekker)
@@ -179,17 +203,55 @@ __device__ __forceinline__ bool inside_axis(T uh, float ul, int n) {
 // floor of uh + ul
 template <typename T>
 __device__ __forceinline__ int ffloor(T uh, float ul) {
-    T f = floor(uh);
+    T f = tfloor(uh);
     int c = (int)f;
     if (f == uh && ul < 0.0f) c -= 1;
     return c;
 }
+
+// floor / ceil of |x| < 2^22 as floats, by rounding with the 1.5 * 2^23
+// shift (no conversion instruction)
+__device__ __forceinline__ float ffloor_f(float x) {
+    float r = __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+    return r > x ? r - 1.0f : r;
+}
+__device__ __forceinline__ float fceil_f(float x) {
+    float r = __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+    return r < x ? r + 1.0f : r;
+}
+__device__ __forceinline__ double ffloor_f(double x) { return floor(x); }
+__device__ __forceinline__ double fceil_f(double x) { return ceil(x); }
 
 // floor / ceil in the arithmetic type (no FP64 for FP32 instances)
 __device__ __forceinline__ int ifloor(float x) { return (int)floorf(x); }
 __device__ __forceinline__ int ifloor(double x) { return (int)floor(x); }
 __device__ __forceinline__ int iceil(float x) { return (int)ceilf(x); }
 __device__ __forceinline__ int iceil(double x) { return (int)ceil(x); }
+
+// v * 2^sh for 0 <= v <= 1, truncated, from the bits of v (integer
+// operations only).  Integer sums of these are exact and independent of the
+// order of the additions, so atomics keep the weights deterministic.  The
+// per-line shift keeps every node's sum below 2^63.
+__device__ __forceinline__ unsigned long long to_fixed(float v, int sh) {
+    const unsigned int bits = __float_as_uint(v);
+    const int e = (int)((bits >> 23) & 0xffu);
+    if (e == 0 || (bits >> 31)) return 0ull;               // zero, subnormal or negative
+    const unsigned long long m = (unsigned long long)((bits & 0x7fffffu) | 0x800000u);
+    const int s = e - 150 + sh;                            // v 2^sh = m 2^(e - 150 + sh)
+    if (s >= 0) return m << s;
+    if (s <= -24) return 0ull;
+    return m >> (-s);
+}
+__device__ __forceinline__ unsigned long long to_fixed(double v, int sh) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((bits >> 52) & 0x7ffull);
+    if (e == 0 || (bits >> 63)) return 0ull;
+    const unsigned long long m = (bits & 0xfffffffffffffull) | 0x10000000000000ull;
+    const int s = e - 1075 + sh;
+    if (s >= 0) return m << s;
+    if (s <= -53) return 0ull;
+    return m >> (-s);
+}
 
 // ---------------------------------------------------------------------------
 // sampling: trilinear (default) or containing cell
@@ -200,7 +262,7 @@ __device__ __forceinline__ void axis_stencil(T uh, float ul, int n, int &i0, T &
     T xh = uh - (T)0.5;                     // coordinate in cell-centre units: xh + ul
     if (xh + (T)ul <= (T)0) { i0 = 0; t = (T)0; return; }
     if (xh + (T)ul >= (T)(n - 1)) { i0 = n - 2; t = (T)1; return; }
-    int i = (int)floor(xh);
+    int i = (int)tfloor(xh);
     T fr = (xh - (T)i) + (T)ul;
     if (fr < (T)0) { i -= 1; fr += (T)1; }
     else if (fr >= (T)1) { i += 1; fr -= (T)1; }
@@ -247,6 +309,11 @@ __device__ bool sample(const GridC &g, int mode, const S *const *f, int ncomp,
     return true;
 }
 
+// 1/h in the arithmetic type (no FP64 division for FP32 instances)
+template <typename C> __device__ __forceinline__ C inv_h(const GridC &g);
+template <> __device__ __forceinline__ float inv_h<float>(const GridC &g) { return g.ih_hi; }
+template <> __device__ __forceinline__ double inv_h<double>(const GridC &g) { return 1.0 / g.h; }
+
 // Quasi-steady line force f* of one actuator point (Secs. 3.2.2-3.2.3) in the
 // arithmetic type C from fields stored as T: preliminary sample, upstream
 // direction with fallback, sampling point, upstream sample (+ alpha,
@@ -271,9 +338,9 @@ __device__ int point_fstar(const GridC &g, const BeamsC &b, const StepPtrs<T> &p
     for (int a = 0; a < 3; ++a) u0r[a] = Ua[a] - Pd[a];
     C ut = u0r[0] * t[0] + u0r[1] * t[1] + u0r[2] * t[2];
     for (int a = 0; a < 3; ++a) u0n[a] = u0r[a] - ut * t[a];
-    C nn = sqrt(u0n[0] * u0n[0] + u0n[1] * u0n[1] + u0n[2] * u0n[2]);
+    C nn = tsqrt(u0n[0] * u0n[0] + u0n[1] * u0n[1] + u0n[2] * u0n[2]);
     if (refine_ok) {
-        C scale = sqrt(Ua[0] * Ua[0] + Ua[1] * Ua[1] + Ua[2] * Ua[2]) + sqrt(Pd[0] * Pd[0] + Pd[1] * Pd[1] + Pd[2] * Pd[2]);
+        C scale = tsqrt(Ua[0] * Ua[0] + Ua[1] * Ua[1] + Ua[2] * Ua[2]) + tsqrt(Pd[0] * Pd[0] + Pd[1] * Pd[1] + Pd[2] * Pd[2]);
         if (nn < (C)1e-2 * scale) return 1;
     }
     if ((double)nn >= b.tau) {
@@ -283,7 +350,7 @@ __device__ int point_fstar(const GridC &g, const BeamsC &b, const StepPtrs<T> &p
         C gp[3];
         C gt = (C)b.g_up[0] * t[0] + (C)b.g_up[1] * t[1] + (C)b.g_up[2] * t[2];
         for (int a = 0; a < 3; ++a) gp[a] = (C)b.g_up[a] - gt * t[a];
-        C gn = sqrt(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2]);
+        C gn = tsqrt(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2]);
         if (gn > (C)0) for (int a = 0; a < 3; ++a) es[a] = gp[a] / gn;
         else { es[0] = es[1] = es[2] = (C)0; atomicAdd(&status[ST_FALLBACK_ZERO], 1); }
     }
@@ -295,7 +362,7 @@ __device__ int point_fstar(const GridC &g, const BeamsC &b, const StepPtrs<T> &p
     C us[3];
     float ls[3];
     for (int a = 0; a < 3; ++a) {
-        C off_c = (v[a] - (C)b.n_p[a] * vn) * (C)(1.0 / g.h);
+        C off_c = (v[a] - (C)b.n_p[a] * vn) * inv_h<C>(g);
         ff_add(ua[a], la[a], off_c, us[a], ls[a]);
     }
     C Us[3], as = (C)0;
@@ -317,11 +384,11 @@ __device__ int point_fstar(const GridC &g, const BeamsC &b, const StepPtrs<T> &p
     const C half = (C)0.5 * rho * (C)b.d[l];
     const C cdn = (C)b.cdn[l], cdt = (C)b.cdt[l];
     if (b.drag_mode == 0) {
-        C m = sqrt(Ur[0] * Ur[0] + Ur[1] * Ur[1] + Ur[2] * Ur[2]);
+        C m = tsqrt(Ur[0] * Ur[0] + Ur[1] * Ur[1] + Ur[2] * Ur[2]);
         for (int a = 0; a < 3; ++a) fstar[a] = half * m * (cdn * Un[a] + cdt * Ut[a]);
     } else {
-        C mt = sqrt(Ut[0] * Ut[0] + Ut[1] * Ut[1] + Ut[2] * Ut[2]);
-        C mn = sqrt(Un[0] * Un[0] + Un[1] * Un[1] + Un[2] * Un[2]);
+        C mt = tsqrt(Ut[0] * Ut[0] + Ut[1] * Ut[1] + Ut[2] * Ut[2]);
+        C mn = tsqrt(Un[0] * Un[0] + Un[1] * Un[1] + Un[2] * Un[2]);
         for (int a = 0; a < 3; ++a) fstar[a] = half * (cdt * mt * Ut[a] + cdn * mn * Un[a]);
     }
     return 0;
@@ -349,7 +416,7 @@ __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, 
         for (int a = 0; a < 3; ++a) t[a] = p.P[a][ip] - p.P[a][im];
     }
     {
-        T nn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+        T nn = tsqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
         if (nn > (T)0) for (int a = 0; a < 3; ++a) t[a] /= nn;
         else t[0] = t[1] = t[2] = (T)0;
     }
@@ -383,6 +450,7 @@ __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, 
         sc.fprev[a * np + i] = f;
         p.F[a][i] = f * L;
     }
+    sc.wfix[i] = 0ull;                                   // fixed-point weights start at zero
     // projection positions in cell units
     for (int a = 0; a < 3; ++a) {
         T uh;
@@ -419,8 +487,8 @@ __device__ void d_segments(const BeamsC &b, const Scratch<T> &sc, const int k) {
     if (q >= 1 && q <= n - 2) {
         T t0[3], t1[3];
         for (int a = 0; a < 3; ++a) { t0[a] = ff_diff(sc, np, a, k, k - 1); t1[a] = ff_diff(sc, np, a, k + 1, k); }
-        T n0 = sqrt(t0[0] * t0[0] + t0[1] * t0[1] + t0[2] * t0[2]);
-        T n1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+        T n0 = tsqrt(t0[0] * t0[0] + t0[1] * t0[1] + t0[2] * t0[2]);
+        T n1 = tsqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
         float tau = 1e30f;
         T m[3] = {(T)0, (T)0, (T)0};
         if (n0 > (T)0 && n1 > (T)0) {
@@ -428,9 +496,9 @@ __device__ void d_segments(const BeamsC &b, const Scratch<T> &sc, const int k) {
             T c = t0[0] * t1[0] + t0[1] * t1[1] + t0[2] * t1[2];
             T cx = t0[1] * t1[2] - t0[2] * t1[1], cy = t0[2] * t1[0] - t0[0] * t1[2],
               cz = t0[0] * t1[1] - t0[1] * t1[0];
-            T sn = sqrt(cx * cx + cy * cy + cz * cz);
+            T sn = tsqrt(cx * cx + cy * cy + cz * cz);
             if ((T)1 + c > (T)1e-3) tau = (float)(sn / ((T)1 + c));   // tan(theta/2)
-            T mn = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+            T mn = tsqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
             if (mn > (T)0) for (int a = 0; a < 3; ++a) m[a] /= mn;
         }
         for (int a = 0; a < 3; ++a) sc.nodeM[a * np + k] = m[a];
@@ -444,22 +512,40 @@ __device__ void d_segments(const BeamsC &b, const Scratch<T> &sc, const int k) {
 // ---------------------------------------------------------------------------
 // k_lines: one warp per line
 //
-// Regularity certificate.  For a cell C and interior node k let
-// sigma_k(C) = (C - P_k) . m_k with m_k the bisector of the two segment
-// directions.  When the perpendicular distance rho of C from segment k's
-// axis satisfies rho (tan(theta_k/2) + tan(theta_{k+1}/2)) < L_k, the sign
-// of sigma_k(C) orders the distances to segments k-1 and k, and the signs
-// are monotone along the line; then the closest segment is the last k with
-// sigma_k(C) > 0 and a walk finds it.  The line is certified when
-//   * every segment has length > 1e-3 cells,
-//   * every segment direction makes an angle < ~72 deg with the chord
-//     (c_a = min t.a > 0.3), so that segments within 3 eps of a cell lie in
-//     one window of arc length <= 2E / c_a,
-//   * Dw (tau_k + tau_{k+1}) <= L_k / 2 for every segment, with
-//     E = brick diagonal + sqrt(3) R + 2 L_max and Dw = E (1 + 2 / c_a),
-//     the largest distance between a cell of a brick and a node the walk
-//     can evaluate for it.
-// Lines that fail take the exhaustive search instead.
+// Walk certificate.  For a cell C and interior node k let
+// sigma_k(C) = (C - P_k) . m_k with m_k the unit bisector of the two segment
+// directions.  If the perpendicular distance rho of C from segment k's axis
+// satisfies rho (tan(theta_k/2) + tan(theta_{k+1}/2)) < L_k, then
+// sigma_k(C) <= 0 implies sigma_{k+1}(C) < 0, and the sign of sigma_k(C)
+// orders the distances to segments k-1 and k (their common node is within
+// reach of both feet).  On a run of nodes where this holds the signs are
+// monotone, and the closest segment is the last k with sigma_k(C) > 0,
+// which a walk finds.  Only cells within R = 3 eps matter (farther cells
+// receive nothing).  Two certificates, both requiring every segment longer
+// than 1e-3 cells and, with margin 2, the inequality above for every segment:
+//
+// regular = 1: for every node of the arc a walk over a brick's candidate
+//   segments can visit.  That arc is at most S = min((brick diagonal +
+//   2 sqrt(3) R + 2 L_max) / c_a, line length) long (c_a = min over segments
+//   of direction . chord, > 0.3), so rho <= R + S min(Theta, 1) with
+//   Theta = (S / L_min + 2) theta_max bounding its turning.  A walk may start
+//   at any candidate segment.
+//
+// regular = 2: lines that climb (every segment's |D_z| / |D| >= c_z > 0.3,
+//   one sign).  Let K be the nodes within rho_s of C, rho_s = r_h + L_max +
+//   0.1 with r_h the crossing-disc radius below (so the segment crossing a
+//   cell's layer starts within rho_s of every cell in its disc).  Two nodes
+//   of K are at most 2 rho_s apart, so the arc between them is at most
+//   lambda = 2 rho_s / c + L_max long, c = cos(Theta_l / 2) with Theta_l the
+//   total turning of the line (all tangents of an arc lie in a cone of
+//   half-angle Theta_l / 2, hence chord >= c arc), and it departs from the
+//   chord by at most lambda/2 sin(Theta_w), Theta_w = min(Theta_l,
+//   (lambda / L_min + 1) theta_max).  Every node between two nodes of K is
+//   then within rho_s + lambda/2 sin(Theta_w) of C; certifying that radius
+//   makes the signs monotone between any two nodes of K.  A walk that starts
+//   in K (checked: |C - P_start| <= rho_s) ends at the closest segment when
+//   that segment is within R, and a walk that ends within R has found the
+//   closest segment whatever its start.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
@@ -477,44 +563,79 @@ __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     if (lane == 0)
         for (int a = 0; a < 3; ++a) sc.lineF[3 * l + a] = fs[a];
 
-    // certificate
-    int ok = (n >= 2);
-    float Lmin = 1e30f, Lmax = 0.0f, ca = 1.0f;
+    // geometry of the line
+    float Lmin = 1e30f, Lmax = 0.0f, ca = 1.0f, czp = 1.0f, czn = 1.0f;
     T ax[3] = {(T)0, (T)0, (T)0};
+    int chord_ok = 0;
     if (n >= 2) {
         for (int a = 0; a < 3; ++a) ax[a] = ff_diff(sc, np, a, off + n - 1, off);
-        T an = sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
-        if (an > (T)0) for (int a = 0; a < 3; ++a) ax[a] /= an;
-        else ok = 0;
+        T an = tsqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
+        if (an > (T)0) { for (int a = 0; a < 3; ++a) ax[a] /= an; chord_ok = 1; }
     }
+    float Ltot = 0.0f, thmax = 0.0f, thsum = 0.0f;
     for (int q = lane; q < n - 1; q += 32) {
         const int k = off + q;
         T D0 = sc.segD[k], D1 = sc.segD[np + k], D2 = sc.segD[2 * np + k];
-        float L = (float)sqrt(D0 * D0 + D1 * D1 + D2 * D2);
+        float L = (float)tsqrt(D0 * D0 + D1 * D1 + D2 * D2);
         Lmin = fminf(Lmin, L);
         Lmax = fmaxf(Lmax, L);
+        Ltot += L;
         float c = L > 0.0f ? (float)((D0 * ax[0] + D1 * ax[1] + D2 * ax[2])) / L : -1.0f;
         ca = fminf(ca, c);
+        const float cz = L > 0.0f ? (float)D2 / L : 0.0f;
+        czp = fminf(czp, cz);
+        czn = fminf(czn, -cz);
+        if (q >= 1) {
+            const float th = 2.0f * atanf(sc.nodeTau[k]);
+            thmax = fmaxf(thmax, th);
+            thsum += th;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         Lmin = fminf(Lmin, __shfl_xor_sync(0xffffffffu, Lmin, o));
         Lmax = fmaxf(Lmax, __shfl_xor_sync(0xffffffffu, Lmax, o));
         ca = fminf(ca, __shfl_xor_sync(0xffffffffu, ca, o));
+        czp = fminf(czp, __shfl_xor_sync(0xffffffffu, czp, o));
+        czn = fminf(czn, __shfl_xor_sync(0xffffffffu, czn, o));
+        Ltot += __shfl_xor_sync(0xffffffffu, Ltot, o);
+        thsum += __shfl_xor_sync(0xffffffffu, thsum, o);
+        thmax = fmaxf(thmax, __shfl_xor_sync(0xffffffffu, thmax, o));
     }
-    if (!(Lmin > 1e-3f) || !(ca > 0.3f)) ok = 0;
-    if (ok) {
-        const float E = BRICK_DIAG + 1.7320508f * Rc + 2.0f * Lmax;
-        const float Dw = E * (1.0f + 2.0f / ca);
-        int bad = 0;
+    const bool base_ok = (n >= 2) && (Lmin > 1e-3f);
+    // radius within which the bisector signs must be monotone, per certificate
+    float D1c = -1.0f, D2c = -1.0f, rho_s = 0.0f;
+    if (base_ok && chord_ok && ca > 0.3f) {
+        const float S = fminf((BRICK_DIAG + 2.0f * 1.7320508f * Rc + 2.0f * Lmax) / ca, Ltot);
+        const float Theta = (S / Lmin + 2.0f) * thmax;
+        D1c = Rc + S * fminf(Theta, 1.0f) + 0.01f;
+    }
+    const float czl = fmaxf(czp, czn);
+    if (base_ok && n >= 3 && czl > 0.3f) {
+        const float lam = Rc / czl + Lmax;
+        const float turn = (lam / Lmin + 1.0f) * thmax;
+        const float rh = (Rc + lam * fminf(1.0f, turn) + 0.02f) / czl + 0.02f;
+        rho_s = rh + Lmax + 0.1f;
+        const float c = cosf(0.5f * fminf(thsum, 3.0f));
+        if (c > 0.3f) {
+            const float lw = 2.0f * rho_s / c + Lmax;
+            const float thw = fminf(thsum, (lw / Lmin + 1.0f) * thmax);
+            if (thw < 1.2f) D2c = rho_s + 0.5f * lw * sinf(thw) + 0.05f;
+        }
+    }
+    int ok1 = D1c > 0.0f, ok2 = D2c > 0.0f;
+    if (ok1 || ok2) {
+        int bad1 = 0, bad2 = 0;
         for (int q = lane; q < n - 1; q += 32) {
             const int k = off + q;
             float t0 = (q >= 1) ? sc.nodeTau[k] : 0.0f;
             float t1 = (q + 1 <= n - 2) ? sc.nodeTau[k + 1] : 0.0f;
             T D0 = sc.segD[k], D1 = sc.segD[np + k], D2 = sc.segD[2 * np + k];
-            float L = (float)sqrt(D0 * D0 + D1 * D1 + D2 * D2);
-            if (!(Dw * (t0 + t1) <= 0.5f * L)) bad = 1;
+            float L = (float)tsqrt(D0 * D0 + D1 * D1 + D2 * D2);
+            if (!(D1c * (t0 + t1) <= 0.5f * L)) bad1 = 1;
+            if (!(D2c * (t0 + t1) <= 0.5f * L)) bad2 = 1;
         }
-        if (__any_sync(0xffffffffu, bad)) ok = 0;
+        if (__any_sync(0xffffffffu, bad1)) ok1 = 0;
+        if (__any_sync(0xffffffffu, bad2)) ok2 = 0;
     }
     if (lane == 0) {
         LineG lg;
@@ -522,14 +643,28 @@ __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
         lg.Rc = Rc;
         lg.R2c = 9.0 * ec * ec;
         lg.inv_eps2c = 1.0 / (ec * ec);
+        lg.inv_eps2c_l2 = 1.4426950408889634 / (ec * ec);
         lg.eta0 = 1.0 / (PI_D * eps * eps);
-        lg.regular = ok;
+        lg.regular = ok2 ? 2 : (ok1 ? 1 : 0);
         lg.first = off;
         lg.n = n;
+        lg.thmax = thmax;
+        lg.Lmin = Lmin;
+        lg.Lmax = Lmax;
+        lg.rho2 = rho_s * rho_s;
+        // largest possible fixed-point sum at a node: the cells within R of
+        // its two segments, each omega eta / eta0 <= 1
+        const float Rp = Rc + 1.0f;
+        const float Q = 3.1415927f * Rp * Rp * 2.0f * (n >= 2 ? Lmax : 0.0f) + 4.1887903f * Rp * Rp * Rp + 1.0f;
+        int sh = 62 - (int)ceilf(log2f(Q));
+        lg.wshift = max(20, min(sh, 60));
         sc.lines[l] = lg;
-        if (!ok && n > 0) atomicAdd(&status[ST_IRREGULAR], 1);
+        if (lg.regular == 0 && n > 0) atomicAdd(&status[ST_IRREGULAR], 1);
     }
 }
+
+// node index of the far end of segment k of a line (first, n)
+__device__ __forceinline__ int seg_end(int k, int n) { return n == 1 ? k : k + 1; }
 
 // conservative R-inflated box of segment k (nodes ka, kb) in cell units
 template <typename T>
@@ -537,7 +672,7 @@ __device__ __forceinline__ void seg_box(const Scratch<T> &sc, long long np, int 
                                         float lo[3], float hi[3]) {
     for (int a = 0; a < 3; ++a) {
         float ua = (float)sc.uhi[a * np + ka], ub = (float)sc.uhi[a * np + kb];
-        float slack = R + 0.01f + 1e-5f * (fabsf(ua) + 1.0f);
+        float slack = fmaxf(R, 0.5f) + 0.01f + 1e-5f * (fabsf(ua) + 1.0f);
         lo[a] = fminf(ua, ub) - slack;
         hi[a] = fmaxf(ua, ub) + slack;
     }
@@ -581,14 +716,15 @@ __device__ void d_mask(const GridC &g, const BeamsC &b, const Scratch<T> &sc, co
 // segment distance evaluated from the caller's original positions.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __noinline__ double dist2_f64(const GridC &g, const StepPtrs<T> &p, int ka, int kb, int ci, int cj, int ck,
-                            double *s_out) {
-    const double c[3] = {__dadd_rn(g.o[0], __dmul_rn((double)ci + 0.5, g.h)),
-                         __dadd_rn(g.o[1], __dmul_rn((double)cj + 0.5, g.h)),
-                         __dadd_rn(g.o[2], __dmul_rn((double)ck + 0.5, g.h))};
+__device__ __noinline__ double dist2_f64_raw(const T *P0, const T *P1, const T *P2, double ox, double oy,
+                                             double oz, double h, int ka, int kb, int ci, int cj, int ck) {
+    const double c[3] = {__dadd_rn(ox, __dmul_rn((double)ci + 0.5, h)),
+                         __dadd_rn(oy, __dmul_rn((double)cj + 0.5, h)),
+                         __dadd_rn(oz, __dmul_rn((double)ck + 0.5, h))};
+    const T *P[3] = {P0, P1, P2};
     double D[3], q[3];
     for (int a = 0; a < 3; ++a) {
-        double A = (double)p.Ps[a][ka], B = (double)p.Ps[a][kb];
+        double A = (double)P[a][ka], B = (double)P[a][kb];
         D[a] = __dsub_rn(B, A);
         q[a] = __dsub_rn(c[a], A);
     }
@@ -601,36 +737,44 @@ __device__ __noinline__ double dist2_f64(const GridC &g, const StepPtrs<T> &p, i
     }
     double e[3];
     for (int a = 0; a < 3; ++a) e[a] = __dsub_rn(q[a], __dmul_rn(s, D[a]));
-    if (s_out) *s_out = s;
     return __dadd_rn(__dadd_rn(__dmul_rn(e[0], e[0]), __dmul_rn(e[1], e[1])), __dmul_rn(e[2], e[2]));
 }
-// node index of the far end of segment k of a line (first, n)
-__device__ __forceinline__ int seg_end(int k, int n) { return n == 1 ? k : k + 1; }
+template <typename T>
+__device__ __forceinline__ double dist2_f64(const GridC &g, const StepPtrs<T> &p, int ka, int kb, int ci, int cj,
+                                            int ck) {
+    return dist2_f64_raw(p.Ps[0], p.Ps[1], p.Ps[2], g.o[0], g.o[1], g.o[2], g.h, ka, kb, ci, cj, ck);
+}
 
 // d_k < d_{k-1} in FP64 (segment k closer than k-1; ties keep k-1)
 template <typename T>
-__device__ bool later_closer_f64(const GridC &g, const StepPtrs<T> &p, int k, int ci, int cj, int ck) {
-    double d1 = dist2_f64(g, p, k, k + 1, ci, cj, ck, nullptr);
-    double d0 = dist2_f64(g, p, k - 1, k, ci, cj, ck, nullptr);
-    return sqrt(d1) < sqrt(d0);
+__device__ __forceinline__ bool later_closer_f64(const GridC &g, const StepPtrs<T> &p, int k, int ci, int cj, int ck) {
+    double d1 = dist2_f64(g, p, k, k + 1, ci, cj, ck);
+    double d0 = dist2_f64(g, p, k - 1, k, ci, cj, ck);
+    return __dsqrt_rn(d1) < __dsqrt_rn(d0);
 }
 // r <= 3 eps in FP64 for segment k
 template <typename T>
-__device__ bool within_f64(const GridC &g, const StepPtrs<T> &p, double eps, int k, int n, int ci, int cj,
-                           int ck) {
-    double d2 = dist2_f64(g, p, k, seg_end(k, n), ci, cj, ck, nullptr);
+__device__ __forceinline__ bool within_f64(const GridC &g, const StepPtrs<T> &p, double eps, int k, int n, int ci,
+                                           int cj, int ck) {
+    double d2 = dist2_f64(g, p, k, seg_end(k, n), ci, cj, ck);
     return __dsqrt_rn(d2) <= __dmul_rn(3.0, eps);
 }
 // argmin over segments [k0, k1] in FP64, lowest index on ties
 template <typename T>
-__device__ __noinline__ int argmin_f64(const GridC &g, const StepPtrs<T> &p, int k0, int k1, int n, int ci, int cj, int ck) {
+__device__ __noinline__ int argmin_f64_raw(const T *P0, const T *P1, const T *P2, double ox, double oy, double oz,
+                                           double h, int k0, int k1, int n, int ci, int cj, int ck) {
     double best = INFINITY;
     int kb = k0;
     for (int k = k0; k <= k1; ++k) {
-        double r = __dsqrt_rn(dist2_f64(g, p, k, seg_end(k, n), ci, cj, ck, nullptr));
+        double r = __dsqrt_rn(dist2_f64_raw(P0, P1, P2, ox, oy, oz, h, k, seg_end(k, n), ci, cj, ck));
         if (r < best) { best = r; kb = k; }
     }
     return kb;
+}
+template <typename T>
+__device__ __forceinline__ int argmin_f64(const GridC &g, const StepPtrs<T> &p, int k0, int k1, int n, int ci,
+                                          int cj, int ck) {
+    return argmin_f64_raw(p.Ps[0], p.Ps[1], p.Ps[2], g.o[0], g.o[1], g.o[2], g.h, k0, k1, n, ci, cj, ck);
 }
 
 // ---------------------------------------------------------------------------
@@ -657,7 +801,7 @@ template <typename T> struct Acc {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct WSeg {
-    int k, q, n, off, nseg, kb;
+    int k, q, n, off, nseg, kb, klo, khi;     // klo/khi unused (kept zero-cost)
     int O[3], lo[3], hi[3];
     T A[3], Bn[3], D[3], il2;
     T m0[3], m1[3];
@@ -668,56 +812,35 @@ struct WSeg {
 
 // membership of cell cg (local centre C) in segment ctx.k and its weights
 template <typename T>
-__device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const int cg[3], const GridC &g,
+__device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const GridC &g,
                                        const Scratch<T> &sc, const StepPtrs<T> &p, bool regular,
                                        int *status, Acc<T> &wa, Acc<T> &wb) {
     const long long np = (long long)p.np;
+    // global cell index, needed only by the FP64 re-decisions (rare)
+#define AL_CG(a) (ifloor(C[a]) + c.O[a])
     T x[3];
     for (int a = 0; a < 3; ++a) x[a] = C[a] - c.A[a];
     if (regular) {
         if (c.has_lo) {
             T sg = x[0] * c.m0[0] + x[1] * c.m0[1] + x[2] * c.m0[2];
-            T gs = Tr<T>::gsig(sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
+            T gs = Tr<T>::gsig(tsqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
             bool pos;
             if (sg > gs) pos = true;
             else if (sg < -gs) pos = false;
-            else { pos = later_closer_f64(g, p, c.k, cg[0], cg[1], cg[2]); atomicAdd(&status[ST_REFINED], 1); }
+            else { pos = later_closer_f64(g, p, c.k, AL_CG(0), AL_CG(1), AL_CG(2)); atomicAdd(&status[ST_REFINED], 1); }
             if (!pos) return;
         }
         if (c.has_hi) {
             T y[3];
             for (int a = 0; a < 3; ++a) y[a] = C[a] - c.Bn[a];
             T sg = y[0] * c.m1[0] + y[1] * c.m1[1] + y[2] * c.m1[2];
-            T gs = Tr<T>::gsig(sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]));
+            T gs = Tr<T>::gsig(tsqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]));
             bool pos;
             if (sg > gs) pos = true;
             else if (sg < -gs) pos = false;
-            else { pos = later_closer_f64(g, p, c.k + 1, cg[0], cg[1], cg[2]); atomicAdd(&status[ST_REFINED], 1); }
+            else { pos = later_closer_f64(g, p, c.k + 1, AL_CG(0), AL_CG(1), AL_CG(2)); atomicAdd(&status[ST_REFINED], 1); }
             if (pos) return;
         }
-    } else {
-        // exhaustive: closest segment over the whole line, FP64 near ties
-        T best = (T)INFINITY, second = (T)INFINITY;
-        int jb = 0;
-        for (int j = 0; j < c.nseg; ++j) {
-            const int ja = c.off + j;
-            T xx[3], Dj[3];
-            for (int a = 0; a < 3; ++a) {
-                xx[a] = C[a] - rel(sc.uhi[a * np + ja], sc.ulo[a * np + ja], c.O[a]);
-                Dj[a] = sc.segD[a * np + ja];
-            }
-            T t = (xx[0] * Dj[0] + xx[1] * Dj[1] + xx[2] * Dj[2]) * sc.segIl2[ja];
-            t = t < (T)0 ? (T)0 : (t > (T)1 ? (T)1 : t);
-            T e0 = xx[0] - t * Dj[0], e1 = xx[1] - t * Dj[1], e2 = xx[2] - t * Dj[2];
-            T r2 = e0 * e0 + e1 * e1 + e2 * e2;
-            if (r2 < best) { second = best; best = r2; jb = j; }
-            else if (r2 < second) second = r2;
-        }
-        if (!(second - best > Tr<T>::grr(best))) {
-            jb = argmin_f64(g, p, c.off, c.off + c.nseg - 1, c.n, cg[0], cg[1], cg[2]) - c.off;
-            atomicAdd(&status[ST_REFINED], 1);
-        }
-        if (jb != c.q) return;
     }
     T s = (x[0] * c.D[0] + x[1] * c.D[1] + x[2] * c.D[2]) * c.il2;
     s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
@@ -726,9 +849,10 @@ __device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const int
     bool in;
     if (r2 < c.R2 - c.gr) in = true;
     else if (r2 > c.R2 + c.gr) in = false;
-    else { in = within_f64(g, p, c.eps, c.k, c.n, cg[0], cg[1], cg[2]); atomicAdd(&status[ST_REFINED], 1); }
+    else { in = within_f64(g, p, c.eps, c.k, c.n, AL_CG(0), AL_CG(1), AL_CG(2)); atomicAdd(&status[ST_REFINED], 1); }
+#undef AL_CG
     if (!in) return;
-    T eta = c.eta0 * Tr<T>::ex(-r2 * c.ie2);
+    T eta = c.eta0 * Tr<T>::ex2(-r2 * c.ie2);
     wa.add(((T)1 - s) * eta);
     wb.add(s * eta);
 }
@@ -760,36 +884,62 @@ __device__ __forceinline__ void w_columns(const WSeg<T> &c, const GridC &g, cons
     constexpr int PA = (AX + 1) % 3, PB = (AX + 2) % 3;
     const int na = c.hi[PA] - c.lo[PA] + 1, nbb = c.hi[PB] - c.lo[PB] + 1;
     const int ncol = na * nbb;
+    if (lane >= ncol) return;
+    // this lane's first column; later columns by stepping 32 (float
+    // coordinates advance with exact additions, no conversions in the loop)
+    int ia = lane % na, ib = lane / na;                       // offsets from lo
+    T fa = (T)(c.lo[PA] + ia - c.O[PA]) + (T)0.5, fb = (T)(c.lo[PB] + ib - c.O[PB]) + (T)0.5;
+    const T fna = (T)na;
+    const T clo0 = (T)(c.lo[AX] - c.O[AX]) + (T)0.5, chi0 = (T)(c.hi[AX] - c.O[AX]) + (T)0.5;
+    const bool p0 = c.has_lo && c.m0[AX] != (T)0, p1 = c.has_hi && c.m1[AX] != (T)0;
+    const T i0 = p0 ? (T)1 / c.m0[AX] : (T)0, i1 = p1 ? (T)1 / c.m1[AX] : (T)0;
+    // the segment projected along the march axis: a column farther than 3 eps
+    // from it in the plane has no cell within 3 eps of the segment
+    const T ua = c.D[PA], ub = c.D[PB];
+    const T uu = ua * ua + ub * ub, iuu = uu > (T)0 ? (T)1 / uu : (T)0;
+    const T lim = c.R2 + c.gr;
     for (int col = lane; col < ncol; col += 32) {
-        const int ia = c.lo[PA] + col % na, ib = c.lo[PB] + col / na;
         T C[3];
-        C[PA] = (T)(ia - c.O[PA]) + (T)0.5;
-        C[PB] = (T)(ib - c.O[PB]) + (T)0.5;
+        C[PA] = fa;
+        C[PB] = fb;
+        {
+            const T qa = fa - c.A[PA], qb = fb - c.A[PB];
+            T t = (qa * ua + qb * ub) * iuu;
+            t = t < (T)0 ? (T)0 : (t > (T)1 ? (T)1 : t);
+            const T ea = qa - t * ua, eb = qb - t * ub;
+            if (ea * ea + eb * eb > lim) goto next_column;
+        }
+        {
         // march-axis interval between the two planes (pruning only; the
         // membership test decides)
-        T clo = (T)(c.lo[AX] - c.O[AX]) + (T)0.5, chi = (T)(c.hi[AX] - c.O[AX]) + (T)0.5;
-        if (c.has_lo && c.m0[AX] != (T)0) {
-            T r = c.A[AX] - ((C[PA] - c.A[PA]) * c.m0[PA] + (C[PB] - c.A[PB]) * c.m0[PB]) / c.m0[AX];
-            if (c.m0[AX] > (T)0) clo = fmax(clo, r - (T)0.05); else chi = fmin(chi, r + (T)0.05);
+        T clo = clo0, chi = chi0;
+        if (p0) {
+            T r = c.A[AX] - ((C[PA] - c.A[PA]) * c.m0[PA] + (C[PB] - c.A[PB]) * c.m0[PB]) * i0;
+            if (c.m0[AX] > (T)0) clo = tmax(clo, r - (T)0.05); else chi = tmin(chi, r + (T)0.05);
         }
-        if (c.has_hi && c.m1[AX] != (T)0) {
-            T r = c.Bn[AX] - ((C[PA] - c.Bn[PA]) * c.m1[PA] + (C[PB] - c.Bn[PB]) * c.m1[PB]) / c.m1[AX];
-            if (c.m1[AX] > (T)0) chi = fmin(chi, r + (T)0.05); else clo = fmax(clo, r - (T)0.05);
+        if (p1) {
+            T r = c.Bn[AX] - ((C[PA] - c.Bn[PA]) * c.m1[PA] + (C[PB] - c.Bn[PB]) * c.m1[PB]) * i1;
+            if (c.m1[AX] > (T)0) chi = tmin(chi, r + (T)0.05); else clo = tmax(clo, r - (T)0.05);
         }
-        const int i0 = max(c.lo[AX], iceil(clo - (T)0.5) + c.O[AX]);
-        const int i1 = min(c.hi[AX], ifloor(chi - (T)0.5) + c.O[AX]);
-        for (int ic = i0; ic <= i1; ++ic) {
-            C[AX] = (T)(ic - c.O[AX]) + (T)0.5;
-            int cg[3];
-            cg[AX] = ic; cg[PA] = ia; cg[PB] = ib;
-            w_cell(c, C, cg, g, sc, p, true, status, wa, wb);
+        // cell centres k + 1/2 inside [clo, chi] and inside the box
+        const T z0 = tmax(fceil_f(clo - (T)0.5) + (T)0.5, clo0);
+        const T z1 = tmin(ffloor_f(chi - (T)0.5) + (T)0.5, chi0);
+        for (T z = z0; z <= z1; z += (T)1) {
+            C[AX] = z;
+            w_cell(c, C, g, sc, p, true, status, wa, wb);
         }
+        }
+    next_column:
+        ia += 32;
+        fa += (T)32;
+        while (ia >= na) { ia -= na; fa -= fna; ++ib; fb += (T)1; }
     }
 }
 
 template <typename T>
 __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
                           const int k, const int lane) {
+    if (g.wmode == 0) return;                               // all weights from the brick pass
     const long long np = b.n_points;
     const int l = b.line_of[k];
     const LineG lg = sc.lines[l];
@@ -798,6 +948,11 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
     if (c.n >= 2 && c.q == c.n - 1) return;                 // the tip starts no segment
     c.nseg = (c.n == 1) ? 1 : c.n - 1;
     c.kb = seg_end(k, c.n);
+    if (!lg.regular) {                                      // weights from the brick pass (k_bweights)
+        if (lane == 0) { sc.segWa[k] = 0.0; sc.segWb[k] = 0.0; }
+        return;
+    }
+    c.klo = 0; c.khi = c.nseg - 1;
     c.eps = b.eps[l];
     for (int a = 0; a < 3; ++a) c.O[a] = ifloor(sc.uhi[a * np + k]);
     for (int a = 0; a < 3; ++a) {
@@ -806,11 +961,11 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
         c.D[a] = sc.segD[a * np + k];
     }
     c.il2 = sc.segIl2[k];
-    c.R2 = (T)lg.R2c; c.gr = Tr<T>::grr(c.R2); c.ie2 = (T)lg.inv_eps2c; c.eta0 = (T)lg.eta0;
+    c.R2 = (T)lg.R2c; c.gr = Tr<T>::grr(c.R2); c.ie2 = (T)lg.inv_eps2c_l2; c.eta0 = (T)lg.eta0;
     const int nn[3] = {g.nx, g.ny, g.nz};
     bool empty = false;
     for (int a = 0; a < 3; ++a) {
-        T l0 = fmin(c.A[a], c.Bn[a]) - (T)lg.Rc - (T)0.01, h0 = fmax(c.A[a], c.Bn[a]) + (T)lg.Rc + (T)0.01;
+        T l0 = tmin(c.A[a], c.Bn[a]) - (T)lg.Rc - (T)0.01, h0 = tmax(c.A[a], c.Bn[a]) + (T)lg.Rc + (T)0.01;
         c.lo[a] = max(0, iceil(l0 - (T)0.5) + c.O[a]);
         c.hi[a] = min(nn[a] - 1, ifloor(h0 - (T)0.5) + c.O[a]);
         if (c.lo[a] > c.hi[a]) empty = true;
@@ -825,20 +980,11 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
     }
     if (!empty && regular) {
         int ax = 0;
-        if (fabs(c.D[1]) > fabs(c.D[ax])) ax = 1;
-        if (fabs(c.D[2]) > fabs(c.D[ax])) ax = 2;
+        if (tabs(c.D[1]) > tabs(c.D[ax])) ax = 1;
+        if (tabs(c.D[2]) > tabs(c.D[ax])) ax = 2;
         if (ax == 0) w_columns<T, 0>(c, g, sc, p, status, lane, wa, wb);
         else if (ax == 1) w_columns<T, 1>(c, g, sc, p, status, lane, wa, wb);
         else w_columns<T, 2>(c, g, sc, p, status, lane, wa, wb);
-    } else if (!empty) {
-        const int n0 = c.hi[0] - c.lo[0] + 1, n1 = c.hi[1] - c.lo[1] + 1, n2 = c.hi[2] - c.lo[2] + 1;
-        const long long ncell = (long long)n0 * n1 * n2;
-        for (long long t = lane; t < ncell; t += 32) {
-            const int cg[3] = {c.lo[0] + (int)(t % n0), c.lo[1] + (int)((t / n0) % n1), c.lo[2] + (int)(t / ((long long)n0 * n1))};
-            T C[3];
-            for (int a = 0; a < 3; ++a) C[a] = (T)(cg[a] - c.O[a]) + (T)0.5;
-            w_cell(c, C, cg, g, sc, p, false, status, wa, wb);
-        }
     }
     const double ta = warp_total(wa), tb = warp_total(wb);
     if (lane == 0) {
@@ -851,13 +997,19 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
 // k_normalise: w_k and f^_k = F_k / w_k
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void d_normalise(const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status, const int k) {
+__device__ void d_normalise(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
+                            const int k) {
     const long long np = b.n_points;
     const int l = b.line_of[k];
     const int off = b.line_off[l], n = b.line_off[l + 1] - off, q = k - off;
     double w = 0.0;
-    if (n == 1) w = sc.segWa[k] + sc.segWb[k];
-    else {
+    const LineG &lg = sc.lines[l];
+    if (g.wmode == 0 || !lg.regular) {
+        // brick pass: fixed-point sum of omega eta / eta0; w = sum eta0 V 2^-wshift
+        w = ldexp((double)sc.wfix[k], -lg.wshift) * (lg.eta0 * g.V);
+    } else if (n == 1) {
+        w = sc.segWa[k] + sc.segWb[k];
+    } else {
         if (q >= 1) w += sc.segWb[k - 1];
         if (q <= n - 2) w += sc.segWa[k];
     }
@@ -866,10 +1018,13 @@ __device__ void d_normalise(const BeamsC &b, const Scratch<T> &sc, const StepPtr
         const T wt = (T)w;                         // FP64 sum, divided in the field precision
         for (int a = 0; a < 3; ++a) sc.fhat[a * np + k] = p.F[a][k] / wt;
     } else {
+        // w_k = 0: the spread deposits F_k in the cell containing the node
         for (int a = 0; a < 3; ++a) sc.fhat[a * np + k] = (T)0;
-        int slot = atomicAdd(sc.zeroCount, 1);
-        sc.zeroList[slot] = k;
         atomicAdd(&status[ST_ZERO_WEIGHT], 1);
+        const int nn[3] = {g.nx, g.ny, g.nz};
+        bool ins = true;
+        for (int a = 0; a < 3; ++a) ins = ins && inside_axis(sc.uhi[a * np + k], sc.ulo[a * np + k], nn[a]);
+        if (!ins) atomicAdd(&status[ST_DEPOSIT_LOST], 1);
     }
 }
 
@@ -877,26 +1032,44 @@ __device__ void d_normalise(const BeamsC &b, const Scratch<T> &sc, const StepPtr
 // k_spread: Eq. almMomentumSource as a cell-centric gather per brick
 // ---------------------------------------------------------------------------
 template <typename T> struct SpreadCap;
-template <> struct SpreadCap<float> { static constexpr int NODES = 768, LIST = 512, ENT = 64; };
-template <> struct SpreadCap<double> { static constexpr int NODES = 384, LIST = 512, ENT = 64; };
+template <> struct SpreadCap<float> { static constexpr int NODES = 640, LIST = 512, ENT = 32; };
+template <> struct SpreadCap<double> { static constexpr int NODES = 320, LIST = 512, ENT = 32; };
 
 template <typename T>
 struct SpreadSmem {
     static constexpr int NN = SpreadCap<T>::NODES, LIST = SpreadCap<T>::LIST, ENT = SpreadCap<T>::ENT;
     T P[3][NN];                  // node positions relative to the brick origin
     T M[3][NN];                  // node bisectors
-    T Fh[3][NN];                 // f^ at the nodes
     T D[3][NN];                  // segment vectors
     T Il2[NN];
+    union {
+        struct {
+            T Fh[3][NN];         // spread: f^ at the nodes
+            int sk[NN];          // spread: global node index of each staged node
+        } s;
+        unsigned long long wq[NN];   // weights pass: fixed-point w of the staged nodes
+    } u;
+    unsigned char zf[NN];        // spread: the node has w_k = 0 (deposit)
     int list[LIST];              // candidate lines of this brick (line order)
-    int nlist, nbatch;
+    int nlist, nbatch, nstaged;
     int e_line[ENT], e_jlo[ENT], e_jhi[ENT], e_base[ENT], e_reg[ENT], e_n[ENT], e_first[ENT];
     float e_lo[ENT][3], e_hi[ENT][3];
     T e_R2[ENT], e_gr[ENT], e_ie2[ENT], e_eta0[ENT];
+    float e_cz[ENT];             // min |D_z| / |D| over the candidates (0: no crossing test)
+    float e_rad[ENT];            // R + curvature slack, cells
+    float e_rho2[ENT];           // regular == 2: squared start radius
+    // per line and layer: where the line crosses the layer's height, the
+    // horizontal radius beyond which no cell of the layer is within 3 eps,
+    // the crossing segment, and the fractional segment index at the crossing
+    // with its gradient in the layer (the walk starts near the foot)
+    float l_xc[ENT][BZ], l_yc[ENT][BZ], l_rh2[ENT][BZ];
+    float l_ac[ENT][BZ], l_gx[ENT][BZ], l_gy[ENT][BZ];
+    int l_jc[ENT][BZ];
     double red[3][SPREAD_THREADS / 32];
+    int redi[SPREAD_THREADS / 32];
 };
 
-// rare paths of the gather, kept out of line so the unrolled cell loop stays small
+// rare paths of the gather, kept out of line so the cell loop stays small
 
 // FP64 re-decision of "segment k closer than k-1" (walk inside the band)
 template <typename T>
@@ -911,14 +1084,22 @@ __device__ __noinline__ bool nl_within(const GridC &g, const StepPtrs<T> &p, dou
     atomicAdd(&status[ST_REFINED], 1);
     return within_f64(g, p, eps, k, n, ci, cj, ck);
 }
-// closest segment over [first + jlo, first + jhi] by exhaustive search
-// (lines without a walk certificate, or longer than the shared-memory stage);
-// returns the line-local segment index
+template <typename T>
+__device__ __noinline__ int nl_argmin(const GridC &g, const StepPtrs<T> &p, int k0, int k1, int n, int ci, int cj,
+                                      int ck, int *status) {
+    atomicAdd(&status[ST_REFINED], 1);
+    return argmin_f64(g, p, k0, k1, n, ci, cj, ck);
+}
+// closest segment over [first + jlo, first + jhi] by exhaustive search from
+// global memory (lines longer than the shared-memory stage); returns the
+// line-local segment index
 template <typename T>
 __device__ __noinline__ int nl_exhaustive(const GridC &g, const Scratch<T> &sc, const StepPtrs<T> &p, int first,
-                                          int n, int jlo, int jhi, const T C[3], const int B[3], int ci, int cj,
-                                          int ck, int *status) {
+                                          int n, int jlo, int jhi, T c0, T c1, T c2, int B0, int B1, int B2,
+                                          int ci, int cj, int ck, int *status) {
     const long long np = p.np;
+    const T C[3] = {c0, c1, c2};
+    const int B[3] = {B0, B1, B2};
     T best = (T)INFINITY, second = (T)INFINITY;
     int js = jlo;
     for (int jj = jlo; jj <= jhi; ++jj) {
@@ -935,10 +1116,28 @@ __device__ __noinline__ int nl_exhaustive(const GridC &g, const Scratch<T> &sc, 
         if (d2 < best) { second = best; best = d2; js = jj; }
         else if (d2 < second) second = d2;
     }
-    if (!(second - best > Tr<T>::grr(best))) {
-        js = argmin_f64(g, p, first + jlo, first + jhi, n, ci, cj, ck) - first;
-        atomicAdd(&status[ST_REFINED], 1);
+    if (!(second - best > Tr<T>::grr(best))) js = nl_argmin(g, p, first + jlo, first + jhi, n, ci, cj, ck, status) - first;
+    return js;
+}
+// the same over the staged candidate segments
+template <typename T>
+__device__ __noinline__ int nl_exhaustive_staged(const SpreadSmem<T> &sm, const GridC &g, const StepPtrs<T> &p,
+                                                 int base, int first, int n, int jlo, int jhi, T c0, T c1, T c2,
+                                                 int ci, int cj, int ck, int *status) {
+    T best = (T)INFINITY, second = (T)INFINITY;
+    int js = jlo;
+    for (int jj = jlo; jj <= jhi; ++jj) {
+        const int ss = base + (jj - jlo);
+        const T x0 = c0 - sm.P[0][ss], x1 = c1 - sm.P[1][ss], x2 = c2 - sm.P[2][ss];
+        const T d0 = sm.D[0][ss], d1 = sm.D[1][ss], d2 = sm.D[2][ss];
+        T t = (x0 * d0 + x1 * d1 + x2 * d2) * sm.Il2[ss];
+        t = t < (T)0 ? (T)0 : (t > (T)1 ? (T)1 : t);
+        const T e0 = x0 - t * d0, e1 = x1 - t * d1, e2 = x2 - t * d2;
+        const T dd = e0 * e0 + e1 * e1 + e2 * e2;
+        if (dd < best) { second = best; best = dd; js = jj; }
+        else if (dd < second) second = dd;
     }
+    if (!(second - best > Tr<T>::grr(best))) js = nl_argmin(g, p, first + jlo, first + jhi, n, ci, cj, ck, status) - first;
     return js;
 }
 
@@ -947,43 +1146,90 @@ __device__ __forceinline__ bool sig_pos(const SpreadSmem<T> &sm, int s, const T 
                                         const StepPtrs<T> &p, int kglob, int ci, int cj, int ck, int *status) {
     const T x0 = C[0] - sm.P[0][s], x1 = C[1] - sm.P[1][s], x2 = C[2] - sm.P[2][s];
     const T sg = x0 * sm.M[0][s] + x1 * sm.M[1][s] + x2 * sm.M[2][s];
-    const T gs = Tr<T>::gsig(sqrt(x0 * x0 + x1 * x1 + x2 * x2));
+    const T gs = Tr<T>::gsig(tsqrt(x0 * x0 + x1 * x1 + x2 * x2));
     if (sg > gs) return true;
     if (sg < -gs) return false;
     return nl_later_closer(g, p, kglob, ci, cj, ck, status);
 }
-
 template <typename T>
-__device__ void d_spread(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
-                         const long long br, SpreadSmem<T> &sm) {
+__device__ __forceinline__ T node_d2(const SpreadSmem<T> &sm, int s, const T C[3]) {
+    const T x0 = C[0] - sm.P[0][s], x1 = C[1] - sm.P[1][s], x2 = C[2] - sm.P[2][s];
+    return x0 * x0 + x1 * x1 + x2 * x2;
+}
+// clamped foot parameter and squared distance of C to staged segment ss
+template <typename T>
+__device__ __forceinline__ void seg_foot(const SpreadSmem<T> &sm, int ss, const T C[3], T &s, T &r2) {
+    const T x0 = C[0] - sm.P[0][ss], x1 = C[1] - sm.P[1][ss], x2 = C[2] - sm.P[2][ss];
+    const T d0 = sm.D[0][ss], d1 = sm.D[1][ss], d2 = sm.D[2][ss];
+    s = (x0 * d0 + x1 * d1 + x2 * d2) * sm.Il2[ss];
+    s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
+    const T e0 = x0 - s * d0, e1 = x1 - s * d1, e2 = x2 - s * d2;
+    r2 = e0 * e0 + e1 * e1 + e2 * e2;
+}
+
+// One brick of cells and the lines near it.  WP = false: the momentum source
+// (Eq. almMomentumSource) of every cell of the brick, written once per cell
+// by the thread that owns its column (no atomics), with the deposits of the
+// zero-weight nodes inside the brick.  WP = true: the nodal weights w_k
+// (Sec. 3.2.4), each (cell, line) pair once, added as fixed-point integers.
+template <typename T, bool WP>
+__device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
+                        const int br, SpreadSmem<T> &sm) {
+    using SM = SpreadSmem<T>;
     const long long np = b.n_points;
-    const int bxi = (int)(br % g.nbx), byi = (int)((br / g.nbx) % g.nby), bzi = (int)(br / ((long long)g.nbx * g.nby));
+    const int nbxy = g.nbx * g.nby;
+    const int bzi = br / nbxy, rem = br - bzi * nbxy;
+    const int byi = rem / g.nbx, bxi = rem - byi * g.nbx;
     const int B0 = bxi * BX, B1 = byi * BY, B2 = bzi * BZ;
-    const int Bv[3] = {B0, B1, B2};
     const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gx = B0 + tx, gy = B1 + ty;
     const bool col_in = gx < g.nx && gy < g.ny;
     const float cx = tx + 0.5f, cy = ty + 0.5f;
-
-    T acc[BZ][3];
-#pragma unroll
-    for (int z = 0; z < BZ; ++z) acc[z][0] = acc[z][1] = acc[z][2] = (T)0;
+    const int nzb = min(BZ, g.nz - B2);              // layers of this brick inside the grid
+    const long long layer = (long long)g.nx * g.ny;
+    const long long col = gx + (long long)g.nx * gy + layer * B2;   // cell (gx, gy, B2)
     int nsupp = 0;                                   // (cell, line) pairs within 3 eps
+    int nbat = 0;                                    // batches done
+    T cs0 = (T)0, cs1 = (T)0, cs2 = (T)0;            // final S of this thread's cells
+    double dep0 = 0.0, dep1 = 0.0, dep2 = 0.0;       // warp 0: deposits of the last batch
 
     const int W = b.mask_words;
-    uint32_t *mrow = sc.mask + br * (long long)W;
+    uint32_t *mrow = sc.mask + (long long)br * W;
     const float blo[3] = {(float)B0, (float)B1, (float)B2};
     const float bhi[3] = {(float)(B0 + BX), (float)(B1 + BY), (float)(B2 + BZ)};
 
-    constexpr int CH = SpreadSmem<T>::LIST / 32;               // mask words per chunk
+    constexpr int CH = SM::LIST / 32;                // mask words per chunk
+    int nleft = 0;                                   // spread: candidate lines not yet processed
+    if (!WP) {
+        if (warp == 0) {
+            int c = 0;
+            for (int w = lane; w < W; w += 32) c += __popc(mrow[w]);
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane == 0) sm.nlist = c;
+        }
+        __syncthreads();
+        nleft = sm.nlist;
+    }
     for (int w0 = 0; w0 < W; w0 += CH) {
         // ---- candidate lines from CH mask words, in line order -------------
         __syncthreads();
         if (warp == 0) {
             const bool mine = lane < CH && w0 + lane < W;
             uint32_t m = mine ? mrow[w0 + lane] : 0u;
-            if (mine && m) mrow[w0 + lane] = 0u;                 // clear for the next step
+            if (WP) {
+                if (g.wmode != 0) {                      // segment pass covers certified lines
+                    uint32_t keep = 0u, t = m;
+                    while (t) {
+                        const int bit = __ffs(t) - 1;
+                        t &= t - 1;
+                        if (!sc.lines[((w0 + lane) << 5) + bit].regular) keep |= 1u << bit;
+                    }
+                    m = keep;
+                }
+            } else if (mine && m) {
+                mrow[w0 + lane] = 0u;                    // clear for the next step
+            }
             int cnt = __popc(m), pre = cnt;
             for (int o = 1; o < 32; o <<= 1) {
                 int v = __shfl_up_sync(0xffffffffu, pre, o);
@@ -996,20 +1242,21 @@ __device__ void d_spread(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
                 m &= m - 1;
                 sm.list[pos++] = ((w0 + lane) << 5) + bit;
             }
-            if (lane == 0) sm.nlist = total;                      // <= 32 * CH = LIST
+            if (lane == 0) sm.nlist = total;             // <= 32 * CH = LIST
         }
         __syncthreads();
         const int nlist = sm.nlist;
         int li = 0;
         while (li < nlist) {
             // ---- batch: candidate segment ranges, one warp per line --------
-            const int nb = min(nlist - li, SpreadSmem<T>::ENT);
+            const int nb = min(nlist - li, SM::ENT);
             for (int e = warp; e < nb; e += SPREAD_THREADS / 32) {
                 const int l = sm.list[li + e];
                 const LineG lg = sc.lines[l];
                 const int nseg = lg.n == 1 ? 1 : lg.n - 1;
                 int jlo = 0x7fffffff, jhi = -1;
                 float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
+                float czp = 1.0f, czn = 1.0f;          // min D_z/|D| over up- and down-going candidates
                 for (int j = lane; j < nseg; j += 32) {
                     const int ka = lg.first + j;
                     float sl[3], sh[3];
@@ -1030,18 +1277,46 @@ __device__ void d_spread(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
                         hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
                     }
                 }
+                // climb rate of every segment of the candidate range [jlo, jhi]
+                for (int j = jlo + lane; j <= jhi; j += 32) {
+                    const int ka = lg.first + j;
+                    const float dx = (float)sc.segD[ka], dy = (float)sc.segD[np + ka], dz = (float)sc.segD[2 * np + ka];
+                    const float ln = sqrtf(dx * dx + dy * dy + dz * dz);
+                    const float cz = ln > 0.0f ? dz / ln : 0.0f;
+                    czp = fminf(czp, cz);
+                    czn = fminf(czn, -cz);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    czp = fminf(czp, __shfl_xor_sync(0xffffffffu, czp, o));
+                    czn = fminf(czn, __shfl_xor_sync(0xffffffffu, czn, o));
+                }
+                // candidates all climbing (or all descending) by at least 0.3 of their length:
+                // cells within 3 eps of the line lie near where it crosses each layer
+                const float czm = fmaxf(czp, czn);
+                const float cz_ok = (lg.n >= 2 && czm > 0.3f) ? czm : 0.0f;
                 if (lane == 0) {
                     sm.e_line[e] = l;
                     sm.e_jlo[e] = jlo;
                     sm.e_jhi[e] = jhi;
-                    sm.e_reg[e] = lg.regular;
+                    sm.e_reg[e] = (lg.regular == 2 && cz_ok <= 0.0f) ? 0 : lg.regular;
                     sm.e_n[e] = lg.n;
                     sm.e_first[e] = lg.first;
                     sm.e_R2[e] = (T)lg.R2c;
                     sm.e_gr[e] = Tr<T>::grr((T)lg.R2c);
-                    sm.e_ie2[e] = (T)lg.inv_eps2c;
-                    sm.e_eta0[e] = (T)lg.eta0;
+                    sm.e_ie2[e] = (T)lg.inv_eps2c_l2;
+                    sm.e_eta0[e] = WP ? (T)lg.wshift : (T)lg.eta0;
+                    sm.e_rho2[e] = lg.rho2;
                     for (int a = 0; a < 3; ++a) { sm.e_lo[e][a] = lo[a] - blo[a]; sm.e_hi[e][a] = hi[a] - blo[a]; }
+                    sm.e_cz[e] = cz_ok;
+                    if (cz_ok > 0.0f) {
+                        // a cell of a layer within 3 eps of the line is within 3 eps + dev of the
+                        // axis of the segment crossing that layer: the foot lies within an arc
+                        // lam = 3 eps / cz + L_max of that segment, over which the polyline
+                        // departs from the axis by at most lam min(1, (lam / L_min + 1) theta_max)
+                        const float lam = lg.Rc / cz_ok + lg.Lmax;
+                        const float turn = (lg.n >= 3 && lg.Lmin > 0.0f) ? (lam / lg.Lmin + 1.0f) * lg.thmax : 0.0f;
+                        sm.e_rad[e] = lg.Rc + lam * fminf(1.0f, turn) + 0.02f;
+                    }
                 }
             }
             __syncthreads();
@@ -1050,15 +1325,18 @@ __device__ void d_spread(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
                 int base = 0, e = 0;
                 for (; e < nb; ++e) {
                     int cnt = sm.e_jhi[e] >= sm.e_jlo[e] ? sm.e_jhi[e] - sm.e_jlo[e] + 2 : 0;
-                    if (base + cnt > SpreadSmem<T>::NN) break;
+                    if (base + cnt > SM::NN) break;
                     sm.e_base[e] = base;
                     base += cnt;
                 }
                 if (e == 0) { e = 1; sm.e_base[0] = -1; }  // one oversized line: global-memory path
                 sm.nbatch = e;
+                sm.nstaged = base;
             }
             __syncthreads();
             const int ne = sm.nbatch;
+            nleft -= ne;
+            const bool last = nleft == 0;                // S of this brick is final after this batch
             // ---- stage nodes of the batch ----------------------------------
             for (int e = 0; e < ne; ++e) {
                 const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e], base = sm.e_base[e];
@@ -1070,68 +1348,125 @@ __device__ void d_spread(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
                     const int kn = (n == 1) ? first : k;    // single-node line: copy the node
                     const int s = base + t;
                     for (int a = 0; a < 3; ++a) {
-                        sm.P[a][s] = rel(sc.uhi[a * np + kn], sc.ulo[a * np + kn], Bv[a]);
+                        sm.P[a][s] = rel(sc.uhi[a * np + kn], sc.ulo[a * np + kn], (a == 0) ? B0 : (a == 1 ? B1 : B2));
                         sm.M[a][s] = sc.nodeM[a * np + kn];
-                        sm.Fh[a][s] = sc.fhat[a * np + kn];
                         sm.D[a][s] = sc.segD[a * np + kn];
                     }
                     sm.Il2[s] = sc.segIl2[kn];
+                    if (WP) {
+                        sm.u.wq[s] = 0ull;
+                    } else {
+                        for (int a = 0; a < 3; ++a) sm.u.s.Fh[a][s] = sc.fhat[a * np + kn];
+                        sm.u.s.sk[s] = kn;
+                        sm.zf[s] = (n != 1 || t == 0) && sc.w[kn] == 0.0;
+                    }
                 }
+            }
+            __syncthreads();
+            // ---- where each line crosses each layer (one warp per line) --------
+            for (int e = warp; e < ne; e += SPREAD_THREADS / 32) {
+                const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e], base = sm.e_base[e];
+                if (lane >= BZ) continue;
+                const float cz = sm.e_cz[e];
+                if (jhi < jlo || base < 0 || cz <= 0.0f) {
+                    sm.l_rh2[e][lane] = 3.0e38f;               // no crossing test for this line
+                    sm.l_xc[e][lane] = sm.l_yc[e][lane] = 0.0f;
+                    sm.l_ac[e][lane] = (float)max(jlo, 0);
+                    sm.l_gx[e][lane] = sm.l_gy[e][lane] = 0.0f;
+                    sm.l_jc[e][lane] = max(jlo, 0);
+                    continue;
+                }
+                const float zc = lane + 0.5f;
+                // the candidate segment containing the height zc, else the end one nearest to it
+                int jc = -1;
+                for (int j = jlo; j <= jhi; ++j) {
+                    const int ss = base + (j - jlo);
+                    const float za = (float)sm.P[2][ss], zb = za + (float)sm.D[2][ss];
+                    if (fminf(za, zb) <= zc && zc <= fmaxf(za, zb)) { jc = j; break; }
+                }
+                if (jc < 0) {
+                    const float za = (float)sm.P[2][base], zb = (float)sm.P[2][base + (jhi - jlo + 1)];
+                    jc = (fabsf(zc - za) < fabsf(zc - zb)) ? jlo : jhi;
+                }
+                const int ss = base + (jc - jlo);
+                const float d0 = (float)sm.D[0][ss], d1 = (float)sm.D[1][ss], dz = (float)sm.D[2][ss];
+                const float t = (zc - (float)sm.P[2][ss]) / dz;      // |dz| >= 0.3 |D| > 0
+                sm.l_xc[e][lane] = (float)sm.P[0][ss] + t * d0;
+                sm.l_yc[e][lane] = (float)sm.P[1][ss] + t * d1;
+                const float rh = sm.e_rad[e] / cz + 0.02f;
+                sm.l_rh2[e][lane] = rh * rh;
+                sm.l_jc[e][lane] = jc;
+                // foot of a cell (dx, dy) away from the crossing, in segment units
+                const float il2 = (float)sm.Il2[ss];
+                sm.l_ac[e][lane] = (float)jc + t;
+                sm.l_gx[e][lane] = d0 * il2;
+                sm.l_gy[e][lane] = d1 * il2;
             }
             __syncthreads();
             // ---- gather: every thread walks only the lines near its column ----
             if (col_in) {
-                uint64_t cm = 0;
+                uint32_t cm = 0;
                 for (int e = 0; e < ne; ++e)
                     if (sm.e_jhi[e] >= sm.e_jlo[e] && cx >= sm.e_lo[e][0] && cx <= sm.e_hi[e][0] &&
                         cy >= sm.e_lo[e][1] && cy <= sm.e_hi[e][1])
-                        cm |= 1ull << e;
-                while (cm) {                                     // increasing e = line order
-                    const int e = __ffsll((long long)cm) - 1;
-                    cm &= cm - 1;
-                    const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e], base = sm.e_base[e];
-                    const int first = sm.e_first[e], n = sm.e_n[e], reg = sm.e_reg[e];
-                    const T R2 = sm.e_R2[e], gr = sm.e_gr[e], ie2 = sm.e_ie2[e], eta0 = sm.e_eta0[e];
-                    const float zlo = sm.e_lo[e][2], zhi = sm.e_hi[e][2];
-                    int j = jlo;                                  // walk state (line-local segment)
-#pragma unroll
-                    for (int z = 0; z < BZ; ++z) {
-                        const float cz = z + 0.5f;
-                        if (cz < zlo || cz > zhi) continue;
-                        const int gz = B2 + z;
-                        if (gz >= g.nz) continue;
+                        cm |= 1u << e;
+                float cz = 0.5f;
+                for (int z = 0; z < nzb; ++z, cz += 1.0f) {
+                    const int gz = B2 + z;
+                    T a0 = (T)0, a1 = (T)0, a2 = (T)0;
+                    uint32_t m = cm;
+                    while (m) {                                  // increasing e = line order
+                        const int e = __ffs(m) - 1;
+                        m &= m - 1;
+                        if (cz < sm.e_lo[e][2] || cz > sm.e_hi[e][2]) continue;
+                        const float dx = cx - sm.l_xc[e][z], dy = cy - sm.l_yc[e][z];
+                        if (dx * dx + dy * dy > sm.l_rh2[e][z]) continue;      // farther than 3 eps
+                        const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e], base = sm.e_base[e];
+                        const int first = sm.e_first[e], n = sm.e_n[e];
                         const T C[3] = {(T)cx, (T)cy, (T)cz};
+                        const T R2 = sm.e_R2[e], gr = sm.e_gr[e];
                         int js;
-                        if (reg && base >= 0) {
-                            while (j > jlo && !sig_pos(sm, base + (j - jlo), C, g, p, first + j, gx, gy, gz, status)) --j;
-                            while (j < jhi && sig_pos(sm, base + (j + 1 - jlo), C, g, p, first + j + 1, gx, gy, gz, status)) ++j;
-                            js = j;
-                        } else {
-                            js = nl_exhaustive(g, sc, p, first, n, jlo, jhi, C, Bv, gx, gy, gz, status);
-                        }
-                        T s, r2, fa[3], fb[3];
-                        if (base >= 0) {
-                            const int ss = base + (js - jlo), sb = (n == 1) ? ss : ss + 1;
-                            const T x0 = C[0] - sm.P[0][ss], x1 = C[1] - sm.P[1][ss], x2 = C[2] - sm.P[2][ss];
-                            const T d0 = sm.D[0][ss], d1 = sm.D[1][ss], d2 = sm.D[2][ss];
-                            s = (x0 * d0 + x1 * d1 + x2 * d2) * sm.Il2[ss];
-                            s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
-                            const T e0 = x0 - s * d0, e1 = x1 - s * d1, e2 = x2 - s * d2;
-                            r2 = e0 * e0 + e1 * e1 + e2 * e2;
-                            for (int a = 0; a < 3; ++a) { fa[a] = sm.Fh[a][ss]; fb[a] = sm.Fh[a][sb]; }
-                        } else {
-                            const int ka = first + js, kb = seg_end(ka, n);
+                        T s, r2;
+                        if (base < 0) {
+                            js = nl_exhaustive(g, sc, p, first, n, jlo, jhi, C[0], C[1], C[2], B0, B1, B2, gx, gy,
+                                               gz, status);
+                            const int ka = first + js;
                             T x[3], Dj[3];
+                            const int Bv[3] = {B0, B1, B2};
                             for (int a = 0; a < 3; ++a) {
                                 x[a] = C[a] - rel(sc.uhi[a * np + ka], sc.ulo[a * np + ka], Bv[a]);
                                 Dj[a] = sc.segD[a * np + ka];
-                                fa[a] = sc.fhat[a * np + ka];
-                                fb[a] = sc.fhat[a * np + kb];
                             }
                             s = (x[0] * Dj[0] + x[1] * Dj[1] + x[2] * Dj[2]) * sc.segIl2[ka];
                             s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
                             const T e0 = x[0] - s * Dj[0], e1 = x[1] - s * Dj[1], e2 = x[2] - s * Dj[2];
                             r2 = e0 * e0 + e1 * e1 + e2 * e2;
+                        } else {
+                            const int reg = sm.e_reg[e];
+                            bool exh = reg == 0, start_ok = true;
+                            js = jlo;
+                            if (!exh) {
+                                // start near the foot: the crossing plus the in-layer offset along the segment
+                                int j = (int)floorf(sm.l_ac[e][z] + dx * sm.l_gx[e][z] + dy * sm.l_gy[e][z]);
+                                j = min(max(j, jlo), jhi);
+                                if (reg == 2) {
+                                    const float rho2 = sm.e_rho2[e];
+                                    if (node_d2(sm, base + (j - jlo), C) > (T)rho2) {
+                                        j = sm.l_jc[e][z];
+                                        start_ok = node_d2(sm, base + (j - jlo), C) <= (T)rho2;
+                                    }
+                                }
+                                while (j > jlo && !sig_pos(sm, base + (j - jlo), C, g, p, first + j, gx, gy, gz, status)) --j;
+                                while (j < jhi && sig_pos(sm, base + (j + 1 - jlo), C, g, p, first + j + 1, gx, gy, gz, status)) ++j;
+                                js = j;
+                            }
+                            seg_foot(sm, base + (js - jlo), C, s, r2);
+                            // a walk from outside the certified radius is exact only when it ends within R
+                            if (exh || (!start_ok && !(r2 < R2 - gr))) {
+                                js = nl_exhaustive_staged(sm, g, p, base, first, n, jlo, jhi, C[0], C[1], C[2], gx,
+                                                          gy, gz, status);
+                                seg_foot(sm, base + (js - jlo), C, s, r2);
+                            }
                         }
                         bool in;
                         if (r2 < R2 - gr) in = true;
@@ -1139,83 +1474,137 @@ __device__ void d_spread(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
                         else in = nl_within(g, p, b.eps[sm.e_line[e]], first + js, n, gx, gy, gz, status);
                         if (!in) continue;
                         ++nsupp;
-                        const T eta = eta0 * Tr<T>::ex(-r2 * ie2);
+                        const T q = Tr<T>::ex2(-r2 * sm.e_ie2[e]);
+                        if (WP) {
+                            // omega eta / eta0 into the two nodes of the closest segment
+                            const int sh = (int)sm.e_eta0[e];
+                            if (base >= 0) {
+                                const int ss = base + (js - jlo), sb = (n == 1) ? ss : ss + 1;
+                                atomicAdd(&sm.u.wq[ss], to_fixed(q * ((T)1 - s), sh));
+                                atomicAdd(&sm.u.wq[sb], to_fixed(q * s, sh));
+                            } else {
+                                const int ka = first + js;
+                                atomicAdd(&sc.wfix[ka], to_fixed(q * ((T)1 - s), sh));
+                                atomicAdd(&sc.wfix[seg_end(ka, n)], to_fixed(q * s, sh));
+                            }
+                            continue;
+                        }
+                        T fa0, fa1, fa2, fb0, fb1, fb2;
+                        if (base >= 0) {
+                            const int ss = base + (js - jlo), sb = (n == 1) ? ss : ss + 1;
+                            fa0 = sm.u.s.Fh[0][ss]; fa1 = sm.u.s.Fh[1][ss]; fa2 = sm.u.s.Fh[2][ss];
+                            fb0 = sm.u.s.Fh[0][sb]; fb1 = sm.u.s.Fh[1][sb]; fb2 = sm.u.s.Fh[2][sb];
+                        } else {
+                            const int ka = first + js, kb = seg_end(ka, n);
+                            fa0 = sc.fhat[ka]; fa1 = sc.fhat[np + ka]; fa2 = sc.fhat[2 * np + ka];
+                            fb0 = sc.fhat[kb]; fb1 = sc.fhat[np + kb]; fb2 = sc.fhat[2 * np + kb];
+                        }
+                        const T eta = sm.e_eta0[e] * q;
                         const T wa = eta * ((T)1 - s), wb = eta * s;
-                        acc[z][0] -= wa * fa[0] + wb * fb[0];
-                        acc[z][1] -= wa * fa[1] + wb * fb[1];
-                        acc[z][2] -= wa * fa[2] + wb * fb[2];
+                        a0 -= wa * fa0 + wb * fb0;
+                        a1 -= wa * fa1 + wb * fb1;
+                        a2 -= wa * fa2 + wb * fb2;
+                    }
+                    if (!WP) {
+                        // the thread owns the cell: the first batch writes it, later ones add to it
+                        const long long idx = col + layer * z;
+                        if (nbat > 0 && (cm || last)) {
+                            a0 += p.S[0][idx]; a1 += p.S[1][idx]; a2 += p.S[2][idx];
+                        }
+                        if (nbat == 0 || cm) { p.S[0][idx] = a0; p.S[1][idx] = a1; p.S[2][idx] = a2; }
+                        if (last) { cs0 += a0; cs1 += a1; cs2 += a2; }
+                    }
+                }
+            }
+            if (WP) {
+                __syncthreads();
+                for (int e = 0; e < ne; ++e) {
+                    const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e], base = sm.e_base[e];
+                    if (jhi < jlo || base < 0) continue;
+                    const int first = sm.e_first[e], n = sm.e_n[e];
+                    const int cnt = (n == 1) ? 1 : jhi - jlo + 2;
+                    for (int t = threadIdx.x; t < cnt; t += SPREAD_THREADS) {
+                        unsigned long long v = sm.u.wq[base + t];
+                        if (n == 1) v += sm.u.wq[base + 1];
+                        if (v) atomicAdd(&sc.wfix[first + jlo + t], v);
+                    }
+                }
+            } else {
+                // ---- deposits of the zero-weight nodes inside this brick, in line and node order
+                __syncthreads();
+                if (warp == 0) {
+                    const int tot = sm.nstaged;
+                    for (int s0 = 0; s0 < tot; s0 += 32) {
+                        const int s = s0 + lane;
+                        int idx3[3];
+                        bool f = s < tot && sm.zf[s];
+                        int k = 0;
+                        if (f) {
+                            k = sm.u.s.sk[s];
+                            const int Bv[3] = {B0, B1, B2}, bs[3] = {BX, BY, BZ}, nn[3] = {g.nx, g.ny, g.nz};
+                            for (int a = 0; a < 3; ++a) {
+                                const T uh = sc.uhi[a * np + k];
+                                const float ul = sc.ulo[a * np + k];
+                                const int c = ffloor(uh, ul);
+                                f = f && inside_axis(uh, ul, nn[a]) && c >= Bv[a] && c < Bv[a] + bs[a];
+                                idx3[a] = c;
+                            }
+                        }
+                        uint32_t bal = __ballot_sync(0xffffffffu, f);
+                        while (bal) {
+                            const int src = __ffs(bal) - 1;
+                            bal &= bal - 1;
+                            if (lane == src) {
+                                const long long idx = idx3[0] + (long long)g.nx * (idx3[1] + (long long)g.ny * idx3[2]);
+                                double d[3];
+                                for (int a = 0; a < 3; ++a) {
+                                    const T old = p.S[a][idx];
+                                    const T nw = old - p.F[a][k] / (T)g.V;
+                                    p.S[a][idx] = nw;
+                                    d[a] = (double)nw - (double)old;
+                                }
+                                // the change enters the brick sum through this lane's counters
+                                if (last) { dep0 += d[0]; dep1 += d[1]; dep2 += d[2]; }
+                            }
+                            __syncwarp();
+                        }
                     }
                 }
             }
             li += ne;
+            ++nbat;
             __syncthreads();
         }
     }
-    // ---- write every cell of the brick once; brick sums of S ----------------
-    T cs[3] = {(T)0, (T)0, (T)0};
-    if (col_in) {
-#pragma unroll
-        for (int z = 0; z < BZ; ++z) {
-            const int gz = B2 + z;
-            if (gz < g.nz) {
-                const long long idx = gx + (long long)g.nx * (gy + (long long)g.ny * gz);
-                p.S[0][idx] = acc[z][0];
-                p.S[1][idx] = acc[z][1];
-                p.S[2][idx] = acc[z][2];
-                cs[0] += acc[z][0]; cs[1] += acc[z][1]; cs[2] += acc[z][2];
-            }
+    if (WP) return;
+    // ---- a brick without candidate lines: zeros ----------------------------
+    if (nbat == 0 && col_in)
+        for (int z = 0; z < nzb; ++z) {
+            const long long idx = col + layer * z;
+            p.S[0][idx] = (T)0; p.S[1][idx] = (T)0; p.S[2][idx] = (T)0;
         }
-    }
+    // ---- brick sums of S and the support count ------------------------------
+    double c0 = (double)cs0 + dep0, c1 = (double)cs1 + dep1, c2 = (double)cs2 + dep2;
     for (int o = 16; o > 0; o >>= 1) {
-        for (int a = 0; a < 3; ++a) cs[a] += __shfl_down_sync(0xffffffffu, cs[a], o);
+        c0 += __shfl_down_sync(0xffffffffu, c0, o);
+        c1 += __shfl_down_sync(0xffffffffu, c1, o);
+        c2 += __shfl_down_sync(0xffffffffu, c2, o);
         nsupp += __shfl_down_sync(0xffffffffu, nsupp, o);
     }
     if (lane == 0) {
-        for (int a = 0; a < 3; ++a) sm.red[a][warp] = (double)cs[a];
-        if (nsupp) atomicAdd(&status[ST_SUPPORT], nsupp);
+        sm.red[0][warp] = c0; sm.red[1][warp] = c1; sm.red[2][warp] = c2;
+        sm.redi[warp] = nsupp;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        int ns = 0;
         for (int a = 0; a < 3; ++a) {
             double t = 0.0;
             for (int w = 0; w < SPREAD_THREADS / 32; ++w) t += sm.red[a][w];
             sc.brickSum[a * g.nbrick + br] = t;
         }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// k_deposit: nodes with w_k = 0 put F_k into the cell that contains them
-// (single thread, fixed order -> deterministic)
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ void d_deposit(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status) {
-    const int cnt = *sc.zeroCount;
-    if (cnt == 0) return;
-    const long long np = b.n_points;
-    for (int i = 1; i < cnt; ++i) {             // insertion sort by node index
-        int v = sc.zeroList[i], j = i - 1;
-        while (j >= 0 && sc.zeroList[j] > v) { sc.zeroList[j + 1] = sc.zeroList[j]; --j; }
-        sc.zeroList[j + 1] = v;
-    }
-    const int nn[3] = {g.nx, g.ny, g.nz};
-    for (int i = 0; i < cnt; ++i) {
-        const int k = sc.zeroList[i];
-        int c[3];
-        bool ins = true;
-        for (int a = 0; a < 3; ++a) {
-            T uh = sc.uhi[a * np + k];
-            float ul = sc.ulo[a * np + k];
-            if (!inside_axis(uh, ul, nn[a])) ins = false;
-            c[a] = min(max(ffloor(uh, ul), 0), nn[a] - 1);
-        }
-        if (!ins) { atomicAdd(&status[ST_DEPOSIT_LOST], 1); continue; }
-        const long long idx = c[0] + (long long)g.nx * (c[1] + (long long)g.ny * c[2]);
-        for (int a = 0; a < 3; ++a) {
-            T dv = p.F[a][k] / (T)g.V;
-            p.S[a][idx] -= dv;
-            sc.depSum[a] -= (double)dv;
-        }
+        for (int w = 0; w < SPREAD_THREADS / 32; ++w) ns += sm.redi[w];
+        if (ns) atomicAdd(&status[ST_SUPPORT], ns);
     }
 }
 
@@ -1238,7 +1627,7 @@ __device__ void d_totals(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
     }
     if (threadIdx.x == 0) {
         for (int a = 0; a < 3; ++a) totals[a] = red[a][0];
-        for (int a = 0; a < 3; ++a) totals[3 + a] = red[3 + a][0] * g.V + sc.depSum[a] * g.V;
+        for (int a = 0; a < 3; ++a) totals[3 + a] = red[3 + a][0] * g.V;
         *sc.hasPrev = 1;                 // the next step relaxes against this one
     }
 }
@@ -1297,20 +1686,23 @@ __global__ void __launch_bounds__(128) k_weights(GridC g, BeamsC b, Scratch<T> s
     if (k < b.n_points) d_weights(g, b, sc, p, status, k, threadIdx.x & 31);
 }
 template <typename T>
-__global__ void __launch_bounds__(256) k_normalise(BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
+__global__ void __launch_bounds__(256) k_normalise(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < b.n_points) d_normalise(b, sc, p, status, k);
+    if (k < b.n_points) d_normalise(g, b, sc, p, status, k);
 }
 template <typename T>
 __global__ void __launch_bounds__(SPREAD_THREADS) k_spread(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
                                                            int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T> &sm = *reinterpret_cast<SpreadSmem<T> *>(smem_raw);
-    d_spread(g, b, sc, p, status, (long long)blockIdx.x, sm);
+    d_brick<T, false>(g, b, sc, p, status, (int)blockIdx.x, sm);
 }
 template <typename T>
-__global__ void k_deposit(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) d_deposit(g, b, sc, p, status);
+__global__ void __launch_bounds__(SPREAD_THREADS) k_bweights(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
+                                                             int *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SpreadSmem<T> &sm = *reinterpret_cast<SpreadSmem<T> *>(smem_raw);
+    d_brick<T, true>(g, b, sc, p, status, (int)blockIdx.x, sm);
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_totals(GridC g, BeamsC b, Scratch<T> sc, double *totals) {
@@ -1380,7 +1772,7 @@ __global__ void __launch_bounds__(256) kb_normalise(const Inst<T> *I, const int 
          gid += (long long)gridDim.x * blockDim.x) {
         const int q = owner(pre, n, gid);
         const Inst<T> &x = I[AL_SEL(q)];
-        d_normalise(x.b, x.sc, x.p, x.status, (int)(gid - pre[q]));
+        d_normalise(x.g, x.b, x.sc, x.p, x.status, (int)(gid - pre[q]));
     }
 }
 // persistent: a fixed grid of CTAs walks the bricks of every instance
@@ -1392,16 +1784,21 @@ __global__ void __launch_bounds__(SPREAD_THREADS) kb_spread(const Inst<T> *I, co
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
         const int q = owner(pre, n, item);
         const Inst<T> &x = I[AL_SEL(q)];
-        d_spread(x.g, x.b, x.sc, x.p, x.status, item - pre[q], sm);
+        d_brick<T, false>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]), sm);
         __syncthreads();
     }
 }
 template <typename T>
-__global__ void kb_deposit(const Inst<T> *I, const int *sel, int n) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < n) {
+__global__ void __launch_bounds__(SPREAD_THREADS) kb_bweights(const Inst<T> *I, const int *sel, const long long *pre,
+                                                              int n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SpreadSmem<T> &sm = *reinterpret_cast<SpreadSmem<T> *>(smem_raw);
+    const long long total = pre[n];
+    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+        const int q = owner(pre, n, item);
         const Inst<T> &x = I[AL_SEL(q)];
-        if (x.b.n_points > 0) d_deposit(x.g, x.b, x.sc, x.p, x.status);
+        d_brick<T, true>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]), sm);
+        __syncthreads();
     }
 }
 template <typename T>
@@ -1411,15 +1808,6 @@ __global__ void __launch_bounds__(256) kb_totals(const Inst<T> *I, const int *se
         const Inst<T> &x = I[AL_SEL(q)];
         d_totals(x.g, x.b, x.sc, x.totals, red);
         __syncthreads();
-    }
-}
-template <typename T>
-__global__ void kb_reset(const Inst<T> *I, const int *sel, int n) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < n) {
-        const Inst<T> &x = I[AL_SEL(q)];
-        *x.sc.zeroCount = 0;
-        x.sc.depSum[0] = x.sc.depSum[1] = x.sc.depSum[2] = 0.0;
     }
 }
 #undef AL_SEL

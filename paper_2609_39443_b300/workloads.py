@@ -392,11 +392,11 @@ def make_batched(seed: int = 0, n_instances: int = 64, *, max_cells: Optional[in
         n_st = int(round(logu(1, 2000)))
         n_cv = int(round(logu(10, 100)))
         sub = int(rng.integers(0, 2 ** 31 - 1))
-        out.append(_random_canopy(sub, nx, ny, nz, h, n_st, n_cv, eps_c, name=f"batch{n}"))
+        out.append(random_canopy(sub, nx, ny, nz, h, n_st, n_cv, eps_c, name=f"batch{n}"))
     return out
 
 
-def _random_canopy(seed, nx, ny, nz, h, n_stems, n_cv, eps_cells, name="canopy"):
+def random_canopy(seed, nx, ny, nz, h, n_stems, n_cv, eps_cells, name="canopy"):
     rng = _rng(seed)
     grid = GridSpec(nx, ny, nz, h, precision="fp32", rho_const=1000.0)
     Lx, Ly, Lz = nx * h, ny * h, nz * h

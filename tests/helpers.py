@@ -62,6 +62,8 @@ def compare(wl, g, o, *, line_mask=None, cell_mask=None, label="", sumF_ref="net
     if line_mask is None:
         scale = max(np.abs(Fo).sum(), 1e-300)
         out["cons"] = float(np.abs(g["totals"][:3] + g["totals"][3:]).max() / scale)
+        # the device total sum S V against the sum of the S array itself
+        out["sumSV"] = float(np.abs(g["totals"][3:] - g["S"].sum(axis=1) * wl.grid.h ** 3).max() / scale)
     msg = f"{label}: {out}"
     if out["S_max_err"] > tS:
         j = int(np.argmax(err))
@@ -71,4 +73,5 @@ def compare(wl, g, o, *, line_mask=None, cell_mask=None, label="", sumF_ref="net
     assert out["sumF_rel"] <= tF, msg
     if "cons" in out:
         assert out["cons"] <= tC, msg
+        assert out["sumSV"] <= tC, msg
     return out

@@ -157,3 +157,23 @@ def test_zero_weight_nodes_deposit():
     g, o = run_gpu(wl), oracle.sample_drag_spread(wl)
     assert g["status"][4] == 3 and o["status"][4] == 3
     compare(wl, g, o, label="zero weight", sumF_ref="abs")
+
+
+def test_dense_stems_several_batches_and_chunks():
+    """More than 512 lines (several mask chunks per brick) and more than 32
+    candidate lines per brick (several batches, S accumulated across them)."""
+    wl = W.random_canopy(11, 64, 48, 32, 0.005, 700, 12, 2.0, name="dense")
+    g, o = run_gpu(wl), oracle.sample_drag_spread(wl)
+    m = compare(wl, g, o, label="dense")
+    assert g["status"][8] == oracle.count_support(wl.grid, wl.beams, wl.step.P)
+    print("dense", m)
+
+
+def test_fine_segments_zero_weight_deposits():
+    """Segments a quarter of a cell long leave many nodes with w_k = 0; each
+    deposits its load in the cell that contains it, inside the projection."""
+    wl = W.random_canopy(12, 48, 40, 32, 0.005, 60, 64, 1.6, name="fine")
+    g, o = run_gpu(wl), oracle.sample_drag_spread(wl)
+    assert o["status"][4] > 0 and g["status"][4] == o["status"][4]
+    m = compare(wl, g, o, label="fine")
+    print("fine", m, "zero-weight nodes", o["status"][4])
