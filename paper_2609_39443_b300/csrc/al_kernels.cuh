@@ -1046,6 +1046,7 @@ struct SpreadSmem {
         struct {
             T Fh[3][NN];         // spread: f^ at the nodes
             int sk[NN];          // spread: global node index of each staged node
+            T acc[BZ][3][BX * BY];   // spread: S of the brick's cells, summed in line order
         } s;
         unsigned long long wq[NN];   // weights pass: fixed-point w of the staged nodes
     } u;
@@ -1141,14 +1142,99 @@ __device__ __noinline__ int nl_exhaustive_staged(const SpreadSmem<T> &sm, const 
     return js;
 }
 
+// float-float arithmetic for the near-tie decisions of FP32 instances
+__device__ __forceinline__ void ff_norm(float &h, float &l) { fast_two_sum(h, l, h, l); }
+__device__ __forceinline__ void ffs_sub(float ah, float al, float bh, float bl, float &rh, float &rl) {
+    float s, e;
+    two_sum(ah, -bh, s, e);
+    e = __fadd_rn(e, __fsub_rn(al, bl));
+    fast_two_sum(s, e, rh, rl);
+}
+__device__ __forceinline__ void ffs_mul(float ah, float al, float bh, float bl, float &rh, float &rl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    fast_two_sum(p, e, rh, rl);
+}
+__device__ __forceinline__ void ffs_add(float ah, float al, float bh, float bl, float &rh, float &rl) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    fast_two_sum(s, e, rh, rl);
+}
+__device__ __forceinline__ void ffs_dot3(const float xh[3], const float xl[3], const float yh[3], const float yl[3],
+                                         float &rh, float &rl) {
+    ffs_mul(xh[0], xl[0], yh[0], yl[0], rh, rl);
+    for (int a = 1; a < 3; ++a) {
+        float ph, pl;
+        ffs_mul(xh[a], xl[a], yh[a], yl[a], ph, pl);
+        ffs_add(rh, rl, ph, pl, rh, rl);
+    }
+}
+
+// "segment k closer to C than segment k-1" for a cell near the bisector
+// plane of node k, from the float-float node positions (about 44 bits).
+// With a = C - P_k, A = a . D_k and B = a . D_{k-1}: the foot on segment k
+// lies past P_k iff A > 0, the foot on segment k-1 lies before P_k iff
+// B < 0, and when both are interior d_{k-1}^2 - d_k^2 has the sign of
+// A^2 |D_{k-1}|^2 - B^2 |D_k|^2.  When both feet sit on P_k the distances
+// are equal and either segment gives the same contribution (the lower index
+// is kept).  Returns 1 / 0, or -1 where the float-float margin does not
+// decide (the FP64 evaluation then decides).
+static __device__ __noinline__ int ff_later_closer(const float *uhi, const float *ulo, long long np, int k, int B0, int B1,
+                                            int B2, float cx, float cy, float cz) {
+    const int Bv[3] = {B0, B1, B2};
+    const float C[3] = {cx, cy, cz};
+    float ph[3][3], pl[3][3];                       // nodes k-1, k, k+1 relative to the brick origin
+    for (int n = 0; n < 3; ++n)
+        for (int a = 0; a < 3; ++a) {
+            float h = __fsub_rn(uhi[a * np + k - 1 + n], (float)Bv[a]);   // exact: |uh| < 2^24, B integer
+            float l = ulo[a * np + k - 1 + n];
+            ff_norm(h, l);
+            ph[n][a] = h;
+            pl[n][a] = l;
+        }
+    float ah[3], al[3], kh[3], kl[3], mh[3], ml[3];
+    for (int a = 0; a < 3; ++a) {
+        ffs_sub(C[a], 0.0f, ph[1][a], pl[1][a], ah[a], al[a]);
+        ffs_sub(ph[2][a], pl[2][a], ph[1][a], pl[1][a], kh[a], kl[a]);    // D_k
+        ffs_sub(ph[1][a], pl[1][a], ph[0][a], pl[0][a], mh[a], ml[a]);    // D_{k-1}
+    }
+    float Ah, Al, Bh, Bl;
+    ffs_dot3(ah, al, kh, kl, Ah, Al);
+    ffs_dot3(ah, al, mh, ml, Bh, Bl);
+    if (Ah <= 0.0f && Bh >= 0.0f) return 0;         // both feet on P_k: equal distances
+    if (Ah > 0.0f && Bh >= 0.0f) return 1;          // only segment k's foot is interior
+    if (Ah <= 0.0f && Bh < 0.0f) return 0;          // only segment k-1's foot is interior
+    float L2h, L2l, L1h, L1l;                       // |D_k|^2, |D_{k-1}|^2
+    ffs_dot3(kh, kl, kh, kl, L2h, L2l);
+    ffs_dot3(mh, ml, mh, ml, L1h, L1l);
+    if (!(Ah < L2h) || !(-Bh < L1h)) return -1;     // a foot clamped at the far end: not this case
+    float t1h, t1l, t2h, t2l, lh, ll, rh, rl, dh, dl;
+    ffs_mul(Ah, Al, Ah, Al, t1h, t1l);
+    ffs_mul(t1h, t1l, L1h, L1l, lh, ll);
+    ffs_mul(Bh, Bl, Bh, Bl, t2h, t2l);
+    ffs_mul(t2h, t2l, L2h, L2l, rh, rl);
+    ffs_sub(lh, ll, rh, rl, dh, dl);
+    if (fabsf(dh) <= 1e-11f * fmaxf(lh, rh)) return -1;
+    return dh > 0.0f ? 1 : 0;
+}
+
 template <typename T>
 __device__ __forceinline__ bool sig_pos(const SpreadSmem<T> &sm, int s, const T C[3], const GridC &g,
-                                        const StepPtrs<T> &p, int kglob, int ci, int cj, int ck, int *status) {
+                                        const StepPtrs<T> &p, const Scratch<T> &sc, int kglob, int B0, int B1,
+                                        int B2, int ci, int cj, int ck, int *status) {
     const T x0 = C[0] - sm.P[0][s], x1 = C[1] - sm.P[1][s], x2 = C[2] - sm.P[2][s];
     const T sg = x0 * sm.M[0][s] + x1 * sm.M[1][s] + x2 * sm.M[2][s];
     const T gs = Tr<T>::gsig(tsqrt(x0 * x0 + x1 * x1 + x2 * x2));
     if (sg > gs) return true;
     if (sg < -gs) return false;
+    if (sizeof(T) == 4) {
+        const int r = ff_later_closer((const float *)sc.uhi, sc.ulo, (long long)p.np, kglob, B0, B1, B2,
+                                      (float)C[0], (float)C[1], (float)C[2]);
+        if (r >= 0) return r == 1;
+    }
     return nl_later_closer(g, p, kglob, ci, cj, ck, status);
 }
 template <typename T>
@@ -1181,18 +1267,12 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     const int bzi = br / nbxy, rem = br - bzi * nbxy;
     const int byi = rem / g.nbx, bxi = rem - byi * g.nbx;
     const int B0 = bxi * BX, B1 = byi * BY, B2 = bzi * BZ;
-    const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gx = B0 + tx, gy = B1 + ty;
-    const bool col_in = gx < g.nx && gy < g.ny;
-    const float cx = tx + 0.5f, cy = ty + 0.5f;
     const int nzb = min(BZ, g.nz - B2);              // layers of this brick inside the grid
-    const long long layer = (long long)g.nx * g.ny;
-    const long long col = gx + (long long)g.nx * gy + layer * B2;   // cell (gx, gy, B2)
+    const int nxb = min(BX, g.nx - B0), nyb = min(BY, g.ny - B1);
     int nsupp = 0;                                   // (cell, line) pairs within 3 eps
-    int nbat = 0;                                    // batches done
-    T cs0 = (T)0, cs1 = (T)0, cs2 = (T)0;            // final S of this thread's cells
-    double dep0 = 0.0, dep1 = 0.0, dep2 = 0.0;       // warp 0: deposits of the last batch
+    if (!WP)
+        for (int i = threadIdx.x; i < BZ * 3 * BX * BY; i += SPREAD_THREADS) (&sm.u.s.acc[0][0][0])[i] = (T)0;
 
     const int W = b.mask_words;
     uint32_t *mrow = sc.mask + (long long)br * W;
@@ -1200,17 +1280,6 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     const float bhi[3] = {(float)(B0 + BX), (float)(B1 + BY), (float)(B2 + BZ)};
 
     constexpr int CH = SM::LIST / 32;                // mask words per chunk
-    int nleft = 0;                                   // spread: candidate lines not yet processed
-    if (!WP) {
-        if (warp == 0) {
-            int c = 0;
-            for (int w = lane; w < W; w += 32) c += __popc(mrow[w]);
-            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-            if (lane == 0) sm.nlist = c;
-        }
-        __syncthreads();
-        nleft = sm.nlist;
-    }
     for (int w0 = 0; w0 < W; w0 += CH) {
         // ---- candidate lines from CH mask words, in line order -------------
         __syncthreads();
@@ -1335,8 +1404,6 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
             }
             __syncthreads();
             const int ne = sm.nbatch;
-            nleft -= ne;
-            const bool last = nleft == 0;                // S of this brick is final after this batch
             // ---- stage nodes of the batch ----------------------------------
             for (int e = 0; e < ne; ++e) {
                 const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e], base = sm.e_base[e];
@@ -1403,121 +1470,146 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                 sm.l_gy[e][lane] = d1 * il2;
             }
             __syncthreads();
-            // ---- gather: every thread walks only the lines near its column ----
-            if (col_in) {
-                uint32_t cm = 0;
-                for (int e = 0; e < ne; ++e)
-                    if (sm.e_jhi[e] >= sm.e_jlo[e] && cx >= sm.e_lo[e][0] && cx <= sm.e_hi[e][0] &&
-                        cy >= sm.e_lo[e][1] && cy <= sm.e_hi[e][1])
-                        cm |= 1u << e;
-                float cz = 0.5f;
-                for (int z = 0; z < nzb; ++z, cz += 1.0f) {
-                    const int gz = B2 + z;
-                    T a0 = (T)0, a1 = (T)0, a2 = (T)0;
-                    uint32_t m = cm;
-                    while (m) {                                  // increasing e = line order
-                        const int e = __ffs(m) - 1;
-                        m &= m - 1;
-                        if (cz < sm.e_lo[e][2] || cz > sm.e_hi[e][2]) continue;
-                        const float dx = cx - sm.l_xc[e][z], dy = cy - sm.l_yc[e][z];
-                        if (dx * dx + dy * dy > sm.l_rh2[e][z]) continue;      // farther than 3 eps
-                        const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e], base = sm.e_base[e];
-                        const int first = sm.e_first[e], n = sm.e_n[e];
-                        const T C[3] = {(T)cx, (T)cy, (T)cz};
-                        const T R2 = sm.e_R2[e], gr = sm.e_gr[e];
-                        int js;
-                        T s, r2;
-                        if (base < 0) {
-                            js = nl_exhaustive(g, sc, p, first, n, jlo, jhi, C[0], C[1], C[2], B0, B1, B2, gx, gy,
-                                               gz, status);
-                            const int ka = first + js;
-                            T x[3], Dj[3];
-                            const int Bv[3] = {B0, B1, B2};
-                            for (int a = 0; a < 3; ++a) {
-                                x[a] = C[a] - rel(sc.uhi[a * np + ka], sc.ulo[a * np + ka], Bv[a]);
-                                Dj[a] = sc.segD[a * np + ka];
-                            }
-                            s = (x[0] * Dj[0] + x[1] * Dj[1] + x[2] * Dj[2]) * sc.segIl2[ka];
-                            s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
-                            const T e0 = x[0] - s * Dj[0], e1 = x[1] - s * Dj[1], e2 = x[2] - s * Dj[2];
-                            r2 = e0 * e0 + e1 * e1 + e2 * e2;
-                        } else {
-                            const int reg = sm.e_reg[e];
-                            bool exh = reg == 0, start_ok = true;
-                            js = jlo;
-                            if (!exh) {
-                                // start near the foot: the crossing plus the in-layer offset along the segment
-                                int j = (int)floorf(sm.l_ac[e][z] + dx * sm.l_gx[e][z] + dy * sm.l_gy[e][z]);
-                                j = min(max(j, jlo), jhi);
-                                if (reg == 2) {
-                                    const float rho2 = sm.e_rho2[e];
-                                    if (node_d2(sm, base + (j - jlo), C) > (T)rho2) {
-                                        j = sm.l_jc[e][z];
+            // ---- gather: warp w takes layer w; for each line in order its lanes take
+            //      the cells of the layer near the line, two rows of 16 at a time, so no
+            //      two lanes share a cell and every cell sums its lines in line order ----
+            for (int z = warp; z < nzb; z += SPREAD_THREADS / 32) {
+                const float czf = z + 0.5f;
+                const int gz = B2 + z;
+                for (int e = 0; e < ne; ++e) {
+                    const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e];
+                    if (jhi < jlo || czf < sm.e_lo[e][2] || czf > sm.e_hi[e][2]) continue;
+                    float xlo = sm.e_lo[e][0], xhi = sm.e_hi[e][0], ylo = sm.e_lo[e][1], yhi = sm.e_hi[e][1];
+                    const float rh2 = sm.l_rh2[e][z], xc = sm.l_xc[e][z], yc = sm.l_yc[e][z];
+                    if (rh2 < 1e30f) {
+                        const float rh = sqrtf(rh2);
+                        xlo = fmaxf(xlo, xc - rh); xhi = fminf(xhi, xc + rh);
+                        ylo = fmaxf(ylo, yc - rh); yhi = fminf(yhi, yc + rh);
+                    }
+                    // columns whose centre i + 1/2 lies in [lo, hi], inside brick and grid
+                    const int ix0 = max(0, (int)ceilf(fmaxf(xlo, -1.0f) - 0.5f));
+                    const int ix1 = min(nxb - 1, (int)floorf(fminf(xhi, (float)BX + 1.0f) - 0.5f));
+                    const int iy0 = max(0, (int)ceilf(fmaxf(ylo, -1.0f) - 0.5f));
+                    const int iy1 = min(nyb - 1, (int)floorf(fminf(yhi, (float)BY + 1.0f) - 0.5f));
+                    if (ix0 > ix1 || iy0 > iy1) continue;
+                    const int base = sm.e_base[e], first = sm.e_first[e], n = sm.e_n[e], reg = sm.e_reg[e];
+                    const T R2 = sm.e_R2[e], gr = sm.e_gr[e], ie2 = sm.e_ie2[e], e0v = sm.e_eta0[e];
+                    const float rho2 = sm.e_rho2[e];
+                    const float ac = sm.l_ac[e][z], gxv = sm.l_gx[e][z], gyv = sm.l_gy[e][z];
+                    const int jcz = sm.l_jc[e][z];
+                    const int tx = ix0 + (lane & 15);
+                    for (int y0 = iy0; y0 <= iy1; y0 += 2) {
+                        const int ty = y0 + (lane >> 4);
+                        const float cx = tx + 0.5f, cy = ty + 0.5f;
+                        const float dx = cx - xc, dy = cy - yc;
+                        bool in = false;
+                        int js = 0;
+                        T s = (T)0, r2 = (T)0;
+                        if (tx <= ix1 && ty <= iy1 && dx * dx + dy * dy <= rh2) {
+                            const int gxc = B0 + tx, gyc = B1 + ty;
+                            const T C[3] = {(T)cx, (T)cy, (T)czf};
+                            if (base < 0) {
+                                js = nl_exhaustive(g, sc, p, first, n, jlo, jhi, C[0], C[1], C[2], B0, B1, B2, gxc, gyc,
+                                                   gz, status);
+                                const int ka = first + js;
+                                T x[3], Dj[3];
+                                const int Bv[3] = {B0, B1, B2};
+                                for (int a = 0; a < 3; ++a) {
+                                    x[a] = C[a] - rel(sc.uhi[a * np + ka], sc.ulo[a * np + ka], Bv[a]);
+                                    Dj[a] = sc.segD[a * np + ka];
+                                }
+                                s = (x[0] * Dj[0] + x[1] * Dj[1] + x[2] * Dj[2]) * sc.segIl2[ka];
+                                s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
+                                const T f0 = x[0] - s * Dj[0], f1 = x[1] - s * Dj[1], f2 = x[2] - s * Dj[2];
+                                r2 = f0 * f0 + f1 * f1 + f2 * f2;
+                            } else {
+                                bool exh = reg == 0, start_ok = true;
+                                js = jlo;
+                                if (!exh) {
+                                    // start near the foot: the crossing plus the in-layer offset along the segment
+                                    int j = (int)floorf(ac + dx * gxv + dy * gyv);
+                                    j = min(max(j, jlo), jhi);
+                                    if (reg == 2 && node_d2(sm, base + (j - jlo), C) > (T)rho2) {
+                                        j = jcz;
                                         start_ok = node_d2(sm, base + (j - jlo), C) <= (T)rho2;
                                     }
+                                    while (j > jlo && !sig_pos(sm, base + (j - jlo), C, g, p, sc, first + j, B0, B1, B2,
+                                                               gxc, gyc, gz, status)) --j;
+                                    while (j < jhi && sig_pos(sm, base + (j + 1 - jlo), C, g, p, sc, first + j + 1, B0,
+                                                              B1, B2, gxc, gyc, gz, status)) ++j;
+                                    js = j;
                                 }
-                                while (j > jlo && !sig_pos(sm, base + (j - jlo), C, g, p, first + j, gx, gy, gz, status)) --j;
-                                while (j < jhi && sig_pos(sm, base + (j + 1 - jlo), C, g, p, first + j + 1, gx, gy, gz, status)) ++j;
-                                js = j;
-                            }
-                            seg_foot(sm, base + (js - jlo), C, s, r2);
-                            // a walk from outside the certified radius is exact only when it ends within R
-                            if (exh || (!start_ok && !(r2 < R2 - gr))) {
-                                js = nl_exhaustive_staged(sm, g, p, base, first, n, jlo, jhi, C[0], C[1], C[2], gx,
-                                                          gy, gz, status);
                                 seg_foot(sm, base + (js - jlo), C, s, r2);
+                                // a walk from outside the certified radius is exact only when it ends within R
+                                if (exh || (!start_ok && !(r2 < R2 - gr))) {
+                                    js = nl_exhaustive_staged(sm, g, p, base, first, n, jlo, jhi, C[0], C[1], C[2],
+                                                              gxc, gyc, gz, status);
+                                    seg_foot(sm, base + (js - jlo), C, s, r2);
+                                }
                             }
+                            if (r2 < R2 - gr) in = true;
+                            else if (r2 > R2 + gr) in = false;
+                            else in = nl_within(g, p, b.eps[sm.e_line[e]], first + js, n, gxc, gyc, gz, status);
                         }
-                        bool in;
-                        if (r2 < R2 - gr) in = true;
-                        else if (r2 > R2 + gr) in = false;
-                        else in = nl_within(g, p, b.eps[sm.e_line[e]], first + js, n, gx, gy, gz, status);
-                        if (!in) continue;
-                        ++nsupp;
-                        const T q = Tr<T>::ex2(-r2 * sm.e_ie2[e]);
-                        if (WP) {
-                            // omega eta / eta0 into the two nodes of the closest segment
-                            const int sh = (int)sm.e_eta0[e];
-                            if (base >= 0) {
-                                const int ss = base + (js - jlo), sb = (n == 1) ? ss : ss + 1;
-                                atomicAdd(&sm.u.wq[ss], to_fixed(q * ((T)1 - s), sh));
-                                atomicAdd(&sm.u.wq[sb], to_fixed(q * s, sh));
-                            } else {
-                                const int ka = first + js;
-                                atomicAdd(&sc.wfix[ka], to_fixed(q * ((T)1 - s), sh));
-                                atomicAdd(&sc.wfix[seg_end(ka, n)], to_fixed(q * s, sh));
+                        T q = (T)0;
+                        if (in) {
+                            ++nsupp;
+                            q = Tr<T>::ex2(-r2 * ie2);
+                        }
+                        if (!WP) {
+                            if (in) {
+                                T fa0, fa1, fa2, fb0, fb1, fb2;
+                                if (base >= 0) {
+                                    const int ss = base + (js - jlo), sb = (n == 1) ? ss : ss + 1;
+                                    fa0 = sm.u.s.Fh[0][ss]; fa1 = sm.u.s.Fh[1][ss]; fa2 = sm.u.s.Fh[2][ss];
+                                    fb0 = sm.u.s.Fh[0][sb]; fb1 = sm.u.s.Fh[1][sb]; fb2 = sm.u.s.Fh[2][sb];
+                                } else {
+                                    const int ka = first + js, kb = seg_end(ka, n);
+                                    fa0 = sc.fhat[ka]; fa1 = sc.fhat[np + ka]; fa2 = sc.fhat[2 * np + ka];
+                                    fb0 = sc.fhat[kb]; fb1 = sc.fhat[np + kb]; fb2 = sc.fhat[2 * np + kb];
+                                }
+                                const T eta = e0v * q;
+                                const T wa = eta * ((T)1 - s), wb = eta * s;
+                                const int c = ty * BX + tx;
+                                sm.u.s.acc[z][0][c] -= wa * fa0 + wb * fb0;
+                                sm.u.s.acc[z][1][c] -= wa * fa1 + wb * fb1;
+                                sm.u.s.acc[z][2][c] -= wa * fa2 + wb * fb2;
                             }
-                            continue;
-                        }
-                        T fa0, fa1, fa2, fb0, fb1, fb2;
-                        if (base >= 0) {
-                            const int ss = base + (js - jlo), sb = (n == 1) ? ss : ss + 1;
-                            fa0 = sm.u.s.Fh[0][ss]; fa1 = sm.u.s.Fh[1][ss]; fa2 = sm.u.s.Fh[2][ss];
-                            fb0 = sm.u.s.Fh[0][sb]; fb1 = sm.u.s.Fh[1][sb]; fb2 = sm.u.s.Fh[2][sb];
                         } else {
-                            const int ka = first + js, kb = seg_end(ka, n);
-                            fa0 = sc.fhat[ka]; fa1 = sc.fhat[np + ka]; fa2 = sc.fhat[2 * np + ka];
-                            fb0 = sc.fhat[kb]; fb1 = sc.fhat[np + kb]; fb2 = sc.fhat[2 * np + kb];
+                            // omega eta / eta0 into the two nodes of the closest segment, as
+                            // fixed-point integers summed over the warp per node (exact)
+                            const int sh = (int)e0v;
+                            unsigned long long va = 0ull, vb = 0ull;
+                            int na = -1, nb2 = -1;
+                            if (in) {
+                                va = to_fixed(q * ((T)1 - s), sh);
+                                vb = to_fixed(q * s, sh);
+                                if (base >= 0) {
+                                    na = base + (js - jlo);
+                                    nb2 = (n == 1) ? na : na + 1;
+                                } else {
+                                    const int ka = first + js;
+                                    atomicAdd(&sc.wfix[ka], va);
+                                    atomicAdd(&sc.wfix[seg_end(ka, n)], vb);
+                                }
+                            }
+                            unsigned pend = __ballot_sync(0xffffffffu, na >= 0 || nb2 >= 0);
+                            while (pend) {
+                                const int leader = __ffs(pend) - 1;
+                                const int tgt = __shfl_sync(0xffffffffu, na >= 0 ? na : nb2, leader);
+                                unsigned long long v = 0ull;
+                                if (na == tgt) { v += va; na = -1; }
+                                if (nb2 == tgt) { v += vb; nb2 = -1; }
+                                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                                if (lane == 0 && v) atomicAdd(&sm.u.wq[tgt], v);
+                                pend = __ballot_sync(0xffffffffu, na >= 0 || nb2 >= 0);
+                            }
                         }
-                        const T eta = sm.e_eta0[e] * q;
-                        const T wa = eta * ((T)1 - s), wb = eta * s;
-                        a0 -= wa * fa0 + wb * fb0;
-                        a1 -= wa * fa1 + wb * fb1;
-                        a2 -= wa * fa2 + wb * fb2;
-                    }
-                    if (!WP) {
-                        // the thread owns the cell: the first batch writes it, later ones add to it
-                        const long long idx = col + layer * z;
-                        if (nbat > 0 && (cm || last)) {
-                            a0 += p.S[0][idx]; a1 += p.S[1][idx]; a2 += p.S[2][idx];
-                        }
-                        if (nbat == 0 || cm) { p.S[0][idx] = a0; p.S[1][idx] = a1; p.S[2][idx] = a2; }
-                        if (last) { cs0 += a0; cs1 += a1; cs2 += a2; }
                     }
                 }
             }
+            __syncthreads();
             if (WP) {
-                __syncthreads();
                 for (int e = 0; e < ne; ++e) {
                     const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e], base = sm.e_base[e];
                     if (jhi < jlo || base < 0) continue;
@@ -1529,62 +1621,58 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                         if (v) atomicAdd(&sc.wfix[first + jlo + t], v);
                     }
                 }
-            } else {
+            } else if (warp == 0) {
                 // ---- deposits of the zero-weight nodes inside this brick, in line and node order
-                __syncthreads();
-                if (warp == 0) {
-                    const int tot = sm.nstaged;
-                    for (int s0 = 0; s0 < tot; s0 += 32) {
-                        const int s = s0 + lane;
-                        int idx3[3];
-                        bool f = s < tot && sm.zf[s];
-                        int k = 0;
-                        if (f) {
-                            k = sm.u.s.sk[s];
-                            const int Bv[3] = {B0, B1, B2}, bs[3] = {BX, BY, BZ}, nn[3] = {g.nx, g.ny, g.nz};
-                            for (int a = 0; a < 3; ++a) {
-                                const T uh = sc.uhi[a * np + k];
-                                const float ul = sc.ulo[a * np + k];
-                                const int c = ffloor(uh, ul);
-                                f = f && inside_axis(uh, ul, nn[a]) && c >= Bv[a] && c < Bv[a] + bs[a];
-                                idx3[a] = c;
-                            }
+                const int tot = sm.nstaged;
+                for (int s0 = 0; s0 < tot; s0 += 32) {
+                    const int sl = s0 + lane;
+                    int c3[3] = {0, 0, 0};
+                    bool f = sl < tot && sm.zf[sl];
+                    int k = 0;
+                    if (f) {
+                        k = sm.u.s.sk[sl];
+                        const int Bv[3] = {B0, B1, B2}, bs[3] = {BX, BY, BZ}, nn[3] = {g.nx, g.ny, g.nz};
+                        for (int a = 0; a < 3; ++a) {
+                            const T uh = sc.uhi[a * np + k];
+                            const float ul = sc.ulo[a * np + k];
+                            const int c = ffloor(uh, ul);
+                            f = f && inside_axis(uh, ul, nn[a]) && c >= Bv[a] && c < Bv[a] + bs[a];
+                            c3[a] = c - Bv[a];
                         }
-                        uint32_t bal = __ballot_sync(0xffffffffu, f);
-                        while (bal) {
-                            const int src = __ffs(bal) - 1;
-                            bal &= bal - 1;
-                            if (lane == src) {
-                                const long long idx = idx3[0] + (long long)g.nx * (idx3[1] + (long long)g.ny * idx3[2]);
-                                double d[3];
-                                for (int a = 0; a < 3; ++a) {
-                                    const T old = p.S[a][idx];
-                                    const T nw = old - p.F[a][k] / (T)g.V;
-                                    p.S[a][idx] = nw;
-                                    d[a] = (double)nw - (double)old;
-                                }
-                                // the change enters the brick sum through this lane's counters
-                                if (last) { dep0 += d[0]; dep1 += d[1]; dep2 += d[2]; }
-                            }
-                            __syncwarp();
-                        }
+                    }
+                    uint32_t bal = __ballot_sync(0xffffffffu, f);
+                    while (bal) {
+                        const int src = __ffs(bal) - 1;
+                        bal &= bal - 1;
+                        if (lane == src)
+                            for (int a = 0; a < 3; ++a)
+                                sm.u.s.acc[c3[2]][a][c3[1] * BX + c3[0]] -= p.F[a][k] / (T)g.V;
+                        __syncwarp();
                     }
                 }
             }
             li += ne;
-            ++nbat;
             __syncthreads();
         }
     }
     if (WP) return;
-    // ---- a brick without candidate lines: zeros ----------------------------
-    if (nbat == 0 && col_in)
-        for (int z = 0; z < nzb; ++z) {
-            const long long idx = col + layer * z;
-            p.S[0][idx] = (T)0; p.S[1][idx] = (T)0; p.S[2][idx] = (T)0;
+    // ---- write every cell of the brick once; brick sums of S -----------------
+    T cs0 = (T)0, cs1 = (T)0, cs2 = (T)0;
+    {
+        const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
+        if (tx < nxb && ty < nyb) {
+            const long long layer = (long long)g.nx * g.ny;
+            const long long col = (B0 + tx) + (long long)g.nx * (B1 + ty) + layer * B2;
+            for (int z = 0; z < nzb; ++z) {
+                const long long idx = col + layer * z;
+                const T v0 = sm.u.s.acc[z][0][threadIdx.x], v1 = sm.u.s.acc[z][1][threadIdx.x],
+                        v2 = sm.u.s.acc[z][2][threadIdx.x];
+                p.S[0][idx] = v0; p.S[1][idx] = v1; p.S[2][idx] = v2;
+                cs0 += v0; cs1 += v1; cs2 += v2;
+            }
         }
-    // ---- brick sums of S and the support count ------------------------------
-    double c0 = (double)cs0 + dep0, c1 = (double)cs1 + dep1, c2 = (double)cs2 + dep2;
+    }
+    double c0 = (double)cs0, c1 = (double)cs1, c2 = (double)cs2;
     for (int o = 16; o > 0; o >>= 1) {
         c0 += __shfl_down_sync(0xffffffffu, c0, o);
         c1 += __shfl_down_sync(0xffffffffu, c1, o);
