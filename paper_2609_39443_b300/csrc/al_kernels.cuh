@@ -1120,13 +1120,19 @@ __device__ __noinline__ int nl_exhaustive(const GridC &g, const Scratch<T> &sc, 
     if (!(second - best > Tr<T>::grr(best))) js = nl_argmin(g, p, first + jlo, first + jhi, n, ci, cj, ck, status) - first;
     return js;
 }
-// the same over the staged candidate segments
+// the same over the staged candidate segments.  A near tie between the two
+// closest segments that share a node is decided by the float-float test of
+// the pair (ff_later_closer, defined below); other near ties by the FP64
+// argmin.
+static __device__ __noinline__ int ff_later_closer(const float *uhi, const float *ulo, long long np, int k, int B0,
+                                                   int B1, int B2, float cx, float cy, float cz);
 template <typename T>
 __device__ __noinline__ int nl_exhaustive_staged(const SpreadSmem<T> &sm, const GridC &g, const StepPtrs<T> &p,
-                                                 int base, int first, int n, int jlo, int jhi, T c0, T c1, T c2,
-                                                 int ci, int cj, int ck, int *status) {
-    T best = (T)INFINITY, second = (T)INFINITY;
-    int js = jlo;
+                                                 const Scratch<T> &sc, int base, int first, int n, int jlo, int jhi,
+                                                 T c0, T c1, T c2, int B0, int B1, int B2, int ci, int cj, int ck,
+                                                 int *status) {
+    T best = (T)INFINITY, second = (T)INFINITY, third = (T)INFINITY;
+    int js = jlo, j2 = jlo;
     for (int jj = jlo; jj <= jhi; ++jj) {
         const int ss = base + (jj - jlo);
         const T x0 = c0 - sm.P[0][ss], x1 = c1 - sm.P[1][ss], x2 = c2 - sm.P[2][ss];
@@ -1135,10 +1141,21 @@ __device__ __noinline__ int nl_exhaustive_staged(const SpreadSmem<T> &sm, const 
         t = t < (T)0 ? (T)0 : (t > (T)1 ? (T)1 : t);
         const T e0 = x0 - t * d0, e1 = x1 - t * d1, e2 = x2 - t * d2;
         const T dd = e0 * e0 + e1 * e1 + e2 * e2;
-        if (dd < best) { second = best; best = dd; js = jj; }
-        else if (dd < second) second = dd;
+        if (dd < best) { third = second; second = best; j2 = js; best = dd; js = jj; }
+        else if (dd < second) { third = second; second = dd; j2 = jj; }
+        else if (dd < third) third = dd;
     }
-    if (!(second - best > Tr<T>::grr(best))) js = nl_argmin(g, p, first + jlo, first + jhi, n, ci, cj, ck, status) - first;
+    const T band = Tr<T>::grr(best);
+    if (!(second - best > band)) {
+        int r = -1;
+        if (sizeof(T) == 4 && third - best > band && abs(js - j2) == 1 && n >= 3) {
+            const int k = max(js, j2);                  // decide d_k < d_{k-1}
+            r = ff_later_closer((const float *)sc.uhi, sc.ulo, (long long)p.np, first + k, B0, B1, B2,
+                                (float)c0, (float)c1, (float)c2);
+            if (r >= 0) js = r ? k : k - 1;
+        }
+        if (r < 0) js = nl_argmin(g, p, first + jlo, first + jhi, n, ci, cj, ck, status) - first;
+    }
     return js;
 }
 
@@ -1201,16 +1218,15 @@ static __device__ __noinline__ int ff_later_closer(const float *uhi, const float
         ffs_sub(ph[2][a], pl[2][a], ph[1][a], pl[1][a], kh[a], kl[a]);    // D_k
         ffs_sub(ph[1][a], pl[1][a], ph[0][a], pl[0][a], mh[a], ml[a]);    // D_{k-1}
     }
-    float Ah, Al, Bh, Bl;
+    float Ah, Al, Bh, Bl, L2h, L2l, L1h, L1l;       // a . D_k, a . D_{k-1}, |D_k|^2, |D_{k-1}|^2
     ffs_dot3(ah, al, kh, kl, Ah, Al);
     ffs_dot3(ah, al, mh, ml, Bh, Bl);
+    ffs_dot3(kh, kl, kh, kl, L2h, L2l);
+    ffs_dot3(mh, ml, mh, ml, L1h, L1l);
+    if (!(Ah < L2h) || !(-Bh < L1h)) return -1;     // a foot clamped at the far end: not decided here
     if (Ah <= 0.0f && Bh >= 0.0f) return 0;         // both feet on P_k: equal distances
     if (Ah > 0.0f && Bh >= 0.0f) return 1;          // only segment k's foot is interior
     if (Ah <= 0.0f && Bh < 0.0f) return 0;          // only segment k-1's foot is interior
-    float L2h, L2l, L1h, L1l;                       // |D_k|^2, |D_{k-1}|^2
-    ffs_dot3(kh, kl, kh, kl, L2h, L2l);
-    ffs_dot3(mh, ml, mh, ml, L1h, L1l);
-    if (!(Ah < L2h) || !(-Bh < L1h)) return -1;     // a foot clamped at the far end: not this case
     float t1h, t1l, t2h, t2l, lh, ll, rh, rl, dh, dl;
     ffs_mul(Ah, Al, Ah, Al, t1h, t1l);
     ffs_mul(t1h, t1l, L1h, L1l, lh, ll);
@@ -1498,6 +1514,10 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                     const float ac = sm.l_ac[e][z], gxv = sm.l_gx[e][z], gyv = sm.l_gy[e][z];
                     const int jcz = sm.l_jc[e][z];
                     const int tx = ix0 + (lane & 15);
+                    // weights pass: per-lane sums for the four nodes around the crossing
+                    // (slots w0s .. w0s + 3), reduced over the warp once per line and layer
+                    unsigned long long wacc0 = 0ull, wacc1 = 0ull, wacc2 = 0ull, wacc3 = 0ull;
+                    const int w0s = (base >= 0) ? base + (jcz - jlo) - 1 : 0;
                     for (int y0 = iy0; y0 <= iy1; y0 += 2) {
                         const int ty = y0 + (lane >> 4);
                         const float cx = tx + 0.5f, cy = ty + 0.5f;
@@ -1542,8 +1562,8 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                                 seg_foot(sm, base + (js - jlo), C, s, r2);
                                 // a walk from outside the certified radius is exact only when it ends within R
                                 if (exh || (!start_ok && !(r2 < R2 - gr))) {
-                                    js = nl_exhaustive_staged(sm, g, p, base, first, n, jlo, jhi, C[0], C[1], C[2],
-                                                              gxc, gyc, gz, status);
+                                    js = nl_exhaustive_staged(sm, g, p, sc, base, first, n, jlo, jhi, C[0], C[1], C[2],
+                                                              B0, B1, B2, gxc, gyc, gz, status);
                                     seg_foot(sm, base + (js - jlo), C, s, r2);
                                 }
                             }
@@ -1593,17 +1613,27 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                                     atomicAdd(&sc.wfix[seg_end(ka, n)], vb);
                                 }
                             }
-                            unsigned pend = __ballot_sync(0xffffffffu, na >= 0 || nb2 >= 0);
-                            while (pend) {
-                                const int leader = __ffs(pend) - 1;
-                                const int tgt = __shfl_sync(0xffffffffu, na >= 0 ? na : nb2, leader);
-                                unsigned long long v = 0ull;
-                                if (na == tgt) { v += va; na = -1; }
-                                if (nb2 == tgt) { v += vb; nb2 = -1; }
-                                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                                if (lane == 0 && v) atomicAdd(&sm.u.wq[tgt], v);
-                                pend = __ballot_sync(0xffffffffu, na >= 0 || nb2 >= 0);
+                            // exact integer sums: near the crossing into the lane's counters,
+                            // elsewhere straight into the shared node sums
+                            if (na >= 0) {
+                                const int oa = na - w0s, ob = nb2 - w0s;
+                                wacc0 += (oa == 0 ? va : 0ull) + (ob == 0 ? vb : 0ull);
+                                wacc1 += (oa == 1 ? va : 0ull) + (ob == 1 ? vb : 0ull);
+                                wacc2 += (oa == 2 ? va : 0ull) + (ob == 2 ? vb : 0ull);
+                                wacc3 += (oa == 3 ? va : 0ull) + (ob == 3 ? vb : 0ull);
+                                if ((unsigned)oa > 3u && va) atomicAdd(&sm.u.wq[na], va);
+                                if ((unsigned)ob > 3u && vb) atomicAdd(&sm.u.wq[nb2], vb);
                             }
+                        }
+                    }
+                    if (WP && base >= 0) {
+                        unsigned long long wv[4] = {wacc0, wacc1, wacc2, wacc3};
+                        for (int q4 = 0; q4 < 4; ++q4) {
+                            unsigned long long v = wv[q4];
+                            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                            const int slot = w0s + q4;
+                            if (lane == 0 && v && slot >= base && slot < base + (jhi - jlo + 2))
+                                atomicAdd(&sm.u.wq[slot], v);
                         }
                     }
                 }
