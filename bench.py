@@ -51,6 +51,7 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default options)")
     return ap.parse_args()
 
 
@@ -228,6 +229,10 @@ def run_ours(a):
 
     wl = _workload(a.workload, rank, a.eps)
     inst = Instance(wl, device=f"cuda:{local}")
+    tuned = {"weights": "brick", "brick_z": 8, "autotuned": False}
+    if not a.no_tune:
+        wmode, bz = inst.autotune(trials=2)
+        tuned = {"weights": "segment" if wmode else "brick", "brick_z": bz, "autotuned": True}
     inst.grid.trace(True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
@@ -319,7 +324,7 @@ def run_ours(a):
                 "dtype": "f64" if wl.grid.precision == "fp64" else "f32", "data": "synthetic",
                 "config": {"workload": wl.name, "cells": wl.grid.n_cells, "points": wl.beams.n_points,
                            "lines": wl.beams.n_lines, "parallelism": f"{world} independent instances",
-                           "l2": "flushed between timed steps (256 MiB write)"},
+                           "l2": "flushed between timed steps (256 MiB write)", "options": tuned},
                 "kernel_cell_updates_per_s": supp * value,
                 "support_pairs_per_step": supp,
                 "phases_ms": {k: float(v) for k, v in zip(PHASES, ph)},
@@ -327,7 +332,7 @@ def run_ours(a):
                              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                              "algorithmic_bytes": alg, "traffic": traffic},
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": KERNELS_PER_STEP * a.steps}
+                "gpu_launches": (KERNELS_PER_STEP + (tuned["weights"] == "segment")) * a.steps}
         print(json.dumps(line), flush=True)
     inst.close()
     if dist:
@@ -350,7 +355,11 @@ def run_batched(a):
         dist.init_process_group("nccl")
     wls = W.make_batched(rank, a.instances)
     insts = [Instance(w, device=f"cuda:{local}") for w in wls]
+    # tile sizes and weight pass: each instance tuned alone (used by the
+    # per-instance launches), then the batch's brick height and persistent grid
+    choices = [i.autotune(trials=1) for i in insts] if not a.no_tune else [(0, 8)] * len(insts)
     batch = Batch(insts, use_graph=True)
+    batch_choice = batch.autotune(trials=1) if not a.no_tune else (8, 0)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
 
@@ -397,7 +406,10 @@ def run_batched(a):
                            "l2": "flushed between timed steps (256 MiB write)"},
                 "per_instance_launch_steps_per_s": world * n * a.steps / t_plain,
                 "batched_speedup": t_plain / t_batch, "clocks": clk,
-                "gpu_launches": 8 * a.steps}
+                "tuning": {"batch_brick_z": batch_choice[0], "batch_ctas_per_sm": batch_choice[1],
+                           "instance_brick_z": {str(z): sum(1 for c in choices if c[1] == z) for z in (4, 8, 16)},
+                           "instance_segment_weights": sum(1 for c in choices if c[0] == 1)},
+                "gpu_launches": (8 + any(c[0] == 1 for c in choices)) * a.steps}
         print(json.dumps(line), flush=True)
     batch.close()
     for i in insts:

@@ -182,7 +182,23 @@ int al_trace_last(al_grid g, float *ms /* [AL_TRACE_N] */);
 #define AL_OPT_WEIGHTS      1
 #define AL_WEIGHTS_BRICK    0
 #define AL_WEIGHTS_SEGMENT  1
+/* AL_OPT_BRICK_Z: height in cells (4, 8 or 16; default 8) of the 16 x 16 x h
+ * bricks the projection tiles the grid into (the bins of the line masks and
+ * the shared-memory tiles of both brick passes). */
+#define AL_OPT_BRICK_Z      2
+/* AL_OPT_SPREAD_CTAS (batches only, al_batch_set_option): persistent CTAs per
+ * SM of the batched brick passes, 0 = as many as fit. */
+#define AL_OPT_SPREAD_CTAS  3
 int al_set_option(al_grid g, int option, int value);
+
+/* Autotuner: runs the caller's step (same in/out as al_sample_drag_spread)
+ * under every combination of AL_OPT_WEIGHTS and AL_OPT_BRICK_Z, `trials`
+ * timed steps each after one warm-up, timed with CUDA events on `stream`, and
+ * keeps the fastest.  The relaxation state and the status counters are
+ * restored afterwards; S, F and totals hold the last trial's outputs.
+ * *choice (optional) = 100 * weights mode + brick height.  Synchronises the
+ * stream; allocates a temporary copy of the relaxation state. */
+int al_autotune(al_grid g, const al_step_in *in, const al_step_out *out, int trials, void *stream, int *choice);
 
 /* Sizes of an instance: cells and points. */
 int al_sizes(al_grid g, long long *n_cells, long long *n_points, int *n_lines);
@@ -223,6 +239,19 @@ int al_batch_run_subset(al_batch b, const int *idx, int n_idx, void *stream);
  * stream see it.  The previous binding must not have steps in flight. */
 int al_batch_assign(al_batch b, int slot, al_grid g, const al_step_in *in, const al_step_out *out, void *stream);
 int al_batch_destroy(al_batch b);
+
+/* Batch execution options after commit: AL_OPT_BRICK_Z (the brick height of
+ * every instance inside the batch; each instance keeps its own for
+ * al_sample_drag_spread) and AL_OPT_SPREAD_CTAS.  Rebuilds the device work
+ * lists (synchronises the device) and drops a captured graph. */
+int al_batch_set_option(al_batch b, int option, int value);
+
+/* Batch autotuner: times al_batch_run under every brick height and
+ * persistent grid size (`trials` runs each after a warm-up) and keeps the
+ * fastest; every instance's relaxation state and status counters are
+ * restored.  *choice (optional) = 10 * brick height + CTAs per SM (0 = as
+ * many as fit).  Every slot must be bound. */
+int al_batch_autotune(al_batch b, int trials, void *stream, int *choice);
 
 /* ---- line forces without device allocation ----------------------------- */
 /* The paper has no counterpart of this entry point: it exists for callers

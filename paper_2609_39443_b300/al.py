@@ -22,7 +22,7 @@ AL_STATUS_N = 16
 (ST_PA_OUTSIDE, ST_PS_OUTSIDE, ST_FALLBACK, ST_FALLBACK_ZERO, ST_ZERO_WEIGHT, ST_DEPOSIT_LOST,
  ST_REFINED, ST_IRREGULAR, ST_SUPPORT) = range(9)
 
-OPT_WEIGHTS = 1
+OPT_WEIGHTS, OPT_BRICK_Z, OPT_SPREAD_CTAS = 1, 2, 3
 WEIGHTS_BRICK, WEIGHTS_SEGMENT = 0, 1
 
 TRACE_N = 6
@@ -87,6 +87,9 @@ def lib():
                                              C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_int), _vp]
         L.al_trace_enable.argtypes = [_vp, C.c_int]
         L.al_set_option.argtypes = [_vp, C.c_int, C.c_int]
+        L.al_autotune.argtypes = [_vp, C.POINTER(StepIn), C.POINTER(StepOut), C.c_int, _vp, C.POINTER(C.c_int)]
+        L.al_batch_set_option.argtypes = [_vp, C.c_int, C.c_int]
+        L.al_batch_autotune.argtypes = [_vp, C.c_int, _vp, C.POINTER(C.c_int)]
         L.al_trace_last.argtypes = [_vp, C.POINTER(C.c_float)]
         L.al_error_string.restype = C.c_char_p
         L.al_error_string.argtypes = [C.c_int]
@@ -270,6 +273,14 @@ class Instance:
         if P_spread is not None:
             self.P_spread.copy_(torch.as_tensor(np.ascontiguousarray(P_spread), dtype=self.dtype))
 
+    def autotune(self, trials: int = 3, stream=None):
+        """al_autotune on this instance's step; returns (weights mode, brick height)."""
+        sin, sout = self.descriptors()
+        ch = C.c_int(0)
+        check(lib().al_autotune(self.grid.h, C.byref(sin), C.byref(sout), int(trials), _stream_ptr(stream),
+                                C.byref(ch)), "al_autotune")
+        return ch.value // 100, ch.value % 100
+
     def descriptors(self):
         return step_descriptors(self.U, self.P, self.Pdot, self.S, self.F, alpha=self.alpha,
                                 P_spread=self.P_spread,
@@ -302,6 +313,15 @@ class Batch:
 
     def run(self, stream=None):
         check(lib().al_batch_run(self.h, _stream_ptr(stream)), "al_batch_run")
+
+    def set_option(self, option: int, value: int) -> None:
+        check(lib().al_batch_set_option(self.h, int(option), int(value)), "al_batch_set_option")
+
+    def autotune(self, trials: int = 2, stream=None):
+        """al_batch_autotune; returns (brick height, CTAs per SM (0 = as many as fit))."""
+        ch = C.c_int(0)
+        check(lib().al_batch_autotune(self.h, int(trials), _stream_ptr(stream), C.byref(ch)), "al_batch_autotune")
+        return ch.value // 10, ch.value % 10
 
     def run_subset(self, idx, stream=None):
         arr = (C.c_int * len(idx))(*[int(i) for i in idx])

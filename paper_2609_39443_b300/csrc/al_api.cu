@@ -36,6 +36,13 @@ cudaError_t dalloc(P **p, size_t n) {
     return cudaMalloc((void **)p, n * sizeof(P));
 }
 
+// brick decomposition of the projection for brick height bz
+void set_brick_z(al::GridC &c, int bz) {
+    c.bz = bz;
+    c.nbz = (c.nz + bz - 1) / bz;
+    c.nbrick = (long long)c.nbx * c.nby * c.nbz;
+}
+
 void split_ff(double v, float &hi, float &lo) {
     hi = (float)v;
     lo = (float)(v - (double)hi);
@@ -48,6 +55,7 @@ struct al_grid_s {
     int device = 0;
     al::GridC gc{};
     size_t esize = 4;                 // bytes per field element
+    long long nbrick_max = 0;         // bricks at the lowest brick height (sizes the masks)
 
     // lines
     bool loaded = false;
@@ -138,8 +146,9 @@ extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
     c.ncell = ncell;
     c.nbx = (d.nx + al::BX - 1) / al::BX;
     c.nby = (d.ny + al::BY - 1) / al::BY;
-    c.nbz = (d.nz + al::BZ - 1) / al::BZ;
-    c.nbrick = (long long)c.nbx * c.nby * c.nbz;
+    set_brick_z(c, al::BZ_MIN);
+    g->nbrick_max = c.nbrick;
+    set_brick_z(c, 8);
     c.h = d.dx;
     c.V = d.dx * d.dx * d.dx;
     for (int a = 0; a < 3; ++a) {
@@ -151,7 +160,7 @@ extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
     c.rho1 = d.rho1; c.rho2 = d.rho2; c.rho_const = d.rho_const;
 
     cudaError_t e;
-    if ((e = dalloc(&g->brickSum, 3 * (size_t)c.nbrick)) != cudaSuccess ||
+    if ((e = dalloc(&g->brickSum, 3 * (size_t)g->nbrick_max)) != cudaSuccess ||
         (e = dalloc(&g->statusInt, AL_STATUS_N)) != cudaSuccess || (e = dalloc(&g->totalsInt, 6)) != cudaSuccess ||
         (e = dalloc(&g->hasPrev, 1)) != cudaSuccess) {
         int rc = cuda_fail(e, "cudaMalloc");
@@ -214,7 +223,7 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     A(&g->segWa, (size_t)np); A(&g->segWb, (size_t)np);
     A(&g->wfix, (size_t)np); A(&g->w, (size_t)np); A(&g->lineF, 3 * nl);
     A(&g->lines, nl);
-    A(&g->mask, (size_t)g->gc.nbrick * g->mask_words);
+    A(&g->mask, (size_t)g->nbrick_max * g->mask_words);
     if (e != cudaSuccess) {
         int rc = cuda_fail(e, "cudaMalloc");
         free_beams(g);
@@ -241,36 +250,52 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
         AL_CUDA(cudaMemcpy(g->d_ell, b.ell_s, nl * sizeof(double), cudaMemcpyHostToDevice));
         AL_CUDA(cudaMemcpy(g->d_af, b.alpha_f, nl * sizeof(double), cudaMemcpyHostToDevice));
     }
-    AL_CUDA(cudaMemset(g->mask, 0, ((size_t)g->gc.nbrick * g->mask_words ? (size_t)g->gc.nbrick * g->mask_words : 1) * sizeof(uint32_t)));
+    AL_CUDA(cudaMemset(g->mask, 0, ((size_t)g->nbrick_max * g->mask_words ? (size_t)g->nbrick_max * g->mask_words : 1) * sizeof(uint32_t)));
     AL_CUDA(cudaMemset(g->hasPrev, 0, sizeof(int)));
     g->loaded = true;
     return AL_OK;
 }
 
-// The projection kernels use more than 48 KB of dynamic shared memory.
+// The projection kernels use more than 48 KB of dynamic shared memory, and
+// prefer shared memory over L1 so that several bricks share an SM.
+template <typename T, int BZ>
+static cudaError_t brick_attrs() {
+    const int bytes = (int)sizeof(al::SpreadSmem<T, BZ>);
+    const void *fns[4] = {(const void *)al::k_spread<T, BZ>, (const void *)al::kb_spread<T, BZ>,
+                          (const void *)al::k_bweights<T, BZ>, (const void *)al::kb_bweights<T, BZ>};
+    for (const void *f : fns) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 template <typename T>
 static cudaError_t spread_smem_attr() {
     static cudaError_t done = cudaErrorNotReady;
     if (done != cudaSuccess) {
-        const int bytes = (int)sizeof(al::SpreadSmem<T>);
-        done = cudaFuncSetAttribute(al::k_spread<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(al::kb_spread<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(al::k_bweights<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(al::kb_bweights<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        // prefer shared memory over L1 so that several bricks share an SM
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(al::k_spread<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(al::kb_spread<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(al::k_bweights<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(al::kb_bweights<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        done = brick_attrs<T, 4>();
+        if (done == cudaSuccess) done = brick_attrs<T, 8>();
+        if (done == cudaSuccess) done = brick_attrs<T, 16>();
     }
     return done;
+}
+
+// the two brick passes of one instance at brick height BZ
+template <typename T, int BZ>
+static void launch_bricks(const al::Inst<T> &I, bool weights, cudaStream_t st) {
+    using namespace al;
+    const size_t smem = sizeof(SpreadSmem<T, BZ>);
+    if (weights) k_bweights<T, BZ><<<(unsigned)I.g.nbrick, SPREAD_THREADS, smem, st>>>(I.g, I.b, I.sc, I.p, I.status);
+    else k_spread<T, BZ><<<(unsigned)I.g.nbrick, SPREAD_THREADS, smem, st>>>(I.g, I.b, I.sc, I.p, I.status);
+}
+template <typename T>
+static void launch_bricks_bz(const al::Inst<T> &I, bool weights, cudaStream_t st) {
+    switch (I.g.bz) {
+    case 4: launch_bricks<T, 4>(I, weights, st); break;
+    case 16: launch_bricks<T, 16>(I, weights, st); break;
+    default: launch_bricks<T, 8>(I, weights, st); break;
+    }
 }
 
 template <typename T>
@@ -332,16 +357,15 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
     trace_mark(g, 1, st);
     if (np > 0) k_mask<T><<<nb, 256, 0, st>>>(gc, bc, sc);
     trace_mark(g, 2, st);
-    const size_t smem = sizeof(SpreadSmem<T>);
     if (np > 0) {
         if (gc.wmode != 0)
             k_weights<T><<<(unsigned)(((long long)np * 32 + 127) / 128), 128, 0, st>>>(gc, bc, sc, p, status);
-        k_bweights<T><<<(unsigned)gc.nbrick, SPREAD_THREADS, smem, st>>>(gc, bc, sc, p, status);
+        launch_bricks_bz<T>(I, true, st);
     }
     trace_mark(g, 3, st);
     if (np > 0) k_normalise<T><<<nb, 256, 0, st>>>(gc, bc, sc, p, status);
     trace_mark(g, 4, st);
-    k_spread<T><<<(unsigned)gc.nbrick, SPREAD_THREADS, smem, st>>>(gc, bc, sc, p, status);
+    launch_bricks_bz<T>(I, false, st);
     trace_mark(g, 5, st);
     k_totals<T><<<1, 256, 0, st>>>(gc, bc, sc, I.totals);
     trace_mark(g, 6, st);
@@ -373,6 +397,10 @@ extern "C" int al_set_option(al_grid g, int option, int value) {
     case AL_OPT_WEIGHTS:
         if (value != AL_WEIGHTS_BRICK && value != AL_WEIGHTS_SEGMENT) return AL_ERR_ARG;
         g->gc.wmode = value;
+        return AL_OK;
+    case AL_OPT_BRICK_Z:
+        if (value != 4 && value != 8 && value != 16) return AL_ERR_ARG;
+        set_brick_z(g->gc, value);
         return AL_OK;
     default:
         return AL_ERR_ARG;
@@ -467,6 +495,9 @@ struct al_batch_s {
     long long *d_pre = nullptr;               // 4 prefix arrays of n + 1: points, lines, bricks, points(warps)
     long long tot_pts = 0, tot_lines = 0, tot_bricks = 0;
     int spread_grid = 0, pt_grid = 0;
+    int bz = 8;                               // brick height of the batch's projection
+    int ctas = 0;                             // persistent CTAs per SM (0: as many as fit)
+    int occ = 1;                              // CTAs per SM that fit at this brick height
     bool any_segment_weights = false;         // some instance sums weights per segment
     // subset runs: a ring of pinned host / device work lists
     static constexpr int RING = 8;
@@ -511,57 +542,77 @@ extern "C" int al_batch_add(al_batch b, al_grid g, const al_step_in *in, const a
     return AL_OK;
 }
 
+// (Re)build the device instance table and work-list prefixes for the
+// batch's brick height and persistent grid size; a captured graph is dropped
+// (it is captured again at the next run).
 template <typename T>
-static int batch_commit_t(al_batch b, int spread_ctas_per_sm) {
+static int batch_rebuild_t(al_batch b) {
+    using namespace al;
+    AL_CUDA(cudaDeviceSynchronize());                    // no step or slot update in flight
+    const int n = b->n;
+    Inst<T> *h = (Inst<T> *)b->h_inst;
+    std::vector<long long> pre(4 * (size_t)(n + 1), 0);
+    b->any_segment_weights = false;
+    b->cnt_pts.assign(n, 0); b->cnt_lines.assign(n, 0); b->cnt_bricks.assign(n, 0);
+    for (int q = 0; q < n; ++q) {
+        const bool used = b->grids[q] != nullptr;
+        if (used) {
+            h[q] = make_inst<T>(b->grids[q], &b->ins[q], &b->outs[q]);
+            set_brick_z(h[q].g, b->bz);
+            if (h[q].g.wmode != 0) b->any_segment_weights = true;
+            b->cnt_pts[q] = b->grids[q]->n_points;
+            b->cnt_lines[q] = b->grids[q]->n_lines;
+            b->cnt_bricks[q] = h[q].g.nbrick;
+        } else {
+            memset((void *)&h[q], 0, sizeof(Inst<T>));
+        }
+        pre[0 * (n + 1) + q + 1] = pre[0 * (n + 1) + q] + b->cnt_pts[q];
+        pre[1 * (n + 1) + q + 1] = pre[1 * (n + 1) + q] + b->cnt_lines[q];
+        pre[2 * (n + 1) + q + 1] = pre[2 * (n + 1) + q] + b->cnt_bricks[q];
+    }
+    b->tot_pts = pre[n];
+    b->tot_lines = pre[(n + 1) + n];
+    b->tot_bricks = pre[2 * (n + 1) + n];
+    AL_CUDA(cudaMemcpy(b->d_inst, h, sizeof(Inst<T>) * n, cudaMemcpyHostToDevice));
+    AL_CUDA(cudaMemcpy(b->d_pre, pre.data(), sizeof(long long) * pre.size(), cudaMemcpyHostToDevice));
+    AL_CUDA(spread_smem_attr<T>());
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    switch (b->bz) {
+    case 4: AL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_spread<T, 4>, SPREAD_THREADS, sizeof(SpreadSmem<T, 4>))); break;
+    case 16: AL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_spread<T, 16>, SPREAD_THREADS, sizeof(SpreadSmem<T, 16>))); break;
+    default: AL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_spread<T, 8>, SPREAD_THREADS, sizeof(SpreadSmem<T, 8>))); break;
+    }
+    if (occ < 1) occ = 1;
+    b->occ = occ;
+    const int per = b->ctas > 0 ? std::min(b->ctas, occ) : occ;
+    b->spread_grid = (int)std::min<long long>((long long)nsm * per, std::max<long long>(b->tot_bricks, 1));
+    b->pt_grid = nsm * 8;
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    return AL_OK;
+}
+
+template <typename T>
+static int batch_commit_t(al_batch b) {
     using namespace al;
     const int added = (int)b->grids.size();
     const int n = std::max(added, b->capacity);
     b->grids.resize(n, nullptr);
     b->ins.resize(n, al_step_in{});
     b->outs.resize(n, al_step_out{});
-    std::vector<Inst<T>> h(n);
-    std::vector<long long> pre(4 * (size_t)(n + 1), 0);
-    for (int q = 0; q < n; ++q) {
-        const bool used = b->grids[q] != nullptr;
-        if (used) h[q] = make_inst<T>(b->grids[q], &b->ins[q], &b->outs[q]);
-        else memset((void *)&h[q], 0, sizeof(Inst<T>));
-        if (used && b->grids[q]->gc.wmode != 0) b->any_segment_weights = true;
-        pre[0 * (n + 1) + q + 1] = pre[0 * (n + 1) + q] + (used ? b->grids[q]->n_points : 0);
-        pre[1 * (n + 1) + q + 1] = pre[1 * (n + 1) + q] + (used ? b->grids[q]->n_lines : 0);
-        pre[2 * (n + 1) + q + 1] = pre[2 * (n + 1) + q] + (used ? b->grids[q]->gc.nbrick : 0);
-    }
-    AL_CUDA(cudaMallocHost(&b->h_inst, sizeof(Inst<T>) * n));
+    AL_CUDA(cudaMallocHost(&b->h_inst, sizeof(Inst<T>) * (n ? n : 1)));
     b->slot_ev.assign(n, nullptr);
     for (int q = 0; q < n; ++q) AL_CUDA(cudaEventCreateWithFlags(&b->slot_ev[q], cudaEventDisableTiming));
-    b->tot_pts = pre[n];
-    b->tot_lines = pre[(n + 1) + n];
-    b->tot_bricks = pre[2 * (n + 1) + n];
-    b->cnt_pts.resize(n); b->cnt_lines.resize(n); b->cnt_bricks.resize(n);
-    for (int q = 0; q < n; ++q) {
-        const bool used = b->grids[q] != nullptr;
-        b->cnt_pts[q] = used ? b->grids[q]->n_points : 0;
-        b->cnt_lines[q] = used ? b->grids[q]->n_lines : 0;
-        b->cnt_bricks[q] = used ? b->grids[q]->gc.nbrick : 0;
-    }
     b->maxn = n;
     const size_t slot = al_batch_s::slot_bytes(n);
     AL_CUDA(cudaMallocHost(&b->h_ring, slot * al_batch_s::RING));
     AL_CUDA(cudaMalloc(&b->d_ring, slot * al_batch_s::RING));
     for (int r = 0; r < al_batch_s::RING; ++r) AL_CUDA(cudaEventCreateWithFlags(&b->ring_ev[r], cudaEventDisableTiming));
     AL_CUDA(cudaMalloc(&b->d_inst, sizeof(Inst<T>) * (n ? n : 1)));
-    AL_CUDA(cudaMalloc(&b->d_pre, sizeof(long long) * pre.size()));
-    AL_CUDA(cudaMemcpy(b->d_inst, h.data(), sizeof(Inst<T>) * n, cudaMemcpyHostToDevice));
-    AL_CUDA(cudaMemcpy(b->d_pre, pre.data(), sizeof(long long) * pre.size(), cudaMemcpyHostToDevice));
-    AL_CUDA(spread_smem_attr<T>());
-    int dev = 0, nsm = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    AL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_spread<T>, SPREAD_THREADS, sizeof(SpreadSmem<T>)));
-    if (occ < 1) occ = 1;
-    const int per = spread_ctas_per_sm > 0 ? (spread_ctas_per_sm < occ ? spread_ctas_per_sm : occ) : occ;
-    b->spread_grid = (int)std::min<long long>((long long)nsm * per, std::max<long long>(b->tot_bricks, 1));
-    b->pt_grid = nsm * 8;
-    return AL_OK;
+    AL_CUDA(cudaMalloc(&b->d_pre, sizeof(long long) * 4 * (size_t)(n + 1)));
+    return batch_rebuild_t<T>(b);
 }
 
 // enqueue one step of n selected instances (sel NULL: all); pre: device
@@ -586,13 +637,21 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
         if (b->any_segment_weights) kb_weights<T><<<grid_for(tot_pts, 4), 128, 0, st>>>(I, sel, pp, n);
         if (tot_bricks > 0) {
             const int gs = (int)std::min<long long>(b->spread_grid, tot_bricks);
-            kb_bweights<T><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T>), st>>>(I, sel, pb, n);
+            switch (b->bz) {
+            case 4: kb_bweights<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4>), st>>>(I, sel, pb, n); break;
+            case 16: kb_bweights<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16>), st>>>(I, sel, pb, n); break;
+            default: kb_bweights<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8>), st>>>(I, sel, pb, n); break;
+            }
         }
         kb_normalise<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
     }
     if (tot_bricks > 0) {
         const int gs = (int)std::min<long long>(b->spread_grid, tot_bricks);
-        kb_spread<T><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T>), st>>>(I, sel, pb, n);
+        switch (b->bz) {
+        case 4: kb_spread<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4>), st>>>(I, sel, pb, n); break;
+        case 16: kb_spread<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16>), st>>>(I, sel, pb, n); break;
+        default: kb_spread<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8>), st>>>(I, sel, pb, n); break;
+        }
     }
     kb_totals<T><<<std::max(1, std::min(n, 1024)), 256, 0, st>>>(I, sel, n);
     AL_CUDA(cudaGetLastError());
@@ -614,8 +673,12 @@ static int batch_assign_t(al_batch b, int slot, al_grid g, const al_step_in *in,
     using namespace al;
     AL_CUDA(cudaEventSynchronize(b->slot_ev[slot]));       // staging of this slot is free again
     Inst<T> *h = (Inst<T> *)b->h_inst + slot;
-    if (g) *h = make_inst<T>(g, in, out);
-    else memset((void *)h, 0, sizeof(Inst<T>));
+    if (g) {
+        *h = make_inst<T>(g, in, out);
+        set_brick_z(h->g, b->bz);
+    } else {
+        memset((void *)h, 0, sizeof(Inst<T>));
+    }
     AL_CUDA(cudaMemcpyAsync((Inst<T> *)b->d_inst + slot, h, sizeof(Inst<T>), cudaMemcpyHostToDevice, st));
     AL_CUDA(cudaEventRecord(b->slot_ev[slot], st));
     b->grids[slot] = g;
@@ -623,7 +686,7 @@ static int batch_assign_t(al_batch b, int slot, al_grid g, const al_step_in *in,
     if (g && g->gc.wmode != 0) b->any_segment_weights = true;
     b->cnt_pts[slot] = g ? g->n_points : 0;
     b->cnt_lines[slot] = g ? g->n_lines : 0;
-    b->cnt_bricks[slot] = g ? g->gc.nbrick : 0;
+    b->cnt_bricks[slot] = g ? h->g.nbrick : 0;
     return AL_OK;
 }
 
@@ -654,8 +717,9 @@ extern "C" int al_batch_commit(al_batch b, int use_graph, int spread_ctas_per_sm
     if (b->grids.empty() && b->capacity == 0) return AL_ERR_ARG;
     if (b->precision < 0) return AL_ERR_ARG;
     b->n = std::max((int)b->grids.size(), b->capacity);
-    int rc = b->precision == AL_FP64 ? batch_commit_t<double>(b, spread_ctas_per_sm)
-                                     : batch_commit_t<float>(b, spread_ctas_per_sm);
+    if (spread_ctas_per_sm < 0) return AL_ERR_ARG;
+    b->ctas = spread_ctas_per_sm;
+    int rc = b->precision == AL_FP64 ? batch_commit_t<double>(b) : batch_commit_t<float>(b);
     if (rc != AL_OK) return rc;
     b->use_graph = use_graph != 0;
     b->committed = true;
@@ -675,7 +739,7 @@ extern "C" int al_batch_run(al_batch b, void *stream) {
     };
     if (!b->use_graph) return enqueue(st);
     if (!b->exec) {
-        AL_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+        if (!b->cap) AL_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
         AL_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
         int rc = enqueue(b->cap);
         cudaGraph_t graph = nullptr;
@@ -743,4 +807,147 @@ extern "C" int al_batch_destroy(al_batch b) {
     if (b->d_pre) cudaFree(b->d_pre);
     delete b;
     return AL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuning: time every execution choice on the caller's own step and keep
+// the fastest.  The relaxation state and the status counters are restored,
+// so tuning leaves the instance as it found it (S, F and totals hold the
+// last trial's outputs).
+// ---------------------------------------------------------------------------
+namespace {
+struct saved_state {
+    void *fprev = nullptr;
+    int has_prev = 0;
+    int status[AL_STATUS_N] = {};
+};
+int save_state(al_grid g, const al_step_out *out, saved_state &sv, cudaStream_t st) {
+    if (g->n_points > 0) AL_CUDA(cudaMalloc(&sv.fprev, 3 * (size_t)g->n_points * g->esize));
+    int rc = al_get_state(g, sv.fprev, &sv.has_prev, st);
+    if (rc != AL_OK) return rc;
+    if (out && out->status)
+        AL_CUDA(cudaMemcpyAsync(sv.status, out->status, sizeof(sv.status), cudaMemcpyDeviceToHost, st));
+    AL_CUDA(cudaStreamSynchronize(st));
+    return AL_OK;
+}
+int restore_state(al_grid g, const al_step_out *out, const saved_state &sv, cudaStream_t st) {
+    int rc = al_set_state(g, sv.fprev, sv.has_prev, st);
+    if (rc != AL_OK) return rc;
+    if (out && out->status)
+        AL_CUDA(cudaMemcpyAsync(out->status, sv.status, sizeof(sv.status), cudaMemcpyHostToDevice, st));
+    AL_CUDA(cudaStreamSynchronize(st));
+    return AL_OK;
+}
+struct event_pair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~event_pair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+}  // namespace
+
+extern "C" int al_autotune(al_grid g, const al_step_in *in, const al_step_out *out, int trials, void *stream,
+                           int *choice) {
+    if (!g || !in || !out || trials < 1 || trials > 1000) return AL_ERR_ARG;
+    if (!g->loaded) return AL_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    saved_state sv;
+    int rc = save_state(g, out, sv, st);
+    event_pair ev;
+    if (rc == AL_OK && (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess))
+        rc = AL_ERR_CUDA;
+    const int wms[2] = {AL_WEIGHTS_BRICK, AL_WEIGHTS_SEGMENT}, bzs[3] = {4, 8, 16};
+    float best = INFINITY;
+    int best_w = g->gc.wmode, best_z = g->gc.bz;
+    for (int wi = 0; wi < 2 && rc == AL_OK; ++wi)
+        for (int zi = 0; zi < 3 && rc == AL_OK; ++zi) {
+            g->gc.wmode = wms[wi];
+            set_brick_z(g->gc, bzs[zi]);
+            if ((rc = restore_state(g, out, sv, st)) != AL_OK) break;
+            if ((rc = al_sample_drag_spread(g, in, out, stream)) != AL_OK) break;       // warm-up
+            if (cudaEventRecord(ev.a, st) != cudaSuccess) { rc = AL_ERR_CUDA; break; }
+            for (int t = 0; t < trials && rc == AL_OK; ++t) rc = al_sample_drag_spread(g, in, out, stream);
+            if (rc != AL_OK) break;
+            if (cudaEventRecord(ev.b, st) != cudaSuccess || cudaEventSynchronize(ev.b) != cudaSuccess) {
+                rc = AL_ERR_CUDA;
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, ev.a, ev.b);
+            if (ms < best) { best = ms; best_w = wms[wi]; best_z = bzs[zi]; }
+        }
+    g->gc.wmode = best_w;
+    set_brick_z(g->gc, best_z);
+    const int rc2 = restore_state(g, out, sv, st);
+    if (sv.fprev) cudaFree(sv.fprev);
+    if (rc == AL_OK) rc = rc2;
+    if (rc == AL_OK && choice) *choice = 100 * best_w + best_z;
+    return rc;
+}
+
+extern "C" int al_batch_set_option(al_batch b, int option, int value) {
+    if (!b) return AL_ERR_ARG;
+    if (!b->committed) return AL_ERR_STATE;
+    switch (option) {
+    case AL_OPT_BRICK_Z:
+        if (value != 4 && value != 8 && value != 16) return AL_ERR_ARG;
+        b->bz = value;
+        break;
+    case AL_OPT_SPREAD_CTAS:
+        if (value < 0 || value > 32) return AL_ERR_ARG;
+        b->ctas = value;
+        break;
+    default:
+        return AL_ERR_ARG;
+    }
+    return b->precision == AL_FP64 ? batch_rebuild_t<double>(b) : batch_rebuild_t<float>(b);
+}
+
+extern "C" int al_batch_autotune(al_batch b, int trials, void *stream, int *choice) {
+    if (!b || trials < 1 || trials > 1000) return AL_ERR_ARG;
+    if (!b->committed) return AL_ERR_STATE;
+    for (int q = 0; q < b->n; ++q)
+        if (!b->grids[q]) return AL_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<saved_state> sv(b->n);
+    int rc = AL_OK;
+    for (int q = 0; q < b->n && rc == AL_OK; ++q) rc = save_state(b->grids[q], &b->outs[q], sv[q], st);
+    event_pair ev;
+    if (rc == AL_OK && (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess))
+        rc = AL_ERR_CUDA;
+    const int bzs[3] = {4, 8, 16}, ctas[2] = {0, 1};
+    float best = INFINITY;
+    int best_z = b->bz, best_c = b->ctas;
+    for (int zi = 0; zi < 3 && rc == AL_OK; ++zi)
+        for (int ci = 0; ci < 2 && rc == AL_OK; ++ci) {
+            b->bz = bzs[zi];
+            b->ctas = ctas[ci];
+            rc = b->precision == AL_FP64 ? batch_rebuild_t<double>(b) : batch_rebuild_t<float>(b);
+            if (rc != AL_OK) break;
+            if (ctas[ci] == 1 && b->occ == 1) continue;       // the same launch as "as many as fit"
+            for (int q = 0; q < b->n && rc == AL_OK; ++q) rc = restore_state(b->grids[q], &b->outs[q], sv[q], st);
+            if (rc != AL_OK || (rc = al_batch_run(b, stream)) != AL_OK) break;        // warm-up (and capture)
+            if (cudaEventRecord(ev.a, st) != cudaSuccess) { rc = AL_ERR_CUDA; break; }
+            for (int t = 0; t < trials && rc == AL_OK; ++t) rc = al_batch_run(b, stream);
+            if (rc != AL_OK) break;
+            if (cudaEventRecord(ev.b, st) != cudaSuccess || cudaEventSynchronize(ev.b) != cudaSuccess) {
+                rc = AL_ERR_CUDA;
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, ev.a, ev.b);
+            if (ms < best) { best = ms; best_z = bzs[zi]; best_c = ctas[ci]; }
+        }
+    b->bz = best_z;
+    b->ctas = best_c;
+    int rc2 = b->precision == AL_FP64 ? batch_rebuild_t<double>(b) : batch_rebuild_t<float>(b);
+    for (int q = 0; q < b->n; ++q) {
+        const int r = restore_state(b->grids[q], &b->outs[q], sv[q], st);
+        if (rc2 == AL_OK) rc2 = r;
+        if (sv[q].fprev) cudaFree(sv[q].fprev);
+    }
+    if (rc == AL_OK) rc = rc2;
+    if (rc == AL_OK && choice) *choice = 10 * best_z + best_c;
+    return rc;
 }

@@ -34,9 +34,10 @@
 
 namespace al {
 
-constexpr int BX = 16, BY = 16, BZ = 8;          // spread brick (cells)
+constexpr int BX = 16, BY = 16;                  // projection brick footprint (cells)
+constexpr int BZ_MIN = 4, BZ_MAX = 16;           // brick heights the kernels are built for
 constexpr int SPREAD_THREADS = BX * BY;          // one thread per column
-constexpr float BRICK_DIAG = 24.0f;              // tsqrt(16^2+16^2+8^2)
+constexpr float BRICK_DIAG = 27.72f;             // diagonal of the tallest brick, 16 x 16 x 16
 constexpr double PI_D = 3.14159265358979323846;
 
 enum { ST_PA_OUTSIDE = 0, ST_PS_OUTSIDE = 1, ST_FALLBACK = 2, ST_FALLBACK_ZERO = 3,
@@ -53,6 +54,7 @@ struct GridC {
     int has_alpha;
     double rho1, rho2, rho_const;
     int wmode;                   // 0: all weights from the brick pass; 1: segment pass for certified lines
+    int bz;                      // brick height of the projection (4, 8 or 16 cells)
 };
 
 struct BeamsC {
@@ -692,7 +694,7 @@ __device__ void d_mask(const GridC &g, const BeamsC &b, const Scratch<T> &sc, co
     seg_box(sc, np, k, kb, sc.lines[l].Rc, lo, hi);
     // cells whose centre c + 0.5 lies in [lo, hi]
     int c0[3], c1[3];
-    const int nn[3] = {g.nx, g.ny, g.nz}, bs[3] = {BX, BY, BZ}, nb[3] = {g.nbx, g.nby, g.nbz};
+    const int nn[3] = {g.nx, g.ny, g.nz}, bs[3] = {BX, BY, g.bz}, nb[3] = {g.nbx, g.nby, g.nbz};
     for (int a = 0; a < 3; ++a) {
         float fl = ceilf(lo[a] - 0.5f), fh = floorf(hi[a] - 0.5f);
         fl = fmaxf(fl, 0.0f);
@@ -1035,7 +1037,7 @@ template <typename T> struct SpreadCap;
 template <> struct SpreadCap<float> { static constexpr int NODES = 640, LIST = 512, ENT = 32; };
 template <> struct SpreadCap<double> { static constexpr int NODES = 320, LIST = 512, ENT = 32; };
 
-template <typename T>
+template <typename T, int BZ>
 struct SpreadSmem {
     static constexpr int NN = SpreadCap<T>::NODES, LIST = SpreadCap<T>::LIST, ENT = SpreadCap<T>::ENT;
     T P[3][NN];                  // node positions relative to the brick origin
@@ -1126,8 +1128,8 @@ __device__ __noinline__ int nl_exhaustive(const GridC &g, const Scratch<T> &sc, 
 // argmin.
 static __device__ __noinline__ int ff_later_closer(const float *uhi, const float *ulo, long long np, int k, int B0,
                                                    int B1, int B2, float cx, float cy, float cz);
-template <typename T>
-__device__ __noinline__ int nl_exhaustive_staged(const SpreadSmem<T> &sm, const GridC &g, const StepPtrs<T> &p,
+template <typename T, int BZ>
+__device__ __noinline__ int nl_exhaustive_staged(const SpreadSmem<T, BZ> &sm, const GridC &g, const StepPtrs<T> &p,
                                                  const Scratch<T> &sc, int base, int first, int n, int jlo, int jhi,
                                                  T c0, T c1, T c2, int B0, int B1, int B2, int ci, int cj, int ck,
                                                  int *status) {
@@ -1237,8 +1239,8 @@ static __device__ __noinline__ int ff_later_closer(const float *uhi, const float
     return dh > 0.0f ? 1 : 0;
 }
 
-template <typename T>
-__device__ __forceinline__ bool sig_pos(const SpreadSmem<T> &sm, int s, const T C[3], const GridC &g,
+template <typename T, int BZ>
+__device__ __forceinline__ bool sig_pos(const SpreadSmem<T, BZ> &sm, int s, const T C[3], const GridC &g,
                                         const StepPtrs<T> &p, const Scratch<T> &sc, int kglob, int B0, int B1,
                                         int B2, int ci, int cj, int ck, int *status) {
     const T x0 = C[0] - sm.P[0][s], x1 = C[1] - sm.P[1][s], x2 = C[2] - sm.P[2][s];
@@ -1253,14 +1255,14 @@ __device__ __forceinline__ bool sig_pos(const SpreadSmem<T> &sm, int s, const T 
     }
     return nl_later_closer(g, p, kglob, ci, cj, ck, status);
 }
-template <typename T>
-__device__ __forceinline__ T node_d2(const SpreadSmem<T> &sm, int s, const T C[3]) {
+template <typename T, int BZ>
+__device__ __forceinline__ T node_d2(const SpreadSmem<T, BZ> &sm, int s, const T C[3]) {
     const T x0 = C[0] - sm.P[0][s], x1 = C[1] - sm.P[1][s], x2 = C[2] - sm.P[2][s];
     return x0 * x0 + x1 * x1 + x2 * x2;
 }
 // clamped foot parameter and squared distance of C to staged segment ss
-template <typename T>
-__device__ __forceinline__ void seg_foot(const SpreadSmem<T> &sm, int ss, const T C[3], T &s, T &r2) {
+template <typename T, int BZ>
+__device__ __forceinline__ void seg_foot(const SpreadSmem<T, BZ> &sm, int ss, const T C[3], T &s, T &r2) {
     const T x0 = C[0] - sm.P[0][ss], x1 = C[1] - sm.P[1][ss], x2 = C[2] - sm.P[2][ss];
     const T d0 = sm.D[0][ss], d1 = sm.D[1][ss], d2 = sm.D[2][ss];
     s = (x0 * d0 + x1 * d1 + x2 * d2) * sm.Il2[ss];
@@ -1274,10 +1276,10 @@ __device__ __forceinline__ void seg_foot(const SpreadSmem<T> &sm, int ss, const 
 // by the thread that owns its column (no atomics), with the deposits of the
 // zero-weight nodes inside the brick.  WP = true: the nodal weights w_k
 // (Sec. 3.2.4), each (cell, line) pair once, added as fixed-point integers.
-template <typename T, bool WP>
+template <typename T, bool WP, int BZ>
 __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
-                        const int br, SpreadSmem<T> &sm) {
-    using SM = SpreadSmem<T>;
+                        const int br, SpreadSmem<T, BZ> &sm) {
+    using SM = SpreadSmem<T, BZ>;
     const long long np = b.n_points;
     const int nbxy = g.nbx * g.nby;
     const int bzi = br / nbxy, rem = br - bzi * nbxy;
@@ -1489,7 +1491,11 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
             // ---- gather: warp w takes layer w; for each line in order its lanes take
             //      the cells of the layer near the line, two rows of 16 at a time, so no
             //      two lanes share a cell and every cell sums its lines in line order ----
-            for (int z = warp; z < nzb; z += SPREAD_THREADS / 32) {
+            // WPL warps share a layer (bricks lower than the warp count), taking
+            // alternate row pairs; taller bricks give each warp several layers
+            constexpr int NW = SPREAD_THREADS / 32, WPL = (BZ < NW) ? NW / BZ : 1;
+            const int zpart = warp % WPL;
+            for (int z = warp / WPL; z < nzb; z += NW / WPL) {
                 const float czf = z + 0.5f;
                 const int gz = B2 + z;
                 for (int e = 0; e < ne; ++e) {
@@ -1518,14 +1524,18 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                     // (slots w0s .. w0s + 3), reduced over the warp once per line and layer
                     unsigned long long wacc0 = 0ull, wacc1 = 0ull, wacc2 = 0ull, wacc3 = 0ull;
                     const int w0s = (base >= 0) ? base + (jcz - jlo) - 1 : 0;
-                    for (int y0 = iy0; y0 <= iy1; y0 += 2) {
+                    // row pairs (2p, 2p + 1) belong to warp p % WPL of the layer, the same
+                    // warp for every line, so a cell is only ever updated by one warp
+                    const int p0 = iy0 >> 1;
+                    const int y0s = (WPL == 1) ? iy0 : 2 * (p0 + (zpart - p0 % WPL + WPL) % WPL);
+                    for (int y0 = y0s; y0 <= iy1; y0 += 2 * WPL) {
                         const int ty = y0 + (lane >> 4);
                         const float cx = tx + 0.5f, cy = ty + 0.5f;
                         const float dx = cx - xc, dy = cy - yc;
                         bool in = false;
                         int js = 0;
                         T s = (T)0, r2 = (T)0;
-                        if (tx <= ix1 && ty <= iy1 && dx * dx + dy * dy <= rh2) {
+                        if (tx <= ix1 && ty >= iy0 && ty <= iy1 && dx * dx + dy * dy <= rh2) {
                             const int gxc = B0 + tx, gyc = B1 + ty;
                             const T C[3] = {(T)cx, (T)cy, (T)czf};
                             if (base < 0) {
@@ -1808,19 +1818,19 @@ __global__ void __launch_bounds__(256) k_normalise(GridC g, BeamsC b, Scratch<T>
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < b.n_points) d_normalise(g, b, sc, p, status, k);
 }
-template <typename T>
+template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) k_spread(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
                                                            int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SpreadSmem<T> &sm = *reinterpret_cast<SpreadSmem<T> *>(smem_raw);
-    d_brick<T, false>(g, b, sc, p, status, (int)blockIdx.x, sm);
+    SpreadSmem<T, BZ> &sm = *reinterpret_cast<SpreadSmem<T, BZ> *>(smem_raw);
+    d_brick<T, false, BZ>(g, b, sc, p, status, (int)blockIdx.x, sm);
 }
-template <typename T>
+template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) k_bweights(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
                                                              int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SpreadSmem<T> &sm = *reinterpret_cast<SpreadSmem<T> *>(smem_raw);
-    d_brick<T, true>(g, b, sc, p, status, (int)blockIdx.x, sm);
+    SpreadSmem<T, BZ> &sm = *reinterpret_cast<SpreadSmem<T, BZ> *>(smem_raw);
+    d_brick<T, true, BZ>(g, b, sc, p, status, (int)blockIdx.x, sm);
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_totals(GridC g, BeamsC b, Scratch<T> sc, double *totals) {
@@ -1894,28 +1904,28 @@ __global__ void __launch_bounds__(256) kb_normalise(const Inst<T> *I, const int 
     }
 }
 // persistent: a fixed grid of CTAs walks the bricks of every instance
-template <typename T>
+template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) kb_spread(const Inst<T> *I, const int *sel, const long long *pre, int n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SpreadSmem<T> &sm = *reinterpret_cast<SpreadSmem<T> *>(smem_raw);
+    SpreadSmem<T, BZ> &sm = *reinterpret_cast<SpreadSmem<T, BZ> *>(smem_raw);
     const long long total = pre[n];
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
         const int q = owner(pre, n, item);
         const Inst<T> &x = I[AL_SEL(q)];
-        d_brick<T, false>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]), sm);
+        d_brick<T, false, BZ>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]), sm);
         __syncthreads();
     }
 }
-template <typename T>
+template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) kb_bweights(const Inst<T> *I, const int *sel, const long long *pre,
                                                               int n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SpreadSmem<T> &sm = *reinterpret_cast<SpreadSmem<T> *>(smem_raw);
+    SpreadSmem<T, BZ> &sm = *reinterpret_cast<SpreadSmem<T, BZ> *>(smem_raw);
     const long long total = pre[n];
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
         const int q = owner(pre, n, item);
         const Inst<T> &x = I[AL_SEL(q)];
-        d_brick<T, true>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]), sm);
+        d_brick<T, true, BZ>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]), sm);
         __syncthreads();
     }
 }

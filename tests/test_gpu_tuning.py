@@ -1,0 +1,113 @@
+"""Execution options and the autotuners.  Every combination of the
+nodal-weight pass and the brick height matches the FP64 oracle; tuning
+restores the relaxation state (the next step equals that of an untouched
+instance set to the chosen options, bit for bit); a batch at any brick
+height and persistent grid size equals its instances alone, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_39443_b300 import workloads as W
+
+from helpers import compare, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _outputs(inst):
+    return (inst.S.cpu().numpy().copy(), inst.F.cpu().numpy().copy(), inst.totals.cpu().numpy().copy(),
+            inst.status.cpu().numpy().copy())
+
+
+@pytest.mark.parametrize("wmode", [0, 1], ids=["brick-weights", "segment-weights"])
+@pytest.mark.parametrize("bz", [4, 8, 16])
+def test_every_option_matches_the_oracle(wmode, bz):
+    from paper_2609_39443_b300.al import Instance, OPT_BRICK_Z, OPT_WEIGHTS
+    cases = [W.make_random(21, 61, 45, 37, n_lines=10, kinds=("stem", "arc", "random", "flat", "point", "dup")),
+             W.random_canopy(22, 64, 40, 48, 0.005, 90, 40, 2.4, name="tune")]
+    for wl in cases:
+        inst = Instance(wl)
+        inst.grid.set_option(OPT_WEIGHTS, wmode)
+        inst.grid.set_option(OPT_BRICK_Z, bz)
+        g = run_gpu(wl, inst=inst)
+        o = oracle.sample_drag_spread(wl)
+        compare(wl, g, o, label=f"{wl.name} w{wmode} bz{bz}", sumF_ref="abs")
+        assert g["status"][8] == oracle.count_support(wl.grid, wl.beams, wl.step.P)
+        inst.close()
+
+
+def test_autotune_restores_state_and_applies_choice():
+    import torch
+    from paper_2609_39443_b300.al import Instance, OPT_BRICK_Z, OPT_WEIGHTS
+    wl = W.random_canopy(23, 80, 48, 40, 0.005, 120, 30, 2.0, name="tuned")
+    a, b = Instance(wl), Instance(wl)
+    a.step()
+    b.step()
+    wmode, bz = a.autotune(trials=1)
+    assert wmode in (0, 1) and bz in (4, 8, 16)
+    b.grid.set_option(OPT_WEIGHTS, wmode)
+    b.grid.set_option(OPT_BRICK_Z, bz)
+    for x in (a, b):
+        x.status.zero_()
+        x.step()
+    torch.cuda.synchronize()
+    for u, v in zip(_outputs(a), _outputs(b)):
+        np.testing.assert_array_equal(u, v)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("bz,ctas", [(4, 1), (16, 0)])
+def test_batch_options_equal_alone(bz, ctas):
+    import torch
+    from paper_2609_39443_b300.al import Batch, Instance, OPT_BRICK_Z, OPT_SPREAD_CTAS
+    wls = W.make_batched(5, 5, max_cells=96 * 64 * 64)
+    alone = [Instance(w) for w in wls]
+    inb = [Instance(w) for w in wls]
+    for a in alone:
+        a.grid.set_option(OPT_BRICK_Z, bz)
+    batch = Batch(inb, use_graph=True)
+    batch.set_option(OPT_BRICK_Z, bz)
+    batch.set_option(OPT_SPREAD_CTAS, ctas)
+    for _ in range(2):
+        for a in alone:
+            a.status.zero_()
+            a.step()
+        for x in inb:
+            x.status.zero_()
+        batch.run()
+        torch.cuda.synchronize()
+        for a, x in zip(alone, inb):
+            for u, v in zip(_outputs(a), _outputs(x)):
+                np.testing.assert_array_equal(u, v)
+    batch.close()
+    for x in alone + inb:
+        x.close()
+
+
+def test_batch_autotune_keeps_results():
+    import torch
+    from paper_2609_39443_b300.al import Batch, Instance, OPT_BRICK_Z
+    wls = W.make_batched(6, 4, max_cells=96 * 64 * 64)
+    alone = [Instance(w) for w in wls]
+    inb = [Instance(w) for w in wls]
+    batch = Batch(inb, use_graph=True)
+    batch.run()
+    for a in alone:
+        a.step()
+    bz, ctas = batch.autotune(trials=1)
+    assert bz in (4, 8, 16)
+    for a in alone:
+        a.grid.set_option(OPT_BRICK_Z, bz)
+        a.status.zero_()
+        a.step()
+    for x in inb:
+        x.status.zero_()
+    batch.run()
+    torch.cuda.synchronize()
+    for a, x in zip(alone, inb):
+        for u, v in zip(_outputs(a), _outputs(x)):
+            np.testing.assert_array_equal(u, v)
+    batch.close()
+    for x in alone + inb:
+        x.close()
