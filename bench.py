@@ -52,6 +52,9 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default options)")
+    ap.add_argument("--no-variants", action="store_true", help="skip timing the scatter projection")
+    ap.add_argument("--weights", choices=["brick", "segment"], default=None, help="fix the weights pass (no tuning)")
+    ap.add_argument("--brick-z", type=int, choices=[4, 8, 16], default=None, help="fix the brick height (no tuning)")
     return ap.parse_args()
 
 
@@ -230,7 +233,12 @@ def run_ours(a):
     wl = _workload(a.workload, rank, a.eps)
     inst = Instance(wl, device=f"cuda:{local}")
     tuned = {"weights": "brick", "brick_z": 8, "autotuned": False}
-    if not a.no_tune:
+    if a.weights or a.brick_z:
+        from paper_2609_39443_b300.al import OPT_BRICK_Z, OPT_WEIGHTS
+        tuned = {"weights": a.weights or "brick", "brick_z": a.brick_z or 8, "autotuned": False}
+        inst.grid.set_option(OPT_WEIGHTS, 1 if tuned["weights"] == "segment" else 0)
+        inst.grid.set_option(OPT_BRICK_Z, tuned["brick_z"])
+    elif not a.no_tune:
         wmode, bz = inst.autotune(trials=2)
         tuned = {"weights": "segment" if wmode else "brick", "brick_z": bz, "autotuned": True}
     inst.grid.trace(True)
@@ -309,6 +317,23 @@ def run_ours(a):
         e2e = {"value": world * n_e2e / te, "unit": "steps/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    # ---- the scatter-with-atomics projection on the same instance (comparison) ----
+    variants = None
+    if not a.no_variants:
+        from paper_2609_39443_b300.al import OPT_SPREAD, SPREAD_GATHER, SPREAD_SCATTER
+        variants = {}
+        for name, mode in (("gather", SPREAD_GATHER), ("scatter_atomics", SPREAD_SCATTER)):
+            inst.grid.set_option(OPT_SPREAD, mode)
+            acc = np.zeros(len(PHASES))
+            for k in range(3 + 5):
+                flush.zero_()
+                inst.step()
+                if k >= 3:
+                    acc += np.array(inst.grid.trace_last())
+            variants[name] = {"projection_ms": float(acc[PHASES.index("spread")] / 5),
+                              "step_ms": float(acc.sum() / 5)}
+        inst.grid.set_option(OPT_SPREAD, SPREAD_GATHER)
+
     peak, peak_kind = _peaks()
     alg = _algorithmic_bytes(wl)
     achieved = alg / spread_s / 1e9
@@ -331,6 +356,7 @@ def run_ours(a):
                 "roofline": {"bound": "hbm", "kernel": "k_spread", "achieved": achieved, "peak": peak,
                              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                              "algorithmic_bytes": alg, "traffic": traffic},
+                "projection_variants": variants,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": (KERNELS_PER_STEP + (tuned["weights"] == "segment")) * a.steps}
         print(json.dumps(line), flush=True)

@@ -189,6 +189,18 @@ int al_trace_last(al_grid g, float *ms /* [AL_TRACE_N] */);
 /* AL_OPT_SPREAD_CTAS (batches only, al_batch_set_option): persistent CTAs per
  * SM of the batched brick passes, 0 = as many as fit. */
 #define AL_OPT_SPREAD_CTAS  3
+/* AL_OPT_SPREAD selects the projection of Eq. almMomentumSource:
+ *   AL_SPREAD_GATHER (default): cell-centric gather per brick, every cell of
+ *     S written once by one thread, lines summed in line order, no atomics
+ *     (bitwise reproducible);
+ *   AL_SPREAD_SCATTER: for comparison, lines with a walk certificate add
+ *     their sources segment by segment with float atomics (summation order,
+ *     hence the last bits, vary run to run); the other lines and the
+ *     zero-weight deposits go through the gather first.  Single instances
+ *     only (a batch always gathers). */
+#define AL_OPT_SPREAD       4
+#define AL_SPREAD_GATHER    0
+#define AL_SPREAD_SCATTER   1
 int al_set_option(al_grid g, int option, int value);
 
 /* Autotuner: runs the caller's step (same in/out as al_sample_drag_spread)

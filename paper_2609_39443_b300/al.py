@@ -22,8 +22,9 @@ AL_STATUS_N = 16
 (ST_PA_OUTSIDE, ST_PS_OUTSIDE, ST_FALLBACK, ST_FALLBACK_ZERO, ST_ZERO_WEIGHT, ST_DEPOSIT_LOST,
  ST_REFINED, ST_IRREGULAR, ST_SUPPORT) = range(9)
 
-OPT_WEIGHTS, OPT_BRICK_Z, OPT_SPREAD_CTAS = 1, 2, 3
+OPT_WEIGHTS, OPT_BRICK_Z, OPT_SPREAD_CTAS, OPT_SPREAD = 1, 2, 3, 4
 WEIGHTS_BRICK, WEIGHTS_SEGMENT = 0, 1
+SPREAD_GATHER, SPREAD_SCATTER = 0, 1
 
 TRACE_N = 6
 PHASES = ("points", "mask", "weights", "normalise", "spread", "totals")

@@ -76,6 +76,7 @@ struct al_grid_s {
 
     // per-grid scratch
     double *brickSum = nullptr;
+    double *scatSum = nullptr;
     int *statusInt = nullptr;
     double *totalsInt = nullptr;
     int *hasPrev = nullptr;           // device flag: f_prev is valid
@@ -161,6 +162,7 @@ extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
 
     cudaError_t e;
     if ((e = dalloc(&g->brickSum, 3 * (size_t)g->nbrick_max)) != cudaSuccess ||
+        (e = dalloc(&g->scatSum, 3)) != cudaSuccess ||
         (e = dalloc(&g->statusInt, AL_STATUS_N)) != cudaSuccess || (e = dalloc(&g->totalsInt, 6)) != cudaSuccess ||
         (e = dalloc(&g->hasPrev, 1)) != cudaSuccess) {
         int rc = cuda_fail(e, "cudaMalloc");
@@ -319,7 +321,7 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     sc.fprev = (T *)g->fprev; sc.uhi = (T *)g->uhi; sc.ulo = g->ulo; sc.segD = (T *)g->segD;
     sc.segIl2 = (T *)g->segIl2; sc.nodeM = (T *)g->nodeM; sc.nodeTau = g->nodeTau;
     sc.segWa = g->segWa; sc.segWb = g->segWb; sc.wfix = g->wfix; sc.w = g->w; sc.fhat = (T *)g->fhat; sc.lineF = g->lineF;
-    sc.lines = g->lines; sc.mask = g->mask; sc.brickSum = g->brickSum;
+    sc.lines = g->lines; sc.mask = g->mask; sc.brickSum = g->brickSum; sc.scatSum = g->scatSum;
     sc.hasPrev = g->hasPrev;
     BeamsC &bc = I.b;
     bc.n_lines = g->n_lines; bc.n_points = np; bc.mask_words = g->mask_words;
@@ -366,6 +368,12 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
     if (np > 0) k_normalise<T><<<nb, 256, 0, st>>>(gc, bc, sc, p, status);
     trace_mark(g, 4, st);
     launch_bricks_bz<T>(I, false, st);
+    if (gc.smode != 0 && np > 0) {
+        // scatter form: certified lines add their sources with atomics after the
+        // gather has written every cell (uncertified lines and deposits)
+        AL_CUDA(cudaMemsetAsync(g->scatSum, 0, 3 * sizeof(double), st));
+        k_scatter<T><<<(unsigned)(((long long)np * 32 + 127) / 128), 128, 0, st>>>(gc, bc, sc, p, status);
+    }
     trace_mark(g, 5, st);
     k_totals<T><<<1, 256, 0, st>>>(gc, bc, sc, I.totals);
     trace_mark(g, 6, st);
@@ -402,6 +410,10 @@ extern "C" int al_set_option(al_grid g, int option, int value) {
         if (value != 4 && value != 8 && value != 16) return AL_ERR_ARG;
         set_brick_z(g->gc, value);
         return AL_OK;
+    case AL_OPT_SPREAD:
+        if (value != AL_SPREAD_GATHER && value != AL_SPREAD_SCATTER) return AL_ERR_ARG;
+        g->gc.smode = value;
+        return AL_OK;
     default:
         return AL_ERR_ARG;
     }
@@ -433,7 +445,7 @@ extern "C" int al_destroy(al_grid g) {
     cudaDeviceSynchronize();
     if (g->trace) al_trace_enable(g, 0);
     free_beams(g);
-    void *ptrs[] = {g->brickSum, g->statusInt, g->totalsInt, g->hasPrev};
+    void *ptrs[] = {g->brickSum, g->scatSum, g->statusInt, g->totalsInt, g->hasPrev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -559,6 +571,7 @@ static int batch_rebuild_t(al_batch b) {
         if (used) {
             h[q] = make_inst<T>(b->grids[q], &b->ins[q], &b->outs[q]);
             set_brick_z(h[q].g, b->bz);
+            h[q].g.smode = 0;                                // batches always gather
             if (h[q].g.wmode != 0) b->any_segment_weights = true;
             b->cnt_pts[q] = b->grids[q]->n_points;
             b->cnt_lines[q] = b->grids[q]->n_lines;
@@ -587,7 +600,7 @@ static int batch_rebuild_t(al_batch b) {
     if (occ < 1) occ = 1;
     b->occ = occ;
     const int per = b->ctas > 0 ? std::min(b->ctas, occ) : occ;
-    b->spread_grid = (int)std::min<long long>((long long)nsm * per, std::max<long long>(b->tot_bricks, 1));
+    b->spread_grid = nsm * per;                          // capped by each run's brick count at launch
     b->pt_grid = nsm * 8;
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -676,6 +689,7 @@ static int batch_assign_t(al_batch b, int slot, al_grid g, const al_step_in *in,
     if (g) {
         *h = make_inst<T>(g, in, out);
         set_brick_z(h->g, b->bz);
+        h->g.smode = 0;
     } else {
         memset((void *)h, 0, sizeof(Inst<T>));
     }

@@ -55,6 +55,7 @@ struct GridC {
     double rho1, rho2, rho_const;
     int wmode;                   // 0: all weights from the brick pass; 1: segment pass for certified lines
     int bz;                      // brick height of the projection (4, 8 or 16 cells)
+    int smode;                   // 0: gather (every line); 1: scatter with atomics for certified lines
 };
 
 struct BeamsC {
@@ -95,6 +96,7 @@ struct Scratch {
     LineG *lines;                // [n_lines]
     uint32_t *mask;              // [nbrick][mask_words] lines touching a brick
     double *brickSum;            // [3][nbrick] sum of S per brick
+    double *scatSum;             // [3] sum of S added by the scatter form
     int *hasPrev;                // [1] a previous relaxed force exists (set by k_totals)
 };
 
@@ -812,12 +814,58 @@ struct WSeg {
     double eps;
 };
 
-// membership of cell cg (local centre C) in segment ctx.k and its weights
+// What a visited cell feeds: the segment's two weight sums (SC = false), or
+// in the scatter form of the projection the cell's momentum source, added
+// to S with atomics (SC = true; the sums of what was added feed the totals).
+template <typename T, bool SC> struct WSink;
+template <typename T> struct WSink<T, false> {
+    Acc<T> wa, wb;
+    __device__ __forceinline__ void add(const GridC &, const StepPtrs<T> &, long long, T eta, T s) {
+        wa.add(((T)1 - s) * eta);
+        wb.add(s * eta);
+    }
+};
+template <typename T> struct WSink<T, true> {
+    T fa[3], fb[3];
+    Acc<T> sum[3];
+    int nsupp = 0;
+    __device__ __forceinline__ void add(const GridC &, const StepPtrs<T> &p, long long idx, T eta, T s) {
+        const T wa = eta * ((T)1 - s), wb = eta * s;
+        for (int a = 0; a < 3; ++a) {
+            const T v = -(wa * fa[a] + wb * fb[a]);
+            atomicAdd(&p.S[a][idx], v);
+            sum[a].add(v);
+        }
+        ++nsupp;
+    }
+};
+
+// "segment k closer than k-1" from float-float node positions (defined with
+// the projection kernels below)
+static __device__ __noinline__ int ff_later_closer(const float *uhi, const float *ulo, long long np, int k, int B0,
+                                                   int B1, int B2, float cx, float cy, float cz);
+
+// near-tie re-decision of "segment k closer than k-1" for a cell at C
+// (relative to the integer origin O): float-float for FP32 instances, FP64
+// where that does not decide, and for FP64 instances
 template <typename T>
+__device__ __noinline__ bool w_later_closer(const GridC &g, const Scratch<T> &sc, const StepPtrs<T> &p, int k,
+                                            const int O[3], T c0, T c1, T c2, int *status) {
+    if (sizeof(T) == 4) {
+        const int r = ff_later_closer((const float *)sc.uhi, sc.ulo, (long long)p.np, k, O[0], O[1], O[2],
+                                      (float)c0, (float)c1, (float)c2);
+        if (r >= 0) return r == 1;
+    }
+    atomicAdd(&status[ST_REFINED], 1);
+    return later_closer_f64(g, p, k, ifloor(c0) + O[0], ifloor(c1) + O[1], ifloor(c2) + O[2]);
+}
+
+// membership of the cell at C (relative to c.O) in segment c.k's share, and
+// what it feeds
+template <typename T, bool SC>
 __device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const GridC &g,
                                        const Scratch<T> &sc, const StepPtrs<T> &p, bool regular,
-                                       int *status, Acc<T> &wa, Acc<T> &wb) {
-    const long long np = (long long)p.np;
+                                       int *status, WSink<T, SC> &sink) {
     // global cell index, needed only by the FP64 re-decisions (rare)
 #define AL_CG(a) (ifloor(C[a]) + c.O[a])
     T x[3];
@@ -829,7 +877,7 @@ __device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const Gri
             bool pos;
             if (sg > gs) pos = true;
             else if (sg < -gs) pos = false;
-            else { pos = later_closer_f64(g, p, c.k, AL_CG(0), AL_CG(1), AL_CG(2)); atomicAdd(&status[ST_REFINED], 1); }
+            else pos = w_later_closer(g, sc, p, c.k, c.O, C[0], C[1], C[2], status);
             if (!pos) return;
         }
         if (c.has_hi) {
@@ -840,7 +888,7 @@ __device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const Gri
             bool pos;
             if (sg > gs) pos = true;
             else if (sg < -gs) pos = false;
-            else { pos = later_closer_f64(g, p, c.k + 1, AL_CG(0), AL_CG(1), AL_CG(2)); atomicAdd(&status[ST_REFINED], 1); }
+            else pos = w_later_closer(g, sc, p, c.k + 1, c.O, C[0], C[1], C[2], status);
             if (pos) return;
         }
     }
@@ -852,11 +900,11 @@ __device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const Gri
     if (r2 < c.R2 - c.gr) in = true;
     else if (r2 > c.R2 + c.gr) in = false;
     else { in = within_f64(g, p, c.eps, c.k, c.n, AL_CG(0), AL_CG(1), AL_CG(2)); atomicAdd(&status[ST_REFINED], 1); }
-#undef AL_CG
     if (!in) return;
     T eta = c.eta0 * Tr<T>::ex2(-r2 * c.ie2);
-    wa.add(((T)1 - s) * eta);
-    wb.add(s * eta);
+    const long long idx = SC ? AL_CG(0) + (long long)g.nx * (AL_CG(1) + (long long)g.ny * AL_CG(2)) : 0;
+#undef AL_CG
+    sink.add(g, p, idx, eta, s);
 }
 
 // warp sum of compensated lane sums, as float-float (FP32) or plain FP64
@@ -879,10 +927,10 @@ __device__ __forceinline__ double warp_total(const Acc<double> &a) {
 
 // the cells of segment c.k's slab, columns along the two axes other than
 // the march axis AX (compile-time, so coordinates stay in registers)
-template <typename T, int AX>
+template <typename T, int AX, bool SC>
 __device__ __forceinline__ void w_columns(const WSeg<T> &c, const GridC &g, const Scratch<T> &sc,
-                                          const StepPtrs<T> &p, int *status, const int lane, Acc<T> &wa,
-                                          Acc<T> &wb) {
+                                          const StepPtrs<T> &p, int *status, const int lane,
+                                          WSink<T, SC> &sink) {
     constexpr int PA = (AX + 1) % 3, PB = (AX + 2) % 3;
     const int na = c.hi[PA] - c.lo[PA] + 1, nbb = c.hi[PB] - c.lo[PB] + 1;
     const int ncol = na * nbb;
@@ -928,7 +976,7 @@ __device__ __forceinline__ void w_columns(const WSeg<T> &c, const GridC &g, cons
         const T z1 = tmin(ffloor_f(chi - (T)0.5) + (T)0.5, chi0);
         for (T z = z0; z <= z1; z += (T)1) {
             C[AX] = z;
-            w_cell(c, C, g, sc, p, true, status, wa, wb);
+            w_cell<T, SC>(c, C, g, sc, p, true, status, sink);
         }
         }
     next_column:
@@ -939,9 +987,32 @@ __device__ __forceinline__ void w_columns(const WSeg<T> &c, const GridC &g, cons
 }
 
 template <typename T>
+__device__ __forceinline__ void w_finish(const GridC &g, const Scratch<T> &sc, int *, int k, int lane,
+                                         WSink<T, false> &sink) {
+    const double ta = warp_total(sink.wa), tb = warp_total(sink.wb);
+    if (lane == 0) {
+        sc.segWa[k] = ta * g.V;
+        sc.segWb[k] = tb * g.V;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void w_finish(const GridC &, const Scratch<T> &sc, int *status, int, int lane,
+                                         WSink<T, true> &sink) {
+    double t[3];
+    for (int a = 0; a < 3; ++a) t[a] = warp_total(sink.sum[a]);
+    int ns = sink.nsupp;
+    for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
+    if (lane == 0) {
+        for (int a = 0; a < 3; ++a)
+            if (t[a] != 0.0) atomicAdd(&sc.scatSum[a], t[a]);
+        if (ns) atomicAdd(&status[ST_SUPPORT], ns);
+    }
+}
+
+template <typename T, bool SC>
 __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
                           const int k, const int lane) {
-    if (g.wmode == 0) return;                               // all weights from the brick pass
+    if (!SC && g.wmode == 0) return;                        // all weights from the brick pass
     const long long np = b.n_points;
     const int l = b.line_of[k];
     const LineG lg = sc.lines[l];
@@ -950,8 +1021,8 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
     if (c.n >= 2 && c.q == c.n - 1) return;                 // the tip starts no segment
     c.nseg = (c.n == 1) ? 1 : c.n - 1;
     c.kb = seg_end(k, c.n);
-    if (!lg.regular) {                                      // weights from the brick pass (k_bweights)
-        if (lane == 0) { sc.segWa[k] = 0.0; sc.segWb[k] = 0.0; }
+    if (!lg.regular) {                                      // the brick passes take this line
+        if (!SC && lane == 0) { sc.segWa[k] = 0.0; sc.segWb[k] = 0.0; }
         return;
     }
     c.klo = 0; c.khi = c.nseg - 1;
@@ -972,7 +1043,9 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
         c.hi[a] = min(nn[a] - 1, ifloor(h0 - (T)0.5) + c.O[a]);
         if (c.lo[a] > c.hi[a]) empty = true;
     }
-    Acc<T> wa, wb;
+    WSink<T, SC> sink;
+    if constexpr (SC)
+        for (int a = 0; a < 3; ++a) { sink.fa[a] = sc.fhat[a * np + k]; sink.fb[a] = sc.fhat[a * np + c.kb]; }
     const bool regular = lg.regular != 0;
     c.has_lo = regular && c.q >= 1;
     c.has_hi = regular && c.q + 1 <= c.n - 2;
@@ -984,15 +1057,11 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
         int ax = 0;
         if (tabs(c.D[1]) > tabs(c.D[ax])) ax = 1;
         if (tabs(c.D[2]) > tabs(c.D[ax])) ax = 2;
-        if (ax == 0) w_columns<T, 0>(c, g, sc, p, status, lane, wa, wb);
-        else if (ax == 1) w_columns<T, 1>(c, g, sc, p, status, lane, wa, wb);
-        else w_columns<T, 2>(c, g, sc, p, status, lane, wa, wb);
+        if (ax == 0) w_columns<T, 0, SC>(c, g, sc, p, status, lane, sink);
+        else if (ax == 1) w_columns<T, 1, SC>(c, g, sc, p, status, lane, sink);
+        else w_columns<T, 2, SC>(c, g, sc, p, status, lane, sink);
     }
-    const double ta = warp_total(wa), tb = warp_total(wb);
-    if (lane == 0) {
-        sc.segWa[k] = ta * g.V;
-        sc.segWb[k] = tb * g.V;
-    }
+    w_finish(g, sc, status, k, lane, sink);
 }
 
 // ---------------------------------------------------------------------------
@@ -1126,8 +1195,6 @@ __device__ __noinline__ int nl_exhaustive(const GridC &g, const Scratch<T> &sc, 
 // closest segments that share a node is decided by the float-float test of
 // the pair (ff_later_closer, defined below); other near ties by the FP64
 // argmin.
-static __device__ __noinline__ int ff_later_closer(const float *uhi, const float *ulo, long long np, int k, int B0,
-                                                   int B1, int B2, float cx, float cy, float cz);
 template <typename T, int BZ>
 __device__ __noinline__ int nl_exhaustive_staged(const SpreadSmem<T, BZ> &sm, const GridC &g, const StepPtrs<T> &p,
                                                  const Scratch<T> &sc, int base, int first, int n, int jlo, int jhi,
@@ -1316,6 +1383,15 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                 }
             } else if (mine && m) {
                 mrow[w0 + lane] = 0u;                    // clear for the next step
+                if (g.smode != 0) {                      // the scatter form takes certified lines
+                    uint32_t keep = 0u, t = m;
+                    while (t) {
+                        const int bit = __ffs(t) - 1;
+                        t &= t - 1;
+                        if (!sc.lines[((w0 + lane) << 5) + bit].regular) keep |= 1u << bit;
+                    }
+                    m = keep;
+                }
             }
             int cnt = __popc(m), pre = cnt;
             for (int o = 1; o < 32; o <<= 1) {
@@ -1755,7 +1831,7 @@ __device__ void d_totals(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
     }
     if (threadIdx.x == 0) {
         for (int a = 0; a < 3; ++a) totals[a] = red[a][0];
-        for (int a = 0; a < 3; ++a) totals[3 + a] = red[3 + a][0] * g.V;
+        for (int a = 0; a < 3; ++a) totals[3 + a] = (red[3 + a][0] + (g.smode ? sc.scatSum[a] : 0.0)) * g.V;
         *sc.hasPrev = 1;                 // the next step relaxes against this one
     }
 }
@@ -1811,7 +1887,13 @@ __global__ void __launch_bounds__(256) k_mask(GridC g, BeamsC b, Scratch<T> sc) 
 template <typename T>
 __global__ void __launch_bounds__(128) k_weights(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (k < b.n_points) d_weights(g, b, sc, p, status, k, threadIdx.x & 31);
+    if (k < b.n_points) d_weights<T, false>(g, b, sc, p, status, k, threadIdx.x & 31);
+}
+// scatter form of the projection: one warp per segment of a certified line
+template <typename T>
+__global__ void __launch_bounds__(128) k_scatter(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k < b.n_points) d_weights<T, true>(g, b, sc, p, status, k, threadIdx.x & 31);
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_normalise(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
@@ -1890,7 +1972,7 @@ __global__ void __launch_bounds__(128) kb_weights(const Inst<T> *I, const int *s
     for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
         const int q = owner(pre, n, w);
         const Inst<T> &x = I[AL_SEL(q)];
-        d_weights(x.g, x.b, x.sc, x.p, x.status, (int)(w - pre[q]), threadIdx.x & 31);
+        d_weights<T, false>(x.g, x.b, x.sc, x.p, x.status, (int)(w - pre[q]), threadIdx.x & 31);
     }
 }
 template <typename T>

@@ -111,3 +111,19 @@ def test_batch_autotune_keeps_results():
     batch.close()
     for x in alone + inb:
         x.close()
+
+
+@pytest.mark.parametrize("name", ["canopy", "random"])
+def test_scatter_form_matches_the_oracle(name):
+    """The scatter-with-atomics projection (kept for comparison) agrees with
+    the oracle within the same tolerances as the gather."""
+    from paper_2609_39443_b300.al import Instance, OPT_SPREAD, SPREAD_SCATTER
+    wl = (W.make_canopy(3, 2.0) if name == "canopy" else
+          W.make_random(24, 52, 44, 36, n_lines=10, kinds=("stem", "arc", "random", "flat", "point", "dup")))
+    inst = Instance(wl)
+    inst.grid.set_option(OPT_SPREAD, SPREAD_SCATTER)
+    g = run_gpu(wl, inst=inst)
+    o = oracle.sample_drag_spread(wl)
+    compare(wl, g, o, label=f"scatter {name}", sumF_ref="net" if name == "canopy" else "abs")
+    assert g["status"][8] == oracle.count_support(wl.grid, wl.beams, wl.step.P)
+    inst.close()
