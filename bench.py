@@ -43,10 +43,10 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="canopy", choices=["canopy", "flume", "plain", "batched", "serve"])
     ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
-    ap.add_argument("--sims", type=int, default=256, help="serve: number of simulations")
-    ap.add_argument("--sim-steps", type=int, default=100, help="serve: steps per simulation")
+    ap.add_argument("--sims", type=int, default=64, help="serve: number of simulations")
+    ap.add_argument("--sim-steps", type=int, default=20, help="serve: steps per simulation")
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000", help="serve: arrival rates (1/s)")
-    ap.add_argument("--budget-gb", type=float, default=2.0, help="serve: HBM budget for resident simulations")
+    ap.add_argument("--budget-gb", type=float, default=0.5, help="serve: HBM budget for resident simulations")
     ap.add_argument("--eps", type=float, default=2.0, help="canopy kernel width in cells")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")

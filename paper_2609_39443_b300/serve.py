@@ -5,7 +5,7 @@ for their next step) as they arrive.  The server keeps each admitted
 simulation's grid, fields, bins and relaxation state resident on the device,
 admits simulations by their HBM footprint under a budget, and advances every
 simulation whose next request has arrived in one batched launch sequence
-(al_batch_run_subset) — a *wave*.  Waves alternate between CUDA streams, so a
+(al_batch_run_subset) -- a *wave*.  Waves alternate between CUDA streams, so a
 wave forms and launches while earlier ones are still running; a simulation
 with a step in flight waits for it (steps of one simulation are ordered).
 Evicted simulations free their slot and memory for waiting ones.
@@ -13,14 +13,16 @@ Evicted simulations free their slot and memory for waiting ones.
 `PlainServer` is the reference path: one al_sample_drag_spread per request
 in arrival order on one stream, with the same copies and admission.
 
-All GPU work is in the CUDA library; this module only schedules and copies.
+The schedulers only decide what runs when; every device operation goes
+through a backend (`CudaBackend`: PyTorch memory and streams plus the CUDA
+library), so the scheduling can be checked on the host with a stand-in.
 """
 from __future__ import annotations
 
 import time
 from collections import deque
 from dataclasses import dataclass, field
-from typing import List
+from typing import Dict, List, Optional, Tuple
 
 import numpy as np
 
@@ -38,9 +40,12 @@ class Sim:
         es = 8 if g.precision == "fp64" else 4
         fields = (3 + 3 + (1 if g.has_alpha else 0)) * es * g.n_cells          # U, S, alpha
         points = b.n_points * (es * 3 * 5 + 120)                                 # P, Pdot, F, staging + scratch
-        bricks = ((g.nx + 15) // 16) * ((g.ny + 15) // 16) * ((g.nz + 7) // 8)
+        bricks = ((g.nx + 15) // 16) * ((g.ny + 15) // 16) * ((g.nz + 3) // 4)   # lowest brick height
         mask = bricks * ((b.n_lines + 31) // 32) * 4 + bricks * 24
         return int(fields + points + mask + 4096)
+
+    def positions(self, k: int) -> np.ndarray:
+        return self.wl.step.P.astype(np.float64) + (k * self.dt) * self.wl.step.Pdot.astype(np.float64)
 
 
 @dataclass
@@ -82,46 +87,100 @@ def poisson_arrivals(sims: List[Sim], rate: float, seed: int):
     return out
 
 
+class CudaBackend:
+    """Device side of the servers: resident instances with pinned staging
+    buffers, the slot batch, streams and events."""
+
+    def __init__(self, device="cuda"):
+        self.device = device
+
+    def stream(self):
+        import torch
+        return torch.cuda.Stream(device=self.device)
+
+    def resident(self, sim: Sim):
+        return _Resident(sim, self.device)
+
+    def batch(self, n_slots: int, precision: str):
+        from .al import Batch
+        return Batch([], use_graph=False, reserve=(n_slots, precision))
+
+    def stream_ctx(self, stream):
+        import torch
+        return torch.cuda.stream(stream)
+
+    def mark(self, stream):
+        import torch
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        return ev
+
+    @staticmethod
+    def done(ev) -> bool:
+        return ev.query()
+
+    @staticmethod
+    def sync(stream) -> None:
+        stream.synchronize()
+
+    def sync_all(self) -> None:
+        import torch
+        torch.cuda.synchronize()
+
+
 class _Resident:
     def __init__(self, sim: Sim, device):
         import torch
         from .al import Instance
         self.sim = sim
         self.inst = Instance(sim.wl, device=device)
-        self.P0 = sim.wl.step.P.astype(np.float64)
-        self.Pd = sim.wl.step.Pdot.astype(np.float64)
         dt = self.inst.dtype
         self.hP = torch.empty(self.inst.P.shape, dtype=dt).pin_memory()
         self.hF = torch.empty(self.inst.F.shape, dtype=dt).pin_memory()
-        self.busy = False
-        self.done_steps = 0
 
-    def stage(self, k: int):
-        # positions of step k into pinned host memory (the client's payload)
-        np.copyto(self.hP.numpy(), self.P0 + (k * self.sim.dt) * self.Pd, casting="same_kind")
+    def upload(self, k: int) -> None:
+        # positions of step k into pinned host memory (the client's payload), then to the device
+        np.copyto(self.hP.numpy(), self.sim.positions(k), casting="same_kind")
+        self.inst.P.copy_(self.hP, non_blocking=True)
 
-    def close(self):
+    def download(self) -> None:
+        self.hF.copy_(self.inst.F, non_blocking=True)
+
+    def step(self, stream) -> None:
+        self.inst.step(stream=stream)
+
+    def result_F(self) -> np.ndarray:
+        return self.hF.numpy()[:, :self.sim.wl.beams.n_points].copy()
+
+    def result_S(self) -> np.ndarray:
+        return self.inst.S.cpu().numpy().copy()
+
+    def close(self) -> None:
         self.inst.close()
 
 
 class _Base:
-    def __init__(self, sims: List[Sim], hbm_budget: int, device="cuda"):
+    def __init__(self, sims: List[Sim], hbm_budget: int, backend=None, record: bool = False):
         self.sims = sims
         self.budget = int(hbm_budget)
-        self.device = device
+        self.be = backend if backend is not None else CudaBackend()
         self.stats = Stats()
         self.mem = 0
-        self.res = {}
-        self.wait_adm = deque()
-        self.queued = set()
-        self.pending = [deque() for _ in sims]
+        self.res: Dict[int, object] = {}
+        self.done_steps = [0] * len(sims)
+        self.busy = [False] * len(sims)
+        self.record = record
+        self.results: Dict[Tuple[int, int], np.ndarray] = {}     # (sim, step) -> F
+        self.final_S: Dict[int, np.ndarray] = {}
+
+    def _fits(self, s: int) -> bool:
+        return self.mem + self.sims[s].footprint() <= self.budget or not self.res
 
     def _admit(self, s: int) -> bool:
-        fp = self.sims[s].footprint()
-        if self.mem + fp > self.budget and self.res:
+        if not self._fits(s):
             return False
-        self.res[s] = _Resident(self.sims[s], self.device)
-        self.mem += fp
+        self.res[s] = self.be.resident(self.sims[s])
+        self.mem += self.sims[s].footprint()
         self.stats.admitted += 1
         self.stats.peak_mem = max(self.stats.peak_mem, self.mem)
         return True
@@ -131,45 +190,57 @@ class _Base:
         r.close()
         self.mem -= self.sims[s].footprint()
 
+    def _finish(self, s: int, k: int, t_arrival: float, now: float):
+        st = self.stats
+        st.latencies.append(now - t_arrival)
+        st.completed += 1
+        r = self.res[s]
+        if self.record:
+            self.results[(s, k)] = r.result_F()
+        self.busy[s] = False
+        self.done_steps[s] += 1
+        if self.done_steps[s] == self.sims[s].n_steps:
+            if self.record:
+                self.final_S[s] = r.result_S()
+            return True
+        return False
+
 
 class BatchServer(_Base):
     """Continuous batching over al_batch_run_subset."""
 
-    def __init__(self, sims, hbm_budget, *, n_slots=64, n_streams=2, max_wave=64, device="cuda"):
-        super().__init__(sims, hbm_budget, device)
-        import torch
-        from .al import Batch
+    def __init__(self, sims, hbm_budget, *, n_slots=64, n_streams=2, max_wave=64, backend=None, record=False):
+        super().__init__(sims, hbm_budget, backend, record)
         prec = sims[0].wl.grid.precision
-        self.batch = Batch([], use_graph=False, reserve=(n_slots, prec))
+        self.batch = self.be.batch(n_slots, prec)
         self.free_slots = deque(range(n_slots))
-        self.slot_of = {}
-        self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
+        self.slot_of: Dict[int, int] = {}
+        self.streams = [self.be.stream() for _ in range(n_streams)]
         self.max_wave = max_wave
         self.inflight = deque()           # (event, stream index, [(sim, step, t_arrival)])
 
     def _admit(self, s):
-        if not self.free_slots:
-            return False
-        if not super()._admit(s):
+        if not self.free_slots or not super()._admit(s):
             return False
         slot = self.free_slots.popleft()
         self.slot_of[s] = slot
         # bind the slot and wait, so every stream sees the new descriptor
         self.batch.assign(slot, self.res[s].inst, stream=self.streams[0])
-        self.streams[0].synchronize()
+        self.be.sync(self.streams[0])
         return True
 
     def _evict(self, s):
         slot = self.slot_of.pop(s)
         self.batch.assign(slot, None, stream=self.streams[0])
-        torch_sync(self.streams[0])
+        self.be.sync(self.streams[0])
         super()._evict(s)
         self.free_slots.append(slot)
 
     def run(self, arrivals):
-        import torch
         st = self.stats
         n_req = len(arrivals)
+        pending = [deque() for _ in self.sims]
+        wait_adm, queued = deque(), set()
         ai = 0
         t0 = time.perf_counter()
         busy_streams = set()
@@ -177,37 +248,32 @@ class BatchServer(_Base):
             now = time.perf_counter() - t0
             while ai < n_req and arrivals[ai][0] <= now:
                 t, s, k = arrivals[ai]
-                self.pending[s].append((k, t))
-                if s not in self.res and s not in self.queued:
-                    self.wait_adm.append(s)
-                    self.queued.add(s)
+                pending[s].append((k, t))
+                if s not in self.res and s not in queued:
+                    wait_adm.append(s)
+                    queued.add(s)
                 ai += 1
             # retire finished waves
-            while self.inflight and self.inflight[0][0].query():
+            while self.inflight and self.be.done(self.inflight[0][0]):
                 ev, si, items = self.inflight.popleft()
                 busy_streams.discard(si)
                 done = time.perf_counter() - t0
                 for s, k, ta in items:
-                    st.latencies.append(done - ta)
-                    st.completed += 1
-                    r = self.res[s]
-                    r.busy = False
-                    r.done_steps += 1
-                    if r.done_steps == self.sims[s].n_steps:
+                    if self._finish(s, k, ta, done):
                         self._evict(s)
             # admissions in arrival order
-            while self.wait_adm:
-                s = self.wait_adm[0]
+            while wait_adm:
+                s = wait_adm[0]
                 if not self._admit(s):
                     break
-                self.wait_adm.popleft()
-                self.queued.discard(s)
-            # form and launch a wave
+                wait_adm.popleft()
+                queued.discard(s)
+            # form and launch a wave: every resident simulation whose next step has arrived
             free = [i for i in range(len(self.streams)) if i not in busy_streams]
             if free:
                 wave = []
-                for s, r in self.res.items():
-                    if not r.busy and self.pending[s] and self.pending[s][0][0] == r.done_steps:
+                for s in self.res:
+                    if not self.busy[s] and pending[s] and pending[s][0][0] == self.done_steps[s]:
                         wave.append(s)
                         if len(wave) >= self.max_wave:
                             break
@@ -215,20 +281,16 @@ class BatchServer(_Base):
                     si = free[0]
                     stream = self.streams[si]
                     items = []
-                    with torch.cuda.stream(stream):
+                    with self.be.stream_ctx(stream):
                         for s in wave:
-                            k, ta = self.pending[s].popleft()
-                            r = self.res[s]
-                            r.stage(k)
-                            r.inst.P.copy_(r.hP, non_blocking=True)
-                            r.busy = True
+                            k, ta = pending[s].popleft()
+                            self.res[s].upload(k)
+                            self.busy[s] = True
                             items.append((s, k, ta))
                         self.batch.run_subset([self.slot_of[s] for s in wave], stream=stream)
                         for s in wave:
-                            r = self.res[s]
-                            r.hF.copy_(r.inst.F, non_blocking=True)
-                        ev = torch.cuda.Event()
-                        ev.record(stream)
+                            self.res[s].download()
+                        ev = self.be.mark(stream)
                     self.inflight.append((ev, si, items))
                     busy_streams.add(si)
                     st.waves += 1
@@ -236,7 +298,7 @@ class BatchServer(_Base):
                     continue
             if ai < n_req and not self.inflight:
                 time.sleep(max(0.0, min(1e-4, arrivals[ai][0] - now)))
-        torch.cuda.synchronize()
+        self.be.sync_all()
         st.wall = time.perf_counter() - t0
         for s in list(self.res):
             self._evict(s)
@@ -249,12 +311,11 @@ class PlainServer(_Base):
     the oldest processable request first, with the same admission rule."""
 
     def run(self, arrivals):
-        import torch
         st = self.stats
         n_req = len(arrivals)
         ai = 0
         queue = []                        # arrived, not yet processed (arrival order)
-        stream = torch.cuda.Stream(device=self.device)
+        stream = self.be.stream()
         t0 = time.perf_counter()
         while st.completed < n_req:
             now = time.perf_counter() - t0
@@ -264,7 +325,7 @@ class PlainServer(_Base):
             pick = None
             for qi, (t, s, k) in enumerate(queue):
                 if s in self.res:
-                    if self.res[s].done_steps == k:
+                    if self.done_steps[s] == k:
                         pick = qi
                         break
                 elif self._admit(s):
@@ -276,24 +337,16 @@ class PlainServer(_Base):
                 continue
             t, s, k = queue.pop(pick)
             r = self.res[s]
-            with torch.cuda.stream(stream):
-                r.stage(k)
-                r.inst.P.copy_(r.hP, non_blocking=True)
-                r.inst.step(stream=stream)
-                r.hF.copy_(r.inst.F, non_blocking=True)
-            stream.synchronize()
-            st.latencies.append(time.perf_counter() - t0 - t)
-            st.completed += 1
+            with self.be.stream_ctx(stream):
+                r.upload(k)
+                r.step(stream)
+                r.download()
+            self.be.sync(stream)
             st.waves += 1
             st.wave_sizes.append(1)
-            r.done_steps += 1
-            if r.done_steps == self.sims[s].n_steps:
+            if self._finish(s, k, t, time.perf_counter() - t0):
                 self._evict(s)
         st.wall = time.perf_counter() - t0
         for s in list(self.res):
             self._evict(s)
         return st
-
-
-def torch_sync(stream):
-    stream.synchronize()
