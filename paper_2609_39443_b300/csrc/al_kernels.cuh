@@ -1113,6 +1113,7 @@ struct SpreadSmem {
     T M[3][NN];                  // node bisectors
     T D[3][NN];                  // segment vectors
     T Il2[NN];
+    float Tau[NN];               // tan(theta_k / 2) at the nodes (0 at the line's ends)
     union {
         struct {
             T Fh[3][NN];         // spread: f^ at the nodes
@@ -1338,6 +1339,17 @@ __device__ __forceinline__ void seg_foot(const SpreadSmem<T, BZ> &sm, int ss, co
     r2 = e0 * e0 + e1 * e1 + e2 * e2;
 }
 
+// seg_foot also returning the unclamped foot parameter
+template <typename T, int BZ>
+__device__ __forceinline__ void seg_foot_raw(const SpreadSmem<T, BZ> &sm, int ss, const T C[3], T &sraw, T &s, T &r2) {
+    const T x0 = C[0] - sm.P[0][ss], x1 = C[1] - sm.P[1][ss], x2 = C[2] - sm.P[2][ss];
+    const T d0 = sm.D[0][ss], d1 = sm.D[1][ss], d2 = sm.D[2][ss];
+    sraw = (x0 * d0 + x1 * d1 + x2 * d2) * sm.Il2[ss];
+    s = sraw < (T)0 ? (T)0 : (sraw > (T)1 ? (T)1 : sraw);
+    const T e0 = x0 - s * d0, e1 = x1 - s * d1, e2 = x2 - s * d2;
+    r2 = e0 * e0 + e1 * e1 + e2 * e2;
+}
+
 // One brick of cells and the lines near it.  WP = false: the momentum source
 // (Eq. almMomentumSource) of every cell of the brick, written once per cell
 // by the thread that owns its column (no atomics), with the deposits of the
@@ -1514,6 +1526,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                         sm.D[a][s] = sc.segD[a * np + kn];
                     }
                     sm.Il2[s] = sc.segIl2[kn];
+                    sm.Tau[s] = sc.nodeTau[kn];
                     if (WP) {
                         sm.u.wq[s] = 0ull;
                     } else {
@@ -1639,13 +1652,31 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                                         j = jcz;
                                         start_ok = node_d2(sm, base + (j - jlo), C) <= (T)rho2;
                                     }
-                                    while (j > jlo && !sig_pos(sm, base + (j - jlo), C, g, p, sc, first + j, B0, B1, B2,
-                                                               gxc, gyc, gz, status)) --j;
-                                    while (j < jhi && sig_pos(sm, base + (j + 1 - jlo), C, g, p, sc, first + j + 1, B0,
-                                                              B1, B2, gxc, gyc, gz, status)) ++j;
+                                    // the foot on the start segment lies inside it by more than
+                                    // r tan(theta/2) at both ends: both bisector tests are decided
+                                    // (sigma = a cos(theta/2) + ... >= a cos(theta/2) - r sin(theta/2))
+                                    bool fast = false;
+                                    if (start_ok) {
+                                        const int sl = base + (j - jlo);
+                                        T sr, sc0, rr;
+                                        seg_foot_raw(sm, sl, C, sr, sc0, rr);
+                                        const T il = tsqrt(sm.Il2[sl]), r = tsqrt(rr);
+                                        const T band = Tr<T>::gsig(r + (T)1 / il);
+                                        const bool lo_ok = j == jlo || sr > (r * (T)sm.Tau[sl] + band) * il;
+                                        const bool hi_ok = j == jhi || (T)1 - sr > (r * (T)sm.Tau[sl + 1] + band) * il;
+                                        if (lo_ok && hi_ok) { fast = true; s = sc0; r2 = rr; }
+                                    }
+                                    if (!fast) {
+                                        while (j > jlo && !sig_pos(sm, base + (j - jlo), C, g, p, sc, first + j, B0, B1,
+                                                                   B2, gxc, gyc, gz, status)) --j;
+                                        while (j < jhi && sig_pos(sm, base + (j + 1 - jlo), C, g, p, sc, first + j + 1,
+                                                                  B0, B1, B2, gxc, gyc, gz, status)) ++j;
+                                        seg_foot(sm, base + (j - jlo), C, s, r2);
+                                    }
                                     js = j;
+                                } else {
+                                    seg_foot(sm, base + (js - jlo), C, s, r2);
                                 }
-                                seg_foot(sm, base + (js - jlo), C, s, r2);
                                 // a walk from outside the certified radius is exact only when it ends within R
                                 if (exh || (!start_ok && !(r2 < R2 - gr))) {
                                     js = nl_exhaustive_staged(sm, g, p, sc, base, first, n, jlo, jhi, C[0], C[1], C[2],
