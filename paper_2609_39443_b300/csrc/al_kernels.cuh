@@ -77,7 +77,13 @@ struct LineG {                   // per line, rebuilt every step
     float Lmin, Lmax;            // shortest / longest segment (cells)
     float rho2;                  // regular == 2: a walk may start at a node within sqrt(rho2) cells
     int wshift;                  // fixed-point weights: omega eta / eta0 in units of 2^-wshift
+    float R2f, ie2f, eta0f;      // FP32 copies of R2c, inv_eps2c_l2, eta0 (no conversions in the hot loops)
 };
+
+// per-line constant in the field precision, without an FP64 conversion for FP32
+template <typename T> __device__ __forceinline__ T lgc(double d, float f);
+template <> __device__ __forceinline__ float lgc<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double lgc<double>(double d, float) { return d; }
 
 template <typename T>
 struct Scratch {
@@ -649,6 +655,9 @@ __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
         lg.inv_eps2c = 1.0 / (ec * ec);
         lg.inv_eps2c_l2 = 1.4426950408889634 / (ec * ec);
         lg.eta0 = 1.0 / (PI_D * eps * eps);
+        lg.R2f = (float)lg.R2c;
+        lg.ie2f = (float)lg.inv_eps2c_l2;
+        lg.eta0f = (float)lg.eta0;
         lg.regular = ok2 ? 2 : (ok1 ? 1 : 0);
         lg.first = off;
         lg.n = n;
@@ -986,14 +995,36 @@ __device__ __forceinline__ void w_columns(const WSeg<T> &c, const GridC &g, cons
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void w_finish(const GridC &g, const Scratch<T> &sc, int *, int k, int lane,
-                                         WSink<T, false> &sink) {
-    const double ta = warp_total(sink.wa), tb = warp_total(sink.wb);
-    if (lane == 0) {
-        sc.segWa[k] = ta * g.V;
-        sc.segWb[k] = tb * g.V;
+// the segment's two weight sums (in units of V): a float-float pair in the
+// slot's 8 bytes for FP32 instances (combined in FP64 per node by
+// k_normalise), a double for FP64 instances
+__device__ __forceinline__ void w_store(double *slot, const Acc<float> &a) {
+    float h = a.s, l = -a.c;
+    for (int o = 16; o > 0; o >>= 1) {
+        float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+        float s, e;
+        two_sum(h, oh, s, e);
+        e = __fadd_rn(e, __fadd_rn(l, ol));
+        fast_two_sum(s, e, h, l);
     }
+    if ((threadIdx.x & 31) == 0) *reinterpret_cast<float2 *>(slot) = make_float2(h, l);
+}
+__device__ __forceinline__ void w_store(double *slot, const Acc<double> &a) {
+    const double v = warp_total(a);
+    if ((threadIdx.x & 31) == 0) *slot = v;
+}
+template <typename T> __device__ __forceinline__ double w_load(const double *slot);
+template <> __device__ __forceinline__ double w_load<float>(const double *slot) {
+    const float2 v = *reinterpret_cast<const float2 *>(slot);
+    return (double)v.x + (double)v.y;
+}
+template <> __device__ __forceinline__ double w_load<double>(const double *slot) { return *slot; }
+
+template <typename T>
+__device__ __forceinline__ void w_finish(const GridC &, const Scratch<T> &sc, int *, int k, int,
+                                         WSink<T, false> &sink) {
+    w_store(&sc.segWa[k], sink.wa);
+    w_store(&sc.segWb[k], sink.wb);
 }
 template <typename T>
 __device__ __forceinline__ void w_finish(const GridC &, const Scratch<T> &sc, int *status, int, int lane,
@@ -1022,7 +1053,7 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
     c.nseg = (c.n == 1) ? 1 : c.n - 1;
     c.kb = seg_end(k, c.n);
     if (!lg.regular) {                                      // the brick passes take this line
-        if (!SC && lane == 0) { sc.segWa[k] = 0.0; sc.segWb[k] = 0.0; }
+        if (!SC && lane == 0) { sc.segWa[k] = 0.0; sc.segWb[k] = 0.0; }   // zero in both encodings
         return;
     }
     c.klo = 0; c.khi = c.nseg - 1;
@@ -1034,7 +1065,8 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
         c.D[a] = sc.segD[a * np + k];
     }
     c.il2 = sc.segIl2[k];
-    c.R2 = (T)lg.R2c; c.gr = Tr<T>::grr(c.R2); c.ie2 = (T)lg.inv_eps2c_l2; c.eta0 = (T)lg.eta0;
+    c.R2 = lgc<T>(lg.R2c, lg.R2f); c.gr = Tr<T>::grr(c.R2); c.ie2 = lgc<T>(lg.inv_eps2c_l2, lg.ie2f);
+    c.eta0 = lgc<T>(lg.eta0, lg.eta0f);
     const int nn[3] = {g.nx, g.ny, g.nz};
     bool empty = false;
     for (int a = 0; a < 3; ++a) {
@@ -1079,10 +1111,11 @@ __device__ void d_normalise(const GridC &g, const BeamsC &b, const Scratch<T> &s
         // brick pass: fixed-point sum of omega eta / eta0; w = sum eta0 V 2^-wshift
         w = ldexp((double)sc.wfix[k], -lg.wshift) * (lg.eta0 * g.V);
     } else if (n == 1) {
-        w = sc.segWa[k] + sc.segWb[k];
+        w = (w_load<T>(&sc.segWa[k]) + w_load<T>(&sc.segWb[k])) * g.V;
     } else {
-        if (q >= 1) w += sc.segWb[k - 1];
-        if (q <= n - 2) w += sc.segWa[k];
+        if (q >= 1) w += w_load<T>(&sc.segWb[k - 1]);
+        if (q <= n - 2) w += w_load<T>(&sc.segWa[k]);
+        w *= g.V;
     }
     sc.w[k] = w;
     if (w > 0.0) {
@@ -1476,10 +1509,10 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                     sm.e_reg[e] = (lg.regular == 2 && cz_ok <= 0.0f) ? 0 : lg.regular;
                     sm.e_n[e] = lg.n;
                     sm.e_first[e] = lg.first;
-                    sm.e_R2[e] = (T)lg.R2c;
-                    sm.e_gr[e] = Tr<T>::grr((T)lg.R2c);
-                    sm.e_ie2[e] = (T)lg.inv_eps2c_l2;
-                    sm.e_eta0[e] = WP ? (T)lg.wshift : (T)lg.eta0;
+                    sm.e_R2[e] = lgc<T>(lg.R2c, lg.R2f);
+                    sm.e_gr[e] = Tr<T>::grr(lgc<T>(lg.R2c, lg.R2f));
+                    sm.e_ie2[e] = lgc<T>(lg.inv_eps2c_l2, lg.ie2f);
+                    sm.e_eta0[e] = WP ? (T)lg.wshift : lgc<T>(lg.eta0, lg.eta0f);
                     sm.e_rho2[e] = lg.rho2;
                     for (int a = 0; a < 3; ++a) { sm.e_lo[e][a] = lo[a] - blo[a]; sm.e_hi[e][a] = hi[a] - blo[a]; }
                     sm.e_cz[e] = cz_ok;
@@ -1819,23 +1852,21 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
             }
         }
     }
-    double c0 = (double)cs0, c1 = (double)cs1, c2 = (double)cs2;
-    for (int o = 16; o > 0; o >>= 1) {
-        c0 += __shfl_down_sync(0xffffffffu, c0, o);
-        c1 += __shfl_down_sync(0xffffffffu, c1, o);
-        c2 += __shfl_down_sync(0xffffffffu, c2, o);
-        nsupp += __shfl_down_sync(0xffffffffu, nsupp, o);
+    // brick sums of S: compensated within the warp in the field precision,
+    // one FP64 combination per brick
+    {
+        Acc<T> a3[3];
+        a3[0].add(cs0); a3[1].add(cs1); a3[2].add(cs2);
+        for (int a = 0; a < 3; ++a) w_store(&sm.red[a][warp], a3[a]);
     }
-    if (lane == 0) {
-        sm.red[0][warp] = c0; sm.red[1][warp] = c1; sm.red[2][warp] = c2;
-        sm.redi[warp] = nsupp;
-    }
+    for (int o = 16; o > 0; o >>= 1) nsupp += __shfl_down_sync(0xffffffffu, nsupp, o);
+    if (lane == 0) sm.redi[warp] = nsupp;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ns = 0;
         for (int a = 0; a < 3; ++a) {
             double t = 0.0;
-            for (int w = 0; w < SPREAD_THREADS / 32; ++w) t += sm.red[a][w];
+            for (int w = 0; w < SPREAD_THREADS / 32; ++w) t += w_load<T>(&sm.red[a][w]);
             sc.brickSum[a * g.nbrick + br] = t;
         }
         for (int w = 0; w < SPREAD_THREADS / 32; ++w) ns += sm.redi[w];
