@@ -214,9 +214,8 @@ def run_reference(a):
 
 def run_ours(a):
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2609_39443_b300.ranks import instance_seed, max_over_ranks, rank_env
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -230,7 +229,7 @@ def run_ours(a):
             dist.barrier()
     from paper_2609_39443_b300.al import Instance, PHASES, ST_SUPPORT
 
-    wl = _workload(a.workload, rank, a.eps)
+    wl = _workload(a.workload, instance_seed(rank), a.eps)
     inst = Instance(wl, device=f"cuda:{local}")
     tuned = {"weights": "brick", "brick_z": 8, "autotuned": False}
     if a.weights or a.brick_z:
@@ -271,10 +270,7 @@ def run_ours(a):
     clk = clocks.stop()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1)]
     total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks([total_s], dist, f"cuda:{local}")[0]
     value = world * a.steps / total_s
     ph = phases / a.steps
     spread_s = ph[PHASES.index("spread")] / 1e3
@@ -310,10 +306,7 @@ def run_ours(a):
             e2e_step()
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([te], dtype=torch.float64, device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks([te], dist, f"cuda:{local}")[0]
         e2e = {"value": world * n_e2e / te, "unit": "steps/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
@@ -371,15 +364,14 @@ def run_batched(a):
     import torch
     from paper_2609_39443_b300 import workloads as W
     from paper_2609_39443_b300.al import Batch, Instance
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2609_39443_b300.ranks import instance_seed, max_over_ranks, rank_env
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    wls = W.make_batched(rank, a.instances)
+    wls = W.make_batched(instance_seed(rank), a.instances)
     insts = [Instance(w, device=f"cuda:{local}") for w in wls]
     # tile sizes and weight pass: each instance tuned alone (used by the
     # per-instance launches), then the batch's brick height and persistent grid
@@ -414,10 +406,7 @@ def run_batched(a):
     t_batch = timed(batch.run, a.steps)
     t_plain = timed(per_instance, a.steps)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([t_batch, t_plain], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_batch, t_plain = (float(x) for x in t.tolist())
+    t_batch, t_plain = max_over_ranks([t_batch, t_plain], dist, f"cuda:{local}")
     n = len(insts)
     value = world * n * a.steps / t_batch
     cells = sum(w.grid.n_cells for w in wls)
