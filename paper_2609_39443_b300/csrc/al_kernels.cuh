@@ -1543,30 +1543,31 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
             }
             __syncthreads();
             const int ne = sm.nbatch;
-            // ---- stage nodes of the batch ----------------------------------
-            for (int e = 0; e < ne; ++e) {
-                const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e], base = sm.e_base[e];
-                if (jhi < jlo || base < 0) continue;
+            // ---- stage the batch's nodes, all threads over all of them ---------
+            // (slot s belongs to the last entry whose base is <= s: entries without
+            // nodes share the next entry's base)
+            for (int s = threadIdx.x; s < sm.nstaged; s += SPREAD_THREADS) {
+                int lo = 0, hi = ne - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (sm.e_base[mid] <= s) lo = mid; else hi = mid - 1;
+                }
+                const int e = lo, t = s - sm.e_base[e];
                 const int first = sm.e_first[e], n = sm.e_n[e];
-                const int cnt = jhi - jlo + 2;
-                for (int t = threadIdx.x; t < cnt; t += SPREAD_THREADS) {
-                    const int k = first + jlo + t;
-                    const int kn = (n == 1) ? first : k;    // single-node line: copy the node
-                    const int s = base + t;
-                    for (int a = 0; a < 3; ++a) {
-                        sm.P[a][s] = rel(sc.uhi[a * np + kn], sc.ulo[a * np + kn], (a == 0) ? B0 : (a == 1 ? B1 : B2));
-                        sm.M[a][s] = sc.nodeM[a * np + kn];
-                        sm.D[a][s] = sc.segD[a * np + kn];
-                    }
-                    sm.Il2[s] = sc.segIl2[kn];
-                    sm.Tau[s] = sc.nodeTau[kn];
-                    if (WP) {
-                        sm.u.wq[s] = 0ull;
-                    } else {
-                        for (int a = 0; a < 3; ++a) sm.u.s.Fh[a][s] = sc.fhat[a * np + kn];
-                        sm.u.s.sk[s] = kn;
-                        sm.zf[s] = (n != 1 || t == 0) && sc.w[kn] == 0.0;
-                    }
+                const int kn = (n == 1) ? first : first + sm.e_jlo[e] + t;   // single-node line: copy the node
+                for (int a = 0; a < 3; ++a) {
+                    sm.P[a][s] = rel(sc.uhi[a * np + kn], sc.ulo[a * np + kn], (a == 0) ? B0 : (a == 1 ? B1 : B2));
+                    sm.M[a][s] = sc.nodeM[a * np + kn];
+                    sm.D[a][s] = sc.segD[a * np + kn];
+                }
+                sm.Il2[s] = sc.segIl2[kn];
+                sm.Tau[s] = sc.nodeTau[kn];
+                if (WP) {
+                    sm.u.wq[s] = 0ull;
+                } else {
+                    for (int a = 0; a < 3; ++a) sm.u.s.Fh[a][s] = sc.fhat[a * np + kn];
+                    sm.u.s.sk[s] = kn;
+                    sm.zf[s] = (n != 1 || t == 0) && sc.w[kn] == 0.0;
                 }
             }
             __syncthreads();
@@ -1584,16 +1585,23 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                     continue;
                 }
                 const float zc = lane + 0.5f;
-                // the candidate segment containing the height zc, else the end one nearest to it
-                int jc = -1;
-                for (int j = jlo; j <= jhi; ++j) {
-                    const int ss = base + (j - jlo);
-                    const float za = (float)sm.P[2][ss], zb = za + (float)sm.D[2][ss];
-                    if (fminf(za, zb) <= zc && zc <= fmaxf(za, zb)) { jc = j; break; }
-                }
-                if (jc < 0) {
-                    const float za = (float)sm.P[2][base], zb = (float)sm.P[2][base + (jhi - jlo + 1)];
-                    jc = (fabsf(zc - za) < fabsf(zc - zb)) ? jlo : jhi;
+                // the candidate segment containing the height zc, else the end one nearest
+                // to it: the candidates all climb (or all descend), so node heights are
+                // monotone and a bisection finds it
+                const float z0 = (float)sm.P[2][base], z1 = (float)sm.P[2][base + (jhi - jlo + 1)];
+                const float sgn = z1 >= z0 ? 1.0f : -1.0f;
+                int jc;
+                if (sgn * (zc - z0) <= 0.0f) {
+                    jc = jlo;
+                } else if (sgn * (zc - z1) >= 0.0f) {
+                    jc = jhi;
+                } else {
+                    int lo = jlo, hi = jhi;                    // largest j with sgn (z_j - zc) <= 0
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (sgn * ((float)sm.P[2][base + (mid - jlo)] - zc) <= 0.0f) lo = mid; else hi = mid - 1;
+                    }
+                    jc = lo;
                 }
                 const int ss = base + (jc - jlo);
                 const float d0 = (float)sm.D[0][ss], d1 = (float)sm.D[1][ss], dz = (float)sm.D[2][ss];
