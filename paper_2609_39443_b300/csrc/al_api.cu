@@ -80,6 +80,7 @@ struct al_grid_s {
     int *statusInt = nullptr;
     double *totalsInt = nullptr;
     int *hasPrev = nullptr;           // device flag: f_prev is valid
+    int *anyIrr = nullptr;            // device flag: some line without a walk certificate
 
     // tracing
     bool trace = false;
@@ -164,7 +165,7 @@ extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
     if ((e = dalloc(&g->brickSum, 3 * (size_t)g->nbrick_max)) != cudaSuccess ||
         (e = dalloc(&g->scatSum, 3)) != cudaSuccess ||
         (e = dalloc(&g->statusInt, AL_STATUS_N)) != cudaSuccess || (e = dalloc(&g->totalsInt, 6)) != cudaSuccess ||
-        (e = dalloc(&g->hasPrev, 1)) != cudaSuccess) {
+        (e = dalloc(&g->hasPrev, 1)) != cudaSuccess || (e = dalloc(&g->anyIrr, 1)) != cudaSuccess) {
         int rc = cuda_fail(e, "cudaMalloc");
         al_destroy(g);
         return rc;
@@ -254,6 +255,7 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     }
     AL_CUDA(cudaMemset(g->mask, 0, ((size_t)g->nbrick_max * g->mask_words ? (size_t)g->nbrick_max * g->mask_words : 1) * sizeof(uint32_t)));
     AL_CUDA(cudaMemset(g->hasPrev, 0, sizeof(int)));
+    AL_CUDA(cudaMemset(g->anyIrr, 0, sizeof(int)));
     g->loaded = true;
     return AL_OK;
 }
@@ -322,7 +324,7 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     sc.segIl2 = (T *)g->segIl2; sc.nodeM = (T *)g->nodeM; sc.nodeTau = g->nodeTau;
     sc.segWa = g->segWa; sc.segWb = g->segWb; sc.wfix = g->wfix; sc.w = g->w; sc.fhat = (T *)g->fhat; sc.lineF = g->lineF;
     sc.lines = g->lines; sc.mask = g->mask; sc.brickSum = g->brickSum; sc.scatSum = g->scatSum;
-    sc.hasPrev = g->hasPrev;
+    sc.hasPrev = g->hasPrev; sc.anyIrr = g->anyIrr;
     BeamsC &bc = I.b;
     bc.n_lines = g->n_lines; bc.n_points = np; bc.mask_words = g->mask_words;
     bc.line_off = g->d_line_off; bc.line_of = g->d_line_of;
@@ -445,7 +447,7 @@ extern "C" int al_destroy(al_grid g) {
     cudaDeviceSynchronize();
     if (g->trace) al_trace_enable(g, 0);
     free_beams(g);
-    void *ptrs[] = {g->brickSum, g->scatSum, g->statusInt, g->totalsInt, g->hasPrev};
+    void *ptrs[] = {g->brickSum, g->scatSum, g->statusInt, g->totalsInt, g->hasPrev, g->anyIrr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete g;

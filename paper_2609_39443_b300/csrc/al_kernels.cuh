@@ -104,6 +104,7 @@ struct Scratch {
     double *brickSum;            // [3][nbrick] sum of S per brick
     double *scatSum;             // [3] sum of S added by the scatter form
     int *hasPrev;                // [1] a previous relaxed force exists (set by k_totals)
+    int *anyIrr;                 // [1] some line has no walk certificate (set by k_lines)
 };
 
 template <typename T>
@@ -461,6 +462,7 @@ __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, 
         p.F[a][i] = f * L;
     }
     sc.wfix[i] = 0ull;                                   // fixed-point weights start at zero
+    if (i == 0) *sc.anyIrr = 0;
     // projection positions in cell units
     for (int a = 0; a < 3; ++a) {
         T uh;
@@ -672,7 +674,10 @@ __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
         int sh = 62 - (int)ceilf(log2f(Q));
         lg.wshift = max(20, min(sh, 60));
         sc.lines[l] = lg;
-        if (lg.regular == 0 && n > 0) atomicAdd(&status[ST_IRREGULAR], 1);
+        if (lg.regular == 0 && n > 0) {
+            atomicAdd(&status[ST_IRREGULAR], 1);
+            *sc.anyIrr = 1;
+        }
     }
 }
 
@@ -1157,7 +1162,7 @@ struct SpreadSmem {
     } u;
     unsigned char zf[NN];        // spread: the node has w_k = 0 (deposit)
     int list[LIST];              // candidate lines of this brick (line order)
-    int nlist, nbatch, nstaged;
+    int nlist, nbatch, nstaged, more;
     int e_line[ENT], e_jlo[ENT], e_jhi[ENT], e_base[ENT], e_reg[ENT], e_n[ENT], e_first[ENT];
     float e_lo[ENT][3], e_hi[ENT][3];
     T e_R2[ENT], e_gr[ENT], e_ie2[ENT], e_eta0[ENT];
@@ -1398,6 +1403,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     const int byi = rem / g.nbx, bxi = rem - byi * g.nbx;
     const int B0 = bxi * BX, B1 = byi * BY, B2 = bzi * BZ;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (WP && g.wmode != 0 && *sc.anyIrr == 0) return;      // the segment pass took every line
     const int nzb = min(BZ, g.nz - B2);              // layers of this brick inside the grid
     const int nxb = min(BX, g.nx - B0), nyb = min(BY, g.ny - B1);
     int nsupp = 0;                                   // (cell, line) pairs within 3 eps
@@ -1409,48 +1415,57 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     const float blo[3] = {(float)B0, (float)B1, (float)B2};
     const float bhi[3] = {(float)(B0 + BX), (float)(B1 + BY), (float)(B2 + BZ)};
 
-    constexpr int CH = SM::LIST / 32;                // mask words per chunk
-    for (int w0 = 0; w0 < W; w0 += CH) {
-        // ---- candidate lines from CH mask words, in line order -------------
+    // candidate lines in line order, up to LIST per pass: warp 0's lanes each
+    // take a contiguous run of mask words, so a prefix over lanes keeps line
+    // order; bricks with more than LIST candidates take several passes (the
+    // spread clears the words in the last one)
+    const bool keep_certified = WP ? (g.wmode == 0) : (g.smode == 0);
+    const int wper = (W + 31) / 32;
+    for (int pass = 0;; ++pass) {
         __syncthreads();
         if (warp == 0) {
-            const bool mine = lane < CH && w0 + lane < W;
-            uint32_t m = mine ? mrow[w0 + lane] : 0u;
-            if (WP) {
-                if (g.wmode != 0) {                      // segment pass covers certified lines
+            const int wa = min(W, lane * wper), wb = min(W, wa + wper);
+            int cnt = 0;
+            for (int w = wa; w < wb; ++w) {
+                uint32_t m = mrow[w];
+                if (!keep_certified) {                   // the segment pass takes certified lines
                     uint32_t keep = 0u, t = m;
                     while (t) {
                         const int bit = __ffs(t) - 1;
                         t &= t - 1;
-                        if (!sc.lines[((w0 + lane) << 5) + bit].regular) keep |= 1u << bit;
+                        if (!sc.lines[(w << 5) + bit].regular) keep |= 1u << bit;
                     }
                     m = keep;
                 }
-            } else if (mine && m) {
-                mrow[w0 + lane] = 0u;                    // clear for the next step
-                if (g.smode != 0) {                      // the scatter form takes certified lines
-                    uint32_t keep = 0u, t = m;
-                    while (t) {
-                        const int bit = __ffs(t) - 1;
-                        t &= t - 1;
-                        if (!sc.lines[((w0 + lane) << 5) + bit].regular) keep |= 1u << bit;
-                    }
-                    m = keep;
-                }
+                cnt += __popc(m);
             }
-            int cnt = __popc(m), pre = cnt;
+            int pre = cnt;
             for (int o = 1; o < 32; o <<= 1) {
                 int v = __shfl_up_sync(0xffffffffu, pre, o);
                 if (lane >= o) pre += v;
             }
-            int total = __shfl_sync(0xffffffffu, pre, 31);
+            const int total = __shfl_sync(0xffffffffu, pre, 31);
+            const int lo = pass * SM::LIST, hi = lo + SM::LIST;
             int pos = pre - cnt;
-            while (m) {
-                int bit = __ffs(m) - 1;
-                m &= m - 1;
-                sm.list[pos++] = ((w0 + lane) << 5) + bit;
+            if (pos < hi && pos + cnt > lo) {
+                for (int w = wa; w < wb; ++w) {
+                    uint32_t m = mrow[w];
+                    while (m) {
+                        const int bit = __ffs(m) - 1;
+                        m &= m - 1;
+                        const int l = (w << 5) + bit;
+                        if (!keep_certified && sc.lines[l].regular) continue;
+                        if (pos >= lo && pos < hi) sm.list[pos - lo] = l;
+                        ++pos;
+                    }
+                }
             }
-            if (lane == 0) sm.nlist = total;             // <= 32 * CH = LIST
+            if (!WP && total <= hi)
+                for (int w = wa; w < wb; ++w) mrow[w] = 0u;      // clear for the next step
+            if (lane == 0) {
+                sm.nlist = max(0, min(total - lo, SM::LIST));
+                sm.more = total > hi;
+            }
         }
         __syncthreads();
         const int nlist = sm.nlist;
@@ -1842,6 +1857,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
             li += ne;
             __syncthreads();
         }
+        if (!sm.more) break;
     }
     if (WP) return;
     // ---- write every cell of the brick once; brick sums of S -----------------
