@@ -38,7 +38,7 @@ class _Beams(C.Structure):
                 ("ell_s", C.POINTER(C.c_double)), ("alpha_f", C.POINTER(C.c_double)),
                 ("cv_len", C.POINTER(C.c_double)), ("n_p", C.c_double * 3),
                 ("g_up", C.c_double * 3), ("tau", C.c_double), ("sample_mode", C.c_int),
-                ("drag_mode", C.c_int)]
+                ("drag_mode", C.c_int), ("cm_n", C.POINTER(C.c_double)), ("cm_t", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -53,7 +53,7 @@ def _load():
         lib = C.CDLL(LIB_PATH)
         dp = C.POINTER(C.c_double)
         lib.or_point_step.argtypes = [C.POINTER(_Grid), C.POINTER(_Beams), dp, dp, dp, dp, dp, dp,
-                                      dp, dp, dp, dp, C.POINTER(C.c_longlong)]
+                                      dp, dp, C.c_double, dp, dp, dp, dp, C.POINTER(C.c_longlong)]
         lib.or_project.argtypes = [C.POINTER(_Grid), C.POINTER(_Beams), dp, dp, C.c_int,
                                    C.POINTER(C.c_ubyte), dp, dp, C.POINTER(C.c_longlong), C.c_int]
         lib.or_sample_field.argtypes = [C.POINTER(_Grid), dp, C.c_int, C.c_int, dp, dp]
@@ -84,9 +84,12 @@ class _BeamsHold:
     def __init__(self, b):
         self.off = np.ascontiguousarray(b.line_off, dtype=np.int32)
         self.arr = [_f64(x) for x in (b.d, b.cdn, b.cdt, b.eps, b.ell_s, b.alpha_f, b.cv_len)]
+        cm_n, cm_t = getattr(b, "cm_n", None), getattr(b, "cm_t", None)
+        self.cm = [_f64(cm_n), _f64(cm_t)] if cm_n is not None else [None, None]
         self.s = _Beams(int(b.n_lines), _ptr(self.off, C.c_int), *[_ptr(a) for a in self.arr],
                         (C.c_double * 3)(*map(float, b.n_p)), (C.c_double * 3)(*map(float, b.g_up)),
-                        float(b.tau), int(b.sample_mode), int(b.drag_mode))
+                        float(b.tau), int(b.sample_mode), int(b.drag_mode),
+                        _ptr(self.cm[0]), _ptr(self.cm[1]))
 
 
 def sample(grid, field, mode, p):
@@ -108,11 +111,14 @@ def point_step(grid, beams, step, f_prev=None):
     U, al = _f64(step.U), _f64(step.alpha)
     P, Pd, T = _f64(step.P), _f64(step.Pdot), _f64(step.tangent) if beams.tangents_given else None
     fp = _f64(f_prev)
+    Up, Pdd = _f64(getattr(step, "U_prev", None)), _f64(getattr(step, "Pddot", None))
+    dt = float(getattr(step, "dt", 0.0) or 0.0)
     F, f, et, Ps = (np.zeros((3, np_)) for _ in range(4))
     st = np.zeros(ST_N, dtype=np.int64)
     g, bh = _grid(grid), _BeamsHold(beams)
     lib.or_point_step(C.byref(g), C.byref(bh.s), _ptr(U), _ptr(al), _ptr(P), _ptr(Pd), _ptr(T),
-                      _ptr(fp), _ptr(F), _ptr(f), _ptr(et), _ptr(Ps), _ptr(st, C.c_longlong))
+                      _ptr(fp), _ptr(Up), _ptr(Pdd), dt, _ptr(F), _ptr(f), _ptr(et), _ptr(Ps),
+                      _ptr(st, C.c_longlong))
     return {"F": F, "f": f, "e_t": et, "P_s": Ps, "status": st}
 
 

@@ -57,6 +57,8 @@ typedef struct {
     double n_p[3], g_up[3], tau;
     int sample_mode;                  /* 0 trilinear, 1 containing cell */
     int drag_mode;                    /* 0 Eq. almLineForce, 1 Eq. fext_drag */
+    const double *cm_n, *cm_t;        /* per line, added-mass coefficients of Eq. fext_addedmass;
+                                         NULL: no inertia term (the paper's model) */
 } or_beams;
 
 /* status counters (same meaning as the CUDA library's) */
@@ -180,6 +182,7 @@ int or_point_step(const or_grid *g, const or_beams *b,
                   const double *U, const double *alpha,
                   const double *P, const double *Pdot, const double *tangent,
                   const double *f_prev,
+                  const double *U_prev, const double *Pddot, double dt,
                   double *F, double *f_out, double *e_t_out, double *P_s_out,
                   long long *status)
 {
@@ -246,6 +249,27 @@ int or_point_step(const or_grid *g, const or_beams *b,
                         double mt = sqrt(dot3(Ut, Ut)), mn = sqrt(dot3(Un, Un));
                         for (int a = 0; a < 3; ++a)
                             fstar[a] = half * (b->cdt[l] * mt * Ut[a] + b->cdn[l] * mn * Un[a]);
+                    }
+                    if (b->cm_n) {
+                        /* Eq. fext_addedmass: fluid acceleration a_f = (U - U_prev) / dt
+                         * sampled at P_s with the same operator, beam acceleration a_b;
+                         * the added-mass reaction follows the fluid's acceleration
+                         * relative to the beam, a_f - a_b, split along the tangent like
+                         * the drag, plus the Froude-Krylov term rho A a_f */
+                        double af[3] = {0.0, 0.0, 0.0}, ab[3] = {0.0, 0.0, 0.0};
+                        if (U_prev) {
+                            double Up[3];
+                            or_sample(g, U_prev, 3, b->sample_mode, Ps, Up);   /* inside: checked above */
+                            for (int a = 0; a < 3; ++a) af[a] = (Us[a] - Up[a]) / dt;
+                        }
+                        if (Pddot) for (int a = 0; a < 3; ++a) ab[a] = Pddot[a * np + i];
+                        double ar[3], art, area = 0.25 * OR_PI * b->d[l] * b->d[l];
+                        for (int a = 0; a < 3; ++a) ar[a] = af[a] - ab[a];
+                        art = dot3(ar, t);
+                        for (int a = 0; a < 3; ++a) {
+                            double at = art * t[a], an = ar[a] - at;
+                            fstar[a] += rho * area * (b->cm_t[l] * at + b->cm_n[l] * an + af[a]);
+                        }
                     }
                 }
             }

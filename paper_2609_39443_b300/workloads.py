@@ -73,6 +73,8 @@ class BeamSpec:
     sample_mode: int = SAMPLE_TRILINEAR
     drag_mode: int = DRAG_DISCRETE
     tangents_given: bool = False
+    cm_n: Optional[np.ndarray] = None   # float64 [n_lines] added-mass coefficients (None: no inertia term)
+    cm_t: Optional[np.ndarray] = None
 
     @property
     def n_lines(self) -> int:
@@ -91,6 +93,9 @@ class StepInput:
     alpha: Optional[np.ndarray] = None       # (N_c,)
     P_spread: Optional[np.ndarray] = None    # (3, N_p) positions used by the projection
     tangent: Optional[np.ndarray] = None     # (3, N_p) caller tangents
+    U_prev: Optional[np.ndarray] = None      # (3, N_c) fluid velocity one time step earlier
+    Pddot: Optional[np.ndarray] = None       # (3, N_p) actuator-point accelerations
+    dt: float = 0.0                          # time step between U_prev and U (s)
 
 
 @dataclass

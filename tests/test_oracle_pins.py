@@ -212,6 +212,79 @@ def test_inclined_cylinder_closed_form(drag_mode):
     assert np.linalg.norm(F[:, 3] - (F[:, 3] @ t) * t) == pytest.approx(0.5 * rho * d * cdn * U0 ** 2 * np.sin(theta) ** p, rel=1e-13)
 
 
+# ----------------------------------------------------------------------------
+# inertia (Eq. fext_addedmass; the paper's model has C_Mn = C_Mt = 0)
+# ----------------------------------------------------------------------------
+
+def _inertia_workload(P, U, U_prev, dt, *, Pddot=None, cm_n=1.0, cm_t=0.0, cdn=0.0, cdt=0.0, rho=1000.0, d=0.02):
+    g = GridSpec(60, 24, 60, 0.01, rho_const=rho)
+    wl = _line_workload(P, U, grid=g, cv=0.01, per_line=dict(d=d, cdn=cdn, cdt=cdt))
+    wl.beams.cm_n = np.full(1, float(cm_n))
+    wl.beams.cm_t = np.full(1, float(cm_t))
+    wl.step.U_prev, wl.step.dt = U_prev, dt
+    wl.step.Pddot = Pddot
+    return wl
+
+
+def _vertical(n=8):
+    return np.stack([np.full(n, 0.3), np.full(n, 0.12), 0.1 + 0.01 * np.arange(n)])
+
+
+@pytest.mark.parametrize("cm_n", [0.0, 1.0, 0.7])
+def test_inertia_in_uniformly_accelerating_flow(cm_n):
+    """A fixed cylinder in a uniform flow accelerating at a: f = rho A (1 + C_Mn) a
+    (the classical Morison inertia coefficient; 1 is the Froude-Krylov part)."""
+    rho, d, a, dt, U0 = 1000.0, 0.02, 0.8, 0.01, 0.3
+    P = _vertical()
+    g = GridSpec(60, 24, 60, 0.01, rho_const=rho)
+    wl = _inertia_workload(P, _uniform(g, (U0, 0, 0)), _uniform(g, (U0 - a * dt, 0, 0)), dt, cm_n=cm_n)
+    f = oracle.point_step(wl.grid, wl.beams, wl.step)["f"]
+    A = np.pi * d * d / 4
+    np.testing.assert_allclose(f[0], rho * A * (1.0 + cm_n) * a, rtol=1e-12)
+    np.testing.assert_allclose(f[1:], 0.0, atol=1e-12)
+
+
+def test_inertia_of_an_accelerating_cylinder_in_still_fluid():
+    """The added mass opposes the body's acceleration: f = -rho A C_Mn a_b."""
+    rho, d, cm = 1000.0, 0.02, 1.3
+    P = _vertical()
+    g = GridSpec(60, 24, 60, 0.01, rho_const=rho)
+    ab = np.array([0.5, -0.2, 0.0])
+    wl = _inertia_workload(P, _uniform(g, (0, 0, 0)), _uniform(g, (0, 0, 0)), 0.01,
+                           Pddot=np.repeat(ab[:, None], P.shape[1], 1), cm_n=cm, cm_t=0.4)
+    f = oracle.point_step(wl.grid, wl.beams, wl.step)["f"]
+    A = np.pi * d * d / 4
+    np.testing.assert_allclose(f, np.repeat((-rho * A * cm * ab)[:, None], P.shape[1], 1), rtol=1e-12, atol=1e-15)
+
+
+def test_inertia_splits_along_the_tangent():
+    """An inclined cylinder in flow accelerating along x: the tangential and
+    normal parts of the acceleration take C_Mt and C_Mn, the Froude-Krylov
+    part is along x."""
+    theta, rho, d, a, dt, cmn, cmt = 0.5, 1000.0, 0.02, 0.9, 0.02, 1.1, 0.25
+    t = np.array([np.cos(theta), 0.0, np.sin(theta)])
+    P = np.array([0.2, 0.12, 0.2])[:, None] + 0.01 * np.arange(8)[None] * t[:, None]
+    g = GridSpec(60, 24, 60, 0.01, rho_const=rho)
+    wl = _inertia_workload(P, _uniform(g, (0.4, 0, 0)), _uniform(g, (0.4 - a * dt, 0, 0)), dt,
+                           cm_n=cmn, cm_t=cmt)
+    f = oracle.point_step(wl.grid, wl.beams, wl.step)["f"]
+    af = np.array([a, 0.0, 0.0])
+    at = (af @ t) * t
+    want = rho * np.pi * d * d / 4 * (cmt * at + cmn * (af - at) + af)
+    np.testing.assert_allclose(f, np.repeat(want[:, None], 8, 1), rtol=1e-12, atol=1e-14)
+
+
+def test_inertia_adds_to_the_drag():
+    """Drag from the current velocity plus the inertia term, nothing else."""
+    rho, d, a, dt, U0, cdn = 1000.0, 0.02, 0.6, 0.01, 0.5, 1.2
+    P = _vertical()
+    g = GridSpec(60, 24, 60, 0.01, rho_const=rho)
+    wl = _inertia_workload(P, _uniform(g, (U0, 0, 0)), _uniform(g, (U0 - a * dt, 0, 0)), dt, cm_n=1.0, cdn=cdn)
+    f = oracle.point_step(wl.grid, wl.beams, wl.step)["f"]
+    want = 0.5 * rho * d * cdn * U0 * U0 + rho * np.pi * d * d / 4 * 2.0 * a
+    np.testing.assert_allclose(f[0], want, rtol=1e-12)
+
+
 def test_relative_velocity_is_galilean():
     rng = np.random.default_rng(5)
     wl = W.make_random(11, 24, 20, 22, n_lines=3, kinds=("stem",))
