@@ -105,6 +105,13 @@ typedef struct {
     int sample_mode;           /* AL_SAMPLE_* (both samples use the same operator) */
     int drag_mode;             /* AL_DRAG_* */
     int tangents_given;        /* 1: al_step_in.tangent is used instead of the centreline tangent */
+    /* Morison inertia (Eq. fext_addedmass; not part of the paper's model, which
+     * has C_Mn = C_Mt = 0): per-line added-mass coefficients, both NULL for a
+     * drag-only closure.  With them, f* gains rho A (C_Mt a_t + C_Mn a_n + a_f)
+     * with A = pi d^2 / 4, a_f = (U - U_prev)/dt sampled at P_s with the same
+     * operator, and a = a_f - a_b (the fluid's acceleration relative to the
+     * beam) split along the tangent. */
+    const double *cm_n, *cm_t; /* [n_lines] or NULL */
 } al_beam_desc;
 
 /* Inputs of one step: DEVICE pointers, element type per grid precision,
@@ -118,6 +125,10 @@ typedef struct {
     const void *P_spread[3];   /* [N_p] optional positions for the projection (Algorithm 1,
                                   step 7: positions after the beam update); NULL: P */
     const void *tangent[3];    /* [N_p] optional tangents (used iff tangents_given) */
+    /* inertia term only (al_beam_desc.cm_n set), otherwise ignored: */
+    const void *U_prev[3];     /* [N_c] fluid velocity dt earlier; NULL: a_f = 0 */
+    const void *Pddot[3];      /* [N_p] actuator-point accelerations (m/s^2); NULL: a_b = 0 */
+    double dt;                 /* time between U_prev and U (s), > 0 when U_prev is given */
 } al_step_in;
 
 /* Outputs of one step: DEVICE pointers. */

@@ -43,12 +43,14 @@ class BeamDesc(C.Structure):
     _fields_ = [("n_lines", C.c_int), ("line_off", C.POINTER(C.c_int)), ("d", _dp), ("cdn", _dp),
                 ("cdt", _dp), ("eps", _dp), ("ell_s", _dp), ("alpha_f", _dp), ("cv_len", _dp),
                 ("n_p", C.c_double * 3), ("g_up", C.c_double * 3), ("tau", C.c_double),
-                ("sample_mode", C.c_int), ("drag_mode", C.c_int), ("tangents_given", C.c_int)]
+                ("sample_mode", C.c_int), ("drag_mode", C.c_int), ("tangents_given", C.c_int),
+                ("cm_n", _dp), ("cm_t", _dp)]
 
 
 class StepIn(C.Structure):
     _fields_ = [("U", _vp * 3), ("alpha", _vp), ("P", _vp * 3), ("Pdot", _vp * 3),
-                ("P_spread", _vp * 3), ("tangent", _vp * 3)]
+                ("P_spread", _vp * 3), ("tangent", _vp * 3), ("U_prev", _vp * 3), ("Pddot", _vp * 3),
+                ("dt", C.c_double)]
 
 
 class StepOut(C.Structure):
@@ -139,15 +141,23 @@ class BeamArrays:
         def p(a, ct=C.c_double):
             return a.ctypes.data_as(C.POINTER(ct))
 
+        cm_n, cm_t = getattr(beams, "cm_n", None), getattr(beams, "cm_t", None)
+        self.cm = [np.ascontiguousarray(x, dtype=np.float64) for x in (cm_n, cm_t)] if cm_n is not None else []
         self.desc = BeamDesc(int(beams.n_lines), p(self.off, C.c_int), *[p(a) for a in self.arr],
                              (C.c_double * 3)(*map(float, beams.n_p)), (C.c_double * 3)(*map(float, beams.g_up)),
                              float(beams.tau), int(beams.sample_mode), int(beams.drag_mode),
-                             int(bool(beams.tangents_given)))
+                             int(bool(beams.tangents_given)), *([p(a) for a in self.cm] or [None, None]))
 
 
-def step_descriptors(U, P, Pdot, S, F, *, alpha=None, P_spread=None, tangent=None, totals=None, status=None):
+def step_descriptors(U, P, Pdot, S, F, *, alpha=None, P_spread=None, tangent=None, totals=None, status=None,
+                     U_prev=None, Pddot=None, dt=0.0):
     """al_step_in / al_step_out for the given device tensors."""
     sin = StepIn()
+    for a, t in enumerate(_three(U_prev)):
+        sin.U_prev[a] = _ptr(t)
+    for a, t in enumerate(_three(Pddot)):
+        sin.Pddot[a] = _ptr(t)
+    sin.dt = float(dt)
     for a, t in enumerate(_three(U)):
         sin.U[a] = _ptr(t)
     for a, t in enumerate(_three(P)):
@@ -192,12 +202,12 @@ class Grid:
         self.n_lines = int(beams.n_lines)
 
     def step(self, U, P, Pdot, S, F, *, alpha=None, P_spread=None, tangent=None, totals=None,
-             status=None, stream=None) -> None:
+             status=None, stream=None, U_prev=None, Pddot=None, dt=0.0) -> None:
         """Enqueue one coupling step.  U, S: (3, N_c); P, Pdot, F, P_spread,
         tangent: (3, N_p) CUDA tensors of the grid precision (or sequences
         of three 1-D tensors); totals: float64[6]; status: int32[16]."""
         sin, sout = step_descriptors(U, P, Pdot, S, F, alpha=alpha, P_spread=P_spread, tangent=tangent,
-                                     totals=totals, status=status)
+                                     totals=totals, status=status, U_prev=U_prev, Pddot=Pddot, dt=dt)
         check(lib().al_sample_drag_spread(self.h, C.byref(sin), C.byref(sout), _stream_ptr(stream)),
               "al_sample_drag_spread")
 
@@ -253,6 +263,8 @@ class Instance:
 
         self.U, self.P, self.Pdot = dev(s.U), dev(s.P), dev(s.Pdot)
         self.alpha, self.P_spread, self.tangent = dev(s.alpha), dev(s.P_spread), dev(s.tangent)
+        self.U_prev, self.Pddot = dev(getattr(s, "U_prev", None)), dev(getattr(s, "Pddot", None))
+        self.dt_prev = float(getattr(s, "dt", 0.0) or 0.0)
         self.S = torch.empty((3, wl.grid.n_cells), dtype=dt, device=device)
         self.F = torch.empty((3, max(wl.beams.n_points, 1)), dtype=dt, device=device)
         self.totals = torch.zeros(6, dtype=torch.float64, device=device)
@@ -263,7 +275,8 @@ class Instance:
     def step(self, stream=None):
         self.grid.step(self.U, self.P, self.Pdot, self.S, self.F, alpha=self.alpha, P_spread=self.P_spread,
                        tangent=self.tangent if self.wl.beams.tangents_given else None,
-                       totals=self.totals, status=self.status, stream=stream)
+                       totals=self.totals, status=self.status, stream=stream,
+                       U_prev=self.U_prev, Pddot=self.Pddot, dt=self.dt_prev)
 
     def set_points(self, P=None, Pdot=None, P_spread=None):
         import torch
@@ -286,7 +299,8 @@ class Instance:
         return step_descriptors(self.U, self.P, self.Pdot, self.S, self.F, alpha=self.alpha,
                                 P_spread=self.P_spread,
                                 tangent=self.tangent if self.wl.beams.tangents_given else None,
-                                totals=self.totals, status=self.status)
+                                totals=self.totals, status=self.status,
+                                U_prev=self.U_prev, Pddot=self.Pddot, dt=self.dt_prev)
 
     def close(self):
         self.grid.close()

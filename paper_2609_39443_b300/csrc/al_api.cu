@@ -62,7 +62,7 @@ struct al_grid_s {
     int n_lines = 0, n_points = 0, mask_words = 0;
     int *d_line_off = nullptr, *d_line_of = nullptr;
     double *d_d = nullptr, *d_cdn = nullptr, *d_cdt = nullptr, *d_eps = nullptr, *d_ell = nullptr,
-           *d_af = nullptr, *d_cvl = nullptr;
+           *d_af = nullptr, *d_cvl = nullptr, *d_cmn = nullptr, *d_cmt = nullptr;
     al_beam_desc bd{};
 
     // per-point scratch (element type per precision)
@@ -93,12 +93,12 @@ static void trace_mark(al_grid g, int i, cudaStream_t st) {
 
 static void free_beams(al_grid g) {
     void *ptrs[] = {g->d_line_off, g->d_line_of, g->d_d, g->d_cdn, g->d_cdt, g->d_eps, g->d_ell, g->d_af,
-                    g->d_cvl, g->fprev, g->uhi, g->segD, g->segIl2, g->nodeM, g->fhat, g->ulo,
+                    g->d_cvl, g->d_cmn, g->d_cmt, g->fprev, g->uhi, g->segD, g->segIl2, g->nodeM, g->fhat, g->ulo,
                     g->nodeTau, g->segWa, g->segWb, g->w, g->lineF, g->lines, g->mask, g->wfix};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     g->d_line_off = g->d_line_of = nullptr;
-    g->d_d = g->d_cdn = g->d_cdt = g->d_eps = g->d_ell = g->d_af = g->d_cvl = nullptr;
+    g->d_d = g->d_cdn = g->d_cdt = g->d_eps = g->d_ell = g->d_af = g->d_cvl = g->d_cmn = g->d_cmt = nullptr;
     g->fprev = g->uhi = g->segD = g->segIl2 = g->nodeM = g->fhat = nullptr;
     g->ulo = g->nodeTau = nullptr;
     g->segWa = g->segWb = g->w = g->lineF = nullptr;
@@ -180,6 +180,7 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     if (b.n_lines < 0) return AL_ERR_ARG;
     if (b.n_lines > 0 && (!b.line_off || !b.d || !b.cdn || !b.cdt || !b.eps || !b.ell_s || !b.alpha_f))
         return AL_ERR_ARG;
+    if ((b.cm_n == nullptr) != (b.cm_t == nullptr)) return AL_ERR_ARG;      // both or neither
     if (b.sample_mode != AL_SAMPLE_TRILINEAR && b.sample_mode != AL_SAMPLE_CELL) return AL_ERR_ARG;
     if (b.drag_mode != AL_DRAG_DISCRETE && b.drag_mode != AL_DRAG_SPLIT) return AL_ERR_ARG;
     if (!(b.tau >= 0.0)) return AL_ERR_ARG;
@@ -195,6 +196,7 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
                 return AL_ERR_ARG;
             // the kernel support 3 eps must span fewer than 2^20 cells
             if (3.0 * b.eps[l] / g->d.dx > 1048576.0) return AL_ERR_ARG;
+            if (b.cm_n && (!std::isfinite(b.cm_n[l]) || !std::isfinite(b.cm_t[l]))) return AL_ERR_ARG;
         }
         np = b.line_off[b.n_lines];
         if (np > 0 && !b.cv_len) return AL_ERR_ARG;
@@ -220,6 +222,7 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     A(&g->d_line_of, (size_t)np);
     A(&g->d_d, nl); A(&g->d_cdn, nl); A(&g->d_cdt, nl); A(&g->d_eps, nl); A(&g->d_ell, nl); A(&g->d_af, nl);
     A(&g->d_cvl, (size_t)np);
+    if (b.cm_n) { A(&g->d_cmn, nl); A(&g->d_cmt, nl); }
     AB(&g->fprev, n3); AB(&g->uhi, n3); AB(&g->segD, n3); AB(&g->segIl2, (size_t)np); AB(&g->nodeM, n3);
     AB(&g->fhat, n3);
     A(&g->ulo, n3); A(&g->nodeTau, (size_t)np);
@@ -252,6 +255,10 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
         AL_CUDA(cudaMemcpy(g->d_eps, b.eps, nl * sizeof(double), cudaMemcpyHostToDevice));
         AL_CUDA(cudaMemcpy(g->d_ell, b.ell_s, nl * sizeof(double), cudaMemcpyHostToDevice));
         AL_CUDA(cudaMemcpy(g->d_af, b.alpha_f, nl * sizeof(double), cudaMemcpyHostToDevice));
+        if (b.cm_n) {
+            AL_CUDA(cudaMemcpy(g->d_cmn, b.cm_n, nl * sizeof(double), cudaMemcpyHostToDevice));
+            AL_CUDA(cudaMemcpy(g->d_cmt, b.cm_t, nl * sizeof(double), cudaMemcpyHostToDevice));
+        }
     }
     AL_CUDA(cudaMemset(g->mask, 0, ((size_t)g->nbrick_max * g->mask_words ? (size_t)g->nbrick_max * g->mask_words : 1) * sizeof(uint32_t)));
     AL_CUDA(cudaMemset(g->hasPrev, 0, sizeof(int)));
@@ -319,6 +326,12 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     }
     p.alpha = (const T *)in->alpha;
     p.np = np;
+    const bool inert = g->d_cmn != nullptr;
+    for (int a = 0; a < 3; ++a) {
+        p.Uprev[a] = inert ? (const T *)in->U_prev[a] : nullptr;
+        p.Pdd[a] = inert ? (const T *)in->Pddot[a] : nullptr;
+    }
+    p.dt = in->dt;
     Scratch<T> &sc = I.sc;
     sc.fprev = (T *)g->fprev; sc.uhi = (T *)g->uhi; sc.ulo = g->ulo; sc.segD = (T *)g->segD;
     sc.segIl2 = (T *)g->segIl2; sc.nodeM = (T *)g->nodeM; sc.nodeTau = g->nodeTau;
@@ -333,6 +346,8 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     for (int a = 0; a < 3; ++a) { bc.n_p[a] = g->bd.n_p[a]; bc.g_up[a] = g->bd.g_up[a]; }
     bc.tau = g->bd.tau; bc.sample_mode = g->bd.sample_mode; bc.drag_mode = g->bd.drag_mode;
     bc.tangents_given = g->bd.tangents_given;
+    bc.cm_n = g->d_cmn; bc.cm_t = g->d_cmt;
+    bc.inertia = (g->d_cmn != nullptr && g->n_lines > 0) ? 1 : 0;
     I.g = g->gc;
     I.status = out->status ? out->status : g->statusInt;
     I.totals = out->totals ? out->totals : g->totalsInt;
@@ -396,6 +411,12 @@ extern "C" int al_sample_drag_spread(al_grid g, const al_step_in *in, const al_s
         }
         const bool sp = in->P_spread[0] != nullptr;
         if ((in->P_spread[1] != nullptr) != sp || (in->P_spread[2] != nullptr) != sp) return AL_ERR_ARG;
+        if (g->d_cmn) {                                   // inertia term: all three or none of each
+            const bool up = in->U_prev[0] != nullptr, pa = in->Pddot[0] != nullptr;
+            for (int a = 1; a < 3; ++a)
+                if ((in->U_prev[a] != nullptr) != up || (in->Pddot[a] != nullptr) != pa) return AL_ERR_ARG;
+            if (up && !(in->dt > 0.0 && std::isfinite(in->dt))) return AL_ERR_ARG;
+        }
     }
     cudaStream_t st = (cudaStream_t)stream;
     return g->d.precision == AL_FP64 ? step_impl<double>(g, in, out, st) : step_impl<float>(g, in, out, st);

@@ -64,6 +64,8 @@ struct BeamsC {
     const double *d, *cdn, *cdt, *eps, *ell_s, *alpha_f, *cv_len;
     double n_p[3], g_up[3], tau;
     int sample_mode, drag_mode, tangents_given;
+    const double *cm_n, *cm_t;   // added-mass coefficients (inertia != 0)
+    int inertia;
 };
 
 struct LineG {                   // per line, rebuilt every step
@@ -118,6 +120,9 @@ struct StepPtrs {
     T *S[3];
     T *F[3];
     int np;
+    const T *Uprev[3];           // inertia: fluid velocity dt earlier (NULL: no fluid acceleration)
+    const T *Pdd[3];             // inertia: actuator-point accelerations (NULL: none)
+    double dt;
 };
 
 // ---------------------------------------------------------------------------
@@ -287,7 +292,10 @@ __device__ __forceinline__ void axis_stencil(T uh, float ul, int n, int &i0, T &
 // S and interpolated in the arithmetic type C.
 template <typename S, typename C>
 __device__ bool sample(const GridC &g, int mode, const S *const *f, int ncomp,
-                       const C uh[3], const float ul[3], C *out) {
+                       const C uh[3], const float ul[3], C *out, const S *const *f2 = nullptr) {
+    // f2 given: the sample of f - f2, the difference taken per cell in the
+    // field precision (so a small time difference keeps its digits)
+#define AL_FV(F, F2, i) ((C)(F2 ? (F[i] - F2[i]) : F[i]))
     const int n[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a)
         if (!inside_axis(uh[a], ul[a], n[a])) return false;
@@ -299,7 +307,10 @@ __device__ bool sample(const GridC &g, int mode, const S *const *f, int ncomp,
             c[a] = c[a] < 0 ? 0 : (c[a] > n[a] - 1 ? n[a] - 1 : c[a]);
         }
         long long idx = c[0] + (long long)g.nx * c[1] + nxy * c[2];
-        for (int q = 0; q < ncomp; ++q) out[q] = (C)f[q][idx];
+        for (int q = 0; q < ncomp; ++q) {
+            const S *F = f[q], *F2 = f2 ? f2[q] : nullptr;
+            out[q] = AL_FV(F, F2, idx);
+        }
         return true;
     }
     int i0[3];
@@ -310,13 +321,14 @@ __device__ bool sample(const GridC &g, int mode, const S *const *f, int ncomp,
     const long long base = i0[0] + (long long)g.nx * i0[1] + nxy * i0[2];
     const C wx0 = (C)1 - t[0], wy0 = (C)1 - t[1], wz0 = (C)1 - t[2];
     for (int q = 0; q < ncomp; ++q) {
-        const S *F = f[q];
-        C c00 = wx0 * (C)F[base] + t[0] * (C)F[base + sx];
-        C c10 = wx0 * (C)F[base + sy] + t[0] * (C)F[base + sy + sx];
-        C c01 = wx0 * (C)F[base + sz] + t[0] * (C)F[base + sz + sx];
-        C c11 = wx0 * (C)F[base + sz + sy] + t[0] * (C)F[base + sz + sy + sx];
+        const S *F = f[q], *F2 = f2 ? f2[q] : nullptr;
+        C c00 = wx0 * AL_FV(F, F2, base) + t[0] * AL_FV(F, F2, base + sx);
+        C c10 = wx0 * AL_FV(F, F2, base + sy) + t[0] * AL_FV(F, F2, base + sy + sx);
+        C c01 = wx0 * AL_FV(F, F2, base + sz) + t[0] * AL_FV(F, F2, base + sz + sx);
+        C c11 = wx0 * AL_FV(F, F2, base + sz + sy) + t[0] * AL_FV(F, F2, base + sz + sy + sx);
         out[q] = wz0 * (wy0 * c00 + t[1] * c10) + t[2] * (wy0 * c01 + t[1] * c11);
     }
+#undef AL_FV
     return true;
 }
 
@@ -334,7 +346,8 @@ template <> __device__ __forceinline__ double inv_h<double>(const GridC &g) { re
 // 1/|u0_n|); the caller then repeats the evaluation in FP64.
 template <typename T, typename C>
 __device__ int point_fstar(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, const int l, const C Pa[3],
-                           const C Pd[3], const C t[3], C fstar[3], int *status, const bool refine_ok) {
+                           const C Pd[3], const C t[3], C fstar[3], int *status, const bool refine_ok,
+                           const C ab[3]) {
     fstar[0] = fstar[1] = fstar[2] = (C)0;
     C ua[3];
     float la[3];
@@ -402,6 +415,25 @@ __device__ int point_fstar(const GridC &g, const BeamsC &b, const StepPtrs<T> &p
         C mn = tsqrt(Un[0] * Un[0] + Un[1] * Un[1] + Un[2] * Un[2]);
         for (int a = 0; a < 3; ++a) fstar[a] = half * (cdt * mt * Ut[a] + cdn * mn * Un[a]);
     }
+    if (b.inertia) {
+        // Eq. fext_addedmass with the fluid acceleration sampled at P_s and the
+        // reaction following the fluid's acceleration relative to the beam
+        C af[3] = {(C)0, (C)0, (C)0};
+        if (p.Uprev[0]) {
+            sample(g, b.sample_mode, p.U, 3, us, ls, af, p.Uprev);          // U - U_prev at P_s
+            const C idt = (C)(1.0 / p.dt);
+            for (int a = 0; a < 3; ++a) af[a] *= idt;
+        }
+        C ar[3];
+        for (int a = 0; a < 3; ++a) ar[a] = af[a] - ab[a];
+        const C art = ar[0] * t[0] + ar[1] * t[1] + ar[2] * t[2];
+        const C ra = rho * (C)(0.25 * PI_D * b.d[l] * b.d[l]);
+        const C cmn = (C)b.cm_n[l], cmt = (C)b.cm_t[l];
+        for (int a = 0; a < 3; ++a) {
+            const C at = art * t[a], an = ar[a] - at;
+            fstar[a] += ra * (cmt * at + cmn * an + af[a]);
+        }
+    }
     return 0;
 }
 
@@ -433,10 +465,13 @@ __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, 
     }
 
     T fstar[3];
-    if (point_fstar<T, T>(g, b, p, l, Pa, Pd, t, fstar, status, sizeof(T) == 4)) {
+    T ab[3] = {(T)0, (T)0, (T)0};
+    if (b.inertia && p.Pdd[0])
+        for (int a = 0; a < 3; ++a) ab[a] = p.Pdd[a][i];
+    if (point_fstar<T, T>(g, b, p, l, Pa, Pd, t, fstar, status, sizeof(T) == 4, ab)) {
         // ill-conditioned upstream direction: the same evaluation in FP64
-        double Pa64[3], Pd64[3], t64[3], f64[3];
-        for (int a = 0; a < 3; ++a) { Pa64[a] = (double)Pa[a]; Pd64[a] = (double)Pd[a]; }
+        double Pa64[3], Pd64[3], t64[3], f64[3], ab64[3];
+        for (int a = 0; a < 3; ++a) { Pa64[a] = (double)Pa[a]; Pd64[a] = (double)Pd[a]; ab64[a] = (double)ab[a]; }
         if (b.tangents_given) {
             for (int a = 0; a < 3; ++a) t64[a] = (double)p.tan[a][i];
         } else if (n == 1) {
@@ -448,7 +483,7 @@ __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, 
         double nn = sqrt(t64[0] * t64[0] + t64[1] * t64[1] + t64[2] * t64[2]);
         if (nn > 0.0) for (int a = 0; a < 3; ++a) t64[a] /= nn;
         else t64[0] = t64[1] = t64[2] = 0.0;
-        point_fstar<T, double>(g, b, p, l, Pa64, Pd64, t64, f64, status, false);
+        point_fstar<T, double>(g, b, p, l, Pa64, Pd64, t64, f64, status, false, ab64);
         for (int a = 0; a < 3; ++a) fstar[a] = (T)f64[a];
         atomicAdd(&status[ST_REFINED], 1);
     }

@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(256) k_na_points(GridC g, BeamsC b, StepPtrs<T
         else t[0] = t[1] = t[2] = (T)0;
     }
     T fstar[3];
-    if (point_fstar<T, T>(g, b, p, l, Pa, Pd, t, fstar, status, sizeof(T) == 4)) {
+    const T ab0[3] = {(T)0, (T)0, (T)0};
+    if (point_fstar<T, T>(g, b, p, l, Pa, Pd, t, fstar, status, sizeof(T) == 4, ab0)) {
         double Pa64[3], Pd64[3], t64[3], f64[3];
         for (int a = 0; a < 3; ++a) { Pa64[a] = (double)Pa[a]; Pd64[a] = (double)Pd[a]; }
         if (b.tangents_given) {
@@ -115,7 +116,8 @@ __global__ void __launch_bounds__(256) k_na_points(GridC g, BeamsC b, StepPtrs<T
         double nn = sqrt(t64[0] * t64[0] + t64[1] * t64[1] + t64[2] * t64[2]);
         if (nn > 0.0) for (int a = 0; a < 3; ++a) t64[a] /= nn;
         else t64[0] = t64[1] = t64[2] = 0.0;
-        point_fstar<T, double>(g, b, p, l, Pa64, Pd64, t64, f64, status, false);
+        const double ab64[3] = {0.0, 0.0, 0.0};
+        point_fstar<T, double>(g, b, p, l, Pa64, Pd64, t64, f64, status, false, ab64);
         for (int a = 0; a < 3; ++a) fstar[a] = (T)f64[a];
         atomicAdd(&status[ST_REFINED], 1);
     }

@@ -432,6 +432,25 @@ def random_canopy(seed, nx, ny, nz, h, n_stems, n_cv, eps_cells, name="canopy"):
                     meta={"eps_cells": eps_cells})
 
 
+def with_inertia(wl: Workload, seed: int, *, cm_n: float = 1.0, cm_t: float = 0.1, dt: float = 1e-3,
+                 accel: float = 2.0) -> Workload:
+    """The same workload with the Morison inertia inputs: added-mass
+    coefficients on every line, the velocity one step dt earlier
+    (U_prev = U - dt a with a a smooth random acceleration field of RMS
+    `accel` m/s^2) and random actuator-point accelerations of RMS accel/2."""
+    rng = _rng(seed)
+    g = wl.grid
+    a = _solenoidal_modes(rng, g, 4, 4).astype(np.float64)
+    a *= accel / max(float(np.sqrt((a ** 2).mean())), 1e-30)
+    dtype = wl.step.U.dtype
+    U_prev = (wl.step.U.astype(np.float64) - dt * a).astype(dtype)
+    Pddot = rng.normal(0.0, 0.5 * accel, size=wl.step.P.shape).astype(wl.step.P.dtype)
+    nl = wl.beams.n_lines
+    beams = replace(wl.beams, cm_n=np.full(nl, float(cm_n)), cm_t=np.full(nl, float(cm_t)))
+    return replace(wl, name=wl.name + "_inertia", beams=beams,
+                   step=replace(wl.step, U_prev=U_prev, Pddot=Pddot, dt=float(dt)))
+
+
 def advance(wl: Workload, seed: int, dt: float = 1e-3) -> Workload:
     """Next coupling step of a served simulation: positions move by
     Pdot * dt plus N(0, (1e-4 h)^2) jitter (a synthetic beam update)."""

@@ -177,3 +177,18 @@ def test_fine_segments_zero_weight_deposits():
     assert o["status"][4] > 0 and g["status"][4] == o["status"][4]
     m = compare(wl, g, o, label="fine")
     print("fine", m, "zero-weight nodes", o["status"][4])
+
+
+@pytest.mark.parametrize("case", ["random-fp32", "random-fp64", "canopy"])
+def test_inertia_term(case):
+    """Morison inertia (added mass and Froude-Krylov, Eq. fext_addedmass) with
+    a time-varying fluid and accelerating beams, against the oracle."""
+    if case == "canopy":
+        wl = W.with_inertia(W.make_canopy(2, 2.0), 6)
+    else:
+        prec = "fp64" if case.endswith("fp64") else "fp32"
+        wl = W.with_inertia(W.make_random(51, 40, 34, 30, n_lines=8, precision=prec, has_alpha=True,
+                                          kinds=("stem", "arc", "random", "flat", "point", "dup")), 5)
+    g, o = run_gpu(wl), oracle.sample_drag_spread(wl)
+    m = compare(wl, g, o, label=f"inertia {case}", sumF_ref="net" if case == "canopy" else "abs")
+    print("inertia", case, m)
