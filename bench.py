@@ -48,6 +48,8 @@ def _args():
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000", help="serve: arrival rates (1/s)")
     ap.add_argument("--budget-gb", type=float, default=0.5, help="serve: HBM budget for resident simulations")
     ap.add_argument("--eps", type=float, default=2.0, help="canopy kernel width in cells")
+    ap.add_argument("--inertia", action="store_true",
+                    help="add the Morison inertia term (accelerating fluid and beams, C_Mn = 1, C_Mt = 0.1)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -230,6 +232,9 @@ def run_ours(a):
     from paper_2609_39443_b300.al import Instance, PHASES, ST_SUPPORT
 
     wl = _workload(a.workload, instance_seed(rank), a.eps)
+    if a.inertia:
+        from paper_2609_39443_b300 import workloads as W
+        wl = W.with_inertia(wl, 1000 + instance_seed(rank))
     inst = Instance(wl, device=f"cuda:{local}")
     tuned = {"weights": "brick", "brick_z": 8, "autotuned": False}
     if a.weights or a.brick_z:
@@ -281,9 +286,10 @@ def run_ours(a):
         def pin(x):
             return None if x is None else torch.as_tensor(np.ascontiguousarray(x)).pin_memory()
         hU, hP, hPd, hal = pin(wl.step.U), pin(wl.step.P), pin(wl.step.Pdot), pin(wl.step.alpha)
+        hUp, hPdd = pin(getattr(wl.step, "U_prev", None)), pin(getattr(wl.step, "Pddot", None))
         hS = torch.empty(inst.S.shape, dtype=inst.S.dtype).pin_memory()
         hF = torch.empty(inst.F.shape, dtype=inst.F.dtype).pin_memory()
-        h2d = sum(int(t.numel() * t.element_size()) for t in (hU, hP, hPd, hal) if t is not None)
+        h2d = sum(int(t.numel() * t.element_size()) for t in (hU, hP, hPd, hal, hUp, hPdd) if t is not None)
         d2h = int(hS.numel() * hS.element_size() + hF.numel() * hF.element_size())
         n_e2e = max(3, min(a.steps, 10))
 
@@ -293,6 +299,9 @@ def run_ours(a):
             inst.Pdot.copy_(hPd, non_blocking=True)
             if hal is not None:
                 inst.alpha.copy_(hal, non_blocking=True)
+            if hUp is not None:
+                inst.U_prev.copy_(hUp, non_blocking=True)
+                inst.Pddot.copy_(hPdd, non_blocking=True)
             inst.step()
             hS.copy_(inst.S, non_blocking=True)
             hF.copy_(inst.F, non_blocking=True)
@@ -341,6 +350,7 @@ def run_ours(a):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if wl.grid.precision == "fp64" else "f32", "data": "synthetic",
                 "config": {"workload": wl.name, "cells": wl.grid.n_cells, "points": wl.beams.n_points,
+                           "inertia": bool(a.inertia),
                            "lines": wl.beams.n_lines, "parallelism": f"{world} independent instances",
                            "l2": "flushed between timed steps (256 MiB write)", "options": tuned},
                 "kernel_cell_updates_per_s": supp * value,
