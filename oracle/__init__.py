@@ -56,7 +56,7 @@ def _load():
                                       dp, dp, C.c_double, dp, dp, dp, dp, C.POINTER(C.c_longlong)]
         lib.or_project.argtypes = [C.POINTER(_Grid), C.POINTER(_Beams), dp, dp, C.c_int,
                                    C.POINTER(C.c_ubyte), dp, dp, C.POINTER(C.c_longlong), C.c_int]
-        lib.or_sample_field.argtypes = [C.POINTER(_Grid), dp, C.c_int, C.c_int, dp, dp]
+        lib.or_sample_field.argtypes = [C.POINTER(_Grid), dp, C.c_int, C.c_int, C.c_double, dp, dp]
         lib.or_count_support.argtypes = [C.POINTER(_Grid), C.POINTER(_Beams), dp, C.c_int]
         lib.or_count_support.restype = C.c_longlong
         lib.or_closest_segment.argtypes = [dp, C.c_int, dp, C.POINTER(C.c_int), dp]
@@ -92,14 +92,15 @@ class _BeamsHold:
                         _ptr(self.cm[0]), _ptr(self.cm[1]))
 
 
-def sample(grid, field, mode, p):
-    """Sample an SoA field (ncomp, N_c) at point p; returns (inside, value)."""
+def sample(grid, field, mode, p, eps=0.0):
+    """Sample an SoA field (ncomp, N_c) at point p; returns (inside, value).
+    eps: kernel width of the Gaussian volume average (mode 2)."""
     f = _f64(field)
     ncomp = 1 if f.ndim == 1 else f.shape[0]
     out = np.zeros(ncomp)
     g = _grid(grid)
     pp = _f64(np.asarray(p))
-    ok = _load().or_sample_field(C.byref(g), _ptr(f), ncomp, int(mode), _ptr(pp), _ptr(out))
+    ok = _load().or_sample_field(C.byref(g), _ptr(f), ncomp, int(mode), float(eps), _ptr(pp), _ptr(out))
     return bool(ok), out
 
 

@@ -55,7 +55,7 @@ typedef struct {
     const double *eps, *ell_s, *alpha_f;
     const double *cv_len;             /* per point */
     double n_p[3], g_up[3], tau;
-    int sample_mode;                  /* 0 trilinear, 1 containing cell */
+    int sample_mode;                  /* 0 trilinear, 1 containing cell, 2 Gaussian volume average */
     int drag_mode;                    /* 0 Eq. almLineForce, 1 Eq. fext_drag */
     const double *cm_n, *cm_t;        /* per line, added-mass coefficients of Eq. fext_addedmass;
                                          NULL: no inertia term (the paper's model) */
@@ -99,8 +99,17 @@ static int or_locate(const or_grid *g, const double p[3], double u[3])
  * mode 0: trilinear interpolation between the 8 surrounding cell centres.
  *         In the half cell next to a wall the index is clamped, i.e. the
  *         wall cell's value is extended to the wall.
+ * mode 2: kernel-weighted volume average with the Gaussian of the
+ *         projection (the smooth sampler the paper's Sec. 6 proposes):
+ *         value = sum_j g_j f_j / sum_j g_j over the cells j of the grid
+ *         whose centre C_j lies within 3 eps of p, g_j = exp(-(|C_j - p|/eps)^2)
+ *         (the truncated profile of Eq. almGaussian; its constant factor
+ *         cancels).  Cells outside the grid do not enter, so near a wall the
+ *         average is one-sided.  When no cell centre lies within 3 eps the
+ *         containing cell's value is returned (the limit of the normalised
+ *         average as eps -> 0: the nearest centre is the containing cell's).
  * Returns 0 (and leaves out untouched) when p lies outside the grid. */
-static int or_sample(const or_grid *g, const double *f, int ncomp, int mode,
+static int or_sample(const or_grid *g, const double *f, int ncomp, int mode, double eps,
                      const double p[3], double *out)
 {
     double u[3];
@@ -108,6 +117,39 @@ static int or_sample(const or_grid *g, const double *f, int ncomp, int mode,
     const int n[3] = {g->nx, g->ny, g->nz};
     const long long nxy = (long long)g->nx * g->ny;
     const long long ncell = nxy * g->nz;
+    if (mode == 2) {
+        const double R = 3.0 * eps;
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            /* every centre within R of p lies in this index range (one cell of slack) */
+            lo[a] = (int)floor(u[a] - 0.5 - R / g->h) - 1;
+            hi[a] = (int)floor(u[a] - 0.5 + R / g->h) + 1;
+            if (lo[a] < 0) lo[a] = 0;
+            if (hi[a] > n[a] - 1) hi[a] = n[a] - 1;
+        }
+        double *acc = (double *)calloc((size_t)ncomp, sizeof(double));
+        double sw = 0.0;
+        for (int k = lo[2]; k <= hi[2]; ++k)
+            for (int j = lo[1]; j <= hi[1]; ++j)
+                for (int i = lo[0]; i <= hi[0]; ++i) {
+                    const double C[3] = {g->o[0] + (i + 0.5) * g->h, g->o[1] + (j + 0.5) * g->h,
+                                         g->o[2] + (k + 0.5) * g->h};
+                    const double d[3] = {C[0] - p[0], C[1] - p[1], C[2] - p[2]};
+                    const double r2 = dot3(d, d);
+                    if (r2 > R * R) continue;
+                    const double wgt = exp(-r2 / (eps * eps));
+                    const long long idx = i + (long long)g->nx * j + nxy * k;
+                    sw += wgt;
+                    for (int q = 0; q < ncomp; ++q) acc[q] += wgt * f[q * ncell + idx];
+                }
+        if (sw > 0.0) {
+            for (int q = 0; q < ncomp; ++q) out[q] = acc[q] / sw;
+            free(acc);
+            return 1;
+        }
+        free(acc);
+        mode = 1;
+    }
     if (mode == 1) {
         int c[3];
         for (int a = 0; a < 3; ++a) {
@@ -145,10 +187,10 @@ static int or_sample(const or_grid *g, const double *f, int ncomp, int mode,
 }
 
 /* Exported for the sampler pins. */
-int or_sample_field(const or_grid *g, const double *f, int ncomp, int mode,
+int or_sample_field(const or_grid *g, const double *f, int ncomp, int mode, double eps,
                     const double *p, double *out)
 {
-    return or_sample(g, f, ncomp, mode, p, out);
+    return or_sample(g, f, ncomp, mode, eps, p, out);
 }
 
 /* ------------------------------------------------------------------ */
@@ -198,7 +240,7 @@ int or_point_step(const or_grid *g, const or_beams *b,
             double fstar[3] = {0.0, 0.0, 0.0};
             double Ps[3] = {Pa[0], Pa[1], Pa[2]};
             double Ua[3];
-            if (!or_sample(g, U, 3, b->sample_mode, Pa, Ua)) {
+            if (!or_sample(g, U, 3, b->sample_mode, b->eps[l], Pa, Ua)) {
                 status[OR_ST_PA_OUTSIDE]++;            /* no load for this step */
             } else {
                 /* Eq. almPreliminaryVelocity and its normal part */
@@ -227,8 +269,8 @@ int or_point_step(const or_grid *g, const or_beams *b,
 
                 double Us[4];
                 int nc = g->has_alpha ? 1 : 0;
-                if (!or_sample(g, U, 3, b->sample_mode, Ps, Us) ||
-                    (nc && !or_sample(g, alpha, 1, b->sample_mode, Ps, Us + 3))) {
+                if (!or_sample(g, U, 3, b->sample_mode, b->eps[l], Ps, Us) ||
+                    (nc && !or_sample(g, alpha, 1, b->sample_mode, b->eps[l], Ps, Us + 3))) {
                     status[OR_ST_PS_OUTSIDE]++;        /* no load for this step */
                 } else {
                     double rho = g->has_alpha ? Us[3] * g->rho1 + (1.0 - Us[3]) * g->rho2 : g->rho_const;
@@ -259,7 +301,7 @@ int or_point_step(const or_grid *g, const or_beams *b,
                         double af[3] = {0.0, 0.0, 0.0}, ab[3] = {0.0, 0.0, 0.0};
                         if (U_prev) {
                             double Up[3];
-                            or_sample(g, U_prev, 3, b->sample_mode, Ps, Up);   /* inside: checked above */
+                            or_sample(g, U_prev, 3, b->sample_mode, b->eps[l], Ps, Up);   /* inside: checked above */
                             for (int a = 0; a < 3; ++a) af[a] = (Us[a] - Up[a]) / dt;
                         }
                         if (Pddot) for (int a = 0; a < 3; ++a) ab[a] = Pddot[a * np + i];

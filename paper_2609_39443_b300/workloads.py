@@ -31,6 +31,7 @@ G_ACC = 9.81
 
 SAMPLE_TRILINEAR = 0
 SAMPLE_CELL = 1
+SAMPLE_GAUSS = 2        # Gaussian-weighted volume average over the projection kernel's support
 DRAG_DISCRETE = 0
 DRAG_SPLIT = 1
 
@@ -449,6 +450,14 @@ def with_inertia(wl: Workload, seed: int, *, cm_n: float = 1.0, cm_t: float = 0.
     beams = replace(wl.beams, cm_n=np.full(nl, float(cm_n)), cm_t=np.full(nl, float(cm_t)))
     return replace(wl, name=wl.name + "_inertia", beams=beams,
                    step=replace(wl.step, U_prev=U_prev, Pddot=Pddot, dt=float(dt)))
+
+
+def with_sample_mode(wl: Workload, mode: str) -> Workload:
+    """The same workload with another sampling operator on every line
+    ("trilinear", "cell" or "gauss")."""
+    m = {"trilinear": SAMPLE_TRILINEAR, "cell": SAMPLE_CELL, "gauss": SAMPLE_GAUSS}[mode]
+    return replace(wl, name=f"{wl.name}_{mode}" if m != wl.beams.sample_mode else wl.name,
+                   beams=replace(wl.beams, sample_mode=m))
 
 
 def advance(wl: Workload, seed: int, dt: float = 1e-3) -> Workload:

@@ -103,6 +103,106 @@ def test_outside_points_are_reported():
 
 
 # ----------------------------------------------------------------------------
+# kernel-weighted volume average (sampling mode 2, the smooth sampler of Sec. 6)
+# ----------------------------------------------------------------------------
+
+def _centres(g):
+    idx = np.arange(g.n_cells)
+    i, j, k = idx % g.nx, (idx // g.nx) % g.ny, idx // (g.nx * g.ny)
+    return np.stack([g.origin[0] + (i + .5) * g.h, g.origin[1] + (j + .5) * g.h, g.origin[2] + (k + .5) * g.h])
+
+
+def test_gauss_average_weights_are_the_truncated_gaussian():
+    """Sampling the identity field (one component per cell) returns every
+    cell's normalised weight at once.  The weights are positive exactly on
+    the cells whose centre lies within 3 eps of p (walls included), sum to
+    one, and the ratio of any two is exp(-(r_a^2 - r_b^2) / eps^2), which
+    does not involve the normaliser."""
+    rng = np.random.default_rng(11)
+    g = GridSpec(9, 8, 10, 0.1, origin=(0.3, -0.2, 0.1))
+    ident = np.eye(g.n_cells)
+    C = _centres(g)
+    for eps in (0.07, 0.13, 0.21):
+        for _ in range(4):
+            p = np.array(g.origin) + rng.uniform(0.1, 0.9, 3) * np.array([g.nx, g.ny, g.nz]) * g.h
+            ok, w = oracle.sample(g, ident, W.SAMPLE_GAUSS, p, eps)
+            assert ok
+            r2 = ((C - p[:, None]) ** 2).sum(0)
+            inside = r2 <= (3 * eps) ** 2
+            assert np.array_equal(w > 0, inside)
+            assert w.sum() == pytest.approx(1.0, abs=1e-14)
+            a = np.flatnonzero(inside)
+            k0 = a[np.argmin(r2[a])]
+            np.testing.assert_allclose(w[a] / w[k0], np.exp(-(r2[a] - r2[k0]) / eps ** 2), rtol=1e-12)
+
+
+def test_gauss_average_reproduces_affine_fields_at_symmetric_points():
+    """About a cell centre, a cell corner or the middle of an edge or a face
+    the lattice of centres and the Gaussian weights are mirror-symmetric on
+    every axis, so with the support inside the grid the weighted centroid
+    is p itself and an affine field is reproduced; elsewhere the centroid
+    is not p and in general it is not."""
+    rng = np.random.default_rng(12)
+    g = GridSpec(16, 15, 17, 0.05, origin=(-0.4, 0.2, 0.0))
+    A = rng.normal(size=(3, 3))
+    b = rng.normal(size=3)
+    U = A @ _centres(g) + b[:, None]
+    eps = 0.08                                     # 3 eps = 4.8 cells
+    for frac in [(0.5, 0.5, 0.5), (0, 0, 0), (0.5, 0, 0), (0, 0.5, 0.5), (0.5, 0.5, 0)]:
+        p = np.array(g.origin) + (np.array([8, 7, 8]) + np.array(frac)) * g.h
+        ok, v = oracle.sample(g, U, W.SAMPLE_GAUSS, p, eps)
+        assert ok
+        np.testing.assert_allclose(v, A @ p + b, rtol=0, atol=1e-12)
+    p = np.array(g.origin) + np.array([8.3, 7.1, 8.2]) * g.h
+    assert np.abs(oracle.sample(g, U, W.SAMPLE_GAUSS, p, eps)[1] - (A @ p + b)).max() > 1e-6
+
+
+def test_gauss_average_of_a_constant_field_at_walls():
+    """Near a wall the support is cut and the weights renormalise over the
+    cells present: a constant field is still returned exactly."""
+    g = GridSpec(8, 6, 7, 0.1)
+    f = np.stack([np.full(g.n_cells, 1.7), np.full(g.n_cells, -0.3)])
+    for p in ([0.001, 0.001, 0.001], [0.79, 0.3, 0.35], [0.4, 0.599, 0.699]):
+        ok, v = oracle.sample(g, f, W.SAMPLE_GAUSS, np.array(p), 0.12)
+        assert ok
+        np.testing.assert_allclose(v, [1.7, -0.3], rtol=1e-14)
+    assert not oracle.sample(g, f, W.SAMPLE_GAUSS, np.array([0.8, 0.3, 0.3]), 0.12)[0]
+
+
+def test_gauss_average_narrow_kernel_is_the_containing_cell():
+    """As eps -> 0 the normalised average tends to the value at the nearest
+    cell centre, the containing cell's.  With 3 eps below half a cell no
+    other centre can enter; when not even that one does, the containing
+    cell's value is returned too."""
+    rng = np.random.default_rng(13)
+    g = GridSpec(6, 5, 7, 0.2, origin=(1.0, 2.0, -1.0))
+    f = rng.normal(size=(3, g.n_cells))
+    for _ in range(100):
+        c = rng.integers([0, 0, 0], [g.nx, g.ny, g.nz])
+        p = np.array(g.origin) + (c + rng.uniform(0.05, 0.95, 3)) * g.h
+        ref = f[:, c[0] + g.nx * (c[1] + g.ny * c[2])]
+        for eps in (0.01, 0.03):                   # 3 eps = 0.15 h and 0.45 h
+            ok, v = oracle.sample(g, f, W.SAMPLE_GAUSS, p, eps)
+            assert ok
+            np.testing.assert_allclose(v, ref, rtol=1e-15, atol=0)
+
+
+def test_gauss_average_is_continuous_across_faces():
+    """The containing cell's value jumps where the point crosses a face; the
+    volume average moves only by O(|step| / eps) plus at most the weight
+    e^-9 of a cell leaving the truncated support."""
+    rng = np.random.default_rng(14)
+    g = GridSpec(12, 12, 12, 0.1)
+    f = rng.normal(size=(1, g.n_cells))
+    for x0 in (0.6, 0.3):
+        xs = x0 + np.array([-1e-7, 1e-7])
+        cell = [oracle.sample(g, f, W.SAMPLE_CELL, np.array([x, 0.63, 0.57]))[1][0] for x in xs]
+        avg = [oracle.sample(g, f, W.SAMPLE_GAUSS, np.array([x, 0.63, 0.57]), 0.15)[1][0] for x in xs]
+        assert abs(cell[1] - cell[0]) > 1e-3
+        assert abs(avg[1] - avg[0]) < 1e-4
+
+
+# ----------------------------------------------------------------------------
 # tangent, sampling point and fallback (Sec. 3.2.2, Eq. almSamplingPoint)
 # ----------------------------------------------------------------------------
 
@@ -190,15 +290,16 @@ def test_cylinder_drag_golden():
     assert r["F"][0].sum() == pytest.approx(gd["F_total"], rel=1e-14)
 
 
+@pytest.mark.parametrize("sample_mode", [W.SAMPLE_TRILINEAR, W.SAMPLE_CELL, W.SAMPLE_GAUSS])
 @pytest.mark.parametrize("drag_mode", [W.DRAG_DISCRETE, W.DRAG_SPLIT])
-def test_inclined_cylinder_closed_form(drag_mode):
+def test_inclined_cylinder_closed_form(drag_mode, sample_mode):
     theta = 0.6                                     # angle between line and flow
     U0, rho, d, cdn, cdt = 0.7, 1000.0, 0.01, 1.3, 0.05
     g = GridSpec(60, 20, 60, 0.01, rho_const=rho)
     t = np.array([np.cos(theta), 0.0, np.sin(theta)])
     P = np.array([0.2, 0.1, 0.2])[:, None] + 0.01 * np.arange(8)[None] * t[:, None]
     wl = _line_workload(P, _uniform(g, (U0, 0, 0)), grid=g, cv=0.01,
-                        per_line=dict(d=d, cdn=cdn, cdt=cdt), drag_mode=drag_mode)
+                        per_line=dict(d=d, cdn=cdn, cdt=cdt), drag_mode=drag_mode, sample_mode=sample_mode)
     F = oracle.point_step(g, wl.beams, wl.step)["F"] / 0.01
     Ut = U0 * np.cos(theta) * t
     Un = np.array([U0, 0, 0]) - Ut
