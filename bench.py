@@ -50,6 +50,8 @@ def _args():
     ap.add_argument("--eps", type=float, default=2.0, help="canopy kernel width in cells")
     ap.add_argument("--inertia", action="store_true",
                     help="add the Morison inertia term (accelerating fluid and beams, C_Mn = 1, C_Mt = 0.1)")
+    ap.add_argument("--sample", default="trilinear", choices=["trilinear", "cell", "gauss"],
+                    help="sampling operator of both velocity samples (cell: the containing cell; gauss: Gaussian volume average)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -235,6 +237,9 @@ def run_ours(a):
     if a.inertia:
         from paper_2609_39443_b300 import workloads as W
         wl = W.with_inertia(wl, 1000 + instance_seed(rank))
+    if a.sample != "trilinear":
+        from paper_2609_39443_b300 import workloads as W
+        wl = W.with_sample_mode(wl, a.sample)
     inst = Instance(wl, device=f"cuda:{local}")
     tuned = {"weights": "brick", "brick_z": 8, "autotuned": False}
     if a.weights or a.brick_z:
@@ -350,7 +355,7 @@ def run_ours(a):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if wl.grid.precision == "fp64" else "f32", "data": "synthetic",
                 "config": {"workload": wl.name, "cells": wl.grid.n_cells, "points": wl.beams.n_points,
-                           "inertia": bool(a.inertia),
+                           "inertia": bool(a.inertia), "sample": a.sample,
                            "lines": wl.beams.n_lines, "parallelism": f"{world} independent instances",
                            "l2": "flushed between timed steps (256 MiB write)", "options": tuned},
                 "kernel_cell_updates_per_s": supp * value,

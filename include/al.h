@@ -55,6 +55,12 @@ extern "C" {
 
 #define AL_SAMPLE_TRILINEAR 0  /* trilinear interpolation of cell values   */
 #define AL_SAMPLE_CELL      1  /* value of the single containing cell (the paper's operator) */
+#define AL_SAMPLE_GAUSS     2  /* kernel-weighted volume average: sum_j g_j U_j / sum_j g_j over the
+                                  cells whose centre lies within 3 eps of the point, g_j =
+                                  exp(-(|C_j - p| / eps)^2) with the line's projection width eps
+                                  (Eq. almGaussian; the smooth sampler proposed in Sec. 6); cells
+                                  outside the grid do not enter; no centre within 3 eps: the
+                                  containing cell */
 
 #define AL_DRAG_DISCRETE 0     /* Eq. almLineForce: |U_r| (C_dn U_n + C_dt U_t)        */
 #define AL_DRAG_SPLIT    1     /* Eq. fext_drag: C_dn |U_n| U_n + C_dt |U_t| U_t        */

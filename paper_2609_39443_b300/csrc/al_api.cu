@@ -181,7 +181,8 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     if (b.n_lines > 0 && (!b.line_off || !b.d || !b.cdn || !b.cdt || !b.eps || !b.ell_s || !b.alpha_f))
         return AL_ERR_ARG;
     if ((b.cm_n == nullptr) != (b.cm_t == nullptr)) return AL_ERR_ARG;      // both or neither
-    if (b.sample_mode != AL_SAMPLE_TRILINEAR && b.sample_mode != AL_SAMPLE_CELL) return AL_ERR_ARG;
+    if (b.sample_mode != AL_SAMPLE_TRILINEAR && b.sample_mode != AL_SAMPLE_CELL && b.sample_mode != AL_SAMPLE_GAUSS)
+        return AL_ERR_ARG;
     if (b.drag_mode != AL_DRAG_DISCRETE && b.drag_mode != AL_DRAG_SPLIT) return AL_ERR_ARG;
     if (!(b.tau >= 0.0)) return AL_ERR_ARG;
     const double npn = std::sqrt(b.n_p[0] * b.n_p[0] + b.n_p[1] * b.n_p[1] + b.n_p[2] * b.n_p[2]);
@@ -369,7 +370,10 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
     trace_mark(g, 0, st);
     const int nb = (np + 255) / 256;
     if (np > 0) {
-        k_points<T><<<nb, 256, 0, st>>>(gc, bc, p, sc, status);
+        if (bc.sample_mode == AL_SAMPLE_GAUSS)               // one warp per point
+            k_points_w<T><<<(unsigned)(((long long)np * 32 + 255) / 256), 256, 0, st>>>(gc, bc, p, sc, status);
+        else
+            k_points<T><<<nb, 256, 0, st>>>(gc, bc, p, sc, status);
         k_segments<T><<<nb, 256, 0, st>>>(bc, sc);
     }
     if (g->n_lines > 0) k_lines<T><<<(g->n_lines + 7) / 8, 256, 0, st>>>(gc, bc, sc, p, status);
@@ -534,6 +538,7 @@ struct al_batch_s {
     int ctas = 0;                             // persistent CTAs per SM (0: as many as fit)
     int occ = 1;                              // CTAs per SM that fit at this brick height
     bool any_segment_weights = false;         // some instance sums weights per segment
+    bool any_gauss = false;                   // some instance samples by volume average (warp per point)
     // subset runs: a ring of pinned host / device work lists
     static constexpr int RING = 8;
     int maxn = 0;
@@ -588,6 +593,7 @@ static int batch_rebuild_t(al_batch b) {
     Inst<T> *h = (Inst<T> *)b->h_inst;
     std::vector<long long> pre(4 * (size_t)(n + 1), 0);
     b->any_segment_weights = false;
+    b->any_gauss = false;
     b->cnt_pts.assign(n, 0); b->cnt_lines.assign(n, 0); b->cnt_bricks.assign(n, 0);
     for (int q = 0; q < n; ++q) {
         const bool used = b->grids[q] != nullptr;
@@ -596,6 +602,7 @@ static int batch_rebuild_t(al_batch b) {
             set_brick_z(h[q].g, b->bz);
             h[q].g.smode = 0;                                // batches always gather
             if (h[q].g.wmode != 0) b->any_segment_weights = true;
+            if (h[q].b.sample_mode == AL_SAMPLE_GAUSS) b->any_gauss = true;
             b->cnt_pts[q] = b->grids[q]->n_points;
             b->cnt_lines[q] = b->grids[q]->n_lines;
             b->cnt_bricks[q] = h[q].g.nbrick;
@@ -664,7 +671,10 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
         return (unsigned)std::max<long long>(1, std::min<long long>(g, (long long)b->pt_grid * 4));
     };
     if (tot_pts > 0) {
-        kb_points<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
+        if (b->any_gauss)
+            kb_points_w<T><<<grid_for(tot_pts, 8), 256, 0, st>>>(I, sel, pp, n);
+        else
+            kb_points<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
         kb_segments<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
     }
     if (tot_lines > 0) kb_lines<T><<<grid_for(tot_lines, 8), 256, 0, st>>>(I, sel, pl, n);
@@ -721,6 +731,7 @@ static int batch_assign_t(al_batch b, int slot, al_grid g, const al_step_in *in,
     b->grids[slot] = g;
     if (g) { b->ins[slot] = *in; b->outs[slot] = *out; }
     if (g && g->gc.wmode != 0) b->any_segment_weights = true;
+    if (g && g->bd.sample_mode == AL_SAMPLE_GAUSS) b->any_gauss = true;
     b->cnt_pts[slot] = g ? g->n_points : 0;
     b->cnt_lines[slot] = g ? g->n_lines : 0;
     b->cnt_bricks[slot] = g ? h->g.nbrick : 0;

@@ -288,19 +288,86 @@ __device__ __forceinline__ void axis_stencil(T uh, float ul, int n, int &i0, T &
     t = fr;
 }
 
-// Returns false when the point lies outside the grid.  Fields are stored as
-// S and interpolated in the arithmetic type C.
-template <typename S, typename C>
-__device__ bool sample(const GridC &g, int mode, const S *const *f, int ncomp,
-                       const C uh[3], const float ul[3], C *out, const S *const *f2 = nullptr) {
-    // f2 given: the sample of f - f2, the difference taken per cell in the
-    // field precision (so a small time difference keeps its digits)
+// f2 given: the sample of f - f2, the difference taken per cell in the
+// field precision (so a small time difference keeps its digits)
 #define AL_FV(F, F2, i) ((C)(F2 ? (F[i] - F2[i]) : F[i]))
+
+// Kernel-weighted volume average (the smooth sampler of Sec. 6): weights
+// exp(-(r/eps)^2) of the projection's truncated Gaussian (Eq. almGaussian,
+// its constant cancels) over the cells of the grid whose centre lies within
+// r <= 3 eps of the point, normalised by their sum; epsc = eps / h.  The
+// cells of the support's bounding box are dealt to LANES lanes (x fastest,
+// so neighbouring lanes read neighbouring cells); with LANES = 32 the whole
+// warp calls with the same arguments and a butterfly reduction leaves the
+// same sums, bit for bit, in every lane.  At most 4 components.  Returns
+// false when no cell centre lies within 3 eps (the caller then takes the
+// containing cell).
+template <int LANES, typename S, typename C>
+__device__ bool gauss_avg(const GridC &g, C epsc, const S *const *f, int ncomp, const C uh[3], const float ul[3],
+                          C *out, const S *const *f2) {
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const C Rc = (C)3 * epsc, R2 = Rc * Rc;
+    const C l2ie2 = (C)1.4426950408889634 / (epsc * epsc);     // log2(e) / eps^2
+    int lo[3], bn[3];
+    for (int a = 0; a < 3; ++a) {
+        const C c = (uh[a] - (C)0.5) + (C)ul[a];                // centre-unit coordinate
+        int l0 = (int)tfloor(c - Rc), h0 = (int)tfloor(c + Rc) + 1;
+        l0 = l0 < 0 ? 0 : l0;
+        h0 = h0 > n[a] - 1 ? n[a] - 1 : h0;
+        lo[a] = l0;
+        bn[a] = h0 - l0 + 1;
+    }
+    const int nplane = bn[0] * bn[1];
+    const long long nbox = (long long)nplane * bn[2];
+    const int lane = LANES == 1 ? 0 : (int)(threadIdx.x & 31);
+    // (i, j, k) of box cell t = lane, then advanced by LANES with carries
+    int k = lane / nplane, r = lane - k * nplane, j = r / bn[0], i = r - j * bn[0];
+    const int dk = LANES / nplane, dr = LANES - dk * nplane, dj = dr / bn[0], di = dr - dj * bn[0];
+    const long long nxy = (long long)g.nx * g.ny;
+    C acc[4] = {(C)0, (C)0, (C)0, (C)0}, sw = (C)0;
+    for (long long t = lane; t < nbox; t += LANES) {
+        const int ci = lo[0] + i, cj = lo[1] + j, ck = lo[2] + k;
+        const C dx = (((C)ci + (C)0.5) - uh[0]) - (C)ul[0];
+        const C dy = (((C)cj + (C)0.5) - uh[1]) - (C)ul[1];
+        const C dz = (((C)ck + (C)0.5) - uh[2]) - (C)ul[2];
+        const C r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 <= R2) {
+            const C w = Tr<C>::ex2(-r2 * l2ie2);
+            const long long idx = ci + (long long)g.nx * cj + nxy * ck;
+            sw += w;
+            for (int q = 0; q < ncomp; ++q) {
+                const S *F = f[q], *F2 = f2 ? f2[q] : nullptr;
+                acc[q] += w * AL_FV(F, F2, idx);
+            }
+        }
+        i += di; j += dj; k += dk;
+        if (i >= bn[0]) { i -= bn[0]; j += 1; }
+        if (j >= bn[1]) { j -= bn[1]; k += 1; }
+    }
+    if (LANES > 1) {
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) {
+            sw += __shfl_xor_sync(0xffffffffu, sw, m);
+            for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], m);
+        }
+    }
+    if (!(sw > (C)0)) return false;
+    for (int q = 0; q < ncomp; ++q) out[q] = acc[q] / sw;
+    return true;
+}
+
+// Returns false when the point lies outside the grid.  Fields are stored as
+// S and interpolated in the arithmetic type C.  mode 2 (the volume average)
+// needs the kernel width epsc = eps / h and LANES lanes calling together.
+template <int LANES = 1, typename S, typename C>
+__device__ bool sample(const GridC &g, int mode, C epsc, const S *const *f, int ncomp,
+                       const C uh[3], const float ul[3], C *out, const S *const *f2 = nullptr) {
     const int n[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a)
         if (!inside_axis(uh[a], ul[a], n[a])) return false;
     const long long nxy = (long long)g.nx * g.ny;
-    if (mode == 1) {
+    if (mode == 2 && gauss_avg<LANES>(g, epsc, f, ncomp, uh, ul, out, f2)) return true;
+    if (mode >= 1) {
         int c[3];
         for (int a = 0; a < 3; ++a) {
             c[a] = ffloor(uh[a], ul[a]);
@@ -328,9 +395,9 @@ __device__ bool sample(const GridC &g, int mode, const S *const *f, int ncomp,
         C c11 = wx0 * AL_FV(F, F2, base + sz + sy) + t[0] * AL_FV(F, F2, base + sz + sy + sx);
         out[q] = wz0 * (wy0 * c00 + t[1] * c10) + t[2] * (wy0 * c01 + t[1] * c11);
     }
-#undef AL_FV
     return true;
 }
+#undef AL_FV
 
 // 1/h in the arithmetic type (no FP64 division for FP32 instances)
 template <typename C> __device__ __forceinline__ C inv_h(const GridC &g);
@@ -344,7 +411,15 @@ template <> __device__ __forceinline__ double inv_h<double>(const GridC &g) { re
 // float and the upstream direction is ill-conditioned (|u0_n| below 1 % of
 // the velocity scale, where FP32 rounding of the samples is amplified by
 // 1/|u0_n|); the caller then repeats the evaluation in FP64.
-template <typename T, typename C>
+// With LANES = 32 a whole warp evaluates one point together (the volume-
+// average sampler shares its cells among the lanes); every lane then holds
+// the same result and lane 0 alone counts the status events.
+template <int LANES>
+__device__ __forceinline__ void st_count(int *status, int e) {
+    if (LANES == 1 || (threadIdx.x & 31) == 0) atomicAdd(&status[e], 1);
+}
+
+template <typename T, typename C, int LANES = 1>
 __device__ int point_fstar(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, const int l, const C Pa[3],
                            const C Pd[3], const C t[3], C fstar[3], int *status, const bool refine_ok,
                            const C ab[3]) {
@@ -352,9 +427,10 @@ __device__ int point_fstar(const GridC &g, const BeamsC &b, const StepPtrs<T> &p
     C ua[3];
     float la[3];
     for (int a = 0; a < 3; ++a) to_cell(g, a, Pa[a], ua[a], la[a]);
+    const C epsc = b.sample_mode == 2 ? (C)(b.eps[l] / g.h) : (C)0;
     C Ua[3];
-    if (!sample(g, b.sample_mode, p.U, 3, ua, la, Ua)) {
-        atomicAdd(&status[ST_PA_OUTSIDE], 1);
+    if (!sample<LANES>(g, b.sample_mode, epsc, p.U, 3, ua, la, Ua)) {
+        st_count<LANES>(status, ST_PA_OUTSIDE);
         return 0;
     }
     // Eq. almPreliminaryVelocity and its component normal to the tangent
@@ -370,13 +446,13 @@ __device__ int point_fstar(const GridC &g, const BeamsC &b, const StepPtrs<T> &p
     if ((double)nn >= b.tau) {
         for (int a = 0; a < 3; ++a) es[a] = -u0n[a] / nn;
     } else {
-        atomicAdd(&status[ST_FALLBACK], 1);
+        st_count<LANES>(status, ST_FALLBACK);
         C gp[3];
         C gt = (C)b.g_up[0] * t[0] + (C)b.g_up[1] * t[1] + (C)b.g_up[2] * t[2];
         for (int a = 0; a < 3; ++a) gp[a] = (C)b.g_up[a] - gt * t[a];
         C gn = tsqrt(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2]);
         if (gn > (C)0) for (int a = 0; a < 3; ++a) es[a] = gp[a] / gn;
-        else { es[0] = es[1] = es[2] = (C)0; atomicAdd(&status[ST_FALLBACK_ZERO], 1); }
+        else { es[0] = es[1] = es[2] = (C)0; st_count<LANES>(status, ST_FALLBACK_ZERO); }
     }
     // Eq. almSamplingPoint: offset (I - n_p n_p^T) l_s e_s
     const C ell = (C)b.ell_s[l];
@@ -389,14 +465,13 @@ __device__ int point_fstar(const GridC &g, const BeamsC &b, const StepPtrs<T> &p
         C off_c = (v[a] - (C)b.n_p[a] * vn) * inv_h<C>(g);
         ff_add(ua[a], la[a], off_c, us[a], ls[a]);
     }
-    C Us[3], as = (C)0;
-    bool ok = sample(g, b.sample_mode, p.U, 3, us, ls, Us);
-    if (ok && g.has_alpha) {
-        const T *af[1] = {p.alpha};
-        ok = sample(g, b.sample_mode, af, 1, us, ls, &as);
-    }
+    // U and alpha at P_s in one pass over the stencil (4 components)
+    C Us[4];
+    const T *fua[4] = {p.U[0], p.U[1], p.U[2], p.alpha};
+    const bool ok = sample<LANES>(g, b.sample_mode, epsc, fua, g.has_alpha ? 4 : 3, us, ls, Us);
+    const C as = g.has_alpha ? Us[3] : (C)0;
     if (!ok) {
-        atomicAdd(&status[ST_PS_OUTSIDE], 1);
+        st_count<LANES>(status, ST_PS_OUTSIDE);
         return 0;
     }
     const C rho = g.has_alpha ? as * (C)g.rho1 + ((C)1 - as) * (C)g.rho2 : (C)g.rho_const;
@@ -420,7 +495,7 @@ __device__ int point_fstar(const GridC &g, const BeamsC &b, const StepPtrs<T> &p
         // reaction following the fluid's acceleration relative to the beam
         C af[3] = {(C)0, (C)0, (C)0};
         if (p.Uprev[0]) {
-            sample(g, b.sample_mode, p.U, 3, us, ls, af, p.Uprev);          // U - U_prev at P_s
+            sample<LANES>(g, b.sample_mode, epsc, p.U, 3, us, ls, af, p.Uprev);   // U - U_prev at P_s
             const C idt = (C)(1.0 / p.dt);
             for (int a = 0; a < 3; ++a) af[a] *= idt;
         }
@@ -438,9 +513,11 @@ __device__ int point_fstar(const GridC &g, const BeamsC &b, const StepPtrs<T> &p
 }
 
 // ---------------------------------------------------------------------------
-// k_points: Sec. 3.2.2 - 3.2.3, one thread per actuator point
+// k_points: Sec. 3.2.2 - 3.2.3, one thread per actuator point (LANES = 1) or
+// one warp per point (LANES = 32, for the volume-average sampler; every lane
+// computes the same values and lane 0 stores them)
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int LANES = 1>
 __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, const Scratch<T> &sc, int *status,
                          const int i) {
     const int has_prev = *sc.hasPrev;
@@ -468,7 +545,7 @@ __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, 
     T ab[3] = {(T)0, (T)0, (T)0};
     if (b.inertia && p.Pdd[0])
         for (int a = 0; a < 3; ++a) ab[a] = p.Pdd[a][i];
-    if (point_fstar<T, T>(g, b, p, l, Pa, Pd, t, fstar, status, sizeof(T) == 4, ab)) {
+    if (point_fstar<T, T, LANES>(g, b, p, l, Pa, Pd, t, fstar, status, sizeof(T) == 4, ab)) {
         // ill-conditioned upstream direction: the same evaluation in FP64
         double Pa64[3], Pd64[3], t64[3], f64[3], ab64[3];
         for (int a = 0; a < 3; ++a) { Pa64[a] = (double)Pa[a]; Pd64[a] = (double)Pd[a]; ab64[a] = (double)ab[a]; }
@@ -483,10 +560,11 @@ __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, 
         double nn = sqrt(t64[0] * t64[0] + t64[1] * t64[1] + t64[2] * t64[2]);
         if (nn > 0.0) for (int a = 0; a < 3; ++a) t64[a] /= nn;
         else t64[0] = t64[1] = t64[2] = 0.0;
-        point_fstar<T, double>(g, b, p, l, Pa64, Pd64, t64, f64, status, false, ab64);
+        point_fstar<T, double, LANES>(g, b, p, l, Pa64, Pd64, t64, f64, status, false, ab64);
         for (int a = 0; a < 3; ++a) fstar[a] = (T)f64[a];
-        atomicAdd(&status[ST_REFINED], 1);
+        st_count<LANES>(status, ST_REFINED);
     }
+    if (LANES > 1 && (threadIdx.x & 31) != 0) return;
     // Eq. almForceRelaxation and the per-CV load
     const T af = (T)b.alpha_f[l];
     const T L = (T)b.cv_len[i];
@@ -1990,6 +2068,12 @@ __global__ void __launch_bounds__(256) k_points(GridC g, BeamsC b, StepPtrs<T> p
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < b.n_points) d_points(g, b, p, sc, status, i);
 }
+// one warp per point (volume-average sampler)
+template <typename T>
+__global__ void __launch_bounds__(256) k_points_w(GridC g, BeamsC b, StepPtrs<T> p, Scratch<T> sc, int *status) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i < b.n_points) d_points<T, 32>(g, b, p, sc, status, i);
+}
 template <typename T>
 __global__ void __launch_bounds__(256) k_segments(BeamsC b, Scratch<T> sc) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2054,6 +2138,17 @@ __global__ void __launch_bounds__(256) kb_points(const Inst<T> *I, const int *se
         const int q = owner(pre, n, gid);
         const Inst<T> &x = I[AL_SEL(q)];
         d_points(x.g, x.b, x.p, x.sc, x.status, (int)(gid - pre[q]));
+    }
+}
+// one warp per point, for batches holding an instance with the volume-average sampler
+template <typename T>
+__global__ void __launch_bounds__(256) kb_points_w(const Inst<T> *I, const int *sel, const long long *pre, int n) {
+    const long long total = pre[n];
+    const long long nw = (long long)gridDim.x * blockDim.x / 32;
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+        const int q = owner(pre, n, w);
+        const Inst<T> &x = I[AL_SEL(q)];
+        d_points<T, 32>(x.g, x.b, x.p, x.sc, x.status, (int)(w - pre[q]));
     }
 }
 template <typename T>
