@@ -75,6 +75,7 @@ extern "C" {
 #define AL_ST_REFINED        6 /* geometric decisions re-taken in FP64 (near ties)     */
 #define AL_ST_IRREGULAR      7 /* lines projected by exhaustive segment search         */
 #define AL_ST_SUPPORT        8 /* (cell, line) pairs within 3 eps: kernel-cell updates   */
+#define AL_ST_REPLAYED       9 /* bricks that replayed recorded pairs instead of gathering them */
 #define AL_STATUS_N         16
 
 /* ---- descriptors ------------------------------------------------------- */
@@ -207,8 +208,9 @@ int al_trace_last(al_grid g, float *ms /* [AL_TRACE_N] */);
  * SM of the batched brick passes, 0 = as many as fit. */
 #define AL_OPT_SPREAD_CTAS  3
 /* AL_OPT_SPREAD selects the projection of Eq. almMomentumSource:
- *   AL_SPREAD_GATHER (default): cell-centric gather per brick, every cell of
- *     S written once by one thread, lines summed in line order, no atomics
+ *   AL_SPREAD_GATHER (default): cell-centric pass per brick, every cell of S
+ *     written once by one thread; each cell's sources are summed as exact
+ *     fixed-point integers, so the result does not depend on their order
  *     (bitwise reproducible);
  *   AL_SPREAD_SCATTER: for comparison, lines with a walk certificate add
  *     their sources segment by segment with float atomics (summation order,
@@ -218,6 +220,15 @@ int al_trace_last(al_grid g, float *ms /* [AL_TRACE_N] */);
 #define AL_OPT_SPREAD       4
 #define AL_SPREAD_GATHER    0
 #define AL_SPREAD_SCATTER   1
+/* AL_OPT_RECORD (default 1): with AL_WEIGHTS_SEGMENT and the gather, the
+ * segment pass records every (cell, segment) pair it finds inside the 3 eps
+ * support (cell, node, the two node weights), in a region per brick sized
+ * from the previous step's counts, and the gather replays the records of
+ * its brick instead of recomputing those pairs.  A brick whose pairs did not
+ * fit its region (the first step, a beam that moved into it) is recomputed,
+ * with the same bits.  The record arena is allocated by al_load_beams from
+ * the lines' length and kernel width (16 bytes per pair in FP32, 24 in FP64). */
+#define AL_OPT_RECORD       5
 int al_set_option(al_grid g, int option, int value);
 
 /* Autotuner: runs the caller's step (same in/out as al_sample_drag_spread)

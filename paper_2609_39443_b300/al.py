@@ -20,9 +20,9 @@ AL_OK, AL_ERR_ARG, AL_ERR_CUDA, AL_ERR_OOM, AL_ERR_STATE, AL_ERR_TIMEOUT, AL_ERR
 AL_FP32, AL_FP64 = 0, 1
 AL_STATUS_N = 16
 (ST_PA_OUTSIDE, ST_PS_OUTSIDE, ST_FALLBACK, ST_FALLBACK_ZERO, ST_ZERO_WEIGHT, ST_DEPOSIT_LOST,
- ST_REFINED, ST_IRREGULAR, ST_SUPPORT) = range(9)
+ ST_REFINED, ST_IRREGULAR, ST_SUPPORT, ST_REPLAYED) = range(10)
 
-OPT_WEIGHTS, OPT_BRICK_Z, OPT_SPREAD_CTAS, OPT_SPREAD = 1, 2, 3, 4
+OPT_WEIGHTS, OPT_BRICK_Z, OPT_SPREAD_CTAS, OPT_SPREAD, OPT_RECORD = 1, 2, 3, 4, 5
 WEIGHTS_BRICK, WEIGHTS_SEGMENT = 0, 1
 SPREAD_GATHER, SPREAD_SCATTER = 0, 1
 

@@ -81,6 +81,13 @@ struct al_grid_s {
     double *totalsInt = nullptr;
     int *hasPrev = nullptr;           // device flag: f_prev is valid
     int *anyIrr = nullptr;            // device flag: some line without a walk certificate
+    unsigned int *smax = nullptr;     // device: bound on one spread contribution (float bits)
+    int *anyZero = nullptr;           // device flag: some node with w_k = 0
+    int *rcnt = nullptr, *rcap = nullptr;   // per brick: records found / region capacity
+    long long *roff = nullptr;        // per brick: region start
+    void *rec = nullptr;              // record arena (rec_total records)
+    long long rec_total = 0;
+    int opt_record = 1;
 
     // tracing
     bool trace = false;
@@ -94,7 +101,7 @@ static void trace_mark(al_grid g, int i, cudaStream_t st) {
 static void free_beams(al_grid g) {
     void *ptrs[] = {g->d_line_off, g->d_line_of, g->d_d, g->d_cdn, g->d_cdt, g->d_eps, g->d_ell, g->d_af,
                     g->d_cvl, g->d_cmn, g->d_cmt, g->fprev, g->uhi, g->segD, g->segIl2, g->nodeM, g->fhat, g->ulo,
-                    g->nodeTau, g->segWa, g->segWb, g->w, g->lineF, g->lines, g->mask, g->wfix};
+                    g->nodeTau, g->segWa, g->segWb, g->w, g->lineF, g->lines, g->mask, g->wfix, g->rec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     g->d_line_off = g->d_line_of = nullptr;
@@ -105,6 +112,8 @@ static void free_beams(al_grid g) {
     g->wfix = nullptr;
     g->lines = nullptr;
     g->mask = nullptr;
+    g->rec = nullptr;
+    g->rec_total = 0;
     g->loaded = false;
     g->n_lines = g->n_points = g->mask_words = 0;
 }
@@ -165,7 +174,11 @@ extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
     if ((e = dalloc(&g->brickSum, 3 * (size_t)g->nbrick_max)) != cudaSuccess ||
         (e = dalloc(&g->scatSum, 3)) != cudaSuccess ||
         (e = dalloc(&g->statusInt, AL_STATUS_N)) != cudaSuccess || (e = dalloc(&g->totalsInt, 6)) != cudaSuccess ||
-        (e = dalloc(&g->hasPrev, 1)) != cudaSuccess || (e = dalloc(&g->anyIrr, 1)) != cudaSuccess) {
+        (e = dalloc(&g->hasPrev, 1)) != cudaSuccess || (e = dalloc(&g->anyIrr, 1)) != cudaSuccess ||
+        (e = dalloc(&g->smax, 1)) != cudaSuccess || (e = dalloc(&g->anyZero, 1)) != cudaSuccess ||
+        (e = dalloc(&g->rcnt, (size_t)g->nbrick_max)) != cudaSuccess ||
+        (e = dalloc(&g->rcap, (size_t)g->nbrick_max)) != cudaSuccess ||
+        (e = dalloc(&g->roff, (size_t)g->nbrick_max)) != cudaSuccess) {
         int rc = cuda_fail(e, "cudaMalloc");
         al_destroy(g);
         return rc;
@@ -264,6 +277,33 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     AL_CUDA(cudaMemset(g->mask, 0, ((size_t)g->nbrick_max * g->mask_words ? (size_t)g->nbrick_max * g->mask_words : 1) * sizeof(uint32_t)));
     AL_CUDA(cudaMemset(g->hasPrev, 0, sizeof(int)));
     AL_CUDA(cudaMemset(g->anyIrr, 0, sizeof(int)));
+    AL_CUDA(cudaMemset(g->smax, 0, sizeof(unsigned int)));
+    AL_CUDA(cudaMemset(g->anyZero, 0, sizeof(int)));
+    // record arena for the replayed gather: cells within R_c = 3 eps / h of a
+    // line of length L_c (cells) number about pi R_c^2 L_c + 4/3 pi R_c^3 plus
+    // half the surface; a quarter more, and 4096
+    {
+        double est = 0.0;
+        for (int l = 0; l < b.n_lines; ++l) {
+            double L = 0.0;
+            for (int i = b.line_off[l]; i < b.line_off[l + 1]; ++i) L += b.cv_len[i];
+            const double Rc = 3.0 * b.eps[l] / g->d.dx, Lc = L / g->d.dx, pi = 3.14159265358979323846;
+            est += pi * Rc * Rc * Lc + 4.0 / 3.0 * pi * Rc * Rc * Rc + pi * Rc * Lc + 2.0 * pi * Rc * Rc + 64.0;
+        }
+        const size_t rsz = g->d.precision == AL_FP64 ? sizeof(al::Rec<double>) : sizeof(al::Rec<float>);
+        long long want = b.n_lines > 0 ? (long long)(1.25 * est) + 4096 : 0;
+        want = std::min<long long>(want, (8ll << 30) / (long long)rsz);       // at most 8 GiB
+        if (want > 0 && cudaMalloc(&g->rec, (size_t)want * rsz) == cudaSuccess) {
+            g->rec_total = want;
+        } else {
+            (void)cudaGetLastError();                  // no arena: every brick is gathered
+            g->rec = nullptr;
+            g->rec_total = 0;
+        }
+        AL_CUDA(cudaMemset(g->rcnt, 0, (size_t)g->nbrick_max * sizeof(int)));
+        AL_CUDA(cudaMemset(g->rcap, 0, (size_t)g->nbrick_max * sizeof(int)));
+        AL_CUDA(cudaMemset(g->roff, 0, (size_t)g->nbrick_max * sizeof(long long)));
+    }
     g->loaded = true;
     return AL_OK;
 }
@@ -338,7 +378,8 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     sc.segIl2 = (T *)g->segIl2; sc.nodeM = (T *)g->nodeM; sc.nodeTau = g->nodeTau;
     sc.segWa = g->segWa; sc.segWb = g->segWb; sc.wfix = g->wfix; sc.w = g->w; sc.fhat = (T *)g->fhat; sc.lineF = g->lineF;
     sc.lines = g->lines; sc.mask = g->mask; sc.brickSum = g->brickSum; sc.scatSum = g->scatSum;
-    sc.hasPrev = g->hasPrev; sc.anyIrr = g->anyIrr;
+    sc.hasPrev = g->hasPrev; sc.anyIrr = g->anyIrr; sc.smax = g->smax; sc.anyZero = g->anyZero;
+    sc.rec = (Rec<T> *)g->rec; sc.rcnt = g->rcnt; sc.rcap = g->rcap; sc.roff = g->roff;
     BeamsC &bc = I.b;
     bc.n_lines = g->n_lines; bc.n_points = np; bc.mask_words = g->mask_words;
     bc.line_off = g->d_line_off; bc.line_of = g->d_line_of;
@@ -350,6 +391,9 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     bc.cm_n = g->d_cmn; bc.cm_t = g->d_cmt;
     bc.inertia = (g->d_cmn != nullptr && g->n_lines > 0) ? 1 : 0;
     I.g = g->gc;
+    I.g.rec_total = g->rec_total;
+    I.g.nbrick_max = g->nbrick_max;
+    I.g.rmode = (g->opt_record && g->gc.wmode != 0 && g->gc.smode == 0 && g->rec_total > 0) ? 1 : 0;
     I.status = out->status ? out->status : g->statusInt;
     I.totals = out->totals ? out->totals : g->totalsInt;
     return I;
@@ -441,6 +485,10 @@ extern "C" int al_set_option(al_grid g, int option, int value) {
         if (value != AL_SPREAD_GATHER && value != AL_SPREAD_SCATTER) return AL_ERR_ARG;
         g->gc.smode = value;
         return AL_OK;
+    case AL_OPT_RECORD:
+        if (value != 0 && value != 1) return AL_ERR_ARG;
+        g->opt_record = value;
+        return AL_OK;
     default:
         return AL_ERR_ARG;
     }
@@ -472,7 +520,8 @@ extern "C" int al_destroy(al_grid g) {
     cudaDeviceSynchronize();
     if (g->trace) al_trace_enable(g, 0);
     free_beams(g);
-    void *ptrs[] = {g->brickSum, g->scatSum, g->statusInt, g->totalsInt, g->hasPrev, g->anyIrr};
+    void *ptrs[] = {g->brickSum, g->scatSum, g->statusInt, g->totalsInt, g->hasPrev, g->anyIrr, g->smax,
+                    g->anyZero, g->rcnt, g->rcap, g->roff};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete g;

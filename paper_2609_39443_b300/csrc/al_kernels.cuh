@@ -11,13 +11,18 @@
 //               FP64 sum of F
 //   k_mask      per segment: marks the bricks its 3-eps box touches
 //   k_weights   per segment: w contributions of the cells whose closest
-//               segment it is (Sec. 3.2.4, w_k), FP32 compensated sums
-//   k_normalise per node: w_k, f^_k = F_k / w_k
-//   k_spread    per brick of 16x16x8 cells: cell-centric gather of
-//               Eq. almMomentumSource over the lines of the brick, every
-//               cell of S written exactly once, no atomics
-//   k_deposit   zero-weight nodes (w_k = 0) deposit their load in their cell
-//   k_totals    FP64 sum F and sum S V
+//               segment it is (Sec. 3.2.4, w_k), FP32 compensated sums;
+//               records every such (cell, segment) pair in its brick's
+//               region of the record arena
+//   k_bweights  per brick: the same sums for lines without a walk
+//               certificate (or all lines), exact fixed-point integers
+//   k_normalise per node: w_k, f^_k = F_k / w_k, and a bound on one source
+//   k_spread    per brick of 16 x 16 x h cells: Eq. almMomentumSource, the
+//               recorded pairs replayed and the other lines gathered, each
+//               cell's sources summed as fixed-point integers in shared
+//               memory, then every cell of S written exactly once; the
+//               zero-weight nodes (w_k = 0) deposit their load in their cell
+//   k_totals    FP64 sum F and sum S V; sizes next step's record regions
 //
 // Geometry runs in cell units.  FP32 instances carry point positions as
 // float-float pairs (hi + lo) so that cell-relative offsets are accurate to
@@ -41,7 +46,8 @@ constexpr float BRICK_DIAG = 27.72f;             // diagonal of the tallest bric
 constexpr double PI_D = 3.14159265358979323846;
 
 enum { ST_PA_OUTSIDE = 0, ST_PS_OUTSIDE = 1, ST_FALLBACK = 2, ST_FALLBACK_ZERO = 3,
-       ST_ZERO_WEIGHT = 4, ST_DEPOSIT_LOST = 5, ST_REFINED = 6, ST_IRREGULAR = 7, ST_SUPPORT = 8 };
+       ST_ZERO_WEIGHT = 4, ST_DEPOSIT_LOST = 5, ST_REFINED = 6, ST_IRREGULAR = 7, ST_SUPPORT = 8,
+       ST_REPLAYED = 9 };
 
 struct GridC {
     int nx, ny, nz;
@@ -56,7 +62,17 @@ struct GridC {
     int wmode;                   // 0: all weights from the brick pass; 1: segment pass for certified lines
     int bz;                      // brick height of the projection (4, 8 or 16 cells)
     int smode;                   // 0: gather (every line); 1: scatter with atomics for certified lines
+    int rmode;                   // 1: the segment pass records its (cell, segment) pairs, the spread replays them
+    long long rec_total;         // capacity of the record arena (records)
+    long long nbrick_max;        // bricks at the lowest brick height (size of the per-brick arrays)
 };
+
+// one (cell, segment) pair of a certified line inside the 3 eps support, as
+// the segment pass found it: the cell within its brick (z * 256 + y * 16 + x),
+// the segment's start node (REC_SINGLE: a one-node line, both ends the same
+// node) and the node weights omega eta of the two ends
+template <typename T> struct Rec { int cell; int ka; T wa, wb; };
+constexpr int REC_SINGLE = 1 << 30;
 
 struct BeamsC {
     int n_lines, n_points, mask_words;
@@ -107,6 +123,12 @@ struct Scratch {
     double *scatSum;             // [3] sum of S added by the scatter form
     int *hasPrev;                // [1] a previous relaxed force exists (set by k_totals)
     int *anyIrr;                 // [1] some line has no walk certificate (set by k_lines)
+    unsigned int *smax;          // [1] bound on one spread contribution (float bits, set by k_normalise)
+    int *anyZero;                // [1] some node has w_k = 0 (set by k_normalise)
+    Rec<T> *rec;                 // [rec_total] pair records, a region per brick
+    int *rcnt;                   // [nbrick_max] records found this step per brick
+    int *rcap;                   // [nbrick_max] capacity of the brick's region this step
+    long long *roff;             // [nbrick_max] start of the brick's region
 };
 
 template <typename T>
@@ -209,6 +231,16 @@ __device__ __forceinline__ float rel(float uh, float ul, int B) {
 }
 __device__ __forceinline__ double rel(double uh, float, int B) { return uh - (double)B; }
 
+// explicitly rounded arithmetic (no contraction or reordering by the
+// compiler): the segment pass and the brick gather compute the same
+// per-pair values and must agree bit for bit
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // inside [0, n) along one axis
 template <typename T>
 __device__ __forceinline__ bool inside_axis(T uh, float ul, int n) {
@@ -267,6 +299,42 @@ __device__ __forceinline__ unsigned long long to_fixed(double v, int sh) {
     if (s >= 0) return m << s;
     if (s <= -53) return 0ull;
     return m >> (-s);
+}
+
+// Signed v 2^sh truncated toward zero (odd in v), from the bits of v: the
+// momentum source of a brick is summed as such integers, exactly and in any
+// order, so every path that produces the same contributions produces the
+// same S.  The caller keeps |v| 2^sh below 2^61.
+__device__ __forceinline__ long long to_fixed_s(float v, int sh) {
+    const unsigned int bits = __float_as_uint(v);
+    const int e = (int)((bits >> 23) & 0xffu);
+    if (e == 0) return 0ll;                                // zero or subnormal
+    const long long m = (long long)((bits & 0x7fffffu) | 0x800000u);
+    const int s = e - 150 + sh;
+    const long long r = s >= 0 ? (m << s) : (s <= -24 ? 0ll : (m >> (-s)));
+    return (bits >> 31) ? -r : r;
+}
+__device__ __forceinline__ long long to_fixed_s(double v, int sh) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((bits >> 52) & 0x7ffull);
+    if (e == 0) return 0ll;
+    const long long m = (long long)((bits & 0xfffffffffffffull) | 0x10000000000000ull);
+    const int s = e - 1075 + sh;
+    const long long r = s >= 0 ? (m << s) : (s <= -53 ? 0ll : (m >> (-s)));
+    return (bits >> 63) ? -r : r;
+}
+// the fixed-point sum back in the field precision (one rounding)
+__device__ __forceinline__ void from_fixed(long long a, int sh, float &v) { v = ldexpf(__ll2float_rn(a), -sh); }
+__device__ __forceinline__ void from_fixed(long long a, int sh, double &v) { v = ldexp(__ll2double_rn(a), -sh); }
+// shift of the spread's fixed point: M bounds every single contribution
+// (|eta f^| or a deposit |F / V|) and a cell receives at most one per line
+// plus one per deposited node, so |sum| 2^sh < 2^61
+__device__ __forceinline__ int spread_shift(unsigned int mbits, long long ncontrib) {
+    const float M = __uint_as_float(mbits);
+    if (!(M > 0.0f)) return 0;
+    int e;
+    frexp((double)M * (double)(ncontrib + 1), &e);        // bound < 2^e
+    return 61 - e;
 }
 
 // ---------------------------------------------------------------------------
@@ -575,7 +643,7 @@ __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, 
         p.F[a][i] = f * L;
     }
     sc.wfix[i] = 0ull;                                   // fixed-point weights start at zero
-    if (i == 0) *sc.anyIrr = 0;
+    if (i == 0) { *sc.anyIrr = 0; *sc.smax = 0u; *sc.anyZero = 0; }
     // projection positions in cell units
     for (int a = 0; a < 3; ++a) {
         T uh;
@@ -941,25 +1009,86 @@ struct WSeg {
     double eps;
 };
 
+// Foot parameter s (clamped to [0, 1]) and squared distance r^2 of a cell
+// from a segment, from the cell's offset x to the segment start and the
+// segment vector D (cell units), every operation rounded explicitly
+template <typename T>
+__device__ __forceinline__ void foot_sr(const T x[3], const T D[3], T il2, T &s, T &r2) {
+    s = r_mul(r_fma(x[2], D[2], r_fma(x[1], D[1], r_mul(x[0], D[0]))), il2);
+    s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
+    const T e0 = r_fma(-s, D[0], x[0]), e1 = r_fma(-s, D[1], x[1]), e2 = r_fma(-s, D[2], x[2]);
+    r2 = r_fma(e2, e2, r_fma(e1, e1, r_mul(e0, e0)));
+}
+// (s, r^2) of the global cell cg against segment ka, with offsets taken from
+// the integer origin floor(u_ka) of the segment's start node: the values the
+// segment pass computes for the same pair
+template <typename T>
+__device__ __forceinline__ void pair_sr(const Scratch<T> &sc, long long np, int ka, const int cg[3], T &s, T &r2) {
+    T x[3], D[3];
+    for (int a = 0; a < 3; ++a) {
+        const T uh = sc.uhi[a * np + ka];
+        const int O = ifloor(uh);
+        x[a] = ((T)(cg[a] - O) + (T)0.5) - rel(uh, sc.ulo[a * np + ka], O);
+        D[a] = sc.segD[a * np + ka];
+    }
+    foot_sr(x, D, sc.segIl2[ka], s, r2);
+}
+// the pair's kernel value eta split over the segment's two nodes (omega eta)
+template <typename T>
+__device__ __forceinline__ void pair_w(T eta, T s, T &wa, T &wb) {
+    wa = r_mul(eta, r_add((T)1, -s));
+    wb = r_mul(eta, s);
+}
+// the pair's momentum source for nodal forces fa, fb (S receives minus this)
+template <typename T>
+__device__ __forceinline__ T pair_src(T wa, T wb, T fa, T fb) { return r_fma(wa, fa, r_mul(wb, fb)); }
+
 // What a visited cell feeds: the segment's two weight sums (SC = false), or
 // in the scatter form of the projection the cell's momentum source, added
 // to S with atomics (SC = true; the sums of what was added feed the totals).
 template <typename T, bool SC> struct WSink;
 template <typename T> struct WSink<T, false> {
     Acc<T> wa, wb;
-    __device__ __forceinline__ void add(const GridC &, const StepPtrs<T> &, long long, T eta, T s) {
-        wa.add(((T)1 - s) * eta);
-        wb.add(s * eta);
+    // rmode: each pair is also recorded in its brick's region for the spread
+    Rec<T> *rec = nullptr;
+    int *rcnt;
+    const int *rcap;
+    const long long *roff;
+    int ka, nbx, nby, bzs;
+    __device__ __forceinline__ void add(const GridC &, const StepPtrs<T> &, const int cg[3], T eta, T s) {
+        T a, b;
+        pair_w(eta, s, a, b);
+        wa.add(a);
+        wb.add(b);
+        if (rec) {
+            // the lanes adding to one brick take consecutive slots with one atomic
+            const int br = (cg[0] >> 4) + nbx * ((cg[1] >> 4) + nby * (cg[2] >> bzs));
+            const int cell = ((cg[2] & ((1 << bzs) - 1)) << 8) | ((cg[1] & 15) << 4) | (cg[0] & 15);
+            const unsigned act = __activemask();
+            const unsigned grp = __match_any_sync(act, br);
+            const int lane = threadIdx.x & 31, lead = __ffs(grp) - 1;
+            int base = 0;
+            if (lane == lead) base = atomicAdd(&rcnt[br], __popc(grp));
+            base = __shfl_sync(grp, base, lead);
+            const int pos = base + __popc(grp & ((1u << lane) - 1u));
+            if (pos < rcap[br]) {
+                Rec<T> r;
+                r.cell = cell; r.ka = ka; r.wa = a; r.wb = b;
+                rec[roff[br] + pos] = r;
+            }
+        }
     }
 };
 template <typename T> struct WSink<T, true> {
     T fa[3], fb[3];
     Acc<T> sum[3];
     int nsupp = 0;
-    __device__ __forceinline__ void add(const GridC &, const StepPtrs<T> &p, long long idx, T eta, T s) {
-        const T wa = eta * ((T)1 - s), wb = eta * s;
+    __device__ __forceinline__ void add(const GridC &g, const StepPtrs<T> &p, const int cg[3], T eta, T s) {
+        const long long idx = cg[0] + (long long)g.nx * (cg[1] + (long long)g.ny * cg[2]);
+        T wa, wb;
+        pair_w(eta, s, wa, wb);
         for (int a = 0; a < 3; ++a) {
-            const T v = -(wa * fa[a] + wb * fb[a]);
+            const T v = -pair_src(wa, wb, fa[a], fb[a]);
             atomicAdd(&p.S[a][idx], v);
             sum[a].add(v);
         }
@@ -1019,19 +1148,17 @@ __device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const Gri
             if (pos) return;
         }
     }
-    T s = (x[0] * c.D[0] + x[1] * c.D[1] + x[2] * c.D[2]) * c.il2;
-    s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
-    T e0 = x[0] - s * c.D[0], e1 = x[1] - s * c.D[1], e2 = x[2] - s * c.D[2];
-    T r2 = e0 * e0 + e1 * e1 + e2 * e2;
+    T s, r2;
+    foot_sr(x, c.D, c.il2, s, r2);
     bool in;
     if (r2 < c.R2 - c.gr) in = true;
     else if (r2 > c.R2 + c.gr) in = false;
     else { in = within_f64(g, p, c.eps, c.k, c.n, AL_CG(0), AL_CG(1), AL_CG(2)); atomicAdd(&status[ST_REFINED], 1); }
     if (!in) return;
-    T eta = c.eta0 * Tr<T>::ex2(-r2 * c.ie2);
-    const long long idx = SC ? AL_CG(0) + (long long)g.nx * (AL_CG(1) + (long long)g.ny * AL_CG(2)) : 0;
+    const T eta = c.eta0 * Tr<T>::ex2(-r2 * c.ie2);
+    const int cg[3] = {AL_CG(0), AL_CG(1), AL_CG(2)};
 #undef AL_CG
-    sink.add(g, p, idx, eta, s);
+    sink.add(g, p, cg, eta, s);
 }
 
 // warp sum of compensated lane sums, as float-float (FP32) or plain FP64
@@ -1196,6 +1323,12 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
     WSink<T, SC> sink;
     if constexpr (SC)
         for (int a = 0; a < 3; ++a) { sink.fa[a] = sc.fhat[a * np + k]; sink.fb[a] = sc.fhat[a * np + c.kb]; }
+    else if (g.rmode) {
+        sink.rec = sc.rec; sink.rcnt = sc.rcnt; sink.rcap = sc.rcap; sink.roff = sc.roff;
+        sink.ka = k | (c.n == 1 ? REC_SINGLE : 0);
+        sink.nbx = g.nbx; sink.nby = g.nby;
+        sink.bzs = g.bz == 4 ? 2 : (g.bz == 8 ? 3 : 4);
+    }
     const bool regular = lg.regular != 0;
     c.has_lo = regular && c.q >= 1;
     c.has_hi = regular && c.q + 1 <= c.n - 2;
@@ -1217,9 +1350,12 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
 // ---------------------------------------------------------------------------
 // k_normalise: w_k and f^_k = F_k / w_k
 // ---------------------------------------------------------------------------
+// Returns a bound (float bits, rounded up) on what node k contributes to one
+// cell of S: eta0 |f^_k| (max over components), or |F_k| / V when it is
+// deposited.
 template <typename T>
-__device__ void d_normalise(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
-                            const int k) {
+__device__ unsigned int d_normalise(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p,
+                                    int *status, const int k) {
     const long long np = b.n_points;
     const int l = b.line_of[k];
     const int off = b.line_off[l], n = b.line_off[l + 1] - off, q = k - off;
@@ -1236,18 +1372,29 @@ __device__ void d_normalise(const GridC &g, const BeamsC &b, const Scratch<T> &s
         w *= g.V;
     }
     sc.w[k] = w;
+    double mb = 0.0;
     if (w > 0.0) {
         const T wt = (T)w;                         // FP64 sum, divided in the field precision
-        for (int a = 0; a < 3; ++a) sc.fhat[a * np + k] = p.F[a][k] / wt;
+        for (int a = 0; a < 3; ++a) {
+            const T fh = p.F[a][k] / wt;
+            sc.fhat[a * np + k] = fh;
+            mb = fmax(mb, fabs((double)fh));
+        }
+        mb *= lg.eta0;
     } else {
+        for (int a = 0; a < 3; ++a) mb = fmax(mb, fabs((double)p.F[a][k]));
+        mb /= g.V;
         // w_k = 0: the spread deposits F_k in the cell containing the node
         for (int a = 0; a < 3; ++a) sc.fhat[a * np + k] = (T)0;
+        *sc.anyZero = 1;
         atomicAdd(&status[ST_ZERO_WEIGHT], 1);
         const int nn[3] = {g.nx, g.ny, g.nz};
         bool ins = true;
         for (int a = 0; a < 3; ++a) ins = ins && inside_axis(sc.uhi[a * np + k], sc.ulo[a * np + k], nn[a]);
         if (!ins) atomicAdd(&status[ST_DEPOSIT_LOST], 1);
     }
+    // rounded up to float with a relative margin (covers FP32 rounding of the products)
+    return __float_as_uint(fminf(__double2float_ru(mb * 1.0000005), 3.0e38f));
 }
 
 // ---------------------------------------------------------------------------
@@ -1269,7 +1416,7 @@ struct SpreadSmem {
         struct {
             T Fh[3][NN];         // spread: f^ at the nodes
             int sk[NN];          // spread: global node index of each staged node
-            T acc[BZ][3][BX * BY];   // spread: S of the brick's cells, summed in line order
+            long long acc[BZ][3][BX * BY];   // spread: S of the brick's cells, fixed point (2^-sh)
         } s;
         unsigned long long wq[NN];   // weights pass: fixed-point w of the staged nodes
     } u;
@@ -1521,7 +1668,35 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     const int nxb = min(BX, g.nx - B0), nyb = min(BY, g.ny - B1);
     int nsupp = 0;                                   // (cell, line) pairs within 3 eps
     if (!WP)
-        for (int i = threadIdx.x; i < BZ * 3 * BX * BY; i += SPREAD_THREADS) (&sm.u.s.acc[0][0][0])[i] = (T)0;
+        for (int i = threadIdx.x; i < BZ * 3 * BX * BY; i += SPREAD_THREADS) (&sm.u.s.acc[0][0][0])[i] = 0ll;
+    const int fsh = WP ? 0 : spread_shift(*sc.smax, (long long)b.n_points + b.n_lines);
+    // replay: the certified lines' pairs of this brick as the segment pass
+    // recorded them (complete when they fitted the brick's region), added in
+    // fixed point, so in any order and with the bits the gather would give;
+    // the gather below then takes only the lines without a certificate.  Not
+    // when a node has w_k = 0 (its deposit goes with the gathered lines).
+    bool replay = false;
+    if (!WP && g.rmode && *sc.anyZero == 0) {
+        const int nrec = sc.rcnt[br];
+        if (nrec <= sc.rcap[br]) {
+            replay = true;
+            __syncthreads();                             // accumulators cleared
+            const Rec<T> *rr = sc.rec + sc.roff[br];
+            for (int r = threadIdx.x; r < nrec; r += SPREAD_THREADS) {
+                const Rec<T> rc = rr[r];
+                const int ka = rc.ka & ~REC_SINGLE, kb = (rc.ka & REC_SINGLE) ? ka : ka + 1;
+                const int z = rc.cell >> 8, c = rc.cell & 255;
+                for (int a = 0; a < 3; ++a) {
+                    const long long v = to_fixed_s(pair_src(rc.wa, rc.wb, sc.fhat[a * np + ka], sc.fhat[a * np + kb]), fsh);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&sm.u.s.acc[z][a][c]), (unsigned long long)(-v));
+                }
+            }
+            if (threadIdx.x == 0 && nrec > 0) {
+                nsupp += nrec;
+                atomicAdd(&status[ST_REPLAYED], 1);
+            }
+        }
+    }
 
     const int W = b.mask_words;
     uint32_t *mrow = sc.mask + (long long)br * W;
@@ -1532,7 +1707,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     // take a contiguous run of mask words, so a prefix over lanes keeps line
     // order; bricks with more than LIST candidates take several passes (the
     // spread clears the words in the last one)
-    const bool keep_certified = WP ? (g.wmode == 0) : (g.smode == 0);
+    const bool keep_certified = WP ? (g.wmode == 0) : (g.smode == 0 && !replay);
     const int wper = (W + 31) / 32;
     for (int pass = 0;; ++pass) {
         __syncthreads();
@@ -1874,12 +2049,16 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                                     fa0 = sc.fhat[ka]; fa1 = sc.fhat[np + ka]; fa2 = sc.fhat[2 * np + ka];
                                     fb0 = sc.fhat[kb]; fb1 = sc.fhat[np + kb]; fb2 = sc.fhat[2 * np + kb];
                                 }
-                                const T eta = e0v * q;
-                                const T wa = eta * ((T)1 - s), wb = eta * s;
+                                // the pair's values as the segment pass computes them
+                                const int cgl[3] = {B0 + tx, B1 + ty, gz};
+                                T s2, r22;
+                                pair_sr(sc, np, first + js, cgl, s2, r22);
+                                T wa, wb;
+                                pair_w(e0v * Tr<T>::ex2(-r22 * ie2), s2, wa, wb);
                                 const int c = ty * BX + tx;
-                                sm.u.s.acc[z][0][c] -= wa * fa0 + wb * fb0;
-                                sm.u.s.acc[z][1][c] -= wa * fa1 + wb * fb1;
-                                sm.u.s.acc[z][2][c] -= wa * fa2 + wb * fb2;
+                                sm.u.s.acc[z][0][c] -= to_fixed_s(pair_src(wa, wb, fa0, fb0), fsh);
+                                sm.u.s.acc[z][1][c] -= to_fixed_s(pair_src(wa, wb, fa1, fb1), fsh);
+                                sm.u.s.acc[z][2][c] -= to_fixed_s(pair_src(wa, wb, fa2, fb2), fsh);
                             }
                         } else {
                             // omega eta / eta0 into the two nodes of the closest segment, as
@@ -1962,7 +2141,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                         bal &= bal - 1;
                         if (lane == src)
                             for (int a = 0; a < 3; ++a)
-                                sm.u.s.acc[c3[2]][a][c3[1] * BX + c3[0]] -= p.F[a][k] / (T)g.V;
+                                sm.u.s.acc[c3[2]][a][c3[1] * BX + c3[0]] -= to_fixed_s(p.F[a][k] / (T)g.V, fsh);
                         __syncwarp();
                     }
                 }
@@ -1982,8 +2161,10 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
             const long long col = (B0 + tx) + (long long)g.nx * (B1 + ty) + layer * B2;
             for (int z = 0; z < nzb; ++z) {
                 const long long idx = col + layer * z;
-                const T v0 = sm.u.s.acc[z][0][threadIdx.x], v1 = sm.u.s.acc[z][1][threadIdx.x],
-                        v2 = sm.u.s.acc[z][2][threadIdx.x];
+                T v0, v1, v2;
+                from_fixed(sm.u.s.acc[z][0][threadIdx.x], fsh, v0);
+                from_fixed(sm.u.s.acc[z][1][threadIdx.x], fsh, v1);
+                from_fixed(sm.u.s.acc[z][2][threadIdx.x], fsh, v2);
                 p.S[0][idx] = v0; p.S[1][idx] = v1; p.S[2][idx] = v2;
                 cs0 += v0; cs1 += v1; cs2 += v2;
             }
@@ -2032,6 +2213,37 @@ __device__ void d_totals(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
         for (int a = 0; a < 3; ++a) totals[a] = red[a][0];
         for (int a = 0; a < 3; ++a) totals[3 + a] = (red[3 + a][0] + (g.smode ? sc.scatSum[a] : 0.0)) * g.V;
         *sc.hasPrev = 1;                 // the next step relaxes against this one
+    }
+    if (g.rmode) {
+        // record regions of the next step: this step's count per brick plus an
+        // eighth and 16, packed in brick order and cut at the arena's end; every
+        // index up to the lowest brick height gets one (disjoint regions whatever
+        // the brick height of the next step)
+        __syncthreads();
+        long long *scan = reinterpret_cast<long long *>(&red[0][0]);
+        long long run = 0;
+        for (long long b0 = 0; b0 < g.nbrick_max; b0 += 256) {
+            const long long bi = b0 + threadIdx.x;
+            const int c = bi < g.nbrick_max ? sc.rcnt[bi] : 0;
+            const long long want = c > 0 ? (long long)c + (c >> 3) + 16 : 0;
+            scan[threadIdx.x] = want;
+            __syncthreads();
+            for (int o = 1; o < 256; o <<= 1) {          // inclusive scan
+                const long long v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
+                __syncthreads();
+                scan[threadIdx.x] += v;
+                __syncthreads();
+            }
+            if (bi < g.nbrick_max) {
+                const long long off = run + scan[threadIdx.x] - want;
+                const long long cap = off >= g.rec_total ? 0 : (off + want > g.rec_total ? g.rec_total - off : want);
+                sc.roff[bi] = off < g.rec_total ? off : 0;
+                sc.rcap[bi] = (int)cap;
+                sc.rcnt[bi] = 0;
+            }
+            run += scan[255];
+            __syncthreads();
+        }
     }
 }
 
@@ -2103,7 +2315,9 @@ __global__ void __launch_bounds__(128) k_scatter(GridC g, BeamsC b, Scratch<T> s
 template <typename T>
 __global__ void __launch_bounds__(256) k_normalise(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < b.n_points) d_normalise(g, b, sc, p, status, k);
+    unsigned int m = k < b.n_points ? d_normalise(g, b, sc, p, status, k) : 0u;
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(sc.smax, m);
 }
 template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) k_spread(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
@@ -2194,11 +2408,19 @@ __global__ void __launch_bounds__(128) kb_weights(const Inst<T> *I, const int *s
 template <typename T>
 __global__ void __launch_bounds__(256) kb_normalise(const Inst<T> *I, const int *sel, const long long *pre, int n) {
     const long long total = pre[n];
-    for (long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x; gid < total;
-         gid += (long long)gridDim.x * blockDim.x) {
-        const int q = owner(pre, n, gid);
-        const Inst<T> &x = I[AL_SEL(q)];
-        d_normalise(x.g, x.b, x.sc, x.p, x.status, (int)(gid - pre[q]));
+    // the whole warp steps together so the bounds reduce per instance
+    for (long long g0 = (long long)blockIdx.x * blockDim.x; g0 < total; g0 += (long long)gridDim.x * blockDim.x) {
+        const long long gid = g0 + threadIdx.x;
+        int q = -1;
+        unsigned int m = 0u;
+        if (gid < total) {
+            q = owner(pre, n, gid);
+            const Inst<T> &x = I[AL_SEL(q)];
+            m = d_normalise(x.g, x.b, x.sc, x.p, x.status, (int)(gid - pre[q]));
+        }
+        const unsigned int grp = __match_any_sync(0xffffffffu, q);
+        m = __reduce_max_sync(grp, m);
+        if (q >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1 && m) atomicMax(I[AL_SEL(q)].sc.smax, m);
     }
 }
 // persistent: a fixed grid of CTAs walks the bricks of every instance
