@@ -1003,35 +1003,56 @@ struct WSeg {
     int k, q, n, off, nseg, kb, klo, khi;     // klo/khi unused (kept zero-cost)
     int O[3], lo[3], hi[3];
     T A[3], Bn[3], D[3], il2;
+    int O1[3];                    // integer origin floor(u) of the end node kb
+    T B1[3];                      // the end node relative to O1
     T m0[3], m1[3];
     bool has_lo, has_hi;
     T R2, gr, ie2, eta0;
     double eps;
 };
 
+// |x|^2 and x.m with every operation rounded explicitly
+template <typename T>
+__device__ __forceinline__ T norm2_r(const T x[3]) { return r_fma(x[2], x[2], r_fma(x[1], x[1], r_mul(x[0], x[0]))); }
+template <typename T>
+__device__ __forceinline__ T dot_r(const T x[3], const T m[3]) { return r_fma(x[2], m[2], r_fma(x[1], m[1], r_mul(x[0], m[0]))); }
+
 // Foot parameter s (clamped to [0, 1]) and squared distance r^2 of a cell
 // from a segment, from the cell's offset x to the segment start and the
 // segment vector D (cell units), every operation rounded explicitly
 template <typename T>
 __device__ __forceinline__ void foot_sr(const T x[3], const T D[3], T il2, T &s, T &r2) {
-    s = r_mul(r_fma(x[2], D[2], r_fma(x[1], D[1], r_mul(x[0], D[0]))), il2);
+    s = r_mul(dot_r(x, D), il2);
     s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
-    const T e0 = r_fma(-s, D[0], x[0]), e1 = r_fma(-s, D[1], x[1]), e2 = r_fma(-s, D[2], x[2]);
-    r2 = r_fma(e2, e2, r_fma(e1, e1, r_mul(e0, e0)));
+    const T e[3] = {r_fma(-s, D[0], x[0]), r_fma(-s, D[1], x[1]), r_fma(-s, D[2], x[2])};
+    r2 = norm2_r(e);
 }
-// (s, r^2) of the global cell cg against segment ka, with offsets taken from
-// the integer origin floor(u_ka) of the segment's start node: the values the
-// segment pass computes for the same pair
+// offset of the global cell cg from node k, taken from the node's own
+// integer origin floor(u_k)
 template <typename T>
-__device__ __forceinline__ void pair_sr(const Scratch<T> &sc, long long np, int ka, const int cg[3], T &s, T &r2) {
-    T x[3], D[3];
+__device__ __forceinline__ void node_off(const Scratch<T> &sc, long long np, int k, const int cg[3], T x[3]) {
     for (int a = 0; a < 3; ++a) {
-        const T uh = sc.uhi[a * np + ka];
+        const T uh = sc.uhi[a * np + k];
         const int O = ifloor(uh);
-        x[a] = ((T)(cg[a] - O) + (T)0.5) - rel(uh, sc.ulo[a * np + ka], O);
-        D[a] = sc.segD[a * np + ka];
+        x[a] = ((T)(cg[a] - O) + (T)0.5) - rel(uh, sc.ulo[a * np + k], O);
     }
+}
+// (s, r^2) of the global cell cg against segment (ka, kb): offsets from the
+// start node's origin, and where the foot clamps to the end node, r^2 from
+// the end node's origin, so a cell whose closest point is a node gets the
+// same bits whichever of the node's two segments takes it (the segment
+// pass computes the same values)
+template <typename T>
+__device__ __forceinline__ void pair_sr(const Scratch<T> &sc, long long np, int ka, int kb, const int cg[3], T &s,
+                                        T &r2) {
+    T x[3], D[3];
+    node_off(sc, np, ka, cg, x);
+    for (int a = 0; a < 3; ++a) D[a] = sc.segD[a * np + ka];
     foot_sr(x, D, sc.segIl2[ka], s, r2);
+    if (s >= (T)1 && kb != ka) {
+        node_off(sc, np, kb, cg, x);
+        r2 = norm2_r(x);
+    }
 }
 // the pair's kernel value eta split over the segment's two nodes (omega eta)
 template <typename T>
@@ -1124,12 +1145,19 @@ __device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const Gri
                                        int *status, WSink<T, SC> &sink) {
     // global cell index, needed only by the FP64 re-decisions (rare)
 #define AL_CG(a) (ifloor(C[a]) + c.O[a])
-    T x[3];
-    for (int a = 0; a < 3; ++a) x[a] = C[a] - c.A[a];
+    // offsets from the start node (origin O) and from the end node (its own
+    // origin O1): the test at a node's bisector plane is evaluated from that
+    // node's origin, so the two segments meeting there take the same
+    // decision bit for bit and exactly one of them keeps the cell
+    T x[3], C1[3], y[3];
+    for (int a = 0; a < 3; ++a) {
+        x[a] = C[a] - c.A[a];
+        C1[a] = C[a] + (T)(c.O[a] - c.O1[a]);
+        y[a] = C1[a] - c.B1[a];
+    }
     if (regular) {
         if (c.has_lo) {
-            T sg = x[0] * c.m0[0] + x[1] * c.m0[1] + x[2] * c.m0[2];
-            T gs = Tr<T>::gsig(tsqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
+            const T sg = dot_r(x, c.m0), gs = Tr<T>::gsig(tsqrt(norm2_r(x)));
             bool pos;
             if (sg > gs) pos = true;
             else if (sg < -gs) pos = false;
@@ -1137,19 +1165,17 @@ __device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const Gri
             if (!pos) return;
         }
         if (c.has_hi) {
-            T y[3];
-            for (int a = 0; a < 3; ++a) y[a] = C[a] - c.Bn[a];
-            T sg = y[0] * c.m1[0] + y[1] * c.m1[1] + y[2] * c.m1[2];
-            T gs = Tr<T>::gsig(tsqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]));
+            const T sg = dot_r(y, c.m1), gs = Tr<T>::gsig(tsqrt(norm2_r(y)));
             bool pos;
             if (sg > gs) pos = true;
             else if (sg < -gs) pos = false;
-            else pos = w_later_closer(g, sc, p, c.k + 1, c.O, C[0], C[1], C[2], status);
+            else pos = w_later_closer(g, sc, p, c.k + 1, c.O1, C1[0], C1[1], C1[2], status);
             if (pos) return;
         }
     }
     T s, r2;
     foot_sr(x, c.D, c.il2, s, r2);
+    if (s >= (T)1 && c.kb != c.k) r2 = norm2_r(y);         // foot on the end node
     bool in;
     if (r2 < c.R2 - c.gr) in = true;
     else if (r2 > c.R2 + c.gr) in = false;
@@ -1307,6 +1333,8 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
     for (int a = 0; a < 3; ++a) {
         c.A[a] = rel(sc.uhi[a * np + k], sc.ulo[a * np + k], c.O[a]);
         c.Bn[a] = rel(sc.uhi[a * np + c.kb], sc.ulo[a * np + c.kb], c.O[a]);
+        c.O1[a] = ifloor(sc.uhi[a * np + c.kb]);
+        c.B1[a] = rel(sc.uhi[a * np + c.kb], sc.ulo[a * np + c.kb], c.O1[a]);
         c.D[a] = sc.segD[a * np + k];
     }
     c.il2 = sc.segIl2[k];
@@ -2052,7 +2080,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                                 // the pair's values as the segment pass computes them
                                 const int cgl[3] = {B0 + tx, B1 + ty, gz};
                                 T s2, r22;
-                                pair_sr(sc, np, first + js, cgl, s2, r22);
+                                pair_sr(sc, np, first + js, (n == 1) ? first + js : first + js + 1, cgl, s2, r22);
                                 T wa, wb;
                                 pair_w(e0v * Tr<T>::ex2(-r22 * ie2), s2, wa, wb);
                                 const int c = ty * BX + tx;

@@ -128,3 +128,19 @@ def test_batch_replay_equals_alone():
     batch.close()
     for x in alone + inb:
         x.close()
+
+
+def test_segment_pass_keeps_every_wedge_cell():
+    """A random canopy instance with a cell in the wedge behind a node, where
+    both segments' feet clamp to the node and its bisector value sits at the
+    edge of the FP32 band: the two segments must agree on which keeps it.
+    One segment-pass step matches the oracle and its support count."""
+    wl = W.make_batched(6, 4, max_cells=96 * 64 * 64)[1]
+    out = _run(wl, 2, True)
+    o = oracle.sample_drag_spread(wl)
+    o1 = oracle.point_step(wl.grid, wl.beams, wl.step)
+    o2 = oracle.sample_drag_spread(wl, f_prev=o1["f"])
+    for k, ref in ((0, o), (1, o2)):
+        g = {key: out[k][key].astype(np.float64) if key in ("S", "F") else out[k][key] for key in out[k]}
+        compare(wl, g, ref, label=f"wedge step {k}", sumF_ref="abs")
+        assert out[k]["status"][ST_SUPPORT] == oracle.count_support(wl.grid, wl.beams, wl.step.P)
