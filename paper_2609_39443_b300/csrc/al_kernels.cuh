@@ -363,11 +363,11 @@ __device__ __forceinline__ void axis_stencil(T uh, float ul, int n, int &i0, T &
 // Kernel-weighted volume average (the smooth sampler of Sec. 6): weights
 // exp(-(r/eps)^2) of the projection's truncated Gaussian (Eq. almGaussian,
 // its constant cancels) over the cells of the grid whose centre lies within
-// r <= 3 eps of the point, normalised by their sum; epsc = eps / h.  The
-// cells of the support's bounding box are dealt to LANES lanes (x fastest,
-// so neighbouring lanes read neighbouring cells); with LANES = 32 the whole
-// warp calls with the same arguments and a butterfly reduction leaves the
-// same sums, bit for bit, in every lane.  At most 4 components.  Returns
+// r <= 3 eps of the point, normalised by their sum; epsc = eps / h.  One
+// thread (LANES = 1) visits every cell of the support's bounding box; a warp
+// (LANES = 32, all lanes calling with the same arguments) visits only the
+// rows that reach the sphere, 16 neighbouring cells at a time, and a
+// butterfly reduction leaves the same sums, bit for bit, in every lane.  At most 4 components.  Returns
 // false when no cell centre lies within 3 eps (the caller then takes the
 // containing cell).
 template <int LANES, typename S, typename C>
@@ -385,14 +385,52 @@ __device__ bool gauss_avg(const GridC &g, C epsc, const S *const *f, int ncomp, 
         lo[a] = l0;
         bn[a] = h0 - l0 + 1;
     }
-    const int nplane = bn[0] * bn[1];
-    const long long nbox = (long long)nplane * bn[2];
-    const int lane = LANES == 1 ? 0 : (int)(threadIdx.x & 31);
-    // (i, j, k) of box cell t = lane, then advanced by LANES with carries
-    int k = lane / nplane, r = lane - k * nplane, j = r / bn[0], i = r - j * bn[0];
-    const int dk = LANES / nplane, dr = LANES - dk * nplane, dj = dr / bn[0], di = dr - dj * bn[0];
     const long long nxy = (long long)g.nx * g.ny;
     C acc[4] = {(C)0, (C)0, (C)0, (C)0}, sw = (C)0;
+    if constexpr (LANES > 1) {
+        // a warp: the rows (j, k) that reach the sphere, two per round (a
+        // half-warp each), 16 lanes along x, so a lane's x and dx^2 stay fixed
+        // over a sweep and only cells inside the sphere are read
+        const int half = (int)((threadIdx.x & 31) >> 4), xl = (int)(threadIdx.x & 15);
+        const C cy = (uh[1] - (C)0.5) + (C)ul[1];
+        for (int k = 0; k < bn[2]; ++k) {
+            const int ck = lo[2] + k;
+            const C dz = (((C)ck + (C)0.5) - uh[2]) - (C)ul[2];
+            const C dz2 = dz * dz;
+            if (dz2 > R2) continue;
+            // rows of this layer whose centre can lie within the radius left
+            const C dyr = tsqrt(R2 - dz2);
+            int j0 = (int)tfloor(cy - dyr), j1 = (int)tfloor(cy + dyr) + 1;
+            j0 = j0 < lo[1] ? lo[1] : j0;
+            j1 = j1 > lo[1] + bn[1] - 1 ? lo[1] + bn[1] - 1 : j1;
+            for (int x0 = 0; x0 < bn[0]; x0 += 16) {
+                const int ix = x0 + xl, ci = lo[0] + ix;
+                const bool xin = ix < bn[0];
+                const C dx = (((C)ci + (C)0.5) - uh[0]) - (C)ul[0];
+                const C dx2 = dx * dx;
+                for (int jb = j0; jb <= j1; jb += 2) {
+                    const int cj = jb + half;
+                    const C dy = (((C)cj + (C)0.5) - uh[1]) - (C)ul[1];
+                    const C r2 = dx2 + (dy * dy + dz2);
+                    if (xin && cj <= j1 && r2 <= R2) {
+                        const C w = Tr<C>::ex2(-r2 * l2ie2);
+                        const long long idx = ci + (long long)g.nx * cj + nxy * ck;
+                        sw += w;
+                        for (int q = 0; q < ncomp; ++q) {
+                            const S *F = f[q], *F2 = f2 ? f2[q] : nullptr;
+                            acc[q] += w * AL_FV(F, F2, idx);
+                        }
+                    }
+                }
+            }
+        }
+    } else {
+    // one thread: every cell of the box in x-fastest order
+    const int nplane = bn[0] * bn[1];
+    const long long nbox = (long long)nplane * bn[2];
+    const int lane = 0;
+    int k = lane / nplane, r = lane - k * nplane, j = r / bn[0], i = r - j * bn[0];
+    const int dk = LANES / nplane, dr = LANES - dk * nplane, dj = dr / bn[0], di = dr - dj * bn[0];
     for (long long t = lane; t < nbox; t += LANES) {
         const int ci = lo[0] + i, cj = lo[1] + j, ck = lo[2] + k;
         const C dx = (((C)ci + (C)0.5) - uh[0]) - (C)ul[0];
@@ -411,6 +449,7 @@ __device__ bool gauss_avg(const GridC &g, C epsc, const S *const *f, int ncomp, 
         i += di; j += dj; k += dk;
         if (i >= bn[0]) { i -= bn[0]; j += 1; }
         if (j >= bn[1]) { j -= bn[1]; k += 1; }
+    }
     }
     if (LANES > 1) {
 #pragma unroll
@@ -1064,6 +1103,75 @@ __device__ __forceinline__ void pair_w(T eta, T s, T &wa, T &wb) {
 template <typename T>
 __device__ __forceinline__ T pair_src(T wa, T wb, T fa, T fb) { return r_fma(wa, fa, r_mul(wb, fb)); }
 
+// Per-CTA staging of the records of a round of segments (one per warp): each
+// record takes a shared-memory slot, and at the end of the round the CTA
+// reserves the slots of each brick (instance, brick key) with one global
+// atomic and writes the records there.  Records beyond CAP, or of a brick
+// that finds the table full, reserve their own slot directly.
+template <typename T> struct RecStage {
+    static constexpr int CAP = 768, NB = 64;
+    Rec<T> rec[CAP];
+    unsigned long long rk[CAP];     // (instance << 32) | brick of each staged record
+    int loc[CAP];                   // (table entry << 16) | rank within the entry; -1: written directly
+    unsigned long long key[NB];     // table of the round's (instance, brick) keys; ~0: empty
+    int cnt[NB], base[NB];
+    int n;
+};
+template <typename T>
+__device__ __forceinline__ void rec_init(RecStage<T> &st) {
+    for (int h = threadIdx.x; h < RecStage<T>::NB; h += blockDim.x) { st.key[h] = ~0ull; st.cnt[h] = 0; }
+    if (threadIdx.x == 0) st.n = 0;
+    __syncthreads();
+}
+// the whole CTA calls this after its round; sc_of(q) gives instance q's scratch
+template <typename T, typename ScOf>
+__device__ void rec_flush(RecStage<T> &st, ScOf sc_of) {
+    constexpr int CAP = RecStage<T>::CAP, NB = RecStage<T>::NB;
+    __syncthreads();
+    const int n = min(st.n, CAP);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long key = st.rk[i];
+        int h = (int)((key * 0x9E3779B97F4A7C15ull) >> 58);
+        int slot = -1;
+        for (int t = 0; t < NB; ++t, h = (h + 1) & (NB - 1)) {
+            const unsigned long long old = atomicCAS(&st.key[h], ~0ull, key);
+            if (old == ~0ull || old == key) { slot = h; break; }
+        }
+        if (slot >= 0) {
+            st.loc[i] = (slot << 16) | atomicAdd(&st.cnt[slot], 1);
+        } else {
+            const Scratch<T> &s = sc_of((int)(key >> 32));
+            const int br = (int)(key & 0xffffffffull);
+            const int pos = atomicAdd(&s.rcnt[br], 1);
+            if (pos < s.rcap[br]) s.rec[s.roff[br] + pos] = st.rec[i];
+            st.loc[i] = -1;
+        }
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < NB; h += blockDim.x) {
+        const unsigned long long key = st.key[h];
+        if (key != ~0ull) {
+            const Scratch<T> &s = sc_of((int)(key >> 32));
+            st.base[h] = atomicAdd(&s.rcnt[(int)(key & 0xffffffffull)], st.cnt[h]);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int lc = st.loc[i];
+        if (lc < 0) continue;
+        const int h = lc >> 16;
+        const unsigned long long key = st.key[h];
+        const Scratch<T> &s = sc_of((int)(key >> 32));
+        const int br = (int)(key & 0xffffffffull);
+        const int pos = st.base[h] + (lc & 0xffff);
+        if (pos < s.rcap[br]) s.rec[s.roff[br] + pos] = st.rec[i];
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < NB; h += blockDim.x) { st.key[h] = ~0ull; st.cnt[h] = 0; }
+    if (threadIdx.x == 0) st.n = 0;
+    __syncthreads();
+}
+
 // What a visited cell feeds: the segment's two weight sums (SC = false), or
 // in the scatter form of the projection the cell's momentum source, added
 // to S with atomics (SC = true; the sums of what was added feed the totals).
@@ -1076,11 +1184,25 @@ template <typename T> struct WSink<T, false> {
     const int *rcap;
     const long long *roff;
     int ka, nbx, nby, bzs;
+    RecStage<T> *st = nullptr;   // the CTA's staging (null: each record reserves its slot)
+    int q = 0;                   // instance index (key of the staging)
     __device__ __forceinline__ void add(const GridC &, const StepPtrs<T> &, const int cg[3], T eta, T s) {
         T a, b;
         pair_w(eta, s, a, b);
         wa.add(a);
         wb.add(b);
+        if (rec && st) {
+            const int br = (cg[0] >> 4) + nbx * ((cg[1] >> 4) + nby * (cg[2] >> bzs));
+            const int slot = atomicAdd(&st->n, 1);
+            if (slot < RecStage<T>::CAP) {
+                Rec<T> r;
+                r.cell = ((cg[2] & ((1 << bzs) - 1)) << 8) | ((cg[1] & 15) << 4) | (cg[0] & 15);
+                r.ka = ka; r.wa = a; r.wb = b;
+                st->rec[slot] = r;
+                st->rk[slot] = ((unsigned long long)(unsigned)q << 32) | (unsigned)br;
+                return;
+            }
+        }
         if (rec) {
             // the lanes adding to one brick take consecutive slots with one atomic
             const int br = (cg[0] >> 4) + nbx * ((cg[1] >> 4) + nby * (cg[2] >> bzs));
@@ -1313,7 +1435,7 @@ __device__ __forceinline__ void w_finish(const GridC &, const Scratch<T> &sc, in
 
 template <typename T, bool SC>
 __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
-                          const int k, const int lane) {
+                          const int k, const int lane, RecStage<T> *st = nullptr, int q = 0) {
     if (!SC && g.wmode == 0) return;                        // all weights from the brick pass
     const long long np = b.n_points;
     const int l = b.line_of[k];
@@ -1356,6 +1478,8 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
         sink.ka = k | (c.n == 1 ? REC_SINGLE : 0);
         sink.nbx = g.nbx; sink.nby = g.nby;
         sink.bzs = g.bz == 4 ? 2 : (g.bz == 8 ? 3 : 4);
+        sink.st = st;
+        sink.q = q;
     }
     const bool regular = lg.regular != 0;
     c.has_lo = regular && c.q >= 1;
@@ -1457,6 +1581,7 @@ struct SpreadSmem {
     float e_cz[ENT];             // min |D_z| / |D| over the candidates (0: no crossing test)
     float e_rad[ENT];            // R + curvature slack, cells
     float e_rho2[ENT];           // regular == 2: squared start radius
+    int e_canon[ENT];            // the line's weights come from the segment pass: its pairs take its values
     // per line and layer: where the line crosses the layer's height, the
     // horizontal radius beyond which no cell of the layer is within 3 eps,
     // the crossing segment, and the fractional segment index at the crossing
@@ -1845,6 +1970,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                     sm.e_ie2[e] = lgc<T>(lg.inv_eps2c_l2, lg.ie2f);
                     sm.e_eta0[e] = WP ? (T)lg.wshift : lgc<T>(lg.eta0, lg.eta0f);
                     sm.e_rho2[e] = lg.rho2;
+                    sm.e_canon[e] = (g.wmode != 0 && lg.regular != 0) ? 1 : 0;
                     for (int a = 0; a < 3; ++a) { sm.e_lo[e][a] = lo[a] - blo[a]; sm.e_hi[e][a] = hi[a] - blo[a]; }
                     sm.e_cz[e] = cz_ok;
                     if (cz_ok > 0.0f) {
@@ -2077,12 +2203,20 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                                     fa0 = sc.fhat[ka]; fa1 = sc.fhat[np + ka]; fa2 = sc.fhat[2 * np + ka];
                                     fb0 = sc.fhat[kb]; fb1 = sc.fhat[np + kb]; fb2 = sc.fhat[2 * np + kb];
                                 }
-                                // the pair's values as the segment pass computes them
-                                const int cgl[3] = {B0 + tx, B1 + ty, gz};
-                                T s2, r22;
-                                pair_sr(sc, np, first + js, (n == 1) ? first + js : first + js + 1, cgl, s2, r22);
+                                // the pair's values as the pass that summed the line's
+                                // weights computed them (a node whose weight is small
+                                // keeps its load only if the two agree): the segment
+                                // pass's for certified lines under segment weights,
+                                // this pass's own otherwise
                                 T wa, wb;
-                                pair_w(e0v * Tr<T>::ex2(-r22 * ie2), s2, wa, wb);
+                                if (sm.e_canon[e]) {
+                                    const int cgl[3] = {B0 + tx, B1 + ty, gz};
+                                    T s2, r22;
+                                    pair_sr(sc, np, first + js, (n == 1) ? first + js : first + js + 1, cgl, s2, r22);
+                                    pair_w(e0v * Tr<T>::ex2(-r22 * ie2), s2, wa, wb);
+                                } else {
+                                    pair_w(e0v * q, s, wa, wb);
+                                }
                                 const int c = ty * BX + tx;
                                 sm.u.s.acc[z][0][c] -= to_fixed_s(pair_src(wa, wb, fa0, fb0), fsh);
                                 sm.u.s.acc[z][1][c] -= to_fixed_s(pair_src(wa, wb, fa1, fb1), fsh);
@@ -2249,28 +2383,32 @@ __device__ void d_totals(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
         // the brick height of the next step)
         __syncthreads();
         long long *scan = reinterpret_cast<long long *>(&red[0][0]);
-        long long run = 0;
-        for (long long b0 = 0; b0 < g.nbrick_max; b0 += 256) {
-            const long long bi = b0 + threadIdx.x;
-            const int c = bi < g.nbrick_max ? sc.rcnt[bi] : 0;
+        // each thread a contiguous run of bricks: its total, one block scan, then
+        // the run's offsets in order
+        const long long per = (g.nbrick_max + 255) / 256;
+        const long long b0 = threadIdx.x * per, b1 = min(b0 + per, g.nbrick_max);
+        long long mine = 0;
+        for (long long bi = b0; bi < b1; ++bi) {
+            const int c = sc.rcnt[bi];
+            mine += c > 0 ? (long long)c + (c >> 3) + 16 : 0;
+        }
+        scan[threadIdx.x] = mine;
+        __syncthreads();
+        for (int o = 1; o < 256; o <<= 1) {              // inclusive scan
+            const long long v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
+            __syncthreads();
+            scan[threadIdx.x] += v;
+            __syncthreads();
+        }
+        long long off = scan[threadIdx.x] - mine;
+        for (long long bi = b0; bi < b1; ++bi) {
+            const int c = sc.rcnt[bi];
             const long long want = c > 0 ? (long long)c + (c >> 3) + 16 : 0;
-            scan[threadIdx.x] = want;
-            __syncthreads();
-            for (int o = 1; o < 256; o <<= 1) {          // inclusive scan
-                const long long v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
-                __syncthreads();
-                scan[threadIdx.x] += v;
-                __syncthreads();
-            }
-            if (bi < g.nbrick_max) {
-                const long long off = run + scan[threadIdx.x] - want;
-                const long long cap = off >= g.rec_total ? 0 : (off + want > g.rec_total ? g.rec_total - off : want);
-                sc.roff[bi] = off < g.rec_total ? off : 0;
-                sc.rcap[bi] = (int)cap;
-                sc.rcnt[bi] = 0;
-            }
-            run += scan[255];
-            __syncthreads();
+            const long long cap = off >= g.rec_total ? 0 : (off + want > g.rec_total ? g.rec_total - off : want);
+            sc.roff[bi] = off < g.rec_total ? off : 0;
+            sc.rcap[bi] = (int)cap;
+            sc.rcnt[bi] = 0;
+            off += want;
         }
     }
 }
@@ -2331,8 +2469,12 @@ __global__ void __launch_bounds__(256) k_mask(GridC g, BeamsC b, Scratch<T> sc) 
 }
 template <typename T>
 __global__ void __launch_bounds__(128) k_weights(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
+    __shared__ RecStage<T> st;
+    const bool stage = g.rmode != 0;
+    if (stage) rec_init(st);
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (k < b.n_points) d_weights<T, false>(g, b, sc, p, status, k, threadIdx.x & 31);
+    if (k < b.n_points) d_weights<T, false>(g, b, sc, p, status, k, threadIdx.x & 31, stage ? &st : nullptr, 0);
+    if (stage) rec_flush(st, [&](int) -> const Scratch<T> & { return sc; });
 }
 // scatter form of the projection: one warp per segment of a certified line
 template <typename T>
@@ -2425,12 +2567,21 @@ __global__ void __launch_bounds__(256) kb_mask(const Inst<T> *I, const int *sel,
 }
 template <typename T>
 __global__ void __launch_bounds__(128) kb_weights(const Inst<T> *I, const int *sel, const long long *pre, int n) {
+    __shared__ RecStage<T> st;
+    rec_init(st);
     const long long total = pre[n];
-    const long long nw = (long long)gridDim.x * blockDim.x / 32;
-    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
-        const int q = owner(pre, n, w);
-        const Inst<T> &x = I[AL_SEL(q)];
-        d_weights<T, false>(x.g, x.b, x.sc, x.p, x.status, (int)(w - pre[q]), threadIdx.x & 31);
+    const int nwb = blockDim.x / 32;
+    // rounds of one segment per warp, the whole CTA together (the staged
+    // records are flushed after each round)
+    for (long long w0 = (long long)blockIdx.x * nwb; w0 < total; w0 += (long long)gridDim.x * nwb) {
+        const long long w = w0 + (threadIdx.x >> 5);
+        if (w < total) {
+            const int q = owner(pre, n, w);
+            const Inst<T> &x = I[AL_SEL(q)];
+            d_weights<T, false>(x.g, x.b, x.sc, x.p, x.status, (int)(w - pre[q]), threadIdx.x & 31,
+                                x.g.rmode ? &st : nullptr, q);
+        }
+        rec_flush(st, [&](int q) -> const Scratch<T> & { return I[AL_SEL(q)].sc; });
     }
 }
 template <typename T>
