@@ -14,9 +14,12 @@ Prints ONE JSON line (rank 0).  Throughput `value` is coupling steps/s over
 all ranks, device-timed with CUDA events; L2 is flushed (256 MiB write)
 between timed steps, outside the events.  `e2e` is the same metric through
 the public API with pinned host buffers, host<->device copies inside the
-timed region.  `roofline` reports the projection kernel (k_spread): its
-algorithmic bytes (the dense S write plus the staged per-node data) over
-its event-timed duration, against the measured HBM copy bandwidth.
+timed region.  `roofline` reports the longer of the two passes over the
+(cell, line) pairs: the projection (k_spread: its algorithmic bytes, the
+dense S write plus the per-node data, over its event-timed duration,
+against the measured HBM copy bandwidth) or the weights pass (k_weights:
+its algorithmic FP32 operations per pair times the pairs, against the FP32
+FMA peak of the SMs at their maximum clock).
 """
 import argparse
 import hashlib
@@ -146,6 +149,15 @@ class Clocks:
                 pass
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# FP32 ALU peak: 148 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.032 GHz
+ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# operations of one (cell, segment) pair of the weights pass by definition:
+# offset to the segment start (3), foot parameter x.D / |D|^2 (6), foot
+# offset and squared distance (6 + 5), Gaussian exp(-(r/eps)^2) eta0 (3),
+# the two node weights (1 - s) eta, s eta (3)
+FLOP_PER_PAIR = 26
 
 
 def _algorithmic_bytes(wl):
@@ -345,6 +357,19 @@ def run_ours(a):
     alg = _algorithmic_bytes(wl)
     achieved = alg / spread_s / 1e9
     traffic = _traffic(wl.name)
+    weights_s = ph[PHASES.index("weights")] / 1e3
+    if weights_s > spread_s and tuned["weights"] == "segment":
+        flop = supp * FLOP_PER_PAIR
+        a_t = flop / weights_s / 1e12
+        roofline = {"bound": "alu", "kernel": "k_weights", "achieved": a_t, "peak": ALU_PEAK_TFLOPS,
+                    "peak_kind": "derived (148 SMs x 128 FP32 lanes x FMA x 2.032 GHz)", "unit": "TFLOP/s",
+                    "frac": a_t / ALU_PEAK_TFLOPS, "algorithmic_flop": flop, "traffic": None,
+                    "k_spread": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                 "frac": achieved / peak, "algorithmic_bytes": alg}}
+    else:
+        roofline = {"bound": "hbm", "kernel": "k_spread", "achieved": achieved, "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                    "algorithmic_bytes": alg, "traffic": traffic}
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         v, cores, sample = _cpu_baseline(wl)
@@ -361,9 +386,7 @@ def run_ours(a):
                 "kernel_cell_updates_per_s": supp * value,
                 "support_pairs_per_step": supp,
                 "phases_ms": {k: float(v) for k, v in zip(PHASES, ph)},
-                "roofline": {"bound": "hbm", "kernel": "k_spread", "achieved": achieved, "peak": peak,
-                             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                             "algorithmic_bytes": alg, "traffic": traffic},
+                "roofline": roofline,
                 "projection_variants": variants,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": (KERNELS_PER_STEP + (tuned["weights"] == "segment")) * a.steps}
