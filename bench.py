@@ -260,8 +260,9 @@ def run_ours(a):
         inst.grid.set_option(OPT_WEIGHTS, 1 if tuned["weights"] == "segment" else 0)
         inst.grid.set_option(OPT_BRICK_Z, tuned["brick_z"])
     elif not a.no_tune:
-        wmode, bz = inst.autotune(trials=2)
-        tuned = {"weights": "segment" if wmode else "brick", "brick_z": bz, "autotuned": True}
+        wmode, bz, rec = inst.autotune(trials=2)
+        tuned = {"weights": "segment" if wmode else "brick", "brick_z": bz, "records": bool(rec),
+                 "autotuned": True}
     inst.grid.trace(True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
@@ -413,7 +414,7 @@ def run_batched(a):
     insts = [Instance(w, device=f"cuda:{local}") for w in wls]
     # tile sizes and weight pass: each instance tuned alone (used by the
     # per-instance launches), then the batch's brick height and persistent grid
-    choices = [i.autotune(trials=1) for i in insts] if not a.no_tune else [(0, 8)] * len(insts)
+    choices = [i.autotune(trials=1)[:2] for i in insts] if not a.no_tune else [(0, 8)] * len(insts)
     batch = Batch(insts, use_graph=True)
     batch_choice = batch.autotune(trials=1) if not a.no_tune else (8, 0)
     stream = torch.cuda.current_stream()

@@ -232,11 +232,12 @@ int al_trace_last(al_grid g, float *ms /* [AL_TRACE_N] */);
 int al_set_option(al_grid g, int option, int value);
 
 /* Autotuner: runs the caller's step (same in/out as al_sample_drag_spread)
- * under every combination of AL_OPT_WEIGHTS and AL_OPT_BRICK_Z, `trials`
+ * under every combination of AL_OPT_WEIGHTS (with AL_WEIGHTS_SEGMENT: with
+ * and without AL_OPT_RECORD) and AL_OPT_BRICK_Z, `trials`
  * timed steps each after one warm-up, timed with CUDA events on `stream`, and
  * keeps the fastest.  The relaxation state and the status counters are
  * restored afterwards; S, F and totals hold the last trial's outputs.
- * *choice (optional) = 100 * weights mode + brick height.  Synchronises the
+ * *choice (optional) = 1000 * records + 100 * weights mode + brick height.  Synchronises the
  * stream; allocates a temporary copy of the relaxation state. */
 int al_autotune(al_grid g, const al_step_in *in, const al_step_out *out, int trials, void *stream, int *choice);
 

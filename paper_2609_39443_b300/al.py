@@ -288,12 +288,12 @@ class Instance:
             self.P_spread.copy_(torch.as_tensor(np.ascontiguousarray(P_spread), dtype=self.dtype))
 
     def autotune(self, trials: int = 3, stream=None):
-        """al_autotune on this instance's step; returns (weights mode, brick height)."""
+        """al_autotune on this instance's step; returns (weights mode, brick height, records)."""
         sin, sout = self.descriptors()
         ch = C.c_int(0)
         check(lib().al_autotune(self.grid.h, C.byref(sin), C.byref(sout), int(trials), _stream_ptr(stream),
                                 C.byref(ch)), "al_autotune")
-        return ch.value // 100, ch.value % 100
+        return (ch.value // 100) % 10, ch.value % 100, ch.value // 1000
 
     def descriptors(self):
         return step_descriptors(self.U, self.P, self.Pdot, self.S, self.F, alpha=self.alpha,

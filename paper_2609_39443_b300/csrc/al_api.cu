@@ -720,10 +720,10 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
         return (unsigned)std::max<long long>(1, std::min<long long>(g, (long long)b->pt_grid * 4));
     };
     if (tot_pts > 0) {
-        if (b->any_gauss)
-            kb_points_w<T><<<grid_for(tot_pts, 8), 256, 0, st>>>(I, sel, pp, n);
-        else
-            kb_points<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
+        // each instance in the same form as alone: a warp per point for the
+        // volume-average sampler, a thread per point otherwise
+        kb_points<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n, b->any_gauss ? 1 : 0);
+        if (b->any_gauss) kb_points_w<T><<<grid_for(tot_pts, 8), 256, 0, st>>>(I, sel, pp, n);
         kb_segments<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
     }
     if (tot_lines > 0) kb_lines<T><<<grid_for(tot_lines, 8), 256, 0, st>>>(I, sel, pl, n);
@@ -954,12 +954,16 @@ extern "C" int al_autotune(al_grid g, const al_step_in *in, const al_step_out *o
     event_pair ev;
     if (rc == AL_OK && (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess))
         rc = AL_ERR_CUDA;
-    const int wms[2] = {AL_WEIGHTS_BRICK, AL_WEIGHTS_SEGMENT}, bzs[3] = {4, 8, 16};
+    // weights pass and records: brick; segment without records; segment with
+    // records (the warm-up step sizes the record regions the timed steps use)
+    const int wms[3] = {AL_WEIGHTS_BRICK, AL_WEIGHTS_SEGMENT, AL_WEIGHTS_SEGMENT}, recs[3] = {0, 0, 1};
+    const int bzs[3] = {4, 8, 16};
     float best = INFINITY;
-    int best_w = g->gc.wmode, best_z = g->gc.bz;
-    for (int wi = 0; wi < 2 && rc == AL_OK; ++wi)
+    int best_w = g->gc.wmode, best_z = g->gc.bz, best_r = g->opt_record;
+    for (int wi = 0; wi < 3 && rc == AL_OK; ++wi)
         for (int zi = 0; zi < 3 && rc == AL_OK; ++zi) {
             g->gc.wmode = wms[wi];
+            g->opt_record = recs[wi];
             set_brick_z(g->gc, bzs[zi]);
             if ((rc = restore_state(g, out, sv, st)) != AL_OK) break;
             if ((rc = al_sample_drag_spread(g, in, out, stream)) != AL_OK) break;       // warm-up
@@ -972,14 +976,15 @@ extern "C" int al_autotune(al_grid g, const al_step_in *in, const al_step_out *o
             }
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, ev.a, ev.b);
-            if (ms < best) { best = ms; best_w = wms[wi]; best_z = bzs[zi]; }
+            if (ms < best) { best = ms; best_w = wms[wi]; best_z = bzs[zi]; best_r = recs[wi]; }
         }
     g->gc.wmode = best_w;
+    g->opt_record = best_r;
     set_brick_z(g->gc, best_z);
     const int rc2 = restore_state(g, out, sv, st);
     if (sv.fprev) cudaFree(sv.fprev);
     if (rc == AL_OK) rc = rc2;
-    if (rc == AL_OK && choice) *choice = 100 * best_w + best_z;
+    if (rc == AL_OK && choice) *choice = 1000 * best_r + 100 * best_w + best_z;
     return rc;
 }
 

@@ -1193,7 +1193,13 @@ template <typename T> struct WSink<T, false> {
         wb.add(b);
         if (rec && st) {
             const int br = (cg[0] >> 4) + nbx * ((cg[1] >> 4) + nby * (cg[2] >> bzs));
-            const int slot = atomicAdd(&st->n, 1);
+            // one shared-memory atomic for the lanes adding together
+            const unsigned act = __activemask();
+            const int lane = threadIdx.x & 31, lead = __ffs(act) - 1;
+            int sbase = 0;
+            if (lane == lead) sbase = atomicAdd(&st->n, __popc(act));
+            sbase = __shfl_sync(act, sbase, lead);
+            const int slot = sbase + __popc(act & ((1u << lane) - 1u));
             if (slot < RecStage<T>::CAP) {
                 Rec<T> r;
                 r.cell = ((cg[2] & ((1 << bzs) - 1)) << 8) | ((cg[1] & 15) << 4) | (cg[0] & 15);
@@ -2441,16 +2447,24 @@ __device__ __forceinline__ int owner(const long long *pre, int n, long long gid)
     return lo;
 }
 
+// One compiled body per form (a thread or a warp per point), called by the
+// single-instance and the batched kernels alike, so an instance's forces
+// have the same bits alone and in a batch.
+template <typename T, int LANES>
+__device__ __noinline__ void d_points_nl(const GridC &g, const BeamsC &b, const StepPtrs<T> &p,
+                                         const Scratch<T> &sc, int *status, int i) {
+    d_points<T, LANES>(g, b, p, sc, status, i);
+}
 template <typename T>
 __global__ void __launch_bounds__(256) k_points(GridC g, BeamsC b, StepPtrs<T> p, Scratch<T> sc, int *status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < b.n_points) d_points(g, b, p, sc, status, i);
+    if (i < b.n_points) d_points_nl<T, 1>(g, b, p, sc, status, i);
 }
 // one warp per point (volume-average sampler)
 template <typename T>
 __global__ void __launch_bounds__(256) k_points_w(GridC g, BeamsC b, StepPtrs<T> p, Scratch<T> sc, int *status) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i < b.n_points) d_points<T, 32>(g, b, p, sc, status, i);
+    if (i < b.n_points) d_points_nl<T, 32>(g, b, p, sc, status, i);
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_segments(BeamsC b, Scratch<T> sc) {
@@ -2514,17 +2528,20 @@ __global__ void __launch_bounds__(256) k_totals(GridC g, BeamsC b, Scratch<T> sc
 // selected instances; sel: instance index of each selected slot (NULL: slot q
 // is instance q)
 #define AL_SEL(q) (sel ? sel[q] : (q))
+// skip_gauss: the volume-average instances are left to kb_points_w
 template <typename T>
-__global__ void __launch_bounds__(256) kb_points(const Inst<T> *I, const int *sel, const long long *pre, int n) {
+__global__ void __launch_bounds__(256) kb_points(const Inst<T> *I, const int *sel, const long long *pre, int n,
+                                                 int skip_gauss) {
     const long long total = pre[n];
     for (long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x; gid < total;
          gid += (long long)gridDim.x * blockDim.x) {
         const int q = owner(pre, n, gid);
         const Inst<T> &x = I[AL_SEL(q)];
-        d_points(x.g, x.b, x.p, x.sc, x.status, (int)(gid - pre[q]));
+        if (skip_gauss && x.b.sample_mode == 2) continue;
+        d_points_nl<T, 1>(x.g, x.b, x.p, x.sc, x.status, (int)(gid - pre[q]));
     }
 }
-// one warp per point, for batches holding an instance with the volume-average sampler
+// one warp per point, for the batch's instances with the volume-average sampler
 template <typename T>
 __global__ void __launch_bounds__(256) kb_points_w(const Inst<T> *I, const int *sel, const long long *pre, int n) {
     const long long total = pre[n];
@@ -2532,7 +2549,8 @@ __global__ void __launch_bounds__(256) kb_points_w(const Inst<T> *I, const int *
     for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
         const int q = owner(pre, n, w);
         const Inst<T> &x = I[AL_SEL(q)];
-        d_points<T, 32>(x.g, x.b, x.p, x.sc, x.status, (int)(w - pre[q]));
+        if (x.b.sample_mode != 2) continue;                 // kb_points takes the others
+        d_points_nl<T, 32>(x.g, x.b, x.p, x.sc, x.status, (int)(w - pre[q]));
     }
 }
 template <typename T>

@@ -43,8 +43,8 @@ def test_autotune_restores_state_and_applies_choice():
     a, b = Instance(wl), Instance(wl)
     a.step()
     b.step()
-    wmode, bz = a.autotune(trials=1)
-    assert wmode in (0, 1) and bz in (4, 8, 16)
+    wmode, bz, rec = a.autotune(trials=1)
+    assert wmode in (0, 1) and bz in (4, 8, 16) and rec in (0, 1)
     b.grid.set_option(OPT_WEIGHTS, wmode)
     b.grid.set_option(OPT_BRICK_Z, bz)
     for x in (a, b):
