@@ -51,8 +51,14 @@ def test_autotune_restores_state_and_applies_choice():
         x.status.zero_()
         x.step()
     torch.cuda.synchronize()
-    for u, v in zip(_outputs(a), _outputs(b)):
+    # every output bit for bit; of the status counters all but the count of
+    # replayed bricks (the tuned instance may already replay its records)
+    from paper_2609_39443_b300.al import ST_REPLAYED
+    oa, ob = _outputs(a), _outputs(b)
+    for u, v in zip(oa[:-1], ob[:-1]):
         np.testing.assert_array_equal(u, v)
+    keep = np.arange(len(oa[-1])) != ST_REPLAYED
+    np.testing.assert_array_equal(oa[-1][keep], ob[-1][keep])
     a.close()
     b.close()
 
