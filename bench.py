@@ -62,6 +62,8 @@ def _args():
     ap.add_argument("--no-variants", action="store_true", help="skip timing the scatter projection")
     ap.add_argument("--weights", choices=["brick", "segment"], default=None, help="fix the weights pass (no tuning)")
     ap.add_argument("--brick-z", type=int, choices=[4, 8, 16], default=None, help="fix the brick height (no tuning)")
+    ap.add_argument("--records", choices=["on", "off"], default=None,
+                    help="fix whether the segment pass records pairs for the spread to replay (no tuning)")
     return ap.parse_args()
 
 
@@ -254,11 +256,13 @@ def run_ours(a):
         wl = W.with_sample_mode(wl, a.sample)
     inst = Instance(wl, device=f"cuda:{local}")
     tuned = {"weights": "brick", "brick_z": 8, "autotuned": False}
-    if a.weights or a.brick_z:
-        from paper_2609_39443_b300.al import OPT_BRICK_Z, OPT_WEIGHTS
-        tuned = {"weights": a.weights or "brick", "brick_z": a.brick_z or 8, "autotuned": False}
+    if a.weights or a.brick_z or a.records:
+        from paper_2609_39443_b300.al import OPT_BRICK_Z, OPT_RECORD, OPT_WEIGHTS
+        tuned = {"weights": a.weights or "brick", "brick_z": a.brick_z or 8, "records": a.records != "off",
+                 "autotuned": False}
         inst.grid.set_option(OPT_WEIGHTS, 1 if tuned["weights"] == "segment" else 0)
         inst.grid.set_option(OPT_BRICK_Z, tuned["brick_z"])
+        inst.grid.set_option(OPT_RECORD, 1 if tuned["records"] else 0)
     elif not a.no_tune:
         wmode, bz, rec = inst.autotune(trials=2)
         tuned = {"weights": "segment" if wmode else "brick", "brick_z": bz, "records": bool(rec),

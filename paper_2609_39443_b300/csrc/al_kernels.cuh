@@ -1841,13 +1841,34 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
             replay = true;
             __syncthreads();                             // accumulators cleared
             const Rec<T> *rr = sc.rec + sc.roff[br];
-            for (int r = threadIdx.x; r < nrec; r += SPREAD_THREADS) {
-                const Rec<T> rc = rr[r];
-                const int ka = rc.ka & ~REC_SINGLE, kb = (rc.ka & REC_SINGLE) ? ka : ka + 1;
-                const int z = rc.cell >> 8, c = rc.cell & 255;
-                for (int a = 0; a < 3; ++a) {
-                    const long long v = to_fixed_s(pair_src(rc.wa, rc.wb, sc.fhat[a * np + ka], sc.fhat[a * np + kb]), fsh);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&sm.u.s.acc[z][a][c]), (unsigned long long)(-v));
+            // four records per thread per round, their loads issued together
+            constexpr int RU = 4;
+            for (int r0 = threadIdx.x; r0 < nrec; r0 += RU * SPREAD_THREADS) {
+                Rec<T> rc[RU];
+                T fa[RU][3], fb[RU][3];
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    const int r = r0 + u * SPREAD_THREADS;
+                    if (r < nrec) rc[u] = rr[r];
+                    else { rc[u].cell = -1; rc[u].ka = 0; rc[u].wa = rc[u].wb = (T)0; }
+                }
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    const int ka = rc[u].ka & ~REC_SINGLE, kb = (rc[u].ka & REC_SINGLE) ? ka : ka + 1;
+                    const bool ok = rc[u].cell >= 0;
+                    for (int a = 0; a < 3; ++a) {
+                        fa[u][a] = ok ? sc.fhat[a * np + ka] : (T)0;
+                        fb[u][a] = ok ? sc.fhat[a * np + kb] : (T)0;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    if (rc[u].cell < 0) continue;
+                    const int z = rc[u].cell >> 8, c = rc[u].cell & 255;
+                    for (int a = 0; a < 3; ++a) {
+                        const long long v = to_fixed_s(pair_src(rc[u].wa, rc[u].wb, fa[u][a], fb[u][a]), fsh);
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&sm.u.s.acc[z][a][c]), (unsigned long long)(-v));
+                    }
                 }
             }
             if (threadIdx.x == 0 && nrec > 0) {
