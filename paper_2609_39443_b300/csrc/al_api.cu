@@ -85,6 +85,8 @@ struct al_grid_s {
     int *anyZero = nullptr;           // device flag: some node with w_k = 0
     int *rcnt = nullptr, *rcap = nullptr;   // per brick: records found / region capacity
     long long *roff = nullptr;        // per brick: region start
+    int *rplan = nullptr;             // [2] brick height of this / the next step's regions
+    unsigned long long *rused = nullptr;    // arena taken by the next step's regions
     void *rec = nullptr;              // record arena (rec_total records)
     long long rec_total = 0;
     int opt_record = 1;
@@ -178,7 +180,8 @@ extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
         (e = dalloc(&g->smax, 1)) != cudaSuccess || (e = dalloc(&g->anyZero, 1)) != cudaSuccess ||
         (e = dalloc(&g->rcnt, (size_t)g->nbrick_max)) != cudaSuccess ||
         (e = dalloc(&g->rcap, (size_t)g->nbrick_max)) != cudaSuccess ||
-        (e = dalloc(&g->roff, (size_t)g->nbrick_max)) != cudaSuccess) {
+        (e = dalloc(&g->roff, (size_t)g->nbrick_max)) != cudaSuccess ||
+        (e = dalloc(&g->rplan, 2)) != cudaSuccess || (e = dalloc(&g->rused, 1)) != cudaSuccess) {
         int rc = cuda_fail(e, "cudaMalloc");
         al_destroy(g);
         return rc;
@@ -303,6 +306,8 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
         AL_CUDA(cudaMemset(g->rcnt, 0, (size_t)g->nbrick_max * sizeof(int)));
         AL_CUDA(cudaMemset(g->rcap, 0, (size_t)g->nbrick_max * sizeof(int)));
         AL_CUDA(cudaMemset(g->roff, 0, (size_t)g->nbrick_max * sizeof(long long)));
+        AL_CUDA(cudaMemset(g->rplan, 0, 2 * sizeof(int)));
+        AL_CUDA(cudaMemset(g->rused, 0, sizeof(unsigned long long)));
     }
     g->loaded = true;
     return AL_OK;
@@ -380,6 +385,7 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     sc.lines = g->lines; sc.mask = g->mask; sc.brickSum = g->brickSum; sc.scatSum = g->scatSum;
     sc.hasPrev = g->hasPrev; sc.anyIrr = g->anyIrr; sc.smax = g->smax; sc.anyZero = g->anyZero;
     sc.rec = (Rec<T> *)g->rec; sc.rcnt = g->rcnt; sc.rcap = g->rcap; sc.roff = g->roff;
+    sc.rplan = g->rplan; sc.rused = g->rused;
     BeamsC &bc = I.b;
     bc.n_lines = g->n_lines; bc.n_points = np; bc.mask_words = g->mask_words;
     bc.line_off = g->d_line_off; bc.line_of = g->d_line_of;
@@ -521,7 +527,7 @@ extern "C" int al_destroy(al_grid g) {
     if (g->trace) al_trace_enable(g, 0);
     free_beams(g);
     void *ptrs[] = {g->brickSum, g->scatSum, g->statusInt, g->totalsInt, g->hasPrev, g->anyIrr, g->smax,
-                    g->anyZero, g->rcnt, g->rcap, g->roff};
+                    g->anyZero, g->rcnt, g->rcap, g->roff, g->rplan, g->rused};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete g;

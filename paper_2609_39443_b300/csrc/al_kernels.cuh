@@ -22,7 +22,7 @@
 //               cell's sources summed as fixed-point integers in shared
 //               memory, then every cell of S written exactly once; the
 //               zero-weight nodes (w_k = 0) deposit their load in their cell
-//   k_totals    FP64 sum F and sum S V; sizes next step's record regions
+//   k_totals    FP64 sum F and sum S V
 //
 // Geometry runs in cell units.  FP32 instances carry point positions as
 // float-float pairs (hi + lo) so that cell-relative offsets are accurate to
@@ -129,6 +129,8 @@ struct Scratch {
     int *rcnt;                   // [nbrick_max] records found this step per brick
     int *rcap;                   // [nbrick_max] capacity of the brick's region this step
     long long *roff;             // [nbrick_max] start of the brick's region
+    int *rplan;                  // [2] brick height the regions of this step / of the next step were sized for
+    unsigned long long *rused;   // [1] arena taken by the next step's regions
 };
 
 template <typename T>
@@ -682,7 +684,12 @@ __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, 
         p.F[a][i] = f * L;
     }
     sc.wfix[i] = 0ull;                                   // fixed-point weights start at zero
-    if (i == 0) { *sc.anyIrr = 0; *sc.smax = 0u; *sc.anyZero = 0; }
+    if (i == 0) {
+        *sc.anyIrr = 0; *sc.smax = 0u; *sc.anyZero = 0;
+        sc.rplan[0] = sc.rplan[1];                        // the regions the last step sized
+        sc.rplan[1] = 0;
+        *sc.rused = 0ull;
+    }
     // projection positions in cell units
     for (int a = 0; a < 3; ++a) {
         T uh;
@@ -1185,13 +1192,14 @@ template <typename T> struct WSink<T, false> {
     const long long *roff;
     int ka, nbx, nby, bzs;
     RecStage<T> *st = nullptr;   // the CTA's staging (null: each record reserves its slot)
+    bool plan_ok = false;        // regions sized for this brick height: write; otherwise only count
     int q = 0;                   // instance index (key of the staging)
     __device__ __forceinline__ void add(const GridC &, const StepPtrs<T> &, const int cg[3], T eta, T s) {
         T a, b;
         pair_w(eta, s, a, b);
         wa.add(a);
         wb.add(b);
-        if (rec && st) {
+        if (rec && st && plan_ok) {
             const int br = (cg[0] >> 4) + nbx * ((cg[1] >> 4) + nby * (cg[2] >> bzs));
             // one shared-memory atomic for the lanes adding together
             const unsigned act = __activemask();
@@ -1220,7 +1228,7 @@ template <typename T> struct WSink<T, false> {
             if (lane == lead) base = atomicAdd(&rcnt[br], __popc(grp));
             base = __shfl_sync(grp, base, lead);
             const int pos = base + __popc(grp & ((1u << lane) - 1u));
-            if (pos < rcap[br]) {
+            if (plan_ok && pos < rcap[br]) {
                 Rec<T> r;
                 r.cell = cell; r.ka = ka; r.wa = a; r.wb = b;
                 rec[roff[br] + pos] = r;
@@ -1481,6 +1489,7 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
         for (int a = 0; a < 3; ++a) { sink.fa[a] = sc.fhat[a * np + k]; sink.fb[a] = sc.fhat[a * np + c.kb]; }
     else if (g.rmode) {
         sink.rec = sc.rec; sink.rcnt = sc.rcnt; sink.rcap = sc.rcap; sink.roff = sc.roff;
+        sink.plan_ok = sc.rplan[0] == g.bz;
         sink.ka = k | (c.n == 1 ? REC_SINGLE : 0);
         sink.nbx = g.nbx; sink.nby = g.nby;
         sink.bzs = g.bz == 4 ? 2 : (g.bz == 8 ? 3 : 4);
@@ -1835,8 +1844,9 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     // the gather below then takes only the lines without a certificate.  Not
     // when a node has w_k = 0 (its deposit goes with the gathered lines).
     bool replay = false;
-    if (!WP && g.rmode && *sc.anyZero == 0) {
-        const int nrec = sc.rcnt[br];
+    const int nrec_b = (!WP && g.rmode) ? sc.rcnt[br] : 0;
+    if (!WP && g.rmode && *sc.anyZero == 0 && sc.rplan[0] == g.bz) {
+        const int nrec = nrec_b;
         if (nrec <= sc.rcap[br]) {
             replay = true;
             __syncthreads();                             // accumulators cleared
@@ -2341,6 +2351,19 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
         if (!sm.more) break;
     }
     if (WP) return;
+    if (g.rmode && threadIdx.x == 0) {
+        // this brick's region of the next step: its count plus an eighth and
+        // 16, taken from the arena by one atomic (placement does not affect
+        // results; a brick that finds the arena full gathers next step)
+        const long long want = nrec_b > 0 ? (long long)nrec_b + (nrec_b >> 3) + 16 : 0;
+        long long off = 0;
+        if (want > 0) off = (long long)atomicAdd(sc.rused, (unsigned long long)want);
+        const bool fits = want > 0 && off + want <= g.rec_total;
+        sc.rcap[br] = fits ? (int)want : 0;
+        sc.roff[br] = fits ? off : 0;
+        sc.rcnt[br] = 0;
+        if (br == 0) sc.rplan[1] = g.bz;
+    }
     // ---- write every cell of the brick once; brick sums of S -----------------
     T cs0 = (T)0, cs1 = (T)0, cs2 = (T)0;
     {
@@ -2402,41 +2425,6 @@ __device__ void d_totals(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
         for (int a = 0; a < 3; ++a) totals[a] = red[a][0];
         for (int a = 0; a < 3; ++a) totals[3 + a] = (red[3 + a][0] + (g.smode ? sc.scatSum[a] : 0.0)) * g.V;
         *sc.hasPrev = 1;                 // the next step relaxes against this one
-    }
-    if (g.rmode) {
-        // record regions of the next step: this step's count per brick plus an
-        // eighth and 16, packed in brick order and cut at the arena's end; every
-        // index up to the lowest brick height gets one (disjoint regions whatever
-        // the brick height of the next step)
-        __syncthreads();
-        long long *scan = reinterpret_cast<long long *>(&red[0][0]);
-        // each thread a contiguous run of bricks: its total, one block scan, then
-        // the run's offsets in order
-        const long long per = (g.nbrick_max + 255) / 256;
-        const long long b0 = threadIdx.x * per, b1 = min(b0 + per, g.nbrick_max);
-        long long mine = 0;
-        for (long long bi = b0; bi < b1; ++bi) {
-            const int c = sc.rcnt[bi];
-            mine += c > 0 ? (long long)c + (c >> 3) + 16 : 0;
-        }
-        scan[threadIdx.x] = mine;
-        __syncthreads();
-        for (int o = 1; o < 256; o <<= 1) {              // inclusive scan
-            const long long v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
-            __syncthreads();
-            scan[threadIdx.x] += v;
-            __syncthreads();
-        }
-        long long off = scan[threadIdx.x] - mine;
-        for (long long bi = b0; bi < b1; ++bi) {
-            const int c = sc.rcnt[bi];
-            const long long want = c > 0 ? (long long)c + (c >> 3) + 16 : 0;
-            const long long cap = off >= g.rec_total ? 0 : (off + want > g.rec_total ? g.rec_total - off : want);
-            sc.roff[bi] = off < g.rec_total ? off : 0;
-            sc.rcap[bi] = (int)cap;
-            sc.rcnt[bi] = 0;
-            off += want;
-        }
     }
 }
 
