@@ -38,7 +38,8 @@ class _Beams(C.Structure):
                 ("ell_s", C.POINTER(C.c_double)), ("alpha_f", C.POINTER(C.c_double)),
                 ("cv_len", C.POINTER(C.c_double)), ("n_p", C.c_double * 3),
                 ("g_up", C.c_double * 3), ("tau", C.c_double), ("sample_mode", C.c_int),
-                ("drag_mode", C.c_int), ("cm_n", C.POINTER(C.c_double)), ("cm_t", C.POINTER(C.c_double))]
+                ("drag_mode", C.c_int), ("proj_mode", C.c_int),
+                ("cm_n", C.POINTER(C.c_double)), ("cm_t", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -60,6 +61,7 @@ def _load():
         lib.or_count_support.argtypes = [C.POINTER(_Grid), C.POINTER(_Beams), dp, C.c_int]
         lib.or_count_support.restype = C.c_longlong
         lib.or_closest_segment.argtypes = [dp, C.c_int, dp, C.POINTER(C.c_int), dp]
+        lib.or_seg_kernel.argtypes = [dp, dp, dp, C.c_double, dp]
         lib.or_closest_segment.restype = C.c_double
         _lib = lib
     return _lib
@@ -88,7 +90,7 @@ class _BeamsHold:
         self.cm = [_f64(cm_n), _f64(cm_t)] if cm_n is not None else [None, None]
         self.s = _Beams(int(b.n_lines), _ptr(self.off, C.c_int), *[_ptr(a) for a in self.arr],
                         (C.c_double * 3)(*map(float, b.n_p)), (C.c_double * 3)(*map(float, b.g_up)),
-                        float(b.tau), int(b.sample_mode), int(b.drag_mode),
+                        float(b.tau), int(b.sample_mode), int(b.drag_mode), int(getattr(b, "proj_mode", 0)),
                         _ptr(self.cm[0]), _ptr(self.cm[1]))
 
 
@@ -102,6 +104,15 @@ def sample(grid, field, mode, p, eps=0.0):
     pp = _f64(np.asarray(p))
     ok = _load().or_sample_field(C.byref(g), _ptr(f), ncomp, int(mode), float(eps), _ptr(pp), _ptr(out))
     return bool(ok), out
+
+
+def seg_kernel(c, A, B, eps):
+    """(K0, K1): integral of the 3-D Gaussian along segment A -> B seen from c,
+    and its first moment in t / L (the segment-integrated projection)."""
+    K = np.zeros(2)
+    c, A, B = (_f64(np.asarray(v)) for v in (c, A, B))
+    _load().or_seg_kernel(_ptr(c), _ptr(A), _ptr(B), float(eps), _ptr(K))
+    return K
 
 
 def point_step(grid, beams, step, f_prev=None):

@@ -57,6 +57,7 @@ typedef struct {
     double n_p[3], g_up[3], tau;
     int sample_mode;                  /* 0 trilinear, 1 containing cell, 2 Gaussian volume average */
     int drag_mode;                    /* 0 Eq. almLineForce, 1 Eq. fext_drag */
+    int proj_mode;                    /* 0 nearest segment (Eq. almProjectionPoint), 1 segment-integrated */
     const double *cm_n, *cm_t;        /* per line, added-mass coefficients of Eq. fext_addedmass;
                                          NULL: no inertia term (the paper's model) */
 } or_beams;
@@ -403,6 +404,35 @@ double or_closest_segment(const double *X, int n, const double *c, int *kbest, d
     return r2;
 }
 
+/* Segment-integrated 3-D Gaussian (the projection variant of Sec. 6): for
+ * the segment A -> B of length L and the point c,
+ *   K0 = int_0^L G3(c - P(t)) dt,   K1 = int_0^L (t / L) G3(c - P(t)) dt,
+ * P(t) = A + t (B - A) / L, G3(x) = exp(-|x|^2 / eps^2) / (pi^(3/2) eps^3),
+ * the 3-D Gaussian whose integral along an infinite line is the 2-D kernel
+ * of Eq. almGaussian.  With t0 the tangential coordinate of c and r_p its
+ * distance from the segment's axis, G3 factors into exp(-r_p^2/eps^2) and a
+ * 1-D Gaussian in t - t0, whose integral and first moment over [0, L] are
+ * erf and exp terms:
+ *   K0 = g E,  E = (erf((L - t0)/eps) + erf(t0/eps)) / 2,
+ *   K1 = (g / L) (t0 E + eps / (2 sqrt(pi)) (exp(-t0^2/eps^2) - exp(-(L-t0)^2/eps^2))),
+ *   g = exp(-r_p^2 / eps^2) / (pi eps^2).
+ * A zero-length segment gives K0 = K1 = 0. */
+void or_seg_kernel(const double *c, const double *A, const double *B, double eps, double *K)
+{
+    double D[3], x[3];
+    for (int a = 0; a < 3; ++a) { D[a] = B[a] - A[a]; x[a] = c[a] - A[a]; }
+    const double L = sqrt(dot3(D, D));
+    if (!(L > 0.0)) { K[0] = K[1] = 0.0; return; }
+    const double t0 = dot3(x, D) / L;
+    double p[3];
+    for (int a = 0; a < 3; ++a) p[a] = x[a] - t0 * D[a] / L;
+    const double g = exp(-dot3(p, p) / (eps * eps)) / (OR_PI * eps * eps);
+    const double E = 0.5 * (erf((L - t0) / eps) + erf(t0 / eps));
+    K[0] = g * E;
+    K[1] = g / L * (t0 * E + eps / (2.0 * sqrt(OR_PI)) *
+                                 (exp(-t0 * t0 / (eps * eps)) - exp(-(L - t0) * (L - t0) / (eps * eps))));
+}
+
 static void or_project_line(const or_grid *g, const or_beams *b, const double *Ps, long long np,
                             const double *F, int l, int cull, or_line_out *o)
 {
@@ -443,6 +473,21 @@ static void or_project_line(const or_grid *g, const or_beams *b, const double *P
             for (int ix = lo[0]; ix <= hi[0]; ++ix) {
                 double c[3] = {g->o[0] + (ix + 0.5) * g->h, g->o[1] + (jy + 0.5) * g->h,
                                g->o[2] + (kz + 0.5) * g->h};
+                if (b->proj_mode == 1 && n >= 2) {
+                    /* every segment whose closest point lies within 3 eps
+                     * contributes its integrated kernel; the record keeps
+                     * eta = K0 and s = K1 / K0, so (1 - s) eta and s eta are
+                     * the two nodes' shares */
+                    for (int k = 0; k + 1 < n; ++k) {
+                        double sk;
+                        if (or_seg_dist2(c, X[k], X[k + 1], &sk) > R * R) continue;
+                        double K[2];
+                        or_seg_kernel(c, X[k], X[k + 1], eps, K);
+                        if (K[0] > 0.0)
+                            or_push(o, ix + (long long)g->nx * jy + nxy * kz, k, K[1] / K[0], K[0]);
+                    }
+                    continue;
+                }
                 double sbest;
                 int kbest;
                 double r = sqrt(or_closest(X, n, c, &kbest, &sbest));

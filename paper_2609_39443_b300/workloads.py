@@ -72,6 +72,7 @@ class BeamSpec:
     g_up: tuple = (-1.0, 0.0, 0.0)   # global upstream fallback direction
     tau: float = 1e-6                # fallback threshold on |u0_n| (m/s)
     sample_mode: int = SAMPLE_TRILINEAR
+    proj_mode: int = 0          # 0 nearest segment (the paper's), 1 segment-integrated 3-D Gaussian
     drag_mode: int = DRAG_DISCRETE
     tangents_given: bool = False
     cm_n: Optional[np.ndarray] = None   # float64 [n_lines] added-mass coefficients (None: no inertia term)
@@ -458,6 +459,13 @@ def with_sample_mode(wl: Workload, mode: str) -> Workload:
     m = {"trilinear": SAMPLE_TRILINEAR, "cell": SAMPLE_CELL, "gauss": SAMPLE_GAUSS}[mode]
     return replace(wl, name=f"{wl.name}_{mode}" if m != wl.beams.sample_mode else wl.name,
                    beams=replace(wl.beams, sample_mode=m))
+
+
+def with_projection(wl: Workload, mode: str) -> Workload:
+    """The same workload with another projection ("nearest" or "integrated")."""
+    m = {"nearest": 0, "integrated": 1}[mode]
+    return replace(wl, name=f"{wl.name}_{mode}" if m != wl.beams.proj_mode else wl.name,
+                   beams=replace(wl.beams, proj_mode=m))
 
 
 def advance(wl: Workload, seed: int, dt: float = 1e-3) -> Workload:

@@ -589,3 +589,129 @@ def test_plain_config_totals():
     # near-uniform flow of 0.5 m/s normal to a near-vertical 0.2 m cylinder: ~0.3 N
     assert r["totals"][0] == pytest.approx(0.3, rel=0.1)
     assert (r["status"][:2] == 0).all()
+
+
+# ----------------------------------------------------------------------------
+# segment-integrated projection (the variant Sec. 6 proposes)
+# ----------------------------------------------------------------------------
+
+def _g3_moments(c, A, B, eps):
+    """Quadrature of the 3-D Gaussian along A -> B: (int G3, int (t/L) G3)."""
+    from scipy.integrate import quad
+    D = B - A
+    L = np.linalg.norm(D)
+
+    def g3(t):
+        x = c - (A + t * D / L)
+        return np.exp(-(x @ x) / eps ** 2) / (np.pi ** 1.5 * eps ** 3)
+    k0 = quad(g3, 0.0, L, epsabs=0, epsrel=1e-13, limit=200)[0]
+    k1 = quad(lambda t: t / L * g3(t), 0.0, L, epsabs=0, epsrel=1e-13, limit=200)[0]
+    return np.array([k0, k1])
+
+
+def test_segment_kernel_matches_quadrature():
+    rng = np.random.default_rng(21)
+    for _ in range(40):
+        eps = rng.uniform(0.5, 2.0)
+        A, B = rng.normal(size=3), rng.normal(size=3) * 2.0
+        c = (A + B) / 2 + rng.normal(size=3) * eps
+        np.testing.assert_allclose(oracle.seg_kernel(c, A, B, eps), _g3_moments(c, A, B, eps), rtol=1e-9, atol=1e-300)
+
+
+def test_segment_kernel_splits_exactly_at_a_node():
+    """A segment cut in two at its midpoint carries the same kernel: the
+    integrals add, and the midpoint node's share splits linearly."""
+    rng = np.random.default_rng(22)
+    for _ in range(40):
+        eps = rng.uniform(0.3, 1.5)
+        A, B = rng.normal(size=3), rng.normal(size=3) * 3.0
+        M = (A + B) / 2
+        c = M + rng.normal(size=3) * eps
+        K = oracle.seg_kernel(c, A, B, eps)
+        K1, K2 = oracle.seg_kernel(c, A, M, eps), oracle.seg_kernel(c, M, B, eps)
+        wa, wb = K[0] - K[1], K[1]
+        wa1, wb1, wa2, wb2 = K1[0] - K1[1], K1[1], K2[0] - K2[1], K2[1]
+        np.testing.assert_allclose(K[0], K1[0] + K2[0], rtol=1e-12)
+        np.testing.assert_allclose(wa, wa1 + 0.5 * (wb1 + wa2), rtol=1e-11, atol=1e-14 * K[0])
+        np.testing.assert_allclose(wb, wb2 + 0.5 * (wb1 + wa2), rtol=1e-11, atol=1e-14 * K[0])
+
+
+def test_segment_kernel_long_segment_is_the_2d_gaussian():
+    """Far from the ends the integral across a long segment is the 2-D
+    kernel of Eq. almGaussian, and the first moment places it at t0 / L."""
+    eps = 0.7
+    A, B = np.array([0.0, 0.0, -50.0]), np.array([0.0, 0.0, 50.0])
+    for r, z in ((0.0, 3.0), (0.9, -7.0), (1.8, 20.0)):
+        c = np.array([r * 0.6, r * 0.8, z])
+        K = oracle.seg_kernel(c, A, B, eps)
+        eta = np.exp(-(r / eps) ** 2) / (np.pi * eps ** 2)
+        np.testing.assert_allclose(K[0], eta, rtol=1e-12)
+        np.testing.assert_allclose(K[1], eta * (z + 50.0) / 100.0, rtol=1e-12)
+    # a zero-length segment carries nothing
+    assert np.all(oracle.seg_kernel(np.ones(3), A, A, eps) == 0.0)
+
+
+def _integrated(wl):
+    return W.with_projection(wl, "integrated")
+
+
+def test_integrated_projection_conserves_and_matches_on_one_node_lines():
+    for seed in (5, 6):
+        wl = W.make_random(seed, 26, 22, 20, n_lines=6, precision="fp64",
+                           kinds=("stem", "arc", "random", "point"))
+        r0 = oracle.sample_drag_spread(wl)
+        r1 = oracle.sample_drag_spread(_integrated(wl))
+        F = r1["F"]
+        SV = r1["S"].sum(axis=1) * wl.grid.h ** 3
+        np.testing.assert_allclose(SV, -F.sum(axis=1), rtol=0, atol=1e-12 * np.abs(F).sum())
+        # one-node lines project the same way in both modes
+        single = [l for l in range(wl.beams.n_lines) if wl.beams.line_off[l + 1] - wl.beams.line_off[l] == 1]
+        for l in single:
+            mask = np.zeros(wl.beams.n_lines, np.uint8)
+            mask[l] = 1
+            a = oracle.project(wl.grid, wl.beams, wl.step.P, r0["F"], line_mask=mask)["S"]
+            b = oracle.project(wl.grid, _integrated(wl).beams, wl.step.P, r0["F"], line_mask=mask)["S"]
+            np.testing.assert_array_equal(a, b)
+
+
+def test_integrated_projection_inside_a_straight_line():
+    """A long straight line with equal loads.  The integrated kernel gives
+    every interior node the weight of its CV length (the nearest-segment
+    weights jitter with the number of cell layers each segment's slab holds:
+    the seams Sec. 6 names), and inside the line the source is the 2-D
+    Gaussian of Eq. almGaussian times the load per length."""
+    g = GridSpec(40, 40, 60, 0.01)
+    n, L, eps = 41, 0.0125, 0.016
+    x0, y0 = 0.2003, 0.1997
+    P = np.stack([np.full(n, x0), np.full(n, y0), 0.05 + L * np.arange(n)])
+    wl = _line_workload(P, _uniform(g, (0.5, 0, 0)), grid=g, cv=L, per_line=dict(eps=eps))
+    F = oracle.point_step(wl.grid, wl.beams, wl.step)["F"]
+    p0 = oracle.project(wl.grid, wl.beams, wl.step.P, F)
+    p1 = oracle.project(wl.grid, _integrated(wl).beams, wl.step.P, F)
+    inner = slice(12, 29)
+    np.testing.assert_allclose(p1["w"][inner] / L, 1.0, atol=1e-3)
+    assert np.abs(p0["w"][inner] / L - 1.0).max() > 1e-2
+    idx = np.arange(g.n_cells)
+    i, j, k = idx % g.nx, (idx // g.nx) % g.ny, idx // (g.nx * g.ny)
+    r2 = ((i + 0.5) * g.h - x0) ** 2 + ((j + 0.5) * g.h - y0) ** 2
+    interior = (k >= 20) & (k <= 35)
+    expect = -np.outer(F[:, 20] / L, np.exp(-r2[interior] / eps ** 2) / (np.pi * eps ** 2))
+    expect[:, r2[interior] > (3 * eps) ** 2] = 0.0
+    scale = np.abs(expect).max()
+    assert np.abs(p1["S"][:, interior] - expect).max() / scale < 2e-3
+
+
+def test_integrated_projection_sends_each_node_share_to_its_end():
+    """One segment, the load on its first node only: the load per length
+    falls linearly from that node to the other, so the source's centroid
+    along the axis lies a third of the way along the segment (the shares
+    swapped would put it at two thirds)."""
+    g = GridSpec(30, 30, 60, 0.01)
+    P = np.array([[0.15, 0.15], [0.15, 0.15], [0.12, 0.42]])
+    wl = _line_workload(P, _uniform(g, (0.5, 0, 0)), grid=g, cv=0.15, per_line=dict(eps=0.02))
+    F = np.zeros((3, 2))
+    F[0, 0] = 1.0
+    S = oracle.project(wl.grid, _integrated(wl).beams, wl.step.P, F)["S"][0]
+    z = (np.arange(g.n_cells) // (g.nx * g.ny) + 0.5) * g.h
+    zc = (np.abs(S) * z).sum() / np.abs(S).sum()
+    assert abs(zc - (0.12 + 0.30 / 3)) < 0.005, zc
