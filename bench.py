@@ -55,6 +55,8 @@ def _args():
                     help="add the Morison inertia term (accelerating fluid and beams, C_Mn = 1, C_Mt = 0.1)")
     ap.add_argument("--sample", default="trilinear", choices=["trilinear", "cell", "gauss"],
                     help="sampling operator of both velocity samples (cell: the containing cell; gauss: Gaussian volume average)")
+    ap.add_argument("--projection", default="nearest", choices=["nearest", "integrated"],
+                    help="projection: nearest segment (the paper's) or segment-integrated 3-D Gaussian")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -254,6 +256,9 @@ def run_ours(a):
     if a.sample != "trilinear":
         from paper_2609_39443_b300 import workloads as W
         wl = W.with_sample_mode(wl, a.sample)
+    if a.projection != "nearest":
+        from paper_2609_39443_b300 import workloads as W
+        wl = W.with_projection(wl, a.projection)
     inst = Instance(wl, device=f"cuda:{local}")
     tuned = {"weights": "brick", "brick_z": 8, "autotuned": False}
     if a.weights or a.brick_z or a.records:
@@ -385,7 +390,7 @@ def run_ours(a):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if wl.grid.precision == "fp64" else "f32", "data": "synthetic",
                 "config": {"workload": wl.name, "cells": wl.grid.n_cells, "points": wl.beams.n_points,
-                           "inertia": bool(a.inertia), "sample": a.sample,
+                           "inertia": bool(a.inertia), "sample": a.sample, "projection": a.projection,
                            "lines": wl.beams.n_lines, "parallelism": f"{world} independent instances",
                            "l2": "flushed between timed steps (256 MiB write)", "options": tuned},
                 "kernel_cell_updates_per_s": supp * value,

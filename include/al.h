@@ -55,6 +55,8 @@ extern "C" {
 
 #define AL_SAMPLE_TRILINEAR 0  /* trilinear interpolation of cell values   */
 #define AL_SAMPLE_CELL      1  /* value of the single containing cell (the paper's operator) */
+#define AL_PROJ_NEAREST     0
+#define AL_PROJ_INTEGRATED  1
 #define AL_SAMPLE_GAUSS     2  /* kernel-weighted volume average: sum_j g_j U_j / sum_j g_j over the
                                   cells whose centre lies within 3 eps of the point, g_j =
                                   exp(-(|C_j - p| / eps)^2) with the line's projection width eps
@@ -119,6 +121,17 @@ typedef struct {
      * operator, and a = a_f - a_b (the fluid's acceleration relative to the
      * beam) split along the tangent. */
     const double *cm_n, *cm_t; /* [n_lines] or NULL */
+    /* Projection (Sec. 3.2.4): AL_PROJ_NEAREST is the paper's (each cell takes
+     * the closest segment of each line, Eq. almProjectionPoint);
+     * AL_PROJ_INTEGRATED is the variant Sec. 6 proposes: every segment whose
+     * closest point lies within 3 eps adds the integral of the 3-D Gaussian
+     * exp(-|x|^2/eps^2) / (pi^(3/2) eps^3) along it, the load per length
+     * interpolated linearly between its nodes (closed forms in erf and exp of
+     * the tangential coordinate; its integral across an infinite line is the
+     * 2-D kernel of Eq. almGaussian).  It takes the segment weights pass and
+     * records for every line; status[AL_ST_SUPPORT] then counts (cell,
+     * segment) pairs. */
+    int proj_mode;
 } al_beam_desc;
 
 /* Inputs of one step: DEVICE pointers, element type per grid precision,

@@ -200,6 +200,7 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     if (b.sample_mode != AL_SAMPLE_TRILINEAR && b.sample_mode != AL_SAMPLE_CELL && b.sample_mode != AL_SAMPLE_GAUSS)
         return AL_ERR_ARG;
     if (b.drag_mode != AL_DRAG_DISCRETE && b.drag_mode != AL_DRAG_SPLIT) return AL_ERR_ARG;
+    if (b.proj_mode != AL_PROJ_NEAREST && b.proj_mode != AL_PROJ_INTEGRATED) return AL_ERR_ARG;
     if (!(b.tau >= 0.0)) return AL_ERR_ARG;
     const double npn = std::sqrt(b.n_p[0] * b.n_p[0] + b.n_p[1] * b.n_p[1] + b.n_p[2] * b.n_p[2]);
     if (!(npn == 0.0 || std::fabs(npn - 1.0) < 1e-9)) return AL_ERR_ARG;
@@ -291,7 +292,11 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
             double L = 0.0;
             for (int i = b.line_off[l]; i < b.line_off[l + 1]; ++i) L += b.cv_len[i];
             const double Rc = 3.0 * b.eps[l] / g->d.dx, Lc = L / g->d.dx, pi = 3.14159265358979323846;
-            est += pi * Rc * Rc * Lc + 4.0 / 3.0 * pi * Rc * Rc * Rc + pi * Rc * Lc + 2.0 * pi * Rc * Rc + 64.0;
+            double pairs = pi * Rc * Rc * Lc + 4.0 / 3.0 * pi * Rc * Rc * Rc + pi * Rc * Lc + 2.0 * pi * Rc * Rc + 64.0;
+            const int nl_pts = b.line_off[l + 1] - b.line_off[l];
+            if (b.proj_mode == AL_PROJ_INTEGRATED && nl_pts >= 2)   // a cell pairs with every segment within 3 eps
+                pairs *= 2.0 * Rc / std::max(Lc / (nl_pts - 1), 0.25) + 2.0;
+            est += pairs;
         }
         const size_t rsz = g->d.precision == AL_FP64 ? sizeof(al::Rec<double>) : sizeof(al::Rec<float>);
         long long want = b.n_lines > 0 ? (long long)(1.25 * est) + 4096 : 0;
@@ -395,11 +400,16 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     bc.tau = g->bd.tau; bc.sample_mode = g->bd.sample_mode; bc.drag_mode = g->bd.drag_mode;
     bc.tangents_given = g->bd.tangents_given;
     bc.cm_n = g->d_cmn; bc.cm_t = g->d_cmt;
+    bc.proj_mode = g->bd.proj_mode;
     bc.inertia = (g->d_cmn != nullptr && g->n_lines > 0) ? 1 : 0;
     I.g = g->gc;
     I.g.rec_total = g->rec_total;
     I.g.nbrick_max = g->nbrick_max;
-    I.g.rmode = (g->opt_record && g->gc.wmode != 0 && g->gc.smode == 0 && g->rec_total > 0) ? 1 : 0;
+    if (g->bd.proj_mode == AL_PROJ_INTEGRATED) {        // segment pass and gather for every line
+        I.g.wmode = AL_WEIGHTS_SEGMENT;
+        I.g.smode = AL_SPREAD_GATHER;
+    }
+    I.g.rmode = (g->opt_record && I.g.wmode != 0 && I.g.smode == 0 && g->rec_total > 0) ? 1 : 0;
     I.status = out->status ? out->status : g->statusInt;
     I.totals = out->totals ? out->totals : g->totalsInt;
     return I;
@@ -785,7 +795,7 @@ static int batch_assign_t(al_batch b, int slot, al_grid g, const al_step_in *in,
     AL_CUDA(cudaEventRecord(b->slot_ev[slot], st));
     b->grids[slot] = g;
     if (g) { b->ins[slot] = *in; b->outs[slot] = *out; }
-    if (g && g->gc.wmode != 0) b->any_segment_weights = true;
+    if (g && h->g.wmode != 0) b->any_segment_weights = true;
     if (g && g->bd.sample_mode == AL_SAMPLE_GAUSS) b->any_gauss = true;
     b->cnt_pts[slot] = g ? g->n_points : 0;
     b->cnt_lines[slot] = g ? g->n_lines : 0;

@@ -82,6 +82,7 @@ struct BeamsC {
     int sample_mode, drag_mode, tangents_given;
     const double *cm_n, *cm_t;   // added-mass coefficients (inertia != 0)
     int inertia;
+    int proj_mode;               // 0 nearest segment, 1 segment-integrated 3-D Gaussian
 };
 
 struct LineG {                   // per line, rebuilt every step
@@ -1055,6 +1056,8 @@ struct WSeg {
     bool has_lo, has_hi;
     T R2, gr, ie2, eta0;
     double eps;
+    int integ;                    // segment-integrated kernel (projection variant, lines of >= 2 nodes)
+    T epsc;                       // eps in cells
 };
 
 // |x|^2 and x.m with every operation rounded explicitly
@@ -1109,6 +1112,42 @@ __device__ __forceinline__ void pair_w(T eta, T s, T &wa, T &wb) {
 // the pair's momentum source for nodal forces fa, fb (S receives minus this)
 template <typename T>
 __device__ __forceinline__ T pair_src(T wa, T wb, T fa, T fb) { return r_fma(wa, fa, r_mul(wb, fb)); }
+
+__device__ __forceinline__ float t_erf(float x) { return erff(x); }
+__device__ __forceinline__ double t_erf(double x) { return erf(x); }
+__device__ __forceinline__ float t_exp(float x) { return expf(x); }
+__device__ __forceinline__ double t_exp(double x) { return exp(x); }
+
+// Segment-integrated 3-D Gaussian (the projection variant of Sec. 6) of the
+// global cell cg against segment (ka, kb): with t0 the cell's tangential
+// coordinate along the segment, r_p its distance from the segment's axis
+// and L the length (cells, eps in cells epsc),
+//   K0 = g E,  K1 = (g / L) (t0 E + epsc / (2 sqrt(pi)) (e^(-t0^2/epsc^2) - e^(-(L-t0)^2/epsc^2))),
+//   E = (erf((L - t0)/epsc) + erf(t0/epsc)) / 2,  g = eta0 exp(-r_p^2/epsc^2),
+// the integral of exp(-|x|^2/eps^2) / (pi^(3/2) eps^3) along the segment and
+// its first moment in t / L; the nodes take wa = K0 - K1, wb = K1.  One
+// compiled body (not inlined) serves the segment pass and the gather, so
+// both produce the same bits for a pair.
+template <typename T>
+__device__ __noinline__ void pair_int(const Scratch<T> &sc, long long np, int ka, const int cg[3], T epsc, T eta0,
+                                      T ie2l, T &wa, T &wb) {
+    T x[3], D[3];
+    node_off(sc, np, ka, cg, x);
+    for (int a = 0; a < 3; ++a) D[a] = sc.segD[a * np + ka];
+    const T L = tsqrt(norm2_r(D));
+    if (!(L > (T)0)) { wa = wb = (T)0; return; }
+    const T t0 = dot_r(x, D) / L;
+    T pp[3];
+    for (int a = 0; a < 3; ++a) pp[a] = r_fma(-t0 / L, D[a], x[a]);
+    const T g = eta0 * Tr<T>::ex2(-norm2_r(pp) * ie2l);
+    const T ie = (T)1 / epsc;
+    const T E = (T)0.5 * (t_erf((L - t0) * ie) + t_erf(t0 * ie));
+    const T m = epsc * (T)0.28209479177387814 *                      // 1 / (2 sqrt(pi))
+                (t_exp(-(t0 * ie) * (t0 * ie)) - t_exp(-((L - t0) * ie) * ((L - t0) * ie)));
+    const T K0 = g * E, K1 = g / L * (t0 * E + m);
+    wa = K0 - K1;
+    wb = K1;
+}
 
 // Per-warp staging of the records of one segment: each record takes a
 // shared-memory slot, and when the segment is done the warp reserves the
@@ -1197,9 +1236,12 @@ template <typename T> struct WSink<T, false> {
     RecStage<T> *st = nullptr;   // the CTA's staging (null: each record reserves its slot)
     bool plan_ok = false;        // regions sized for this brick height: write; otherwise only count
     int q = 0;                   // instance index (key of the staging)
-    __device__ __forceinline__ void add(const GridC &, const StepPtrs<T> &, const int cg[3], T eta, T s) {
+    __device__ __forceinline__ void add(const GridC &g, const StepPtrs<T> &p, const int cg[3], T eta, T s) {
         T a, b;
         pair_w(eta, s, a, b);
+        add_w(g, p, cg, a, b);
+    }
+    __device__ __forceinline__ void add_w(const GridC &, const StepPtrs<T> &, const int cg[3], T a, T b) {
         wa.add(a);
         wb.add(b);
         if (rec && st && plan_ok) {
@@ -1244,9 +1286,12 @@ template <typename T> struct WSink<T, true> {
     Acc<T> sum[3];
     int nsupp = 0;
     __device__ __forceinline__ void add(const GridC &g, const StepPtrs<T> &p, const int cg[3], T eta, T s) {
-        const long long idx = cg[0] + (long long)g.nx * (cg[1] + (long long)g.ny * cg[2]);
         T wa, wb;
         pair_w(eta, s, wa, wb);
+        add_w(g, p, cg, wa, wb);
+    }
+    __device__ __forceinline__ void add_w(const GridC &g, const StepPtrs<T> &p, const int cg[3], T wa, T wb) {
+        const long long idx = cg[0] + (long long)g.nx * (cg[1] + (long long)g.ny * cg[2]);
         for (int a = 0; a < 3; ++a) {
             const T v = -pair_src(wa, wb, fa[a], fb[a]);
             atomicAdd(&p.S[a][idx], v);
@@ -1320,9 +1365,15 @@ __device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const Gri
     else if (r2 > c.R2 + c.gr) in = false;
     else { in = within_f64(g, p, c.eps, c.k, c.n, AL_CG(0), AL_CG(1), AL_CG(2)); atomicAdd(&status[ST_REFINED], 1); }
     if (!in) return;
-    const T eta = c.eta0 * Tr<T>::ex2(-r2 * c.ie2);
     const int cg[3] = {AL_CG(0), AL_CG(1), AL_CG(2)};
 #undef AL_CG
+    if (c.integ) {                                          // the segment's integrated kernel
+        T a, b;
+        pair_int(sc, (long long)p.np, c.k, cg, c.epsc, c.eta0, c.ie2, a, b);
+        sink.add_w(g, p, cg, a, b);
+        return;
+    }
+    const T eta = c.eta0 * Tr<T>::ex2(-r2 * c.ie2);
     sink.add(g, p, cg, eta, s);
 }
 
@@ -1462,7 +1513,7 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
     if (c.n >= 2 && c.q == c.n - 1) return;                 // the tip starts no segment
     c.nseg = (c.n == 1) ? 1 : c.n - 1;
     c.kb = seg_end(k, c.n);
-    if (!lg.regular) {                                      // the brick passes take this line
+    if (!lg.regular && !b.proj_mode) {                      // the brick passes take this line
         if (!SC && lane == 0) { sc.segWa[k] = 0.0; sc.segWb[k] = 0.0; }   // zero in both encodings
         return;
     }
@@ -1499,9 +1550,13 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
         sink.st = st;
         sink.q = q;
     }
-    const bool regular = lg.regular != 0;
-    c.has_lo = regular && c.q >= 1;
-    c.has_hi = regular && c.q + 1 <= c.n - 2;
+    // the integrated projection takes every segment within 3 eps: no
+    // bisector planes bound a segment's cells
+    const bool regular = lg.regular != 0 || b.proj_mode;
+    c.integ = (b.proj_mode && c.n >= 2) ? 1 : 0;
+    c.epsc = (T)(b.eps[l] / g.h);
+    c.has_lo = !b.proj_mode && regular && c.q >= 1;
+    c.has_hi = !b.proj_mode && regular && c.q + 1 <= c.n - 2;
     for (int a = 0; a < 3; ++a) {
         c.m0[a] = c.has_lo ? sc.nodeM[a * np + k] : (T)0;
         c.m1[a] = c.has_hi ? sc.nodeM[a * np + k + 1] : (T)0;
@@ -1531,7 +1586,7 @@ __device__ unsigned int d_normalise(const GridC &g, const BeamsC &b, const Scrat
     const int off = b.line_off[l], n = b.line_off[l + 1] - off, q = k - off;
     double w = 0.0;
     const LineG &lg = sc.lines[l];
-    if (g.wmode == 0 || !lg.regular) {
+    if ((g.wmode == 0 || !lg.regular) && !b.proj_mode) {
         // brick pass: fixed-point sum of omega eta / eta0; w = sum eta0 V 2^-wshift
         w = ldexp((double)sc.wfix[k], -lg.wshift) * (lg.eta0 * g.V);
     } else if (n == 1) {
@@ -1835,6 +1890,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     const int B0 = bxi * BX, B1 = byi * BY, B2 = bzi * BZ;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (WP && g.wmode != 0 && *sc.anyIrr == 0) return;      // the segment pass took every line
+    if (WP && b.proj_mode) return;                           // the integrated projection: segment pass only
     const int nzb = min(BZ, g.nz - B2);              // layers of this brick inside the grid
     const int nxb = min(BX, g.nx - B0), nyb = min(BY, g.ny - B1);
     int nsupp = 0;                                   // (cell, line) pairs within 3 eps
@@ -1901,6 +1957,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     // order; bricks with more than LIST candidates take several passes (the
     // spread clears the words in the last one)
     const bool keep_certified = WP ? (g.wmode == 0) : (g.smode == 0 && !replay);
+    const bool keep_none = !WP && replay && b.proj_mode;     // integrated: the records hold every line
     const int wper = (W + 31) / 32;
     for (int pass = 0;; ++pass) {
         __syncthreads();
@@ -1908,8 +1965,8 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
             const int wa = min(W, lane * wper), wb = min(W, wa + wper);
             int cnt = 0;
             for (int w = wa; w < wb; ++w) {
-                uint32_t m = mrow[w];
-                if (!keep_certified) {                   // the segment pass takes certified lines
+                uint32_t m = keep_none ? 0u : mrow[w];
+                if (!keep_certified && m) {              // the segment pass takes certified lines
                     uint32_t keep = 0u, t = m;
                     while (t) {
                         const int bit = __ffs(t) - 1;
@@ -1930,7 +1987,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
             int pos = pre - cnt;
             if (pos < hi && pos + cnt > lo) {
                 for (int w = wa; w < wb; ++w) {
-                    uint32_t m = mrow[w];
+                    uint32_t m = keep_none ? 0u : mrow[w];
                     while (m) {
                         const int bit = __ffs(m) - 1;
                         m &= m - 1;
@@ -2162,7 +2219,36 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                         bool in = false;
                         int js = 0;
                         T s = (T)0, r2 = (T)0;
-                        if (tx <= ix1 && ty >= iy0 && ty <= iy1 && dx * dx + dy * dy <= rh2) {
+                        if (!WP && b.proj_mode && n >= 2 && tx <= ix1 && ty >= iy0 && ty <= iy1 &&
+                            dx * dx + dy * dy <= rh2) {
+                            // integrated projection: every candidate segment within 3 eps
+                            // adds its integrated kernel, with the segment pass's values
+                            const int cgl[3] = {B0 + tx, B1 + ty, gz};
+                            const T epsc = (T)(b.eps[sm.e_line[e]] / g.h);
+                            const int c = ty * BX + tx;
+                            for (int jj = jlo; jj <= jhi; ++jj) {
+                                const int ka = first + jj;
+                                T s2, r22;
+                                pair_sr(sc, np, ka, ka + 1, cgl, s2, r22);
+                                bool inj;
+                                if (r22 < R2 - gr) inj = true;
+                                else if (r22 > R2 + gr) inj = false;
+                                else inj = nl_within(g, p, b.eps[sm.e_line[e]], ka, n, cgl[0], cgl[1], cgl[2], status);
+                                if (!inj) continue;
+                                ++nsupp;
+                                T wa, wb;
+                                pair_int(sc, np, ka, cgl, epsc, e0v, ie2, wa, wb);
+                                T fa3[3], fb3[3];
+                                if (base >= 0) {
+                                    const int ss = base + (jj - jlo);
+                                    for (int a = 0; a < 3; ++a) { fa3[a] = sm.u.s.Fh[a][ss]; fb3[a] = sm.u.s.Fh[a][ss + 1]; }
+                                } else {
+                                    for (int a = 0; a < 3; ++a) { fa3[a] = sc.fhat[a * np + ka]; fb3[a] = sc.fhat[a * np + ka + 1]; }
+                                }
+                                for (int a = 0; a < 3; ++a)
+                                    sm.u.s.acc[z][a][c] -= to_fixed_s(pair_src(wa, wb, fa3[a], fb3[a]), fsh);
+                            }
+                        } else if (tx <= ix1 && ty >= iy0 && ty <= iy1 && dx * dx + dy * dy <= rh2) {
                             const int gxc = B0 + tx, gyc = B1 + ty;
                             const T C[3] = {(T)cx, (T)cy, (T)czf};
                             if (base < 0) {
