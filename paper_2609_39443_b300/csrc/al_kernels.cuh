@@ -1149,38 +1149,35 @@ __device__ __noinline__ void pair_int(const Scratch<T> &sc, long long np, int ka
     wb = K1;
 }
 
-// Per-warp staging of the records of one segment: each record takes a
-// shared-memory slot, and when the segment is done the warp reserves the
-// slots of each brick (instance, brick key) with one global atomic and
-// writes the records there; warps never wait for one another.  Records
-// beyond CAP, or of a brick that finds the table full, reserve their own
-// slot directly.
+// Per-CTA staging of the records of a round of segments (one per warp): each
+// record takes a shared-memory slot, and at the end of the round the CTA
+// reserves the slots of each brick (instance, brick key) with one global
+// atomic and writes the records there.  Records beyond CAP, or of a brick
+// that finds the table full, reserve their own slot directly.
 template <typename T> struct RecStage {
-    static constexpr int CAP = 192, NB = 16;
+    static constexpr int CAP = 768, NB = 64;
     Rec<T> rec[CAP];
     unsigned long long rk[CAP];     // (instance << 32) | brick of each staged record
     int loc[CAP];                   // (table entry << 16) | rank within the entry; -1: written directly
-    unsigned long long key[NB];     // table of the segment's (instance, brick) keys; ~0: empty
+    unsigned long long key[NB];     // table of the round's (instance, brick) keys; ~0: empty
     int cnt[NB], base[NB];
     int n;
 };
 template <typename T>
 __device__ __forceinline__ void rec_init(RecStage<T> &st) {
-    const int lane = threadIdx.x & 31;
-    if (lane < RecStage<T>::NB) { st.key[lane] = ~0ull; st.cnt[lane] = 0; }
-    if (lane == 0) st.n = 0;
-    __syncwarp();
+    for (int h = threadIdx.x; h < RecStage<T>::NB; h += blockDim.x) { st.key[h] = ~0ull; st.cnt[h] = 0; }
+    if (threadIdx.x == 0) st.n = 0;
+    __syncthreads();
 }
-// the whole warp calls this after its segment; sc_of(q) gives instance q's scratch
+// the whole CTA calls this after its round; sc_of(q) gives instance q's scratch
 template <typename T, typename ScOf>
 __device__ void rec_flush(RecStage<T> &st, ScOf sc_of) {
     constexpr int CAP = RecStage<T>::CAP, NB = RecStage<T>::NB;
-    const int lane = threadIdx.x & 31;
-    __syncwarp();
+    __syncthreads();
     const int n = min(st.n, CAP);
-    for (int i = lane; i < n; i += 32) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const unsigned long long key = st.rk[i];
-        int h = (int)((key * 0x9E3779B97F4A7C15ull) >> 60);
+        int h = (int)((key * 0x9E3779B97F4A7C15ull) >> 58);
         int slot = -1;
         for (int t = 0; t < NB; ++t, h = (h + 1) & (NB - 1)) {
             const unsigned long long old = atomicCAS(&st.key[h], ~0ull, key);
@@ -1196,16 +1193,16 @@ __device__ void rec_flush(RecStage<T> &st, ScOf sc_of) {
             st.loc[i] = -1;
         }
     }
-    __syncwarp();
-    if (lane < NB) {
-        const unsigned long long key = st.key[lane];
+    __syncthreads();
+    for (int h = threadIdx.x; h < NB; h += blockDim.x) {
+        const unsigned long long key = st.key[h];
         if (key != ~0ull) {
             const Scratch<T> &s = sc_of((int)(key >> 32));
-            st.base[lane] = atomicAdd(&s.rcnt[(int)(key & 0xffffffffull)], st.cnt[lane]);
+            st.base[h] = atomicAdd(&s.rcnt[(int)(key & 0xffffffffull)], st.cnt[h]);
         }
     }
-    __syncwarp();
-    for (int i = lane; i < n; i += 32) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int lc = st.loc[i];
         if (lc < 0) continue;
         const int h = lc >> 16;
@@ -1215,10 +1212,10 @@ __device__ void rec_flush(RecStage<T> &st, ScOf sc_of) {
         const int pos = st.base[h] + (lc & 0xffff);
         if (pos < s.rcap[br]) s.rec[s.roff[br] + pos] = st.rec[i];
     }
-    __syncwarp();
-    if (lane < NB) { st.key[lane] = ~0ull; st.cnt[lane] = 0; }
-    if (lane == 0) st.n = 0;
-    __syncwarp();
+    __syncthreads();
+    for (int h = threadIdx.x; h < NB; h += blockDim.x) { st.key[h] = ~0ull; st.cnt[h] = 0; }
+    if (threadIdx.x == 0) st.n = 0;
+    __syncthreads();
 }
 
 // What a visited cell feeds: the segment's two weight sums (SC = false), or
@@ -2581,13 +2578,11 @@ __global__ void __launch_bounds__(256) k_mask(GridC g, BeamsC b, Scratch<T> sc) 
 }
 template <typename T>
 __global__ void __launch_bounds__(128) k_weights(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
-    __shared__ RecStage<T> stw[4];
-    RecStage<T> &st = stw[threadIdx.x >> 5];
-    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (k >= b.n_points) return;                                 // whole warps
+    __shared__ RecStage<T> st;
     const bool stage = g.rmode != 0;
     if (stage) rec_init(st);
-    d_weights<T, false>(g, b, sc, p, status, k, threadIdx.x & 31, stage ? &st : nullptr, 0);
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k < b.n_points) d_weights<T, false>(g, b, sc, p, status, k, threadIdx.x & 31, stage ? &st : nullptr, 0);
     if (stage) rec_flush(st, [&](int) -> const Scratch<T> & { return sc; });
 }
 // scatter form of the projection: one warp per segment of a certified line
@@ -2685,17 +2680,21 @@ __global__ void __launch_bounds__(256) kb_mask(const Inst<T> *I, const int *sel,
 }
 template <typename T>
 __global__ void __launch_bounds__(128) kb_weights(const Inst<T> *I, const int *sel, const long long *pre, int n) {
-    __shared__ RecStage<T> stw[4];
-    RecStage<T> &st = stw[threadIdx.x >> 5];
+    __shared__ RecStage<T> st;
     rec_init(st);
     const long long total = pre[n];
-    const long long nw = (long long)gridDim.x * blockDim.x / 32;
-    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
-        const int q = owner(pre, n, w);
-        const Inst<T> &x = I[AL_SEL(q)];
-        d_weights<T, false>(x.g, x.b, x.sc, x.p, x.status, (int)(w - pre[q]), threadIdx.x & 31,
-                            x.g.rmode ? &st : nullptr, q);
-        rec_flush(st, [&](int q2) -> const Scratch<T> & { return I[AL_SEL(q2)].sc; });
+    const int nwb = blockDim.x / 32;
+    // rounds of one segment per warp, the whole CTA together (the staged
+    // records are flushed after each round)
+    for (long long w0 = (long long)blockIdx.x * nwb; w0 < total; w0 += (long long)gridDim.x * nwb) {
+        const long long w = w0 + (threadIdx.x >> 5);
+        if (w < total) {
+            const int q = owner(pre, n, w);
+            const Inst<T> &x = I[AL_SEL(q)];
+            d_weights<T, false>(x.g, x.b, x.sc, x.p, x.status, (int)(w - pre[q]), threadIdx.x & 31,
+                                x.g.rmode ? &st : nullptr, q);
+        }
+        rec_flush(st, [&](int q) -> const Scratch<T> & { return I[AL_SEL(q)].sc; });
     }
 }
 template <typename T>
