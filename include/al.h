@@ -222,9 +222,10 @@ int al_trace_last(al_grid g, float *ms /* [AL_TRACE_N] */);
 #define AL_OPT_SPREAD_CTAS  3
 /* AL_OPT_SPREAD selects the projection of Eq. almMomentumSource:
  *   AL_SPREAD_GATHER (default): cell-centric pass per brick, every cell of S
- *     written once by one thread; each cell's sources are summed as exact
- *     fixed-point integers, so the result does not depend on their order
- *     (bitwise reproducible);
+ *     written once by one thread, its sources summed in line order, or, when
+ *     records are replayed (AL_OPT_RECORD) or the integrated projection is
+ *     chosen, as exact fixed-point integers, whose sum does not depend on
+ *     the order (bitwise reproducible either way);
  *   AL_SPREAD_SCATTER: for comparison, lines with a walk certificate add
  *     their sources segment by segment with float atomics (summation order,
  *     hence the last bits, vary run to run); the other lines and the
@@ -233,7 +234,9 @@ int al_trace_last(al_grid g, float *ms /* [AL_TRACE_N] */);
 #define AL_OPT_SPREAD       4
 #define AL_SPREAD_GATHER    0
 #define AL_SPREAD_SCATTER   1
-/* AL_OPT_RECORD (default 1): with AL_WEIGHTS_SEGMENT and the gather, the
+/* AL_OPT_RECORD (default 1; 0: off; 2: no records, but the gather sums in
+ * the fixed point a replay uses, which gives the replay's bits, for checks):
+ * with AL_WEIGHTS_SEGMENT and the gather, the
  * segment pass records every (cell, segment) pair it finds inside the 3 eps
  * support (cell, node, the two node weights), in a region per brick sized
  * from the previous step's counts, and the gather replays the records of

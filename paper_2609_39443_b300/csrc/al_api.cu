@@ -322,10 +322,14 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
 // prefer shared memory over L1 so that several bricks share an SM.
 template <typename T, int BZ>
 static cudaError_t brick_attrs() {
-    const int bytes = (int)sizeof(al::SpreadSmem<T, BZ>);
-    const void *fns[4] = {(const void *)al::k_spread<T, BZ>, (const void *)al::kb_spread<T, BZ>,
-                          (const void *)al::k_bweights<T, BZ>, (const void *)al::kb_bweights<T, BZ>};
-    for (const void *f : fns) {
+    const int fx = (int)sizeof(al::SpreadSmem<T, BZ, true>), fl = (int)sizeof(al::SpreadSmem<T, BZ, false>);
+    const void *fns[5] = {(const void *)al::k_spread<T, BZ, true>, (const void *)al::k_spread<T, BZ, false>,
+                          (const void *)al::kb_spread<T, BZ>, (const void *)al::k_bweights<T, BZ>,
+                          (const void *)al::kb_bweights<T, BZ>};
+    const int bytes_of[5] = {fx, fl, fx, fl, fl};
+    for (int i = 0; i < 5; ++i) {
+        const void *f = fns[i];
+        const int bytes = bytes_of[i];
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
@@ -347,9 +351,15 @@ static cudaError_t spread_smem_attr() {
 template <typename T, int BZ>
 static void launch_bricks(const al::Inst<T> &I, bool weights, cudaStream_t st) {
     using namespace al;
-    const size_t smem = sizeof(SpreadSmem<T, BZ>);
-    if (weights) k_bweights<T, BZ><<<(unsigned)I.g.nbrick, SPREAD_THREADS, smem, st>>>(I.g, I.b, I.sc, I.p, I.status);
-    else k_spread<T, BZ><<<(unsigned)I.g.nbrick, SPREAD_THREADS, smem, st>>>(I.g, I.b, I.sc, I.p, I.status);
+    if (weights)
+        k_bweights<T, BZ><<<(unsigned)I.g.nbrick, SPREAD_THREADS, sizeof(SpreadSmem<T, BZ, false>), st>>>(
+            I.g, I.b, I.sc, I.p, I.status);
+    else if (I.g.fx)
+        k_spread<T, BZ, true><<<(unsigned)I.g.nbrick, SPREAD_THREADS, sizeof(SpreadSmem<T, BZ, true>), st>>>(
+            I.g, I.b, I.sc, I.p, I.status);
+    else
+        k_spread<T, BZ, false><<<(unsigned)I.g.nbrick, SPREAD_THREADS, sizeof(SpreadSmem<T, BZ, false>), st>>>(
+            I.g, I.b, I.sc, I.p, I.status);
 }
 template <typename T>
 static void launch_bricks_bz(const al::Inst<T> &I, bool weights, cudaStream_t st) {
@@ -409,7 +419,8 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
         I.g.wmode = AL_WEIGHTS_SEGMENT;
         I.g.smode = AL_SPREAD_GATHER;
     }
-    I.g.rmode = (g->opt_record && I.g.wmode != 0 && I.g.smode == 0 && g->rec_total > 0) ? 1 : 0;
+    I.g.rmode = (g->opt_record == 1 && I.g.wmode != 0 && I.g.smode == 0 && g->rec_total > 0) ? 1 : 0;
+    I.g.fx = (I.g.rmode || g->opt_record == 2 || g->bd.proj_mode == AL_PROJ_INTEGRATED) ? 1 : 0;
     I.status = out->status ? out->status : g->statusInt;
     I.totals = out->totals ? out->totals : g->totalsInt;
     return I;
@@ -502,7 +513,7 @@ extern "C" int al_set_option(al_grid g, int option, int value) {
         g->gc.smode = value;
         return AL_OK;
     case AL_OPT_RECORD:
-        if (value != 0 && value != 1) return AL_ERR_ARG;
+        if (value < 0 || value > 2) return AL_ERR_ARG;
         g->opt_record = value;
         return AL_OK;
     default:
@@ -688,9 +699,9 @@ static int batch_rebuild_t(al_batch b) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     switch (b->bz) {
-    case 4: AL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_spread<T, 4>, SPREAD_THREADS, sizeof(SpreadSmem<T, 4>))); break;
-    case 16: AL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_spread<T, 16>, SPREAD_THREADS, sizeof(SpreadSmem<T, 16>))); break;
-    default: AL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_spread<T, 8>, SPREAD_THREADS, sizeof(SpreadSmem<T, 8>))); break;
+    case 4: AL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_spread<T, 4>, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, true>))); break;
+    case 16: AL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_spread<T, 16>, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, true>))); break;
+    default: AL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_spread<T, 8>, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, true>))); break;
     }
     if (occ < 1) occ = 1;
     b->occ = occ;
@@ -749,9 +760,9 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
         if (tot_bricks > 0) {
             const int gs = (int)std::min<long long>(b->spread_grid, tot_bricks);
             switch (b->bz) {
-            case 4: kb_bweights<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4>), st>>>(I, sel, pb, n); break;
-            case 16: kb_bweights<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16>), st>>>(I, sel, pb, n); break;
-            default: kb_bweights<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8>), st>>>(I, sel, pb, n); break;
+            case 4: kb_bweights<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, false>), st>>>(I, sel, pb, n); break;
+            case 16: kb_bweights<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, false>), st>>>(I, sel, pb, n); break;
+            default: kb_bweights<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, false>), st>>>(I, sel, pb, n); break;
             }
         }
         kb_normalise<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
@@ -759,9 +770,9 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
     if (tot_bricks > 0) {
         const int gs = (int)std::min<long long>(b->spread_grid, tot_bricks);
         switch (b->bz) {
-        case 4: kb_spread<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4>), st>>>(I, sel, pb, n); break;
-        case 16: kb_spread<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16>), st>>>(I, sel, pb, n); break;
-        default: kb_spread<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8>), st>>>(I, sel, pb, n); break;
+        case 4: kb_spread<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, true>), st>>>(I, sel, pb, n); break;
+        case 16: kb_spread<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, true>), st>>>(I, sel, pb, n); break;
+        default: kb_spread<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, true>), st>>>(I, sel, pb, n); break;
         }
     }
     kb_totals<T><<<std::max(1, std::min(n, 1024)), 256, 0, st>>>(I, sel, n);

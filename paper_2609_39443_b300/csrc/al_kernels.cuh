@@ -36,6 +36,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <math.h>
+#include <type_traits>
 
 namespace al {
 
@@ -63,6 +64,7 @@ struct GridC {
     int bz;                      // brick height of the projection (4, 8 or 16 cells)
     int smode;                   // 0: gather (every line); 1: scatter with atomics for certified lines
     int rmode;                   // 1: the segment pass records its (cell, segment) pairs, the spread replays them
+    int fx;                      // 1: the spread sums fixed-point integers (replay, integrated projection)
     long long rec_total;         // capacity of the record arena (records)
     long long nbrick_max;        // bricks at the lowest brick height (size of the per-brick arrays)
 };
@@ -1626,8 +1628,9 @@ template <typename T> struct SpreadCap;
 template <> struct SpreadCap<float> { static constexpr int NODES = 640, LIST = 512, ENT = 32; };
 template <> struct SpreadCap<double> { static constexpr int NODES = 320, LIST = 512, ENT = 32; };
 
-template <typename T, int BZ>
+template <typename T, int BZ, bool FX>
 struct SpreadSmem {
+    using AccT = typename std::conditional<FX, long long, T>::type;
     static constexpr int NN = SpreadCap<T>::NODES, LIST = SpreadCap<T>::LIST, ENT = SpreadCap<T>::ENT;
     T P[3][NN];                  // node positions relative to the brick origin
     T M[3][NN];                  // node bisectors
@@ -1638,7 +1641,7 @@ struct SpreadSmem {
         struct {
             T Fh[3][NN];         // spread: f^ at the nodes
             int sk[NN];          // spread: global node index of each staged node
-            long long acc[BZ][3][BX * BY];   // spread: S of the brick's cells, fixed point (2^-sh)
+            AccT acc[BZ][3][BX * BY];   // spread: S of the brick's cells (FX: fixed point, 2^-sh)
         } s;
         unsigned long long wq[NN];   // weights pass: fixed-point w of the staged nodes
     } u;
@@ -1717,8 +1720,8 @@ __device__ __noinline__ int nl_exhaustive(const GridC &g, const Scratch<T> &sc, 
 // closest segments that share a node is decided by the float-float test of
 // the pair (ff_later_closer, defined below); other near ties by the FP64
 // argmin.
-template <typename T, int BZ>
-__device__ __noinline__ int nl_exhaustive_staged(const SpreadSmem<T, BZ> &sm, const GridC &g, const StepPtrs<T> &p,
+template <typename T, typename SMT>
+__device__ __noinline__ int nl_exhaustive_staged(const SMT &sm, const GridC &g, const StepPtrs<T> &p,
                                                  const Scratch<T> &sc, int base, int first, int n, int jlo, int jhi,
                                                  T c0, T c1, T c2, int B0, int B1, int B2, int ci, int cj, int ck,
                                                  int *status) {
@@ -1828,8 +1831,8 @@ static __device__ __noinline__ int ff_later_closer(const float *uhi, const float
     return dh > 0.0f ? 1 : 0;
 }
 
-template <typename T, int BZ>
-__device__ __forceinline__ bool sig_pos(const SpreadSmem<T, BZ> &sm, int s, const T C[3], const GridC &g,
+template <typename T, typename SMT>
+__device__ __forceinline__ bool sig_pos(const SMT &sm, int s, const T C[3], const GridC &g,
                                         const StepPtrs<T> &p, const Scratch<T> &sc, int kglob, int B0, int B1,
                                         int B2, int ci, int cj, int ck, int *status) {
     const T x0 = C[0] - sm.P[0][s], x1 = C[1] - sm.P[1][s], x2 = C[2] - sm.P[2][s];
@@ -1844,14 +1847,14 @@ __device__ __forceinline__ bool sig_pos(const SpreadSmem<T, BZ> &sm, int s, cons
     }
     return nl_later_closer(g, p, kglob, ci, cj, ck, status);
 }
-template <typename T, int BZ>
-__device__ __forceinline__ T node_d2(const SpreadSmem<T, BZ> &sm, int s, const T C[3]) {
+template <typename T, typename SMT>
+__device__ __forceinline__ T node_d2(const SMT &sm, int s, const T C[3]) {
     const T x0 = C[0] - sm.P[0][s], x1 = C[1] - sm.P[1][s], x2 = C[2] - sm.P[2][s];
     return x0 * x0 + x1 * x1 + x2 * x2;
 }
 // clamped foot parameter and squared distance of C to staged segment ss
-template <typename T, int BZ>
-__device__ __forceinline__ void seg_foot(const SpreadSmem<T, BZ> &sm, int ss, const T C[3], T &s, T &r2) {
+template <typename T, typename SMT>
+__device__ __forceinline__ void seg_foot(const SMT &sm, int ss, const T C[3], T &s, T &r2) {
     const T x0 = C[0] - sm.P[0][ss], x1 = C[1] - sm.P[1][ss], x2 = C[2] - sm.P[2][ss];
     const T d0 = sm.D[0][ss], d1 = sm.D[1][ss], d2 = sm.D[2][ss];
     s = (x0 * d0 + x1 * d1 + x2 * d2) * sm.Il2[ss];
@@ -1861,8 +1864,8 @@ __device__ __forceinline__ void seg_foot(const SpreadSmem<T, BZ> &sm, int ss, co
 }
 
 // seg_foot also returning the unclamped foot parameter
-template <typename T, int BZ>
-__device__ __forceinline__ void seg_foot_raw(const SpreadSmem<T, BZ> &sm, int ss, const T C[3], T &sraw, T &s, T &r2) {
+template <typename T, typename SMT>
+__device__ __forceinline__ void seg_foot_raw(const SMT &sm, int ss, const T C[3], T &sraw, T &s, T &r2) {
     const T x0 = C[0] - sm.P[0][ss], x1 = C[1] - sm.P[1][ss], x2 = C[2] - sm.P[2][ss];
     const T d0 = sm.D[0][ss], d1 = sm.D[1][ss], d2 = sm.D[2][ss];
     sraw = (x0 * d0 + x1 * d1 + x2 * d2) * sm.Il2[ss];
@@ -1876,10 +1879,18 @@ __device__ __forceinline__ void seg_foot_raw(const SpreadSmem<T, BZ> &sm, int ss
 // by the thread that owns its column (no atomics), with the deposits of the
 // zero-weight nodes inside the brick.  WP = true: the nodal weights w_k
 // (Sec. 3.2.4), each (cell, line) pair once, added as fixed-point integers.
-template <typename T, bool WP, int BZ>
+// subtract a source from a cell's accumulator: as a fixed-point integer
+// (FX) or in the field precision
+template <bool FX, typename A, typename T>
+__device__ __forceinline__ void acc_sub(A &acc, T v, int fsh) {
+    if constexpr (FX) acc -= to_fixed_s(v, fsh);
+    else acc -= v;
+}
+
+template <typename T, bool WP, int BZ, bool FX>
 __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
-                        const int br, SpreadSmem<T, BZ> &sm) {
-    using SM = SpreadSmem<T, BZ>;
+                        const int br, SpreadSmem<T, BZ, FX> &sm) {
+    using SM = SpreadSmem<T, BZ, FX>;
     const long long np = b.n_points;
     const int nbxy = g.nbx * g.nby;
     const int bzi = br / nbxy, rem = br - bzi * nbxy;
@@ -1892,7 +1903,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     const int nxb = min(BX, g.nx - B0), nyb = min(BY, g.ny - B1);
     int nsupp = 0;                                   // (cell, line) pairs within 3 eps
     if (!WP)
-        for (int i = threadIdx.x; i < BZ * 3 * BX * BY; i += SPREAD_THREADS) (&sm.u.s.acc[0][0][0])[i] = 0ll;
+        for (int i = threadIdx.x; i < BZ * 3 * BX * BY; i += SPREAD_THREADS) (&sm.u.s.acc[0][0][0])[i] = (typename SM::AccT)0;
     const int fsh = WP ? 0 : spread_shift(*sc.smax, (long long)b.n_points + b.n_lines);
     // replay: the certified lines' pairs of this brick as the segment pass
     // recorded them (complete when they fitted the brick's region), added in
@@ -1901,6 +1912,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     // when a node has w_k = 0 (its deposit goes with the gathered lines).
     bool replay = false;
     const int nrec_b = (!WP && g.rmode) ? sc.rcnt[br] : 0;
+    if constexpr (FX)
     if (!WP && g.rmode && *sc.anyZero == 0 && sc.rplan[0] == g.bz) {
         const int nrec = nrec_b;
         if (nrec <= sc.rcap[br]) {
@@ -2216,7 +2228,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                         bool in = false;
                         int js = 0;
                         T s = (T)0, r2 = (T)0;
-                        if (!WP && b.proj_mode && n >= 2 && tx <= ix1 && ty >= iy0 && ty <= iy1 &&
+                        if (FX && !WP && b.proj_mode && n >= 2 && tx <= ix1 && ty >= iy0 && ty <= iy1 &&
                             dx * dx + dy * dy <= rh2) {
                             // integrated projection: every candidate segment within 3 eps
                             // adds its integrated kernel, with the segment pass's values
@@ -2243,7 +2255,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                                     for (int a = 0; a < 3; ++a) { fa3[a] = sc.fhat[a * np + ka]; fb3[a] = sc.fhat[a * np + ka + 1]; }
                                 }
                                 for (int a = 0; a < 3; ++a)
-                                    sm.u.s.acc[z][a][c] -= to_fixed_s(pair_src(wa, wb, fa3[a], fb3[a]), fsh);
+                                    acc_sub<FX>(sm.u.s.acc[z][a][c], pair_src(wa, wb, fa3[a], fb3[a]), fsh);
                             }
                         } else if (tx <= ix1 && ty >= iy0 && ty <= iy1 && dx * dx + dy * dy <= rh2) {
                             const int gxc = B0 + tx, gyc = B1 + ty;
@@ -2332,7 +2344,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                                 // pass's for certified lines under segment weights,
                                 // this pass's own otherwise
                                 T wa, wb;
-                                if (sm.e_canon[e]) {
+                                if (FX && sm.e_canon[e]) {
                                     const int cgl[3] = {B0 + tx, B1 + ty, gz};
                                     T s2, r22;
                                     pair_sr(sc, np, first + js, (n == 1) ? first + js : first + js + 1, cgl, s2, r22);
@@ -2341,9 +2353,9 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                                     pair_w(e0v * q, s, wa, wb);
                                 }
                                 const int c = ty * BX + tx;
-                                sm.u.s.acc[z][0][c] -= to_fixed_s(pair_src(wa, wb, fa0, fb0), fsh);
-                                sm.u.s.acc[z][1][c] -= to_fixed_s(pair_src(wa, wb, fa1, fb1), fsh);
-                                sm.u.s.acc[z][2][c] -= to_fixed_s(pair_src(wa, wb, fa2, fb2), fsh);
+                                acc_sub<FX>(sm.u.s.acc[z][0][c], pair_src(wa, wb, fa0, fb0), fsh);
+                                acc_sub<FX>(sm.u.s.acc[z][1][c], pair_src(wa, wb, fa1, fb1), fsh);
+                                acc_sub<FX>(sm.u.s.acc[z][2][c], pair_src(wa, wb, fa2, fb2), fsh);
                             }
                         } else {
                             // omega eta / eta0 into the two nodes of the closest segment, as
@@ -2426,7 +2438,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                         bal &= bal - 1;
                         if (lane == src)
                             for (int a = 0; a < 3; ++a)
-                                sm.u.s.acc[c3[2]][a][c3[1] * BX + c3[0]] -= to_fixed_s(p.F[a][k] / (T)g.V, fsh);
+                                acc_sub<FX>(sm.u.s.acc[c3[2]][a][c3[1] * BX + c3[0]], p.F[a][k] / (T)g.V, fsh);
                         __syncwarp();
                     }
                 }
@@ -2460,9 +2472,15 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
             for (int z = 0; z < nzb; ++z) {
                 const long long idx = col + layer * z;
                 T v0, v1, v2;
-                from_fixed(sm.u.s.acc[z][0][threadIdx.x], fsh, v0);
-                from_fixed(sm.u.s.acc[z][1][threadIdx.x], fsh, v1);
-                from_fixed(sm.u.s.acc[z][2][threadIdx.x], fsh, v2);
+                if constexpr (FX) {
+                    from_fixed(sm.u.s.acc[z][0][threadIdx.x], fsh, v0);
+                    from_fixed(sm.u.s.acc[z][1][threadIdx.x], fsh, v1);
+                    from_fixed(sm.u.s.acc[z][2][threadIdx.x], fsh, v2);
+                } else {
+                    v0 = sm.u.s.acc[z][0][threadIdx.x];
+                    v1 = sm.u.s.acc[z][1][threadIdx.x];
+                    v2 = sm.u.s.acc[z][2][threadIdx.x];
+                }
                 p.S[0][idx] = v0; p.S[1][idx] = v1; p.S[2][idx] = v2;
                 cs0 += v0; cs1 += v1; cs2 += v2;
             }
@@ -2598,19 +2616,19 @@ __global__ void __launch_bounds__(256) k_normalise(GridC g, BeamsC b, Scratch<T>
     m = __reduce_max_sync(0xffffffffu, m);
     if ((threadIdx.x & 31) == 0 && m) atomicMax(sc.smax, m);
 }
-template <typename T, int BZ>
+template <typename T, int BZ, bool FX>
 __global__ void __launch_bounds__(SPREAD_THREADS) k_spread(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
                                                            int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SpreadSmem<T, BZ> &sm = *reinterpret_cast<SpreadSmem<T, BZ> *>(smem_raw);
-    d_brick<T, false, BZ>(g, b, sc, p, status, (int)blockIdx.x, sm);
+    SpreadSmem<T, BZ, FX> &sm = *reinterpret_cast<SpreadSmem<T, BZ, FX> *>(smem_raw);
+    d_brick<T, false, BZ, FX>(g, b, sc, p, status, (int)blockIdx.x, sm);
 }
 template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) k_bweights(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
                                                              int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SpreadSmem<T, BZ> &sm = *reinterpret_cast<SpreadSmem<T, BZ> *>(smem_raw);
-    d_brick<T, true, BZ>(g, b, sc, p, status, (int)blockIdx.x, sm);
+    SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
+    d_brick<T, true, BZ, false>(g, b, sc, p, status, (int)blockIdx.x, sm);
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_totals(GridC g, BeamsC b, Scratch<T> sc, double *totals) {
@@ -2719,12 +2737,18 @@ __global__ void __launch_bounds__(256) kb_normalise(const Inst<T> *I, const int 
 template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) kb_spread(const Inst<T> *I, const int *sel, const long long *pre, int n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SpreadSmem<T, BZ> &sm = *reinterpret_cast<SpreadSmem<T, BZ> *>(smem_raw);
+    // each instance in the accumulation form it has alone (the shared memory
+    // is sized for the larger, fixed-point form)
     const long long total = pre[n];
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
         const int q = owner(pre, n, item);
         const Inst<T> &x = I[AL_SEL(q)];
-        d_brick<T, false, BZ>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]), sm);
+        if (x.g.fx)
+            d_brick<T, false, BZ, true>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]),
+                                        *reinterpret_cast<SpreadSmem<T, BZ, true> *>(smem_raw));
+        else
+            d_brick<T, false, BZ, false>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]),
+                                         *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw));
         __syncthreads();
     }
 }
@@ -2732,12 +2756,12 @@ template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) kb_bweights(const Inst<T> *I, const int *sel, const long long *pre,
                                                               int n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SpreadSmem<T, BZ> &sm = *reinterpret_cast<SpreadSmem<T, BZ> *>(smem_raw);
+    SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
     const long long total = pre[n];
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
         const int q = owner(pre, n, item);
         const Inst<T> &x = I[AL_SEL(q)];
-        d_brick<T, true, BZ>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]), sm);
+        d_brick<T, true, BZ, false>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]), sm);
         __syncthreads();
     }
 }

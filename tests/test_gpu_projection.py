@@ -35,7 +35,7 @@ def _steps(wl, n, record):
     import torch
     from paper_2609_39443_b300.al import Instance
     inst = Instance(wl)
-    inst.grid.set_option(OPT_RECORD, int(record))
+    inst.grid.set_option(OPT_RECORD, 1 if record else 2)
     out = []
     for _ in range(n):
         inst.status.zero_()

@@ -24,13 +24,15 @@ def _outs(inst, npts):
 
 
 def _run(wl, steps, record, moves=None, bz=None):
-    """`steps` steps with the segment weights pass; moves[k] (optional) are
-    the positions of step k.  Returns the outputs of every step."""
+    """`steps` steps with the segment weights pass, recording and replaying
+    pairs (record True) or gathering them in the same fixed point (False);
+    moves[k] (optional) are the positions of step k.  Returns the outputs
+    of every step."""
     import torch
     from paper_2609_39443_b300.al import OPT_BRICK_Z, Instance
     inst = Instance(wl)
     inst.grid.set_option(OPT_WEIGHTS, WEIGHTS_SEGMENT)
-    inst.grid.set_option(OPT_RECORD, int(record))
+    inst.grid.set_option(OPT_RECORD, 1 if record else 2)
     if bz:
         inst.grid.set_option(OPT_BRICK_Z, bz)
     out = []
@@ -111,7 +113,7 @@ def test_batch_replay_equals_alone():
     for x in alone + inb:
         x.grid.set_option(OPT_WEIGHTS, WEIGHTS_SEGMENT)
     for x in alone:
-        x.grid.set_option(OPT_RECORD, 0)              # alone recomputes every pair
+        x.grid.set_option(OPT_RECORD, 2)              # alone recomputes every pair
     batch = Batch(inb, use_graph=True)
     for _ in range(3):
         for a in alone:
