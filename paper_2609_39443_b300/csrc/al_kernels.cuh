@@ -1322,7 +1322,7 @@ __device__ __noinline__ bool w_later_closer(const GridC &g, const Scratch<T> &sc
 
 // membership of the cell at C (relative to c.O) in segment c.k's share, and
 // what it feeds
-template <typename T, bool SC>
+template <typename T, bool SC, bool INTEG>
 __device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const GridC &g,
                                        const Scratch<T> &sc, const StepPtrs<T> &p, bool regular,
                                        int *status, WSink<T, SC> &sink) {
@@ -1366,7 +1366,7 @@ __device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const Gri
     if (!in) return;
     const int cg[3] = {AL_CG(0), AL_CG(1), AL_CG(2)};
 #undef AL_CG
-    if (c.integ) {                                          // the segment's integrated kernel
+    if constexpr (INTEG) {                                  // the segment's integrated kernel
         T a, b;
         pair_int(sc, (long long)p.np, c.k, cg, c.epsc, c.eta0, c.ie2, a, b);
         sink.add_w(g, p, cg, a, b);
@@ -1396,7 +1396,7 @@ __device__ __forceinline__ double warp_total(const Acc<double> &a) {
 
 // the cells of segment c.k's slab, columns along the two axes other than
 // the march axis AX (compile-time, so coordinates stay in registers)
-template <typename T, int AX, bool SC>
+template <typename T, int AX, bool SC, bool INTEG>
 __device__ __forceinline__ void w_columns(const WSeg<T> &c, const GridC &g, const Scratch<T> &sc,
                                           const StepPtrs<T> &p, int *status, const int lane,
                                           WSink<T, SC> &sink) {
@@ -1445,7 +1445,7 @@ __device__ __forceinline__ void w_columns(const WSeg<T> &c, const GridC &g, cons
         const T z1 = tmin(ffloor_f(chi - (T)0.5) + (T)0.5, chi0);
         for (T z = z0; z <= z1; z += (T)1) {
             C[AX] = z;
-            w_cell<T, SC>(c, C, g, sc, p, true, status, sink);
+            w_cell<T, SC, INTEG>(c, C, g, sc, p, true, status, sink);
         }
         }
     next_column:
@@ -1564,9 +1564,19 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
         int ax = 0;
         if (tabs(c.D[1]) > tabs(c.D[ax])) ax = 1;
         if (tabs(c.D[2]) > tabs(c.D[ax])) ax = 2;
-        if (ax == 0) w_columns<T, 0, SC>(c, g, sc, p, status, lane, sink);
-        else if (ax == 1) w_columns<T, 1, SC>(c, g, sc, p, status, lane, sink);
-        else w_columns<T, 2, SC>(c, g, sc, p, status, lane, sink);
+        // the integrated projection's cell loop is a separate instantiation, so
+        // the nearest-segment loop carries no call to its kernel
+        if (c.integ) {
+            if constexpr (!SC) {
+                if (ax == 0) w_columns<T, 0, SC, true>(c, g, sc, p, status, lane, sink);
+                else if (ax == 1) w_columns<T, 1, SC, true>(c, g, sc, p, status, lane, sink);
+                else w_columns<T, 2, SC, true>(c, g, sc, p, status, lane, sink);
+            }
+        } else {
+            if (ax == 0) w_columns<T, 0, SC, false>(c, g, sc, p, status, lane, sink);
+            else if (ax == 1) w_columns<T, 1, SC, false>(c, g, sc, p, status, lane, sink);
+            else w_columns<T, 2, SC, false>(c, g, sc, p, status, lane, sink);
+        }
     }
     w_finish(g, sc, status, k, lane, sink);
 }
@@ -2595,7 +2605,7 @@ __global__ void __launch_bounds__(256) k_mask(GridC g, BeamsC b, Scratch<T> sc) 
     if (k < b.n_points) d_mask(g, b, sc, k);
 }
 template <typename T>
-__global__ void __launch_bounds__(128) k_weights(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
+__global__ void __launch_bounds__(128, 4) k_weights(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
     __shared__ RecStage<T> st;
     const bool stage = g.rmode != 0;
     if (stage) rec_init(st);
@@ -2697,7 +2707,7 @@ __global__ void __launch_bounds__(256) kb_mask(const Inst<T> *I, const int *sel,
     }
 }
 template <typename T>
-__global__ void __launch_bounds__(128) kb_weights(const Inst<T> *I, const int *sel, const long long *pre, int n) {
+__global__ void __launch_bounds__(128, 4) kb_weights(const Inst<T> *I, const int *sel, const long long *pre, int n) {
     __shared__ RecStage<T> st;
     rec_init(st);
     const long long total = pre[n];
