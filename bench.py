@@ -93,14 +93,14 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(workload_name):
-    """dram bytes per k_spread launch from a committed ncu summary, if it was
-    taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "spread_traffic.json")
+def _traffic(workload_name, kernel="k_spread"):
+    """dram bytes per launch of a kernel from a committed ncu summary, if it
+    was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    e = d.get(workload_name)
+    e = d.get(f"{workload_name}/{kernel}")
     if not e or e.get("kernel_hash") != _kernel_hash():
         return None
     return e.get("dram_bytes_per_launch")
@@ -373,7 +373,8 @@ def run_ours(a):
         a_t = flop / weights_s / 1e12
         roofline = {"bound": "alu", "kernel": "k_weights", "achieved": a_t, "peak": ALU_PEAK_TFLOPS,
                     "peak_kind": "derived (148 SMs x 128 FP32 lanes x FMA x 2.032 GHz)", "unit": "TFLOP/s",
-                    "frac": a_t / ALU_PEAK_TFLOPS, "algorithmic_flop": flop, "traffic": None,
+                    "frac": a_t / ALU_PEAK_TFLOPS, "algorithmic_flop": flop,
+                    "traffic": _traffic(wl.name, "k_weights"),
                     "k_spread": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                  "frac": achieved / peak, "algorithmic_bytes": alg}}
     else:
