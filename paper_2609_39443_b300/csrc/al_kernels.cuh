@@ -1403,6 +1403,7 @@ __device__ __forceinline__ void w_columns(const WSeg<T> &c, const GridC &g, cons
     constexpr int PA = (AX + 1) % 3, PB = (AX + 2) % 3;
     const int na = c.hi[PA] - c.lo[PA] + 1, nbb = c.hi[PB] - c.lo[PB] + 1;
     const int ncol = na * nbb;
+    if (lane >= ncol) return;
     // this lane's first column; later columns by stepping 32 (float
     // coordinates advance with exact additions, no conversions in the loop)
     int ia = lane % na, ib = lane / na;                       // offsets from lo
@@ -1416,68 +1417,41 @@ __device__ __forceinline__ void w_columns(const WSeg<T> &c, const GridC &g, cons
     const T ua = c.D[PA], ub = c.D[PB];
     const T uu = ua * ua + ub * ub, iuu = uu > (T)0 ? (T)1 / uu : (T)0;
     const T lim = c.R2 + c.gr;
-    // rounds of 32 columns, one per lane: each lane finds its column's
-    // interval of cells, then the round's cells are dealt evenly to the lanes
-    // (lanes never idle while another marches a long column)
-    (void)fa; (void)fb; (void)fna;
-    for (int c0 = 0; c0 < ncol; c0 += 32) {
-        const int col = c0 + lane;
-        int nzc = 0;
-        T za = (T)0, fa_l = (T)0, fb_l = (T)0;
-        if (col < ncol) {
-            const int ia_l = col % na, ib_l = col / na;
-            fa_l = (T)(c.lo[PA] + ia_l - c.O[PA]) + (T)0.5;
-            fb_l = (T)(c.lo[PB] + ib_l - c.O[PB]) + (T)0.5;
-            const T qa = fa_l - c.A[PA], qb = fb_l - c.A[PB];
+    for (int col = lane; col < ncol; col += 32) {
+        T C[3];
+        C[PA] = fa;
+        C[PB] = fb;
+        {
+            const T qa = fa - c.A[PA], qb = fb - c.A[PB];
             T t = (qa * ua + qb * ub) * iuu;
             t = t < (T)0 ? (T)0 : (t > (T)1 ? (T)1 : t);
             const T ea = qa - t * ua, eb = qb - t * ub;
-            if (ea * ea + eb * eb <= lim) {
-                // march-axis interval between the two planes (pruning only; the
-                // membership test decides)
-                T clo = clo0, chi = chi0;
-                if (p0) {
-                    T r = c.A[AX] - ((fa_l - c.A[PA]) * c.m0[PA] + (fb_l - c.A[PB]) * c.m0[PB]) * i0;
-                    if (c.m0[AX] > (T)0) clo = tmax(clo, r - (T)0.05); else chi = tmin(chi, r + (T)0.05);
-                }
-                if (p1) {
-                    T r = c.Bn[AX] - ((fa_l - c.Bn[PA]) * c.m1[PA] + (fb_l - c.Bn[PB]) * c.m1[PB]) * i1;
-                    if (c.m1[AX] > (T)0) chi = tmin(chi, r + (T)0.05); else clo = tmax(clo, r - (T)0.05);
-                }
-                // cell centres k + 1/2 inside [clo, chi] and inside the box
-                const T z0 = tmax(fceil_f(clo - (T)0.5) + (T)0.5, clo0);
-                const T z1 = tmin(ffloor_f(chi - (T)0.5) + (T)0.5, chi0);
-                if (z1 >= z0) { za = z0; nzc = (int)(z1 - z0) + 1; }
-            }
+            if (ea * ea + eb * eb > lim) goto next_column;
         }
-        // inclusive prefix of the cell counts over the lanes
-        int incl = nzc;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
+        {
+        // march-axis interval between the two planes (pruning only; the
+        // membership test decides)
+        T clo = clo0, chi = chi0;
+        if (p0) {
+            T r = c.A[AX] - ((C[PA] - c.A[PA]) * c.m0[PA] + (C[PB] - c.A[PB]) * c.m0[PB]) * i0;
+            if (c.m0[AX] > (T)0) clo = tmax(clo, r - (T)0.05); else chi = tmin(chi, r + (T)0.05);
         }
-        const int excl = incl - nzc;
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        for (int t0 = 0; t0 < total; t0 += 32) {
-            const int tc = t0 + lane;
-            // the lane whose column holds cell tc: the last lane with excl <= tc
-            int lo_l = 0;
-            for (int step = 16; step >= 1; step >>= 1) {
-                const int probe = lo_l + step;
-                const int ev = __shfl_sync(0xffffffffu, excl, probe & 31);
-                if (probe < 32 && ev <= tc) lo_l = probe;
-            }
-            const T fa_c = __shfl_sync(0xffffffffu, fa_l, lo_l), fb_c = __shfl_sync(0xffffffffu, fb_l, lo_l);
-            const T za_c = __shfl_sync(0xffffffffu, za, lo_l);
-            const int ex_c = __shfl_sync(0xffffffffu, excl, lo_l);
-            if (tc < total) {
-                T C[3];
-                C[PA] = fa_c;
-                C[PB] = fb_c;
-                C[AX] = za_c + (T)(tc - ex_c);
-                w_cell<T, SC, INTEG>(c, C, g, sc, p, true, status, sink);
-            }
+        if (p1) {
+            T r = c.Bn[AX] - ((C[PA] - c.Bn[PA]) * c.m1[PA] + (C[PB] - c.Bn[PB]) * c.m1[PB]) * i1;
+            if (c.m1[AX] > (T)0) chi = tmin(chi, r + (T)0.05); else clo = tmax(clo, r - (T)0.05);
         }
+        // cell centres k + 1/2 inside [clo, chi] and inside the box
+        const T z0 = tmax(fceil_f(clo - (T)0.5) + (T)0.5, clo0);
+        const T z1 = tmin(ffloor_f(chi - (T)0.5) + (T)0.5, chi0);
+        for (T z = z0; z <= z1; z += (T)1) {
+            C[AX] = z;
+            w_cell<T, SC, INTEG>(c, C, g, sc, p, true, status, sink);
+        }
+        }
+    next_column:
+        ia += 32;
+        fa += (T)32;
+        while (ia >= na) { ia -= na; fa -= fna; ++ib; fb += (T)1; }
     }
 }
 
