@@ -62,6 +62,7 @@ def _load():
         lib.or_count_support.restype = C.c_longlong
         lib.or_closest_segment.argtypes = [dp, C.c_int, dp, C.POINTER(C.c_int), dp]
         lib.or_seg_kernel.argtypes = [dp, dp, dp, C.c_double, dp]
+        lib.or_beam_quasistatic.argtypes = [C.POINTER(_Beams), dp, dp, dp, dp, dp]
         lib.or_closest_segment.restype = C.c_double
         _lib = lib
     return _lib
@@ -113,6 +114,19 @@ def seg_kernel(c, A, B, eps):
     c, A, B = (_f64(np.asarray(v)) for v in (c, A, B))
     _load().or_seg_kernel(_ptr(c), _ptr(A), _ptr(B), float(eps), _ptr(K))
     return K
+
+
+def beam_quasistatic(beams, EI, axis, P0, F):
+    """Quasi-static reconstruction: every node's load as a static point load
+    on a linear Euler-Bernoulli cantilever along `axis` (rest positions P0,
+    root at each line's first node); returns the displaced positions."""
+    EI = _f64(np.broadcast_to(np.asarray(EI, float), (beams.n_lines,)).copy())
+    ax = _f64(np.asarray(axis, float))
+    P0, Ff = _f64(P0), _f64(F)
+    out = np.zeros_like(P0)
+    bh = _BeamsHold(beams)
+    _load().or_beam_quasistatic(C.byref(bh.s), _ptr(EI), _ptr(ax), _ptr(P0), _ptr(Ff), _ptr(out))
+    return out
 
 
 def point_step(grid, beams, step, f_prev=None):

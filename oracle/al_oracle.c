@@ -606,3 +606,47 @@ long long or_count_support(const or_grid *g, const or_beams *b, const double *Ps
     }
     return total;
 }
+
+/* ------------------------------------------------------------------ */
+/* Quasi-static reconstruction (Sec. 7, the E5 test): each CV's load    */
+/* as a static point load on a linear Euler-Bernoulli cantilever        */
+/* ------------------------------------------------------------------ */
+
+/* Deflection at x of a cantilever clamped at 0 under a unit point load at
+ * a (both measured from the root along the axis), times EI:
+ *   x <= a: x^2 (3a - x) / 6,   x >= a: a^2 (3x - a) / 6. */
+static double or_cantilever_g(double x, double a)
+{
+    return x <= a ? x * x * (3.0 * a - x) / 6.0 : a * a * (3.0 * x - a) / 6.0;
+}
+
+/* For every line: the rest positions P0 define the straight axis (unit
+ * vector `axis`, root at the line's first node) and each node's station
+ * a_k = (P0_k - P0_root) . axis; the loads F_k (3 x np) act at the nodes;
+ * only their parts normal to the axis bend the beam.  Writes
+ * P_out_i = P0_i + sum_k F_perp_k g(a_i, a_k) / EI_l. */
+void or_beam_quasistatic(const or_beams *b, const double *EI, const double *axis, const double *P0,
+                         const double *F, double *P_out)
+{
+    const long long np = b->line_off[b->n_lines];
+    for (int l = 0; l < b->n_lines; ++l) {
+        const int off = b->line_off[l], n = b->line_off[l + 1] - off;
+        for (int q = 0; q < n; ++q) {
+            const long long i = off + q;
+            double xi = 0.0;
+            for (int a = 0; a < 3; ++a) xi += (P0[a * np + i] - P0[a * np + off]) * axis[a];
+            double w[3] = {0.0, 0.0, 0.0};
+            for (int r = 0; r < n; ++r) {
+                const long long k = off + r;
+                double ak = 0.0, fa = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    ak += (P0[a * np + k] - P0[a * np + off]) * axis[a];
+                    fa += F[a * np + k] * axis[a];
+                }
+                const double gk = or_cantilever_g(xi, ak);
+                for (int a = 0; a < 3; ++a) w[a] += (F[a * np + k] - fa * axis[a]) * gk;
+            }
+            for (int a = 0; a < 3; ++a) P_out[a * np + i] = P0[a * np + i] + w[a] / EI[l];
+        }
+    }
+}

@@ -715,3 +715,69 @@ def test_integrated_projection_sends_each_node_share_to_its_end():
     z = (np.arange(g.n_cells) // (g.nx * g.ny) + 0.5) * g.h
     zc = (np.abs(S) * z).sum() / np.abs(S).sum()
     assert abs(zc - (0.12 + 0.30 / 3)) < 0.005, zc
+
+
+# ----------------------------------------------------------------------------
+# quasi-static reconstruction: point loads on a linear Euler-Bernoulli
+# cantilever (the structural check of Sec. 7)
+# ----------------------------------------------------------------------------
+
+def _stem(n, L=1.0, axis=(0.0, 0.0, 1.0), root=(0.2, -0.1, 0.3), n_lines=1):
+    ax = np.asarray(axis, float) / np.linalg.norm(axis)
+    s = np.linspace(0.0, L, n)
+    P0 = np.concatenate([np.asarray(root)[:, None] + s[None] * ax[:, None]] * n_lines, axis=1)
+    b = BeamSpec(line_off=np.arange(n_lines + 1, dtype=np.int32) * n, d=np.ones(n_lines), cdn=np.ones(n_lines),
+                 cdt=np.ones(n_lines), eps=np.ones(n_lines), ell_s=np.ones(n_lines), alpha_f=np.ones(n_lines),
+                 cv_len=np.full(n * n_lines, L / (n - 1)))
+    return b, P0, ax, s
+
+
+def test_cantilever_tip_load_curve():
+    """w(x) = P x^2 (3L - x) / (6 EI) under a tip load P."""
+    b, P0, ax, s = _stem(41, L=0.8)
+    F = np.zeros_like(P0)
+    F[0, -1], F[1, -1] = 0.3, -0.2
+    EI = 0.0259
+    dP = oracle.beam_quasistatic(b, EI, ax, P0, F) - P0
+    w = s ** 2 * (3 * 0.8 - s) / (6 * EI)
+    np.testing.assert_allclose(dP[0], 0.3 * w, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(dP[1], -0.2 * w, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(dP[2], 0.0, atol=1e-15)
+
+
+def test_cantilever_uniform_load_converges_to_closed_form():
+    """Nodal point loads q L / (n - 1) (halved at the ends) tend to the
+    distributed load q: tip deflection q L^4 / (8 EI)."""
+    for n, tol in ((101, 2e-4), (401, 2e-5)):
+        b, P0, ax, s = _stem(n, L=0.4)
+        q, EI = 0.758, 0.02591
+        F = np.zeros_like(P0)
+        F[1] = q * 0.4 / (n - 1)
+        F[1, 0] *= 0.5
+        F[1, -1] *= 0.5
+        tip = (oracle.beam_quasistatic(b, EI, ax, P0, F) - P0)[1, -1]
+        assert abs(tip / (q * 0.4 ** 4 / (8 * EI)) - 1) < tol
+
+
+def test_cantilever_axial_loads_reciprocity_and_rotation():
+    rng = np.random.default_rng(31)
+    b, P0, ax, s = _stem(17, L=0.5)
+    EI = 0.7
+    # loads along the axis bend nothing
+    F = np.outer(ax, rng.normal(size=17))
+    np.testing.assert_allclose(oracle.beam_quasistatic(b, EI, ax, P0, F), P0, atol=1e-15)
+    # Maxwell-Betti: the deflection at i under a unit load at k equals that at k under a unit load at i
+    for i, k in ((3, 11), (16, 5), (8, 8)):
+        Fi, Fk = np.zeros_like(P0), np.zeros_like(P0)
+        Fi[0, i], Fk[0, k] = 1.0, 1.0
+        d_k = (oracle.beam_quasistatic(b, EI, ax, P0, Fi) - P0)[0, k]
+        d_i = (oracle.beam_quasistatic(b, EI, ax, P0, Fk) - P0)[0, i]
+        assert d_k == pytest.approx(d_i, rel=1e-13)
+    # rotating stem and loads together rotates the deflection
+    th = 0.7
+    Rm = np.array([[np.cos(th), 0, np.sin(th)], [0, 1, 0], [-np.sin(th), 0, np.cos(th)]])
+    F = rng.normal(size=(3, 17))
+    d0 = oracle.beam_quasistatic(b, EI, ax, P0, F) - P0
+    b2, P2, ax2, _ = _stem(17, L=0.5, axis=Rm @ ax, root=Rm @ np.array([0.2, -0.1, 0.3]))
+    d2 = oracle.beam_quasistatic(b2, EI, ax2, P2, Rm @ F) - P2
+    np.testing.assert_allclose(d2, Rm @ d0, rtol=1e-12, atol=1e-14)
