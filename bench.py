@@ -307,6 +307,20 @@ def run_ours(a):
     ph = phases / a.steps
     spread_s = ph[PHASES.index("spread")] / 1e3
 
+    # ---- the quasi-static beam reconstruction on this step's forces ---------
+    beam_ms = None
+    if a.workload in ("canopy", "flume"):
+        P_out = torch.empty_like(inst.P)
+        EI = np.full(wl.beams.n_lines, 5e-3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        inst.grid.beam_quasistatic(EI, (0.0, 0.0, 1.0), inst.P, inst.F, P_out)
+        e0.record(stream)
+        for _ in range(10):
+            inst.grid.beam_quasistatic(EI, (0.0, 0.0, 1.0), inst.P, inst.F, P_out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        beam_ms = e0.elapsed_time(e1) / 10
+
     # ---- end to end through the public API with host buffers -----------------
     e2e = None
     if not a.no_e2e:
@@ -399,6 +413,7 @@ def run_ours(a):
                 "phases_ms": {k: float(v) for k, v in zip(PHASES, ph)},
                 "roofline": roofline,
                 "projection_variants": variants,
+                "beam_quasistatic_ms": beam_ms,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": (KERNELS_PER_STEP + (tuned["weights"] == "segment")) * a.steps}
         print(json.dumps(line), flush=True)

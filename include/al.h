@@ -260,6 +260,25 @@ int al_autotune(al_grid g, const al_step_in *in, const al_step_out *out, int tri
 /* Sizes of an instance: cells and points. */
 int al_sizes(al_grid g, long long *n_cells, long long *n_points, int *n_lines);
 
+/* Quasi-static reconstruction of the beam side (the structural check of the
+ * wave-flume case, Sec. 7): each node's load F_k (per-CV line force, e.g.
+ * the F of the last al_sample_drag_spread) acts as a static point load on a
+ * linear Euler-Bernoulli cantilever per line, clamped at the line's first
+ * node and straight along the unit vector `axis` in its rest positions P0.
+ * With stations a_k = (P0_k - P0_root).axis and only the load normal to the
+ * axis bending the beam,
+ *   P_out_i = P0_i + sum_k F_perp,k g(a_i, a_k) / EI_l,
+ *   g(x, a) = x^2 (3a - x) / 6 (x <= a),  a^2 (3x - a) / 6 (x >= a).
+ * Feeding P_out back as the next step's positions closes a coupled step on
+ * the GPU (quasi-static structure, no beam dynamics).
+ * P0, F, P_out: DEVICE SoA in the grid's precision, n_points each (P_out may
+ * not alias P0 or F).  EI: HOST [n_lines] bending stiffness (N m^2), > 0,
+ * copied to the grid's device buffer.  axis: host, unit length.
+ * Stream-ordered on `stream`; AL_ERR_ARG for a bad argument, AL_ERR_STATE
+ * before al_load_beams. */
+int al_beam_quasistatic(al_grid g, const double *EI, const double axis[3], const void *const P0[3],
+                        const void *const F[3], void *const P_out[3], void *stream);
+
 /* ---- batched form ------------------------------------------------------ */
 /* Many independent instances advanced together: every phase of the step is
  * one launch over the work items of all instances (points, lines, bricks),

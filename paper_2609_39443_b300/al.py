@@ -78,6 +78,8 @@ def lib():
         L.al_get_state.argtypes = [_vp, _vp, C.POINTER(C.c_int), _vp]
         L.al_set_state.argtypes = [_vp, _vp, C.c_int, _vp]
         L.al_sizes.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
+        L.al_beam_quasistatic.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp * 3, _vp * 3,
+                                          _vp * 3, _vp]
         L.al_batch_create.argtypes = [C.POINTER(_vp)]
         L.al_batch_add.argtypes = [_vp, _vp, C.POINTER(StepIn), C.POINTER(StepOut)]
         L.al_batch_commit.argtypes = [_vp, C.c_int, C.c_int]
@@ -224,6 +226,16 @@ class Grid:
         """al_set_option: execution choices that leave results within the
         parity tolerances (e.g. OPT_WEIGHTS = WEIGHTS_BRICK | WEIGHTS_SEGMENT)."""
         check(lib().al_set_option(self.h, int(option), int(value)), "al_set_option")
+
+    def beam_quasistatic(self, EI, axis, P0, F, P_out, stream=None) -> None:
+        """al_beam_quasistatic: each node's load F as a static point load on a
+        linear Euler-Bernoulli cantilever per line (rest positions P0, unit
+        `axis`, bending stiffness EI per line); writes P_out (device tensors)."""
+        ei = np.ascontiguousarray(np.broadcast_to(np.asarray(EI, float), (self.n_lines,)), dtype=np.float64)
+        ax = (C.c_double * 3)(*map(float, axis))
+        rows = [(_vp * 3)(*[_ptr(t) for t in _three(x)]) for x in (P0, F, P_out)]
+        check(lib().al_beam_quasistatic(self.h, ei.ctypes.data_as(C.POINTER(C.c_double)), ax, rows[0], rows[1],
+                                        rows[2], _stream_ptr(stream)), "al_beam_quasistatic")
 
     def trace(self, on: bool = True) -> None:
         check(lib().al_trace_enable(self.h, int(bool(on))), "al_trace_enable")

@@ -62,7 +62,7 @@ struct al_grid_s {
     int n_lines = 0, n_points = 0, mask_words = 0;
     int *d_line_off = nullptr, *d_line_of = nullptr;
     double *d_d = nullptr, *d_cdn = nullptr, *d_cdt = nullptr, *d_eps = nullptr, *d_ell = nullptr,
-           *d_af = nullptr, *d_cvl = nullptr, *d_cmn = nullptr, *d_cmt = nullptr;
+           *d_af = nullptr, *d_cvl = nullptr, *d_cmn = nullptr, *d_cmt = nullptr, *d_EI = nullptr;
     al_beam_desc bd{};
 
     // per-point scratch (element type per precision)
@@ -102,12 +102,13 @@ static void trace_mark(al_grid g, int i, cudaStream_t st) {
 
 static void free_beams(al_grid g) {
     void *ptrs[] = {g->d_line_off, g->d_line_of, g->d_d, g->d_cdn, g->d_cdt, g->d_eps, g->d_ell, g->d_af,
-                    g->d_cvl, g->d_cmn, g->d_cmt, g->fprev, g->uhi, g->segD, g->segIl2, g->nodeM, g->fhat, g->ulo,
+                    g->d_cvl, g->d_cmn, g->d_cmt, g->d_EI, g->fprev, g->uhi, g->segD, g->segIl2, g->nodeM, g->fhat, g->ulo,
                     g->nodeTau, g->segWa, g->segWb, g->w, g->lineF, g->lines, g->mask, g->wfix, g->rec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     g->d_line_off = g->d_line_of = nullptr;
     g->d_d = g->d_cdn = g->d_cdt = g->d_eps = g->d_ell = g->d_af = g->d_cvl = g->d_cmn = g->d_cmt = nullptr;
+    g->d_EI = nullptr;
     g->fprev = g->uhi = g->segD = g->segIl2 = g->nodeM = g->fhat = nullptr;
     g->ulo = g->nodeTau = nullptr;
     g->segWa = g->segWb = g->w = g->lineF = nullptr;
@@ -241,6 +242,7 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     A(&g->d_d, nl); A(&g->d_cdn, nl); A(&g->d_cdt, nl); A(&g->d_eps, nl); A(&g->d_ell, nl); A(&g->d_af, nl);
     A(&g->d_cvl, (size_t)np);
     if (b.cm_n) { A(&g->d_cmn, nl); A(&g->d_cmt, nl); }
+    A(&g->d_EI, nl);
     AB(&g->fprev, n3); AB(&g->uhi, n3); AB(&g->segD, n3); AB(&g->segIl2, (size_t)np); AB(&g->nodeM, n3);
     AB(&g->fhat, n3);
     A(&g->ulo, n3); A(&g->nodeTau, (size_t)np);
@@ -581,6 +583,44 @@ extern "C" int al_set_state(al_grid g, const void *f_prev_dev, int has_prev, voi
     AL_CUDA(cudaMemsetAsync(g->hasPrev, has_prev ? 0x01 : 0, 1, st));
     AL_CUDA(cudaMemsetAsync((char *)g->hasPrev + 1, 0, sizeof(int) - 1, st));
     return AL_OK;
+}
+
+template <typename T>
+static int beam_qs_t(al_grid g, const double *EI, const double axis[3], const void *const P0[3],
+                     const void *const F[3], void *const P_out[3], cudaStream_t st) {
+    using namespace al;
+    StepPtrs<T> p{};
+    for (int a = 0; a < 3; ++a) {
+        p.P[a] = (const T *)P0[a];
+        p.F[a] = (T *)F[a];
+        p.S[a] = (T *)P_out[a];
+    }
+    BeamsC bc{};
+    bc.n_lines = g->n_lines; bc.n_points = g->n_points; bc.line_off = g->d_line_off;
+    AL_CUDA(cudaMemcpyAsync(g->d_EI, EI, (size_t)g->n_lines * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_beam_qs<T><<<(unsigned)((g->n_lines + 7) / 8), 256, 0, st>>>(bc, g->d_EI, (T)axis[0], (T)axis[1],
+                                                                     (T)axis[2], p);
+    AL_CUDA(cudaGetLastError());
+    return AL_OK;
+}
+
+extern "C" int al_beam_quasistatic(al_grid g, const double *EI, const double axis[3], const void *const P0[3],
+                                   const void *const F[3], void *const P_out[3], void *stream) {
+    if (!g || !axis || !P0 || !F || !P_out) return AL_ERR_ARG;
+    if (!g->loaded) return AL_ERR_STATE;
+    if (g->n_lines == 0) return AL_OK;
+    if (!EI) return AL_ERR_ARG;
+    for (int l = 0; l < g->n_lines; ++l)
+        if (!(EI[l] > 0.0) || !std::isfinite(EI[l])) return AL_ERR_ARG;
+    const double an = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
+    if (!(std::fabs(an - 1.0) < 1e-9)) return AL_ERR_ARG;
+    for (int a = 0; a < 3; ++a) {
+        if (!P0[a] || !F[a] || !P_out[a]) return AL_ERR_ARG;
+        if (P_out[a] == P0[a] || P_out[a] == F[a]) return AL_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    return g->d.precision == AL_FP64 ? beam_qs_t<double>(g, EI, axis, P0, F, P_out, st)
+                                     : beam_qs_t<float>(g, EI, axis, P0, F, P_out, st);
 }
 
 extern "C" int al_sizes(al_grid g, long long *n_cells, long long *n_points, int *n_lines) {

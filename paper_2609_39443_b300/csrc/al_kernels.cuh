@@ -2544,6 +2544,45 @@ __device__ void d_totals(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
 
 
 // ---------------------------------------------------------------------------
+// k_beam_qs: quasi-static reconstruction (Sec. 7), one warp per line: node
+// i's displacement is the sum over the line's nodes k of the normal part of
+// F_k times the cantilever's influence g(a_i, a_k) / EI
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T cantilever_g(T x, T a) {
+    return x <= a ? x * x * ((T)3 * a - x) / (T)6 : a * a * ((T)3 * x - a) / (T)6;
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_beam_qs(BeamsC b, const double *EI, T ax0, T ax1, T ax2,
+                                                 StepPtrs<T> p) {
+    // p.P: rest positions P0, p.F: loads, p.S[0..2]: output positions
+    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (l >= b.n_lines) return;
+    const int off = b.line_off[l], n = b.line_off[l + 1] - off;
+    const T ax[3] = {ax0, ax1, ax2};
+    const T r0[3] = {p.P[0][off], p.P[1][off], p.P[2][off]};
+    const T iEI = (T)(1.0 / EI[l]);
+    for (int q = lane; q < n; q += 32) {
+        const int i = off + q;
+        T xi = (T)0;
+        for (int a = 0; a < 3; ++a) xi += (p.P[a][i] - r0[a]) * ax[a];
+        T w[3] = {(T)0, (T)0, (T)0};
+        for (int r = 0; r < n; ++r) {
+            const int k = off + r;
+            T ak = (T)0, fa = (T)0, f[3];
+            for (int a = 0; a < 3; ++a) {
+                f[a] = p.F[a][k];
+                ak += (p.P[a][k] - r0[a]) * ax[a];
+                fa += f[a] * ax[a];
+            }
+            const T gk = cantilever_g(xi, ak);
+            for (int a = 0; a < 3; ++a) w[a] += (f[a] - fa * ax[a]) * gk;
+        }
+        for (int a = 0; a < 3; ++a) p.S[a][i] = p.P[a][i] + w[a] * iEI;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers.  Single instance: one launch per phase.  Batched: one launch per
 // phase over the work items of every instance of a batch; each work item is
 // mapped to its instance by a binary search over the prefix sums of the
