@@ -63,6 +63,7 @@ struct al_grid_s {
     int *d_line_off = nullptr, *d_line_of = nullptr;
     double *d_d = nullptr, *d_cdn = nullptr, *d_cdt = nullptr, *d_eps = nullptr, *d_ell = nullptr,
            *d_af = nullptr, *d_cvl = nullptr, *d_cmn = nullptr, *d_cmt = nullptr, *d_EI = nullptr;
+    std::vector<double> h_EI;         // the stiffnesses last copied to d_EI
     al_beam_desc bd{};
 
     // per-point scratch (element type per precision)
@@ -109,6 +110,7 @@ static void free_beams(al_grid g) {
     g->d_line_off = g->d_line_of = nullptr;
     g->d_d = g->d_cdn = g->d_cdt = g->d_eps = g->d_ell = g->d_af = g->d_cvl = g->d_cmn = g->d_cmt = nullptr;
     g->d_EI = nullptr;
+    g->h_EI.clear();
     g->fprev = g->uhi = g->segD = g->segIl2 = g->nodeM = g->fhat = nullptr;
     g->ulo = g->nodeTau = nullptr;
     g->segWa = g->segWb = g->w = g->lineF = nullptr;
@@ -597,7 +599,12 @@ static int beam_qs_t(al_grid g, const double *EI, const double axis[3], const vo
     }
     BeamsC bc{};
     bc.n_lines = g->n_lines; bc.n_points = g->n_points; bc.line_off = g->d_line_off;
-    AL_CUDA(cudaMemcpyAsync(g->d_EI, EI, (size_t)g->n_lines * sizeof(double), cudaMemcpyHostToDevice, st));
+    // the stiffnesses go to the device only when they change
+    if (g->h_EI.size() != (size_t)g->n_lines || !std::equal(EI, EI + g->n_lines, g->h_EI.begin())) {
+        g->h_EI.assign(EI, EI + g->n_lines);
+        AL_CUDA(cudaMemcpyAsync(g->d_EI, g->h_EI.data(), (size_t)g->n_lines * sizeof(double),
+                                cudaMemcpyHostToDevice, st));
+    }
     k_beam_qs<T><<<(unsigned)((g->n_lines + 7) / 8), 256, 0, st>>>(bc, g->d_EI, (T)axis[0], (T)axis[1],
                                                                      (T)axis[2], p);
     AL_CUDA(cudaGetLastError());

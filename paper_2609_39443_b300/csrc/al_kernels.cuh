@@ -2556,27 +2556,52 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_beam_qs(BeamsC b, const double *EI, T ax0, T ax1, T ax2,
                                                  StepPtrs<T> p) {
     // p.P: rest positions P0, p.F: loads, p.S[0..2]: output positions
+    // each warp stages its line's stations and normal loads in shared memory
+    // (lines of up to QS_N nodes; longer lines read them from global memory)
+    constexpr int QS_N = 128;
+    __shared__ T st_a[8][QS_N], st_f[8][3][QS_N];
+    const int wib = threadIdx.x >> 5;
     const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (l >= b.n_lines) return;
     const int off = b.line_off[l], n = b.line_off[l + 1] - off;
     const T ax[3] = {ax0, ax1, ax2};
     const T r0[3] = {p.P[0][off], p.P[1][off], p.P[2][off]};
     const T iEI = (T)(1.0 / EI[l]);
+    auto node = [&](int k, T &ak, T fp[3]) {
+        T fa = (T)0, f[3];
+        ak = (T)0;
+        for (int a = 0; a < 3; ++a) {
+            f[a] = p.F[a][k];
+            ak += (p.P[a][k] - r0[a]) * ax[a];
+            fa += f[a] * ax[a];
+        }
+        for (int a = 0; a < 3; ++a) fp[a] = f[a] - fa * ax[a];
+    };
+    const bool staged = n <= QS_N;
+    if (staged) {
+        for (int q = lane; q < n; q += 32) {
+            T ak, fp[3];
+            node(off + q, ak, fp);
+            st_a[wib][q] = ak;
+            for (int a = 0; a < 3; ++a) st_f[wib][a][q] = fp[a];
+        }
+        __syncwarp();
+    }
     for (int q = lane; q < n; q += 32) {
         const int i = off + q;
         T xi = (T)0;
         for (int a = 0; a < 3; ++a) xi += (p.P[a][i] - r0[a]) * ax[a];
         T w[3] = {(T)0, (T)0, (T)0};
         for (int r = 0; r < n; ++r) {
-            const int k = off + r;
-            T ak = (T)0, fa = (T)0, f[3];
-            for (int a = 0; a < 3; ++a) {
-                f[a] = p.F[a][k];
-                ak += (p.P[a][k] - r0[a]) * ax[a];
-                fa += f[a] * ax[a];
+            T ak, fp[3];
+            if (staged) {
+                ak = st_a[wib][r];
+                for (int a = 0; a < 3; ++a) fp[a] = st_f[wib][a][r];
+            } else {
+                node(off + r, ak, fp);
             }
             const T gk = cantilever_g(xi, ak);
-            for (int a = 0; a < 3; ++a) w[a] += (f[a] - fa * ax[a]) * gk;
+            for (int a = 0; a < 3; ++a) w[a] += fp[a] * gk;
         }
         for (int a = 0; a < 3; ++a) p.S[a][i] = p.P[a][i] + w[a] * iEI;
     }
