@@ -2192,11 +2192,12 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
             }
             __syncthreads();
             // ---- gather: warp w takes layer w; for each line in order its lanes take
-            //      the cells of the layer near the line, two rows of 16 at a time, so no
-            //      two lanes share a cell and every cell sums its lines in line order ----
+            //      the cells of the layer near the line, 32 at a time, so no two lanes
+            //      share a cell and every cell sums its lines in line order ----
             // WPL warps share a layer (bricks lower than the warp count), taking
             // alternate row pairs; taller bricks give each warp several layers
             constexpr int NW = SPREAD_THREADS / 32, WPL = (BZ < NW) ? NW / BZ : 1;
+            static_assert(BY <= 32 && (BY & (BY - 1)) == 0, "one lane per row, a power of two");
             const int zpart = warp % WPL;
             for (int z = warp / WPL; z < nzb; z += NW / WPL) {
                 const float czf = z + 0.5f;
@@ -2222,17 +2223,50 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                     const float rho2 = sm.e_rho2[e];
                     const float ac = sm.l_ac[e][z], gxv = sm.l_gx[e][z], gyv = sm.l_gy[e][z];
                     const int jcz = sm.l_jc[e][z];
-                    const int tx = ix0 + (lane & 15);
                     // weights pass: per-lane sums for the four nodes around the crossing
                     // (slots w0s .. w0s + 3), reduced over the warp once per line and layer
                     unsigned long long wacc0 = 0ull, wacc1 = 0ull, wacc2 = 0ull, wacc3 = 0ull;
                     const int w0s = (base >= 0) ? base + (jcz - jlo) - 1 : 0;
-                    // row pairs (2p, 2p + 1) belong to warp p % WPL of the layer, the same
-                    // warp for every line, so a cell is only ever updated by one warp
-                    const int p0 = iy0 >> 1;
-                    const int y0s = (WPL == 1) ? iy0 : 2 * (p0 + (zpart - p0 % WPL + WPL) % WPL);
-                    for (int y0 = y0s; y0 <= iy1; y0 += 2 * WPL) {
-                        const int ty = y0 + (lane >> 4);
+                    // the cells to test, packed over the lanes: lane r takes row iy0 + r's
+                    // run of columns (the disc around the crossing widened by a column on
+                    // each side, so it holds every cell the disc test below passes), a
+                    // scan places the runs end to end, and the lanes take cells q, q + 32,
+                    // ... of that order.  Row pairs (2p, 2p + 1) belong to warp p % WPL of
+                    // the layer, the same warp for every line, so a cell is only ever
+                    // updated by one warp, once per line, in line order.
+                    int rcnt = 0, rx0 = 0;
+                    {
+                        const int ry = iy0 + lane;
+                        if (ry <= iy1 && (WPL == 1 || ((ry >> 1) % WPL) == zpart)) {
+                            int xa = ix0, xb = ix1;
+                            if (rh2 < 1e30f) {
+                                const float dyr = (ry + 0.5f) - yc;
+                                const float hw = sqrtf(fmaxf(rh2 - dyr * dyr, 0.0f));
+                                xa = max(ix0, (int)ceilf(xc - hw - 0.5f) - 1);
+                                xb = min(ix1, (int)floorf(xc + hw - 0.5f) + 1);
+                            }
+                            rcnt = max(0, xb - xa + 1);
+                            rx0 = xa;
+                        }
+                    }
+                    int rinc = rcnt;                 // inclusive scan over the (at most BY) rows
+                    for (int o = 1; o < BY; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, rinc, o);
+                        if (lane >= o) rinc += v;
+                    }
+                    const int ncell = __shfl_sync(0xffffffffu, rinc, BY - 1);
+                    for (int q0 = 0; q0 < ncell; q0 += 32) {
+                        const int qc = q0 + lane;
+                        int r = 0;                   // rows whose runs end at or before qc
+#pragma unroll
+                        for (int st = BY / 2; st > 0; st >>= 1) {
+                            const int v = __shfl_sync(0xffffffffu, rinc, r + st - 1);
+                            if (v <= qc) r += st;
+                        }
+                        const int rb = __shfl_sync(0xffffffffu, rinc - rcnt, r);
+                        const int rx = __shfl_sync(0xffffffffu, rx0, r);
+                        const int tx = qc < ncell ? rx + (qc - rb) : ix1 + 1;
+                        const int ty = iy0 + r;
                         const float cx = tx + 0.5f, cy = ty + 0.5f;
                         const float dx = cx - xc, dy = cy - yc;
                         bool in = false;
