@@ -93,9 +93,10 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(workload_name, kernel="k_spread"):
+def _traffic(workload_name, kernel="k_spread", options=None):
     """dram bytes per launch of a kernel from a committed ncu summary, if it
-    was taken on the current kernel source."""
+    was taken on the current kernel source with the same options (weights
+    pass, brick height, records)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -103,6 +104,9 @@ def _traffic(workload_name, kernel="k_spread"):
     e = d.get(f"{workload_name}/{kernel}")
     if not e or e.get("kernel_hash") != _kernel_hash():
         return None
+    if options is not None and "options" in e:
+        if any(e["options"].get(k) != options.get(k) for k in ("weights", "brick_z", "records")):
+            return None
     return e.get("dram_bytes_per_launch")
 
 
@@ -383,7 +387,7 @@ def run_ours(a):
     peak, peak_kind = _peaks()
     alg = _algorithmic_bytes(wl)
     achieved = alg / spread_s / 1e9
-    traffic = _traffic(wl.name)
+    traffic = _traffic(wl.name, options=tuned)
     weights_s = ph[PHASES.index("weights")] / 1e3
     if weights_s > spread_s and tuned["weights"] == "segment":
         flop = supp * FLOP_PER_PAIR
@@ -391,7 +395,7 @@ def run_ours(a):
         roofline = {"bound": "alu", "kernel": "k_weights", "achieved": a_t, "peak": ALU_PEAK_TFLOPS,
                     "peak_kind": "derived (148 SMs x 128 FP32 lanes x FMA x 2.032 GHz)", "unit": "TFLOP/s",
                     "frac": a_t / ALU_PEAK_TFLOPS, "algorithmic_flop": flop,
-                    "traffic": _traffic(wl.name, "k_weights"),
+                    "traffic": _traffic(wl.name, "k_weights", tuned),
                     "k_spread": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                  "frac": achieved / peak, "algorithmic_bytes": alg}}
     else:
