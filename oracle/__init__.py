@@ -39,7 +39,8 @@ class _Beams(C.Structure):
                 ("cv_len", C.POINTER(C.c_double)), ("n_p", C.c_double * 3),
                 ("g_up", C.c_double * 3), ("tau", C.c_double), ("sample_mode", C.c_int),
                 ("drag_mode", C.c_int), ("proj_mode", C.c_int),
-                ("cm_n", C.POINTER(C.c_double)), ("cm_t", C.POINTER(C.c_double))]
+                ("cm_n", C.POINTER(C.c_double)), ("cm_t", C.POINTER(C.c_double)),
+                ("wall_reflect", C.c_int)]
 
 
 _lib = None
@@ -92,7 +93,7 @@ class _BeamsHold:
         self.s = _Beams(int(b.n_lines), _ptr(self.off, C.c_int), *[_ptr(a) for a in self.arr],
                         (C.c_double * 3)(*map(float, b.n_p)), (C.c_double * 3)(*map(float, b.g_up)),
                         float(b.tau), int(b.sample_mode), int(b.drag_mode), int(getattr(b, "proj_mode", 0)),
-                        _ptr(self.cm[0]), _ptr(self.cm[1]))
+                        _ptr(self.cm[0]), _ptr(self.cm[1]), int(getattr(b, "wall_reflect", 0)))
 
 
 def sample(grid, field, mode, p, eps=0.0):

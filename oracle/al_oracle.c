@@ -60,6 +60,8 @@ typedef struct {
     int proj_mode;                    /* 0 nearest segment (Eq. almProjectionPoint), 1 segment-integrated */
     const double *cm_n, *cm_t;        /* per line, added-mass coefficients of Eq. fext_addedmass;
                                          NULL: no inertia term (the paper's model) */
+    int wall_reflect;                 /* bit 2a (2a+1): the low (high) face of axis a reflects
+                                         the kernel (the projection variant of Sec. 6) */
 } or_beams;
 
 /* status counters (same meaning as the CUDA library's) */
@@ -433,6 +435,13 @@ void or_seg_kernel(const double *c, const double *A, const double *B, double eps
                                  (exp(-t0 * t0 / (eps * eps)) - exp(-(L - t0) * (L - t0) / (eps * eps))));
 }
 
+/* Index of the grid cell a ghost cell beyond a reflecting face mirrors
+ * onto: -1 - i below the low face, 2n - 1 - i above the high face. */
+static int or_fold(int i, int n)
+{
+    return i < 0 ? -1 - i : (i >= n ? 2 * n - 1 - i : i);
+}
+
 static void or_project_line(const or_grid *g, const or_beams *b, const double *Ps, long long np,
                             const double *F, int l, int cull, or_line_out *o)
 {
@@ -455,16 +464,30 @@ static void or_project_line(const or_grid *g, const or_beams *b, const double *P
      * widened by one cell so that rounding of the box bounds can never drop
      * a cell inside it (cells beyond the box are farther than R from every
      * segment, so extra cells change nothing). */
+    /* A reflecting face (the one-sided kernel of Sec. 6, read as a mirror)
+     * adds G = ceil(3 eps / h) + 1 layers of ghost cells beyond it: the
+     * kernel is evaluated at their centres like at any cell's, and each
+     * ghost's share goes to the grid cell it mirrors (or_fold), so the mass
+     * that falls outside the domain comes back next to the wall rather than
+     * being spread over the node's whole support by the normalisation.  One
+     * reflection per face: at most n ghost layers. */
     const int nn[3] = {g->nx, g->ny, g->nz};
+    const int G = (int)ceil(R / g->h) + 1;
+    int glo[3], ghi[3];
+    for (int a = 0; a < 3; ++a) {
+        const int gd = G < nn[a] ? G : nn[a];
+        glo[a] = ((b->wall_reflect >> (2 * a)) & 1) ? -gd : 0;
+        ghi[a] = ((b->wall_reflect >> (2 * a + 1)) & 1) ? nn[a] - 1 + gd : nn[a] - 1;
+    }
     int lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
-        if (!cull) { lo[a] = 0; hi[a] = nn[a] - 1; continue; }
+        if (!cull) { lo[a] = glo[a]; hi[a] = ghi[a]; continue; }
         double mn = X[0][a], mx = X[0][a];
         for (int k = 1; k < n; ++k) { if (X[k][a] < mn) mn = X[k][a]; if (X[k][a] > mx) mx = X[k][a]; }
         double il = ceil((mn - R - g->o[a]) / g->h - 0.5) - 1.0;
         double ih = floor((mx + R - g->o[a]) / g->h - 0.5) + 1.0;
-        if (il < 0.0) il = 0.0;
-        if (ih > nn[a] - 1.0) ih = nn[a] - 1.0;
+        if (il < glo[a]) il = glo[a];
+        if (ih > ghi[a]) ih = ghi[a];
         lo[a] = (int)il; hi[a] = (int)ih;
     }
     const long long nxy = (long long)g->nx * g->ny;
@@ -473,6 +496,8 @@ static void or_project_line(const or_grid *g, const or_beams *b, const double *P
             for (int ix = lo[0]; ix <= hi[0]; ++ix) {
                 double c[3] = {g->o[0] + (ix + 0.5) * g->h, g->o[1] + (jy + 0.5) * g->h,
                                g->o[2] + (kz + 0.5) * g->h};
+                const long long cell = or_fold(ix, g->nx) + (long long)g->nx * or_fold(jy, g->ny) +
+                                       nxy * or_fold(kz, g->nz);
                 if (b->proj_mode == 1 && n >= 2) {
                     /* every segment whose closest point lies within 3 eps
                      * contributes its integrated kernel; the record keeps
@@ -484,7 +509,7 @@ static void or_project_line(const or_grid *g, const or_beams *b, const double *P
                         double K[2];
                         or_seg_kernel(c, X[k], X[k + 1], eps, K);
                         if (K[0] > 0.0)
-                            or_push(o, ix + (long long)g->nx * jy + nxy * kz, k, K[1] / K[0], K[0]);
+                            or_push(o, cell, k, K[1] / K[0], K[0]);
                     }
                     continue;
                 }
@@ -494,7 +519,7 @@ static void or_project_line(const or_grid *g, const or_beams *b, const double *P
                 if (r <= R) {                   /* truncation at 3 eps, inclusive */
                     double x = r / eps;
                     double eta = exp(-x * x) / (OR_PI * eps * eps);   /* Eq. almGaussian */
-                    or_push(o, ix + (long long)g->nx * jy + nxy * kz, kbest, sbest, eta);
+                    or_push(o, cell, kbest, sbest, eta);
                 }
             }
     /* nodal weights w_k = sum_j omega_jk eta_j V_j with omega_ji = 1 - s_j,

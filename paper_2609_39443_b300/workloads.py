@@ -77,6 +77,7 @@ class BeamSpec:
     tangents_given: bool = False
     cm_n: Optional[np.ndarray] = None   # float64 [n_lines] added-mass coefficients (None: no inertia term)
     cm_t: Optional[np.ndarray] = None
+    wall_reflect: int = 0       # bit 2a (2a + 1): the low (high) face of axis a reflects the kernel
 
     @property
     def n_lines(self) -> int:
@@ -459,6 +460,16 @@ def with_sample_mode(wl: Workload, mode: str) -> Workload:
     m = {"trilinear": SAMPLE_TRILINEAR, "cell": SAMPLE_CELL, "gauss": SAMPLE_GAUSS}[mode]
     return replace(wl, name=f"{wl.name}_{mode}" if m != wl.beams.sample_mode else wl.name,
                    beams=replace(wl.beams, sample_mode=m))
+
+
+REFLECT_X_LO, REFLECT_X_HI, REFLECT_Y_LO, REFLECT_Y_HI, REFLECT_Z_LO, REFLECT_Z_HI = (1 << a for a in range(6))
+
+
+def with_reflect(wl: Workload, mask: int) -> Workload:
+    """The same workload with the kernel reflected at the grid faces in
+    `mask` (REFLECT_* bits; 0: the paper's truncated kernel)."""
+    return replace(wl, name=f"{wl.name}_reflect{mask}" if mask else wl.name,
+                   beams=replace(wl.beams, wall_reflect=int(mask)))
 
 
 def with_projection(wl: Workload, mode: str) -> Workload:

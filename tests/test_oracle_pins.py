@@ -7,6 +7,7 @@ under a re-typed formula: they use closed forms, exact reproductions,
 invariants, brute force and the golden values under tests/golden/.
 """
 import os
+from dataclasses import replace
 
 import numpy as np
 import pytest
@@ -781,3 +782,88 @@ def test_cantilever_axial_loads_reciprocity_and_rotation():
     b2, P2, ax2, _ = _stem(17, L=0.5, axis=Rm @ ax, root=Rm @ np.array([0.2, -0.1, 0.3]))
     d2 = oracle.beam_quasistatic(b2, EI, ax2, P2, Rm @ F) - P2
     np.testing.assert_allclose(d2, Rm @ d0, rtol=1e-12, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# reflected kernel at the grid faces (the one-sided kernel of Sec. 6, read as
+# a mirror): pinned against the plain truncated kernel of the mirror lines
+# ----------------------------------------------------------------------------
+
+def _mirror(P, g, axis, high):
+    """P mirrored across the low (high) face of `axis` of grid g."""
+    Q = np.array(P, float, copy=True)
+    face = g.origin[axis] + ((g.nx, g.ny, g.nz)[axis] * g.h if high else 0.0)
+    Q[axis] = 2.0 * face - Q[axis]
+    return Q
+
+
+def _corner_line(g):
+    # a bent line rooted on the z- face near the x- / y- edge, inside the grid
+    n = 7
+    t = np.linspace(0.0, 1.0, n)
+    P = np.stack([g.origin[0] + g.h * (1.3 + 2.0 * t ** 2), g.origin[1] + g.h * (0.8 + 0.7 * t),
+                  g.origin[2] + g.h * 7.0 * t])
+    b = _beams([0, n], np.full(n, g.h), per_line=dict(eps=1.5 * g.h))
+    F = np.stack([np.linspace(1.0, 2.0, n), np.linspace(-0.5, 0.5, n), np.full(n, 0.25)])
+    return P, b, F
+
+
+@pytest.mark.parametrize("faces", [(0, 1, 2), (2,), (0,)])
+def test_reflected_weights_are_the_mirror_lines_weights(faces):
+    """w_k with reflection = sum over the line's mirror images of their plain
+    (truncated) w_k: each ghost cell sees the line as the grid cell it mirrors
+    sees the mirrored line."""
+    g = GridSpec(14, 12, 13, 0.01, origin=(0.1, -0.2, 0.05), precision="fp64")
+    P, b, F = _corner_line(g)
+    mask = sum(1 << (2 * a) for a in faces)
+    wr = oracle.project(g, replace(b, wall_reflect=mask), P, F)["w"]
+    total = np.zeros_like(wr)
+    for bits in range(1 << len(faces)):
+        Q = P
+        for i, a in enumerate(faces):
+            if bits >> i & 1:
+                Q = _mirror(Q, g, a, False)
+        total += oracle.project(g, b, Q, F)["w"]
+    np.testing.assert_allclose(wr, total, rtol=1e-12)
+    plain = oracle.project(g, b, P, F)["w"]
+    assert (wr >= plain).all() and (wr > plain).any()
+    if 2 in faces:
+        assert wr[0] > 1.5 * plain[0]                             # the root sits on the z- face
+
+
+def test_reflected_source_is_the_mirror_lines_sources():
+    """S with reflection at the x+ and z- faces equals the plain sources of the
+    line and its mirror images, each carrying F_k w_k(image) / w_k(reflected):
+    the fold puts every ghost's share in the cell it mirrors."""
+    g = GridSpec(12, 11, 13, 0.01, precision="fp64")
+    P, b, F = _corner_line(g)
+    P[0] = g.nx * g.h - (P[0] - g.origin[0])          # near the x+ face instead
+    mask = (1 << 1) | (1 << 4)
+    r = oracle.project(g, replace(b, wall_reflect=mask), P, F)
+    images = [P, _mirror(P, g, 0, True), _mirror(P, g, 2, False), _mirror(_mirror(P, g, 0, True), g, 2, False)]
+    S = np.zeros_like(r["S"])
+    for Q in images:
+        wq = oracle.project(g, b, Q, F)["w"]
+        S += oracle.project(g, b, Q, F * (wq / r["w"]))["S"]
+    np.testing.assert_allclose(r["S"], S, rtol=1e-11, atol=1e-12 * np.abs(S).max())
+
+
+def test_reflection_conserves_and_leaves_far_lines_alone():
+    for seed in range(4):
+        wl = W.make_random(400 + seed, 18, 16, 14, n_lines=4, precision="fp64",
+                           kinds=("stem", "arc", "random", "point"))
+        plain = oracle.sample_drag_spread(wl)
+        r = oracle.sample_drag_spread(W.with_reflect(wl, 63))
+        assert r["status"][oracle.ST_DEPOSIT_LOST] == 0
+        np.testing.assert_allclose(r["totals"][3:], -r["totals"][:3], atol=1e-12 * np.abs(r["F"]).sum())
+        np.testing.assert_array_equal(r["F"], plain["F"])
+        # brute force over every cell and ghost cell gives the same bits
+        b = oracle.project(wl.grid, W.with_reflect(wl, 63).beams, wl.step.P, r["F"], cull=False)
+        np.testing.assert_array_equal(b["S"], r["S"])
+    # a line farther than 3 eps from every face: reflection changes nothing
+    g = GridSpec(30, 30, 30, 0.01, precision="fp64")
+    bl, P, F = _straight_z_line(g, 0.155, 0.145, 0.09, 0.02, 6, np.ones((3, 6)))
+    a = oracle.project(g, bl, P, F)
+    c = oracle.project(g, replace(bl, wall_reflect=63), P, F)
+    np.testing.assert_array_equal(a["S"], c["S"])
+    np.testing.assert_array_equal(a["w"], c["w"])
