@@ -57,6 +57,8 @@ def _args():
                     help="sampling operator of both velocity samples (cell: the containing cell; gauss: Gaussian volume average)")
     ap.add_argument("--projection", default="nearest", choices=["nearest", "integrated"],
                     help="projection: nearest segment (the paper's) or segment-integrated 3-D Gaussian")
+    ap.add_argument("--reflect", type=int, default=0,
+                    help="faces that reflect the kernel (bit mask: 1 x-, 2 x+, 4 y-, 8 y+, 16 z-, 32 z+)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -263,6 +265,9 @@ def run_ours(a):
     if a.projection != "nearest":
         from paper_2609_39443_b300 import workloads as W
         wl = W.with_projection(wl, a.projection)
+    if a.reflect:
+        from paper_2609_39443_b300 import workloads as W
+        wl = W.with_reflect(wl, a.reflect)
     inst = Instance(wl, device=f"cuda:{local}")
     tuned = {"weights": "brick", "brick_z": 8, "autotuned": False}
     if a.weights or a.brick_z or a.records:
@@ -276,6 +281,8 @@ def run_ours(a):
         wmode, bz, rec = inst.autotune(trials=2)
         tuned = {"weights": "segment" if wmode else "brick", "brick_z": bz, "records": bool(rec),
                  "autotuned": True}
+    if a.reflect:                                    # the library takes the brick passes for it
+        tuned.update(weights="brick", records=False)
     inst.grid.trace(True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
@@ -369,7 +376,7 @@ def run_ours(a):
 
     # ---- the scatter-with-atomics projection on the same instance (comparison) ----
     variants = None
-    if not a.no_variants:
+    if not a.no_variants and not a.reflect:          # the reflected kernel always gathers
         from paper_2609_39443_b300.al import OPT_SPREAD, SPREAD_GATHER, SPREAD_SCATTER
         variants = {}
         for name, mode in (("gather", SPREAD_GATHER), ("scatter_atomics", SPREAD_SCATTER)):
@@ -412,7 +419,7 @@ def run_ours(a):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if wl.grid.precision == "fp64" else "f32", "data": "synthetic",
                 "config": {"workload": wl.name, "cells": wl.grid.n_cells, "points": wl.beams.n_points,
-                           "inertia": bool(a.inertia), "sample": a.sample, "projection": a.projection,
+                           "inertia": bool(a.inertia), "sample": a.sample, "projection": a.projection, "reflect": a.reflect,
                            "lines": wl.beams.n_lines, "parallelism": f"{world} independent instances",
                            "l2": "flushed between timed steps (256 MiB write)", "options": tuned},
                 "kernel_cell_updates_per_s": supp * value,

@@ -57,6 +57,12 @@ extern "C" {
 #define AL_SAMPLE_CELL      1  /* value of the single containing cell (the paper's operator) */
 #define AL_PROJ_NEAREST     0
 #define AL_PROJ_INTEGRATED  1
+#define AL_REFLECT_X_LO 1      /* al_beam_desc.wall_reflect bits: faces that reflect the kernel */
+#define AL_REFLECT_X_HI 2
+#define AL_REFLECT_Y_LO 4
+#define AL_REFLECT_Y_HI 8
+#define AL_REFLECT_Z_LO 16
+#define AL_REFLECT_Z_HI 32
 #define AL_SAMPLE_GAUSS     2  /* kernel-weighted volume average: sum_j g_j U_j / sum_j g_j over the
                                   cells whose centre lies within 3 eps of the point, g_j =
                                   exp(-(|C_j - p| / eps)^2) with the line's projection width eps
@@ -132,6 +138,21 @@ typedef struct {
      * records for every line; status[AL_ST_SUPPORT] then counts (cell,
      * segment) pairs. */
     int proj_mode;
+    /* Kernel reflected at grid faces (the one-sided or reflected kernel that
+     * Sec. 6 proposes, read as a mirror); 0 keeps the paper's truncated
+     * kernel.  Bit 2a (2a + 1) of this AL_REFLECT_* mask makes the low (high)
+     * face of axis a = x, y, z reflect.  The kernel is then also evaluated at
+     * ghost cells up to ceil(3 eps / h) + 1 layers beyond such a face, and each
+     * ghost's share goes to the grid cell it mirrors: kernel mass that falls
+     * outside the domain comes back next to the wall instead of being spread
+     * over the node's whole support by the normalisation.
+     * Requirements (AL_ERR_ARG otherwise):
+     *   - AL_PROJ_NEAREST;
+     *   - ceil(3 eps / h) + 1 <= n on every reflecting axis.
+     * The nodes must lie inside the grid box.  The brick weights pass and the
+     * gather without records are used, whatever the options say.
+     * status[AL_ST_SUPPORT] counts ghost pairs too. */
+    int wall_reflect;
 } al_beam_desc;
 
 /* Inputs of one step: DEVICE pointers, element type per grid precision,

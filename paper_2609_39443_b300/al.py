@@ -44,7 +44,8 @@ class BeamDesc(C.Structure):
                 ("cdt", _dp), ("eps", _dp), ("ell_s", _dp), ("alpha_f", _dp), ("cv_len", _dp),
                 ("n_p", C.c_double * 3), ("g_up", C.c_double * 3), ("tau", C.c_double),
                 ("sample_mode", C.c_int), ("drag_mode", C.c_int), ("tangents_given", C.c_int),
-                ("cm_n", _dp), ("cm_t", _dp), ("proj_mode", C.c_int)]
+                ("cm_n", _dp), ("cm_t", _dp), ("proj_mode", C.c_int),
+                ("wall_reflect", C.c_int)]
 
 
 class StepIn(C.Structure):
@@ -149,7 +150,8 @@ class BeamArrays:
                              (C.c_double * 3)(*map(float, beams.n_p)), (C.c_double * 3)(*map(float, beams.g_up)),
                              float(beams.tau), int(beams.sample_mode), int(beams.drag_mode),
                              int(bool(beams.tangents_given)), *([p(a) for a in self.cm] or [None, None]),
-                             int(getattr(beams, "proj_mode", 0)))
+                             int(getattr(beams, "proj_mode", 0)),
+                             int(getattr(beams, "wall_reflect", 0)))
 
 
 def step_descriptors(U, P, Pdot, S, F, *, alpha=None, P_spread=None, tangent=None, totals=None, status=None,

@@ -204,6 +204,8 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
         return AL_ERR_ARG;
     if (b.drag_mode != AL_DRAG_DISCRETE && b.drag_mode != AL_DRAG_SPLIT) return AL_ERR_ARG;
     if (b.proj_mode != AL_PROJ_NEAREST && b.proj_mode != AL_PROJ_INTEGRATED) return AL_ERR_ARG;
+    if (b.wall_reflect < 0 || b.wall_reflect > 63) return AL_ERR_ARG;
+    if (b.wall_reflect && b.proj_mode != AL_PROJ_NEAREST) return AL_ERR_ARG;
     if (!(b.tau >= 0.0)) return AL_ERR_ARG;
     const double npn = std::sqrt(b.n_p[0] * b.n_p[0] + b.n_p[1] * b.n_p[1] + b.n_p[2] * b.n_p[2]);
     if (!(npn == 0.0 || std::fabs(npn - 1.0) < 1e-9)) return AL_ERR_ARG;
@@ -221,6 +223,14 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
         }
         np = b.line_off[b.n_lines];
         if (np > 0 && !b.cv_len) return AL_ERR_ARG;
+        if (b.wall_reflect) {                            // one reflection per face: ghosts <= n deep
+            double emax = 0.0;
+            for (int l = 0; l < b.n_lines; ++l) emax = std::max(emax, b.eps[l]);
+            const double gd = std::ceil(3.0 * emax / g->d.dx) + 1.0;
+            const int nn[3] = {g->d.nx, g->d.ny, g->d.nz};
+            for (int a = 0; a < 3; ++a)
+                if (((b.wall_reflect >> (2 * a)) & 3) && gd > (double)nn[a]) return AL_ERR_ARG;
+        }
         for (int i = 0; i < np; ++i)
             if (!(b.cv_len[i] >= 0.0) || !std::isfinite(b.cv_len[i])) return AL_ERR_ARG;
     }
@@ -327,11 +337,12 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
 template <typename T, int BZ>
 static cudaError_t brick_attrs() {
     const int fx = (int)sizeof(al::SpreadSmem<T, BZ, true>), fl = (int)sizeof(al::SpreadSmem<T, BZ, false>);
-    const void *fns[5] = {(const void *)al::k_spread<T, BZ, true>, (const void *)al::k_spread<T, BZ, false>,
+    const void *fns[7] = {(const void *)al::k_spread<T, BZ, true>, (const void *)al::k_spread<T, BZ, false>,
                           (const void *)al::kb_spread<T, BZ>, (const void *)al::k_bweights<T, BZ>,
-                          (const void *)al::kb_bweights<T, BZ>};
-    const int bytes_of[5] = {fx, fl, fx, fl, fl};
-    for (int i = 0; i < 5; ++i) {
+                          (const void *)al::kb_bweights<T, BZ>, (const void *)al::k_spread_refl<T, BZ>,
+                          (const void *)al::k_bweights_refl<T, BZ>};
+    const int bytes_of[7] = {fx, fl, fx, fl, fl, fl, fl};
+    for (int i = 0; i < 7; ++i) {
         const void *f = fns[i];
         const int bytes = bytes_of[i];
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -355,8 +366,14 @@ static cudaError_t spread_smem_attr() {
 template <typename T, int BZ>
 static void launch_bricks(const al::Inst<T> &I, bool weights, cudaStream_t st) {
     using namespace al;
-    if (weights)
+    if (weights && I.b.reflect)
+        k_bweights_refl<T, BZ><<<(unsigned)I.g.nbrick, SPREAD_THREADS, sizeof(SpreadSmem<T, BZ, false>), st>>>(
+            I.g, I.b, I.sc, I.p, I.status);
+    else if (weights)
         k_bweights<T, BZ><<<(unsigned)I.g.nbrick, SPREAD_THREADS, sizeof(SpreadSmem<T, BZ, false>), st>>>(
+            I.g, I.b, I.sc, I.p, I.status);
+    else if (I.b.reflect)
+        k_spread_refl<T, BZ><<<(unsigned)I.g.nbrick, SPREAD_THREADS, sizeof(SpreadSmem<T, BZ, false>), st>>>(
             I.g, I.b, I.sc, I.p, I.status);
     else if (I.g.fx)
         k_spread<T, BZ, true><<<(unsigned)I.g.nbrick, SPREAD_THREADS, sizeof(SpreadSmem<T, BZ, true>), st>>>(
@@ -415,6 +432,7 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     bc.tangents_given = g->bd.tangents_given;
     bc.cm_n = g->d_cmn; bc.cm_t = g->d_cmt;
     bc.proj_mode = g->bd.proj_mode;
+    bc.reflect = g->bd.wall_reflect;
     bc.inertia = (g->d_cmn != nullptr && g->n_lines > 0) ? 1 : 0;
     I.g = g->gc;
     I.g.rec_total = g->rec_total;
@@ -423,8 +441,13 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
         I.g.wmode = AL_WEIGHTS_SEGMENT;
         I.g.smode = AL_SPREAD_GATHER;
     }
+    if (g->bd.wall_reflect) {                           // ghost cells: the brick passes for every line
+        I.g.wmode = AL_WEIGHTS_BRICK;
+        I.g.smode = AL_SPREAD_GATHER;
+    }
     I.g.rmode = (g->opt_record == 1 && I.g.wmode != 0 && I.g.smode == 0 && g->rec_total > 0) ? 1 : 0;
     I.g.fx = (I.g.rmode || g->opt_record == 2 || g->bd.proj_mode == AL_PROJ_INTEGRATED) ? 1 : 0;
+    if (g->bd.wall_reflect) I.g.fx = 0;                 // the reflected passes gather in line order
     I.status = out->status ? out->status : g->statusInt;
     I.totals = out->totals ? out->totals : g->totalsInt;
     return I;
@@ -691,6 +714,7 @@ extern "C" int al_batch_add(al_batch b, al_grid g, const al_step_in *in, const a
     if (b->committed) return AL_ERR_STATE;
     if (!g->loaded) return AL_ERR_STATE;
     if (b->precision >= 0 && b->precision != g->d.precision) return AL_ERR_ARG;
+    if (g->bd.wall_reflect) return AL_ERR_ARG;         // the reflected kernel runs alone only
     for (int a = 0; a < 3; ++a)
         if (!in->U[a] || !out->S[a]) return AL_ERR_ARG;
     if (g->d.has_alpha && !in->alpha) return AL_ERR_ARG;
@@ -868,6 +892,7 @@ extern "C" int al_batch_assign(al_batch b, int slot, al_grid g, const al_step_in
     if (slot < 0 || slot >= b->n) return AL_ERR_ARG;
     if (g) {
         if (!in || !out || !g->loaded || g->d.precision != b->precision) return AL_ERR_ARG;
+        if (g->bd.wall_reflect) return AL_ERR_ARG;     // the reflected kernel runs alone only
         for (int a = 0; a < 3; ++a)
             if (!in->U[a] || !out->S[a]) return AL_ERR_ARG;
         if (g->d.has_alpha && !in->alpha) return AL_ERR_ARG;

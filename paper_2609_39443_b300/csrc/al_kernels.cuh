@@ -85,6 +85,7 @@ struct BeamsC {
     const double *cm_n, *cm_t;   // added-mass coefficients (inertia != 0)
     int inertia;
     int proj_mode;               // 0 nearest segment, 1 segment-integrated 3-D Gaussian
+    int reflect;                 // faces that reflect the kernel: bit 2a (2a + 1) low (high) face of axis a
 };
 
 struct LineG {                   // per line, rebuilt every step
@@ -1897,7 +1898,144 @@ __device__ __forceinline__ void acc_sub(A &acc, T v, int fsh) {
     else acc -= v;
 }
 
+// The mirror images of cell (tx, ty, z) of the brick beyond the reflecting
+// faces within reach of it (b.reflect), for line entry e: each image is a
+// ghost cell whose pair with the line is found and weighed like a grid
+// cell's (exhaustive closest segment, the same in/out decision, the same
+// per-pair values in both brick passes), and its share goes to the cell it
+// mirrors.  A ghost farther than 3 eps + 1 cell from the face cannot be
+// within 3 eps of a line inside the grid.  Returns the pairs within 3 eps.
 template <typename T, bool WP, int BZ, bool FX>
+__device__ __forceinline__ int d_images(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p,
+                                     int *status, SpreadSmem<T, BZ, FX> &sm, int e, int z, int tx, int ty, int B0,
+                                     int B1, int B2, int fsh) {
+    const long long np = b.n_points;
+    const int gc[3] = {B0 + tx, B1 + ty, B2 + z}, nn[3] = {g.nx, g.ny, g.nz}, Bv[3] = {B0, B1, B2};
+    const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e], base = sm.e_base[e], first = sm.e_first[e], n = sm.e_n[e];
+    const T R2 = sm.e_R2[e], gr = sm.e_gr[e], ie2 = sm.e_ie2[e], e0v = sm.e_eta0[e];
+    const int G = (int)ceilf(sqrtf((float)R2)) + 1;
+    int opt[3][3], nopt[3];
+    for (int a = 0; a < 3; ++a) {
+        nopt[a] = 1;
+        opt[a][0] = gc[a];
+        if (((b.reflect >> (2 * a)) & 1) && gc[a] < G) opt[a][nopt[a]++] = -1 - gc[a];
+        if (((b.reflect >> (2 * a + 1)) & 1) && gc[a] > nn[a] - 1 - G) opt[a][nopt[a]++] = 2 * nn[a] - 1 - gc[a];
+    }
+    if (nopt[0] * nopt[1] * nopt[2] == 1) return 0;
+    const int c = ty * BX + tx;
+    int ns = 0;
+    for (int i0 = 0; i0 < nopt[0]; ++i0)
+        for (int i1 = 0; i1 < nopt[1]; ++i1)
+            for (int i2 = 0; i2 < nopt[2]; ++i2) {
+                if (i0 == 0 && i1 == 0 && i2 == 0) continue;             // the cell itself
+                const int gi[3] = {opt[0][i0], opt[1][i1], opt[2][i2]};
+                T C[3];
+                for (int a = 0; a < 3; ++a) C[a] = (T)(gi[a] - Bv[a]) + (T)0.5;
+                int js;
+                T s, r2;
+                if (base >= 0) {
+                    js = nl_exhaustive_staged(sm, g, p, sc, base, first, n, jlo, jhi, C[0], C[1], C[2], B0, B1, B2,
+                                              gi[0], gi[1], gi[2], status);
+                    seg_foot(sm, base + (js - jlo), C, s, r2);
+                } else {
+                    js = nl_exhaustive(g, sc, p, first, n, jlo, jhi, C[0], C[1], C[2], B0, B1, B2, gi[0], gi[1],
+                                       gi[2], status);
+                    const int ka = first + js;
+                    T x[3], Dj[3];
+                    for (int a = 0; a < 3; ++a) {
+                        x[a] = C[a] - rel(sc.uhi[a * np + ka], sc.ulo[a * np + ka], Bv[a]);
+                        Dj[a] = sc.segD[a * np + ka];
+                    }
+                    s = (x[0] * Dj[0] + x[1] * Dj[1] + x[2] * Dj[2]) * sc.segIl2[ka];
+                    s = s < (T)0 ? (T)0 : (s > (T)1 ? (T)1 : s);
+                    const T f0 = x[0] - s * Dj[0], f1 = x[1] - s * Dj[1], f2 = x[2] - s * Dj[2];
+                    r2 = f0 * f0 + f1 * f1 + f2 * f2;
+                }
+                bool in;
+                if (r2 < R2 - gr) in = true;
+                else if (r2 > R2 + gr) in = false;
+                else in = nl_within(g, p, b.eps[sm.e_line[e]], first + js, n, gi[0], gi[1], gi[2], status);
+                if (!in) continue;
+                ++ns;
+                const T q = Tr<T>::ex2(-r2 * ie2);
+                const int ka = first + js, kb = seg_end(ka, n);
+                if constexpr (!WP) {
+                    T fa[3], fb[3];
+                    if (base >= 0) {
+                        const int ss = base + (js - jlo), sb = (n == 1) ? ss : ss + 1;
+                        for (int a = 0; a < 3; ++a) { fa[a] = sm.u.s.Fh[a][ss]; fb[a] = sm.u.s.Fh[a][sb]; }
+                    } else {
+                        for (int a = 0; a < 3; ++a) { fa[a] = sc.fhat[a * np + ka]; fb[a] = sc.fhat[a * np + kb]; }
+                    }
+                    T wa, wb;
+                    pair_w(e0v * q, s, wa, wb);
+                    for (int a = 0; a < 3; ++a) acc_sub<FX>(sm.u.s.acc[z][a][c], pair_src(wa, wb, fa[a], fb[a]), fsh);
+                } else {
+                    const int sh = (int)e0v;
+                    const unsigned long long va = to_fixed(q * ((T)1 - s), sh), vb = to_fixed(q * s, sh);
+                    if (base >= 0) {
+                        const int na = base + (js - jlo), nb2 = (n == 1) ? na : na + 1;
+                        if (va) atomicAdd(&sm.u.wq[na], va);
+                        if (vb) atomicAdd(&sm.u.wq[nb2], vb);
+                    } else {
+                        atomicAdd(&sc.wfix[ka], va);
+                        atomicAdd(&sc.wfix[kb], vb);
+                    }
+                }
+            }
+    return ns;
+}
+
+// The mirror-image phase of a batch (reflecting faces within reach of the
+// brick): the cells the gather visited, with the same layer and row-pair
+// ownership, so each cell is still updated by one warp only.  Kept out of
+// line so the gather's cell loop is compiled as without it.
+template <typename T, bool WP, int BZ, bool FX>
+__device__ __forceinline__ int d_images_phase(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
+                                           const StepPtrs<T> &p, int *status, SpreadSmem<T, BZ, FX> &sm, int ne,
+                                           int B0, int B1, int B2, int fsh) {
+    constexpr int NW = SPREAD_THREADS / 32, WPL = (BZ < NW) ? NW / BZ : 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, zpart = warp % WPL;
+    const int nzb = min(BZ, g.nz - B2), nxb = min(BX, g.nx - B0), nyb = min(BY, g.ny - B1);
+    const int Bv[3] = {B0, B1, B2}, bs[3] = {BX, BY, BZ}, nn[3] = {g.nx, g.ny, g.nz};
+    int ns = 0;
+    for (int z = warp / WPL; z < nzb; z += NW / WPL) {
+        const float czf = z + 0.5f;
+        for (int e = 0; e < ne; ++e) {
+            const int jlo = sm.e_jlo[e], jhi = sm.e_jhi[e];
+            if (jhi < jlo || czf < sm.e_lo[e][2] || czf > sm.e_hi[e][2]) continue;
+            // no cell of the brick within 3 eps + 1 cell of a reflecting face: no images
+            const int G = (int)ceilf(sqrtf((float)sm.e_R2[e])) + 1;
+            bool near = false;
+            for (int a = 0; a < 3; ++a)
+                near = near || (((b.reflect >> (2 * a)) & 1) && Bv[a] < G) ||
+                       (((b.reflect >> (2 * a + 1)) & 1) && Bv[a] + bs[a] > nn[a] - G);
+            if (!near) continue;
+            float xlo = sm.e_lo[e][0], xhi = sm.e_hi[e][0], ylo = sm.e_lo[e][1], yhi = sm.e_hi[e][1];
+            const float rh2 = sm.l_rh2[e][z], xc = sm.l_xc[e][z], yc = sm.l_yc[e][z];
+            if (rh2 < 1e30f) {
+                const float rh = sqrtf(rh2);
+                xlo = fmaxf(xlo, xc - rh); xhi = fminf(xhi, xc + rh);
+                ylo = fmaxf(ylo, yc - rh); yhi = fminf(yhi, yc + rh);
+            }
+            const int ix0 = max(0, (int)ceilf(fmaxf(xlo, -1.0f) - 0.5f));
+            const int ix1 = min(nxb - 1, (int)floorf(fminf(xhi, (float)BX + 1.0f) - 0.5f));
+            const int iy0 = max(0, (int)ceilf(fmaxf(ylo, -1.0f) - 0.5f));
+            const int iy1 = min(nyb - 1, (int)floorf(fminf(yhi, (float)BY + 1.0f) - 0.5f));
+            if (ix0 > ix1 || iy0 > iy1) continue;
+            const int w = ix1 - ix0 + 1, ncell = w * (iy1 - iy0 + 1);
+            for (int q = lane; q < ncell; q += 32) {
+                const int tx = ix0 + q % w, ty = iy0 + q / w;
+                if (WPL > 1 && ((ty >> 1) % WPL) != zpart) continue;
+                const float dx = (tx + 0.5f) - xc, dy = (ty + 0.5f) - yc;
+                if (dx * dx + dy * dy <= rh2) ns += d_images<T, WP, BZ, FX>(g, b, sc, p, status, sm, e, z, tx, ty, B0, B1, B2, fsh);
+            }
+        }
+    }
+    return ns;
+}
+
+template <typename T, bool WP, int BZ, bool FX, bool REFL = false>
 __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
                         const int br, SpreadSmem<T, BZ, FX> &sm) {
     using SM = SpreadSmem<T, BZ, FX>;
@@ -2037,12 +2175,24 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                 int jlo = 0x7fffffff, jhi = -1;
                 float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
                 float czp = 1.0f, czn = 1.0f;          // min D_z/|D| over up- and down-going candidates
+                // the box a candidate's support must meet: the brick's, and with
+                // reflecting faces within reach the boxes of its mirror images too
+                float olo[3] = {blo[0], blo[1], blo[2]}, ohi[3] = {bhi[0], bhi[1], bhi[2]};
+                if (REFL) {
+                    const float gd = ceilf(lg.Rc) + 1.0f;
+                    const float nnf[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
+                    for (int a = 0; a < 3; ++a) {
+                        if (((b.reflect >> (2 * a)) & 1) && blo[a] < gd) olo[a] = fminf(olo[a], -bhi[a]);
+                        if (((b.reflect >> (2 * a + 1)) & 1) && bhi[a] > nnf[a] - gd)
+                            ohi[a] = fmaxf(ohi[a], 2.0f * nnf[a] - blo[a]);
+                    }
+                }
                 for (int j = lane; j < nseg; j += 32) {
                     const int ka = lg.first + j;
                     float sl[3], sh[3];
                     seg_box(sc, np, ka, seg_end(ka, lg.n), lg.Rc, sl, sh);
                     bool ov = true;
-                    for (int a = 0; a < 3; ++a) ov = ov && (sh[a] >= blo[a] && sl[a] <= bhi[a]);
+                    for (int a = 0; a < 3; ++a) ov = ov && (sh[a] >= olo[a] && sl[a] <= ohi[a]);
                     if (ov) {
                         jlo = min(jlo, j);
                         jhi = max(jhi, j);
@@ -2444,6 +2594,8 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                     }
                 }
             }
+            // mirror images beyond reflecting faces within reach of this brick
+            if constexpr (REFL) nsupp += d_images_phase<T, WP, BZ, FX>(g, b, sc, p, status, sm, ne, B0, B1, B2, fsh);
             __syncthreads();
             if (WP) {
                 for (int e = 0; e < ne; ++e) {
@@ -2737,6 +2889,22 @@ __global__ void __launch_bounds__(SPREAD_THREADS) k_bweights(GridC g, BeamsC b, 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
     d_brick<T, true, BZ, false>(g, b, sc, p, status, (int)blockIdx.x, sm);
+}
+
+// the two brick passes with the kernel reflected at grid faces (ghost cells)
+template <typename T, int BZ>
+__global__ void __launch_bounds__(SPREAD_THREADS) k_spread_refl(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
+                                                                int *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
+    d_brick<T, false, BZ, false, true>(g, b, sc, p, status, (int)blockIdx.x, sm);
+}
+template <typename T, int BZ>
+__global__ void __launch_bounds__(SPREAD_THREADS) k_bweights_refl(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
+                                                                  int *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
+    d_brick<T, true, BZ, false, true>(g, b, sc, p, status, (int)blockIdx.x, sm);
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_totals(GridC g, BeamsC b, Scratch<T> sc, double *totals) {

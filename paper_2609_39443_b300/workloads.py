@@ -242,6 +242,45 @@ def make_canopy(seed: int = 0, eps_cells: float = 2.0, *, nx=256, ny=128, nz=128
                     meta={"eps_cells": eps_cells})
 
 
+def make_walls(seed: int = 0, *, nx=40, ny=36, nz=30, h=0.01, precision="fp32") -> Workload:
+    """Lines against the grid faces, for the kernel reflected at walls:
+    - a stem rooted on the bed in the x- / y- corner;
+    - a stem rooted on the bed next to the y- face;
+    - a horizontal line along the x+ face;
+    - an arc under the top face near y+;
+    - a single point in the x+ / y+ / z+ corner.
+    Every node lies inside the grid box.  The flow is uniform plus noise,
+    eps is drawn in [1.5, 2.5] h, and l_s = h / 2."""
+    rng = _rng(seed)
+    grid = GridSpec(nx, ny, nz, h, precision=precision, rho_const=1000.0)
+    Lx, Ly, Lz = nx * h, ny * h, nz * h
+    t = np.linspace(0.0, 1.0, 16)
+    th = np.linspace(0.0, np.pi, 12)
+    lines = [
+        np.stack([h * (0.7 + 2.0 * rng.uniform(0.5, 1.0) * t ** 2), h * (1.1 + rng.uniform(0.0, 1.0) * t),
+                  0.6 * Lz * t]),
+        np.stack([0.5 * Lx + h * rng.uniform(-2.0, 2.0) * t, np.full_like(t, h * rng.uniform(2.0, 3.0)),
+                  0.5 * Lz * t]),
+        np.stack([Lx - h * (1.5 + 0.5 * np.sin(3.0 * t)), 0.2 * Ly + 0.6 * Ly * t, np.full_like(t, 0.5 * Lz)]),
+        np.stack([0.3 * Lx + 4.0 * h * np.cos(th), Ly - h * (2.5 + 1.5 * np.sin(th)), Lz - h * (1.2 + 2.0 * np.sin(th))]),
+        np.array([[Lx - 0.8 * h], [Ly - 1.2 * h], [Lz - 0.9 * h]]),
+    ]
+    for P in lines:
+        assert (P >= 0.0).all() and (P[0] <= Lx).all() and (P[1] <= Ly).all() and (P[2] <= Lz).all()
+    lens = [np.full(P.shape[1], max(float(np.linalg.norm(np.diff(P, axis=1), axis=0).mean()) if P.shape[1] > 1
+                                    else h, 1e-9)) for P in lines]
+    U = rng.normal(0.0, 0.03, size=(3, grid.n_cells))
+    U[0] += 0.3
+    U[1] += 0.05
+    P = np.concatenate(lines, axis=1)
+    Pdot = rng.normal(0.0, 0.01, size=P.shape)
+    eps = rng.uniform(1.5, 2.5) * h
+    beams = _beams_from_lines(lines, lens, d=0.005, cdn=1.2, cdt=0.01, eps=eps, ell_s=0.5 * h)
+    ft = np.float64 if precision == "fp64" else np.float32
+    return Workload(f"walls_{nx}x{ny}x{nz}", grid, beams,
+                    StepInput(U=U.astype(ft), P=P.astype(ft), Pdot=Pdot.astype(ft)))
+
+
 def wave_number(omega: float, depth: float) -> float:
     """Root of the linear dispersion relation omega^2 = g k tanh(k depth)."""
     k = omega * omega / G_ACC
