@@ -70,3 +70,16 @@ def test_batches_refuse_the_reflected_kernel():
             Batch([inst])
     finally:
         inst.close()
+
+
+@pytest.mark.parametrize("bad", ["integrated", "mask", "too_deep"])
+def test_reflection_arguments_are_checked(bad):
+    wl = W.make_walls(2)
+    if bad == "integrated":
+        wl = W.with_reflect(W.with_projection(wl, "integrated"), 16)
+    elif bad == "mask":
+        wl = W.with_reflect(wl, 64)
+    else:                           # 3 eps / h = 4.5 + 1 ghost layers > the 4 cells along x
+        wl = W.with_reflect(W.make_random(9, 4, 12, 12, n_lines=1, eps_cells=(1.5, 1.5), kinds=("stem",)), 1)
+    with pytest.raises(ALError):
+        Instance(wl)
