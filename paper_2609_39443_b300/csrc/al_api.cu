@@ -337,12 +337,13 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
 template <typename T, int BZ>
 static cudaError_t brick_attrs() {
     const int fx = (int)sizeof(al::SpreadSmem<T, BZ, true>), fl = (int)sizeof(al::SpreadSmem<T, BZ, false>);
-    const void *fns[7] = {(const void *)al::k_spread<T, BZ, true>, (const void *)al::k_spread<T, BZ, false>,
+    const void *fns[9] = {(const void *)al::k_spread<T, BZ, true>, (const void *)al::k_spread<T, BZ, false>,
                           (const void *)al::kb_spread<T, BZ>, (const void *)al::k_bweights<T, BZ>,
                           (const void *)al::kb_bweights<T, BZ>, (const void *)al::k_spread_refl<T, BZ>,
-                          (const void *)al::k_bweights_refl<T, BZ>};
-    const int bytes_of[7] = {fx, fl, fx, fl, fl, fl, fl};
-    for (int i = 0; i < 7; ++i) {
+                          (const void *)al::k_bweights_refl<T, BZ>, (const void *)al::kb_spread_refl<T, BZ>,
+                          (const void *)al::kb_bweights_refl<T, BZ>};
+    const int bytes_of[9] = {fx, fl, fx, fl, fl, fl, fl, fl, fl};
+    for (int i = 0; i < 9; ++i) {
         const void *f = fns[i];
         const int bytes = bytes_of[i];
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -685,6 +686,7 @@ struct al_batch_s {
     int occ = 1;                              // CTAs per SM that fit at this brick height
     bool any_segment_weights = false;         // some instance sums weights per segment
     bool any_gauss = false;                   // some instance samples by volume average (warp per point)
+    bool any_reflect = false;                 // some instance reflects its kernel at grid faces
     // subset runs: a ring of pinned host / device work lists
     static constexpr int RING = 8;
     int maxn = 0;
@@ -714,7 +716,6 @@ extern "C" int al_batch_add(al_batch b, al_grid g, const al_step_in *in, const a
     if (b->committed) return AL_ERR_STATE;
     if (!g->loaded) return AL_ERR_STATE;
     if (b->precision >= 0 && b->precision != g->d.precision) return AL_ERR_ARG;
-    if (g->bd.wall_reflect) return AL_ERR_ARG;         // the reflected kernel runs alone only
     for (int a = 0; a < 3; ++a)
         if (!in->U[a] || !out->S[a]) return AL_ERR_ARG;
     if (g->d.has_alpha && !in->alpha) return AL_ERR_ARG;
@@ -741,6 +742,7 @@ static int batch_rebuild_t(al_batch b) {
     std::vector<long long> pre(4 * (size_t)(n + 1), 0);
     b->any_segment_weights = false;
     b->any_gauss = false;
+    b->any_reflect = false;
     b->cnt_pts.assign(n, 0); b->cnt_lines.assign(n, 0); b->cnt_bricks.assign(n, 0);
     for (int q = 0; q < n; ++q) {
         const bool used = b->grids[q] != nullptr;
@@ -750,6 +752,7 @@ static int batch_rebuild_t(al_batch b) {
             h[q].g.smode = 0;                                // batches always gather
             if (h[q].g.wmode != 0) b->any_segment_weights = true;
             if (h[q].b.sample_mode == AL_SAMPLE_GAUSS) b->any_gauss = true;
+            if (h[q].b.reflect) b->any_reflect = true;
             b->cnt_pts[q] = b->grids[q]->n_points;
             b->cnt_lines[q] = b->grids[q]->n_lines;
             b->cnt_bricks[q] = h[q].g.nbrick;
@@ -835,6 +838,11 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
             case 16: kb_bweights<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, false>), st>>>(I, sel, pb, n); break;
             default: kb_bweights<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, false>), st>>>(I, sel, pb, n); break;
             }
+            if (b->any_reflect) switch (b->bz) {
+            case 4: kb_bweights_refl<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, false>), st>>>(I, sel, pb, n); break;
+            case 16: kb_bweights_refl<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, false>), st>>>(I, sel, pb, n); break;
+            default: kb_bweights_refl<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, false>), st>>>(I, sel, pb, n); break;
+            }
         }
         kb_normalise<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
     }
@@ -844,6 +852,11 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
         case 4: kb_spread<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, true>), st>>>(I, sel, pb, n); break;
         case 16: kb_spread<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, true>), st>>>(I, sel, pb, n); break;
         default: kb_spread<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, true>), st>>>(I, sel, pb, n); break;
+        }
+        if (b->any_reflect) switch (b->bz) {
+        case 4: kb_spread_refl<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, false>), st>>>(I, sel, pb, n); break;
+        case 16: kb_spread_refl<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, false>), st>>>(I, sel, pb, n); break;
+        default: kb_spread_refl<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, false>), st>>>(I, sel, pb, n); break;
         }
     }
     kb_totals<T><<<std::max(1, std::min(n, 1024)), 256, 0, st>>>(I, sel, n);
@@ -879,6 +892,7 @@ static int batch_assign_t(al_batch b, int slot, al_grid g, const al_step_in *in,
     if (g) { b->ins[slot] = *in; b->outs[slot] = *out; }
     if (g && h->g.wmode != 0) b->any_segment_weights = true;
     if (g && g->bd.sample_mode == AL_SAMPLE_GAUSS) b->any_gauss = true;
+    if (g && g->bd.wall_reflect) b->any_reflect = true;
     b->cnt_pts[slot] = g ? g->n_points : 0;
     b->cnt_lines[slot] = g ? g->n_lines : 0;
     b->cnt_bricks[slot] = g ? h->g.nbrick : 0;
@@ -892,7 +906,6 @@ extern "C" int al_batch_assign(al_batch b, int slot, al_grid g, const al_step_in
     if (slot < 0 || slot >= b->n) return AL_ERR_ARG;
     if (g) {
         if (!in || !out || !g->loaded || g->d.precision != b->precision) return AL_ERR_ARG;
-        if (g->bd.wall_reflect) return AL_ERR_ARG;     // the reflected kernel runs alone only
         for (int a = 0; a < 3; ++a)
             if (!in->U[a] || !out->S[a]) return AL_ERR_ARG;
         if (g->d.has_alpha && !in->alpha) return AL_ERR_ARG;

@@ -3019,12 +3019,27 @@ __global__ void __launch_bounds__(SPREAD_THREADS) kb_spread(const Inst<T> *I, co
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
         const int q = owner(pre, n, item);
         const Inst<T> &x = I[AL_SEL(q)];
+        if (x.b.reflect) continue;                   // kb_spread_refl takes these
         if (x.g.fx)
             d_brick<T, false, BZ, true>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]),
                                         *reinterpret_cast<SpreadSmem<T, BZ, true> *>(smem_raw));
         else
             d_brick<T, false, BZ, false>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]),
                                          *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw));
+        __syncthreads();
+    }
+}
+template <typename T, int BZ>
+__global__ void __launch_bounds__(SPREAD_THREADS) kb_spread_refl(const Inst<T> *I, const int *sel,
+                                                                 const long long *pre, int n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
+    const long long total = pre[n];
+    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+        const int q = owner(pre, n, item);
+        const Inst<T> &x = I[AL_SEL(q)];
+        if (!x.b.reflect) continue;
+        d_brick<T, false, BZ, false, true>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]), sm);
         __syncthreads();
     }
 }
@@ -3037,7 +3052,23 @@ __global__ void __launch_bounds__(SPREAD_THREADS) kb_bweights(const Inst<T> *I, 
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
         const int q = owner(pre, n, item);
         const Inst<T> &x = I[AL_SEL(q)];
+        if (x.b.reflect) continue;                   // kb_bweights_refl takes these
         d_brick<T, true, BZ, false>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]), sm);
+        __syncthreads();
+    }
+}
+// the same for the instances whose kernel is reflected at grid faces
+template <typename T, int BZ>
+__global__ void __launch_bounds__(SPREAD_THREADS) kb_bweights_refl(const Inst<T> *I, const int *sel,
+                                                                   const long long *pre, int n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
+    const long long total = pre[n];
+    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+        const int q = owner(pre, n, item);
+        const Inst<T> &x = I[AL_SEL(q)];
+        if (!x.b.reflect) continue;
+        d_brick<T, true, BZ, false, true>(x.g, x.b, x.sc, x.p, x.status, (int)(item - pre[q]), sm);
         __syncthreads();
     }
 }

@@ -2,7 +2,8 @@
 kernel Sec. 6 proposes, read as a mirror) on the GPU against the FP64
 oracle: lines against faces, edges and corners in both precisions, the
 plain cantilever and a small canopy rooted on a reflecting bed, no change
-for lines out of reach of the reflecting faces, and batches refusing it."""
+for lines out of reach of the reflecting faces, and reflected instances
+in a batch equal to each alone."""
 import numpy as np
 import pytest
 
@@ -63,13 +64,34 @@ def test_faces_out_of_reach_change_nothing():
         np.testing.assert_array_equal(outs[0][k], outs[1][k], err_msg=k)
 
 
-def test_batches_refuse_the_reflected_kernel():
-    inst = Instance(W.with_reflect(W.make_walls(1), 63))
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_with_reflected_instances_equals_alone(use_graph):
+    """Reflected and plain instances in one batch: each gives the bits it
+    gives alone (the reflected ones run in their own batched kernels)."""
+    import torch
+    wls = [W.with_reflect(W.make_walls(11), 63), W.make_walls(12),
+           W.with_reflect(W.make_canopy(4, 2.0, nx=64, ny=48, nz=64, n_sx=3, n_sy=3, n_cv=24, height=0.12),
+                          W.REFLECT_Z_LO)]
+    alone = [Instance(w) for w in wls]
+    inb = [Instance(w) for w in wls]
+    batch = Batch(inb, use_graph=use_graph)
     try:
-        with pytest.raises(ALError):
-            Batch([inst])
+        for _ in range(2):
+            for a in alone:
+                a.status.zero_()
+                a.step()
+            for x in inb:
+                x.status.zero_()
+            batch.run()
+            torch.cuda.synchronize()
+            for w, a, x in zip(wls, alone, inb):
+                for k in ("S", "F", "totals", "status"):
+                    np.testing.assert_array_equal(getattr(a, k).cpu().numpy(), getattr(x, k).cpu().numpy(),
+                                                  err_msg=f"{w.name} {k}")
     finally:
-        inst.close()
+        batch.close()
+        for x in alone + inb:
+            x.close()
 
 
 @pytest.mark.parametrize("bad", ["integrated", "mask", "too_deep"])
