@@ -394,11 +394,13 @@ __device__ bool gauss_avg(const GridC &g, C epsc, const S *const *f, int ncomp, 
     const long long nxy = (long long)g.nx * g.ny;
     C acc[4] = {(C)0, (C)0, (C)0, (C)0}, sw = (C)0;
     if constexpr (LANES > 1) {
-        // a warp: the rows (j, k) that reach the sphere, two per round (a
-        // half-warp each), 16 lanes along x, so a lane's x and dx^2 stay fixed
-        // over a sweep and only cells inside the sphere are read
-        const int half = (int)((threadIdx.x & 31) >> 4), xl = (int)(threadIdx.x & 15);
-        const C cy = (uh[1] - (C)0.5) + (C)ul[1];
+        // a warp: per layer, lane r sizes row r's run of cells on the chord of
+        // the sphere's disc (widened by a cell on each side; the r^2 test
+        // decides), a scan places the runs end to end, and the lanes take 32
+        // consecutive cells at a time, so only cells near the sphere are read
+        const int lane = (int)(threadIdx.x & 31);
+        const C cy = (uh[1] - (C)0.5) + (C)ul[1], cx = (uh[0] - (C)0.5) + (C)ul[0];
+        const int xlo = lo[0], xhi = lo[0] + bn[0] - 1;
         for (int k = 0; k < bn[2]; ++k) {
             const int ck = lo[2] + k;
             const C dz = (((C)ck + (C)0.5) - uh[2]) - (C)ul[2];
@@ -409,22 +411,47 @@ __device__ bool gauss_avg(const GridC &g, C epsc, const S *const *f, int ncomp, 
             int j0 = (int)tfloor(cy - dyr), j1 = (int)tfloor(cy + dyr) + 1;
             j0 = j0 < lo[1] ? lo[1] : j0;
             j1 = j1 > lo[1] + bn[1] - 1 ? lo[1] + bn[1] - 1 : j1;
-            for (int x0 = 0; x0 < bn[0]; x0 += 16) {
-                const int ix = x0 + xl, ci = lo[0] + ix;
-                const bool xin = ix < bn[0];
-                const C dx = (((C)ci + (C)0.5) - uh[0]) - (C)ul[0];
-                const C dx2 = dx * dx;
-                for (int jb = j0; jb <= j1; jb += 2) {
-                    const int cj = jb + half;
+            for (int r0 = j0; r0 <= j1; r0 += 32) {
+                int rcnt = 0, rx0 = 0;
+                const int cjr = r0 + lane;
+                if (cjr <= j1) {
+                    const C dy = (((C)cjr + (C)0.5) - uh[1]) - (C)ul[1];
+                    const C q = R2 - dz2 - dy * dy;
+                    if (q >= (C)0) {
+                        const C hw = tsqrt(q);
+                        int xa = (int)tfloor(cx - hw) - 1, xb = (int)tfloor(cx + hw) + 1;
+                        xa = xa < xlo ? xlo : xa;
+                        xb = xb > xhi ? xhi : xb;
+                        rcnt = xb >= xa ? xb - xa + 1 : 0;
+                        rx0 = xa;
+                    }
+                }
+                int rinc = rcnt;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, rinc, o);
+                    if (lane >= o) rinc += v;
+                }
+                const int ncell = __shfl_sync(0xffffffffu, rinc, 31);
+                for (int q0 = 0; q0 < ncell; q0 += 32) {
+                    const int qc = q0 + lane;
+                    int r = 0;                           // rows whose runs end at or before qc
+#pragma unroll
+                    for (int st = 16; st > 0; st >>= 1) {
+                        const int v = __shfl_sync(0xffffffffu, rinc, r + st - 1);
+                        if (v <= qc) r += st;
+                    }
+                    const int cb = __shfl_sync(0xffffffffu, rinc - rcnt, r);
+                    const int ci = __shfl_sync(0xffffffffu, rx0, r) + (qc - cb), cj = r0 + r;
+                    const C dx = (((C)ci + (C)0.5) - uh[0]) - (C)ul[0];
                     const C dy = (((C)cj + (C)0.5) - uh[1]) - (C)ul[1];
-                    const C r2 = dx2 + (dy * dy + dz2);
-                    if (xin && cj <= j1 && r2 <= R2) {
+                    const C r2 = dx * dx + (dy * dy + dz2);
+                    if (qc < ncell && r2 <= R2) {
                         const C w = Tr<C>::ex2(-r2 * l2ie2);
                         const long long idx = ci + (long long)g.nx * cj + nxy * ck;
                         sw += w;
-                        for (int q = 0; q < ncomp; ++q) {
-                            const S *F = f[q], *F2 = f2 ? f2[q] : nullptr;
-                            acc[q] += w * AL_FV(F, F2, idx);
+                        for (int qq = 0; qq < ncomp; ++qq) {
+                            const S *F = f[qq], *F2 = f2 ? f2[qq] : nullptr;
+                            acc[qq] += w * AL_FV(F, F2, idx);
                         }
                     }
                 }
