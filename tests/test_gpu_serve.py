@@ -11,10 +11,13 @@ from paper_2609_39443_b300.serve import BatchServer, Sim, poisson_arrivals
 pytestmark = pytest.mark.gpu
 
 
-def test_served_mix_equals_each_simulation_alone():
+@pytest.mark.parametrize("reflect", [False, True], ids=["truncated", "reflected-bed"])
+def test_served_mix_equals_each_simulation_alone(reflect):
     import torch
     from paper_2609_39443_b300.al import Instance
     wls = W.make_batched(31, 6, max_cells=64 * 48 * 40)
+    if reflect:                     # every other simulation reflects its kernel at the bed
+        wls = [W.with_reflect(w, W.REFLECT_Z_LO) if i % 2 == 0 else w for i, w in enumerate(wls)]
     sims = [Sim(w, 3) for w in wls]
     budget = int(2.5 * max(s.footprint() for s in sims))     # two or three resident at a time
     arr = poisson_arrivals(sims, 5000.0, seed=11)
