@@ -55,20 +55,22 @@ extern "C" {
 
 #define AL_SAMPLE_TRILINEAR 0  /* trilinear interpolation of cell values   */
 #define AL_SAMPLE_CELL      1  /* value of the single containing cell (the paper's operator) */
-#define AL_PROJ_NEAREST     0
-#define AL_PROJ_INTEGRATED  1
-#define AL_REFLECT_X_LO 1      /* al_beam_desc.wall_reflect bits: faces that reflect the kernel */
-#define AL_REFLECT_X_HI 2
-#define AL_REFLECT_Y_LO 4
-#define AL_REFLECT_Y_HI 8
-#define AL_REFLECT_Z_LO 16
-#define AL_REFLECT_Z_HI 32
 #define AL_SAMPLE_GAUSS     2  /* kernel-weighted volume average: sum_j g_j U_j / sum_j g_j over the
                                   cells whose centre lies within 3 eps of the point, g_j =
                                   exp(-(|C_j - p| / eps)^2) with the line's projection width eps
                                   (Eq. almGaussian; the smooth sampler proposed in Sec. 6); cells
                                   outside the grid do not enter; no centre within 3 eps: the
                                   containing cell */
+
+#define AL_PROJ_NEAREST     0  /* al_beam_desc.proj_mode: the closest segment of each line */
+#define AL_PROJ_INTEGRATED  1  /* ... every segment within 3 eps, integrated 3-D Gaussian */
+
+#define AL_REFLECT_X_LO 1      /* al_beam_desc.wall_reflect bits: faces that reflect the kernel */
+#define AL_REFLECT_X_HI 2
+#define AL_REFLECT_Y_LO 4
+#define AL_REFLECT_Y_HI 8
+#define AL_REFLECT_Z_LO 16
+#define AL_REFLECT_Z_HI 32
 
 #define AL_DRAG_DISCRETE 0     /* Eq. almLineForce: |U_r| (C_dn U_n + C_dt U_t)        */
 #define AL_DRAG_SPLIT    1     /* Eq. fext_drag: C_dn |U_n| U_n + C_dt |U_t| U_t        */
