@@ -105,3 +105,25 @@ def test_reflection_arguments_are_checked(bad):
         wl = W.with_reflect(W.make_random(9, 4, 12, 12, n_lines=1, eps_cells=(1.5, 1.5), kinds=("stem",)), 1)
     with pytest.raises(ALError):
         Instance(wl)
+
+
+def test_reflection_from_both_faces_of_a_narrow_grid():
+    """A grid only a few kernel widths across: cells near both faces of an
+    axis take images across each (three choices per axis, up to 26 images
+    at once), with ghosts as deep as the grid allows."""
+    from paper_2609_39443_b300.workloads import GridSpec, StepInput, Workload, _beams_from_lines
+    h = 0.01
+    g = GridSpec(10, 9, 8, h, precision="fp64", rho_const=1000.0)
+    rng = np.random.default_rng(3)
+    t = np.linspace(0.0, 1.0, 7)
+    lines = [np.stack([h * (2.0 + 5.0 * t), h * (4.5 + 0.5 * np.sin(4 * t)), h * (1.0 + 6.0 * t)]),
+             np.stack([h * (8.5 - 2.0 * t), h * (1.0 + 7.0 * t), np.full_like(t, 4.2 * h)])]
+    U = rng.normal(0.0, 0.05, size=(3, g.n_cells))
+    U[0] += 0.2
+    P = np.concatenate(lines, axis=1)
+    beams = _beams_from_lines(lines, [np.full(7, h), np.full(7, h)], d=0.004, cdn=1.2, cdt=0.01, eps=1.5 * h,
+                              ell_s=0.5 * h)
+    wl = W.with_reflect(Workload("narrow", g, beams, StepInput(U=U, P=P, Pdot=rng.normal(0, 0.01, P.shape))), 63)
+    g_out, o = run_gpu(wl), oracle.sample_drag_spread(wl)
+    compare(wl, g_out, o, label="narrow grid, all faces")
+    assert g_out["status"][ST_SUPPORT] == oracle.count_support(wl.grid, wl.beams, wl.step.P)
