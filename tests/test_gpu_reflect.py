@@ -127,3 +127,13 @@ def test_reflection_from_both_faces_of_a_narrow_grid():
     g_out, o = run_gpu(wl), oracle.sample_drag_spread(wl)
     compare(wl, g_out, o, label="narrow grid, all faces")
     assert g_out["status"][ST_SUPPORT] == oracle.count_support(wl.grid, wl.beams, wl.step.P)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_reflection_with_volume_average_and_inertia(prec):
+    """The variants compose: the Gaussian volume-average sampler and the
+    inertia term at the points, the kernel reflected at every face in the
+    projection."""
+    wl = W.with_reflect(W.with_sample_mode(W.with_inertia(W.make_walls(13, precision=prec), 14), "gauss"), 63)
+    g, o = run_gpu(wl), oracle.sample_drag_spread(wl)
+    compare(wl, g, o, label=f"walls gauss inertia reflected {prec}")
