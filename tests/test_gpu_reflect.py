@@ -137,3 +137,16 @@ def test_reflection_with_volume_average_and_inertia(prec):
     wl = W.with_reflect(W.with_sample_mode(W.with_inertia(W.make_walls(13, precision=prec), 14), "gauss"), 63)
     g, o = run_gpu(wl), oracle.sample_drag_spread(wl)
     compare(wl, g, o, label=f"walls gauss inertia reflected {prec}")
+
+
+def test_reflected_bed_full_canopy():
+    """The full canopy (256x128x128, 400 stems) with a reflecting bed, in the
+    options the bench uses for it, against the oracle."""
+    wl = W.with_reflect(W.make_canopy(0, 2.0), W.REFLECT_Z_LO)
+    inst = Instance(wl)
+    inst.autotune()
+    g = run_gpu(wl, inst=inst)
+    inst.close()
+    o = oracle.sample_drag_spread(wl)
+    compare(wl, g, o, label="canopy reflected bed")
+    assert g["status"][ST_SUPPORT] == oracle.count_support(wl.grid, wl.beams, wl.step.P)
