@@ -1085,6 +1085,7 @@ struct WSeg {
     T m0[3], m1[3];
     bool has_lo, has_hi;
     T R2, gr, ie2, eta0;
+    T gsb;                        // guard band of the bisector tests, for the farthest cell of the box
     double eps;
     int integ;                    // segment-integrated kernel (projection variant, lines of >= 2 nodes)
     T epsc;                       // eps in cells
@@ -1368,7 +1369,7 @@ __device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const Gri
     }
     if (regular) {
         if (c.has_lo) {
-            const T sg = dot_r(x, c.m0), gs = Tr<T>::gsig(tsqrt(norm2_r(x)));
+            const T sg = dot_r(x, c.m0), gs = c.gsb;
             bool pos;
             if (sg > gs) pos = true;
             else if (sg < -gs) pos = false;
@@ -1376,7 +1377,7 @@ __device__ __forceinline__ void w_cell(const WSeg<T> &c, const T C[3], const Gri
             if (!pos) return;
         }
         if (c.has_hi) {
-            const T sg = dot_r(y, c.m1), gs = Tr<T>::gsig(tsqrt(norm2_r(y)));
+            const T sg = dot_r(y, c.m1), gs = c.gsb;
             bool pos;
             if (sg > gs) pos = true;
             else if (sg < -gs) pos = false;
@@ -1555,6 +1556,11 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
         c.D[a] = sc.segD[a * np + k];
     }
     c.il2 = sc.segIl2[k];
+    // every cell of the segment's box lies within |D| + sqrt(3) (3 eps + 0.01)
+    // cells of either node, so one band, taken at that distance, covers the
+    // rounding of every bisector test of the segment (a wider band only sends
+    // more near-plane cells to the exact re-decision)
+    c.gsb = Tr<T>::gsig(tsqrt(c.D[0] * c.D[0] + c.D[1] * c.D[1] + c.D[2] * c.D[2]) + (T)1.75 * ((T)lg.Rc + (T)1));
     c.R2 = lgc<T>(lg.R2c, lg.R2f); c.gr = Tr<T>::grr(c.R2); c.ie2 = lgc<T>(lg.inv_eps2c_l2, lg.ie2f);
     c.eta0 = lgc<T>(lg.eta0, lg.eta0f);
     const int nn[3] = {g.nx, g.ny, g.nz};
