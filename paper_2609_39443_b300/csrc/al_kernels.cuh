@@ -1681,6 +1681,7 @@ struct SpreadSmem {
     T D[3][NN];                  // segment vectors
     T Il2[NN];
     float Tau[NN];               // tan(theta_k / 2) at the nodes (0 at the line's ends)
+    T Ls[NN];                    // length |D| of the segment starting at the node, in cells
     union {
         struct {
             T Fh[3][NN];         // spread: f^ at the nodes
@@ -2318,6 +2319,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                 }
                 sm.Il2[s] = sc.segIl2[kn];
                 sm.Tau[s] = sc.nodeTau[kn];
+                sm.Ls[s] = (T)1 / tsqrt(sc.segIl2[kn]);
                 if (WP) {
                     sm.u.wq[s] = 0ull;
                 } else {
@@ -2520,10 +2522,12 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                                         const int sl = base + (j - jlo);
                                         T sr, sc0, rr;
                                         seg_foot_raw(sm, sl, C, sr, sc0, rr);
-                                        const T il = tsqrt(sm.Il2[sl]), r = tsqrt(rr);
-                                        const T band = Tr<T>::gsig(r + (T)1 / il);
-                                        const bool lo_ok = j == jlo || sr > (r * (T)sm.Tau[sl] + band) * il;
-                                        const bool hi_ok = j == jhi || (T)1 - sr > (r * (T)sm.Tau[sl + 1] + band) * il;
+                                        // distances along the segment in cells (its length staged
+                                        // per node, so no root or division per pair)
+                                        const T L = sm.Ls[sl], r = tsqrt(rr);
+                                        const T band = Tr<T>::gsig(r + L);
+                                        const bool lo_ok = j == jlo || sr * L > r * (T)sm.Tau[sl] + band;
+                                        const bool hi_ok = j == jhi || ((T)1 - sr) * L > r * (T)sm.Tau[sl + 1] + band;
                                         if (lo_ok && hi_ok) { fast = true; s = sc0; r2 = rr; }
                                     }
                                     if (!fast) {
