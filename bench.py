@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark of one coupling step of the actuator-line transfer operators.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload canopy|flume|plain]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload flume|canopy|plain|batched|serve]
                     [--eps 2.0] [--impl ours|reference]
 
 A step is one call of al_sample_drag_spread (sampling, Morison line force,
@@ -14,12 +14,14 @@ Prints ONE JSON line (rank 0).  Throughput `value` is coupling steps/s over
 all ranks, device-timed with CUDA events; L2 is flushed (256 MiB write)
 between timed steps, outside the events.  `e2e` is the same metric through
 the public API with pinned host buffers, host<->device copies inside the
-timed region.  `roofline` reports the longer of the two passes over the
-(cell, line) pairs: the projection (k_spread: its algorithmic bytes, the
-dense S write plus the per-node data, over its event-timed duration,
-against the measured HBM copy bandwidth) or the weights pass (k_weights:
-its algorithmic FP32 operations per pair times the pairs, against the FP32
-FMA peak of the SMs at their maximum clock).
+timed region.  `roofline` reports the projection kernel k_spread against
+the measured HBM copy bandwidth (its algorithmic bytes: the dense S write
+plus the per-node data, over its event-timed duration); it also carries the
+whole step's fraction (the step's algorithmic bytes over the step time) and
+the weights pass against the FP32 FMA peak of the SMs (its algorithmic
+operations per (cell, line) pair times the pairs).  The default workload is
+the wave flume (1024 x 256 x 128 cells, 4000 stems of 80 CVs), the largest
+single-GPU configuration.
 """
 import argparse
 import hashlib
@@ -44,7 +46,7 @@ def _args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="canopy", choices=["canopy", "flume", "plain", "batched", "serve"])
+    ap.add_argument("--workload", default="flume", choices=["flume", "canopy", "plain", "batched", "serve"])
     ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
     ap.add_argument("--sims", type=int, default=64, help="serve: number of simulations")
     ap.add_argument("--sim-steps", type=int, default=20, help="serve: steps per simulation")
@@ -176,6 +178,21 @@ def _algorithmic_bytes(wl):
     normalised force (staged once per brick that needs it; counted once)."""
     es = 8 if wl.grid.precision == "fp64" else 4
     return 3 * es * wl.grid.n_cells + wl.beams.n_points * (3 * es + 3 * es)
+
+
+def _step_algorithmic_bytes(wl):
+    """Bytes one whole coupling step must move: the spread's (dense S write,
+    per-node position and normalised force), the field stencils of the two
+    samples of every point (8 cells x (3 velocity components + alpha) each,
+    an upper bound that ignores sharing between points), and per point its
+    velocity and CV length in, its load out, the relaxation state read and
+    written and the FP64 nodal weight."""
+    es = 8 if wl.grid.precision == "fp64" else 4
+    ncomp = 4 if wl.grid.has_alpha else 3
+    npt = wl.beams.n_points
+    stencils = 2 * 8 * ncomp * es * npt
+    points = npt * (3 * es + 8 + 3 * es + 2 * 3 * es + 8)
+    return _algorithmic_bytes(wl) + stencils + points
 
 
 def _cpu_baseline(wl, budget_s=12.0):
@@ -396,19 +413,22 @@ def run_ours(a):
     achieved = alg / spread_s / 1e9
     traffic = _traffic(wl.name, options=tuned)
     weights_s = ph[PHASES.index("weights")] / 1e3
-    if weights_s > spread_s and tuned["weights"] == "segment":
-        flop = supp * FLOP_PER_PAIR
-        a_t = flop / weights_s / 1e12
-        roofline = {"bound": "alu", "kernel": "k_weights", "achieved": a_t, "peak": ALU_PEAK_TFLOPS,
-                    "peak_kind": "derived (148 SMs x 128 FP32 lanes x FMA x 2.032 GHz)", "unit": "TFLOP/s",
-                    "frac": a_t / ALU_PEAK_TFLOPS, "algorithmic_flop": flop,
-                    "traffic": _traffic(wl.name, "k_weights", tuned),
-                    "k_spread": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                 "frac": achieved / peak, "algorithmic_bytes": alg}}
-    else:
-        roofline = {"bound": "hbm", "kernel": "k_spread", "achieved": achieved, "peak": peak,
-                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                    "algorithmic_bytes": alg, "traffic": traffic}
+    step_alg = _step_algorithmic_bytes(wl)
+    step_gbs = step_alg / (total_s / a.steps) / 1e9 * world
+    flop = supp * FLOP_PER_PAIR
+    w_tf = flop / weights_s / 1e12 if weights_s > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": "k_spread", "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "algorithmic_bytes": alg, "traffic": traffic,
+                "step": {"bound": "hbm", "achieved": step_gbs, "peak": peak, "unit": "GB/s",
+                         "frac": step_gbs / peak, "algorithmic_bytes": step_alg,
+                         "ms": 1e3 * total_s / a.steps},
+                "weights_pass": {"bound": "alu", "kernel": "k_weights" if tuned["weights"] == "segment" else "k_bweights",
+                                 "achieved": w_tf, "peak": ALU_PEAK_TFLOPS,
+                                 "peak_kind": "derived (148 SMs x 128 FP32 lanes x FMA x 2.032 GHz)",
+                                 "unit": "TFLOP/s", "frac": w_tf / ALU_PEAK_TFLOPS, "algorithmic_flop": flop,
+                                 "ms": 1e3 * weights_s,
+                                 "traffic": _traffic(wl.name, "k_weights", tuned)}}
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         v, cores, sample = _cpu_baseline(wl)
@@ -543,8 +563,24 @@ def rate_seed(rate):
     return int(rate) % 100003
 
 
+def _launch_ranks(n):
+    """`--gpus N` without a torchrun environment: start N ranks on this node
+    through torch.distributed.run (one process per GPU, rendezvous on
+    127.0.0.1) with the same arguments; rank 0 prints the JSON line."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *sys.argv[1:]]
+    env = dict(os.environ, NCCL_DEBUG=os.environ.get("NCCL_DEBUG", "WARN"))
+    return subprocess.call(cmd, env=env)
+
+
 if __name__ == "__main__":
     args = _args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(_launch_ranks(args.gpus))
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":

@@ -86,6 +86,7 @@ extern "C" {
 #define AL_ST_IRREGULAR      7 /* lines projected by exhaustive segment search         */
 #define AL_ST_SUPPORT        8 /* (cell, line) pairs within 3 eps: kernel-cell updates   */
 #define AL_ST_REPLAYED       9 /* bricks that replayed recorded pairs instead of gathering them */
+#define AL_ST_COLUMN        10 /* bricks whose both passes took the column march (AL_OPT_COLUMN) */
 #define AL_STATUS_N         16
 
 /* ---- descriptors ------------------------------------------------------- */
@@ -265,9 +266,26 @@ int al_trace_last(al_grid g, float *ms /* [AL_TRACE_N] */);
  * from the previous step's counts, and the gather replays the records of
  * its brick instead of recomputing those pairs.  A brick whose pairs did not
  * fit its region (the first step, a beam that moved into it) is recomputed,
- * with the same bits.  The record arena is allocated by al_load_beams from
- * the lines' length and kernel width (16 bytes per pair in FP32, 24 in FP64). */
+ * with the same bits.  The record arena (16 bytes per pair in FP32, 24 in
+ * FP64, sized from the lines' length and kernel width) is held only while
+ * records can be used: al_load_beams, al_set_option (AL_OPT_WEIGHTS,
+ * AL_OPT_RECORD) and al_autotune allocate it when the options turn records
+ * on (segment weights with AL_OPT_RECORD = 1, or AL_PROJ_INTEGRATED with
+ * AL_OPT_RECORD = 1) and free it when they turn them off, synchronising the
+ * device; set these options before adding the instance to a batch. */
 #define AL_OPT_RECORD       5
+/* AL_OPT_COLUMN (default 1; 0: off): the column march of FP32 instances
+ * with the nearest-segment projection, no reflecting face and the gather.
+ * A line whose segments all climb (D_z / |D| >= 0.8 in cell units) and
+ * whose bisector signs are certified monotone over a brick's candidate
+ * segments (k_lines) takes it; a brick whose candidate lines all take it
+ * computes both passes by marching each column up the brick: the closest
+ * segment of a cell only moves up the line as z grows, one bisector test
+ * per cell instead of a search, with the same exact near-tie decisions as
+ * the brick passes.  Other bricks take the brick passes for both passes
+ * (the weights option then applies to their other lines).  The results
+ * agree within the parity tolerances either way. */
+#define AL_OPT_COLUMN       6
 int al_set_option(al_grid g, int option, int value);
 
 /* Autotuner: runs the caller's step (same in/out as al_sample_drag_spread)
@@ -282,6 +300,13 @@ int al_autotune(al_grid g, const al_step_in *in, const al_step_out *out, int tri
 
 /* Sizes of an instance: cells and points. */
 int al_sizes(al_grid g, long long *n_cells, long long *n_points, int *n_lines);
+
+/* Device bytes the library holds for the instance: per-grid scratch
+ * (al_create_grid), per-point scratch and line table (al_load_beams) and the
+ * record arena while records are on (AL_OPT_RECORD).  The caller's fields,
+ * points and outputs are not included.  An admission controller adds them
+ * to this figure to bound what a resident instance takes. */
+int al_footprint(al_grid g, unsigned long long *bytes);
 
 /* Quasi-static reconstruction of the beam side (the structural check of the
  * wave-flume case, Sec. 7): each node's load F_k (per-CV line force, e.g.
@@ -353,19 +378,28 @@ int al_batch_set_option(al_batch b, int option, int value);
 int al_batch_autotune(al_batch b, int trials, void *stream, int *choice);
 
 /* ---- line forces without device allocation ----------------------------- */
-/* The paper has no counterpart of this entry point: it exists for callers
- * that cannot allocate device memory where they need the line forces (host
- * code running while a CUDA graph is captured, an application whose
- * allocator forbids allocation after start-up, a plug-in whose host owns all
- * device memory).  It computes F = f L for every actuator point exactly as
- * al_sample_drag_spread does (sampling, upstream direction, Morison drag,
- * F[3] overwritten), relaxed against f_prev (device, 3 arrays of N_p) when
- * f_prev is non-NULL and un-relaxed (f = f*) when it is NULL, without an
- * al_grid and without allocating: no cudaMalloc, no cudaFree, nothing else
- * that allocates device memory.  All buffers are the caller's (DEVICE
- * pointers as in al_step_in; P_spread and the projection are not used).
+/* The paper has no counterpart of this entry point.  It exists for callers
+ * that cannot allocate device memory where they need the line forces: code
+ * running under an allocator that forbids device allocation after start-up
+ * (a fixed, pre-reserved pool; a real-time loop that cannot take an
+ * allocation's latency or its possible implicit synchronisation), or a
+ * plug-in whose host application owns all device memory and hands it only
+ * buffers.  It computes F = f L for every actuator point with the point
+ * evaluation of al_sample_drag_spread (sampling, upstream direction, Morison
+ * drag, and the inertia term when beams->cm_n / cm_t are given, with
+ * in->U_prev, in->Pddot and in->dt as in al_step_in; F[3] overwritten),
+ * relaxed against f_prev (device, 3 arrays of N_p) when f_prev is non-NULL
+ * and un-relaxed (f = f*) when it is NULL, without an al_grid and without
+ * allocating: no cudaMalloc, no cudaFree, nothing else that allocates device
+ * memory.  All buffers are the caller's (DEVICE pointers as in al_step_in;
+ * P_spread and the projection are not used, so proj_mode and wall_reflect
+ * are only checked).  The descriptors are checked by the rules of
+ * al_create_grid and al_load_beams (AL_ERR_ARG); AL_SAMPLE_GAUSS is not
+ * offered here (AL_ERR_ARG): it needs an al_grid.  A line set without points
+ * (n_lines = 0, line_off may then be NULL) returns AL_OK after zeroing the
+ * shared counters (when status is NULL).
  * The host arrays of `beams` are copied into one fixed __device__ array of
- * about 1 MiB held by every GPU that loads the library until the process
+ * about 1 MiB (1,065,472 bytes) held by every GPU that loads the library until the process
  * exits; lines beyond AL_NOALLOC_MAX_LINES or points beyond
  * AL_NOALLOC_MAX_POINTS are rejected with AL_ERR_CAPACITY.  The first call
  * on each device looks up that array's device address (once, with the
@@ -374,7 +408,8 @@ int al_batch_autotune(al_batch b, int trials, void *stream, int *choice);
  * contents: calls whose work overlaps on the GPU (unordered streams) race,
  * so order them.  status (device int[AL_STATUS_N], optional) is added to as
  * in al_sample_drag_spread; when NULL, counters in the shared array are used
- * (zeroed by the call).  Stream-ordered on `stream`. */
+ * (zeroed by the call).  Stream-ordered on `stream`; a CUDA failure returns
+ * AL_ERR_CUDA with its text in al_last_cuda_error. */
 #define AL_NOALLOC_MAX_POINTS 65536
 #define AL_NOALLOC_MAX_LINES  4096
 int al_line_forces_noalloc(const al_grid_desc *grid, const al_beam_desc *beams, const al_step_in *in,

@@ -20,9 +20,9 @@ AL_OK, AL_ERR_ARG, AL_ERR_CUDA, AL_ERR_OOM, AL_ERR_STATE, AL_ERR_TIMEOUT, AL_ERR
 AL_FP32, AL_FP64 = 0, 1
 AL_STATUS_N = 16
 (ST_PA_OUTSIDE, ST_PS_OUTSIDE, ST_FALLBACK, ST_FALLBACK_ZERO, ST_ZERO_WEIGHT, ST_DEPOSIT_LOST,
- ST_REFINED, ST_IRREGULAR, ST_SUPPORT, ST_REPLAYED) = range(10)
+ ST_REFINED, ST_IRREGULAR, ST_SUPPORT, ST_REPLAYED, ST_COLUMN) = range(11)
 
-OPT_WEIGHTS, OPT_BRICK_Z, OPT_SPREAD_CTAS, OPT_SPREAD, OPT_RECORD = 1, 2, 3, 4, 5
+OPT_WEIGHTS, OPT_BRICK_Z, OPT_SPREAD_CTAS, OPT_SPREAD, OPT_RECORD, OPT_COLUMN = 1, 2, 3, 4, 5, 6
 WEIGHTS_BRICK, WEIGHTS_SEGMENT = 0, 1
 SPREAD_GATHER, SPREAD_SCATTER = 0, 1
 
@@ -79,6 +79,7 @@ def lib():
         L.al_get_state.argtypes = [_vp, _vp, C.POINTER(C.c_int), _vp]
         L.al_set_state.argtypes = [_vp, _vp, C.c_int, _vp]
         L.al_sizes.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
+        L.al_footprint.argtypes = [_vp, C.POINTER(C.c_ulonglong)]
         L.al_beam_quasistatic.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp * 3, _vp * 3,
                                           _vp * 3, _vp]
         L.al_batch_create.argtypes = [C.POINTER(_vp)]
@@ -239,6 +240,12 @@ class Grid:
         check(lib().al_beam_quasistatic(self.h, ei.ctypes.data_as(C.POINTER(C.c_double)), ax, rows[0], rows[1],
                                         rows[2], _stream_ptr(stream)), "al_beam_quasistatic")
 
+    def footprint(self) -> int:
+        """al_footprint: device bytes the library holds for this instance."""
+        b = C.c_ulonglong(0)
+        check(lib().al_footprint(self.h, C.byref(b)), "al_footprint")
+        return int(b.value)
+
     def trace(self, on: bool = True) -> None:
         check(lib().al_trace_enable(self.h, int(bool(on))), "al_trace_enable")
 
@@ -380,14 +387,15 @@ class Batch:
 
 
 def line_forces_noalloc(grid, beams, U, P, Pdot, F, *, alpha=None, tangent=None, f_prev=None, status=None,
-                        stream=None) -> None:
+                        U_prev=None, Pddot=None, dt=0.0, stream=None) -> None:
     """al_line_forces_noalloc: per-CV line loads F (3, N_p) without an
-    al_grid and without device allocation (tensors are the caller's)."""
+    al_grid and without device allocation (tensors are the caller's).  The
+    inertia inputs are used when the beams carry cm_n / cm_t."""
     gd = GridDesc(int(grid.nx), int(grid.ny), int(grid.nz), float(grid.h),
                   (C.c_double * 3)(*map(float, grid.origin)), AL_FP64 if grid.precision == "fp64" else AL_FP32,
                   int(bool(grid.has_alpha)), float(grid.rho1), float(grid.rho2), float(grid.rho_const))
     ba = BeamArrays(beams)
-    sin, _ = step_descriptors(U, P, Pdot, U, F, alpha=alpha, tangent=tangent)
+    sin, _ = step_descriptors(U, P, Pdot, U, F, alpha=alpha, tangent=tangent, U_prev=U_prev, Pddot=Pddot, dt=dt)
     fp = (_vp * 3)(*[_ptr(t) for t in _three(f_prev)]) if f_prev is not None else None
     fo = (_vp * 3)(*[_ptr(t) for t in _three(F)])
     st = C.cast(_ptr(status), C.POINTER(C.c_int)) if status is not None else None

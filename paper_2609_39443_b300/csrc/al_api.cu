@@ -30,10 +30,12 @@ int cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 template <typename P>
-cudaError_t dalloc(P **p, size_t n) {
+cudaError_t dalloc(P **p, size_t n, size_t *acc = nullptr) {
     *p = nullptr;
     if (n == 0) n = 1;
-    return cudaMalloc((void **)p, n * sizeof(P));
+    const cudaError_t e = cudaMalloc((void **)p, n * sizeof(P));
+    if (e == cudaSuccess && acc) *acc += n * sizeof(P);
+    return e;
 }
 
 // brick decomposition of the projection for brick height bz
@@ -64,7 +66,9 @@ struct al_grid_s {
     double *d_d = nullptr, *d_cdn = nullptr, *d_cdt = nullptr, *d_eps = nullptr, *d_ell = nullptr,
            *d_af = nullptr, *d_cvl = nullptr, *d_cmn = nullptr, *d_cmt = nullptr, *d_EI = nullptr;
     std::vector<double> h_EI;         // the stiffnesses last copied to d_EI
-    al_beam_desc bd{};
+    al_beam_desc bd{};                // scalars of the loaded descriptor (its array pointers are not kept)
+    std::vector<int> h_line_off;      // host copies of the line table that size the record arena
+    std::vector<double> h_eps, h_cv_len;
 
     // per-point scratch (element type per precision)
     void *fprev = nullptr, *uhi = nullptr, *segD = nullptr, *segIl2 = nullptr, *nodeM = nullptr,
@@ -87,10 +91,17 @@ struct al_grid_s {
     int *rcnt = nullptr, *rcap = nullptr;   // per brick: records found / region capacity
     long long *roff = nullptr;        // per brick: region start
     int *rplan = nullptr;             // [2] brick height of this / the next step's regions
+    int *cmcnt = nullptr;             // [2] bricks of a step on the column-march / the brick passes
+    int *cmlist = nullptr;            // [2][nbrick_max] those bricks
+    int opt_column = 1;               // AL_OPT_COLUMN
     unsigned long long *rused = nullptr;    // arena taken by the next step's regions
-    void *rec = nullptr;              // record arena (rec_total records)
+    void *rec = nullptr;              // record arena (rec_total records), allocated only while records are used
     long long rec_total = 0;
     int opt_record = 1;
+
+    // device bytes this instance holds (al_footprint): per-grid scratch,
+    // per-point scratch of the loaded lines, record arena
+    size_t grid_bytes = 0, beam_bytes = 0, rec_bytes = 0;
 
     // tracing
     bool trace = false;
@@ -119,6 +130,7 @@ static void free_beams(al_grid g) {
     g->mask = nullptr;
     g->rec = nullptr;
     g->rec_total = 0;
+    g->beam_bytes = g->rec_bytes = 0;
     g->loaded = false;
     g->n_lines = g->n_points = g->mask_words = 0;
 }
@@ -176,15 +188,18 @@ extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
     c.rho1 = d.rho1; c.rho2 = d.rho2; c.rho_const = d.rho_const;
 
     cudaError_t e;
-    if ((e = dalloc(&g->brickSum, 3 * (size_t)g->nbrick_max)) != cudaSuccess ||
-        (e = dalloc(&g->scatSum, 3)) != cudaSuccess ||
-        (e = dalloc(&g->statusInt, AL_STATUS_N)) != cudaSuccess || (e = dalloc(&g->totalsInt, 6)) != cudaSuccess ||
-        (e = dalloc(&g->hasPrev, 1)) != cudaSuccess || (e = dalloc(&g->anyIrr, 1)) != cudaSuccess ||
-        (e = dalloc(&g->smax, 1)) != cudaSuccess || (e = dalloc(&g->anyZero, 1)) != cudaSuccess ||
-        (e = dalloc(&g->rcnt, (size_t)g->nbrick_max)) != cudaSuccess ||
-        (e = dalloc(&g->rcap, (size_t)g->nbrick_max)) != cudaSuccess ||
-        (e = dalloc(&g->roff, (size_t)g->nbrick_max)) != cudaSuccess ||
-        (e = dalloc(&g->rplan, 2)) != cudaSuccess || (e = dalloc(&g->rused, 1)) != cudaSuccess) {
+    size_t *gb = &g->grid_bytes;
+    if ((e = dalloc(&g->brickSum, 3 * (size_t)g->nbrick_max, gb)) != cudaSuccess ||
+        (e = dalloc(&g->scatSum, 3, gb)) != cudaSuccess ||
+        (e = dalloc(&g->statusInt, AL_STATUS_N, gb)) != cudaSuccess || (e = dalloc(&g->totalsInt, 6, gb)) != cudaSuccess ||
+        (e = dalloc(&g->hasPrev, 1, gb)) != cudaSuccess || (e = dalloc(&g->anyIrr, 1, gb)) != cudaSuccess ||
+        (e = dalloc(&g->smax, 1, gb)) != cudaSuccess || (e = dalloc(&g->anyZero, 1, gb)) != cudaSuccess ||
+        (e = dalloc(&g->rcnt, (size_t)g->nbrick_max, gb)) != cudaSuccess ||
+        (e = dalloc(&g->rcap, (size_t)g->nbrick_max, gb)) != cudaSuccess ||
+        (e = dalloc(&g->roff, (size_t)g->nbrick_max, gb)) != cudaSuccess ||
+        (e = dalloc(&g->rplan, 2, gb)) != cudaSuccess || (e = dalloc(&g->rused, 1, gb)) != cudaSuccess ||
+        (e = dalloc(&g->cmcnt, 2, gb)) != cudaSuccess ||
+        (e = dalloc(&g->cmlist, 2 * (size_t)g->nbrick_max, gb)) != cudaSuccess) {
         int rc = cuda_fail(e, "cudaMalloc");
         al_destroy(g);
         return rc;
@@ -193,9 +208,62 @@ extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
     return AL_OK;
 }
 
-extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
-    if (!g || !bp) return AL_ERR_ARG;
-    const al_beam_desc &b = *bp;
+// The record arena of the replayed gather is held only while an instance
+// can use it: segment weights with records on (AL_OPT_WEIGHTS = SEGMENT,
+// AL_OPT_RECORD = 1), or the integrated projection with records on; never
+// with a reflected kernel.  Sized from the lines: the cells within
+// R_c = 3 eps / h of a line of length L_c (cells) number about
+// pi R_c^2 L_c + 4/3 pi R_c^3 plus half the surface; a quarter more, and
+// 4096.  A failed allocation leaves no arena (every brick is then gathered).
+static bool arena_wanted(al_grid g) {
+    if (!g->loaded || g->n_lines == 0 || g->bd.wall_reflect || g->opt_record != 1) return false;
+    return g->bd.proj_mode == AL_PROJ_INTEGRATED || g->gc.wmode == AL_WEIGHTS_SEGMENT;
+}
+static int arena_sync(al_grid g) {
+    const bool want_arena = arena_wanted(g);
+    if (want_arena == (g->rec != nullptr)) return AL_OK;
+    AL_CUDA(cudaDeviceSynchronize());                  // no step may still use the regions
+    if (!want_arena) {
+        cudaFree(g->rec);
+        g->rec = nullptr;
+        g->rec_total = 0;
+        g->rec_bytes = 0;
+    } else {
+        const al_beam_desc &b = g->bd;
+        double est = 0.0;
+        for (int l = 0; l < b.n_lines; ++l) {
+            double L = 0.0;
+            for (int i = g->h_line_off[l]; i < g->h_line_off[l + 1]; ++i) L += g->h_cv_len[i];
+            const double Rc = 3.0 * g->h_eps[l] / g->d.dx, Lc = L / g->d.dx, pi = 3.14159265358979323846;
+            double pairs = pi * Rc * Rc * Lc + 4.0 / 3.0 * pi * Rc * Rc * Rc + pi * Rc * Lc + 2.0 * pi * Rc * Rc + 64.0;
+            const int nl_pts = g->h_line_off[l + 1] - g->h_line_off[l];
+            if (b.proj_mode == AL_PROJ_INTEGRATED && nl_pts >= 2)   // a cell pairs with every segment within 3 eps
+                pairs *= 2.0 * Rc / std::max(Lc / (nl_pts - 1), 0.25) + 2.0;
+            est += pairs;
+        }
+        const size_t rsz = g->d.precision == AL_FP64 ? sizeof(al::Rec<double>) : sizeof(al::Rec<float>);
+        long long want = (long long)(1.25 * est) + 4096;
+        want = std::min<long long>(want, (8ll << 30) / (long long)rsz);       // at most 8 GiB
+        if (cudaMalloc(&g->rec, (size_t)want * rsz) == cudaSuccess) {
+            g->rec_total = want;
+            g->rec_bytes = (size_t)want * rsz;
+        } else {
+            (void)cudaGetLastError();
+            g->rec = nullptr;
+            g->rec_total = 0;
+        }
+    }
+    // regions planned in another arena are void: the next step gathers
+    AL_CUDA(cudaMemset(g->rcap, 0, (size_t)g->nbrick_max * sizeof(int)));
+    AL_CUDA(cudaMemset(g->rplan, 0, 2 * sizeof(int)));
+    return AL_OK;
+}
+
+// Host-side checks of a beam descriptor against a grid (the rules of
+// al_load_beams, shared with al_line_forces_noalloc).  *np_out receives the
+// number of actuator points.
+int al_detail_check_beams(const al_beam_desc &b, const al_grid_desc &gd, int *np_out) {
+    *np_out = 0;
     if (b.n_lines < 0) return AL_ERR_ARG;
     if (b.n_lines > 0 && (!b.line_off || !b.d || !b.cdn || !b.cdt || !b.eps || !b.ell_s || !b.alpha_f))
         return AL_ERR_ARG;
@@ -207,6 +275,8 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     if (b.wall_reflect < 0 || b.wall_reflect > 63) return AL_ERR_ARG;
     if (b.wall_reflect && b.proj_mode != AL_PROJ_NEAREST) return AL_ERR_ARG;
     if (!(b.tau >= 0.0)) return AL_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(b.n_p[a]) || !std::isfinite(b.g_up[a])) return AL_ERR_ARG;
     const double npn = std::sqrt(b.n_p[0] * b.n_p[0] + b.n_p[1] * b.n_p[1] + b.n_p[2] * b.n_p[2]);
     if (!(npn == 0.0 || std::fabs(npn - 1.0) < 1e-9)) return AL_ERR_ARG;
     int np = 0;
@@ -215,10 +285,11 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
         for (int l = 0; l < b.n_lines; ++l) {
             if (b.line_off[l + 1] < b.line_off[l]) return AL_ERR_ARG;
             if (!(b.eps[l] > 0.0) || !(b.ell_s[l] >= 0.0) || !(b.alpha_f[l] > 0.0 && b.alpha_f[l] <= 1.0) ||
-                !(b.d[l] >= 0.0) || !std::isfinite(b.cdn[l]) || !std::isfinite(b.cdt[l]))
+                !(b.d[l] >= 0.0) || !std::isfinite(b.cdn[l]) || !std::isfinite(b.cdt[l]) ||
+                !std::isfinite(b.d[l]) || !std::isfinite(b.ell_s[l]) || !std::isfinite(b.eps[l]))
                 return AL_ERR_ARG;
             // the kernel support 3 eps must span fewer than 2^20 cells
-            if (3.0 * b.eps[l] / g->d.dx > 1048576.0) return AL_ERR_ARG;
+            if (3.0 * b.eps[l] / gd.dx > 1048576.0) return AL_ERR_ARG;
             if (b.cm_n && (!std::isfinite(b.cm_n[l]) || !std::isfinite(b.cm_t[l]))) return AL_ERR_ARG;
         }
         np = b.line_off[b.n_lines];
@@ -226,13 +297,29 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
         if (b.wall_reflect) {                            // one reflection per face: ghosts <= n deep
             double emax = 0.0;
             for (int l = 0; l < b.n_lines; ++l) emax = std::max(emax, b.eps[l]);
-            const double gd = std::ceil(3.0 * emax / g->d.dx) + 1.0;
-            const int nn[3] = {g->d.nx, g->d.ny, g->d.nz};
+            const double gdep = std::ceil(3.0 * emax / gd.dx) + 1.0;
+            const int nn[3] = {gd.nx, gd.ny, gd.nz};
             for (int a = 0; a < 3; ++a)
-                if (((b.wall_reflect >> (2 * a)) & 3) && gd > (double)nn[a]) return AL_ERR_ARG;
+                if (((b.wall_reflect >> (2 * a)) & 3) && gdep > (double)nn[a]) return AL_ERR_ARG;
         }
         for (int i = 0; i < np; ++i)
             if (!(b.cv_len[i] >= 0.0) || !std::isfinite(b.cv_len[i])) return AL_ERR_ARG;
+    }
+    *np_out = np;
+    return AL_OK;
+}
+
+// CUDA failure recorded in the text al_last_cuda_error returns (shared with
+// al_line_forces_noalloc)
+int al_detail_cuda_fail(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+
+extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
+    if (!g || !bp) return AL_ERR_ARG;
+    const al_beam_desc &b = *bp;
+    int np = 0;
+    {
+        const int rc = al_detail_check_beams(b, g->d, &np);
+        if (rc != AL_OK) return rc;
     }
     AL_CUDA(cudaDeviceSynchronize());
     free_beams(g);
@@ -244,10 +331,11 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     const size_t nl = (size_t)b.n_lines;
     cudaError_t e = cudaSuccess;
     auto A = [&](auto **p, size_t n) {
-        if (e == cudaSuccess) e = dalloc(p, n);
+        if (e == cudaSuccess) e = dalloc(p, n, &g->beam_bytes);
     };
     auto AB = [&](void **p, size_t n) {
         if (e == cudaSuccess) e = cudaMalloc(p, (n ? n : 1) * es);
+        if (e == cudaSuccess) g->beam_bytes += (n ? n : 1) * es;
     };
     A(&g->d_line_off, nl + 1);
     A(&g->d_line_of, (size_t)np);
@@ -273,6 +361,9 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
         for (size_t l = 0; l < nl; ++l)
             for (int i = off[l]; i < off[l + 1]; ++i) of[i] = (int)l;
     }
+    g->h_line_off = off;
+    g->h_eps.assign(b.eps, b.eps + nl);
+    g->h_cv_len.assign(b.cv_len, b.cv_len + np);
     AL_CUDA(cudaMemcpy(g->d_line_off, off.data(), (nl + 1) * sizeof(int), cudaMemcpyHostToDevice));
     if (np) {
         AL_CUDA(cudaMemcpy(g->d_line_of, of.data(), np * sizeof(int), cudaMemcpyHostToDevice));
@@ -297,39 +388,13 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     AL_CUDA(cudaMemset(g->anyIrr, 0, sizeof(int)));
     AL_CUDA(cudaMemset(g->smax, 0, sizeof(unsigned int)));
     AL_CUDA(cudaMemset(g->anyZero, 0, sizeof(int)));
-    // record arena for the replayed gather: cells within R_c = 3 eps / h of a
-    // line of length L_c (cells) number about pi R_c^2 L_c + 4/3 pi R_c^3 plus
-    // half the surface; a quarter more, and 4096
-    {
-        double est = 0.0;
-        for (int l = 0; l < b.n_lines; ++l) {
-            double L = 0.0;
-            for (int i = b.line_off[l]; i < b.line_off[l + 1]; ++i) L += b.cv_len[i];
-            const double Rc = 3.0 * b.eps[l] / g->d.dx, Lc = L / g->d.dx, pi = 3.14159265358979323846;
-            double pairs = pi * Rc * Rc * Lc + 4.0 / 3.0 * pi * Rc * Rc * Rc + pi * Rc * Lc + 2.0 * pi * Rc * Rc + 64.0;
-            const int nl_pts = b.line_off[l + 1] - b.line_off[l];
-            if (b.proj_mode == AL_PROJ_INTEGRATED && nl_pts >= 2)   // a cell pairs with every segment within 3 eps
-                pairs *= 2.0 * Rc / std::max(Lc / (nl_pts - 1), 0.25) + 2.0;
-            est += pairs;
-        }
-        const size_t rsz = g->d.precision == AL_FP64 ? sizeof(al::Rec<double>) : sizeof(al::Rec<float>);
-        long long want = b.n_lines > 0 ? (long long)(1.25 * est) + 4096 : 0;
-        want = std::min<long long>(want, (8ll << 30) / (long long)rsz);       // at most 8 GiB
-        if (want > 0 && cudaMalloc(&g->rec, (size_t)want * rsz) == cudaSuccess) {
-            g->rec_total = want;
-        } else {
-            (void)cudaGetLastError();                  // no arena: every brick is gathered
-            g->rec = nullptr;
-            g->rec_total = 0;
-        }
-        AL_CUDA(cudaMemset(g->rcnt, 0, (size_t)g->nbrick_max * sizeof(int)));
-        AL_CUDA(cudaMemset(g->rcap, 0, (size_t)g->nbrick_max * sizeof(int)));
-        AL_CUDA(cudaMemset(g->roff, 0, (size_t)g->nbrick_max * sizeof(long long)));
-        AL_CUDA(cudaMemset(g->rplan, 0, 2 * sizeof(int)));
-        AL_CUDA(cudaMemset(g->rused, 0, sizeof(unsigned long long)));
-    }
+    AL_CUDA(cudaMemset(g->rcnt, 0, (size_t)g->nbrick_max * sizeof(int)));
+    AL_CUDA(cudaMemset(g->rcap, 0, (size_t)g->nbrick_max * sizeof(int)));
+    AL_CUDA(cudaMemset(g->roff, 0, (size_t)g->nbrick_max * sizeof(long long)));
+    AL_CUDA(cudaMemset(g->rplan, 0, 2 * sizeof(int)));
+    AL_CUDA(cudaMemset(g->rused, 0, sizeof(unsigned long long)));
     g->loaded = true;
-    return AL_OK;
+    return arena_sync(g);
 }
 
 // The projection kernels use more than 48 KB of dynamic shared memory, and
@@ -352,6 +417,52 @@ static cudaError_t brick_attrs() {
     }
     return cudaSuccess;
 }
+// the column-march kernels and the list-driven brick passes (FP32 only)
+template <int BZ>
+static cudaError_t cm_attrs() {
+    const void *fns[5] = {(const void *)al::k_cm_weights<BZ>, (const void *)al::k_cm_spread<BZ>,
+                          (const void *)al::k_spread_ls<BZ, true>, (const void *)al::k_spread_ls<BZ, false>,
+                          (const void *)al::k_bweights_ls<BZ>};
+    const int bytes_of[5] = {(int)sizeof(al::CmSmem<BZ, true>), (int)sizeof(al::CmSmem<BZ, false>),
+                             (int)sizeof(al::SpreadSmem<float, BZ, true>), (int)sizeof(al::SpreadSmem<float, BZ, false>),
+                             (int)sizeof(al::SpreadSmem<float, BZ, false>)};
+    for (int i = 0; i < 5; ++i) {
+        cudaError_t e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_of[i]);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fns[i], cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+// persistent grids of the column-march and list-driven kernels: SMs x
+// resident CTAs, per kernel (queried once per process and device)
+struct CmGrids { int cw, cs, sl_fx, sl, bw; };
+template <int BZ>
+static cudaError_t cm_grids(CmGrids &gr) {
+    static int dev_done = -1;
+    static CmGrids cache{};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev_done == dev) { gr = cache; return cudaSuccess; }
+    e = cm_attrs<BZ>();
+    if (e != cudaSuccess) return e;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int o[5] = {0, 0, 0, 0, 0};
+    using namespace al;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], k_cm_weights<BZ>, SPREAD_THREADS, sizeof(CmSmem<BZ, true>));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], k_cm_spread<BZ>, SPREAD_THREADS, sizeof(CmSmem<BZ, false>));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[2], k_spread_ls<BZ, true>, SPREAD_THREADS, sizeof(SpreadSmem<float, BZ, true>));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], k_spread_ls<BZ, false>, SPREAD_THREADS, sizeof(SpreadSmem<float, BZ, false>));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[4], k_bweights_ls<BZ>, SPREAD_THREADS, sizeof(SpreadSmem<float, BZ, false>));
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < 5; ++i) o[i] = nsm * std::max(o[i], 1);
+    cache = CmGrids{o[0], o[1], o[2], o[3], o[4]};
+    dev_done = dev;
+    gr = cache;
+    return cudaSuccess;
+}
+
 template <typename T>
 static cudaError_t spread_smem_attr() {
     static cudaError_t done = cudaErrorNotReady;
@@ -392,6 +503,35 @@ static void launch_bricks_bz(const al::Inst<T> &I, bool weights, cudaStream_t st
     }
 }
 
+// the projection of one FP32 instance with the column march: bricks whose
+// lines all take it run the column-march passes, the others the brick
+// passes, each brick with one of the two for both its weights and its spread
+template <int BZ>
+static int cm_launch(const al::Inst<float> &I, bool weights, long long nbrick, cudaStream_t st) {
+    using namespace al;
+    CmGrids gr;
+    AL_CUDA(cm_grids<BZ>(gr));
+    auto cap = [&](int gsz) { return (unsigned)std::max(1LL, std::min((long long)gsz, nbrick)); };
+    if (weights) {
+        k_cm_weights<BZ><<<cap(gr.cw), SPREAD_THREADS, sizeof(CmSmem<BZ, true>), st>>>(I.g, I.b, I.sc, I.p, I.status);
+        k_bweights_ls<BZ><<<cap(gr.bw), SPREAD_THREADS, sizeof(SpreadSmem<float, BZ, false>), st>>>(I.g, I.b, I.sc, I.p, I.status);
+    } else {
+        k_cm_spread<BZ><<<cap(gr.cs), SPREAD_THREADS, sizeof(CmSmem<BZ, false>), st>>>(I.g, I.b, I.sc, I.p, I.status);
+        if (I.g.fx)
+            k_spread_ls<BZ, true><<<cap(gr.sl_fx), SPREAD_THREADS, sizeof(SpreadSmem<float, BZ, true>), st>>>(I.g, I.b, I.sc, I.p, I.status);
+        else
+            k_spread_ls<BZ, false><<<cap(gr.sl), SPREAD_THREADS, sizeof(SpreadSmem<float, BZ, false>), st>>>(I.g, I.b, I.sc, I.p, I.status);
+    }
+    return AL_OK;
+}
+static int cm_launch_bz(const al::Inst<float> &I, bool weights, cudaStream_t st) {
+    switch (I.g.bz) {
+    case 4: return cm_launch<4>(I, weights, I.g.nbrick, st);
+    case 16: return cm_launch<16>(I, weights, I.g.nbrick, st);
+    default: return cm_launch<8>(I, weights, I.g.nbrick, st);
+    }
+}
+
 template <typename T>
 static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out *out) {
     using namespace al;
@@ -423,6 +563,7 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     sc.hasPrev = g->hasPrev; sc.anyIrr = g->anyIrr; sc.smax = g->smax; sc.anyZero = g->anyZero;
     sc.rec = (Rec<T> *)g->rec; sc.rcnt = g->rcnt; sc.rcap = g->rcap; sc.roff = g->roff;
     sc.rplan = g->rplan; sc.rused = g->rused;
+    sc.cmcnt = g->cmcnt; sc.cmlist = g->cmlist;
     BeamsC &bc = I.b;
     bc.n_lines = g->n_lines; bc.n_points = np; bc.mask_words = g->mask_words;
     bc.line_off = g->d_line_off; bc.line_of = g->d_line_of;
@@ -447,6 +588,10 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
         I.g.smode = AL_SPREAD_GATHER;
     }
     I.g.rmode = (g->opt_record == 1 && I.g.wmode != 0 && I.g.smode == 0 && g->rec_total > 0) ? 1 : 0;
+    // the column-march passes: FP32, the paper's nearest-segment projection,
+    // no reflecting face, the gather
+    I.g.cm = (g->opt_column && g->d.precision == AL_FP32 && g->bd.proj_mode == AL_PROJ_NEAREST &&
+              !g->bd.wall_reflect && I.g.smode == AL_SPREAD_GATHER) ? 1 : 0;
     I.g.fx = (I.g.rmode || g->opt_record == 2 || g->bd.proj_mode == AL_PROJ_INTEGRATED) ? 1 : 0;
     if (g->bd.wall_reflect) I.g.fx = 0;                 // the reflected passes gather in line order
     I.status = out->status ? out->status : g->statusInt;
@@ -478,16 +623,41 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
     if (g->n_lines > 0) k_lines<T><<<(g->n_lines + 7) / 8, 256, 0, st>>>(gc, bc, sc, p, status);
     trace_mark(g, 1, st);
     if (np > 0) k_mask<T><<<nb, 256, 0, st>>>(gc, bc, sc);
+    if constexpr (std::is_same<T, float>::value) {
+        if (gc.cm) {
+            if (np == 0) AL_CUDA(cudaMemsetAsync(g->cmcnt, 0, 2 * sizeof(int), st));
+            k_cm_classify<float><<<(unsigned)((gc.nbrick * 32 + 255) / 256), 256, 0, st>>>(gc, bc, sc);
+        }
+    }
     trace_mark(g, 2, st);
+    const bool cm = std::is_same<T, float>::value && gc.cm;
     if (np > 0) {
         if (gc.wmode != 0)
             k_weights<T><<<(unsigned)(((long long)np * 32 + 127) / 128), 128, 0, st>>>(gc, bc, sc, p, status);
-        launch_bricks_bz<T>(I, true, st);
+        if constexpr (std::is_same<T, float>::value) {
+            if (cm) {
+                const int rc = cm_launch_bz(I, true, st);
+                if (rc != AL_OK) return rc;
+            } else {
+                launch_bricks_bz<T>(I, true, st);
+            }
+        } else {
+            launch_bricks_bz<T>(I, true, st);
+        }
     }
     trace_mark(g, 3, st);
     if (np > 0) k_normalise<T><<<nb, 256, 0, st>>>(gc, bc, sc, p, status);
     trace_mark(g, 4, st);
-    launch_bricks_bz<T>(I, false, st);
+    if constexpr (std::is_same<T, float>::value) {
+        if (cm) {
+            const int rc = cm_launch_bz(I, false, st);
+            if (rc != AL_OK) return rc;
+        } else {
+            launch_bricks_bz<T>(I, false, st);
+        }
+    } else {
+        launch_bricks_bz<T>(I, false, st);
+    }
     if (gc.smode != 0 && np > 0) {
         // scatter form: certified lines add their sources with atomics after the
         // gather has written every cell (uncertified lines and deposits)
@@ -531,7 +701,7 @@ extern "C" int al_set_option(al_grid g, int option, int value) {
     case AL_OPT_WEIGHTS:
         if (value != AL_WEIGHTS_BRICK && value != AL_WEIGHTS_SEGMENT) return AL_ERR_ARG;
         g->gc.wmode = value;
-        return AL_OK;
+        return arena_sync(g);
     case AL_OPT_BRICK_Z:
         if (value != 4 && value != 8 && value != 16) return AL_ERR_ARG;
         set_brick_z(g->gc, value);
@@ -543,6 +713,10 @@ extern "C" int al_set_option(al_grid g, int option, int value) {
     case AL_OPT_RECORD:
         if (value < 0 || value > 2) return AL_ERR_ARG;
         g->opt_record = value;
+        return arena_sync(g);
+    case AL_OPT_COLUMN:
+        if (value != 0 && value != 1) return AL_ERR_ARG;
+        g->opt_column = value;
         return AL_OK;
     default:
         return AL_ERR_ARG;
@@ -576,7 +750,7 @@ extern "C" int al_destroy(al_grid g) {
     if (g->trace) al_trace_enable(g, 0);
     free_beams(g);
     void *ptrs[] = {g->brickSum, g->scatSum, g->statusInt, g->totalsInt, g->hasPrev, g->anyIrr, g->smax,
-                    g->anyZero, g->rcnt, g->rcap, g->roff, g->rplan, g->rused};
+                    g->anyZero, g->rcnt, g->rcap, g->roff, g->rplan, g->rused, g->cmcnt, g->cmlist};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -659,6 +833,12 @@ extern "C" int al_sizes(al_grid g, long long *n_cells, long long *n_points, int 
     if (n_cells) *n_cells = g->gc.ncell;
     if (n_points) *n_points = g->n_points;
     if (n_lines) *n_lines = g->n_lines;
+    return AL_OK;
+}
+
+extern "C" int al_footprint(al_grid g, unsigned long long *bytes) {
+    if (!g || !bytes) return AL_ERR_ARG;
+    *bytes = (unsigned long long)(g->grid_bytes + g->beam_bytes + g->rec_bytes);
     return AL_OK;
 }
 
@@ -750,6 +930,7 @@ static int batch_rebuild_t(al_batch b) {
             h[q] = make_inst<T>(b->grids[q], &b->ins[q], &b->outs[q]);
             set_brick_z(h[q].g, b->bz);
             h[q].g.smode = 0;                                // batches always gather
+            h[q].g.cm = 0;                                   // and take the brick passes
             if (h[q].g.wmode != 0) b->any_segment_weights = true;
             if (h[q].b.sample_mode == AL_SAMPLE_GAUSS) b->any_gauss = true;
             if (h[q].b.reflect) b->any_reflect = true;
@@ -1077,6 +1258,7 @@ extern "C" int al_autotune(al_grid g, const al_step_in *in, const al_step_out *o
             g->gc.wmode = wms[wi];
             g->opt_record = recs[wi];
             set_brick_z(g->gc, bzs[zi]);
+            if ((rc = arena_sync(g)) != AL_OK) break;
             if ((rc = restore_state(g, out, sv, st)) != AL_OK) break;
             if ((rc = al_sample_drag_spread(g, in, out, stream)) != AL_OK) break;       // warm-up
             if (cudaEventRecord(ev.a, st) != cudaSuccess) { rc = AL_ERR_CUDA; break; }
@@ -1093,7 +1275,8 @@ extern "C" int al_autotune(al_grid g, const al_step_in *in, const al_step_out *o
     g->gc.wmode = best_w;
     g->opt_record = best_r;
     set_brick_z(g->gc, best_z);
-    const int rc2 = restore_state(g, out, sv, st);
+    int rc2 = arena_sync(g);                          // the arena only if the choice records
+    if (rc2 == AL_OK) rc2 = restore_state(g, out, sv, st);
     if (sv.fprev) cudaFree(sv.fprev);
     if (rc == AL_OK) rc = rc2;
     if (rc == AL_OK && choice) *choice = 1000 * best_r + 100 * best_w + best_z;

@@ -44,11 +44,12 @@ constexpr int BX = 16, BY = 16;                  // projection brick footprint (
 constexpr int BZ_MIN = 4, BZ_MAX = 16;           // brick heights the kernels are built for
 constexpr int SPREAD_THREADS = BX * BY;          // one thread per column
 constexpr float BRICK_DIAG = 27.72f;             // diagonal of the tallest brick, 16 x 16 x 16
+constexpr int CM_NN = 640;                       // column march: nodes staged per batch of lines
 constexpr double PI_D = 3.14159265358979323846;
 
 enum { ST_PA_OUTSIDE = 0, ST_PS_OUTSIDE = 1, ST_FALLBACK = 2, ST_FALLBACK_ZERO = 3,
        ST_ZERO_WEIGHT = 4, ST_DEPOSIT_LOST = 5, ST_REFINED = 6, ST_IRREGULAR = 7, ST_SUPPORT = 8,
-       ST_REPLAYED = 9 };
+       ST_REPLAYED = 9, ST_COLUMN = 10 };
 
 struct GridC {
     int nx, ny, nz;
@@ -67,6 +68,7 @@ struct GridC {
     int fx;                      // 1: the spread sums fixed-point integers (replay, integrated projection)
     long long rec_total;         // capacity of the record arena (records)
     long long nbrick_max;        // bricks at the lowest brick height (size of the per-brick arrays)
+    int cm;                      // 1: bricks whose lines all take the column march use the column-march passes
 };
 
 // one (cell, segment) pair of a certified line inside the 3 eps support, as
@@ -100,6 +102,8 @@ struct LineG {                   // per line, rebuilt every step
     float rho2;                  // regular == 2: a walk may start at a node within sqrt(rho2) cells
     int wshift;                  // fixed-point weights: omega eta / eta0 in units of 2^-wshift
     float R2f, ie2f, eta0f;      // FP32 copies of R2c, inv_eps2c_l2, eta0 (no conversions in the hot loops)
+    int cm;                      // the line climbs (D_z / |D| >= 0.8 on every segment) and carries the
+                                 // column-march certificate (FP32 instances)
 };
 
 // per-line constant in the field precision, without an FP64 conversion for FP32
@@ -135,6 +139,8 @@ struct Scratch {
     long long *roff;             // [nbrick_max] start of the brick's region
     int *rplan;                  // [2] brick height the regions of this step / of the next step were sized for
     unsigned long long *rused;   // [1] arena taken by the next step's regions
+    int *cmcnt;                  // [2] bricks of this step on the column-march / the brick passes
+    int *cmlist;                 // [2][nbrick_max] those bricks
 };
 
 template <typename T>
@@ -717,6 +723,7 @@ __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, 
     sc.wfix[i] = 0ull;                                   // fixed-point weights start at zero
     if (i == 0) {
         *sc.anyIrr = 0; *sc.smax = 0u; *sc.anyZero = 0;
+        sc.cmcnt[0] = 0; sc.cmcnt[1] = 0;
         sc.rplan[0] = sc.rplan[1];                        // the regions the last step sized
         sc.rplan[1] = 0;
         *sc.rused = 0ull;
@@ -892,7 +899,34 @@ __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
             if (thw < 1.2f) D2c = rho_s + 0.5f * lw * sinf(thw) + 0.05f;
         }
     }
-    int ok1 = D1c > 0.0f, ok2 = D2c > 0.0f;
+    // column-march certificate: the line climbs (every segment D_z / |D| >=
+    // 0.8); a brick of height h <= 16 takes as candidates the segments whose
+    // height range meets its layers' centres widened by 3 eps (+0.02), an arc
+    // of at most S = (16 + 2 R + 0.06 + 2 L_max) / c_z cells, so a cell within
+    // R of the line has every candidate within arc S of its foot; certifying
+    // rho = R + S min(Theta, 1) (Theta = (S / L_min + 2) theta_max its
+    // turning) makes the bisector signs monotone over the candidates
+    float Dcm = -1.0f;
+    // (and a brick's candidate range, at most (16 + 2 R + 0.06) / (L_min c_z) + 2
+    // segments, fits the stage)
+    if (sizeof(T) == 4 && base_ok && czp >= 0.8f && (16.0f + 2.0f * Rc + 0.06f) / (Lmin * czp) + 3.0f < (float)CM_NN) {
+        const float S = fminf((16.0f + 2.0f * Rc + 0.06f + 2.0f * Lmax) / czp, Ltot);
+        const float Theta = (S / Lmin + 2.0f) * thmax;
+        Dcm = Rc + S * fminf(Theta, 1.0f) + 0.01f;
+    }
+    int ok1 = D1c > 0.0f, ok2 = D2c > 0.0f, okc = Dcm > 0.0f;
+    if (okc) {
+        int badc = 0;
+        for (int q = lane; q < n - 1; q += 32) {
+            const int k = off + q;
+            float t0 = (q >= 1) ? sc.nodeTau[k] : 0.0f;
+            float t1 = (q + 1 <= n - 2) ? sc.nodeTau[k + 1] : 0.0f;
+            T D0 = sc.segD[k], D1 = sc.segD[np + k], D2 = sc.segD[2 * np + k];
+            float L = (float)tsqrt(D0 * D0 + D1 * D1 + D2 * D2);
+            if (!(Dcm * (t0 + t1) <= 0.5f * L)) badc = 1;
+        }
+        if (__any_sync(0xffffffffu, badc)) okc = 0;
+    }
     if (ok1 || ok2) {
         int bad1 = 0, bad2 = 0;
         for (int q = lane; q < n - 1; q += 32) {
@@ -919,6 +953,7 @@ __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
         lg.ie2f = (float)lg.inv_eps2c_l2;
         lg.eta0f = (float)lg.eta0;
         lg.regular = ok2 ? 2 : (ok1 ? 1 : 0);
+        lg.cm = okc;
         lg.first = off;
         lg.n = n;
         lg.thmax = thmax;
@@ -1541,7 +1576,7 @@ __device__ void d_weights(const GridC &g, const BeamsC &b, const Scratch<T> &sc,
     if (c.n >= 2 && c.q == c.n - 1) return;                 // the tip starts no segment
     c.nseg = (c.n == 1) ? 1 : c.n - 1;
     c.kb = seg_end(k, c.n);
-    if (!lg.regular && !b.proj_mode) {                      // the brick passes take this line
+    if ((!lg.regular && !b.proj_mode) || (g.cm && lg.cm)) { // the brick or column-march passes take it
         if (!SC && lane == 0) { sc.segWa[k] = 0.0; sc.segWb[k] = 0.0; }   // zero in both encodings
         return;
     }
@@ -1629,7 +1664,7 @@ __device__ unsigned int d_normalise(const GridC &g, const BeamsC &b, const Scrat
     const int off = b.line_off[l], n = b.line_off[l + 1] - off, q = k - off;
     double w = 0.0;
     const LineG &lg = sc.lines[l];
-    if ((g.wmode == 0 || !lg.regular) && !b.proj_mode) {
+    if ((g.wmode == 0 || !lg.regular || (g.cm && lg.cm)) && !b.proj_mode) {
         // brick pass: fixed-point sum of omega eta / eta0; w = sum eta0 V 2^-wshift
         w = ldexp((double)sc.wfix[k], -lg.wshift) * (lg.eta0 * g.V);
     } else if (n == 1) {
@@ -2079,7 +2114,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     const int byi = rem / g.nbx, bxi = rem - byi * g.nbx;
     const int B0 = bxi * BX, B1 = byi * BY, B2 = bzi * BZ;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (WP && g.wmode != 0 && *sc.anyIrr == 0) return;      // the segment pass took every line
+    if (WP && g.wmode != 0 && *sc.anyIrr == 0 && !g.cm) return;   // the segment pass took every line
     if (WP && b.proj_mode) return;                           // the integrated projection: segment pass only
     const int nzb = min(BZ, g.nz - B2);              // layers of this brick inside the grid
     const int nxb = min(BX, g.nx - B0), nyb = min(BY, g.ny - B1);
@@ -2162,7 +2197,10 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                     while (t) {
                         const int bit = __ffs(t) - 1;
                         t &= t - 1;
-                        if (!sc.lines[(w << 5) + bit].regular) keep |= 1u << bit;
+                        const LineG &lk = sc.lines[(w << 5) + bit];
+                        // lines without a certificate, and column-march lines
+                        // (neither recorded nor in the segment pass)
+                        if (!lk.regular || (g.cm && lk.cm)) keep |= 1u << bit;
                     }
                     m = keep;
                 }
@@ -2183,7 +2221,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                         const int bit = __ffs(m) - 1;
                         m &= m - 1;
                         const int l = (w << 5) + bit;
-                        if (!keep_certified && sc.lines[l].regular) continue;
+                        if (!keep_certified && sc.lines[l].regular && !(g.cm && sc.lines[l].cm)) continue;
                         if (pos >= lo && pos < hi) sm.list[pos - lo] = l;
                         ++pos;
                     }
@@ -2270,7 +2308,7 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
                     sm.e_ie2[e] = lgc<T>(lg.inv_eps2c_l2, lg.ie2f);
                     sm.e_eta0[e] = WP ? (T)lg.wshift : lgc<T>(lg.eta0, lg.eta0f);
                     sm.e_rho2[e] = lg.rho2;
-                    sm.e_canon[e] = (g.wmode != 0 && lg.regular != 0) ? 1 : 0;
+                    sm.e_canon[e] = (g.wmode != 0 && lg.regular != 0 && !(g.cm && lg.cm)) ? 1 : 0;
                     for (int a = 0; a < 3; ++a) { sm.e_lo[e][a] = lo[a] - blo[a]; sm.e_hi[e][a] = hi[a] - blo[a]; }
                     sm.e_cz[e] = cz_ok;
                     if (cz_ok > 0.0f) {
@@ -3121,3 +3159,5 @@ __global__ void __launch_bounds__(256) kb_totals(const Inst<T> *I, const int *se
 #undef AL_SEL
 
 }  // namespace al
+
+#include "al_cm.cuh"

@@ -43,7 +43,13 @@ def compare(wl, g, o, *, line_mask=None, cell_mask=None, label="", sumF_ref="net
     S: max over cells of |S_gpu - S_oracle| relative to max|S_oracle|.
     F: max over points of |F_gpu - F_oracle| relative to max|F_oracle|.
     sumF: |sum F_gpu - sum F_oracle| relative to |sum F_oracle| ("net"), or to
-    sum |F_oracle| ("abs", for small random cases whose net force cancels).
+    sum |F_oracle| ("abs").  The random cases use "abs": their lines point
+    every way (arcs, random walks, horizontal lines) in fields with random
+    components, so the loads largely cancel and |sum F| can be orders of
+    magnitude below sum |F|; the FP32 rounding of each F_i is relative to
+    |F_i|, so |sum F| is not a scale it can be measured against there.  The
+    configured workloads (canopy, flume, plain), whose loads point
+    downstream and do not cancel, use "net", the criterion as stated.
     cons: |sum S V + sum F| on the GPU relative to sum |F|."""
     tS, tF, tC = tolerances(wl)
     out = {}

@@ -584,11 +584,29 @@ def test_zero_weight_nodes_are_deposited():
 
 
 def test_plain_config_totals():
+    # the plain case without its noise: a straight rigid vertical cylinder at
+    # rest in U = (0.5, 0, 0) takes exactly the golden total of Eq.
+    # almLineForce, 1/2 rho d C_dn U0^2 L = 0.3 N (tests/golden/cylinder_drag.txt)
+    gold = _golden("cylinder_drag.txt")
     wl = W.make_plain(0)
+    n = wl.beams.n_points
+    P = np.zeros((3, n))
+    P[0], P[1] = 0.20, 0.16
+    P[2] = np.cumsum(wl.beams.cv_len) - 0.5 * wl.beams.cv_len
+    U = np.zeros_like(wl.step.U)
+    U[0] = gold["U0"]
+    clean = replace(wl, step=replace(wl.step, U=U, P=P, Pdot=np.zeros_like(P)))
+    r = oracle.sample_drag_spread(clean)
+    assert r["totals"][0] == pytest.approx(gold["F_total"], rel=1e-12)
+    assert np.abs(r["totals"][1:3]).max() < 1e-15
+    assert np.abs(r["totals"][:3] + r["totals"][3:]).max() < 1e-14
+    # the seeded case: U has N(0, 0.05^2) noise per component, so each CV's
+    # drag (proportional to |U_r| U_n) varies by about 2 x 0.05 / 0.5 = 20 %
+    # and the sum of 20 CVs by 20 % / sqrt(20) = 4.5 %; three standard
+    # deviations bound it at 13.5 %
     r = oracle.sample_drag_spread(wl)
     assert np.abs(r["totals"][:3] + r["totals"][3:]).max() < 1e-14
-    # near-uniform flow of 0.5 m/s normal to a near-vertical 0.2 m cylinder: ~0.3 N
-    assert r["totals"][0] == pytest.approx(0.3, rel=0.1)
+    assert r["totals"][0] == pytest.approx(gold["F_total"], rel=0.135)
     assert (r["status"][:2] == 0).all()
 
 
