@@ -53,6 +53,9 @@ def _args():
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000", help="serve: arrival rates (1/s)")
     ap.add_argument("--budget-gb", type=float, default=0.5, help="serve: HBM budget for resident simulations")
     ap.add_argument("--eps", type=float, default=2.0, help="canopy kernel width in cells")
+    ap.add_argument("--reduced", action="store_true",
+                    help="a reduced grid of the same workload (flume 256x64x128 with 20x8 stems, canopy "
+                         "128x64x128 with 10x10 stems): for profiler captures, not a bench line")
     ap.add_argument("--inertia", action="store_true",
                     help="add the Morison inertia term (accelerating fluid and beams, C_Mn = 1, C_Mt = 0.1)")
     ap.add_argument("--sample", default="trilinear", choices=["trilinear", "cell", "gauss"],
@@ -73,12 +76,12 @@ def _args():
     return ap.parse_args()
 
 
-def _workload(name, seed, eps):
+def _workload(name, seed, eps, reduced=False):
     from paper_2609_39443_b300 import workloads as W
     if name == "canopy":
-        return W.make_canopy(seed, eps)
+        return W.make_canopy(seed, eps, nx=128, ny=64, n_sx=10, n_sy=10) if reduced else W.make_canopy(seed, eps)
     if name == "flume":
-        return W.make_flume(seed)
+        return W.make_flume(seed, nx=256, ny=64, nz=128, n_sx=20, n_sy=8) if reduced else W.make_flume(seed)
     return W.make_plain(seed)
 
 
@@ -244,7 +247,7 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = _workload(a.workload, 0, a.eps)
+    wl = _workload(a.workload, 0, a.eps, a.reduced)
     v, cores, sample = _cpu_baseline(wl, budget_s=max(5.0, min(60.0, 2.0 * (a.steps + a.warmup))))
     line = {"impl": "reference", "metric": "coupling steps/s", "value": v, "unit": "steps/s",
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 / v,
@@ -272,7 +275,7 @@ def run_ours(a):
             dist.barrier()
     from paper_2609_39443_b300.al import Instance, PHASES, ST_SUPPORT
 
-    wl = _workload(a.workload, instance_seed(rank), a.eps)
+    wl = _workload(a.workload, instance_seed(rank), a.eps, a.reduced)
     if a.inertia:
         from paper_2609_39443_b300 import workloads as W
         wl = W.with_inertia(wl, 1000 + instance_seed(rank))

@@ -87,6 +87,8 @@ extern "C" {
 #define AL_ST_SUPPORT        8 /* (cell, line) pairs within 3 eps: kernel-cell updates   */
 #define AL_ST_REPLAYED       9 /* bricks that replayed recorded pairs instead of gathering them */
 #define AL_ST_COLUMN        10 /* bricks whose both passes took the column march (AL_OPT_COLUMN) */
+#define AL_ST_GUARD         15 /* bit flags of index guards in the column-march set-up that skipped an
+                                  access (never expected to be set; tests require zero) */
 #define AL_STATUS_N         16
 
 /* ---- descriptors ------------------------------------------------------- */
@@ -376,6 +378,58 @@ int al_batch_set_option(al_batch b, int option, int value);
  * restored.  *choice (optional) = 10 * brick height + CTAs per SM (0 = as
  * many as fit).  Every slot must be bound. */
 int al_batch_autotune(al_batch b, int trials, void *stream, int *choice);
+
+/* ---- serving: continuous batching of coupling-step requests ------------ */
+/* Many simulations send coupling-step requests (the actuator-point positions
+ * of their next step, Algorithm 1 step 1) as they arrive; the server keeps
+ * each admitted simulation resident (its instance bound to a slot of one
+ * batch, with the caller's device fields and outputs) and advances every
+ * resident simulation that has a queued request and no step in flight in
+ * one batched launch sequence, a wave; waves alternate between two streams
+ * of the server's own, so one forms and launches while the previous one
+ * runs.  A simulation's requests run in submission order, one at a time, and
+ * a served step gives the bits of the same step run in a batch.  Per wave
+ * the requests' positions travel in one host-to-device copy and the line
+ * forces in one device-to-host copy (packed in pinned staging buffers). */
+typedef struct al_server_s *al_server;
+typedef struct {
+    unsigned long long hbm_budget; /* device bytes the resident simulations may hold: for each, the
+                                      library's (al_footprint of its instance) plus what the caller
+                                      declares for its own buffers at admission */
+    int max_sims;                  /* slots: simulations resident at a time, >= 1 */
+    int max_wave;                  /* simulations advanced by one wave, 1 .. max_sims */
+    int max_points;                /* largest N_p of a simulation (sizes the staging buffers) */
+    int precision;                 /* AL_FP32 or AL_FP64, shared by every simulation */
+} al_server_desc;
+int al_server_create(const al_server_desc *desc, al_server *out);
+/* Admit a simulation: creates its instance (al_create_grid, al_load_beams)
+ * and binds it to a free slot.  in / out are its DEVICE buffers as for
+ * al_sample_drag_spread (caller-owned, valid until al_server_release;
+ * in->P is overwritten by each request's positions); caller_bytes is what
+ * those buffers take.  AL_ERR_CAPACITY, with nothing kept, when no slot is
+ * free, N_p > max_points, or footprint + caller_bytes would pass the
+ * budget.  Synchronous. *sim receives the slot. */
+int al_server_admit(al_server s, const al_grid_desc *grid, const al_beam_desc *beams, const al_step_in *in,
+                    const al_step_out *out, unsigned long long caller_bytes, int *sim);
+/* Queue one coupling step of simulation sim: P_host (HOST, 3 x N_p SoA in the
+ * precision, read when the step is launched) and F_host (HOST, 3 x N_p,
+ * written when the step is retired by a poll); tag identifies it in
+ * al_server_poll.  Both buffers stay valid until then. */
+int al_server_submit(al_server s, int sim, const void *P_host, void *F_host, long long tag);
+/* Progress: retire the waves that completed (their forces unpacked into the
+ * requests' F_host), then launch one wave on a free stream.  Writes up to
+ * max_done tags of completed requests (the rest are reported by later
+ * polls).  wait != 0: if nothing has completed, wait for the oldest wave in
+ * flight. */
+int al_server_poll(al_server s, long long *done_tags, int max_done, int *n_done, int wait);
+/* Evict: waits for the simulation's step in flight, unbinds and destroys its
+ * instance, frees its slot and budget share.  AL_ERR_STATE while requests
+ * are still queued. */
+int al_server_release(al_server s, int sim);
+/* Device bytes held by the resident simulations (as counted at admission)
+ * and how many are resident (optional). */
+int al_server_footprint(al_server s, unsigned long long *bytes, int *resident);
+int al_server_destroy(al_server s);
 
 /* ---- line forces without device allocation ----------------------------- */
 /* The paper has no counterpart of this entry point.  It exists for callers

@@ -21,6 +21,7 @@ AL_FP32, AL_FP64 = 0, 1
 AL_STATUS_N = 16
 (ST_PA_OUTSIDE, ST_PS_OUTSIDE, ST_FALLBACK, ST_FALLBACK_ZERO, ST_ZERO_WEIGHT, ST_DEPOSIT_LOST,
  ST_REFINED, ST_IRREGULAR, ST_SUPPORT, ST_REPLAYED, ST_COLUMN) = range(11)
+ST_GUARD = 15
 
 OPT_WEIGHTS, OPT_BRICK_Z, OPT_SPREAD_CTAS, OPT_SPREAD, OPT_RECORD, OPT_COLUMN = 1, 2, 3, 4, 5, 6
 WEIGHTS_BRICK, WEIGHTS_SEGMENT = 0, 1
@@ -272,7 +273,7 @@ class Instance:
     """A Grid plus device-resident copies of one workload's inputs and its
     output buffers (data movement only)."""
 
-    def __init__(self, wl, device="cuda"):
+    def __init__(self, wl, device="cuda", options=None):
         import torch
         self.wl = wl
         self.device = device
@@ -293,6 +294,8 @@ class Instance:
         self.status = torch.zeros(AL_STATUS_N, dtype=torch.int32, device=device)
         self.grid = Grid(wl.grid)
         self.grid.load_beams(wl.beams)
+        for opt, value in (options or {}).items():   # al_set_option for each (option, value)
+            self.grid.set_option(opt, value)
 
     def step(self, stream=None):
         self.grid.step(self.U, self.P, self.Pdot, self.S, self.F, alpha=self.alpha, P_spread=self.P_spread,

@@ -10,8 +10,10 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libal.so")
-SOURCES = [os.path.join(HERE, "csrc", "al_api.cu"), os.path.join(HERE, "csrc", "al_noalloc.cu")]
-HEADERS = [os.path.join(HERE, "csrc", "al_kernels.cuh"), os.path.join(ROOT, "include", "al.h")]
+SOURCES = [os.path.join(HERE, "csrc", "al_api.cu"), os.path.join(HERE, "csrc", "al_serve.cu"),
+           os.path.join(HERE, "csrc", "al_noalloc.cu")]
+HEADERS = [os.path.join(HERE, "csrc", "al_kernels.cuh"), os.path.join(HERE, "csrc", "al_cm.cuh"),
+           os.path.join(ROOT, "include", "al.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -94,6 +94,12 @@ struct al_grid_s {
     int *cmcnt = nullptr;             // [2] bricks of a step on the column-march / the brick passes
     int *cmlist = nullptr;            // [2][nbrick_max] those bricks
     int opt_column = 1;               // AL_OPT_COLUMN
+    // column march (FP32, nearest-segment projection, no reflection): node
+    // records, entries of the column-march bricks
+    float4 *cmN = nullptr;            // [np][4] node records
+    al::CmEnt *cment = nullptr;
+    int *cment_n = nullptr, *bent_off = nullptr, *bent_n = nullptr;
+    long long cment_cap = 0;
     unsigned long long *rused = nullptr;    // arena taken by the next step's regions
     void *rec = nullptr;              // record arena (rec_total records), allocated only while records are used
     long long rec_total = 0;
@@ -115,7 +121,8 @@ static void trace_mark(al_grid g, int i, cudaStream_t st) {
 static void free_beams(al_grid g) {
     void *ptrs[] = {g->d_line_off, g->d_line_of, g->d_d, g->d_cdn, g->d_cdt, g->d_eps, g->d_ell, g->d_af,
                     g->d_cvl, g->d_cmn, g->d_cmt, g->d_EI, g->fprev, g->uhi, g->segD, g->segIl2, g->nodeM, g->fhat, g->ulo,
-                    g->nodeTau, g->segWa, g->segWb, g->w, g->lineF, g->lines, g->mask, g->wfix, g->rec};
+                    g->nodeTau, g->segWa, g->segWb, g->w, g->lineF, g->lines, g->mask, g->wfix, g->rec,
+                    g->cmN, g->cment, g->cment_n, g->bent_off, g->bent_n};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     g->d_line_off = g->d_line_of = nullptr;
@@ -130,6 +137,10 @@ static void free_beams(al_grid g) {
     g->mask = nullptr;
     g->rec = nullptr;
     g->rec_total = 0;
+    g->cmN = nullptr;
+    g->cment = nullptr;
+    g->cment_n = g->bent_off = g->bent_n = nullptr;
+    g->cment_cap = 0;
     g->beam_bytes = g->rec_bytes = 0;
     g->loaded = false;
     g->n_lines = g->n_points = g->mask_words = 0;
@@ -350,6 +361,17 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     A(&g->wfix, (size_t)np); A(&g->w, (size_t)np); A(&g->lineF, 3 * nl);
     A(&g->lines, nl);
     A(&g->mask, (size_t)g->nbrick_max * g->mask_words);
+    if (g->d.precision == AL_FP32 && b.proj_mode == AL_PROJ_NEAREST && !b.wall_reflect && np > 0) {
+        // the column march: four float4 records per node, and an entry pool of
+        // 16 entries per brick at the lowest brick height (bricks beyond it in
+        // a step take the brick passes)
+        A(&g->cmN, 4 * (size_t)np);
+        g->cment_cap = 16 * g->nbrick_max;
+        A(&g->cment, (size_t)g->cment_cap);
+        A(&g->cment_n, 1);
+        A(&g->bent_off, (size_t)g->nbrick_max);
+        A(&g->bent_n, (size_t)g->nbrick_max);
+    }
     if (e != cudaSuccess) {
         int rc = cuda_fail(e, "cudaMalloc");
         free_beams(g);
@@ -420,10 +442,10 @@ static cudaError_t brick_attrs() {
 // the column-march kernels and the list-driven brick passes (FP32 only)
 template <int BZ>
 static cudaError_t cm_attrs() {
-    const void *fns[5] = {(const void *)al::k_cm_weights<BZ>, (const void *)al::k_cm_spread<BZ>,
+    const void *fns[5] = {(const void *)al::k_cm_weights<float>, (const void *)al::k_cm_spread<BZ>,
                           (const void *)al::k_spread_ls<BZ, true>, (const void *)al::k_spread_ls<BZ, false>,
                           (const void *)al::k_bweights_ls<BZ>};
-    const int bytes_of[5] = {(int)sizeof(al::CmSmem<BZ, true>), (int)sizeof(al::CmSmem<BZ, false>),
+    const int bytes_of[5] = {(int)(sizeof(al::CmWeightSmem)), (int)sizeof(al::CmSpreadSmem<BZ>),
                              (int)sizeof(al::SpreadSmem<float, BZ, true>), (int)sizeof(al::SpreadSmem<float, BZ, false>),
                              (int)sizeof(al::SpreadSmem<float, BZ, false>)};
     for (int i = 0; i < 5; ++i) {
@@ -434,7 +456,7 @@ static cudaError_t cm_attrs() {
     return cudaSuccess;
 }
 // persistent grids of the column-march and list-driven kernels: SMs x
-// resident CTAs, per kernel (queried once per process and device)
+// resident CTAs, per kernel (queried once per process, device and height)
 struct CmGrids { int cw, cs, sl_fx, sl, bw; };
 template <int BZ>
 static cudaError_t cm_grids(CmGrids &gr) {
@@ -450,8 +472,8 @@ static cudaError_t cm_grids(CmGrids &gr) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int o[5] = {0, 0, 0, 0, 0};
     using namespace al;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], k_cm_weights<BZ>, SPREAD_THREADS, sizeof(CmSmem<BZ, true>));
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], k_cm_spread<BZ>, SPREAD_THREADS, sizeof(CmSmem<BZ, false>));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], k_cm_weights<float>, CM_WTHREADS, sizeof(CmWeightSmem));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], k_cm_spread<BZ>, CM_STHREADS, sizeof(CmSpreadSmem<BZ>));
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[2], k_spread_ls<BZ, true>, SPREAD_THREADS, sizeof(SpreadSmem<float, BZ, true>));
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], k_spread_ls<BZ, false>, SPREAD_THREADS, sizeof(SpreadSmem<float, BZ, false>));
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[4], k_bweights_ls<BZ>, SPREAD_THREADS, sizeof(SpreadSmem<float, BZ, false>));
@@ -513,10 +535,11 @@ static int cm_launch(const al::Inst<float> &I, bool weights, long long nbrick, c
     AL_CUDA(cm_grids<BZ>(gr));
     auto cap = [&](int gsz) { return (unsigned)std::max(1LL, std::min((long long)gsz, nbrick)); };
     if (weights) {
-        k_cm_weights<BZ><<<cap(gr.cw), SPREAD_THREADS, sizeof(CmSmem<BZ, true>), st>>>(I.g, I.b, I.sc, I.p, I.status);
+        // one warp per entry of the bricks of list 0, then the brick passes over list 1
+        k_cm_weights<float><<<(unsigned)gr.cw, CM_WTHREADS, sizeof(CmWeightSmem), st>>>(I.g, I.b, I.sc, I.p, I.status);
         k_bweights_ls<BZ><<<cap(gr.bw), SPREAD_THREADS, sizeof(SpreadSmem<float, BZ, false>), st>>>(I.g, I.b, I.sc, I.p, I.status);
     } else {
-        k_cm_spread<BZ><<<cap(gr.cs), SPREAD_THREADS, sizeof(CmSmem<BZ, false>), st>>>(I.g, I.b, I.sc, I.p, I.status);
+        k_cm_spread<BZ><<<cap(gr.cs), CM_STHREADS, sizeof(CmSpreadSmem<BZ>), st>>>(I.g, I.b, I.sc, I.p, I.status);
         if (I.g.fx)
             k_spread_ls<BZ, true><<<cap(gr.sl_fx), SPREAD_THREADS, sizeof(SpreadSmem<float, BZ, true>), st>>>(I.g, I.b, I.sc, I.p, I.status);
         else
@@ -590,8 +613,10 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     I.g.rmode = (g->opt_record == 1 && I.g.wmode != 0 && I.g.smode == 0 && g->rec_total > 0) ? 1 : 0;
     // the column-march passes: FP32, the paper's nearest-segment projection,
     // no reflecting face, the gather
-    I.g.cm = (g->opt_column && g->d.precision == AL_FP32 && g->bd.proj_mode == AL_PROJ_NEAREST &&
-              !g->bd.wall_reflect && I.g.smode == AL_SPREAD_GATHER) ? 1 : 0;
+    I.g.cm = (g->opt_column && g->cmN && I.g.smode == AL_SPREAD_GATHER) ? 1 : 0;
+    sc.cmN = I.g.cm ? g->cmN : nullptr;
+    sc.cment = g->cment; sc.cment_n = I.g.cm ? g->cment_n : nullptr; sc.cment_cap = g->cment_cap;
+    sc.bent_off = g->bent_off; sc.bent_n = g->bent_n;
     I.g.fx = (I.g.rmode || g->opt_record == 2 || g->bd.proj_mode == AL_PROJ_INTEGRATED) ? 1 : 0;
     if (g->bd.wall_reflect) I.g.fx = 0;                 // the reflected passes gather in line order
     I.status = out->status ? out->status : g->statusInt;
@@ -625,8 +650,8 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
     if (np > 0) k_mask<T><<<nb, 256, 0, st>>>(gc, bc, sc);
     if constexpr (std::is_same<T, float>::value) {
         if (gc.cm) {
-            if (np == 0) AL_CUDA(cudaMemsetAsync(g->cmcnt, 0, 2 * sizeof(int), st));
-            k_cm_classify<float><<<(unsigned)((gc.nbrick * 32 + 255) / 256), 256, 0, st>>>(gc, bc, sc);
+            if (np == 0) AL_CUDA(cudaMemsetAsync(g->cmcnt, 0, 2 * sizeof(int), st));   // (k_points resets them)
+            k_cm_entries<float><<<(unsigned)((gc.nbrick * 32 + 255) / 256), 256, 0, st>>>(gc, bc, sc, status);
         }
     }
     trace_mark(g, 2, st);
@@ -931,6 +956,8 @@ static int batch_rebuild_t(al_batch b) {
             set_brick_z(h[q].g, b->bz);
             h[q].g.smode = 0;                                // batches always gather
             h[q].g.cm = 0;                                   // and take the brick passes
+            h[q].sc.cmN = nullptr;
+            h[q].sc.cment_n = nullptr;
             if (h[q].g.wmode != 0) b->any_segment_weights = true;
             if (h[q].b.sample_mode == AL_SAMPLE_GAUSS) b->any_gauss = true;
             if (h[q].b.reflect) b->any_reflect = true;

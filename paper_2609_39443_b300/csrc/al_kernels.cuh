@@ -49,7 +49,7 @@ constexpr double PI_D = 3.14159265358979323846;
 
 enum { ST_PA_OUTSIDE = 0, ST_PS_OUTSIDE = 1, ST_FALLBACK = 2, ST_FALLBACK_ZERO = 3,
        ST_ZERO_WEIGHT = 4, ST_DEPOSIT_LOST = 5, ST_REFINED = 6, ST_IRREGULAR = 7, ST_SUPPORT = 8,
-       ST_REPLAYED = 9, ST_COLUMN = 10 };
+       ST_REPLAYED = 9, ST_COLUMN = 10, ST_GUARD = 15 };
 
 struct GridC {
     int nx, ny, nz;
@@ -111,6 +111,8 @@ template <typename T> __device__ __forceinline__ T lgc(double d, float f);
 template <> __device__ __forceinline__ float lgc<float>(double, float f) { return f; }
 template <> __device__ __forceinline__ double lgc<double>(double d, float) { return d; }
 
+struct CmEnt;                    // column march: one candidate line of a brick (al_cm.cuh)
+
 template <typename T>
 struct Scratch {
     T *fprev;                    // [3][np] relaxed force of the previous step
@@ -141,6 +143,11 @@ struct Scratch {
     unsigned long long *rused;   // [1] arena taken by the next step's regions
     int *cmcnt;                  // [2] bricks of this step on the column-march / the brick passes
     int *cmlist;                 // [2][nbrick_max] those bricks
+    float4 *cmN;                 // [np][4] node records of the column march (NULL: not used)
+    CmEnt *cment;                // [cment_cap] entries of the column-march bricks
+    int *cment_n;                // [1] entries taken this step
+    long long cment_cap;
+    int *bent_off, *bent_n;      // [nbrick_max] a column-march brick's entries
 };
 
 template <typename T>
@@ -724,6 +731,7 @@ __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, 
     if (i == 0) {
         *sc.anyIrr = 0; *sc.smax = 0u; *sc.anyZero = 0;
         sc.cmcnt[0] = 0; sc.cmcnt[1] = 0;
+        if (sc.cment_n) *sc.cment_n = 0;
         sc.rplan[0] = sc.rplan[1];                        // the regions the last step sized
         sc.rplan[1] = 0;
         *sc.rused = 0ull;
@@ -784,6 +792,7 @@ __device__ void d_segments(const BeamsC &b, const Scratch<T> &sc, const int k) {
         for (int a = 0; a < 3; ++a) sc.nodeM[a * np + k] = (T)0;
         sc.nodeTau[k] = 0.0f;
     }
+    cm_write_node(sc, np, k, off);
 }
 
 // ---------------------------------------------------------------------------
@@ -907,9 +916,10 @@ __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     // rho = R + S min(Theta, 1) (Theta = (S / L_min + 2) theta_max its
     // turning) makes the bisector signs monotone over the candidates
     float Dcm = -1.0f;
-    // (and a brick's candidate range, at most (16 + 2 R + 0.06) / (L_min c_z) + 2
-    // segments, fits the stage)
-    if (sizeof(T) == 4 && base_ok && czp >= 0.8f && (16.0f + 2.0f * Rc + 0.06f) / (Lmin * czp) + 3.0f < (float)CM_NN) {
+    // (a brick's candidate range, at most (16 + 2 R + 0.06) / (L_min c_z) + 2
+    // segments, fits the stage; node positions relative to the line's first
+    // node stay below 256 cells, so their FP32 rounding is below 8e-6 cells)
+    if (sizeof(T) == 4 && base_ok && czp >= 0.8f && Ltot < 250.0f && (16.0f + 2.0f * Rc + 0.06f) / (Lmin * czp) + 3.0f < (float)CM_NN) {
         const float S = fminf((16.0f + 2.0f * Rc + 0.06f + 2.0f * Lmax) / czp, Ltot);
         const float Theta = (S / Lmin + 2.0f) * thmax;
         Dcm = Rc + S * fminf(Theta, 1.0f) + 0.01f;
@@ -1696,6 +1706,7 @@ __device__ unsigned int d_normalise(const GridC &g, const BeamsC &b, const Scrat
         for (int a = 0; a < 3; ++a) ins = ins && inside_axis(sc.uhi[a * np + k], sc.ulo[a * np + k], nn[a]);
         if (!ins) atomicAdd(&status[ST_DEPOSIT_LOST], 1);
     }
+    cm_write_fhat(sc, np, k, w);
     // rounded up to float with a relative margin (covers FP32 rounding of the products)
     return __float_as_uint(fminf(__double2float_ru(mb * 1.0000005), 3.0e38f));
 }

@@ -12,6 +12,14 @@ TOL_S_FP64 = 1e-11
 TOL_SUMF_FP64 = 1e-12
 TOL_CONS_FP64 = 1e-12
 
+# A batch (al_batch_*, and the server built on it) runs the brick passes for
+# every brick; an instance alone takes the column march where its bricks
+# allow.  Both are checked against the oracle; bit for bit, a batch equals
+# its instances run alone with the column march off.
+from paper_2609_39443_b300.al import OPT_COLUMN  # noqa: E402
+
+BRICK_PASSES = {OPT_COLUMN: 0}
+
 
 def run_gpu(wl, steps=1, inst=None):
     """Run `steps` coupling steps of a workload; returns numpy outputs of the last."""

@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_2609_39443_b300 import workloads as W
 
-from helpers import compare
+from helpers import BRICK_PASSES, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -29,7 +29,7 @@ def test_batch_equals_alone_bitwise(use_graph):
     import torch
     from paper_2609_39443_b300.al import Batch, Instance
     wls = _instances(1)
-    alone = [Instance(w) for w in wls]
+    alone = [Instance(w, options=BRICK_PASSES) for w in wls]
     inb = [Instance(w) for w in wls]
     batch = Batch(inb, use_graph=use_graph)
     for step in range(3):

@@ -32,6 +32,7 @@ def _run(wl, column=1, bz=None, steps=1, weights=None):
     torch.cuda.synchronize()
     out = {"S": inst.S.double().cpu().numpy(), "F": inst.F[:, :wl.beams.n_points].double().cpu().numpy(),
            "totals": inst.totals.cpu().numpy(), "status": inst.status.cpu().numpy()}
+    assert out["status"][15] == 0                    # no column-march index guard fired
     nbrick = -(-wl.grid.nx // 16) * -(-wl.grid.ny // 16) * -(-wl.grid.nz // (bz or 8))
     inst.close()
     return out, nbrick

@@ -10,7 +10,7 @@ import oracle
 from paper_2609_39443_b300 import workloads as W
 from paper_2609_39443_b300.al import OPT_RECORD, ST_REPLAYED
 
-from helpers import compare, run_gpu
+from helpers import BRICK_PASSES, compare, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -77,7 +77,7 @@ def test_integrated_batch_equals_alone():
     from paper_2609_39443_b300.al import Batch, Instance
     wls = W.make_batched(9, 4, max_cells=96 * 64 * 64)
     wls = [W.with_projection(w, "integrated") if q % 2 == 0 else w for q, w in enumerate(wls)]
-    alone, inb = [Instance(w) for w in wls], [Instance(w) for w in wls]
+    alone, inb = [Instance(w, options=BRICK_PASSES) for w in wls], [Instance(w) for w in wls]
     batch = Batch(inb, use_graph=True)
     for _ in range(3):
         for a in alone:

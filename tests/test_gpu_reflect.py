@@ -12,7 +12,7 @@ from paper_2609_39443_b300 import workloads as W
 from paper_2609_39443_b300.al import (OPT_RECORD, OPT_WEIGHTS, ST_SUPPORT, WEIGHTS_BRICK, ALError, Batch,
                                       Instance)
 
-from helpers import compare, run_gpu
+from helpers import BRICK_PASSES, compare, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +55,7 @@ def test_faces_out_of_reach_change_nothing():
     wl = W.make_canopy(3, 2.0, nx=96, ny=64, nz=48, n_sx=3, n_sy=3, n_cv=20, height=0.1)
     outs = []
     for mask in (0, W.REFLECT_X_HI | W.REFLECT_Y_LO):
-        inst = Instance(W.with_reflect(wl, mask))
+        inst = Instance(W.with_reflect(wl, mask), options=BRICK_PASSES)
         inst.grid.set_option(OPT_WEIGHTS, WEIGHTS_BRICK)
         inst.grid.set_option(OPT_RECORD, 0)
         outs.append(run_gpu(wl, inst=inst))
@@ -72,7 +72,7 @@ def test_batch_with_reflected_instances_equals_alone(use_graph):
     wls = [W.with_reflect(W.make_walls(11), 63), W.make_walls(12),
            W.with_reflect(W.make_canopy(4, 2.0, nx=64, ny=48, nz=64, n_sx=3, n_sy=3, n_cv=24, height=0.12),
                           W.REFLECT_Z_LO)]
-    alone = [Instance(w) for w in wls]
+    alone = [Instance(w, options=BRICK_PASSES) for w in wls]
     inb = [Instance(w) for w in wls]
     batch = Batch(inb, use_graph=use_graph)
     try:

@@ -13,7 +13,7 @@ import oracle
 from paper_2609_39443_b300 import workloads as W
 from paper_2609_39443_b300.al import (OPT_RECORD, OPT_WEIGHTS, ST_REPLAYED, ST_SUPPORT, WEIGHTS_SEGMENT)
 
-from helpers import compare
+from helpers import BRICK_PASSES, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +30,7 @@ def _run(wl, steps, record, moves=None, bz=None):
     of every step."""
     import torch
     from paper_2609_39443_b300.al import OPT_BRICK_Z, Instance
-    inst = Instance(wl)
+    inst = Instance(wl, options=BRICK_PASSES)
     inst.grid.set_option(OPT_WEIGHTS, WEIGHTS_SEGMENT)
     inst.grid.set_option(OPT_RECORD, 1 if record else 2)
     if bz:
@@ -109,7 +109,7 @@ def test_batch_replay_equals_alone():
     import torch
     from paper_2609_39443_b300.al import Batch, Instance
     wls = W.make_batched(6, 4, max_cells=96 * 64 * 64)
-    alone, inb = [Instance(w) for w in wls], [Instance(w) for w in wls]
+    alone, inb = [Instance(w, options=BRICK_PASSES) for w in wls], [Instance(w) for w in wls]
     for x in alone + inb:
         x.grid.set_option(OPT_WEIGHTS, WEIGHTS_SEGMENT)
     for x in alone:

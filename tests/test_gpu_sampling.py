@@ -11,7 +11,7 @@ import pytest
 import oracle
 from paper_2609_39443_b300 import workloads as W
 
-from helpers import compare, run_gpu
+from helpers import BRICK_PASSES, compare, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -85,7 +85,7 @@ def test_batch_with_volume_average_equals_alone(use_graph):
     from paper_2609_39443_b300.al import Batch, Instance
     wls = W.make_batched(5, 4, max_cells=96 * 64 * 64)
     wls = [W.with_sample_mode(w, "gauss") if q % 2 == 0 else w for q, w in enumerate(wls)]
-    alone = [Instance(w) for w in wls]
+    alone = [Instance(w, options=BRICK_PASSES) for w in wls]
     inb = [Instance(w) for w in wls]
     batch = Batch(inb, use_graph=use_graph)
     for _ in range(2):

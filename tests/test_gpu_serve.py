@@ -8,6 +8,8 @@ import pytest
 from paper_2609_39443_b300 import workloads as W
 from paper_2609_39443_b300.serve import BatchServer, Sim, poisson_arrivals
 
+from helpers import BRICK_PASSES
+
 pytestmark = pytest.mark.gpu
 
 
@@ -26,7 +28,7 @@ def test_served_mix_equals_each_simulation_alone(reflect):
     assert st.completed == len(arr)
     assert st.peak_mem <= budget
     for s, sim in enumerate(sims):
-        inst = Instance(sim.wl)
+        inst = Instance(sim.wl, options=BRICK_PASSES)
         for k in range(sim.n_steps):
             inst.set_points(P=sim.positions(k))
             inst.step()

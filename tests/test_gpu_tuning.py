@@ -9,7 +9,7 @@ import pytest
 import oracle
 from paper_2609_39443_b300 import workloads as W
 
-from helpers import compare, run_gpu
+from helpers import BRICK_PASSES, compare, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -68,7 +68,7 @@ def test_batch_options_equal_alone(bz, ctas):
     import torch
     from paper_2609_39443_b300.al import Batch, Instance, OPT_BRICK_Z, OPT_SPREAD_CTAS
     wls = W.make_batched(5, 5, max_cells=96 * 64 * 64)
-    alone = [Instance(w) for w in wls]
+    alone = [Instance(w, options=BRICK_PASSES) for w in wls]
     inb = [Instance(w) for w in wls]
     for a in alone:
         a.grid.set_option(OPT_BRICK_Z, bz)
@@ -95,7 +95,7 @@ def test_batch_autotune_keeps_results():
     import torch
     from paper_2609_39443_b300.al import Batch, Instance, OPT_BRICK_Z
     wls = W.make_batched(6, 4, max_cells=96 * 64 * 64)
-    alone = [Instance(w) for w in wls]
+    alone = [Instance(w, options=BRICK_PASSES) for w in wls]
     inb = [Instance(w) for w in wls]
     batch = Batch(inb, use_graph=True)
     batch.run()
