@@ -290,13 +290,19 @@ int al_trace_last(al_grid g, float *ms /* [AL_TRACE_N] */);
 #define AL_OPT_COLUMN       6
 int al_set_option(al_grid g, int option, int value);
 
+/* Kernels this instance's al_sample_drag_spread calls have launched so far
+ * (cumulative, counted on the host as they are enqueued; the autotuner's
+ * trial steps count too).  Returns AL_ERR_ARG for a NULL argument. */
+int al_launches(al_grid g, long long *n);
+
 /* Autotuner: runs the caller's step (same in/out as al_sample_drag_spread)
  * under every combination of AL_OPT_WEIGHTS (with AL_WEIGHTS_SEGMENT: with
- * and without AL_OPT_RECORD) and AL_OPT_BRICK_Z, `trials`
- * timed steps each after one warm-up, timed with CUDA events on `stream`, and
- * keeps the fastest.  The relaxation state and the status counters are
- * restored afterwards; S, F and totals hold the last trial's outputs.
- * *choice (optional) = 1000 * records + 100 * weights mode + brick height.  Synchronises the
+ * and without AL_OPT_RECORD), AL_OPT_BRICK_Z and, for instances that can take
+ * it, AL_OPT_COLUMN on and off, `trials` timed steps each after one warm-up,
+ * timed with CUDA events on `stream`, and keeps the fastest.  The relaxation
+ * state and the status counters are restored afterwards; S, F and totals
+ * hold the last trial's outputs.  *choice (optional) = 10000 * column march
+ * + 1000 * records + 100 * weights mode + brick height.  Synchronises the
  * stream; allocates a temporary copy of the relaxation state. */
 int al_autotune(al_grid g, const al_step_in *in, const al_step_out *out, int trials, void *stream, int *choice);
 

@@ -81,6 +81,7 @@ def lib():
         L.al_set_state.argtypes = [_vp, _vp, C.c_int, _vp]
         L.al_sizes.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
         L.al_footprint.argtypes = [_vp, C.POINTER(C.c_ulonglong)]
+        L.al_launches.argtypes = [_vp, C.POINTER(C.c_longlong)]
         L.al_beam_quasistatic.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp * 3, _vp * 3,
                                           _vp * 3, _vp]
         L.al_batch_create.argtypes = [C.POINTER(_vp)]
@@ -247,6 +248,12 @@ class Grid:
         check(lib().al_footprint(self.h, C.byref(b)), "al_footprint")
         return int(b.value)
 
+    def launches(self) -> int:
+        """al_launches: kernels this instance's steps have launched so far."""
+        n = C.c_longlong(0)
+        check(lib().al_launches(self.h, C.byref(n)), "al_launches")
+        return int(n.value)
+
     def trace(self, on: bool = True) -> None:
         check(lib().al_trace_enable(self.h, int(bool(on))), "al_trace_enable")
 
@@ -313,12 +320,14 @@ class Instance:
             self.P_spread.copy_(torch.as_tensor(np.ascontiguousarray(P_spread), dtype=self.dtype))
 
     def autotune(self, trials: int = 3, stream=None):
-        """al_autotune on this instance's step; returns (weights mode, brick height, records)."""
+        """al_autotune on this instance's step; returns (weights mode, brick height, records,
+        column march)."""
         sin, sout = self.descriptors()
         ch = C.c_int(0)
         check(lib().al_autotune(self.grid.h, C.byref(sin), C.byref(sout), int(trials), _stream_ptr(stream),
                                 C.byref(ch)), "al_autotune")
-        return (ch.value // 100) % 10, ch.value % 100, ch.value // 1000
+        v = ch.value
+        return (v // 100) % 10, v % 100, (v // 1000) % 10, v // 10000
 
     def descriptors(self):
         return step_descriptors(self.U, self.P, self.Pdot, self.S, self.F, alpha=self.alpha,

@@ -94,6 +94,7 @@ struct al_grid_s {
     int *cmcnt = nullptr;             // [2] bricks of a step on the column-march / the brick passes
     int *cmlist = nullptr;            // [2][nbrick_max] those bricks
     int opt_column = 1;               // AL_OPT_COLUMN
+    long long launches = 0;           // kernels launched by this instance's steps (al_launches)
     // column march (FP32, nearest-segment projection, no reflection): node
     // records, entries of the column-march bricks
     float4 *cmN = nullptr;            // [np][4] node records
@@ -638,27 +639,33 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
     AL_CUDA(spread_smem_attr<T>());
     trace_mark(g, 0, st);
     const int nb = (np + 255) / 256;
+    long long nl = 0;                                        // kernels launched by this step
     if (np > 0) {
+        nl += 2;
         if (bc.sample_mode == AL_SAMPLE_GAUSS)               // one warp per point
             k_points_w<T><<<(unsigned)(((long long)np * 32 + 255) / 256), 256, 0, st>>>(gc, bc, p, sc, status);
         else
             k_points<T><<<nb, 256, 0, st>>>(gc, bc, p, sc, status);
         k_segments<T><<<nb, 256, 0, st>>>(bc, sc);
     }
-    if (g->n_lines > 0) k_lines<T><<<(g->n_lines + 7) / 8, 256, 0, st>>>(gc, bc, sc, p, status);
+    if (g->n_lines > 0) { k_lines<T><<<(g->n_lines + 7) / 8, 256, 0, st>>>(gc, bc, sc, p, status); ++nl; }
     trace_mark(g, 1, st);
-    if (np > 0) k_mask<T><<<nb, 256, 0, st>>>(gc, bc, sc);
+    if (np > 0) { k_mask<T><<<nb, 256, 0, st>>>(gc, bc, sc); ++nl; }
     if constexpr (std::is_same<T, float>::value) {
         if (gc.cm) {
             if (np == 0) AL_CUDA(cudaMemsetAsync(g->cmcnt, 0, 2 * sizeof(int), st));   // (k_points resets them)
             k_cm_entries<float><<<(unsigned)((gc.nbrick * 32 + 255) / 256), 256, 0, st>>>(gc, bc, sc, status);
+            ++nl;
         }
     }
     trace_mark(g, 2, st);
     const bool cm = std::is_same<T, float>::value && gc.cm;
     if (np > 0) {
-        if (gc.wmode != 0)
+        if (gc.wmode != 0) {
             k_weights<T><<<(unsigned)(((long long)np * 32 + 127) / 128), 128, 0, st>>>(gc, bc, sc, p, status);
+            ++nl;
+        }
+        nl += cm ? 2 : 1;
         if constexpr (std::is_same<T, float>::value) {
             if (cm) {
                 const int rc = cm_launch_bz(I, true, st);
@@ -671,8 +678,9 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
         }
     }
     trace_mark(g, 3, st);
-    if (np > 0) k_normalise<T><<<nb, 256, 0, st>>>(gc, bc, sc, p, status);
+    if (np > 0) { k_normalise<T><<<nb, 256, 0, st>>>(gc, bc, sc, p, status); ++nl; }
     trace_mark(g, 4, st);
+    nl += cm ? 2 : 1;
     if constexpr (std::is_same<T, float>::value) {
         if (cm) {
             const int rc = cm_launch_bz(I, false, st);
@@ -688,9 +696,12 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
         // gather has written every cell (uncertified lines and deposits)
         AL_CUDA(cudaMemsetAsync(g->scatSum, 0, 3 * sizeof(double), st));
         k_scatter<T><<<(unsigned)(((long long)np * 32 + 127) / 128), 128, 0, st>>>(gc, bc, sc, p, status);
+        ++nl;
     }
     trace_mark(g, 5, st);
     k_totals<T><<<1, 256, 0, st>>>(gc, bc, sc, I.totals);
+    ++nl;
+    g->launches += nl;
     trace_mark(g, 6, st);
     AL_CUDA(cudaGetLastError());
     return AL_OK;
@@ -1275,30 +1286,35 @@ extern "C" int al_autotune(al_grid g, const al_step_in *in, const al_step_out *o
     if (rc == AL_OK && (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess))
         rc = AL_ERR_CUDA;
     // weights pass and records: brick; segment without records; segment with
-    // records (the warm-up step sizes the record regions the timed steps use)
+    // records (the warm-up step sizes the record regions the timed steps use);
+    // the column march on and off where the instance can take it
     const int wms[3] = {AL_WEIGHTS_BRICK, AL_WEIGHTS_SEGMENT, AL_WEIGHTS_SEGMENT}, recs[3] = {0, 0, 1};
     const int bzs[3] = {4, 8, 16};
+    const int ncol = g->cmN ? 2 : 1;
     float best = INFINITY;
-    int best_w = g->gc.wmode, best_z = g->gc.bz, best_r = g->opt_record;
-    for (int wi = 0; wi < 3 && rc == AL_OK; ++wi)
-        for (int zi = 0; zi < 3 && rc == AL_OK; ++zi) {
-            g->gc.wmode = wms[wi];
-            g->opt_record = recs[wi];
-            set_brick_z(g->gc, bzs[zi]);
-            if ((rc = arena_sync(g)) != AL_OK) break;
-            if ((rc = restore_state(g, out, sv, st)) != AL_OK) break;
-            if ((rc = al_sample_drag_spread(g, in, out, stream)) != AL_OK) break;       // warm-up
-            if (cudaEventRecord(ev.a, st) != cudaSuccess) { rc = AL_ERR_CUDA; break; }
-            for (int t = 0; t < trials && rc == AL_OK; ++t) rc = al_sample_drag_spread(g, in, out, stream);
-            if (rc != AL_OK) break;
-            if (cudaEventRecord(ev.b, st) != cudaSuccess || cudaEventSynchronize(ev.b) != cudaSuccess) {
-                rc = AL_ERR_CUDA;
-                break;
+    int best_w = g->gc.wmode, best_z = g->gc.bz, best_r = g->opt_record, best_c = g->opt_column;
+    for (int ci = 0; ci < ncol && rc == AL_OK; ++ci)
+        for (int wi = 0; wi < 3 && rc == AL_OK; ++wi)
+            for (int zi = 0; zi < 3 && rc == AL_OK; ++zi) {
+                g->opt_column = ncol == 2 ? 1 - ci : g->opt_column;
+                g->gc.wmode = wms[wi];
+                g->opt_record = recs[wi];
+                set_brick_z(g->gc, bzs[zi]);
+                if ((rc = arena_sync(g)) != AL_OK) break;
+                if ((rc = restore_state(g, out, sv, st)) != AL_OK) break;
+                if ((rc = al_sample_drag_spread(g, in, out, stream)) != AL_OK) break;       // warm-up
+                if (cudaEventRecord(ev.a, st) != cudaSuccess) { rc = AL_ERR_CUDA; break; }
+                for (int t = 0; t < trials && rc == AL_OK; ++t) rc = al_sample_drag_spread(g, in, out, stream);
+                if (rc != AL_OK) break;
+                if (cudaEventRecord(ev.b, st) != cudaSuccess || cudaEventSynchronize(ev.b) != cudaSuccess) {
+                    rc = AL_ERR_CUDA;
+                    break;
+                }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, ev.a, ev.b);
+                if (ms < best) { best = ms; best_w = wms[wi]; best_z = bzs[zi]; best_r = recs[wi]; best_c = g->opt_column; }
             }
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, ev.a, ev.b);
-            if (ms < best) { best = ms; best_w = wms[wi]; best_z = bzs[zi]; best_r = recs[wi]; }
-        }
+    g->opt_column = best_c;
     g->gc.wmode = best_w;
     g->opt_record = best_r;
     set_brick_z(g->gc, best_z);
@@ -1306,7 +1322,7 @@ extern "C" int al_autotune(al_grid g, const al_step_in *in, const al_step_out *o
     if (rc2 == AL_OK) rc2 = restore_state(g, out, sv, st);
     if (sv.fprev) cudaFree(sv.fprev);
     if (rc == AL_OK) rc = rc2;
-    if (rc == AL_OK && choice) *choice = 1000 * best_r + 100 * best_w + best_z;
+    if (rc == AL_OK && choice) *choice = 10000 * best_c + 1000 * best_r + 100 * best_w + best_z;
     return rc;
 }
 
@@ -1374,4 +1390,10 @@ extern "C" int al_batch_autotune(al_batch b, int trials, void *stream, int *choi
     if (rc == AL_OK) rc = rc2;
     if (rc == AL_OK && choice) *choice = 10 * best_z + best_c;
     return rc;
+}
+
+extern "C" int al_launches(al_grid g, long long *n) {
+    if (!g || !n) return AL_ERR_ARG;
+    *n = g->launches;
+    return AL_OK;
 }

@@ -52,7 +52,7 @@ def test_autotuner_keeps_the_arena_only_for_a_recording_choice():
     wl = W.make_canopy(1, 2.0, nx=128, ny=64, nz=64, n_sx=10, n_sy=10)
     inst = Instance(wl)
     base = inst.grid.footprint()
-    wmode, bz, rec = inst.autotune(trials=1)
+    wmode, bz, rec, _ = inst.autotune(trials=1)
     fp = inst.grid.footprint()
     assert (fp > base) == bool(rec and wmode == 1), (fp, base, wmode, rec)
     g = run_gpu(wl, inst=inst)

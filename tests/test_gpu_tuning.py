@@ -38,15 +38,16 @@ def test_every_option_matches_the_oracle(wmode, bz):
 
 def test_autotune_restores_state_and_applies_choice():
     import torch
-    from paper_2609_39443_b300.al import Instance, OPT_BRICK_Z, OPT_WEIGHTS
+    from paper_2609_39443_b300.al import Instance, OPT_BRICK_Z, OPT_COLUMN, OPT_WEIGHTS
     wl = W.random_canopy(23, 80, 48, 40, 0.005, 120, 30, 2.0, name="tuned")
     a, b = Instance(wl), Instance(wl)
     a.step()
     b.step()
-    wmode, bz, rec = a.autotune(trials=1)
-    assert wmode in (0, 1) and bz in (4, 8, 16) and rec in (0, 1)
+    wmode, bz, rec, col = a.autotune(trials=1)
+    assert wmode in (0, 1) and bz in (4, 8, 16) and rec in (0, 1) and col in (0, 1)
     b.grid.set_option(OPT_WEIGHTS, wmode)
     b.grid.set_option(OPT_BRICK_Z, bz)
+    b.grid.set_option(OPT_COLUMN, col)
     for x in (a, b):
         x.status.zero_()
         x.step()
