@@ -309,11 +309,13 @@ int al_autotune(al_grid g, const al_step_in *in, const al_step_out *out, int tri
 /* Sizes of an instance: cells and points. */
 int al_sizes(al_grid g, long long *n_cells, long long *n_points, int *n_lines);
 
-/* Device bytes the library holds for the instance: per-grid scratch
- * (al_create_grid), per-point scratch and line table (al_load_beams) and the
- * record arena while records are on (AL_OPT_RECORD).  The caller's fields,
- * points and outputs are not included.  An admission controller adds them
- * to this figure to bound what a resident instance takes. */
+/* Device bytes the library holds for the instance.  It holds at most three
+ * allocations: per-grid scratch (al_create_grid), per-point scratch and line
+ * table (al_load_beams) and the record arena while records are on
+ * (AL_OPT_RECORD); each is counted rounded up to whole 2 MiB pages, the unit
+ * the driver commits.  The caller's fields, points and outputs are not
+ * included.  An admission controller adds them to this figure to bound what
+ * a resident instance takes. */
 int al_footprint(al_grid g, unsigned long long *bytes);
 
 /* Quasi-static reconstruction of the beam side (the structural check of the
@@ -404,7 +406,8 @@ typedef struct {
                                       declares for its own buffers at admission */
     int max_sims;                  /* slots: simulations resident at a time, >= 1 */
     int max_wave;                  /* simulations advanced by one wave, 1 .. max_sims */
-    int max_points;                /* largest N_p of a simulation (sizes the staging buffers) */
+    int max_points;                /* points one wave carries at most (sizes the staging buffers);
+                                      no simulation may have more */
     int precision;                 /* AL_FP32 or AL_FP64, shared by every simulation */
 } al_server_desc;
 int al_server_create(const al_server_desc *desc, al_server *out);
@@ -423,7 +426,7 @@ int al_server_admit(al_server s, const al_grid_desc *grid, const al_beam_desc *b
  * al_server_poll.  Both buffers stay valid until then. */
 int al_server_submit(al_server s, int sim, const void *P_host, void *F_host, long long tag);
 /* Progress: retire the waves that completed (their forces unpacked into the
- * requests' F_host), then launch one wave on a free stream.  Writes up to
+ * requests' F_host), then launch a wave on each free stream.  Writes up to
  * max_done tags of completed requests (the rest are reported by later
  * polls).  wait != 0: if nothing has completed, wait for the oldest wave in
  * flight. */
@@ -435,6 +438,8 @@ int al_server_release(al_server s, int sim);
 /* Device bytes held by the resident simulations (as counted at admission)
  * and how many are resident (optional). */
 int al_server_footprint(al_server s, unsigned long long *bytes, int *resident);
+/* Waves launched so far and the steps they carried (mean wave = steps / waves). */
+int al_server_stats(al_server s, long long *waves, long long *steps);
 int al_server_destroy(al_server s);
 
 /* ---- line forces without device allocation ----------------------------- */

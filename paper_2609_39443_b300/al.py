@@ -59,6 +59,11 @@ class StepOut(C.Structure):
     _fields_ = [("S", _vp * 3), ("F", _vp * 3), ("totals", _dp), ("status", C.POINTER(C.c_int))]
 
 
+class ServerDesc(C.Structure):
+    _fields_ = [("hbm_budget", C.c_ulonglong), ("max_sims", C.c_int), ("max_wave", C.c_int),
+                ("max_points", C.c_int), ("precision", C.c_int)]
+
+
 class ALError(RuntimeError):
     pass
 
@@ -100,6 +105,15 @@ def lib():
         L.al_batch_set_option.argtypes = [_vp, C.c_int, C.c_int]
         L.al_batch_autotune.argtypes = [_vp, C.c_int, _vp, C.POINTER(C.c_int)]
         L.al_trace_last.argtypes = [_vp, C.POINTER(C.c_float)]
+        L.al_server_create.argtypes = [C.POINTER(ServerDesc), C.POINTER(_vp)]
+        L.al_server_admit.argtypes = [_vp, C.POINTER(GridDesc), C.POINTER(BeamDesc), C.POINTER(StepIn),
+                                      C.POINTER(StepOut), C.c_ulonglong, C.POINTER(C.c_int)]
+        L.al_server_submit.argtypes = [_vp, C.c_int, _vp, _vp, C.c_longlong]
+        L.al_server_poll.argtypes = [_vp, C.POINTER(C.c_longlong), C.c_int, C.POINTER(C.c_int), C.c_int]
+        L.al_server_release.argtypes = [_vp, C.c_int]
+        L.al_server_footprint.argtypes = [_vp, C.POINTER(C.c_ulonglong), C.POINTER(C.c_int)]
+        L.al_server_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+        L.al_server_destroy.argtypes = [_vp]
         L.al_error_string.restype = C.c_char_p
         L.al_error_string.argtypes = [C.c_int]
         L.al_last_cuda_error.restype = C.c_char_p
@@ -191,12 +205,16 @@ class Grid:
     """One actuator-line instance: al_create_grid / al_load_beams /
     al_sample_drag_spread / al_destroy."""
 
+    @staticmethod
+    def descriptor(grid) -> GridDesc:
+        return GridDesc(int(grid.nx), int(grid.ny), int(grid.nz), float(grid.h),
+                        (C.c_double * 3)(*map(float, grid.origin)),
+                        AL_FP64 if grid.precision == "fp64" else AL_FP32, int(bool(grid.has_alpha)),
+                        float(grid.rho1), float(grid.rho2), float(grid.rho_const))
+
     def __init__(self, grid):
         self.spec = grid
-        self.desc = GridDesc(int(grid.nx), int(grid.ny), int(grid.nz), float(grid.h),
-                             (C.c_double * 3)(*map(float, grid.origin)),
-                             AL_FP64 if grid.precision == "fp64" else AL_FP32, int(bool(grid.has_alpha)),
-                             float(grid.rho1), float(grid.rho2), float(grid.rho_const))
+        self.desc = Grid.descriptor(grid)
         h = _vp()
         check(lib().al_create_grid(C.byref(self.desc), C.byref(h)), "al_create_grid")
         self.h = h
@@ -413,3 +431,70 @@ def line_forces_noalloc(grid, beams, U, P, Pdot, F, *, alpha=None, tangent=None,
     st = C.cast(_ptr(status), C.POINTER(C.c_int)) if status is not None else None
     check(lib().al_line_forces_noalloc(C.byref(gd), C.byref(ba.desc), C.byref(sin), fp, fo, st,
                                        _stream_ptr(stream)), "al_line_forces_noalloc")
+
+
+class Server:
+    """al_server_*: continuous batching of coupling-step requests in the
+    library.  Simulations are admitted with their own device buffers
+    (descriptors as for al_sample_drag_spread); requests carry host positions
+    and receive host line forces; poll() retires finished waves and launches
+    the next one."""
+
+    def __init__(self, hbm_budget: int, max_sims: int, max_wave: int, max_points: int, precision: str = "fp32"):
+        self.desc = ServerDesc(int(hbm_budget), int(max_sims), int(max_wave), int(max_points),
+                               AL_FP64 if precision == "fp64" else AL_FP32)
+        h = _vp()
+        check(lib().al_server_create(C.byref(self.desc), C.byref(h)), "al_server_create")
+        self.h = h
+        self._done = (C.c_longlong * 4096)()
+
+    def admit(self, grid_spec, beams, sin, sout, caller_bytes: int) -> Optional[int]:
+        """The slot of the admitted simulation, or None when it does not fit
+        (no free slot, too many points, or over the budget)."""
+        gd = Grid.descriptor(grid_spec)
+        ba = BeamArrays(beams)
+        sim = C.c_int(-1)
+        rc = lib().al_server_admit(self.h, C.byref(gd), C.byref(ba.desc), C.byref(sin), C.byref(sout),
+                                   int(caller_bytes), C.byref(sim))
+        if rc == AL_ERR_CAPACITY:
+            return None
+        check(rc, "al_server_admit")
+        return int(sim.value)
+
+    def submit(self, sim: int, P_host: np.ndarray, F_host: np.ndarray, tag: int) -> None:
+        """P_host / F_host: C-contiguous (3, N_p) host arrays of the precision,
+        kept alive by the caller until the tag is reported."""
+        check(lib().al_server_submit(self.h, int(sim), P_host.ctypes.data, F_host.ctypes.data, int(tag)),
+              "al_server_submit")
+
+    def poll(self, wait: bool = False):
+        n = C.c_int(0)
+        check(lib().al_server_poll(self.h, self._done, len(self._done), C.byref(n), int(bool(wait))),
+              "al_server_poll")
+        return [int(self._done[i]) for i in range(n.value)]
+
+    def release(self, sim: int) -> None:
+        check(lib().al_server_release(self.h, int(sim)), "al_server_release")
+
+    def footprint(self):
+        """(device bytes held by the resident simulations, how many are resident)"""
+        b, r = C.c_ulonglong(0), C.c_int(0)
+        check(lib().al_server_footprint(self.h, C.byref(b), C.byref(r)), "al_server_footprint")
+        return int(b.value), int(r.value)
+
+    def waves(self):
+        """(waves launched, steps they carried)"""
+        w, n = C.c_longlong(0), C.c_longlong(0)
+        check(lib().al_server_stats(self.h, C.byref(w), C.byref(n)), "al_server_stats")
+        return int(w.value), int(n.value)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            check(lib().al_server_destroy(self.h), "al_server_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

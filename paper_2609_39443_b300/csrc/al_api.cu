@@ -29,14 +29,23 @@ int cuda_fail(cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
 
-template <typename P>
-cudaError_t dalloc(P **p, size_t n, size_t *acc = nullptr) {
-    *p = nullptr;
-    if (n == 0) n = 1;
-    const cudaError_t e = cudaMalloc((void **)p, n * sizeof(P));
-    if (e == cudaSuccess && acc) *acc += n * sizeof(P);
-    return e;
-}
+// One device allocation carved into an instance's arrays, 256-byte aligned:
+// the same sequence of take() calls first sizes it (base == nullptr), then
+// hands out the pointers.  A few allocations per instance instead of one per
+// array: admission is cheaper and the memory it holds is exactly the slabs.
+struct Slab {
+    size_t off = 0;
+    char *base = nullptr;
+    void *take_bytes(size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        void *p = base ? base + off : nullptr;
+        off += bytes ? bytes : 1;
+        return p;
+    }
+    template <typename P> void take(P **p, size_t n) { *p = static_cast<P *>(take_bytes((n ? n : 1) * sizeof(P))); }
+};
+// device bytes the driver commits for an allocation: whole 2 MiB pages
+static size_t page_round(size_t bytes) { return bytes ? (bytes + (2u << 20) - 1) & ~(size_t)((2u << 20) - 1) : 0; }
 
 // brick decomposition of the projection for brick height bz
 void set_brick_z(al::GridC &c, int bz) {
@@ -109,6 +118,7 @@ struct al_grid_s {
     // device bytes this instance holds (al_footprint): per-grid scratch,
     // per-point scratch of the loaded lines, record arena
     size_t grid_bytes = 0, beam_bytes = 0, rec_bytes = 0;
+    void *grid_slab = nullptr, *beam_slab = nullptr;   // the allocations the per-grid / per-line arrays live in
 
     // tracing
     bool trace = false;
@@ -120,12 +130,9 @@ static void trace_mark(al_grid g, int i, cudaStream_t st) {
 }
 
 static void free_beams(al_grid g) {
-    void *ptrs[] = {g->d_line_off, g->d_line_of, g->d_d, g->d_cdn, g->d_cdt, g->d_eps, g->d_ell, g->d_af,
-                    g->d_cvl, g->d_cmn, g->d_cmt, g->d_EI, g->fprev, g->uhi, g->segD, g->segIl2, g->nodeM, g->fhat, g->ulo,
-                    g->nodeTau, g->segWa, g->segWb, g->w, g->lineF, g->lines, g->mask, g->wfix, g->rec,
-                    g->cmN, g->cment, g->cment_n, g->bent_off, g->bent_n};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
+    if (g->beam_slab) cudaFree(g->beam_slab);
+    if (g->rec) cudaFree(g->rec);
+    g->beam_slab = nullptr;
     g->d_line_off = g->d_line_of = nullptr;
     g->d_d = g->d_cdn = g->d_cdt = g->d_eps = g->d_ell = g->d_af = g->d_cvl = g->d_cmn = g->d_cmt = nullptr;
     g->d_EI = nullptr;
@@ -199,23 +206,28 @@ extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
     c.has_alpha = d.has_alpha ? 1 : 0;
     c.rho1 = d.rho1; c.rho2 = d.rho2; c.rho_const = d.rho_const;
 
-    cudaError_t e;
-    size_t *gb = &g->grid_bytes;
-    if ((e = dalloc(&g->brickSum, 3 * (size_t)g->nbrick_max, gb)) != cudaSuccess ||
-        (e = dalloc(&g->scatSum, 3, gb)) != cudaSuccess ||
-        (e = dalloc(&g->statusInt, AL_STATUS_N, gb)) != cudaSuccess || (e = dalloc(&g->totalsInt, 6, gb)) != cudaSuccess ||
-        (e = dalloc(&g->hasPrev, 1, gb)) != cudaSuccess || (e = dalloc(&g->anyIrr, 1, gb)) != cudaSuccess ||
-        (e = dalloc(&g->smax, 1, gb)) != cudaSuccess || (e = dalloc(&g->anyZero, 1, gb)) != cudaSuccess ||
-        (e = dalloc(&g->rcnt, (size_t)g->nbrick_max, gb)) != cudaSuccess ||
-        (e = dalloc(&g->rcap, (size_t)g->nbrick_max, gb)) != cudaSuccess ||
-        (e = dalloc(&g->roff, (size_t)g->nbrick_max, gb)) != cudaSuccess ||
-        (e = dalloc(&g->rplan, 2, gb)) != cudaSuccess || (e = dalloc(&g->rused, 1, gb)) != cudaSuccess ||
-        (e = dalloc(&g->cmcnt, 2, gb)) != cudaSuccess ||
-        (e = dalloc(&g->cmlist, 2 * (size_t)g->nbrick_max, gb)) != cudaSuccess) {
+    auto carve = [&](Slab &sl) {
+        sl.take(&g->brickSum, 3 * (size_t)g->nbrick_max);
+        sl.take(&g->scatSum, 3);
+        sl.take(&g->statusInt, AL_STATUS_N); sl.take(&g->totalsInt, 6);
+        sl.take(&g->hasPrev, 1); sl.take(&g->anyIrr, 1); sl.take(&g->smax, 1); sl.take(&g->anyZero, 1);
+        sl.take(&g->rcnt, (size_t)g->nbrick_max); sl.take(&g->rcap, (size_t)g->nbrick_max);
+        sl.take(&g->roff, (size_t)g->nbrick_max);
+        sl.take(&g->rplan, 2); sl.take(&g->rused, 1);
+        sl.take(&g->cmcnt, 2); sl.take(&g->cmlist, 2 * (size_t)g->nbrick_max);
+    };
+    Slab size;
+    carve(size);
+    Slab sl;
+    const cudaError_t e = cudaMalloc((void **)&sl.base, size.off);
+    if (e != cudaSuccess) {
         int rc = cuda_fail(e, "cudaMalloc");
         al_destroy(g);
         return rc;
     }
+    carve(sl);
+    g->grid_slab = sl.base;
+    g->grid_bytes = size.off;
     *out = g;
     return AL_OK;
 }
@@ -341,43 +353,47 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     g->bd = b;
     const size_t es = g->esize, n3 = 3 * (size_t)np;
     const size_t nl = (size_t)b.n_lines;
-    cudaError_t e = cudaSuccess;
-    auto A = [&](auto **p, size_t n) {
-        if (e == cudaSuccess) e = dalloc(p, n, &g->beam_bytes);
+    g->cment_cap = 0;
+    auto carve = [&](Slab &sl) {
+        auto A = [&](auto **p, size_t n) { sl.take(p, n); };
+        auto AB = [&](void **p, size_t n) { *p = sl.take_bytes((n ? n : 1) * es); };
+        A(&g->d_line_off, nl + 1);
+        A(&g->d_line_of, (size_t)np);
+        A(&g->d_d, nl); A(&g->d_cdn, nl); A(&g->d_cdt, nl); A(&g->d_eps, nl); A(&g->d_ell, nl); A(&g->d_af, nl);
+        A(&g->d_cvl, (size_t)np);
+        if (b.cm_n) { A(&g->d_cmn, nl); A(&g->d_cmt, nl); }
+        A(&g->d_EI, nl);
+        AB(&g->fprev, n3); AB(&g->uhi, n3); AB(&g->segD, n3); AB(&g->segIl2, (size_t)np); AB(&g->nodeM, n3);
+        AB(&g->fhat, n3);
+        A(&g->ulo, n3); A(&g->nodeTau, (size_t)np);
+        A(&g->segWa, (size_t)np); A(&g->segWb, (size_t)np);
+        A(&g->wfix, (size_t)np); A(&g->w, (size_t)np); A(&g->lineF, 3 * nl);
+        A(&g->lines, nl);
+        A(&g->mask, (size_t)g->nbrick_max * g->mask_words);
+        if (g->d.precision == AL_FP32 && b.proj_mode == AL_PROJ_NEAREST && !b.wall_reflect && np > 0) {
+            // the column march: four float4 records per node, and an entry pool of
+            // 16 entries per brick at the lowest brick height (bricks beyond it in
+            // a step take the brick passes)
+            A(&g->cmN, 4 * (size_t)np);
+            g->cment_cap = 16 * g->nbrick_max;
+            A(&g->cment, (size_t)g->cment_cap);
+            A(&g->cment_n, 1);
+            A(&g->bent_off, (size_t)g->nbrick_max);
+            A(&g->bent_n, (size_t)g->nbrick_max);
+        }
     };
-    auto AB = [&](void **p, size_t n) {
-        if (e == cudaSuccess) e = cudaMalloc(p, (n ? n : 1) * es);
-        if (e == cudaSuccess) g->beam_bytes += (n ? n : 1) * es;
-    };
-    A(&g->d_line_off, nl + 1);
-    A(&g->d_line_of, (size_t)np);
-    A(&g->d_d, nl); A(&g->d_cdn, nl); A(&g->d_cdt, nl); A(&g->d_eps, nl); A(&g->d_ell, nl); A(&g->d_af, nl);
-    A(&g->d_cvl, (size_t)np);
-    if (b.cm_n) { A(&g->d_cmn, nl); A(&g->d_cmt, nl); }
-    A(&g->d_EI, nl);
-    AB(&g->fprev, n3); AB(&g->uhi, n3); AB(&g->segD, n3); AB(&g->segIl2, (size_t)np); AB(&g->nodeM, n3);
-    AB(&g->fhat, n3);
-    A(&g->ulo, n3); A(&g->nodeTau, (size_t)np);
-    A(&g->segWa, (size_t)np); A(&g->segWb, (size_t)np);
-    A(&g->wfix, (size_t)np); A(&g->w, (size_t)np); A(&g->lineF, 3 * nl);
-    A(&g->lines, nl);
-    A(&g->mask, (size_t)g->nbrick_max * g->mask_words);
-    if (g->d.precision == AL_FP32 && b.proj_mode == AL_PROJ_NEAREST && !b.wall_reflect && np > 0) {
-        // the column march: four float4 records per node, and an entry pool of
-        // 16 entries per brick at the lowest brick height (bricks beyond it in
-        // a step take the brick passes)
-        A(&g->cmN, 4 * (size_t)np);
-        g->cment_cap = 16 * g->nbrick_max;
-        A(&g->cment, (size_t)g->cment_cap);
-        A(&g->cment_n, 1);
-        A(&g->bent_off, (size_t)g->nbrick_max);
-        A(&g->bent_n, (size_t)g->nbrick_max);
-    }
+    Slab size;
+    carve(size);
+    Slab sl;
+    const cudaError_t e = cudaMalloc((void **)&sl.base, size.off);
     if (e != cudaSuccess) {
         int rc = cuda_fail(e, "cudaMalloc");
         free_beams(g);
         return rc;
     }
+    carve(sl);
+    g->beam_slab = sl.base;
+    g->beam_bytes = size.off;
     std::vector<int> off(nl + 1, 0), of((size_t)np);
     if (b.n_lines > 0) {
         for (size_t l = 0; l <= nl; ++l) off[l] = b.line_off[l];
@@ -785,10 +801,7 @@ extern "C" int al_destroy(al_grid g) {
     cudaDeviceSynchronize();
     if (g->trace) al_trace_enable(g, 0);
     free_beams(g);
-    void *ptrs[] = {g->brickSum, g->scatSum, g->statusInt, g->totalsInt, g->hasPrev, g->anyIrr, g->smax,
-                    g->anyZero, g->rcnt, g->rcap, g->roff, g->rplan, g->rused, g->cmcnt, g->cmlist};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
+    if (g->grid_slab) cudaFree(g->grid_slab);
     delete g;
     return AL_OK;
 }
@@ -874,7 +887,7 @@ extern "C" int al_sizes(al_grid g, long long *n_cells, long long *n_points, int 
 
 extern "C" int al_footprint(al_grid g, unsigned long long *bytes) {
     if (!g || !bytes) return AL_ERR_ARG;
-    *bytes = (unsigned long long)(g->grid_bytes + g->beam_bytes + g->rec_bytes);
+    *bytes = (unsigned long long)(page_round(g->grid_bytes) + page_round(g->beam_bytes) + page_round(g->rec_bytes));
     return AL_OK;
 }
 

@@ -113,9 +113,10 @@ struct al_server_s {
     int next_stream = 0;
     int rr = 0;                       // round-robin start of wave formation
     std::vector<long long> done;      // tags completed, not yet reported
+    long long n_waves = 0, n_wave_steps = 0;   // waves launched, steps they carried
 };
 
-static size_t sv_stage_elems(const al_server_desc &d) { return 3 * (size_t)d.max_wave * (size_t)d.max_points; }
+static size_t sv_stage_elems(const al_server_desc &d) { return 3 * (size_t)d.max_points; }
 
 extern "C" int al_server_create(const al_server_desc *d, al_server *out) {
     if (!d || !out) return AL_ERR_ARG;
@@ -273,20 +274,20 @@ extern "C" int al_server_poll(al_server s, long long *done_tags, int max_done, i
         const int rc = sv_retire(s, k, false);
         if (rc != AL_OK) return rc;
     }
-    // one wave on a free stream: each resident simulation with a queued request and none in flight
-    int k = -1;
+    // a wave on each free stream: each resident simulation with a queued
+    // request and none in flight (the second wave takes what the first left)
+    const int k0 = s->next_stream;
     for (int t = 0; t < 2; ++t) {
-        const int c = (s->next_stream + t) & 1;
-        if (!s->wave[c].live) { k = c; break; }
-    }
-    if (k >= 0) {
+        const int k = (k0 + t) & 1;
+        if (s->wave[k].live) continue;
         Wave &w = s->wave[k];
         const int ns = (int)s->sims.size();
         long long off = 0;
-        for (int t = 0; t < ns && (int)w.sims.size() < s->d.max_wave; ++t) {
-            const int q = (s->rr + t) % ns;
+        for (int u = 0; u < ns && (int)w.sims.size() < s->d.max_wave; ++u) {
+            const int q = (s->rr + u) % ns;
             Sim &m = s->sims[q];
             if (!m.used || m.busy || m.queue.empty()) continue;
+            if (off + 3 * (long long)m.n_points > 3 * (long long)s->d.max_points) continue;   // staging full
             w.sims.push_back(q);
             w.reqs.push_back(m.queue.front());
             w.offs.push_back(off);
@@ -294,12 +295,13 @@ extern "C" int al_server_poll(al_server s, long long *done_tags, int max_done, i
             m.busy = true;
             off += 3 * (long long)m.n_points;
         }
-        if (!w.sims.empty()) {
-            s->rr = (w.sims.back() + 1) % ns;
-            const int rc = s->d.precision == AL_FP64 ? sv_launch<double>(s, k) : sv_launch<float>(s, k);
-            if (rc != AL_OK) return rc;
-            s->next_stream = k ^ 1;
-        }
+        if (w.sims.empty()) break;
+        s->rr = (w.sims.back() + 1) % ns;
+        const int rc = s->d.precision == AL_FP64 ? sv_launch<double>(s, k) : sv_launch<float>(s, k);
+        if (rc != AL_OK) return rc;
+        ++s->n_waves;
+        s->n_wave_steps += (long long)w.sims.size();
+        s->next_stream = k ^ 1;
     }
     if (wait && s->done.empty()) {
         // nothing completed yet: wait for the oldest wave in flight
@@ -349,6 +351,13 @@ extern "C" int al_server_footprint(al_server s, unsigned long long *bytes, int *
         for (const Sim &m : s->sims) r += m.used ? 1 : 0;
         *resident = r;
     }
+    return AL_OK;
+}
+
+extern "C" int al_server_stats(al_server s, long long *waves, long long *steps) {
+    if (!s || !waves || !steps) return AL_ERR_ARG;
+    *waves = s->n_waves;
+    *steps = s->n_wave_steps;
     return AL_OK;
 }
 

@@ -1,30 +1,37 @@
-"""Continuous-batching server of coupling steps.
+"""Continuous-batching server of coupling steps: the scheduling side.
 
 Many simulations send coupling-step requests (new actuator-point positions
-for their next step) as they arrive.  The server keeps each admitted
-simulation's grid, fields, bins and relaxation state resident on the device,
-admits simulations by their HBM footprint under a budget, and advances every
-simulation whose next request has arrived in one batched launch sequence
-(al_batch_run_subset) -- a *wave*.  Waves alternate between CUDA streams, so a
-wave forms and launches while earlier ones are still running; a simulation
-with a step in flight waits for it (steps of one simulation are ordered).
-Evicted simulations free their slot and memory for waiting ones.
+for their next step) as they arrive.  The library's server (al_server_*)
+keeps each admitted simulation resident on the device, advances every
+resident simulation whose next request has arrived in one batched launch
+sequence (a wave, over al_batch_run_subset), alternates waves between two
+streams so that one forms while the previous one runs, and moves each
+wave's positions and forces in one host-to-device and one device-to-host
+copy.  What stays here is scheduling: arrivals, admission in arrival order
+by device bytes (the library's al_footprint of the instance plus the
+simulation's own buffers, one allocation each), release of finished
+simulations, and latency / throughput statistics.
 
 `PlainServer` is the reference path: one al_sample_drag_spread per request
-in arrival order on one stream, with the same copies and admission.
+in arrival order on one stream, with the same admission rule.
 
-The schedulers only decide what runs when; every device operation goes
-through a backend (`CudaBackend`: PyTorch memory and streams plus the CUDA
-library), so the scheduling can be checked on the host with a stand-in.
+Every device operation goes through a backend (`CudaBackend`), so the
+scheduling can be checked on the host with a stand-in.
 """
 from __future__ import annotations
 
 import time
 from collections import deque
 from dataclasses import dataclass, field
-from typing import Dict, List, Optional, Tuple
+from typing import Dict, List, Tuple
 
 import numpy as np
+
+PAGE = 2 << 20          # the driver commits device memory in 2 MiB pages
+
+
+def _pages(nbytes: int) -> int:
+    return -(-int(nbytes) // PAGE) * PAGE
 
 
 @dataclass
@@ -35,17 +42,24 @@ class Sim:
     n_steps: int
     dt: float = 1e-3
 
-    def footprint(self) -> int:
+    @property
+    def n_points(self) -> int:
+        return int(self.wl.beams.n_points)
+
+    def dtype(self):
+        return np.float64 if self.wl.grid.precision == "fp64" else np.float32
+
+    def buffer_bytes(self) -> int:
+        """Device bytes of the simulation's own buffers (fields, points,
+        outputs) in their one allocation."""
         g, b = self.wl.grid, self.wl.beams
         es = 8 if g.precision == "fp64" else 4
-        fields = (3 + 3 + (1 if g.has_alpha else 0)) * es * g.n_cells          # U, S, alpha
-        points = b.n_points * (es * 3 * 5 + 120)                                 # P, Pdot, F, staging + scratch
-        bricks = ((g.nx + 15) // 16) * ((g.ny + 15) // 16) * ((g.nz + 3) // 4)   # lowest brick height
-        mask = bricks * ((b.n_lines + 31) // 32) * 4 + bricks * 24
-        return int(fields + points + mask + 4096)
+        n = (6 + (1 if g.has_alpha else 0)) * g.n_cells + 9 * max(b.n_points, 1)     # U, S, alpha; P, Pdot, F
+        return _pages(es * n + 6 * 8 + 16 * 4 + 4096)
 
     def positions(self, k: int) -> np.ndarray:
-        return self.wl.step.P.astype(np.float64) + (k * self.dt) * self.wl.step.Pdot.astype(np.float64)
+        P = self.wl.step.P.astype(np.float64) + (k * self.dt) * self.wl.step.Pdot.astype(np.float64)
+        return np.ascontiguousarray(P, dtype=self.dtype())
 
 
 @dataclass
@@ -87,48 +101,125 @@ def poisson_arrivals(sims: List[Sim], rate: float, seed: int):
     return out
 
 
+def instance_footprint(sim: Sim) -> int:
+    """al_footprint of the simulation's instance (one is created and destroyed)."""
+    from .al import Grid
+    g = Grid(sim.wl.grid)
+    try:
+        g.load_beams(sim.wl.beams)
+        return g.footprint()
+    finally:
+        g.close()
+
+
+class _Buffers:
+    """One simulation's device buffers in one cudaMalloc of whole pages (so
+    the bytes declared at admission are the bytes the device gives up): U,
+    S, alpha (fields), P, Pdot, F (points), totals and status."""
+
+    def __init__(self, sim: Sim, device):
+        from cuda.bindings import runtime as cudart
+        from .al import AL_STATUS_N, StepIn, StepOut
+        self._rt = cudart
+        wl = sim.wl
+        es = 8 if wl.grid.precision == "fp64" else 4
+        dt = np.float64 if es == 8 else np.float32
+        nc, npts = int(wl.grid.n_cells), max(int(wl.beams.n_points), 1)
+        self.nbytes = sim.buffer_bytes()
+        self.nc, self.es, self.dt = nc, es, dt
+        err, base = cudart.cudaMalloc(self.nbytes)
+        if err != cudart.cudaError_t.cudaSuccess:
+            raise MemoryError(f"cudaMalloc({self.nbytes}): {err}")
+        self.base = int(base)
+        off = [0]
+
+        def take(nbytes):
+            o = (off[0] + 255) // 256 * 256
+            off[0] = o + nbytes
+            return self.base + o
+
+        U = [take(nc * es) for _ in range(3)]
+        self.S = [take(nc * es) for _ in range(3)]
+        alpha = take(nc * es) if wl.grid.has_alpha else None
+        P = [take(npts * es) for _ in range(3)]
+        Pdot = [take(npts * es) for _ in range(3)]
+        F = [take(npts * es) for _ in range(3)]
+        totals, status = take(6 * 8), take(AL_STATUS_N * 4)
+        assert off[0] <= self.nbytes
+        st = wl.step
+        for a in range(3):
+            self._put(U[a], st.U[a], dt)
+            if wl.beams.n_points:
+                self._put(P[a], st.P[a], dt)
+                self._put(Pdot[a], st.Pdot[a], dt)
+        if alpha is not None:
+            self._put(alpha, st.alpha, dt)
+        cudart.cudaMemset(totals, 0, 6 * 8)
+        cudart.cudaMemset(status, 0, AL_STATUS_N * 4)
+        self.sin, self.sout = StepIn(), StepOut()
+        for a in range(3):
+            self.sin.U[a], self.sin.P[a], self.sin.Pdot[a] = U[a], P[a], Pdot[a]
+            self.sout.S[a], self.sout.F[a] = self.S[a], F[a]
+        self.sin.alpha = alpha
+        import ctypes as C
+        self.sout.totals = C.cast(C.c_void_p(totals), C.POINTER(C.c_double))
+        self.sout.status = C.cast(C.c_void_p(status), C.POINTER(C.c_int))
+
+    def _put(self, dst, host, dt):
+        h = np.ascontiguousarray(host, dtype=dt)
+        err, = self._rt.cudaMemcpy(dst, h.ctypes.data, h.nbytes, self._rt.cudaMemcpyKind.cudaMemcpyHostToDevice)
+        if err != self._rt.cudaError_t.cudaSuccess:
+            raise RuntimeError(f"cudaMemcpy: {err}")
+
+    def S_host(self) -> np.ndarray:
+        out = np.empty((3, self.nc), dtype=self.dt)
+        for a in range(3):
+            self._rt.cudaMemcpy(out[a].ctypes.data, self.S[a], self.nc * self.es,
+                                self._rt.cudaMemcpyKind.cudaMemcpyDeviceToHost)
+        return out
+
+    def __del__(self):
+        if getattr(self, "base", 0):
+            self._rt.cudaFree(self.base)
+            self.base = 0
+
+
 class CudaBackend:
-    """Device side of the servers: resident instances with pinned staging
-    buffers, the slot batch, streams and events."""
+    """Device side of the servers: the library's server with each
+    simulation's buffers, and the resident instances of the plain path."""
 
     def __init__(self, device="cuda"):
         self.device = device
+
+    def server(self, budget, max_sims, max_wave, max_points, precision):
+        from .al import Server
+        return Server(budget, max_sims, max_wave, max_points, precision)
+
+    def buffers(self, sim: Sim):
+        return _Buffers(sim, self.device)
+
+    def final_S(self, buffers) -> np.ndarray:
+        return buffers.S_host()
+
+    def resident(self, sim: Sim):
+        return _Resident(sim, self.device)
 
     def stream(self):
         import torch
         return torch.cuda.Stream(device=self.device)
 
-    def resident(self, sim: Sim):
-        return _Resident(sim, self.device)
-
-    def batch(self, n_slots: int, precision: str):
-        from .al import Batch
-        return Batch([], use_graph=False, reserve=(n_slots, precision))
-
     def stream_ctx(self, stream):
         import torch
         return torch.cuda.stream(stream)
-
-    def mark(self, stream):
-        import torch
-        ev = torch.cuda.Event()
-        ev.record(stream)
-        return ev
-
-    @staticmethod
-    def done(ev) -> bool:
-        return ev.query()
 
     @staticmethod
     def sync(stream) -> None:
         stream.synchronize()
 
-    def sync_all(self) -> None:
-        import torch
-        torch.cuda.synchronize()
-
 
 class _Resident:
+    """The plain path's simulation: an instance stepped alone."""
+
     def __init__(self, sim: Sim, device):
         import torch
         from .al import Instance
@@ -138,8 +229,13 @@ class _Resident:
         self.hP = torch.empty(self.inst.P.shape, dtype=dt).pin_memory()
         self.hF = torch.empty(self.inst.F.shape, dtype=dt).pin_memory()
 
+    def footprint(self) -> int:
+        i = self.inst
+        own = sum(t.numel() * t.element_size() for t in (i.U, i.P, i.Pdot, i.S, i.F, i.totals, i.status)
+                  + ((i.alpha,) if i.alpha is not None else ()))
+        return self.inst.grid.footprint() + _pages(own)
+
     def upload(self, k: int) -> None:
-        # positions of step k into pinned host memory (the client's payload), then to the device
         np.copyto(self.hP.numpy(), self.sim.positions(k), casting="same_kind")
         self.inst.P.copy_(self.hP, non_blocking=True)
 
@@ -150,7 +246,7 @@ class _Resident:
         self.inst.step(stream=stream)
 
     def result_F(self) -> np.ndarray:
-        return self.hF.numpy()[:, :self.sim.wl.beams.n_points].copy()
+        return self.hF.numpy()[:, :self.sim.n_points].copy()
 
     def result_S(self) -> np.ndarray:
         return self.inst.S.cpu().numpy().copy()
@@ -159,156 +255,150 @@ class _Resident:
         self.inst.close()
 
 
-class _Base:
-    def __init__(self, sims: List[Sim], hbm_budget: int, backend=None, record: bool = False):
+class BatchServer:
+    """Continuous batching through the library's server: this side admits
+    simulations in arrival order, submits each arrived request, polls for
+    completions and releases finished simulations."""
+
+    def __init__(self, sims: List[Sim], hbm_budget: int, *, n_slots: int = 64, max_wave: int = 64, backend=None,
+                 record: bool = False, preadmit: bool = False):
         self.sims = sims
+        self.preadmit = preadmit          # admit (in order of first arrival) before the clock starts
         self.budget = int(hbm_budget)
+        self.n_slots = int(n_slots)
+        self.max_wave = min(int(max_wave), self.n_slots)
         self.be = backend if backend is not None else CudaBackend()
-        self.stats = Stats()
-        self.mem = 0
-        self.res: Dict[int, object] = {}
-        self.done_steps = [0] * len(sims)
-        self.busy = [False] * len(sims)
         self.record = record
+        self.stats = Stats()
         self.results: Dict[Tuple[int, int], np.ndarray] = {}     # (sim, step) -> F
         self.final_S: Dict[int, np.ndarray] = {}
 
-    def _fits(self, s: int) -> bool:
-        return self.mem + self.sims[s].footprint() <= self.budget or not self.res
-
-    def _admit(self, s: int) -> bool:
-        if not self._fits(s):
-            return False
-        self.res[s] = self.be.resident(self.sims[s])
-        self.mem += self.sims[s].footprint()
-        self.stats.admitted += 1
-        self.stats.peak_mem = max(self.stats.peak_mem, self.mem)
-        return True
-
-    def _evict(self, s: int):
-        r = self.res.pop(s)
-        r.close()
-        self.mem -= self.sims[s].footprint()
-
-    def _finish(self, s: int, k: int, t_arrival: float, now: float):
-        st = self.stats
-        st.latencies.append(now - t_arrival)
-        st.completed += 1
-        r = self.res[s]
-        if self.record:
-            self.results[(s, k)] = r.result_F()
-        self.busy[s] = False
-        self.done_steps[s] += 1
-        if self.done_steps[s] == self.sims[s].n_steps:
-            if self.record:
-                self.final_S[s] = r.result_S()
-            return True
-        return False
-
-
-class BatchServer(_Base):
-    """Continuous batching over al_batch_run_subset."""
-
-    def __init__(self, sims, hbm_budget, *, n_slots=64, n_streams=2, max_wave=64, backend=None, record=False):
-        super().__init__(sims, hbm_budget, backend, record)
-        prec = sims[0].wl.grid.precision
-        self.batch = self.be.batch(n_slots, prec)
-        self.free_slots = deque(range(n_slots))
-        self.slot_of: Dict[int, int] = {}
-        self.streams = [self.be.stream() for _ in range(n_streams)]
-        self.max_wave = max_wave
-        self.inflight = deque()           # (event, stream index, [(sim, step, t_arrival)])
-
-    def _admit(self, s):
-        if not self.free_slots or not super()._admit(s):
-            return False
-        slot = self.free_slots.popleft()
-        self.slot_of[s] = slot
-        # bind the slot and wait, so every stream sees the new descriptor
-        self.batch.assign(slot, self.res[s].inst, stream=self.streams[0])
-        self.be.sync(self.streams[0])
-        return True
-
-    def _evict(self, s):
-        slot = self.slot_of.pop(s)
-        self.batch.assign(slot, None, stream=self.streams[0])
-        self.be.sync(self.streams[0])
-        super()._evict(s)
-        self.free_slots.append(slot)
-
     def run(self, arrivals):
         st = self.stats
+        sims = self.sims
+        pts = sorted(max(s.n_points, 1) for s in sims)
+        wave_points = max(pts[-1], min(sum(pts[-self.max_wave:]), 1 << 22))     # staging of one wave
+        srv = self.be.server(self.budget, self.n_slots, self.max_wave, wave_points, sims[0].wl.grid.precision)
         n_req = len(arrivals)
-        pending = [deque() for _ in self.sims]
-        wait_adm, queued = deque(), set()
+        slot: Dict[int, int] = {}                 # simulation -> server slot
+        bufs: Dict[int, object] = {}
+        waiting: Dict[int, deque] = {}            # arrived before admission: (step, arrival)
+        adm_queue: deque = deque()
+        inflight: Dict[int, tuple] = {}           # tag -> (sim, step, arrival, P, F)
+        done_steps = [0] * len(sims)
+        releases, refused_at = 0, -1              # admission is retried after each release
         ai = 0
+        if self.preadmit:                         # a warm server: simulations resident before requests
+            for _, s, _ in arrivals:
+                if s in slot or s in waiting:
+                    continue
+                used, resident = srv.footprint()
+                if resident >= self.n_slots or (resident and used + sims[s].buffer_bytes() > self.budget):
+                    break
+                b = self.be.buffers(sims[s])
+                q = srv.admit(sims[s].wl.grid, sims[s].wl.beams, b.sin, b.sout, b.nbytes)
+                if q is None:
+                    break
+                slot[s], bufs[s] = q, b
+                st.admitted += 1
+            st.peak_mem = srv.footprint()[0]
         t0 = time.perf_counter()
-        busy_streams = set()
+
+        def submit(s, k, ta):
+            tag = s * 1_000_000 + k
+            P = sims[s].positions(k)
+            F = np.empty_like(P)
+            inflight[tag] = (s, k, ta, P, F)
+            srv.submit(slot[s], P, F, tag)
+
         while st.completed < n_req:
             now = time.perf_counter() - t0
             while ai < n_req and arrivals[ai][0] <= now:
                 t, s, k = arrivals[ai]
-                pending[s].append((k, t))
-                if s not in self.res and s not in queued:
-                    wait_adm.append(s)
-                    queued.add(s)
                 ai += 1
-            # retire finished waves
-            while self.inflight and self.be.done(self.inflight[0][0]):
-                ev, si, items = self.inflight.popleft()
-                busy_streams.discard(si)
-                done = time.perf_counter() - t0
-                for s, k, ta in items:
-                    if self._finish(s, k, ta, done):
-                        self._evict(s)
-            # admissions in arrival order
-            while wait_adm:
-                s = wait_adm[0]
-                if not self._admit(s):
+                if s in slot:
+                    submit(s, k, t)
+                else:
+                    if s not in waiting:
+                        waiting[s] = deque()
+                        adm_queue.append(s)
+                    waiting[s].append((k, t))
+            # admissions in arrival order; after a refusal the head waits for a release
+            while adm_queue and refused_at != releases:
+                s = adm_queue[0]
+                used, resident = srv.footprint()
+                if resident >= self.n_slots or (resident and used + sims[s].buffer_bytes() > self.budget):
+                    refused_at = releases
                     break
-                wait_adm.popleft()
-                queued.discard(s)
-            # form and launch a wave: every resident simulation whose next step has arrived
-            free = [i for i in range(len(self.streams)) if i not in busy_streams]
-            if free:
-                wave = []
-                for s in self.res:
-                    if not self.busy[s] and pending[s] and pending[s][0][0] == self.done_steps[s]:
-                        wave.append(s)
-                        if len(wave) >= self.max_wave:
-                            break
-                if wave:
-                    si = free[0]
-                    stream = self.streams[si]
-                    items = []
-                    with self.be.stream_ctx(stream):
-                        for s in wave:
-                            k, ta = pending[s].popleft()
-                            self.res[s].upload(k)
-                            self.busy[s] = True
-                            items.append((s, k, ta))
-                        self.batch.run_subset([self.slot_of[s] for s in wave], stream=stream)
-                        for s in wave:
-                            self.res[s].download()
-                        ev = self.be.mark(stream)
-                    self.inflight.append((ev, si, items))
-                    busy_streams.add(si)
-                    st.waves += 1
-                    st.wave_sizes.append(len(wave))
-                    continue
-            if ai < n_req and not self.inflight:
-                time.sleep(max(0.0, min(1e-4, arrivals[ai][0] - now)))
-        self.be.sync_all()
+                b = self.be.buffers(sims[s])
+                q = srv.admit(sims[s].wl.grid, sims[s].wl.beams, b.sin, b.sout, b.nbytes)
+                if q is None:
+                    del b
+                    refused_at = releases
+                    break
+                adm_queue.popleft()
+                slot[s], bufs[s] = q, b
+                st.admitted += 1
+                st.peak_mem = max(st.peak_mem, srv.footprint()[0])
+                for k, t in waiting.pop(s):
+                    submit(s, k, t)
+            # completions (waiting for the oldest wave when nothing else can happen)
+            idle = (not adm_queue or refused_at == releases) and \
+                (ai >= n_req or arrivals[ai][0] > time.perf_counter() - t0 + 2e-4)
+            tags = srv.poll(wait=bool(inflight) and idle)
+            now = time.perf_counter() - t0
+            for tag in tags:
+                s, k, ta, P, F = inflight.pop(tag)
+                st.latencies.append(now - ta)
+                st.completed += 1
+                done_steps[s] += 1
+                if self.record:
+                    self.results[(s, k)] = F[:, :sims[s].n_points]
+                if done_steps[s] == sims[s].n_steps:
+                    if self.record:
+                        self.final_S[s] = self.be.final_S(bufs[s])
+                    srv.release(slot.pop(s))
+                    del bufs[s]
+                    releases += 1
+            if not tags and not inflight and ai < n_req and not adm_queue:
+                time.sleep(max(0.0, min(1e-4, arrivals[ai][0] - (time.perf_counter() - t0))))
         st.wall = time.perf_counter() - t0
-        for s in list(self.res):
-            self._evict(s)
-        self.batch.close()
+        st.waves, steps = srv.waves()
+        st.wave_sizes = [steps / max(st.waves, 1)]
+        srv.close()
         return st
 
 
-class PlainServer(_Base):
+class PlainServer:
     """Reference path: one al_sample_drag_spread per request on one stream,
     the oldest processable request first, with the same admission rule."""
+
+    def __init__(self, sims: List[Sim], hbm_budget: int, backend=None, record: bool = False,
+                 preadmit: bool = False):
+        self.sims = sims
+        self.preadmit = preadmit
+        self.budget = int(hbm_budget)
+        self.be = backend if backend is not None else CudaBackend()
+        self.record = record
+        self.stats = Stats()
+        self.mem = 0
+        self.res: Dict[int, object] = {}
+        self.fp: Dict[int, int] = {}
+        self.done_steps = [0] * len(sims)
+        self.results: Dict[Tuple[int, int], np.ndarray] = {}
+        self.final_S: Dict[int, np.ndarray] = {}
+
+    def _admit(self, s: int) -> bool:
+        r = self.be.resident(self.sims[s])
+        fp = r.footprint()
+        if self.res and self.mem + fp > self.budget:
+            r.close()
+            return False
+        self.res[s], self.fp[s] = r, fp
+        self.mem += fp
+        self.stats.admitted += 1
+        self.stats.peak_mem = max(self.stats.peak_mem, self.mem)
+        return True
 
     def run(self, arrivals):
         st = self.stats
@@ -316,6 +406,10 @@ class PlainServer(_Base):
         ai = 0
         queue = []                        # arrived, not yet processed (arrival order)
         stream = self.be.stream()
+        if self.preadmit:
+            for _, s, _ in arrivals:
+                if s not in self.res and not self._admit(s):
+                    break
         t0 = time.perf_counter()
         while st.completed < n_req:
             now = time.perf_counter() - t0
@@ -344,9 +438,17 @@ class PlainServer(_Base):
             self.be.sync(stream)
             st.waves += 1
             st.wave_sizes.append(1)
-            if self._finish(s, k, t, time.perf_counter() - t0):
-                self._evict(s)
+            st.latencies.append(time.perf_counter() - t0 - t)
+            st.completed += 1
+            if self.record:
+                self.results[(s, k)] = r.result_F()
+            self.done_steps[s] += 1
+            if self.done_steps[s] == self.sims[s].n_steps:
+                if self.record:
+                    self.final_S[s] = r.result_S()
+                self.res.pop(s).close()
+                self.mem -= self.fp.pop(s)
         st.wall = time.perf_counter() - t0
         for s in list(self.res):
-            self._evict(s)
+            self.res.pop(s).close()
         return st

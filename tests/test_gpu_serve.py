@@ -1,12 +1,13 @@
-"""Continuous batching on the device: simulations served in a mix of waves
-(with admission by HBM footprint forcing some to wait for others to leave)
-produce, step for step, the same line forces and final momentum source as
-each simulation run alone, bit for bit."""
+"""Continuous batching in the library (al_server_*): simulations served in
+a mix of waves (with admission by device bytes forcing some to wait for
+others to leave) produce, step for step, the same line forces and final
+momentum source as each simulation run alone, bit for bit; and what the
+server admits is what the device gives up (cudaMemGetInfo)."""
 import numpy as np
 import pytest
 
 from paper_2609_39443_b300 import workloads as W
-from paper_2609_39443_b300.serve import BatchServer, Sim, poisson_arrivals
+from paper_2609_39443_b300.serve import BatchServer, Sim, instance_footprint, poisson_arrivals
 
 from helpers import BRICK_PASSES
 
@@ -21,7 +22,8 @@ def test_served_mix_equals_each_simulation_alone(reflect):
     if reflect:                     # every other simulation reflects its kernel at the bed
         wls = [W.with_reflect(w, W.REFLECT_Z_LO) if i % 2 == 0 else w for i, w in enumerate(wls)]
     sims = [Sim(w, 3) for w in wls]
-    budget = int(2.5 * max(s.footprint() for s in sims))     # two or three resident at a time
+    need = [s.buffer_bytes() + instance_footprint(s) for s in sims]
+    budget = int(2.5 * max(need))                             # two or three resident at a time
     arr = poisson_arrivals(sims, 5000.0, seed=11)
     srv = BatchServer(sims, budget, n_slots=4, record=True)
     st = srv.run(arr)
@@ -37,3 +39,51 @@ def test_served_mix_equals_each_simulation_alone(reflect):
             np.testing.assert_array_equal(F, srv.results[(s, k)])
         np.testing.assert_array_equal(inst.S.cpu().numpy(), srv.final_S[s])
         inst.close()
+
+
+def test_admitted_memory_stays_within_the_budget():
+    """Admit simulations through the C ABI until the server refuses: the
+    device memory they took (library instances and the caller's buffers, by
+    cudaMemGetInfo) is what the server counts, up to page rounding, and
+    stays within the budget."""
+    import torch
+    from paper_2609_39443_b300.al import Server
+    from paper_2609_39443_b300.serve import CudaBackend
+    wls = W.make_batched(41, 8, max_cells=96 * 64 * 64)
+    sims = [Sim(w, 1) for w in wls]
+    need = [s.buffer_bytes() + instance_footprint(s) for s in sims]
+    budget = int(sum(sorted(need)[:5]) + 1)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free0 = torch.cuda.mem_get_info()[0]
+    srv = Server(budget, 8, 8, max(s.n_points for s in sims), "fp32")
+    be = CudaBackend()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]             # the server's own staging
+    keep, admitted = [], 0
+    for s in sims:
+        b = be.buffers(s)
+        q = srv.admit(s.wl.grid, s.wl.beams, b.sin, b.sout, b.nbytes)
+        if q is None:
+            del b
+            continue
+        keep.append(b)
+        admitted += 1
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free2 = torch.cuda.mem_get_info()[0]
+    used, resident = srv.footprint()
+    assert resident == admitted >= 2
+    assert used <= budget
+    taken = free1 - free2
+    assert taken <= budget, (taken, budget)
+    # the server never counts less than the device gives up; it counts at
+    # most a page of rounding more per allocation (three per simulation: the
+    # library's two slabs and the caller's buffers; small slabs share pages)
+    assert taken <= used + 2 * 2 ** 20, (taken, used)
+    assert used - taken <= 3 * 2 * 2 ** 20 * resident, (taken, used)
+    srv.close()
+    del keep
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) <= 8 * 2 ** 20     # everything returned

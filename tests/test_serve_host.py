@@ -1,39 +1,115 @@
-"""Host logic of the continuous-batching server, with a stand-in backend
-(no GPU): every request completes once, each simulation's steps run in
-order and never two at a time, no wave holds a simulation twice, resident
-memory never exceeds the HBM budget, and slots are reused after eviction."""
+"""Host logic of the continuous-batching server, with a stand-in for the
+library's server (no GPU): every request completes once, each simulation's
+steps run in order and never two at a time, no wave holds a simulation
+twice, resident device bytes never exceed the budget, admission follows
+arrival order, and slots are reused after release."""
 import numpy as np
 import pytest
 
 from paper_2609_39443_b300 import workloads as W
 from paper_2609_39443_b300.serve import BatchServer, PlainServer, Sim, poisson_arrivals
 
+LIB = 3 << 20                       # the stand-in's library bytes per simulation
 
-class _Event:
-    def __init__(self, polls):
-        self.polls = polls
 
-    def done(self):
-        self.polls -= 1
-        return self.polls < 0
+class _Bufs:
+    def __init__(self, sim):
+        self.nbytes = sim.buffer_bytes()
+        self.sin = self.sout = self
+        self.steps = 0
+
+
+class FakeServer:
+    """The semantics of al_server_*: slots, a budget on declared bytes, one
+    step per simulation in flight, waves on two streams that complete after
+    a few polls (or at once when waited for)."""
+
+    def __init__(self, budget, max_sims, max_wave, max_points, precision, polls=2):
+        self.budget, self.max_sims, self.max_wave, self.polls = budget, max_sims, max_wave, polls
+        self.slots = [None] * max_sims
+        self.used = 0
+        self.inflight = []                    # waves: [countdown, [(slot, tag, F)]]
+        self.done = []
+        self.n_waves = self.n_steps = 0
+        self.peak = 0
+        self.wave_log = []
+
+    def admit(self, grid, beams, sin, sout, nbytes):
+        free = [i for i, x in enumerate(self.slots) if x is None]
+        if not free or self.used + nbytes + LIB > self.budget:
+            return None
+        q = free[0]
+        self.slots[q] = {"buf": sin, "bytes": nbytes + LIB, "queue": [], "busy": False}
+        self.used += nbytes + LIB
+        self.peak = max(self.peak, self.used)
+        return q
+
+    def submit(self, q, P, F, tag):
+        assert self.slots[q] is not None, "submit to a free slot"
+        self.slots[q]["queue"].append((tag, F))
+
+    def _retire(self, w):
+        for q, tag, F in w[1]:
+            m = self.slots[q]
+            F[...] = m["buf"].steps                  # the step this request ran as
+            m["buf"].steps += 1
+            m["busy"] = False
+            self.done.append(tag)
+
+    def poll(self, wait=False):
+        for w in list(self.inflight):
+            w[0] -= 1
+            if w[0] < 0:
+                self.inflight.remove(w)
+                self._retire(w)
+        while len(self.inflight) < 2:
+            items = []
+            for q, m in enumerate(self.slots):
+                if m is not None and not m["busy"] and m["queue"] and len(items) < self.max_wave:
+                    tag, F = m["queue"].pop(0)
+                    m["busy"] = True
+                    items.append((q, tag, F))
+            if not items:
+                break
+            assert len({q for q, _, _ in items}) == len(items), "a simulation twice in one wave"
+            self.inflight.append([self.polls, items])
+            self.wave_log.append([q for q, _, _ in items])
+            self.n_waves += 1
+            self.n_steps += len(items)
+        if wait and not self.done and self.inflight:
+            self._retire(self.inflight.pop(0))
+        out, self.done = self.done, []
+        return out
+
+    def release(self, q):
+        m = self.slots[q]
+        assert not m["queue"] and not m["busy"], "release with work left"
+        self.used -= m["bytes"]
+        self.slots[q] = None
+
+    def footprint(self):
+        return self.used, sum(m is not None for m in self.slots)
+
+    def waves(self):
+        return self.n_waves, self.n_steps
+
+    def close(self):
+        assert all(m is None for m in self.slots), "simulations left resident"
 
 
 class _Res:
-    def __init__(self, sim, log):
-        self.sim, self.log = sim, log
-        self.inst = self                 # what the batch binds to a slot
-        self.next_k, self.staged, self.in_flight, self.closed = 0, None, False, False
+    def __init__(self, sim):
+        self.sim = sim
+        self.next_k, self.staged, self.in_flight = 0, None, False
+
+    def footprint(self):
+        return self.sim.buffer_bytes() + LIB
 
     def upload(self, k):
-        assert not self.in_flight, "a step of this simulation is already in flight"
-        assert k == self.next_k, (k, self.next_k)
+        assert not self.in_flight and k == self.next_k, (k, self.next_k)
         self.staged, self.in_flight = k, True
 
     def step(self, stream):
-        self.advance()
-
-    def advance(self):
-        assert self.in_flight
         self.next_k += 1
         self.in_flight = False
 
@@ -45,25 +121,6 @@ class _Res:
 
     def result_S(self):
         return np.array([self.next_k])
-
-    def close(self):
-        self.closed = True
-
-
-class _Batch:
-    def __init__(self, n_slots):
-        self.slots = [None] * n_slots
-        self.waves = []
-
-    def assign(self, slot, inst, stream=None):
-        self.slots[slot] = inst
-
-    def run_subset(self, idx, stream=None):
-        assert len(set(idx)) == len(idx), "a slot twice in one wave"
-        for i in idx:
-            assert self.slots[i] is not None, "run of an unbound slot"
-            self.slots[i].advance()
-        self.waves.append(list(idx))
 
     def close(self):
         pass
@@ -78,37 +135,31 @@ class _Ctx:
 
 
 class FakeBackend:
-    def __init__(self, polls=2):
-        self.polls = polls
-        self.batches = []
-        self.log = []
+    def __init__(self):
+        self.servers = []
+
+    def server(self, budget, max_sims, max_wave, max_points, precision):
+        s = FakeServer(budget, max_sims, max_wave, max_points, precision)
+        self.servers.append(s)
+        return s
+
+    def buffers(self, sim):
+        return _Bufs(sim)
+
+    def final_S(self, b):
+        return np.array([b.steps])
+
+    def resident(self, sim):
+        return _Res(sim)
 
     def stream(self):
         return object()
 
-    def resident(self, sim):
-        return _Res(sim, self.log)
-
-    def batch(self, n_slots, precision):
-        b = _Batch(n_slots)
-        self.batches.append(b)
-        return b
-
     def stream_ctx(self, stream):
         return _Ctx()
 
-    def mark(self, stream):
-        return _Event(self.polls)
-
-    @staticmethod
-    def done(ev):
-        return ev.done()
-
     @staticmethod
     def sync(stream):
-        pass
-
-    def sync_all(self):
         pass
 
 
@@ -121,7 +172,7 @@ def _sims(n=12, steps=5):
 @pytest.mark.parametrize("server", ["batched", "plain"])
 def test_scheduler_invariants(server, rate):
     sims = _sims()
-    budget = 3 * max(s.footprint() for s in sims)          # about three resident at a time
+    budget = 3 * max(s.buffer_bytes() + LIB for s in sims)          # about three resident at a time
     arr = poisson_arrivals(sims, rate, seed=7)
     be = FakeBackend()
     if server == "batched":
@@ -132,16 +183,47 @@ def test_scheduler_invariants(server, rate):
     assert st.completed == len(arr) == sum(s.n_steps for s in sims)
     assert sorted(srv.results) == sorted((s, k) for s in range(len(sims)) for k in range(sims[s].n_steps))
     for (s, k), v in srv.results.items():
-        assert int(v[0]) == k                                # the staged step is the one reported
+        assert int(np.ravel(v)[0]) == k                     # each request ran as its own step, in order
     assert all(int(srv.final_S[s][0]) == sims[s].n_steps for s in range(len(sims)))
     assert st.peak_mem <= budget
     assert st.admitted == len(sims)
-    assert not srv.res                                       # everything evicted at the end
     assert len(st.latencies) == len(arr) and min(st.latencies) >= 0.0
     if server == "batched":
-        waves = be.batches[0].waves
-        assert sum(len(w) for w in waves) == len(arr)
-        assert st.waves == len(waves)
+        fs = be.servers[0]
+        assert fs.peak <= budget
+        assert sum(len(w) for w in fs.wave_log) == len(arr)
+        assert st.waves == len(fs.wave_log)
+    else:
+        assert not srv.res                                   # everything released at the end
+
+
+def test_admission_follows_arrival_order():
+    """With room for one simulation at a time, simulations are admitted in
+    the order of their first arrivals."""
+    sims = _sims(6, 3)
+    budget = max(s.buffer_bytes() + LIB for s in sims)
+    arr = poisson_arrivals(sims, 2000.0, seed=5)
+    first = []
+    for _, s, _ in arr:
+        if s not in first:
+            first.append(s)
+    be = FakeBackend()
+    srv = BatchServer(sims, budget, n_slots=2, backend=be, record=True)
+    order = []
+    orig = FakeServer.admit
+
+    def spy(self, grid, beams, sin, sout, nbytes):
+        q = orig(self, grid, beams, sin, sout, nbytes)
+        if q is not None:
+            order.append(next(i for i, x in enumerate(sims) if x.wl.grid is grid))
+        return q
+
+    FakeServer.admit = spy
+    try:
+        srv.run(arr)
+    finally:
+        FakeServer.admit = orig
+    assert order == first
 
 
 def test_poisson_arrivals_keep_per_simulation_order():
