@@ -68,6 +68,9 @@ def _args():
     ap.add_argument("--reflect", type=int, default=0,
                     help="faces that reflect the kernel (bit mask: 1 x-, 2 x+, 4 y-, 8 y+, 16 z-, 32 z+)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--split", default="none", choices=["none", "slab"],
+                    help="slab: one instance split along x over the ranks (strong scaling); "
+                         "none: one instance per rank (weak scaling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default options)")
@@ -464,6 +467,72 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_slab(a):
+    """One flume (or canopy) split along x over the N ranks (strong scaling):
+    each rank steps its slab, the ranks all-reduce the fixed-point partial
+    weights (NCCL, int64 sum) between the two phases of the step."""
+    import torch
+    from paper_2609_39443_b300 import slab
+    from paper_2609_39443_b300.ranks import max_over_ranks, rank_env
+    world, rank, local = rank_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = _workload(a.workload, 0, a.eps, a.reduced)       # the same instance on every rank
+    sr = slab.SlabRank(wl, world, rank, device=f"cuda:{local}")
+    glob = torch.zeros(max(wl.beams.n_points, 1), dtype=torch.int64, device=f"cuda:{local}")
+
+    def step():
+        sr.begin()
+        glob.zero_()
+        sr.partial(glob)
+        if dist:
+            dist.all_reduce(glob)
+        sr.end(glob)
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    launches0 = sr.inst.grid.launches()
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = sr.inst.grid.launches() - launches0
+    total_s = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
+    total_s = max_over_ranks([total_s], dist, f"cuda:{local}")[0]
+    if rank == 0:
+        p = sr.plan
+        line = {"metric": "coupling steps/s", "value": a.steps / total_s, "unit": "steps/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total_s / a.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": wl.name, "cells": wl.grid.n_cells, "points": wl.beams.n_points,
+                           "parallelism": f"x-slabs over {world} ranks, int64 all-reduce of partial weights",
+                           "rank0_slab": {"owned": [p.x0, p.x1], "local": [p.lx0, p.lx1], "halo": p.halo,
+                                          "lines": int(len(p.lines))},
+                           "l2": "flushed between timed steps (256 MiB write)"},
+                "clocks": clk, "gpu_launches": launches * world}
+        print(json.dumps(line), flush=True)
+    sr.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def run_batched(a):
     """64 independent instances of uneven size: one batched launch sequence
     (CUDA graph) per step vs one launch sequence per instance."""
@@ -633,5 +702,7 @@ if __name__ == "__main__":
         run_batched(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.split == "slab":
+        run_slab(args)
     else:
         run_ours(args)

@@ -288,6 +288,18 @@ int al_trace_last(al_grid g, float *ms /* [AL_TRACE_N] */);
  * (the weights option then applies to their other lines).  The results
  * agree within the parity tolerances either way. */
 #define AL_OPT_COLUMN       6
+/* AL_OPT_OWN_X0 / AL_OPT_OWN_X1 (defaults 0 and -1 = nx): the instance owns
+ * the cells with x index in [x0, x1) of its grid, one slab of a
+ * decomposition of a larger grid along x (al_slab_plan); x0 a multiple of 16
+ * (a brick column), x1 too or nx.  The weights pass adds only the owned
+ * cells' contributions (partial sums, exchanged between slabs with
+ * al_weights_get / al_weights_set between al_step_begin and al_step_end),
+ * and the spread writes only the owned cells of S (the others are left as
+ * they are).  A slab takes the brick weights, the gather and no records
+ * whatever the other options say; it refuses a reflecting face, the
+ * integrated projection (AL_ERR_STATE at the step) and batches. */
+#define AL_OPT_OWN_X0       7
+#define AL_OPT_OWN_X1       8
 int al_set_option(al_grid g, int option, int value);
 
 /* Kernels this instance's al_sample_drag_spread calls have launched so far
@@ -386,6 +398,46 @@ int al_batch_set_option(al_batch b, int option, int value);
  * restored.  *choice (optional) = 10 * brick height + CTAs per SM (0 = as
  * many as fit).  Every slot must be bound. */
 int al_batch_autotune(al_batch b, int trials, void *stream, int *choice);
+
+/* ---- the step in two phases (decomposition along x, Sec. 3.2.5) ------- */
+/* al_step_begin runs a step up to the nodal weights (Algorithm 1 steps 1-3:
+ * points, line geometry, bins and the weights pass); al_step_end runs the
+ * rest (normalisation, spread and totals).  Together they equal
+ * al_sample_drag_spread (same in / out).  Between them the nodal weights of
+ * the brick pass, w_k / (eta0 V) as unsigned fixed-point integers in units
+ * of 2^-wshift of their line (one unsigned long long per point, a line's
+ * shift being a function of its geometry only), can be read and replaced:
+ * the slabs of a decomposition sum their partial weights there (an exact,
+ * order-free integer all-reduce) before each ends its step.  al_weights_get
+ * / _set copy them to / from a DEVICE array of N_p (stream-ordered);
+ * AL_ERR_STATE unless the instance takes the brick weights (a slab always
+ * does). */
+int al_step_begin(al_grid g, const al_step_in *in, const al_step_out *out, void *stream);
+int al_step_end(al_grid g, const al_step_in *in, const al_step_out *out, void *stream);
+int al_weights_get(al_grid g, void *dst, void *stream);
+int al_weights_set(al_grid g, const void *src, void *stream);
+
+/* Slab plan of rank `rank` of `n_ranks` for a grid split along x (host only,
+ * no device work): the owned cells [x0, x1) are whole brick columns dealt
+ * evenly; the local grid [lx0, lx1) adds a halo of `halo` cells each side
+ * (clipped to the grid), with halo = ceil((ell_s + 3 eps + L) / h) + 2
+ * rounded up to a multiple of 16, the largest over the lines (ell_s the
+ * sampling distance, L the longest segment): every point whose segments come
+ * within 3 eps of an owned cell samples inside the local grid.  A line is
+ * taken (whole) when its points' x range widened by 3 eps + L + h meets the
+ * owned cells; `lines` (optional, n_lines entries) receives their indices in
+ * increasing order, and owner (optional, N_p entries) the rank whose owned
+ * cells contain each point's x (clamped to the grid).  P_host: HOST, 3 x N_p
+ * doubles, the positions the projection uses.  AL_ERR_ARG for a bad
+ * descriptor or rank. */
+typedef struct {
+    int x0, x1;          /* owned cells along x, global indices */
+    int lx0, lx1;        /* the local grid's cells along x, global indices */
+    int halo;            /* halo width in cells */
+    int n_lines;         /* lines the rank takes */
+} al_slab;
+int al_slab_plan(const al_grid_desc *grid, const al_beam_desc *beams, const double *P_host, int n_ranks, int rank,
+                 al_slab *out, int *lines, int *owner);
 
 /* ---- serving: continuous batching of coupling-step requests ------------ */
 /* Many simulations send coupling-step requests (the actuator-point positions

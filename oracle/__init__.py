@@ -65,6 +65,7 @@ def _load():
         lib.or_seg_kernel.argtypes = [dp, dp, dp, C.c_double, dp]
         lib.or_beam_quasistatic.argtypes = [C.POINTER(_Beams), dp, dp, dp, dp, dp]
         lib.or_closest_segment.restype = C.c_double
+        lib.or_project_slab.argtypes = [C.POINTER(_Grid), C.POINTER(_Beams), dp, dp, C.c_int, C.c_int, dp, dp, dp]
         _lib = lib
     return _lib
 
@@ -162,6 +163,23 @@ def project(grid, beams, P_spread, F, *, cull=True, line_mask=None, n_threads=0)
     lib.or_project(C.byref(g), C.byref(bh.s), _ptr(Ps), _ptr(Ff), int(bool(cull)),
                    _ptr(m, C.c_ubyte), _ptr(S), _ptr(w), _ptr(st, C.c_longlong), int(n_threads))
     return {"S": S, "w": w, "status": st}
+
+
+def project_slab(grid, beams, P_spread, F, x0, x1, w_in=None):
+    """The projection over the cells with x index in [x0, x1) only (a slab,
+    Sec. 3.2.5).  w_in None: returns {"w": the slab's partial nodal weights};
+    else (w_in the full weights): {"S": the slab's sources}."""
+    lib = _load()
+    Ps, Ff = _f64(P_spread), _f64(F)
+    g, bh = _grid(grid), _BeamsHold(beams)
+    if w_in is None:
+        w = np.zeros(beams.n_points)
+        lib.or_project_slab(C.byref(g), C.byref(bh.s), _ptr(Ps), _ptr(Ff), int(x0), int(x1), None, None, _ptr(w))
+        return {"w": w}
+    wi = _f64(w_in)
+    S = np.zeros((3, grid.n_cells))
+    lib.or_project_slab(C.byref(g), C.byref(bh.s), _ptr(Ps), _ptr(Ff), int(x0), int(x1), _ptr(wi), _ptr(S), None)
+    return {"S": S}
 
 
 def sample_drag_spread(workload, f_prev=None, *, line_mask=None, n_threads=0, cull=True):

@@ -611,6 +611,62 @@ int or_project(const or_grid *g, const or_beams *b, const double *Pspread, const
     return 0;
 }
 
+/* The projection restricted to one slab of a decomposition along x (the
+ * parallel update of Sec. 3.2.5): only cells with x index in [x0, x1) take
+ * part.  The kernel values and closest segments are those of or_project
+ * (the same records); only the sums are restricted.
+ *   w_in == NULL: w_out[k] += the part of w_k = sum_j omega_jk eta_j V_j
+ *                 over the slab's cells (the slab's partial sum);
+ *   w_in != NULL: w_in holds the full weights (every slab's partial sums
+ *                 added): f^_k = F_k / w_in[k], S -= the sources of the
+ *                 slab's cells (Eq. almMomentumSource), and a node with
+ *                 w_in[k] = 0 deposits F_k / V in its cell when that cell
+ *                 is in the slab. */
+int or_project_slab(const or_grid *g, const or_beams *b, const double *Pspread, const double *F, int x0, int x1,
+                    const double *w_in, double *S, double *w_out)
+{
+    const long long np = b->line_off[b->n_lines];
+    const long long ncell = (long long)g->nx * g->ny * g->nz;
+    const double V = g->h * g->h * g->h;
+    for (int l = 0; l < b->n_lines; ++l) {
+        const int off = b->line_off[l], n = b->line_off[l + 1] - off;
+        if (n <= 0) continue;
+        or_line_out o;
+        or_project_line(g, b, Pspread, np, F, l, 1, &o);
+        for (long long r = 0; r < o.nrec; ++r) {
+            const int ix = (int)(o.rec[r].cell % g->nx);
+            if (ix < x0 || ix >= x1) continue;
+            const int ka = o.rec[r].seg, kb = (n == 1) ? ka : ka + 1;
+            const double s = o.rec[r].s, eta = o.rec[r].eta;
+            if (!w_in) {
+                w_out[off + ka] += (1.0 - s) * eta * V;
+                w_out[off + kb] += s * eta * V;
+            } else {
+                for (int a = 0; a < 3; ++a) {
+                    const double fa = w_in[off + ka] > 0.0 ? F[a * np + off + ka] / w_in[off + ka] : 0.0;
+                    const double fb = w_in[off + kb] > 0.0 ? F[a * np + off + kb] / w_in[off + kb] : 0.0;
+                    S[a * ncell + o.rec[r].cell] -= eta * ((1.0 - s) * fa + s * fb);
+                }
+            }
+        }
+        if (w_in)
+            for (int k = 0; k < n; ++k) {
+                if (w_in[off + k] > 0.0) continue;
+                double u[3];
+                const double X[3] = {Pspread[off + k], Pspread[np + off + k], Pspread[2 * np + off + k]};
+                if (!or_locate(g, X, u)) continue;
+                const int nn[3] = {g->nx, g->ny, g->nz};
+                long long cc[3];
+                for (int a = 0; a < 3; ++a) { cc[a] = (long long)floor(u[a]); if (cc[a] > nn[a] - 1) cc[a] = nn[a] - 1; }
+                if (cc[0] < x0 || cc[0] >= x1) continue;
+                const long long cell = cc[0] + (long long)g->nx * cc[1] + (long long)g->nx * g->ny * cc[2];
+                for (int a = 0; a < 3; ++a) S[a * ncell + cell] -= F[a * np + off + k] / V;
+            }
+        or_free_line(&o);
+    }
+    return 0;
+}
+
 /* Number of cells within 3 eps of each line (the kernel-cell updates a
  * coupling step performs), for throughput reporting. */
 long long or_count_support(const or_grid *g, const or_beams *b, const double *Pspread, int n_threads)

@@ -24,6 +24,7 @@ AL_STATUS_N = 16
 ST_GUARD = 15
 
 OPT_WEIGHTS, OPT_BRICK_Z, OPT_SPREAD_CTAS, OPT_SPREAD, OPT_RECORD, OPT_COLUMN = 1, 2, 3, 4, 5, 6
+OPT_OWN_X0, OPT_OWN_X1 = 7, 8
 WEIGHTS_BRICK, WEIGHTS_SEGMENT = 0, 1
 SPREAD_GATHER, SPREAD_SCATTER = 0, 1
 
@@ -105,6 +106,11 @@ def lib():
         L.al_batch_set_option.argtypes = [_vp, C.c_int, C.c_int]
         L.al_batch_autotune.argtypes = [_vp, C.c_int, _vp, C.POINTER(C.c_int)]
         L.al_trace_last.argtypes = [_vp, C.POINTER(C.c_float)]
+        L.al_step_begin.argtypes = [_vp, C.POINTER(StepIn), C.POINTER(StepOut), _vp]
+        L.al_step_end.argtypes = [_vp, C.POINTER(StepIn), C.POINTER(StepOut), _vp]
+        L.al_weights_get.argtypes = [_vp, _vp, _vp]
+        L.al_weights_set.argtypes = [_vp, _vp, _vp]
+        L.al_slab_plan.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp]
         L.al_server_create.argtypes = [C.POINTER(ServerDesc), C.POINTER(_vp)]
         L.al_server_admit.argtypes = [_vp, C.POINTER(GridDesc), C.POINTER(BeamDesc), C.POINTER(StepIn),
                                       C.POINTER(StepOut), C.c_ulonglong, C.POINTER(C.c_int)]

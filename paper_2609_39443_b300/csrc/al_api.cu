@@ -103,6 +103,7 @@ struct al_grid_s {
     int *cmcnt = nullptr;             // [2] bricks of a step on the column-march / the brick passes
     int *cmlist = nullptr;            // [2][nbrick_max] those bricks
     int opt_column = 1;               // AL_OPT_COLUMN
+    int own_x0 = 0, own_x1 = -1;      // AL_OPT_OWN_X0 / X1: owned cells along x (-1: to the end)
     long long launches = 0;           // kernels launched by this instance's steps (al_launches)
     // column march (FP32, nearest-segment projection, no reflection): node
     // records, entries of the column-march bricks
@@ -572,6 +573,9 @@ static int cm_launch_bz(const al::Inst<float> &I, bool weights, cudaStream_t st)
     }
 }
 
+// the instance owns only part of its grid's cells along x
+static bool owns_part(const al_grid_s *g) { return g->own_x0 > 0 || (g->own_x1 >= 0 && g->own_x1 < g->d.nx); }
+
 template <typename T>
 static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out *out) {
     using namespace al;
@@ -636,13 +640,25 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     sc.bent_off = g->bent_off; sc.bent_n = g->bent_n;
     I.g.fx = (I.g.rmode || g->opt_record == 2 || g->bd.proj_mode == AL_PROJ_INTEGRATED) ? 1 : 0;
     if (g->bd.wall_reflect) I.g.fx = 0;                 // the reflected passes gather in line order
+    // a slab of a decomposition along x: the brick passes (or the column
+    // march) on the owned brick columns, weights as fixed-point partial sums
+    I.g.own_bx0 = g->own_x0 / al::BX;
+    I.g.own_bx1 = g->own_x1 < 0 ? I.g.nbx : (g->own_x1 + al::BX - 1) / al::BX;
+    if (owns_part(g)) {
+        I.g.wmode = AL_WEIGHTS_BRICK;
+        I.g.smode = AL_SPREAD_GATHER;
+        I.g.rmode = 0;
+        I.g.fx = 0;
+    }
     I.status = out->status ? out->status : g->statusInt;
     I.totals = out->totals ? out->totals : g->totalsInt;
     return I;
 }
 
+// phases: 1 = points, line geometry, bins and weights (up to the weights'
+// partial sums); 2 = normalisation, spread and totals; 3 = the whole step
 template <typename T>
-static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cudaStream_t st) {
+static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cudaStream_t st, int phases = 3) {
     using namespace al;
     const al::Inst<T> I = make_inst<T>(g, in, out);
     const GridC &gc = I.g;
@@ -653,9 +669,11 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
     const int np = g->n_points;
 
     AL_CUDA(spread_smem_attr<T>());
-    trace_mark(g, 0, st);
     const int nb = (np + 255) / 256;
     long long nl = 0;                                        // kernels launched by this step
+    const bool cm = std::is_same<T, float>::value && gc.cm;
+    if (phases & 1) {
+    trace_mark(g, 0, st);
     if (np > 0) {
         nl += 2;
         if (bc.sample_mode == AL_SAMPLE_GAUSS)               // one warp per point
@@ -675,7 +693,6 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
         }
     }
     trace_mark(g, 2, st);
-    const bool cm = std::is_same<T, float>::value && gc.cm;
     if (np > 0) {
         if (gc.wmode != 0) {
             k_weights<T><<<(unsigned)(((long long)np * 32 + 127) / 128), 128, 0, st>>>(gc, bc, sc, p, status);
@@ -694,6 +711,12 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
         }
     }
     trace_mark(g, 3, st);
+    }
+    if (!(phases & 2)) {
+        g->launches += nl;
+        AL_CUDA(cudaGetLastError());
+        return AL_OK;
+    }
     if (np > 0) { k_normalise<T><<<nb, 256, 0, st>>>(gc, bc, sc, p, status); ++nl; }
     trace_mark(g, 4, st);
     nl += cm ? 2 : 1;
@@ -723,7 +746,50 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
     return AL_OK;
 }
 
+static int check_step(al_grid g, const al_step_in *in, const al_step_out *out);
+
 extern "C" int al_sample_drag_spread(al_grid g, const al_step_in *in, const al_step_out *out, void *stream) {
+    const int rc = check_step(g, in, out);
+    if (rc != AL_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    return g->d.precision == AL_FP64 ? step_impl<double>(g, in, out, st) : step_impl<float>(g, in, out, st);
+}
+
+extern "C" int al_step_begin(al_grid g, const al_step_in *in, const al_step_out *out, void *stream) {
+    const int rc = check_step(g, in, out);
+    if (rc != AL_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    return g->d.precision == AL_FP64 ? step_impl<double>(g, in, out, st, 1) : step_impl<float>(g, in, out, st, 1);
+}
+
+extern "C" int al_step_end(al_grid g, const al_step_in *in, const al_step_out *out, void *stream) {
+    const int rc = check_step(g, in, out);
+    if (rc != AL_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    return g->d.precision == AL_FP64 ? step_impl<double>(g, in, out, st, 2) : step_impl<float>(g, in, out, st, 2);
+}
+
+extern "C" int al_weights_get(al_grid g, void *dst, void *stream) {
+    if (!g || (!dst && g->n_points > 0)) return AL_ERR_ARG;
+    if (!g->loaded) return AL_ERR_STATE;
+    if (!owns_part(g) && g->gc.wmode != AL_WEIGHTS_BRICK) return AL_ERR_STATE;
+    if (g->n_points > 0)
+        AL_CUDA(cudaMemcpyAsync(dst, g->wfix, (size_t)g->n_points * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return AL_OK;
+}
+
+extern "C" int al_weights_set(al_grid g, const void *src, void *stream) {
+    if (!g || (!src && g->n_points > 0)) return AL_ERR_ARG;
+    if (!g->loaded) return AL_ERR_STATE;
+    if (!owns_part(g) && g->gc.wmode != AL_WEIGHTS_BRICK) return AL_ERR_STATE;
+    if (g->n_points > 0)
+        AL_CUDA(cudaMemcpyAsync(g->wfix, src, (size_t)g->n_points * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return AL_OK;
+}
+
+static int check_step(al_grid g, const al_step_in *in, const al_step_out *out) {
     if (!g || !in || !out) return AL_ERR_ARG;
     if (!g->loaded) return AL_ERR_STATE;
     for (int a = 0; a < 3; ++a)
@@ -743,8 +809,9 @@ extern "C" int al_sample_drag_spread(al_grid g, const al_step_in *in, const al_s
             if (up && !(in->dt > 0.0 && std::isfinite(in->dt))) return AL_ERR_ARG;
         }
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    return g->d.precision == AL_FP64 ? step_impl<double>(g, in, out, st) : step_impl<float>(g, in, out, st);
+    // a slab: no reflecting face and the paper's nearest-segment projection
+    if (owns_part(g) && (g->bd.wall_reflect || g->bd.proj_mode != AL_PROJ_NEAREST)) return AL_ERR_STATE;
+    return AL_OK;
 }
 
 extern "C" int al_set_option(al_grid g, int option, int value) {
@@ -769,6 +836,15 @@ extern "C" int al_set_option(al_grid g, int option, int value) {
     case AL_OPT_COLUMN:
         if (value != 0 && value != 1) return AL_ERR_ARG;
         g->opt_column = value;
+        return AL_OK;
+    case AL_OPT_OWN_X0:
+        if (value < 0 || value % al::BX != 0 || value >= g->d.nx) return AL_ERR_ARG;
+        g->own_x0 = value;
+        return AL_OK;
+    case AL_OPT_OWN_X1:
+        if (value != -1 && (value <= 0 || value > g->d.nx || (value % al::BX != 0 && value != g->d.nx)))
+            return AL_ERR_ARG;
+        g->own_x1 = value;
         return AL_OK;
     default:
         return AL_ERR_ARG;
@@ -943,7 +1019,7 @@ extern "C" int al_batch_create(al_batch *out) {
 extern "C" int al_batch_add(al_batch b, al_grid g, const al_step_in *in, const al_step_out *out) {
     if (!b || !g || !in || !out) return AL_ERR_ARG;
     if (b->committed) return AL_ERR_STATE;
-    if (!g->loaded) return AL_ERR_STATE;
+    if (!g->loaded || owns_part(g)) return AL_ERR_STATE;
     if (b->precision >= 0 && b->precision != g->d.precision) return AL_ERR_ARG;
     for (int a = 0; a < 3; ++a)
         if (!in->U[a] || !out->S[a]) return AL_ERR_ARG;
@@ -1138,6 +1214,7 @@ extern "C" int al_batch_assign(al_batch b, int slot, al_grid g, const al_step_in
     if (slot < 0 || slot >= b->n) return AL_ERR_ARG;
     if (g) {
         if (!in || !out || !g->loaded || g->d.precision != b->precision) return AL_ERR_ARG;
+        if (owns_part(g)) return AL_ERR_STATE;
         for (int a = 0; a < 3; ++a)
             if (!in->U[a] || !out->S[a]) return AL_ERR_ARG;
         if (g->d.has_alpha && !in->alpha) return AL_ERR_ARG;
@@ -1408,5 +1485,72 @@ extern "C" int al_batch_autotune(al_batch b, int trials, void *stream, int *choi
 extern "C" int al_launches(al_grid g, long long *n) {
     if (!g || !n) return AL_ERR_ARG;
     *n = g->launches;
+    return AL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// slab plan of a decomposition along x (host logic)
+// ---------------------------------------------------------------------------
+extern "C" int al_slab_plan(const al_grid_desc *grid, const al_beam_desc *beams, const double *P_host, int n_ranks,
+                            int rank, al_slab *out, int *lines, int *owner) {
+    if (!grid || !beams || !out || n_ranks < 1 || rank < 0 || rank >= n_ranks) return AL_ERR_ARG;
+    if (grid->nx < 1 || !(grid->dx > 0.0) || beams->n_lines < 0) return AL_ERR_ARG;
+    int np = 0;
+    const int rc = al_detail_check_beams(*beams, *grid, &np);
+    if (rc != AL_OK) return rc;
+    if (np > 0 && !P_host) return AL_ERR_ARG;
+    const double h = grid->dx, ox = grid->origin[0];
+    const int nbx = (grid->nx + al::BX - 1) / al::BX;
+    const int bx0 = (int)((long long)rank * nbx / n_ranks), bx1 = (int)((long long)(rank + 1) * nbx / n_ranks);
+    out->x0 = std::min(bx0 * al::BX, grid->nx);
+    out->x1 = std::min(bx1 * al::BX, grid->nx);
+    // per line: x range of its points and its reach 3 eps + L (longest segment)
+    double need = 0.0;
+    std::vector<double> lo(beams->n_lines), hi(beams->n_lines), reach(beams->n_lines);
+    for (int l = 0; l < beams->n_lines; ++l) {
+        const int a = beams->line_off[l], b = beams->line_off[l + 1];
+        double mn = INFINITY, mx = -INFINITY, L = 0.0;
+        for (int i = a; i < b; ++i) {
+            mn = std::min(mn, P_host[i]);
+            mx = std::max(mx, P_host[i]);
+            if (i + 1 < b) {
+                double d2 = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    const double d = P_host[(size_t)c * np + i + 1] - P_host[(size_t)c * np + i];
+                    d2 += d * d;
+                }
+                L = std::max(L, std::sqrt(d2));
+            }
+        }
+        lo[l] = mn; hi[l] = mx;
+        reach[l] = 3.0 * beams->eps[l] + L;
+        need = std::max(need, beams->ell_s[l] + reach[l]);
+    }
+    int halo = (int)std::ceil(need / h) + 2;
+    halo = (halo + al::BX - 1) / al::BX * al::BX;
+    out->halo = halo;
+    out->lx0 = std::max(0, out->x0 - halo);
+    out->lx1 = std::min(grid->nx, out->x1 + halo);
+    const double X0 = ox + out->x0 * h, X1 = ox + out->x1 * h;
+    int n = 0;
+    for (int l = 0; l < beams->n_lines; ++l) {
+        if (beams->line_off[l + 1] == beams->line_off[l]) continue;
+        const double r = reach[l] + h;
+        if (hi[l] + r >= X0 && lo[l] - r < X1 && out->x1 > out->x0) {
+            if (lines) lines[n] = l;
+            ++n;
+        }
+    }
+    out->n_lines = n;
+    if (owner)
+        for (int i = 0; i < np; ++i) {
+            long long c = (long long)std::floor((P_host[i] - ox) / h);
+            c = std::max(0ll, std::min((long long)grid->nx - 1, c));
+            int r = 0;
+            while (r + 1 < n_ranks && c >= std::min((long long)((long long)(r + 1) * nbx / n_ranks) * al::BX,
+                                                    (long long)grid->nx))
+                ++r;
+            owner[i] = r;
+        }
     return AL_OK;
 }

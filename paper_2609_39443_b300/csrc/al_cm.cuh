@@ -462,6 +462,12 @@ __global__ void __launch_bounds__(256) k_cm_entries(GridC g, BeamsC b, Scratch<T
     const int W = b.mask_words, wper = (W + 31) / 32;
     uint32_t *mrow = sc.mask + (long long)br * W;
     const int wa = min(W, lane * wper), wb = min(W, wa + wper);
+    if (!brick_owned(g, br)) {                         // another slab's cells: neither pass visits them
+        if (lane < 3) sc.brickSum[lane * g.nbrick + br] = 0.0;
+        if (lane == 0) { CHK(br < g.nbrick_max, 8) { sc.bent_off[br] = 0; sc.bent_n[br] = 0; } }
+        for (int w = wa; w < wb; ++w) mrow[w] = 0u;
+        return;
+    }
     int cnt = 0, bad = 0;
     for (int w = wa; w < wb; ++w) {
         uint32_t m = mrow[w];

@@ -69,7 +69,15 @@ struct GridC {
     long long rec_total;         // capacity of the record arena (records)
     long long nbrick_max;        // bricks at the lowest brick height (size of the per-brick arrays)
     int cm;                      // 1: bricks whose lines all take the column march use the column-march passes
+    int own_bx0, own_bx1;        // brick columns along x whose cells this instance owns (a slab of a
+                                 // decomposition along x): the weights and spread passes work on them only
 };
+
+// the brick's cells are owned (the weights and spread passes visit it)
+__device__ __forceinline__ bool brick_owned(const GridC &g, long long br) {
+    const int bx = (int)(br % g.nbx);
+    return bx >= g.own_bx0 && bx < g.own_bx1;
+}
 
 // one (cell, segment) pair of a certified line inside the 3 eps support, as
 // the segment pass found it: the cell within its brick (z * 256 + y * 16 + x),
@@ -2967,6 +2975,10 @@ __global__ void __launch_bounds__(SPREAD_THREADS) k_spread(GridC g, BeamsC b, Sc
                                                            int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T, BZ, FX> &sm = *reinterpret_cast<SpreadSmem<T, BZ, FX> *>(smem_raw);
+    if (!brick_owned(g, blockIdx.x)) {                 // another slab's cells: no sources, no sum
+        if (threadIdx.x < 3) sc.brickSum[threadIdx.x * g.nbrick + blockIdx.x] = 0.0;
+        return;
+    }
     d_brick<T, false, BZ, FX>(g, b, sc, p, status, (int)blockIdx.x, sm);
 }
 template <typename T, int BZ>
@@ -2974,6 +2986,7 @@ __global__ void __launch_bounds__(SPREAD_THREADS) k_bweights(GridC g, BeamsC b, 
                                                              int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
+    if (!brick_owned(g, blockIdx.x)) return;           // another slab's cells add nothing to the weights
     d_brick<T, true, BZ, false>(g, b, sc, p, status, (int)blockIdx.x, sm);
 }
 
