@@ -77,6 +77,8 @@ def _args():
     ap.add_argument("--no-variants", action="store_true", help="skip timing the scatter projection")
     ap.add_argument("--weights", choices=["brick", "segment"], default=None, help="fix the weights pass (no tuning)")
     ap.add_argument("--brick-z", type=int, choices=[4, 8, 16], default=None, help="fix the brick height (no tuning)")
+    ap.add_argument("--column", choices=["on", "off"], default=None,
+                    help="fix the column march on or off (no tuning)")
     ap.add_argument("--records", choices=["on", "off"], default=None,
                     help="fix whether the segment pass records pairs for the spread to replay (no tuning)")
     return ap.parse_args()
@@ -101,7 +103,8 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for f in ("paper_2609_39443_b300/csrc/al_kernels.cuh", "paper_2609_39443_b300/csrc/al_api.cu"):
+    for f in ("paper_2609_39443_b300/csrc/al_kernels.cuh", "paper_2609_39443_b300/csrc/al_cm.cuh",
+              "paper_2609_39443_b300/csrc/al_api.cu"):
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -118,7 +121,7 @@ def _traffic(workload_name, kernel="k_spread", options=None):
     if not e or e.get("kernel_hash") != _kernel_hash():
         return None
     if options is not None and "options" in e:
-        if any(e["options"].get(k) != options.get(k) for k in ("weights", "brick_z", "records")):
+        if any(e["options"].get(k) != options.get(k) for k in ("weights", "brick_z", "records", "column_march")):
             return None
     return e.get("dram_bytes_per_launch")
 
@@ -279,7 +282,7 @@ def run_ours(a):
             B.build()
         if dist:
             dist.barrier()
-    from paper_2609_39443_b300.al import Instance, PHASES, ST_SUPPORT
+    from paper_2609_39443_b300.al import Instance, PHASES, ST_COLUMN, ST_SUPPORT
 
     wl = _workload(a.workload, instance_seed(rank), a.eps, a.reduced)
     if a.inertia:
@@ -296,19 +299,20 @@ def run_ours(a):
         wl = W.with_reflect(wl, a.reflect)
     inst = Instance(wl, device=f"cuda:{local}")
     tuned = {"weights": "brick", "brick_z": 8, "autotuned": False}
-    if a.weights or a.brick_z or a.records:
-        from paper_2609_39443_b300.al import OPT_BRICK_Z, OPT_RECORD, OPT_WEIGHTS
+    if a.weights or a.brick_z or a.records or a.column:
+        from paper_2609_39443_b300.al import OPT_BRICK_Z, OPT_COLUMN, OPT_RECORD, OPT_WEIGHTS
         tuned = {"weights": a.weights or "brick", "brick_z": a.brick_z or 8, "records": a.records != "off",
-                 "autotuned": False}
+                 "column_march": a.column != "off", "autotuned": False}
         inst.grid.set_option(OPT_WEIGHTS, 1 if tuned["weights"] == "segment" else 0)
         inst.grid.set_option(OPT_BRICK_Z, tuned["brick_z"])
         inst.grid.set_option(OPT_RECORD, 1 if tuned["records"] else 0)
+        inst.grid.set_option(OPT_COLUMN, 1 if tuned["column_march"] else 0)
     elif not a.no_tune:
         wmode, bz, rec, col = inst.autotune(trials=2)
         tuned = {"weights": "segment" if wmode else "brick", "brick_z": bz, "records": bool(rec),
                  "column_march": bool(col), "autotuned": True}
     if a.reflect:                                    # the library takes the brick passes for it
-        tuned.update(weights="brick", records=False)
+        tuned.update(weights="brick", records=False, column_march=False)
     inst.grid.trace(True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
@@ -318,6 +322,7 @@ def run_ours(a):
         inst.step()
     torch.cuda.synchronize()
     supp = int(inst.status[ST_SUPPORT].item())
+    tuned["column_march"] = int(inst.status[ST_COLUMN].item()) > 0       # bricks that took it in the last step
 
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
@@ -422,24 +427,27 @@ def run_ours(a):
     peak, peak_kind = _peaks()
     alg = _algorithmic_bytes(wl)
     achieved = alg / spread_s / 1e9
-    traffic = _traffic(wl.name, options=tuned)
+    cmk = bool(tuned.get("column_march"))
+    spread_kernel = "k_cm_spread" if cmk else "k_spread"
+    weights_kernel = "k_cm_weights" if cmk else ("k_weights" if tuned["weights"] == "segment" else "k_bweights")
+    traffic = _traffic(wl.name, spread_kernel, options=tuned)
     weights_s = ph[PHASES.index("weights")] / 1e3
     step_alg = _step_algorithmic_bytes(wl)
     step_gbs = step_alg / (total_s / a.steps) / 1e9 * world
     flop = supp * FLOP_PER_PAIR
     w_tf = flop / weights_s / 1e12 if weights_s > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": "k_spread", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "hbm", "kernel": spread_kernel, "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "algorithmic_bytes": alg, "traffic": traffic,
                 "step": {"bound": "hbm", "achieved": step_gbs, "peak": peak, "unit": "GB/s",
                          "frac": step_gbs / peak, "algorithmic_bytes": step_alg,
                          "ms": 1e3 * total_s / a.steps},
-                "weights_pass": {"bound": "alu", "kernel": "k_weights" if tuned["weights"] == "segment" else "k_bweights",
+                "weights_pass": {"bound": "alu", "kernel": weights_kernel,
                                  "achieved": w_tf, "peak": ALU_PEAK_TFLOPS,
                                  "peak_kind": "derived (148 SMs x 128 FP32 lanes x FMA x 2.032 GHz)",
                                  "unit": "TFLOP/s", "frac": w_tf / ALU_PEAK_TFLOPS, "algorithmic_flop": flop,
                                  "ms": 1e3 * weights_s,
-                                 "traffic": _traffic(wl.name, "k_weights", tuned)}}
+                                 "traffic": _traffic(wl.name, weights_kernel, tuned)}}
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         v, cores, sample = _cpu_baseline(wl)

@@ -992,21 +992,32 @@ __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, con
             }
         }
     }
+    // the brick's sums: float-float over the warp (the three components
+    // interleaved), then the warps' pairs in FP64, one lane per component
     {
-        Acc<float> a3[3];
-        a3[0].add(cs0); a3[1].add(cs1); a3[2].add(cs2);
-        for (int a = 0; a < 3; ++a) w_store(&sm.red[a][warp], a3[a]);
+        float h[3] = {cs0, cs1, cs2}, l[3] = {0.0f, 0.0f, 0.0f};
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float oh = __shfl_xor_sync(0xffffffffu, h[a], o), ol = __shfl_xor_sync(0xffffffffu, l[a], o);
+                float su, er;
+                two_sum(h[a], oh, su, er);
+                er = __fadd_rn(er, __fadd_rn(l[a], ol));
+                fast_two_sum(su, er, h[a], l[a]);
+            }
+        }
+        if (lane == 0)
+            for (int a = 0; a < 3; ++a) *reinterpret_cast<float2 *>(&sm.red[a][warp]) = make_float2(h[a], l[a]);
     }
     for (int o = 16; o > 0; o >>= 1) nsupp += __shfl_down_sync(0xffffffffu, nsupp, o);
     if (lane == 0) sm.redi[warp] = nsupp;
     __syncthreads();
-    if (tid == 0) {
+    if (warp == 0 && lane < 3) {
+        double t = 0.0;
+        for (int w2 = 0; w2 < NW; ++w2) t += w_load<float>(&sm.red[lane][w2]);
+        sc.brickSum[lane * g.nbrick + br] = t;
+    } else if (warp == 0 && lane == 3) {
         int ns = 0;
-        for (int a = 0; a < 3; ++a) {
-            double t = 0.0;
-            for (int w2 = 0; w2 < NW; ++w2) t += w_load<float>(&sm.red[a][w2]);
-            sc.brickSum[a * g.nbrick + br] = t;
-        }
         for (int w2 = 0; w2 < NW; ++w2) ns += sm.redi[w2];
         if (ns) atomicAdd(&status[ST_SUPPORT], ns);
         atomicAdd(&status[ST_COLUMN], 1);

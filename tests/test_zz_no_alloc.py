@@ -71,6 +71,13 @@ def test_noalloc_line_forces_match_the_step_and_the_oracle_on_two_calls():
     s_new = st1.cpu().numpy()
     for k in (0, 1, 2, 3):
         assert s_ref[k] == s_new[k] == o1["status"][k]
+    # later calls take no device memory: the free bytes do not move
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        line_forces_noalloc(w2.grid, w2.beams, ref2.U, ref2.P, ref2.Pdot, F2, alpha=ref2.alpha, f_prev=f_prev)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
     ref1.close()
     ref2.close()
 
