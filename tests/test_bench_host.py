@@ -29,6 +29,7 @@ def test_committed_traffic_entries_are_well_formed():
     assert d
     for key, e in d.items():
         wl, kernel = key.split("/")
-        assert kernel in ("k_spread", "k_weights")
+        assert kernel in ("k_spread", "k_weights", "k_bweights", "k_cm_spread", "k_cm_weights")
         assert e["dram_bytes_per_launch"] > 0 and len(e["kernel_hash"]) == 16
-        assert set(e["options"]) == {"weights", "brick_z", "records"}
+        assert {"weights", "brick_z", "records"} <= set(e["options"]) <= {"weights", "brick_z", "records",
+                                                                          "column_march"}
