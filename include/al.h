@@ -399,6 +399,12 @@ int al_batch_set_option(al_batch b, int option, int value);
  * many as fit).  Every slot must be bound. */
 int al_batch_autotune(al_batch b, int trials, void *stream, int *choice);
 
+/* Kernels the batch's al_batch_run / al_batch_run_subset calls have
+ * launched so far (cumulative, counted on the host: an enqueue counts its
+ * kernels, a graph replay the kernels captured in the graph; the batch
+ * autotuner's trial runs count too).  Returns AL_ERR_ARG for a NULL argument. */
+int al_batch_launches(al_batch b, long long *n);
+
 /* ---- the step in two phases (decomposition along x, Sec. 3.2.5) ------- */
 /* al_step_begin runs a step up to the nodal weights (Algorithm 1 steps 1-3:
  * points, line geometry, bins and the weights pass); al_step_end runs the

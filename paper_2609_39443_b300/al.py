@@ -105,6 +105,7 @@ def lib():
         L.al_autotune.argtypes = [_vp, C.POINTER(StepIn), C.POINTER(StepOut), C.c_int, _vp, C.POINTER(C.c_int)]
         L.al_batch_set_option.argtypes = [_vp, C.c_int, C.c_int]
         L.al_batch_autotune.argtypes = [_vp, C.c_int, _vp, C.POINTER(C.c_int)]
+        L.al_batch_launches.argtypes = [_vp, C.POINTER(C.c_longlong)]
         L.al_trace_last.argtypes = [_vp, C.POINTER(C.c_float)]
         L.al_step_begin.argtypes = [_vp, C.POINTER(StepIn), C.POINTER(StepOut), _vp]
         L.al_step_end.argtypes = [_vp, C.POINTER(StepIn), C.POINTER(StepOut), _vp]
@@ -395,6 +396,12 @@ class Batch:
         ch = C.c_int(0)
         check(lib().al_batch_autotune(self.h, int(trials), _stream_ptr(stream), C.byref(ch)), "al_batch_autotune")
         return ch.value // 10, ch.value % 10
+
+    def launches(self) -> int:
+        """al_batch_launches: kernels the batch's runs have launched so far."""
+        n = C.c_longlong(0)
+        check(lib().al_batch_launches(self.h, C.byref(n)), "al_batch_launches")
+        return n.value
 
     def run_subset(self, idx, stream=None):
         arr = (C.c_int * len(idx))(*[int(i) for i in idx])

@@ -91,6 +91,7 @@ struct al_grid_s {
     // per-grid scratch
     double *brickSum = nullptr;
     double *scatSum = nullptr;
+    double *totPart = nullptr;        // [TOT_PARTS][6] partial totals
     int *statusInt = nullptr;
     double *totalsInt = nullptr;
     int *hasPrev = nullptr;           // device flag: f_prev is valid
@@ -108,6 +109,7 @@ struct al_grid_s {
     // column march (FP32, nearest-segment projection, no reflection): node
     // records, entries of the column-march bricks
     float4 *cmN = nullptr;            // [np][4] node records
+    int2 *cmrange = nullptr;          // [n_lines][(nz + 3) / 4] candidate segments per brick layer
     al::CmEnt *cment = nullptr;
     int *cment_n = nullptr, *bent_off = nullptr, *bent_n = nullptr;
     long long cment_cap = 0;
@@ -147,6 +149,7 @@ static void free_beams(al_grid g) {
     g->rec = nullptr;
     g->rec_total = 0;
     g->cmN = nullptr;
+    g->cmrange = nullptr;
     g->cment = nullptr;
     g->cment_n = g->bent_off = g->bent_n = nullptr;
     g->cment_cap = 0;
@@ -210,6 +213,7 @@ extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
     auto carve = [&](Slab &sl) {
         sl.take(&g->brickSum, 3 * (size_t)g->nbrick_max);
         sl.take(&g->scatSum, 3);
+        sl.take(&g->totPart, 6 * (size_t)al::TOT_PARTS);
         sl.take(&g->statusInt, AL_STATUS_N); sl.take(&g->totalsInt, 6);
         sl.take(&g->hasPrev, 1); sl.take(&g->anyIrr, 1); sl.take(&g->smax, 1); sl.take(&g->anyZero, 1);
         sl.take(&g->rcnt, (size_t)g->nbrick_max); sl.take(&g->rcap, (size_t)g->nbrick_max);
@@ -376,6 +380,7 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
             // 16 entries per brick at the lowest brick height (bricks beyond it in
             // a step take the brick passes)
             A(&g->cmN, 4 * (size_t)np);
+            A(&g->cmrange, nl * (size_t)((g->d.nz + 3) / 4));
             g->cment_cap = 16 * g->nbrick_max;
             A(&g->cment, (size_t)g->cment_cap);
             A(&g->cment_n, 1);
@@ -604,6 +609,7 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     sc.segIl2 = (T *)g->segIl2; sc.nodeM = (T *)g->nodeM; sc.nodeTau = g->nodeTau;
     sc.segWa = g->segWa; sc.segWb = g->segWb; sc.wfix = g->wfix; sc.w = g->w; sc.fhat = (T *)g->fhat; sc.lineF = g->lineF;
     sc.lines = g->lines; sc.mask = g->mask; sc.brickSum = g->brickSum; sc.scatSum = g->scatSum;
+    sc.totPart = g->totPart;
     sc.hasPrev = g->hasPrev; sc.anyIrr = g->anyIrr; sc.smax = g->smax; sc.anyZero = g->anyZero;
     sc.rec = (Rec<T> *)g->rec; sc.rcnt = g->rcnt; sc.rcap = g->rcap; sc.roff = g->roff;
     sc.rplan = g->rplan; sc.rused = g->rused;
@@ -636,6 +642,7 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     // no reflecting face, the gather
     I.g.cm = (g->opt_column && g->cmN && I.g.smode == AL_SPREAD_GATHER) ? 1 : 0;
     sc.cmN = I.g.cm ? g->cmN : nullptr;
+    sc.cmrange = I.g.cm ? g->cmrange : nullptr;
     sc.cment = g->cment; sc.cment_n = I.g.cm ? g->cment_n : nullptr; sc.cment_cap = g->cment_cap;
     sc.bent_off = g->bent_off; sc.bent_n = g->bent_n;
     I.g.fx = (I.g.rmode || g->opt_record == 2 || g->bd.proj_mode == AL_PROJ_INTEGRATED) ? 1 : 0;
@@ -738,8 +745,9 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
         ++nl;
     }
     trace_mark(g, 5, st);
-    k_totals<T><<<1, 256, 0, st>>>(gc, bc, sc, I.totals);
-    ++nl;
+    k_totals<T><<<TOT_PARTS, 256, 0, st>>>(gc, bc, sc);
+    k_totals_fin<T><<<1, 32, 0, st>>>(gc, sc, I.totals);
+    nl += 2;
     g->launches += nl;
     trace_mark(g, 6, st);
     AL_CUDA(cudaGetLastError());
@@ -1003,6 +1011,9 @@ struct al_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;
+    long long launches = 0;                   // kernels the batch's runs launched (al_batch_launches)
+    int last_nl = 0;                          // kernels of the last enqueue
+    int graph_nl = 0;                         // kernels in the captured graph
 
     static size_t slot_bytes(int n) {
         size_t a = ((size_t)n * sizeof(int) + 15) & ~(size_t)15;
@@ -1057,6 +1068,7 @@ static int batch_rebuild_t(al_batch b) {
             h[q].g.smode = 0;                                // batches always gather
             h[q].g.cm = 0;                                   // and take the brick passes
             h[q].sc.cmN = nullptr;
+            h[q].sc.cmrange = nullptr;
             h[q].sc.cment_n = nullptr;
             if (h[q].g.wmode != 0) b->any_segment_weights = true;
             if (h[q].b.sample_mode == AL_SAMPLE_GAUSS) b->any_gauss = true;
@@ -1128,17 +1140,20 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
         long long g = (items + per_block - 1) / per_block;
         return (unsigned)std::max<long long>(1, std::min<long long>(g, (long long)b->pt_grid * 4));
     };
+    int nl = 0;
     if (tot_pts > 0) {
         // each instance in the same form as alone: a warp per point for the
         // volume-average sampler, a thread per point otherwise
         kb_points<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n, b->any_gauss ? 1 : 0);
         if (b->any_gauss) kb_points_w<T><<<grid_for(tot_pts, 8), 256, 0, st>>>(I, sel, pp, n);
         kb_segments<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
+        nl += b->any_gauss ? 3 : 2;
     }
-    if (tot_lines > 0) kb_lines<T><<<grid_for(tot_lines, 8), 256, 0, st>>>(I, sel, pl, n);
+    if (tot_lines > 0) { kb_lines<T><<<grid_for(tot_lines, 8), 256, 0, st>>>(I, sel, pl, n); ++nl; }
     if (tot_pts > 0) {
         kb_mask<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
-        if (b->any_segment_weights) kb_weights<T><<<grid_for(tot_pts, 4), 128, 0, st>>>(I, sel, pp, n);
+        ++nl;
+        if (b->any_segment_weights) { kb_weights<T><<<grid_for(tot_pts, 4), 128, 0, st>>>(I, sel, pp, n); ++nl; }
         if (tot_bricks > 0) {
             const int gs = (int)std::min<long long>(b->spread_grid, tot_bricks);
             switch (b->bz) {
@@ -1151,8 +1166,10 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
             case 16: kb_bweights_refl<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, false>), st>>>(I, sel, pb, n); break;
             default: kb_bweights_refl<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, false>), st>>>(I, sel, pb, n); break;
             }
+            nl += b->any_reflect ? 2 : 1;
         }
         kb_normalise<T><<<grid_for(tot_pts, 256), 256, 0, st>>>(I, sel, pp, n);
+        ++nl;
     }
     if (tot_bricks > 0) {
         const int gs = (int)std::min<long long>(b->spread_grid, tot_bricks);
@@ -1166,8 +1183,12 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
         case 16: kb_spread_refl<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, false>), st>>>(I, sel, pb, n); break;
         default: kb_spread_refl<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, false>), st>>>(I, sel, pb, n); break;
         }
+        nl += b->any_reflect ? 2 : 1;
     }
-    kb_totals<T><<<std::max(1, std::min(n, 1024)), 256, 0, st>>>(I, sel, n);
+    kb_totals<T><<<std::max(1, std::min(n * TOT_PARTS, 2048)), 256, 0, st>>>(I, sel, n);
+    kb_totals_fin<T><<<std::max(1, std::min(n, 1024)), 32, 0, st>>>(I, sel, n);
+    nl += 2;
+    b->last_nl = nl;
     AL_CUDA(cudaGetLastError());
     return AL_OK;
 }
@@ -1255,7 +1276,11 @@ extern "C" int al_batch_run(al_batch b, void *stream) {
                    ? batch_enqueue_t<double>(b, s, nullptr, b->d_pre, b->n, b->tot_pts, b->tot_lines, b->tot_bricks)
                    : batch_enqueue_t<float>(b, s, nullptr, b->d_pre, b->n, b->tot_pts, b->tot_lines, b->tot_bricks);
     };
-    if (!b->use_graph) return enqueue(st);
+    if (!b->use_graph) {
+        int rc = enqueue(st);
+        if (rc == AL_OK) b->launches += b->last_nl;
+        return rc;
+    }
     if (!b->exec) {
         if (!b->cap) AL_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
         AL_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
@@ -1265,9 +1290,11 @@ extern "C" int al_batch_run(al_batch b, void *stream) {
         if (rc != AL_OK) return rc;
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
         b->graph = graph;
+        b->graph_nl = b->last_nl;
         AL_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
     }
     AL_CUDA(cudaGraphLaunch(b->exec, st));
+    b->launches += b->graph_nl;
     return AL_OK;
 }
 
@@ -1304,6 +1331,7 @@ extern "C" int al_batch_run_subset(al_batch b, const int *idx, int n_idx, void *
     int rc = b->precision == AL_FP64 ? batch_enqueue_t<double>(b, st, ds, dp, n_idx, tp, tl, tb)
                                      : batch_enqueue_t<float>(b, st, ds, dp, n_idx, tp, tl, tb);
     if (rc != AL_OK) return rc;
+    b->launches += b->last_nl;
     AL_CUDA(cudaEventRecord(b->ring_ev[r], st));
     return AL_OK;
 }
@@ -1480,6 +1508,12 @@ extern "C" int al_batch_autotune(al_batch b, int trials, void *stream, int *choi
     if (rc == AL_OK) rc = rc2;
     if (rc == AL_OK && choice) *choice = 10 * best_z + best_c;
     return rc;
+}
+
+extern "C" int al_batch_launches(al_batch b, long long *n) {
+    if (!b || !n) return AL_ERR_ARG;
+    *n = b->launches;
+    return AL_OK;
 }
 
 extern "C" int al_launches(al_grid g, long long *n) {

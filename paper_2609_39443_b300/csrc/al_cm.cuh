@@ -270,6 +270,39 @@ __device__ __forceinline__ void cm_walk_at(const CmCtx &c, CmWalk &w, int j, flo
     w.n2M = cm_rec(c, j2, CM_M);
 }
 
+// The walk without records held ahead (for records in shared memory, where
+// a load at the advance is cheap): the same state, from the same operations
+// on the same records, as CmWalk's.
+struct CmWalkL {
+    int j;
+    float xx, xy, pz, il2, dx, dy, dz, dxy, b1, m1z;
+};
+__device__ __forceinline__ void cm_walkl_at(const CmCtx &c, CmWalkL &w, int j, float Xl, float Yl) {
+    const float4 P = cm_rec(c, j, CM_P), D = cm_rec(c, j, CM_D);
+    w.j = j;
+    w.xx = __fsub_rn(Xl, P.x);
+    w.xy = __fsub_rn(Yl, P.y);
+    w.pz = P.z;
+    w.il2 = P.w;
+    w.dx = D.x; w.dy = D.y; w.dz = D.z;
+    w.dxy = __fmaf_rn(w.xy, D.y, __fmul_rn(w.xx, D.x));
+    if (j + 1 < c.nseg) {
+        const float4 P1 = cm_rec(c, j + 1, CM_P), M1 = cm_rec(c, j + 1, CM_M);
+        w.b1 = cm_b1(Xl, Yl, P1, M1);
+        w.m1z = M1.z;
+    } else {
+        w.b1 = -INFINITY;
+        w.m1z = 0.0f;
+    }
+}
+__device__ __forceinline__ void cm_geoml(const CmWalkL &w, float Zl, float &s, float &r2) {
+    const float xz = __fsub_rn(Zl, w.pz);
+    const float dot = __fmaf_rn(xz, w.dz, w.dxy);
+    s = __saturatef(__fmul_rn(dot, w.il2));
+    const float ex = __fmaf_rn(-s, w.dx, w.xx), ey = __fmaf_rn(-s, w.dy, w.xy), ez = __fmaf_rn(-s, w.dz, xz);
+    r2 = __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
+}
+
 // foot s (clamped) and r^2 of the cell at height Zl and the current segment
 __device__ __forceinline__ void cm_geom(const CmWalk &w, float Zl, float &s, float &r2) {
     const float xz = __fsub_rn(Zl, w.pz);
@@ -369,27 +402,39 @@ __device__ __forceinline__ void cm_exact_init(CmExact &x, const GridC &g, const 
 // line, so they form a range), and at least the brick's own height range,
 // so that a node inside the brick is a candidate node for its zero-weight
 // deposit
-static __device__ void cm_make_entry(const BeamsC &b, const Scratch<float> &sc, int br, int l, int B0, int B1, int B2,
-                                     int nzb, int bz, CmEnt &e, int *status) {
+// per brick layer of a certified line (one warp, k_lines): the candidate
+// segments [jlo, jhi] of the layer's bricks
+static __device__ void cm_layer_ranges(const GridC &g, const Scratch<float> &sc, long long np, int l, int off, int n,
+                                float Rc, int lane) {
+    const int nbz_max = (g.nz + 3) / 4;
+    const float *uz = sc.uhi + 2 * np + off;
+    for (int bzi = lane; bzi < g.nbz; bzi += 32) {
+        const int B2 = bzi * g.bz, nzb = min(g.bz, g.nz - B2);
+        const float zlo = (float)B2 + fminf(0.5f - Rc, 0.0f) - 0.02f;
+        const float zhi = (float)B2 + (float)nzb + fmaxf(Rc - 0.5f, 0.0f) + 0.02f;
+        int lo = 1, hi = n;                      // first node q >= 1 with z_q >= zlo (n: none)
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (uz[mid] >= zlo) hi = mid; else lo = mid + 1;
+        }
+        const int jlo = lo - 1;
+        lo = -1; hi = n - 2;                     // last node q <= n - 2 with z_q <= zhi (-1: none)
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (uz[mid] <= zhi) lo = mid; else hi = mid - 1;
+        }
+        sc.cmrange[(long long)l * nbz_max + bzi] = make_int2(jlo, lo);
+    }
+}
+
+static __device__ void cm_make_entry(const GridC &g, const BeamsC &b, const Scratch<float> &sc, int br, int l, int B0,
+                                     int B1, int B2, int nzb, int bz, CmEnt &e, int *status) {
     const long long np = b.n_points;
     const LineG &lg = sc.lines[l];
     const int first = lg.first, n = lg.n;
     const float Rc = lg.Rc;
-    const float zlo = (float)B2 + fminf(0.5f - Rc, 0.0f) - 0.02f;
-    const float zhi = (float)B2 + (float)nzb + fmaxf(Rc - 0.5f, 0.0f) + 0.02f;
-    const float *uz = sc.uhi + 2 * np + first;
-    int lo = 1, hi = n;                      // first node q >= 1 with z_q >= zlo (n: none)
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (uz[mid] >= zlo) hi = mid; else lo = mid + 1;
-    }
-    const int jlo = lo - 1;
-    lo = -1; hi = n - 2;                     // last node q <= n - 2 with z_q <= zhi (-1: none)
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (uz[mid] <= zhi) lo = mid; else hi = mid - 1;
-    }
-    const int jhi = lo;
+    const int2 jr = sc.cmrange[(long long)l * ((g.nz + 3) / 4) + B2 / bz];
+    const int jlo = jr.x, jhi = jr.y;
     e.br = br;
     e.line = l;
     e.kfirst = first + jlo;
@@ -530,7 +575,7 @@ __global__ void __launch_bounds__(256) k_cm_entries(GridC g, BeamsC b, Scratch<T
             const int l = lst[wib][i];
             CHK(l >= 0 && l < b.n_lines, 32) {
                 if constexpr (std::is_same<T, float>::value)
-                    cm_make_entry(b, sc, br, l, B0, B1, B2, nzb, g.bz, e, status);
+                    cm_make_entry(g, b, sc, br, l, B0, B1, B2, nzb, g.bz, e, status);
                 CHK((long long)off + p0 + i < sc.cment_cap && off + p0 + i >= 0, 64) sc.cment[off + p0 + i] = e;
             }
         }
@@ -752,8 +797,8 @@ static __device__ __noinline__ int cm_tail(const CmCtx *c, CmWalk *w, const floa
 // same values).  A value inside a band stops the march at its layer, which
 // is returned (BZ: none); cm_tail continues from there.
 template <int BZ>
-__device__ __forceinline__ int cm_march_acc(const CmCtx &c, CmWalk &w, float Xl, float Yl, int zf, int zl, float eta0,
-                                            float4 &fa, float4 &fb, float4 &nF, float (&acc)[BZ][3], int &nsupp) {
+__device__ __forceinline__ int cm_march_acc(const CmCtx &c, CmWalkL &w, float Xl, float Yl, int zf, int zl, float eta0,
+                                            float3 &fa, float3 &fb, float (&acc)[BZ][3], int &nsupp) {
     const float Z0 = __fadd_rn(0.5f, c.oz);
     int stop = BZ;
 #pragma unroll
@@ -762,16 +807,15 @@ __device__ __forceinline__ int cm_march_acc(const CmCtx &c, CmWalk &w, float Xl,
         const float Zl = __fadd_rn(Z0, (float)z);
         float sg = __fmaf_rn(Zl, w.m1z, w.b1);
         while (sg >= c.gs) {
-            const int jp = w.j;
-            cm_adv(c, w, Xl, Yl);
+            cm_walkl_at(c, w, w.j + 1, Xl, Yl);
             fa = fb;
-            fb = nF;
-            nF = cm_rec(c, min(jp + 3, c.nseg), CM_F);
+            const float4 f = cm_rec(c, w.j + 1, CM_F);
+            fb = make_float3(f.x, f.y, f.z);
             sg = __fmaf_rn(Zl, w.m1z, w.b1);
         }
         if (sg > -c.gs) { stop = z; continue; }
         float s, r2;
-        cm_geom(w, Zl, s, r2);
+        cm_geoml(w, Zl, s, r2);
         if (r2 < c.R2lo) {
             ++nsupp;
             const float meq = -__fmul_rn(eta0, Tr<float>::ex2(__fmul_rn(-r2, c.ie2)));
@@ -896,16 +940,22 @@ __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, con
                     const CmCtx cc = c;
                     j = cm_start_slow(&cc, e.j0, Xl, Yl, Zl0);
                 }
-                CmWalk w;
-                cm_walk_at(c, w, j, Xl, Yl);
-                float4 f[3] = {cm_rec(c, j, CM_F), cm_rec(c, j + 1, CM_F), cm_rec(c, min(j + 2, c.nseg), CM_F)};
-                const float eta0 = e.eta0;
-                const int zs = cm_march_acc<BZ>(c, w, Xl, Yl, e.zf, e.zl, eta0, f[0], f[1], f[2], acc, nsupp);
+                CmWalkL w;
+                cm_walkl_at(c, w, j, Xl, Yl);
+                const float4 f0 = cm_rec(c, j, CM_F), f1 = cm_rec(c, j + 1, CM_F);
+                float3 fa = make_float3(f0.x, f0.y, f0.z), fb = make_float3(f1.x, f1.y, f1.z);
+                const int zs = cm_march_acc<BZ>(c, w, Xl, Yl, e.zf, e.zl, e.eta0, fa, fb, acc, nsupp);
                 if (zs <= e.zl) {
-                    const CmCtx cc = c;
-                    CmWalk wc = w;
-                    const float4 fc[3] = {f[0], f[1], f[2]};
-                    nsupp += cm_tail(&cc, &wc, fc, Xl, Yl, zs, e.zl, eta0, &sm.out[0][0][cc_col]);
+                    // the rest of the column out of line, from a walk rebuilt at
+                    // the same segment (the same state from the same records)
+                    const CmEnt &e2 = sm.ent[i];
+                    const CmCtx cc = cm_ctx(staged ? &sm.nodes[4 * sm.npre[i]] : sc.cmN + 4 * (long long)e2.kfirst,
+                                            &sm.x, e2, B0, B1, B2);
+                    CmWalk wc;
+                    cm_walk_at(cc, wc, w.j, Xl, Yl);
+                    const float4 fc[3] = {cm_rec(cc, w.j, CM_F), cm_rec(cc, w.j + 1, CM_F),
+                                          cm_rec(cc, min(w.j + 2, cc.nseg), CM_F)};
+                    nsupp += cm_tail(&cc, &wc, fc, Xl, Yl, zs, e2.zl, e2.eta0, &sm.out[0][0][cc_col]);
                 }
             }
 #pragma unroll

@@ -139,6 +139,7 @@ struct Scratch {
     uint32_t *mask;              // [nbrick][mask_words] lines touching a brick
     double *brickSum;            // [3][nbrick] sum of S per brick
     double *scatSum;             // [3] sum of S added by the scatter form
+    double *totPart;             // [TOT_PARTS][6] partial sums of the totals
     int *hasPrev;                // [1] a previous relaxed force exists (set by k_totals)
     int *anyIrr;                 // [1] some line has no walk certificate (set by k_lines)
     unsigned int *smax;          // [1] bound on one spread contribution (float bits, set by k_normalise)
@@ -152,6 +153,7 @@ struct Scratch {
     int *cmcnt;                  // [2] bricks of this step on the column-march / the brick passes
     int *cmlist;                 // [2][nbrick_max] those bricks
     float4 *cmN;                 // [np][4] node records of the column march (NULL: not used)
+    int2 *cmrange;               // [n_lines][(nz + 3) / 4] per line and brick layer: candidate segments [x, y]
     CmEnt *cment;                // [cment_cap] entries of the column-march bricks
     int *cment_n;                // [1] entries taken this step
     long long cment_cap;
@@ -841,6 +843,9 @@ __device__ void d_segments(const BeamsC &b, const Scratch<T> &sc, const int k) {
 //   that segment is within R, and a walk that ends within R has found the
 //   closest segment whatever its start.
 // ---------------------------------------------------------------------------
+static __device__ void cm_layer_ranges(const GridC &g, const Scratch<float> &sc, long long np, int l, int off, int n,
+                                float Rc, int lane);
+
 template <typename T>
 __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
                         const int l, const int lane) {
@@ -989,6 +994,11 @@ __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
             atomicAdd(&status[ST_IRREGULAR], 1);
             *sc.anyIrr = 1;
         }
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        // the column march's candidate segments of each brick layer (node
+        // heights increase along a climbing line, so they form a range)
+        if (okc && sc.cmrange && n >= 2) cm_layer_ranges(g, sc, np, l, off, n, Rc, lane);
     }
 }
 
@@ -2801,12 +2811,19 @@ __device__ void d_brick(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
 // ---------------------------------------------------------------------------
 // k_totals: FP64 sum F and sum S V, fixed reduction order
 // ---------------------------------------------------------------------------
+// Conservation totals (sum F per line, sum S per brick, in FP64): TOT_PARTS
+// fixed slices of the lines and bricks, each summed by one CTA
+// (d_totals_part), then the slices added in order (d_totals_fin); the same
+// two steps in the batched kernels, so the bits match.
+constexpr int TOT_PARTS = 32;
 template <typename T>
-__device__ void d_totals(const GridC &g, const BeamsC &b, const Scratch<T> &sc, double *totals, double (*red)[256]) {
+__device__ void d_totals_part(const GridC &g, const BeamsC &b, const Scratch<T> &sc, int part, double (*red)[256]) {
     double v[6] = {0, 0, 0, 0, 0, 0};
-    for (int l = threadIdx.x; l < b.n_lines; l += 256)
+    const long long l0 = (long long)b.n_lines * part / TOT_PARTS, l1 = (long long)b.n_lines * (part + 1) / TOT_PARTS;
+    const long long r0 = g.nbrick * part / TOT_PARTS, r1 = g.nbrick * (part + 1) / TOT_PARTS;
+    for (long long l = l0 + threadIdx.x; l < l1; l += 256)
         for (int a = 0; a < 3; ++a) v[a] += sc.lineF[3 * l + a];
-    for (long long r = threadIdx.x; r < g.nbrick; r += 256)
+    for (long long r = r0 + threadIdx.x; r < r1; r += 256)
         for (int a = 0; a < 3; ++a) v[3 + a] += sc.brickSum[a * g.nbrick + r];
     for (int a = 0; a < 6; ++a) red[a][threadIdx.x] = v[a];
     __syncthreads();
@@ -2815,11 +2832,18 @@ __device__ void d_totals(const GridC &g, const BeamsC &b, const Scratch<T> &sc, 
             for (int a = 0; a < 6; ++a) red[a][threadIdx.x] += red[a][threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        for (int a = 0; a < 3; ++a) totals[a] = red[a][0];
-        for (int a = 0; a < 3; ++a) totals[3 + a] = (red[3 + a][0] + (g.smode ? sc.scatSum[a] : 0.0)) * g.V;
-        *sc.hasPrev = 1;                 // the next step relaxes against this one
+    if (threadIdx.x < 6) sc.totPart[part * 6 + threadIdx.x] = red[threadIdx.x][0];
+}
+template <typename T>
+__device__ void d_totals_fin(const GridC &g, const Scratch<T> &sc, double *totals) {
+    if (threadIdx.x < 6) {
+        const int a = threadIdx.x;
+        double t = 0.0;
+        for (int q = 0; q < TOT_PARTS; ++q) t += sc.totPart[q * 6 + a];
+        if (a < 3) totals[a] = t;
+        else totals[a] = (t + (g.smode ? sc.scatSum[a - 3] : 0.0)) * g.V;
     }
+    if (threadIdx.x == 0) *sc.hasPrev = 1;                 // the next step relaxes against this one
 }
 
 
@@ -3006,9 +3030,13 @@ __global__ void __launch_bounds__(SPREAD_THREADS) k_bweights_refl(GridC g, Beams
     d_brick<T, true, BZ, false, true>(g, b, sc, p, status, (int)blockIdx.x, sm);
 }
 template <typename T>
-__global__ void __launch_bounds__(256) k_totals(GridC g, BeamsC b, Scratch<T> sc, double *totals) {
+__global__ void __launch_bounds__(256) k_totals(GridC g, BeamsC b, Scratch<T> sc) {
     __shared__ double red[6][256];
-    d_totals(g, b, sc, totals, red);
+    d_totals_part(g, b, sc, (int)blockIdx.x, red);
+}
+template <typename T>
+__global__ void __launch_bounds__(32) k_totals_fin(GridC g, Scratch<T> sc, double *totals) {
+    d_totals_fin(g, sc, totals);
 }
 
 // ---- batched -------------------------------------------------------------
@@ -3174,10 +3202,17 @@ __global__ void __launch_bounds__(SPREAD_THREADS) kb_bweights_refl(const Inst<T>
 template <typename T>
 __global__ void __launch_bounds__(256) kb_totals(const Inst<T> *I, const int *sel, int n) {
     __shared__ double red[6][256];
+    for (long long w = blockIdx.x; w < (long long)n * TOT_PARTS; w += gridDim.x) {
+        const Inst<T> &x = I[AL_SEL((int)(w / TOT_PARTS))];
+        d_totals_part(x.g, x.b, x.sc, (int)(w % TOT_PARTS), red);
+        __syncthreads();
+    }
+}
+template <typename T>
+__global__ void __launch_bounds__(32) kb_totals_fin(const Inst<T> *I, const int *sel, int n) {
     for (int q = blockIdx.x; q < n; q += gridDim.x) {
         const Inst<T> &x = I[AL_SEL(q)];
-        d_totals(x.g, x.b, x.sc, x.totals, red);
-        __syncthreads();
+        d_totals_fin(x.g, x.sc, x.totals);
     }
 }
 #undef AL_SEL
