@@ -109,7 +109,7 @@ struct al_grid_s {
     // column march (FP32, nearest-segment projection, no reflection): node
     // records, entries of the column-march bricks
     float4 *cmN = nullptr;            // [np][4] node records
-    int2 *cmrange = nullptr;          // [n_lines][(nz + 3) / 4] candidate segments per brick layer
+    al::CmLay *cmlay = nullptr;       // [n_lines][(nz + 3) / 4] per line and brick layer
     al::CmEnt *cment = nullptr;
     int *cment_n = nullptr, *bent_off = nullptr, *bent_n = nullptr;
     long long cment_cap = 0;
@@ -149,7 +149,7 @@ static void free_beams(al_grid g) {
     g->rec = nullptr;
     g->rec_total = 0;
     g->cmN = nullptr;
-    g->cmrange = nullptr;
+    g->cmlay = nullptr;
     g->cment = nullptr;
     g->cment_n = g->bent_off = g->bent_n = nullptr;
     g->cment_cap = 0;
@@ -380,7 +380,7 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
             // 16 entries per brick at the lowest brick height (bricks beyond it in
             // a step take the brick passes)
             A(&g->cmN, 4 * (size_t)np);
-            A(&g->cmrange, nl * (size_t)((g->d.nz + 3) / 4));
+            A(&g->cmlay, nl * (size_t)((g->d.nz + 3) / 4));
             g->cment_cap = 16 * g->nbrick_max;
             A(&g->cment, (size_t)g->cment_cap);
             A(&g->cment_n, 1);
@@ -642,7 +642,7 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     // no reflecting face, the gather
     I.g.cm = (g->opt_column && g->cmN && I.g.smode == AL_SPREAD_GATHER) ? 1 : 0;
     sc.cmN = I.g.cm ? g->cmN : nullptr;
-    sc.cmrange = I.g.cm ? g->cmrange : nullptr;
+    sc.cmlay = I.g.cm ? g->cmlay : nullptr;
     sc.cment = g->cment; sc.cment_n = I.g.cm ? g->cment_n : nullptr; sc.cment_cap = g->cment_cap;
     sc.bent_off = g->bent_off; sc.bent_n = g->bent_n;
     I.g.fx = (I.g.rmode || g->opt_record == 2 || g->bd.proj_mode == AL_PROJ_INTEGRATED) ? 1 : 0;
@@ -1068,7 +1068,7 @@ static int batch_rebuild_t(al_batch b) {
             h[q].g.smode = 0;                                // batches always gather
             h[q].g.cm = 0;                                   // and take the brick passes
             h[q].sc.cmN = nullptr;
-            h[q].sc.cmrange = nullptr;
+            h[q].sc.cmlay = nullptr;
             h[q].sc.cment_n = nullptr;
             if (h[q].g.wmode != 0) b->any_segment_weights = true;
             if (h[q].b.sample_mode == AL_SAMPLE_GAUSS) b->any_gauss = true;

@@ -77,6 +77,15 @@ struct alignas(16) CmEnt {
     float ie2, eta0, pad0, pad1; // log2(e) / eps^2 (cells), 1 / (pi eps^2)
 };
 
+// one brick layer of a certified line (k_lines): what its entries in that
+// layer share; an entry adds the brick's corner
+struct alignas(16) CmLay {
+    int kfirst, nseg, zf, zl;     // first candidate node (global), candidate segments (0: none), layer range
+    int j0, O0, O1, pad;          // segment containing the height of layer zf; the line's origin cell (x, y)
+    float oz, gs, ux, uy;         // layer corner minus the origin (z); bisector band; 2-D chord vector
+    float iuu, reach2, ax, ay;    // 1/|u|^2; squared reach (-1: no column); chord start (line-local)
+};
+
 // ---- node records (per step, FP32 instances with the column march) ---------
 __device__ __forceinline__ void cm_line_origin(const Scratch<float> &sc, long long np, int first, int O[3]) {
     for (int a = 0; a < 3; ++a) O[a] = ifloor(sc.uhi[a * np + first]);
@@ -402,12 +411,19 @@ __device__ __forceinline__ void cm_exact_init(CmExact &x, const GridC &g, const 
 // line, so they form a range), and at least the brick's own height range,
 // so that a node inside the brick is a candidate node for its zero-weight
 // deposit
-// per brick layer of a certified line (one warp, k_lines): the candidate
-// segments [jlo, jhi] of the layer's bricks
-static __device__ void cm_layer_ranges(const GridC &g, const Scratch<float> &sc, long long np, int l, int off, int n,
-                                float Rc, int lane) {
+// per brick layer of a certified line (one warp, k_lines, a lane per
+// layer): the candidate segments [jlo, jhi] (node heights increase along a
+// climbing line, so they form a range), the layers within 3 eps (+0.02) of
+// their height range, the start segment, the 2-D chord of the candidate
+// nodes with its reach (3 eps + their largest departure from it + 0.02) and
+// the bisector band; index guards flag status[ST_GUARD] and leave the layer
+// without candidates
+static __device__ void cm_layer_records(const GridC &g, const Scratch<float> &sc, long long np, int l, int off,
+                                        int n, float Rc, float Lmax, int lane, int *status) {
     const int nbz_max = (g.nz + 3) / 4;
     const float *uz = sc.uhi + 2 * np + off;
+    int O[3];
+    cm_line_origin(sc, np, off, O);
     for (int bzi = lane; bzi < g.nbz; bzi += 32) {
         const int B2 = bzi * g.bz, nzb = min(g.bz, g.nz - B2);
         const float zlo = (float)B2 + fminf(0.5f - Rc, 0.0f) - 0.02f;
@@ -423,26 +439,72 @@ static __device__ void cm_layer_ranges(const GridC &g, const Scratch<float> &sc,
             const int mid = (lo + hi + 1) >> 1;
             if (uz[mid] <= zhi) lo = mid; else hi = mid - 1;
         }
-        sc.cmrange[(long long)l * nbz_max + bzi] = make_int2(jlo, lo);
+        const int jhi = lo;
+        CmLay r;
+        r.kfirst = off + jlo;
+        r.nseg = jhi >= jlo ? jhi - jlo + 1 : 0;
+        r.zf = 1; r.zl = 0; r.j0 = 0;
+        r.O0 = O[0]; r.O1 = O[1]; r.pad = 0;
+        r.oz = (float)(B2 - O[2]);
+        r.gs = 0.0f;
+        r.ux = r.uy = r.iuu = 0.0f;
+        r.reach2 = -1.0f;
+        r.ax = r.ay = 0.0f;
+        if (!(jlo >= 0 && jlo <= n - 1 && jhi <= n - 2 && off >= 0 && off + n <= np)) {
+            atomicOr(&status[ST_GUARD], 128);
+            r.nseg = 0;
+        }
+        if (r.nseg > 0) {
+            const float4 *N = sc.cmN + 4 * (long long)r.kfirst;
+            const float4 a0 = N[CM_P], a1 = N[4 * r.nseg + CM_P];
+            const float ux = a1.x - a0.x, uy = a1.y - a0.y, uu = ux * ux + uy * uy;
+            const float iuu = uu > 0.0f ? 1.0f / uu : 0.0f;
+            // layers: cell centres z + 1/2 (brick-relative) within 3 eps (+0.02)
+            // of the candidate nodes' height range
+            r.zf = max(0, (int)ceilf(a0.z - r.oz - Rc - 0.02f - 0.5f));
+            r.zl = min(nzb - 1, (int)floorf(a1.z - r.oz + Rc + 0.02f - 0.5f));
+            const float Zf = (float)r.zf + 0.5f + r.oz;
+            float dev = 0.0f;
+            int j0 = 0;                          // last segment starting at or below the height of layer zf
+            for (int t = 0; t <= r.nseg; ++t) {
+                const float4 a = (t == 0) ? a0 : (t == r.nseg ? a1 : N[4 * t + CM_P]);
+                const float qx = a.x - a0.x, qy = a.y - a0.y;
+                const float tt = __saturatef((qx * ux + qy * uy) * iuu);
+                const float ex = qx - tt * ux, ey = qy - tt * uy;
+                dev = fmaxf(dev, sqrtf(ex * ex + ey * ey));
+                if (t <= r.nseg - 1 && a.z <= Zf) j0 = t;
+            }
+            r.j0 = j0;
+            const float reach = Rc + dev + 0.02f;
+            r.ux = ux; r.uy = uy; r.iuu = iuu;
+            r.ax = a0.x; r.ay = a0.y;
+            r.reach2 = r.zf <= r.zl ? reach * reach : -1.0f;
+            // every tested cell is within reach + dev + |chord| of a node
+            // horizontally and within the brick height + 3 eps + L_max + 1
+            // vertically: the band of the FP32 bisector error there
+            r.gs = Tr<float>::gsig(reach + dev + sqrtf(uu) + (float)g.bz + Rc + Lmax + 1.0f);
+        }
+        sc.cmlay[(long long)l * nbz_max + bzi] = r;
     }
 }
 
-static __device__ void cm_make_entry(const GridC &g, const BeamsC &b, const Scratch<float> &sc, int br, int l, int B0,
-                                     int B1, int B2, int nzb, int bz, CmEnt &e, int *status) {
-    const long long np = b.n_points;
+// the entry of line l in brick br: the layer's record and the brick's corner
+static __device__ void cm_make_entry(const GridC &g, const Scratch<float> &sc, int br, int l, int B0, int B1,
+                                     int B2, int bz, CmEnt &e) {
     const LineG &lg = sc.lines[l];
-    const int first = lg.first, n = lg.n;
-    const float Rc = lg.Rc;
-    const int2 jr = sc.cmrange[(long long)l * ((g.nz + 3) / 4) + B2 / bz];
-    const int jlo = jr.x, jhi = jr.y;
+    const CmLay r = sc.cmlay[(long long)l * ((g.nz + 3) / 4) + B2 / bz];
     e.br = br;
     e.line = l;
-    e.kfirst = first + jlo;
-    e.zf = 1; e.zl = 0; e.j0 = 0;
+    e.kfirst = r.kfirst;
+    e.nseg = r.nseg;
+    e.zf = r.zf; e.zl = r.zl; e.j0 = r.j0;
     e.wsh = lg.wshift;
-    e.ux = e.uy = e.iuu = 0.0f;
-    e.reach2 = -1.0f;
-    e.bx = e.by = 0.0f;
+    e.ox = (float)(B0 - r.O0); e.oy = (float)(B1 - r.O1); e.oz = r.oz;
+    e.gs = r.gs;
+    e.ux = r.ux; e.uy = r.uy; e.iuu = r.iuu;
+    e.reach2 = r.reach2;
+    e.bx = r.nseg > 0 ? __fsub_rn(r.ax, e.ox) : 0.0f;     // exact: a node within reach of the brick
+    e.by = r.nseg > 0 ? __fsub_rn(r.ay, e.oy) : 0.0f;
     {
         const float gr = Tr<float>::grr(lg.R2f);
         e.R2lo = lg.R2f - gr;
@@ -451,44 +513,6 @@ static __device__ void cm_make_entry(const GridC &g, const BeamsC &b, const Scra
     e.ie2 = lg.ie2f;
     e.eta0 = lg.eta0f;
     e.pad0 = e.pad1 = 0.0f;
-    e.nseg = jhi >= jlo ? jhi - jlo + 1 : 0;
-    if (!(jlo >= 0 && jlo <= n - 1 && jhi <= n - 2 && first >= 0 && first + n <= np)) {
-        atomicOr(&status[ST_GUARD], 128);
-        e.nseg = 0;
-    }
-    if (e.nseg <= 0) return;
-    int O[3];
-    cm_line_origin(sc, np, first, O);
-    e.ox = (float)(B0 - O[0]); e.oy = (float)(B1 - O[1]); e.oz = (float)(B2 - O[2]);
-    const float4 *N = sc.cmN + 4 * (long long)e.kfirst;
-    const float4 a0 = __ldg(&N[CM_P]), a1 = __ldg(&N[4 * e.nseg + CM_P]);
-    const float ux = a1.x - a0.x, uy = a1.y - a0.y, uu = ux * ux + uy * uy;
-    const float iuu = uu > 0.0f ? 1.0f / uu : 0.0f;
-    // layers: cell centres z + 1/2 (brick-relative) within 3 eps (+0.02) of the
-    // candidate nodes' height range
-    e.zf = max(0, (int)ceilf(a0.z - e.oz - Rc - 0.02f - 0.5f));
-    e.zl = min(nzb - 1, (int)floorf(a1.z - e.oz + Rc + 0.02f - 0.5f));
-    const float Zf = (float)e.zf + 0.5f + e.oz;
-    float dev = 0.0f;
-    int j0 = 0;                              // last segment starting at or below the height of layer zf
-    for (int t = 0; t <= e.nseg; ++t) {
-        const float4 a = (t == 0) ? a0 : (t == e.nseg ? a1 : __ldg(&N[4 * t + CM_P]));
-        const float qx = a.x - a0.x, qy = a.y - a0.y;
-        const float tt = __saturatef((qx * ux + qy * uy) * iuu);
-        const float ex = qx - tt * ux, ey = qy - tt * uy;
-        dev = fmaxf(dev, sqrtf(ex * ex + ey * ey));
-        if (t <= e.nseg - 1 && a.z <= Zf) j0 = t;
-    }
-    e.j0 = j0;
-    const float reach = Rc + dev + 0.02f;
-    e.ux = ux; e.uy = uy; e.iuu = iuu;
-    e.bx = __fsub_rn(a0.x, e.ox);            // exact: a node within reach of the brick
-    e.by = __fsub_rn(a0.y, e.oy);
-    e.reach2 = e.zf <= e.zl ? reach * reach : -1.0f;
-    // every tested cell is within reach + dev + |chord| of a node horizontally
-    // and within the brick height + 3 eps + L_max + 1 vertically: the band
-    // of the FP32 bisector error there
-    e.gs = Tr<float>::gsig(reach + dev + sqrtf(uu) + (float)bz + Rc + lg.Lmax + 1.0f);
 }
 
 // one warp per brick: which passes take it, and the entries of a
@@ -574,8 +598,7 @@ __global__ void __launch_bounds__(256) k_cm_entries(GridC g, BeamsC b, Scratch<T
             CmEnt e;
             const int l = lst[wib][i];
             CHK(l >= 0 && l < b.n_lines, 32) {
-                if constexpr (std::is_same<T, float>::value)
-                    cm_make_entry(g, b, sc, br, l, B0, B1, B2, nzb, g.bz, e, status);
+                if constexpr (std::is_same<T, float>::value) cm_make_entry(g, sc, br, l, B0, B1, B2, g.bz, e);
                 CHK((long long)off + p0 + i < sc.cment_cap && off + p0 + i >= 0, 64) sc.cment[off + p0 + i] = e;
             }
         }
@@ -878,14 +901,16 @@ __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, con
             sm.npre[lane + 32] = s1 - c1;
             if (lane == 0) sm.npre[CM_SB] = ntot;
         }
-        const bool staged = ntot <= CM_SNODES;
-        if (staged)
-            for (int i = warp; i < ne; i += NW) {
-                const int pi = __shfl_sync(0xffffffffu, i < 32 ? s0 - c0 : s1 - c1, i & 31);
-                const int nr = 4 * (max(sm.ent[i].nseg, 0) + 1);
+        // an entry's records are staged when they fit after the entries before it
+        for (int i = warp; i < ne; i += NW) {
+            const int pi = __shfl_sync(0xffffffffu, i < 32 ? s0 - c0 : s1 - c1, i & 31);
+            const int nn = max(sm.ent[i].nseg, 0) + 1;
+            if (pi + nn <= CM_SNODES) {
+                const int nr = 4 * nn;
                 const float4 *src = sc.cmN + 4 * (long long)sm.ent[i].kfirst;
                 for (int r = lane; r < nr; r += 32) cm_cp16(&sm.nodes[4 * pi + r], &src[r]);
             }
+        }
         // the entries in reach of each column
         for (int cc = tid; cc < BX * BY; cc += NT) {
             const int tx = cc & (BX - 1), ty = cc / BX;
@@ -931,6 +956,7 @@ __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, con
                 const int i = __ffsll((long long)m) - 1;
                 m &= m - 1;
                 const CmEnt &e = sm.ent[i];
+                const bool staged = sm.npre[i + 1] <= CM_SNODES;
                 const CmCtx c = cm_ctx(staged ? &sm.nodes[4 * sm.npre[i]] : sc.cmN + 4 * (long long)e.kfirst, &sm.x,
                                        e, B0, B1, B2);
                 const float Xl = X + c.ox, Yl = Y + c.oy;
@@ -949,7 +975,8 @@ __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, con
                     // the rest of the column out of line, from a walk rebuilt at
                     // the same segment (the same state from the same records)
                     const CmEnt &e2 = sm.ent[i];
-                    const CmCtx cc = cm_ctx(staged ? &sm.nodes[4 * sm.npre[i]] : sc.cmN + 4 * (long long)e2.kfirst,
+                    const CmCtx cc = cm_ctx(sm.npre[i + 1] <= CM_SNODES ? &sm.nodes[4 * sm.npre[i]]
+                                                                         : sc.cmN + 4 * (long long)e2.kfirst,
                                             &sm.x, e2, B0, B1, B2);
                     CmWalk wc;
                     cm_walk_at(cc, wc, w.j, Xl, Yl);

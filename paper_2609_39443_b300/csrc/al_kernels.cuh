@@ -120,6 +120,7 @@ template <> __device__ __forceinline__ float lgc<float>(double, float f) { retur
 template <> __device__ __forceinline__ double lgc<double>(double d, float) { return d; }
 
 struct CmEnt;                    // column march: one candidate line of a brick (al_cm.cuh)
+struct CmLay;                    // column march: one brick layer of a line (al_cm.cuh)
 
 template <typename T>
 struct Scratch {
@@ -153,7 +154,7 @@ struct Scratch {
     int *cmcnt;                  // [2] bricks of this step on the column-march / the brick passes
     int *cmlist;                 // [2][nbrick_max] those bricks
     float4 *cmN;                 // [np][4] node records of the column march (NULL: not used)
-    int2 *cmrange;               // [n_lines][(nz + 3) / 4] per line and brick layer: candidate segments [x, y]
+    CmLay *cmlay;                // [n_lines][(nz + 3) / 4] per line and brick layer: what its entries share
     CmEnt *cment;                // [cment_cap] entries of the column-march bricks
     int *cment_n;                // [1] entries taken this step
     long long cment_cap;
@@ -843,8 +844,8 @@ __device__ void d_segments(const BeamsC &b, const Scratch<T> &sc, const int k) {
 //   that segment is within R, and a walk that ends within R has found the
 //   closest segment whatever its start.
 // ---------------------------------------------------------------------------
-static __device__ void cm_layer_ranges(const GridC &g, const Scratch<float> &sc, long long np, int l, int off, int n,
-                                float Rc, int lane);
+static __device__ void cm_layer_records(const GridC &g, const Scratch<float> &sc, long long np, int l, int off,
+                                        int n, float Rc, float Lmax, int lane, int *status);
 
 template <typename T>
 __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
@@ -996,9 +997,8 @@ __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
         }
     }
     if constexpr (std::is_same<T, float>::value) {
-        // the column march's candidate segments of each brick layer (node
-        // heights increase along a climbing line, so they form a range)
-        if (okc && sc.cmrange && n >= 2) cm_layer_ranges(g, sc, np, l, off, n, Rc, lane);
+        // what the column march's entries of each brick layer share
+        if (okc && sc.cmlay && n >= 2) cm_layer_records(g, sc, np, l, off, n, Rc, Lmax, lane, status);
     }
 }
 
