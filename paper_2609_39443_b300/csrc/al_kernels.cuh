@@ -676,30 +676,6 @@ __device__ int point_fstar(const GridC &g, const BeamsC &b, const StepPtrs<T> &p
     return 0;
 }
 
-// the point's f* again in FP64 (ill-conditioned upstream direction; rare,
-// out of line so that the FP32 evaluation keeps its registers)
-template <typename T, int LANES>
-__device__ __noinline__ void points_refine(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, int *status,
-                                           const int i, const int l, const int n, const int q, const T Pa[3],
-                                           const T Pd[3], const T ab[3], T fstar[3]) {
-    double Pa64[3], Pd64[3], t64[3], f64[3], ab64[3];
-    for (int a = 0; a < 3; ++a) { Pa64[a] = (double)Pa[a]; Pd64[a] = (double)Pd[a]; ab64[a] = (double)ab[a]; }
-    if (b.tangents_given) {
-        for (int a = 0; a < 3; ++a) t64[a] = (double)p.tan[a][i];
-    } else if (n == 1) {
-        t64[0] = t64[1] = t64[2] = 0.0;
-    } else {
-        const int ip = (q == n - 1) ? i : i + 1, im = (q == 0) ? i : i - 1;
-        for (int a = 0; a < 3; ++a) t64[a] = (double)p.P[a][ip] - (double)p.P[a][im];
-    }
-    double nn = sqrt(t64[0] * t64[0] + t64[1] * t64[1] + t64[2] * t64[2]);
-    if (nn > 0.0) for (int a = 0; a < 3; ++a) t64[a] /= nn;
-    else t64[0] = t64[1] = t64[2] = 0.0;
-    point_fstar<T, double, LANES>(g, b, p, l, Pa64, Pd64, t64, f64, status, false, ab64);
-    for (int a = 0; a < 3; ++a) fstar[a] = (T)f64[a];
-    st_count<LANES>(status, ST_REFINED);
-}
-
 // ---------------------------------------------------------------------------
 // k_points: Sec. 3.2.2 - 3.2.3, one thread per actuator point (LANES = 1) or
 // one warp per point (LANES = 32, for the volume-average sampler; every lane
@@ -733,8 +709,25 @@ __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, 
     T ab[3] = {(T)0, (T)0, (T)0};
     if (b.inertia && p.Pdd[0])
         for (int a = 0; a < 3; ++a) ab[a] = p.Pdd[a][i];
-    if (point_fstar<T, T, LANES>(g, b, p, l, Pa, Pd, t, fstar, status, sizeof(T) == 4, ab))
-        points_refine<T, LANES>(g, b, p, status, i, l, n, q, Pa, Pd, ab, fstar);
+    if (point_fstar<T, T, LANES>(g, b, p, l, Pa, Pd, t, fstar, status, sizeof(T) == 4, ab)) {
+        // ill-conditioned upstream direction: the same evaluation in FP64
+        double Pa64[3], Pd64[3], t64[3], f64[3], ab64[3];
+        for (int a = 0; a < 3; ++a) { Pa64[a] = (double)Pa[a]; Pd64[a] = (double)Pd[a]; ab64[a] = (double)ab[a]; }
+        if (b.tangents_given) {
+            for (int a = 0; a < 3; ++a) t64[a] = (double)p.tan[a][i];
+        } else if (n == 1) {
+            t64[0] = t64[1] = t64[2] = 0.0;
+        } else {
+            const int ip = (q == n - 1) ? i : i + 1, im = (q == 0) ? i : i - 1;
+            for (int a = 0; a < 3; ++a) t64[a] = (double)p.P[a][ip] - (double)p.P[a][im];
+        }
+        double nn = sqrt(t64[0] * t64[0] + t64[1] * t64[1] + t64[2] * t64[2]);
+        if (nn > 0.0) for (int a = 0; a < 3; ++a) t64[a] /= nn;
+        else t64[0] = t64[1] = t64[2] = 0.0;
+        point_fstar<T, double, LANES>(g, b, p, l, Pa64, Pd64, t64, f64, status, false, ab64);
+        for (int a = 0; a < 3; ++a) fstar[a] = (T)f64[a];
+        st_count<LANES>(status, ST_REFINED);
+    }
     if (LANES > 1 && (threadIdx.x & 31) != 0) return;
     // Eq. almForceRelaxation and the per-CV load
     const T af = (T)b.alpha_f[l];
@@ -2954,7 +2947,7 @@ __device__ __noinline__ void d_points_nl(const GridC &g, const BeamsC &b, const 
     d_points<T, LANES>(g, b, p, sc, status, i);
 }
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_points(GridC g, BeamsC b, StepPtrs<T> p, Scratch<T> sc, int *status) {
+__global__ void __launch_bounds__(256) k_points(GridC g, BeamsC b, StepPtrs<T> p, Scratch<T> sc, int *status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < b.n_points) d_points_nl<T, 1>(g, b, p, sc, status, i);
 }
