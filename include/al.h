@@ -302,6 +302,25 @@ int al_trace_last(al_grid g, float *ms /* [AL_TRACE_N] */);
 #define AL_OPT_OWN_X1       8
 int al_set_option(al_grid g, int option, int value);
 
+/* One coupling step with the fields and results in host memory (Algorithm 1
+ * steps 1-5 and 7-8 with the transfers a coupled solver makes every step):
+ * on `stream`, copy each input of host_in into the same field of dev_in
+ * (U, alpha, P, Pdot, and P_spread, tangent, U_prev, Pddot where dev_in has
+ * them; host_in's pointers: pinned host memory, the same layout and sizes),
+ * run the step of al_sample_drag_spread on dev_in / dev_out, and copy S and
+ * F of dev_out into host_out's S and F (pinned host memory; a NULL host
+ * field is not copied).  totals and status stay where dev_out puts them.
+ * The step of a call waits for the step of the previous al_step_host call
+ * on the same instance, whatever its stream: a caller that alternates two
+ * streams and two sets of device buffers overlaps the copies of one step
+ * with the step and the copies of the other, with the steps in call order.
+ * A buffer set must not be reused before the call that last used it has
+ * completed on its stream (same stream: ordered).  Returns AL_ERR_ARG for
+ * a NULL descriptor and the errors of al_sample_drag_spread; allocates no
+ * device memory (one event, created at the first call). */
+int al_step_host(al_grid g, const al_step_in *host_in, const al_step_out *host_out, const al_step_in *dev_in,
+                 const al_step_out *dev_out, void *stream);
+
 /* Kernels this instance's al_sample_drag_spread calls have launched so far
  * (cumulative, counted on the host as they are enqueued; the autotuner's
  * trial steps count too).  Returns AL_ERR_ARG for a NULL argument. */

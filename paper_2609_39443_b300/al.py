@@ -108,6 +108,8 @@ def lib():
         L.al_batch_launches.argtypes = [_vp, C.POINTER(C.c_longlong)]
         L.al_trace_last.argtypes = [_vp, C.POINTER(C.c_float)]
         L.al_step_begin.argtypes = [_vp, C.POINTER(StepIn), C.POINTER(StepOut), _vp]
+        L.al_step_host.argtypes = [_vp, C.POINTER(StepIn), C.POINTER(StepOut), C.POINTER(StepIn),
+                                   C.POINTER(StepOut), _vp]
         L.al_step_end.argtypes = [_vp, C.POINTER(StepIn), C.POINTER(StepOut), _vp]
         L.al_weights_get.argtypes = [_vp, _vp, _vp]
         L.al_weights_set.argtypes = [_vp, _vp, _vp]
@@ -334,6 +336,36 @@ class Instance:
                        tangent=self.tangent if self.wl.beams.tangents_given else None,
                        totals=self.totals, status=self.status, stream=stream,
                        U_prev=self.U_prev, Pddot=self.Pddot, dt=self.dt_prev)
+
+    _FIELDS = ("U", "P", "Pdot", "alpha", "P_spread", "tangent", "U_prev", "Pddot", "S", "F")
+
+    def own_buffers(self) -> dict:
+        """This instance's device inputs and outputs, by field name."""
+        return {k: getattr(self, k) for k in self._FIELDS}
+
+    def buffers(self) -> dict:
+        """A second set of device buffers shaped like own_buffers() (for
+        al_step_host calls that alternate two sets)."""
+        import torch
+        return {k: (None if getattr(self, k) is None else torch.empty_like(getattr(self, k))) for k in self._FIELDS}
+
+    def step_host(self, host: dict, dev: Optional[dict] = None, stream=None):
+        """al_step_host: host holds pinned host tensors by field name (the
+        inputs, and S and F to receive the results); dev is a device buffer
+        set (own_buffers() by default).  totals and status are the
+        instance's."""
+        d = dev if dev is not None else self.own_buffers()
+        tg = self.wl.beams.tangents_given
+        hin, hout = step_descriptors(host["U"], host["P"], host["Pdot"], host.get("S"), host.get("F"),
+                                     alpha=host.get("alpha"), P_spread=host.get("P_spread"),
+                                     tangent=host.get("tangent") if tg else None, U_prev=host.get("U_prev"),
+                                     Pddot=host.get("Pddot"), dt=self.dt_prev)
+        din, dout = step_descriptors(d["U"], d["P"], d["Pdot"], d["S"], d["F"], alpha=d["alpha"],
+                                     P_spread=d["P_spread"], tangent=d["tangent"] if tg else None,
+                                     totals=self.totals, status=self.status, U_prev=d["U_prev"],
+                                     Pddot=d["Pddot"], dt=self.dt_prev)
+        check(lib().al_step_host(self.grid.h, C.byref(hin), C.byref(hout), C.byref(din), C.byref(dout),
+                                 _stream_ptr(stream)), "al_step_host")
 
     def set_points(self, P=None, Pdot=None, P_spread=None):
         import torch

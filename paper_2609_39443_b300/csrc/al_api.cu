@@ -106,6 +106,8 @@ struct al_grid_s {
     int opt_column = 1;               // AL_OPT_COLUMN
     int own_x0 = 0, own_x1 = -1;      // AL_OPT_OWN_X0 / X1: owned cells along x (-1: to the end)
     long long launches = 0;           // kernels launched by this instance's steps (al_launches)
+    cudaEvent_t host_ev = nullptr;    // end of the last al_step_host step (orders steps across streams)
+    bool host_ev_set = false;
     // column march (FP32, nearest-segment projection, no reflection): node
     // records, entries of the column-march bricks
     float4 *cmN = nullptr;            // [np][4] node records
@@ -763,6 +765,46 @@ extern "C" int al_sample_drag_spread(al_grid g, const al_step_in *in, const al_s
     return g->d.precision == AL_FP64 ? step_impl<double>(g, in, out, st) : step_impl<float>(g, in, out, st);
 }
 
+// one step with host inputs and results: the copies in, the step (after the
+// previous al_step_host step of the instance, whatever its stream), the
+// copies out, all on `stream`
+extern "C" int al_step_host(al_grid g, const al_step_in *host_in, const al_step_out *host_out,
+                            const al_step_in *dev_in, const al_step_out *dev_out, void *stream) {
+    if (!g || !host_in || !host_out) return AL_ERR_ARG;
+    int rc = check_step(g, dev_in, dev_out);
+    if (rc != AL_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = g->d.precision == AL_FP64 ? sizeof(double) : sizeof(float);
+    const size_t bc = es * (size_t)g->d.nx * g->d.ny * g->d.nz, bp = es * (size_t)g->n_points;
+    auto h2d = [&](const void *dst, const void *src, size_t bytes) -> int {
+        if (!src || !dst || bytes == 0) return AL_OK;
+        AL_CUDA(cudaMemcpyAsync(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice, st));
+        return AL_OK;
+    };
+    for (int a = 0; a < 3 && rc == AL_OK; ++a) rc = h2d(dev_in->U[a], host_in->U[a], bc);
+    if (rc == AL_OK && g->d.has_alpha) rc = h2d(dev_in->alpha, host_in->alpha, bc);
+    for (int a = 0; a < 3 && rc == AL_OK; ++a) {
+        rc = h2d(dev_in->P[a], host_in->P[a], bp);
+        if (rc == AL_OK) rc = h2d(dev_in->Pdot[a], host_in->Pdot[a], bp);
+        if (rc == AL_OK && dev_in->P_spread[a]) rc = h2d(dev_in->P_spread[a], host_in->P_spread[a], bp);
+        if (rc == AL_OK && g->bd.tangents_given) rc = h2d(dev_in->tangent[a], host_in->tangent[a], bp);
+        if (rc == AL_OK && g->d_cmn && dev_in->U_prev[a]) rc = h2d(dev_in->U_prev[a], host_in->U_prev[a], bc);
+        if (rc == AL_OK && g->d_cmn && dev_in->Pddot[a]) rc = h2d(dev_in->Pddot[a], host_in->Pddot[a], bp);
+    }
+    if (rc != AL_OK) return rc;
+    if (!g->host_ev) AL_CUDA(cudaEventCreateWithFlags(&g->host_ev, cudaEventDisableTiming));
+    if (g->host_ev_set) AL_CUDA(cudaStreamWaitEvent(st, g->host_ev, 0));
+    rc = g->d.precision == AL_FP64 ? step_impl<double>(g, dev_in, dev_out, st) : step_impl<float>(g, dev_in, dev_out, st);
+    if (rc != AL_OK) return rc;
+    AL_CUDA(cudaEventRecord(g->host_ev, st));
+    g->host_ev_set = true;
+    for (int a = 0; a < 3; ++a) {
+        if (host_out->S[a]) AL_CUDA(cudaMemcpyAsync(host_out->S[a], dev_out->S[a], bc, cudaMemcpyDeviceToHost, st));
+        if (host_out->F[a] && bp) AL_CUDA(cudaMemcpyAsync(host_out->F[a], dev_out->F[a], bp, cudaMemcpyDeviceToHost, st));
+    }
+    return AL_OK;
+}
+
 extern "C" int al_step_begin(al_grid g, const al_step_in *in, const al_step_out *out, void *stream) {
     const int rc = check_step(g, in, out);
     if (rc != AL_OK) return rc;
@@ -886,6 +928,7 @@ extern "C" int al_destroy(al_grid g) {
     if (g->trace) al_trace_enable(g, 0);
     free_beams(g);
     if (g->grid_slab) cudaFree(g->grid_slab);
+    if (g->host_ev) cudaEventDestroy(g->host_ev);
     delete g;
     return AL_OK;
 }

@@ -464,16 +464,18 @@ static __device__ void cm_layer_records(const GridC &g, const Scratch<float> &sc
             r.zf = max(0, (int)ceilf(a0.z - r.oz - Rc - 0.02f - 0.5f));
             r.zl = min(nzb - 1, (int)floorf(a1.z - r.oz + Rc + 0.02f - 0.5f));
             const float Zf = (float)r.zf + 0.5f + r.oz;
-            float dev = 0.0f;
+            float dev2 = 0.0f;                   // the largest squared departure (sqrt is monotone)
             int j0 = 0;                          // last segment starting at or below the height of layer zf
+#pragma unroll 4
             for (int t = 0; t <= r.nseg; ++t) {
-                const float4 a = (t == 0) ? a0 : (t == r.nseg ? a1 : N[4 * t + CM_P]);
+                const float4 a = N[4 * t + CM_P];
                 const float qx = a.x - a0.x, qy = a.y - a0.y;
                 const float tt = __saturatef((qx * ux + qy * uy) * iuu);
                 const float ex = qx - tt * ux, ey = qy - tt * uy;
-                dev = fmaxf(dev, sqrtf(ex * ex + ey * ey));
+                dev2 = fmaxf(dev2, ex * ex + ey * ey);
                 if (t <= r.nseg - 1 && a.z <= Zf) j0 = t;
             }
+            const float dev = sqrtf(dev2);
             r.j0 = j0;
             const float reach = Rc + dev + 0.02f;
             r.ux = ux; r.uy = uy; r.iuu = iuu;
