@@ -750,10 +750,18 @@ __global__ void __launch_bounds__(CM_WTHREADS, 3) k_cm_weights(GridC g, BeamsC b
     __syncthreads();
     CmWarpBuf &wb = sm.wb[threadIdx.x >> 5];
     const int n = (int)min((long long)*sc.cment_n, sc.cment_cap);
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
-        const CmEnt e = sc.cment[i];
-        d_cm_weights_entry(g, sc, &sm.x, e, wb);
+    // the warps take the entries CM_WGRAB at a time from a counter, so the
+    // last entries end together
+    constexpr int CM_WGRAB = 4;
+    for (;;) {
+        int i0 = 0;
+        if ((threadIdx.x & 31) == 0) i0 = atomicAdd(&sc.cmcnt[3], CM_WGRAB);
+        i0 = __shfl_sync(0xffffffffu, i0, 0);
+        if (i0 >= n) break;
+        for (int i = i0; i < min(i0 + CM_WGRAB, n); ++i) {
+            const CmEnt e = sc.cment[i];
+            d_cm_weights_entry(g, sc, &sm.x, e, wb);
+        }
     }
 }
 
@@ -779,6 +787,7 @@ template <int BZ> struct CmSpreadSmem {
     int hist[CM_SB + 2];
     int npre[CM_SB + 1];              // candidate nodes before each entry
     int next;                         // next column to take
+    int brick;                        // the brick this CTA takes next (list 0 index)
     CmExact x;
     double red[3][CM_STHREADS / 32];
     int redi[CM_STHREADS / 32];
@@ -1103,7 +1112,8 @@ __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, con
     }
 }
 
-// persistent: the CTAs walk the bricks of list 0
+// persistent: the CTAs take the bricks of list 0 one at a time from a
+// counter, so the last bricks end together
 template <int BZ>
 __global__ void __launch_bounds__(CM_STHREADS, 4) k_cm_spread(GridC g, BeamsC b, Scratch<float> sc, StepPtrs<float> p,
                                                               int *status) {
@@ -1111,7 +1121,11 @@ __global__ void __launch_bounds__(CM_STHREADS, 4) k_cm_spread(GridC g, BeamsC b,
     CmSpreadSmem<BZ> &sm = *reinterpret_cast<CmSpreadSmem<BZ> *>(smem_raw);
     if (threadIdx.x == 0) cm_exact_init(sm.x, g, b, sc, p, status);
     const int n = sc.cmcnt[0];
-    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) sm.brick = atomicAdd(&sc.cmcnt[2], 1);
+        __syncthreads();
+        const int i = sm.brick;
+        if (i >= n) break;
         d_cm_spread<BZ>(g, b, sc, p, status, sc.cmlist[i], sm);
         __syncthreads();
     }
