@@ -1036,6 +1036,7 @@ struct al_batch_s {
     int n = 0;
     void *d_inst = nullptr;                   // Inst<T>[n]
     long long *d_pre = nullptr;               // 4 prefix arrays of n + 1: points, lines, bricks, points(warps)
+    unsigned long long *d_ctr = nullptr;      // [4] brick counters of the persistent passes (al_batch_run)
     long long tot_pts = 0, tot_lines = 0, tot_bricks = 0;
     int spread_grid = 0, pt_grid = 0;
     int bz = 8;                               // brick height of the batch's projection
@@ -1059,9 +1060,10 @@ struct al_batch_s {
     int last_nl = 0;                          // kernels of the last enqueue
     int graph_nl = 0;                         // kernels in the captured graph
 
+    // a subset run's slot: selection, 3 prefix arrays, 4 brick counters
     static size_t slot_bytes(int n) {
         size_t a = ((size_t)n * sizeof(int) + 15) & ~(size_t)15;
-        return a + 3 * (size_t)(n + 1) * sizeof(long long);
+        return a + 3 * (size_t)(n + 1) * sizeof(long long) + 4 * sizeof(unsigned long long);
     }
 };
 
@@ -1169,6 +1171,7 @@ static int batch_commit_t(al_batch b) {
     for (int r = 0; r < al_batch_s::RING; ++r) AL_CUDA(cudaEventCreateWithFlags(&b->ring_ev[r], cudaEventDisableTiming));
     AL_CUDA(cudaMalloc(&b->d_inst, sizeof(Inst<T>) * (n ? n : 1)));
     AL_CUDA(cudaMalloc(&b->d_pre, sizeof(long long) * 4 * (size_t)(n + 1)));
+    AL_CUDA(cudaMalloc(&b->d_ctr, 4 * sizeof(unsigned long long)));
     return batch_rebuild_t<T>(b);
 }
 
@@ -1176,8 +1179,9 @@ static int batch_commit_t(al_batch b) {
 // prefix arrays (points, lines, bricks) of the selection; totals: host copies
 template <typename T>
 static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const long long *pre, int n,
-                           long long tot_pts, long long tot_lines, long long tot_bricks) {
+                           long long tot_pts, long long tot_lines, long long tot_bricks, unsigned long long *ctr) {
     using namespace al;
+    AL_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), st));
     const Inst<T> *I = (const Inst<T> *)b->d_inst;
     const long long *pp = pre, *pl = pre + (n + 1), *pb = pre + 2 * (n + 1);
     auto grid_for = [&](long long items, int per_block) {
@@ -1201,14 +1205,14 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
         if (tot_bricks > 0) {
             const int gs = (int)std::min<long long>(b->spread_grid, tot_bricks);
             switch (b->bz) {
-            case 4: kb_bweights<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, false>), st>>>(I, sel, pb, n); break;
-            case 16: kb_bweights<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, false>), st>>>(I, sel, pb, n); break;
-            default: kb_bweights<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, false>), st>>>(I, sel, pb, n); break;
+            case 4: kb_bweights<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, false>), st>>>(I, sel, pb, n, ctr); break;
+            case 16: kb_bweights<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, false>), st>>>(I, sel, pb, n, ctr); break;
+            default: kb_bweights<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, false>), st>>>(I, sel, pb, n, ctr); break;
             }
             if (b->any_reflect) switch (b->bz) {
-            case 4: kb_bweights_refl<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, false>), st>>>(I, sel, pb, n); break;
-            case 16: kb_bweights_refl<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, false>), st>>>(I, sel, pb, n); break;
-            default: kb_bweights_refl<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, false>), st>>>(I, sel, pb, n); break;
+            case 4: kb_bweights_refl<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, false>), st>>>(I, sel, pb, n, ctr); break;
+            case 16: kb_bweights_refl<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, false>), st>>>(I, sel, pb, n, ctr); break;
+            default: kb_bweights_refl<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, false>), st>>>(I, sel, pb, n, ctr); break;
             }
             nl += b->any_reflect ? 2 : 1;
         }
@@ -1218,14 +1222,14 @@ static int batch_enqueue_t(al_batch b, cudaStream_t st, const int *sel, const lo
     if (tot_bricks > 0) {
         const int gs = (int)std::min<long long>(b->spread_grid, tot_bricks);
         switch (b->bz) {
-        case 4: kb_spread<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, true>), st>>>(I, sel, pb, n); break;
-        case 16: kb_spread<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, true>), st>>>(I, sel, pb, n); break;
-        default: kb_spread<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, true>), st>>>(I, sel, pb, n); break;
+        case 4: kb_spread<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, true>), st>>>(I, sel, pb, n, ctr); break;
+        case 16: kb_spread<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, true>), st>>>(I, sel, pb, n, ctr); break;
+        default: kb_spread<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, true>), st>>>(I, sel, pb, n, ctr); break;
         }
         if (b->any_reflect) switch (b->bz) {
-        case 4: kb_spread_refl<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, false>), st>>>(I, sel, pb, n); break;
-        case 16: kb_spread_refl<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, false>), st>>>(I, sel, pb, n); break;
-        default: kb_spread_refl<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, false>), st>>>(I, sel, pb, n); break;
+        case 4: kb_spread_refl<T, 4><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 4, false>), st>>>(I, sel, pb, n, ctr); break;
+        case 16: kb_spread_refl<T, 16><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 16, false>), st>>>(I, sel, pb, n, ctr); break;
+        default: kb_spread_refl<T, 8><<<gs, SPREAD_THREADS, sizeof(SpreadSmem<T, 8, false>), st>>>(I, sel, pb, n, ctr); break;
         }
         nl += b->any_reflect ? 2 : 1;
     }
@@ -1317,8 +1321,10 @@ extern "C" int al_batch_run(al_batch b, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     auto enqueue = [&](cudaStream_t s) {
         return b->precision == AL_FP64
-                   ? batch_enqueue_t<double>(b, s, nullptr, b->d_pre, b->n, b->tot_pts, b->tot_lines, b->tot_bricks)
-                   : batch_enqueue_t<float>(b, s, nullptr, b->d_pre, b->n, b->tot_pts, b->tot_lines, b->tot_bricks);
+                   ? batch_enqueue_t<double>(b, s, nullptr, b->d_pre, b->n, b->tot_pts, b->tot_lines, b->tot_bricks,
+                                             b->d_ctr)
+                   : batch_enqueue_t<float>(b, s, nullptr, b->d_pre, b->n, b->tot_pts, b->tot_lines, b->tot_bricks,
+                                            b->d_ctr);
     };
     if (!b->use_graph) {
         int rc = enqueue(st);
@@ -1372,8 +1378,10 @@ extern "C" int al_batch_run_subset(al_batch b, const int *idx, int n_idx, void *
     AL_CUDA(cudaMemcpyAsync(d, h, off_pre + 3 * (size_t)(n_idx + 1) * sizeof(long long), cudaMemcpyHostToDevice, st));
     const int *ds = (const int *)d;
     const long long *dp = (const long long *)(d + off_pre);
-    int rc = b->precision == AL_FP64 ? batch_enqueue_t<double>(b, st, ds, dp, n_idx, tp, tl, tb)
-                                     : batch_enqueue_t<float>(b, st, ds, dp, n_idx, tp, tl, tb);
+    unsigned long long *dc =
+        reinterpret_cast<unsigned long long *>(d + off_pre + 3 * (size_t)(n_idx + 1) * sizeof(long long));
+    int rc = b->precision == AL_FP64 ? batch_enqueue_t<double>(b, st, ds, dp, n_idx, tp, tl, tb, dc)
+                                     : batch_enqueue_t<float>(b, st, ds, dp, n_idx, tp, tl, tb, dc);
     if (rc != AL_OK) return rc;
     b->launches += b->last_nl;
     AL_CUDA(cudaEventRecord(b->ring_ev[r], st));
@@ -1395,6 +1403,7 @@ extern "C" int al_batch_destroy(al_batch b) {
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->d_pre) cudaFree(b->d_pre);
+    if (b->d_ctr) cudaFree(b->d_ctr);
     delete b;
     return AL_OK;
 }

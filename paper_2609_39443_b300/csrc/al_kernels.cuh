@@ -3137,14 +3137,24 @@ __global__ void __launch_bounds__(256) kb_normalise(const Inst<T> *I, const int 
         if (q >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1 && m) atomicMax(I[AL_SEL(q)].sc.smax, m);
     }
 }
-// persistent: a fixed grid of CTAs walks the bricks of every instance
+// the next brick item of a persistent batched pass, taken by the CTA from a
+// counter of the run (every thread has read the previous one first)
+__device__ __forceinline__ long long kb_take(unsigned long long *ctr, long long *slot) {
+    __syncthreads();
+    if (threadIdx.x == 0) *slot = (long long)atomicAdd(ctr, 1ull);
+    __syncthreads();
+    return *slot;
+}
+// persistent: a fixed grid of CTAs takes the bricks of every instance from a counter
 template <typename T, int BZ>
-__global__ void __launch_bounds__(SPREAD_THREADS) kb_spread(const Inst<T> *I, const int *sel, const long long *pre, int n) {
+__global__ void __launch_bounds__(SPREAD_THREADS) kb_spread(const Inst<T> *I, const int *sel, const long long *pre, int n,
+                                                            unsigned long long *ctr) {
+    __shared__ long long s_item;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // each instance in the accumulation form it has alone (the shared memory
     // is sized for the larger, fixed-point form)
     const long long total = pre[n];
-    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    for (long long item = kb_take(ctr + 2, &s_item); item < total; item = kb_take(ctr + 2, &s_item)) {
         const int q = owner(pre, n, item);
         const Inst<T> &x = I[AL_SEL(q)];
         if (x.b.reflect) continue;                   // kb_spread_refl takes these
@@ -3159,11 +3169,13 @@ __global__ void __launch_bounds__(SPREAD_THREADS) kb_spread(const Inst<T> *I, co
 }
 template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) kb_spread_refl(const Inst<T> *I, const int *sel,
-                                                                 const long long *pre, int n) {
+                                                                 const long long *pre, int n,
+                                                                 unsigned long long *ctr) {
+    __shared__ long long s_item;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
     const long long total = pre[n];
-    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    for (long long item = kb_take(ctr + 3, &s_item); item < total; item = kb_take(ctr + 3, &s_item)) {
         const int q = owner(pre, n, item);
         const Inst<T> &x = I[AL_SEL(q)];
         if (!x.b.reflect) continue;
@@ -3173,11 +3185,12 @@ __global__ void __launch_bounds__(SPREAD_THREADS) kb_spread_refl(const Inst<T> *
 }
 template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) kb_bweights(const Inst<T> *I, const int *sel, const long long *pre,
-                                                              int n) {
+                                                              int n, unsigned long long *ctr) {
+    __shared__ long long s_item;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
     const long long total = pre[n];
-    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    for (long long item = kb_take(ctr + 0, &s_item); item < total; item = kb_take(ctr + 0, &s_item)) {
         const int q = owner(pre, n, item);
         const Inst<T> &x = I[AL_SEL(q)];
         if (x.b.reflect) continue;                   // kb_bweights_refl takes these
@@ -3188,11 +3201,13 @@ __global__ void __launch_bounds__(SPREAD_THREADS) kb_bweights(const Inst<T> *I, 
 // the same for the instances whose kernel is reflected at grid faces
 template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) kb_bweights_refl(const Inst<T> *I, const int *sel,
-                                                                   const long long *pre, int n) {
+                                                                   const long long *pre, int n,
+                                                                   unsigned long long *ctr) {
+    __shared__ long long s_item;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
     const long long total = pre[n];
-    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    for (long long item = kb_take(ctr + 1, &s_item); item < total; item = kb_take(ctr + 1, &s_item)) {
         const int q = owner(pre, n, item);
         const Inst<T> &x = I[AL_SEL(q)];
         if (!x.b.reflect) continue;
