@@ -750,18 +750,15 @@ __global__ void __launch_bounds__(CM_WTHREADS, 3) k_cm_weights(GridC g, BeamsC b
     __syncthreads();
     CmWarpBuf &wb = sm.wb[threadIdx.x >> 5];
     const int n = (int)min((long long)*sc.cment_n, sc.cment_cap);
-    // the warps take the entries CM_WGRAB at a time from a counter, so the
-    // last entries end together
-    constexpr int CM_WGRAB = 4;
+    // the warps take the entries one at a time from a counter, so the last
+    // entries end together
     for (;;) {
-        int i0 = 0;
-        if ((threadIdx.x & 31) == 0) i0 = atomicAdd(&sc.cmcnt[3], CM_WGRAB);
-        i0 = __shfl_sync(0xffffffffu, i0, 0);
-        if (i0 >= n) break;
-        for (int i = i0; i < min(i0 + CM_WGRAB, n); ++i) {
-            const CmEnt e = sc.cment[i];
-            d_cm_weights_entry(g, sc, &sm.x, e, wb);
-        }
+        int i = 0;
+        if ((threadIdx.x & 31) == 0) i = atomicAdd(&sc.cmcnt[3], 1);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= n) break;
+        const CmEnt e = sc.cment[i];
+        d_cm_weights_entry(g, sc, &sm.x, e, wb);
     }
 }
 
