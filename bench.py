@@ -637,8 +637,9 @@ def run_serve(a):
     wls = W.make_batched(1000 + rank, a.sims)
     sims = [Sim(w, a.sim_steps) for w in wls]
     budget = int(a.budget_gb * 2 ** 30)
-    # the batched form on the same simulations (the server runs its batches)
-    nb = min(64, len(sims))
+    # the batched form on the same simulations (all of them in one batch, as
+    # the server holds them resident)
+    nb = len(sims)
     insts = [Instance(w, options={OPT_COLUMN: 0}) for w in wls[:nb]]
     batch = Batch(insts, use_graph=True)
     for _ in range(3):
@@ -663,7 +664,8 @@ def run_serve(a):
         remap = {s: i for i, s in enumerate(used)}
         sub = [Sim(sims[s].wl, sum(1 for _, x, _ in arr if x == s)) for s in used]
         arr_sub = [(t, remap[s], k) for t, s, k in arr]
-        sb = BatchServer(sub, budget, n_slots=a.slots, max_wave=64, preadmit=True).run(arr_sub).summary()
+        # two waves of up to half the slots in flight at once
+        sb = BatchServer(sub, budget, n_slots=a.slots, max_wave=max(1, a.slots // 2), preadmit=True).run(arr_sub).summary()
         row = {"rate": rate, "requests": n, "simulations": len(sub), "batched": sb}
         if rate in (float(x) for x in a.plain_rates.split(",")):
             row["plain"] = PlainServer(sub, budget, preadmit=True).run(arr_sub).summary()

@@ -1259,7 +1259,11 @@ static int batch_assign_t(al_batch b, int slot, al_grid g, const al_step_in *in,
     if (g) {
         *h = make_inst<T>(g, in, out);
         set_brick_z(h->g, b->bz);
-        h->g.smode = 0;
+        h->g.smode = 0;                                      // batches always gather
+        h->g.cm = 0;                                         // and take the brick passes
+        h->sc.cmN = nullptr;
+        h->sc.cmlay = nullptr;
+        h->sc.cment_n = nullptr;
     } else {
         memset((void *)h, 0, sizeof(Inst<T>));
     }

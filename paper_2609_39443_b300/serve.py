@@ -23,7 +23,7 @@ from __future__ import annotations
 import time
 from collections import deque
 from dataclasses import dataclass, field
-from typing import Dict, List, Tuple
+from typing import Dict, List, Optional, Tuple
 
 import numpy as np
 
@@ -37,10 +37,16 @@ def _pages(nbytes: int) -> int:
 @dataclass
 class Sim:
     """One client simulation: its initial workload and step count.  Request
-    k carries positions P0 + k dt Pdot (the synthetic beam motion)."""
+    k carries positions P0 + k dt V, a smooth synthetic beam motion: each
+    line bends about its first node, V at a node being the line's mean Pdot
+    times the node's arc length from the first node over the line's length
+    (a beam solver hands back smooth centrelines; moving every node by its
+    own random velocity would crumple the lines instead)."""
     wl: object
     n_steps: int
     dt: float = 1e-3
+    _V: Optional[np.ndarray] = field(default=None, init=False, repr=False)
+    _P0: Optional[np.ndarray] = field(default=None, init=False, repr=False)
 
     @property
     def n_points(self) -> int:
@@ -57,8 +63,28 @@ class Sim:
         n = (6 + (1 if g.has_alpha else 0)) * g.n_cells + 9 * max(b.n_points, 1)     # U, S, alpha; P, Pdot, F
         return _pages(es * n + 6 * 8 + 16 * 4 + 4096)
 
+    def velocity(self) -> np.ndarray:
+        """V (3, N_p): the smooth motion of the requests' positions."""
+        if self._V is None:
+            P = np.asarray(self.wl.step.P, dtype=np.float64)
+            Pd = np.asarray(self.wl.step.Pdot, dtype=np.float64)
+            off = np.asarray(self.wl.beams.line_off, dtype=np.int64)
+            V = np.zeros_like(P)
+            for l in range(len(off) - 1):
+                a, b = int(off[l]), int(off[l + 1])
+                if b - a < 2:
+                    V[:, a:b] = Pd[:, a:b].mean(axis=1, keepdims=True)
+                    continue
+                ds = np.linalg.norm(np.diff(P[:, a:b], axis=1), axis=0)
+                s = np.concatenate([[0.0], np.cumsum(ds)])
+                V[:, a:b] = Pd[:, a:b].mean(axis=1, keepdims=True) * (s / max(s[-1], 1e-300))[None, :]
+            self._V = V
+        return self._V
+
     def positions(self, k: int) -> np.ndarray:
-        P = self.wl.step.P.astype(np.float64) + (k * self.dt) * self.wl.step.Pdot.astype(np.float64)
+        if self._P0 is None:
+            self._P0 = np.asarray(self.wl.step.P, dtype=np.float64)
+        P = self._P0 + (k * self.dt) * self.velocity()
         return np.ascontiguousarray(P, dtype=self.dtype())
 
 
