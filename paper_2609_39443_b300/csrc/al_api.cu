@@ -101,8 +101,9 @@ struct al_grid_s {
     int *rcnt = nullptr, *rcap = nullptr;   // per brick: records found / region capacity
     long long *roff = nullptr;        // per brick: region start
     int *rplan = nullptr;             // [2] brick height of this / the next step's regions
-    int *cmcnt = nullptr;             // [4] bricks of a step on the column-march / the brick passes; the
-                                      // next column-march brick of the spread / entry of the weights pass
+    int *cmcnt = nullptr;             // [5] bricks of a step on the column-march (with candidate lines) /
+                                      // the brick passes; the next column-march brick of the spread / entry
+                                      // of the weights pass; column-march bricks without candidate lines
     int *cmlist = nullptr;            // [2][nbrick_max] those bricks
     int opt_column = 1;               // AL_OPT_COLUMN
     int own_x0 = 0, own_x1 = -1;      // AL_OPT_OWN_X0 / X1: owned cells along x (-1: to the end)
@@ -222,7 +223,7 @@ extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
         sl.take(&g->rcnt, (size_t)g->nbrick_max); sl.take(&g->rcap, (size_t)g->nbrick_max);
         sl.take(&g->roff, (size_t)g->nbrick_max);
         sl.take(&g->rplan, 2); sl.take(&g->rused, 1);
-        sl.take(&g->cmcnt, 4); sl.take(&g->cmlist, 2 * (size_t)g->nbrick_max);
+        sl.take(&g->cmcnt, 5); sl.take(&g->cmlist, 2 * (size_t)g->nbrick_max);
     };
     Slab size;
     carve(size);
@@ -697,7 +698,7 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
     if (np > 0) { k_mask<T><<<nb, 256, 0, st>>>(gc, bc, sc); ++nl; }
     if constexpr (std::is_same<T, float>::value) {
         if (gc.cm) {
-            if (np == 0) AL_CUDA(cudaMemsetAsync(g->cmcnt, 0, 4 * sizeof(int), st));   // (k_points resets them)
+            if (np == 0) AL_CUDA(cudaMemsetAsync(g->cmcnt, 0, 5 * sizeof(int), st));   // (k_points resets them)
             k_cm_entries<float><<<(unsigned)((gc.nbrick * 32 + 255) / 256), 256, 0, st>>>(gc, bc, sc, status);
             ++nl;
         }

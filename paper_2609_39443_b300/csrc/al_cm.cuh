@@ -569,9 +569,12 @@ __global__ void __launch_bounds__(256) k_cm_entries(GridC g, BeamsC b, Scratch<T
         }
     }
     if (lane == 0) {
+        // list 0: bricks with candidate lines from the front, bricks without
+        // from the back (the spread takes the costly ones first)
         const int t = bad ? 1 : 0;
-        const int pos = atomicAdd(&sc.cmcnt[t], 1);
-        CHK(pos >= 0 && pos < g.nbrick_max, 4) sc.cmlist[t * g.nbrick_max + pos] = br;
+        const bool back = !bad && total == 0;
+        const int pos = atomicAdd(&sc.cmcnt[back ? 4 : t], 1);
+        CHK(pos >= 0 && pos < g.nbrick_max, 4) sc.cmlist[back ? g.nbrick_max - 1 - pos : t * g.nbrick_max + pos] = br;
         CHK(br >= 0 && br < g.nbrick_max, 8) { sc.bent_off[br] = bad ? 0 : off; sc.bent_n[br] = bad ? 0 : total; }
     }
     if (bad) return;
@@ -1117,13 +1120,13 @@ __global__ void __launch_bounds__(CM_STHREADS, 4) k_cm_spread(GridC g, BeamsC b,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CmSpreadSmem<BZ> &sm = *reinterpret_cast<CmSpreadSmem<BZ> *>(smem_raw);
     if (threadIdx.x == 0) cm_exact_init(sm.x, g, b, sc, p, status);
-    const int n = sc.cmcnt[0];
+    const int n0 = sc.cmcnt[0], n = n0 + sc.cmcnt[4];
     for (;;) {
         if (threadIdx.x == 0) sm.brick = atomicAdd(&sc.cmcnt[2], 1);
         __syncthreads();
         const int i = sm.brick;
         if (i >= n) break;
-        d_cm_spread<BZ>(g, b, sc, p, status, sc.cmlist[i], sm);
+        d_cm_spread<BZ>(g, b, sc, p, status, sc.cmlist[i < n0 ? i : g.nbrick_max - 1 - (i - n0)], sm);
         __syncthreads();
     }
 }

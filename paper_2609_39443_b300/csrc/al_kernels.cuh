@@ -151,8 +151,9 @@ struct Scratch {
     long long *roff;             // [nbrick_max] start of the brick's region
     int *rplan;                  // [2] brick height the regions of this step / of the next step were sized for
     unsigned long long *rused;   // [1] arena taken by the next step's regions
-    int *cmcnt;                  // [4] bricks of this step on the column-march / the brick passes; the
-                                 // next column-march brick of the spread / entry of the weights pass
+    int *cmcnt;                  // [5] bricks of this step on the column-march (with candidate lines) /
+                                 // the brick passes; the next column-march brick of the spread / entry of
+                                 // the weights pass; column-march bricks without candidate lines
     int *cmlist;                 // [2][nbrick_max] those bricks
     float4 *cmN;                 // [np][4] node records of the column march (NULL: not used)
     CmLay *cmlay;                // [n_lines][(nz + 3) / 4] per line and brick layer: what its entries share
@@ -742,7 +743,7 @@ __device__ void d_points(const GridC &g, const BeamsC &b, const StepPtrs<T> &p, 
     sc.wfix[i] = 0ull;                                   // fixed-point weights start at zero
     if (i == 0) {
         *sc.anyIrr = 0; *sc.smax = 0u; *sc.anyZero = 0;
-        sc.cmcnt[0] = 0; sc.cmcnt[1] = 0; sc.cmcnt[2] = 0; sc.cmcnt[3] = 0;
+        sc.cmcnt[0] = 0; sc.cmcnt[1] = 0; sc.cmcnt[2] = 0; sc.cmcnt[3] = 0; sc.cmcnt[4] = 0;
         if (sc.cment_n) *sc.cment_n = 0;
         sc.rplan[0] = sc.rplan[1];                        // the regions the last step sized
         sc.rplan[1] = 0;

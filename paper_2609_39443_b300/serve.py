@@ -82,10 +82,11 @@ class Sim:
         return self._V
 
     def positions(self, k: int) -> np.ndarray:
+        """P0 + k dt V, evaluated in the simulation's precision."""
         if self._P0 is None:
-            self._P0 = np.asarray(self.wl.step.P, dtype=np.float64)
-        P = self._P0 + (k * self.dt) * self.velocity()
-        return np.ascontiguousarray(P, dtype=self.dtype())
+            self._P0 = np.ascontiguousarray(self.wl.step.P, dtype=self.dtype())
+            self._V = np.ascontiguousarray(self.velocity(), dtype=self.dtype())
+        return self._P0 + self.dtype()(k * self.dt) * self._V
 
 
 @dataclass
