@@ -545,8 +545,7 @@ int al_server_destroy(al_server s);
  * exits; lines beyond AL_NOALLOC_MAX_LINES or points beyond
  * AL_NOALLOC_MAX_POINTS are rejected with AL_ERR_CAPACITY.  The first call
  * on each device looks up that array's device address (once, with the
- * device current), so make the first call on a device before any stream
- * capture.  Every call shares the array and it keeps the last call's
+ * device current).  Every call shares the array and it keeps the last call's
  * contents: calls whose work overlaps on the GPU (unordered streams) race,
  * so order them.  status (device int[AL_STATUS_N], optional) is added to as
  * in al_sample_drag_spread; when NULL, counters in the shared array are used
