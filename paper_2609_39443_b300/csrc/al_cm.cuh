@@ -677,6 +677,14 @@ static __device__ __noinline__ void cm_tail_w(const CmCtx *c, CmWalk *w, float X
     cm_march(*c, *w, Xl, Yl, z, zl, *sk);
 }
 
+// 16-byte copies global -> shared that complete in the background (cp.async),
+// and the wait for a thread's copies
+__device__ __forceinline__ void cm_cp16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src));
+}
+__device__ __forceinline__ void cm_cp_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 static __device__ __forceinline__ void d_cm_weights_entry(const GridC &g, const Scratch<float> &sc,
                                                           const CmExact *x, const CmEnt &e, CmWarpBuf &wb) {
     const int lane = threadIdx.x & 31;
@@ -687,8 +695,8 @@ static __device__ __forceinline__ void d_cm_weights_entry(const GridC &g, const 
     const int nseg = e.nseg, zf = e.zf, zl = e.zl, j0 = e.j0;
     const bool buf = nseg + 1 <= CM_EN;
     const float4 *src = sc.cmN + 4 * (long long)e.kfirst;
-    if (buf) {
-        for (int r = lane; r < 4 * (nseg + 1); r += 32) wb.nodes[r] = __ldg(&src[r]);
+    if (buf) {                                   // the records arrive while the columns are listed
+        for (int r = lane; r < 4 * (nseg + 1); r += 32) cm_cp16(&wb.nodes[r], &src[r]);
         for (int t = 0; t <= nseg; ++t) wb.E[t][lane] = 0.0f;
     }
     const CmCtx c = cm_ctx(buf ? wb.nodes : src, x, e, B0, B1, B2);
@@ -705,6 +713,7 @@ static __device__ __forceinline__ void d_cm_weights_entry(const GridC &g, const 
         if (ok) wb.cols[nc + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)col;
         nc += __popc(bal);
     }
+    cm_cp_wait();
     __syncwarp();
     const float Zl0 = __fadd_rn((float)zf + 0.5f, c.oz);
     for (int r0 = 0; r0 < nc; r0 += 32) {
@@ -862,12 +871,6 @@ __device__ __forceinline__ int cm_march_acc(const CmCtx &c, CmWalkL &w, float Xl
     }
     return stop;
 }
-
-__device__ __forceinline__ void cm_cp16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-                 "l"(src));
-}
-__device__ __forceinline__ void cm_cp_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <int BZ>
 __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, const Scratch<float> &sc,
