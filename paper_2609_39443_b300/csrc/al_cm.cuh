@@ -796,6 +796,7 @@ template <int BZ> struct CmSpreadSmem {
     int hist[CM_SB + 2];
     int npre[CM_SB + 1];              // candidate nodes before each entry
     int next;                         // next column to take
+    int nnz;                          // columns with at least one entry
     int brick;                        // the brick this CTA takes next (list 0 index)
     CmExact x;
     double red[3][CM_STHREADS / 32];
@@ -950,10 +951,11 @@ __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, con
                 if (k >= 0) sm.hist[k] = run + inc - v;
                 run += __shfl_sync(0xffffffffu, inc, 31);
             }
+            __syncwarp();
+            if (lane == 0) sm.nnz = sm.hist[0];        // columns with at least one entry
         }
         __syncthreads();
-        const int nnz = sm.hist[0];                    // columns with at least one entry
-        __syncthreads();
+        const int nnz = sm.nnz;
         for (int cc = tid; cc < BX * BY; cc += NT) sm.order[atomicAdd(&sm.hist[__popcll(sm.mask[cc])], 1)] = (unsigned short)cc;
         __syncthreads();
         // the columns, most entries first, each taken whole by one thread
