@@ -7,6 +7,8 @@
 #include "al.h"
 #include "al_kernels.cuh"
 
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -552,6 +554,42 @@ static void launch_bricks_bz(const al::Inst<T> &I, bool weights, cudaStream_t st
     }
 }
 
+// the descriptors of S for the spread's tile stores: a 3-D tensor per
+// component (x fastest), boxes of a brick; off when the driver's encoder is
+// missing or refuses (S not 16-byte aligned, rows not a multiple of 16 bytes)
+template <int BZ>
+static al::CmStore cm_store(const al::Inst<float> &I) {
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+        else
+            (void)cudaGetLastError();
+    }
+    al::CmStore tm;
+    memset(&tm, 0, sizeof(tm));
+    const int nx = I.g.nx, ny = I.g.ny, nz = I.g.nz;
+    bool ok = enc != nullptr && (nx % 4) == 0;
+    for (int a = 0; a < 3 && ok; ++a) ok = (reinterpret_cast<uintptr_t>(I.p.S[a]) & 15) == 0;
+    if (ok) {
+        const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+        const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+        const cuuint32_t box[3] = {(cuuint32_t)al::BX, (cuuint32_t)al::BY, (cuuint32_t)BZ};
+        const cuuint32_t es[3] = {1, 1, 1};
+        for (int a = 0; a < 3 && ok; ++a)
+            ok = enc(&tm.m[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)I.p.S[a], dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    tm.on = ok ? 1 : 0;
+    return tm;
+}
+
 // the projection of one FP32 instance with the column march: bricks whose
 // lines all take it run the column-march passes, the others the brick
 // passes, each brick with one of the two for both its weights and its spread
@@ -566,7 +604,8 @@ static int cm_launch(const al::Inst<float> &I, bool weights, long long nbrick, c
         k_cm_weights<float><<<(unsigned)gr.cw, CM_WTHREADS, sizeof(CmWeightSmem), st>>>(I.g, I.b, I.sc, I.p, I.status);
         k_bweights_ls<BZ><<<cap(gr.bw), SPREAD_THREADS, sizeof(SpreadSmem<float, BZ, false>), st>>>(I.g, I.b, I.sc, I.p, I.status);
     } else {
-        k_cm_spread<BZ><<<cap(gr.cs), CM_STHREADS, sizeof(CmSpreadSmem<BZ>), st>>>(I.g, I.b, I.sc, I.p, I.status);
+        const CmStore tm = cm_store<BZ>(I);
+        k_cm_spread<BZ><<<cap(gr.cs), CM_STHREADS, sizeof(CmSpreadSmem<BZ>), st>>>(I.g, I.b, I.sc, I.p, I.status, tm);
         if (I.g.fx)
             k_spread_ls<BZ, true><<<cap(gr.sl_fx), SPREAD_THREADS, sizeof(SpreadSmem<float, BZ, true>), st>>>(I.g, I.b, I.sc, I.p, I.status);
         else

@@ -55,6 +55,8 @@
 // same decisions and the same (s, eta) bits for every pair.
 #pragma once
 
+#include <cuda.h>                 // CUtensorMap (the descriptors of the S tile stores)
+
 namespace al {
 
 constexpr int CM_ENT = 32;       // entries per batch of a brick
@@ -787,8 +789,16 @@ constexpr int CM_STHREADS = 128;      // threads per brick
 constexpr int CM_SB = 64;             // entries per batch (one bit each in a column's mask)
 constexpr int CM_SNODES = 256;        // node records of a batch kept in shared memory (more: read from global)
 
-template <int BZ> struct CmSpreadSmem {
-    float out[BZ][3][BX * BY];        // S of the brick's cells
+// the S tile of a brick goes out by three TMA stores (one per component)
+// when the host could describe S as 3-D tensors (16-byte aligned, rows a
+// multiple of 16 bytes): on = 1
+struct CmStore {
+    CUtensorMap m[3];
+    int on;
+};
+
+template <int BZ> struct alignas(128) CmSpreadSmem {
+    float out[3][BZ][BX * BY];        // S of the brick's cells (component, layer, column)
     float4 nodes[CM_SNODES * 4];      // the batch's candidate nodes' records
     CmEnt ent[CM_SB];
     unsigned long long mask[BX * BY]; // per column: the entries in reach
@@ -807,6 +817,7 @@ template <int BZ> struct CmSpreadSmem {
 // decisions, the sources added straight to the column in shared memory
 struct CmOutSink {
     float *col;                      // &out[0][0][column]
+    int cs;                          // the tile's component stride (layers x columns)
     float eta0;
     float4 fa, fb, nF;
     int nsupp;
@@ -818,16 +829,17 @@ struct CmOutSink {
     __device__ __forceinline__ void pair(const CmCtx &, int z, float s, float q) {
         ++nsupp;
         const float meq = -__fmul_rn(eta0, q);
-        float *o = col + z * (3 * BX * BY);
+        float *o = col + z * (BX * BY);
         o[0] = __fmaf_rn(meq, __fmaf_rn(s, __fsub_rn(fb.x, fa.x), fa.x), o[0]);
-        o[BX * BY] = __fmaf_rn(meq, __fmaf_rn(s, __fsub_rn(fb.y, fa.y), fa.y), o[BX * BY]);
-        o[2 * BX * BY] = __fmaf_rn(meq, __fmaf_rn(s, __fsub_rn(fb.z, fa.z), fa.z), o[2 * BX * BY]);
+        o[cs] = __fmaf_rn(meq, __fmaf_rn(s, __fsub_rn(fb.y, fa.y), fa.y), o[cs]);
+        o[2 * cs] = __fmaf_rn(meq, __fmaf_rn(s, __fsub_rn(fb.z, fa.z), fa.z), o[2 * cs]);
     }
 };
 static __device__ __noinline__ int cm_tail(const CmCtx *c, CmWalk *w, const float4 *f, float Xl, float Yl, int z,
-                                           int zl, float eta0, float *col) {
+                                           int zl, float eta0, float *col, int cs) {
     CmOutSink sk;
     sk.col = col;
+    sk.cs = cs;
     sk.eta0 = eta0;
     sk.fa = f[0]; sk.fb = f[1]; sk.nF = f[2];
     sk.nsupp = 0;
@@ -875,7 +887,8 @@ __device__ __forceinline__ int cm_march_acc(const CmCtx &c, CmWalkL &w, float Xl
 
 template <int BZ>
 __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, const Scratch<float> &sc,
-                                            const StepPtrs<float> &p, int *status, const int br, CmSpreadSmem<BZ> &sm) {
+                                            const StepPtrs<float> &p, int *status, const int br, CmSpreadSmem<BZ> &sm,
+                                            const CmStore &tma) {
     int B0, B1, B2;
     cm_brick_origin(g, br, BZ, B0, B1, B2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
@@ -998,14 +1011,14 @@ __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, con
                     cm_walk_at(cc, wc, w.j, Xl, Yl);
                     const float4 fc[3] = {cm_rec(cc, w.j, CM_F), cm_rec(cc, w.j + 1, CM_F),
                                           cm_rec(cc, min(w.j + 2, cc.nseg), CM_F)};
-                    nsupp += cm_tail(&cc, &wc, fc, Xl, Yl, zs, e2.zl, e2.eta0, &sm.out[0][0][cc_col]);
+                    nsupp += cm_tail(&cc, &wc, fc, Xl, Yl, zs, e2.zl, e2.eta0, &sm.out[0][0][cc_col], BZ * BX * BY);
                 }
             }
 #pragma unroll
             for (int z = 0; z < BZ; ++z) {
-                sm.out[z][0][cc_col] = __fadd_rn(sm.out[z][0][cc_col], acc[z][0]);
-                sm.out[z][1][cc_col] = __fadd_rn(sm.out[z][1][cc_col], acc[z][1]);
-                sm.out[z][2][cc_col] = __fadd_rn(sm.out[z][2][cc_col], acc[z][2]);
+                sm.out[0][z][cc_col] = __fadd_rn(sm.out[0][z][cc_col], acc[z][0]);
+                sm.out[1][z][cc_col] = __fadd_rn(sm.out[1][z][cc_col], acc[z][1]);
+                sm.out[2][z][cc_col] = __fadd_rn(sm.out[2][z][cc_col], acc[z][2]);
             }
         }
         // deposits of the zero-weight nodes inside this brick, in line and node order
@@ -1035,7 +1048,7 @@ __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, con
                             bal &= bal - 1;
                             if (lane == src)
                                 for (int a = 0; a < 3; ++a) {
-                                    float &o = sm.out[c3[2]][a][c3[1] * BX + c3[0]];
+                                    float &o = sm.out[a][c3[2]][c3[1] * BX + c3[0]];
                                     o = __fsub_rn(o, p.F[a][k] / (float)g.V);
                                 }
                             __syncwarp();
@@ -1050,23 +1063,35 @@ __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, con
         sc.rcnt[br] = 0;
         if (br == 0) sc.rplan[1] = g.bz;
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the tile's writes, to the TMA
     __syncthreads();
     // ---- write every cell of the brick once; brick sums of S -----------------
-    // (four cells along x per store where the rows allow it)
+    // one TMA store of the tile per component where S allows it (the brick's
+    // cells outside the grid are clipped), else four cells along x per store
+    // where the rows allow it, else one
     float cs0 = 0.0f, cs1 = 0.0f, cs2 = 0.0f;
     const long long layer = (long long)g.nx * g.ny;
     const long long base = B0 + (long long)g.nx * B1 + layer * B2;
+    const bool use_tma = tma.on != 0;
     const bool vec = (g.nx & 3) == 0 && (nxb & 3) == 0 &&
                      ((reinterpret_cast<uintptr_t>(p.S[0]) | reinterpret_cast<uintptr_t>(p.S[1]) |
                        reinterpret_cast<uintptr_t>(p.S[2])) & 15) == 0;
-    if (vec) {
+    if (use_tma && tid == 0) {
+        for (int a = 0; a < 3; ++a)
+            asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+                         :: "l"(reinterpret_cast<unsigned long long>(&tma.m[a])), "r"(B0), "r"(B1), "r"(B2),
+                            "r"((unsigned)__cvta_generic_to_shared(&sm.out[a][0][0]))
+                         : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+    if (use_tma || vec) {
         for (int q = tid; q < BZ * 3 * (BX * BY / 4); q += NT) {
             const int za = q / (BX * BY / 4), quad = q - za * (BX * BY / 4);
             const int z = za / 3, a = za - 3 * z;
             const int ty = quad / (BX / 4), tx = (quad - ty * (BX / 4)) * 4;
             if (z < nzb && ty < nyb && tx < nxb) {
-                const float4 v = *reinterpret_cast<const float4 *>(&sm.out[z][a][ty * BX + tx]);
-                *reinterpret_cast<float4 *>(p.S[a] + base + tx + (long long)g.nx * ty + layer * z) = v;
+                const float4 v = *reinterpret_cast<const float4 *>(&sm.out[a][z][ty * BX + tx]);
+                if (!use_tma) *reinterpret_cast<float4 *>(p.S[a] + base + tx + (long long)g.nx * ty + layer * z) = v;
                 const float t = (v.x + v.y) + (v.z + v.w);
                 if (a == 0) cs0 += t; else if (a == 1) cs1 += t; else cs2 += t;
             }
@@ -1078,7 +1103,7 @@ __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, con
                 const long long col = base + tx + (long long)g.nx * ty;
                 float *S0 = p.S[0] + col, *S1 = p.S[1] + col, *S2 = p.S[2] + col;
                 for (int z = 0; z < nzb; ++z) {
-                    const float v0 = sm.out[z][0][cc], v1 = sm.out[z][1][cc], v2 = sm.out[z][2][cc];
+                    const float v0 = sm.out[0][z][cc], v1 = sm.out[1][z][cc], v2 = sm.out[2][z][cc];
                     S0[layer * z] = v0; S1[layer * z] = v1; S2[layer * z] = v2;
                     cs0 += v0; cs1 += v1; cs2 += v2;
                 }
@@ -1121,8 +1146,8 @@ __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, con
 // counter, so the last bricks end together
 template <int BZ>
 __global__ void __launch_bounds__(CM_STHREADS, 4) k_cm_spread(GridC g, BeamsC b, Scratch<float> sc, StepPtrs<float> p,
-                                                              int *status) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                              int *status, const __grid_constant__ CmStore tma) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     CmSpreadSmem<BZ> &sm = *reinterpret_cast<CmSpreadSmem<BZ> *>(smem_raw);
     if (threadIdx.x == 0) cm_exact_init(sm.x, g, b, sc, p, status);
     const int n0 = sc.cmcnt[0], n = n0 + sc.cmcnt[4];
@@ -1131,9 +1156,12 @@ __global__ void __launch_bounds__(CM_STHREADS, 4) k_cm_spread(GridC g, BeamsC b,
         __syncthreads();
         const int i = sm.brick;
         if (i >= n) break;
-        d_cm_spread<BZ>(g, b, sc, p, status, sc.cmlist[i < n0 ? i : g.nbrick_max - 1 - (i - n0)], sm);
+        d_cm_spread<BZ>(g, b, sc, p, status, sc.cmlist[i < n0 ? i : g.nbrick_max - 1 - (i - n0)], sm, tma);
+        // the tile's stores have read it before the next brick writes it
+        if (threadIdx.x == 0 && tma.on) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         __syncthreads();
     }
+    if (threadIdx.x == 0 && tma.on) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // written
 }
 // the brick passes over the bricks of list 1
 template <int BZ, bool FX>
