@@ -94,6 +94,7 @@ struct al_grid_s {
     double *brickSum = nullptr;
     double *scatSum = nullptr;
     double *totPart = nullptr;        // [TOT_PARTS][6] partial totals
+    int *totDone = nullptr;           // parts of the totals done in a step
     int *statusInt = nullptr;
     double *totalsInt = nullptr;
     int *hasPrev = nullptr;           // device flag: f_prev is valid
@@ -220,6 +221,7 @@ extern "C" int al_create_grid(const al_grid_desc *desc, al_grid *out) {
         sl.take(&g->brickSum, 3 * (size_t)g->nbrick_max);
         sl.take(&g->scatSum, 3);
         sl.take(&g->totPart, 6 * (size_t)al::TOT_PARTS);
+        sl.take(&g->totDone, 1);
         sl.take(&g->statusInt, AL_STATUS_N); sl.take(&g->totalsInt, 6);
         sl.take(&g->hasPrev, 1); sl.take(&g->anyIrr, 1); sl.take(&g->smax, 1); sl.take(&g->anyZero, 1);
         sl.take(&g->rcnt, (size_t)g->nbrick_max); sl.take(&g->rcap, (size_t)g->nbrick_max);
@@ -436,6 +438,7 @@ extern "C" int al_load_beams(al_grid g, const al_beam_desc *bp) {
     }
     AL_CUDA(cudaMemset(g->mask, 0, ((size_t)g->nbrick_max * g->mask_words ? (size_t)g->nbrick_max * g->mask_words : 1) * sizeof(uint32_t)));
     AL_CUDA(cudaMemset(g->hasPrev, 0, sizeof(int)));
+    AL_CUDA(cudaMemset(g->totDone, 0, sizeof(int)));
     AL_CUDA(cudaMemset(g->anyIrr, 0, sizeof(int)));
     AL_CUDA(cudaMemset(g->smax, 0, sizeof(unsigned int)));
     AL_CUDA(cudaMemset(g->anyZero, 0, sizeof(int)));
@@ -653,6 +656,7 @@ static al::Inst<T> make_inst(al_grid g, const al_step_in *in, const al_step_out 
     sc.segWa = g->segWa; sc.segWb = g->segWb; sc.wfix = g->wfix; sc.w = g->w; sc.fhat = (T *)g->fhat; sc.lineF = g->lineF;
     sc.lines = g->lines; sc.mask = g->mask; sc.brickSum = g->brickSum; sc.scatSum = g->scatSum;
     sc.totPart = g->totPart;
+    sc.totDone = g->totDone;
     sc.hasPrev = g->hasPrev; sc.anyIrr = g->anyIrr; sc.smax = g->smax; sc.anyZero = g->anyZero;
     sc.rec = (Rec<T> *)g->rec; sc.rcnt = g->rcnt; sc.rcap = g->rcap; sc.roff = g->roff;
     sc.rplan = g->rplan; sc.rused = g->rused;
@@ -788,9 +792,8 @@ static int step_impl(al_grid g, const al_step_in *in, const al_step_out *out, cu
         ++nl;
     }
     trace_mark(g, 5, st);
-    k_totals<T><<<TOT_PARTS, 256, 0, st>>>(gc, bc, sc);
-    k_totals_fin<T><<<1, 32, 0, st>>>(gc, sc, I.totals);
-    nl += 2;
+    k_totals<T><<<TOT_PARTS, 256, 0, st>>>(gc, bc, sc, I.totals);
+    ++nl;
     g->launches += nl;
     trace_mark(g, 6, st);
     AL_CUDA(cudaGetLastError());

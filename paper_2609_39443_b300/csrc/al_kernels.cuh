@@ -141,6 +141,7 @@ struct Scratch {
     double *brickSum;            // [3][nbrick] sum of S per brick
     double *scatSum;             // [3] sum of S added by the scatter form
     double *totPart;             // [TOT_PARTS][6] partial sums of the totals
+    int *totDone;                // [1] parts of the totals done this step (the last part adds them)
     int *hasPrev;                // [1] a previous relaxed force exists (set by k_totals)
     int *anyIrr;                 // [1] some line has no walk certificate (set by k_lines)
     unsigned int *smax;          // [1] bound on one spread contribution (float bits, set by k_normalise)
@@ -2841,7 +2842,7 @@ __device__ void d_totals_fin(const GridC &g, const Scratch<T> &sc, double *total
     if (threadIdx.x < 6) {
         const int a = threadIdx.x;
         double t = 0.0;
-        for (int q = 0; q < TOT_PARTS; ++q) t += sc.totPart[q * 6 + a];
+        for (int q = 0; q < TOT_PARTS; ++q) t += __ldcg(&sc.totPart[q * 6 + a]);
         if (a < 3) totals[a] = t;
         else totals[a] = (t + (g.smode ? sc.scatSum[a - 3] : 0.0)) * g.V;
     }
@@ -3031,14 +3032,21 @@ __global__ void __launch_bounds__(SPREAD_THREADS) k_bweights_refl(GridC g, Beams
     SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
     d_brick<T, true, BZ, false, true>(g, b, sc, p, status, (int)blockIdx.x, sm);
 }
+// the TOT_PARTS parts, one per CTA; the CTA that finishes last adds them
 template <typename T>
-__global__ void __launch_bounds__(256) k_totals(GridC g, BeamsC b, Scratch<T> sc) {
+__global__ void __launch_bounds__(256) k_totals(GridC g, BeamsC b, Scratch<T> sc, double *totals) {
     __shared__ double red[6][256];
+    __shared__ int last;
     d_totals_part(g, b, sc, (int)blockIdx.x, red);
-}
-template <typename T>
-__global__ void __launch_bounds__(32) k_totals_fin(GridC g, Scratch<T> sc, double *totals) {
-    d_totals_fin(g, sc, totals);
+    __threadfence();                                     // this part, before the count that publishes it
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(sc.totDone, 1) == TOT_PARTS - 1;
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        d_totals_fin(g, sc, totals);
+        if (threadIdx.x == 0) *sc.totDone = 0;           // for the next step
+    }
 }
 
 // ---- batched -------------------------------------------------------------
