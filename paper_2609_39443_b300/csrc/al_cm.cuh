@@ -421,11 +421,22 @@ __device__ __forceinline__ void cm_exact_init(CmExact &x, const GridC &g, const 
 // the bisector band; index guards flag status[ST_GUARD] and leave the layer
 // without candidates
 static __device__ void cm_layer_records(const GridC &g, const Scratch<float> &sc, long long np, int l, int off,
-                                        int n, float Rc, float Lmax, int lane, int *status) {
+                                        int n, float Rc, float Lmax, int lane, int *status, float *sZ, float4 *sP) {
     const int nbz_max = (g.nz + 3) / 4;
     const float *uz = sc.uhi + 2 * np + off;
     int O[3];
     cm_line_origin(sc, np, off, O);
+    // the line's node heights and positions (records) in the warp's shared
+    // memory when they fit: the searches below then wait on no global load
+    const bool st = sZ != nullptr && sP != nullptr && n <= CM_LN && off >= 0 && off + n <= np;
+    if (st) {
+        for (int q = lane; q < n; q += 32) {
+            sZ[q] = uz[q];
+            sP[q] = sc.cmN[4 * (long long)(off + q) + CM_P];
+        }
+        __syncwarp();
+    }
+    const float *Z = st ? sZ : uz;
     for (int bzi = lane; bzi < g.nbz; bzi += 32) {
         const int B2 = bzi * g.bz, nzb = min(g.bz, g.nz - B2);
         const float zlo = (float)B2 + fminf(0.5f - Rc, 0.0f) - 0.02f;
@@ -433,13 +444,13 @@ static __device__ void cm_layer_records(const GridC &g, const Scratch<float> &sc
         int lo = 1, hi = n;                      // first node q >= 1 with z_q >= zlo (n: none)
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (uz[mid] >= zlo) hi = mid; else lo = mid + 1;
+            if (Z[mid] >= zlo) hi = mid; else lo = mid + 1;
         }
         const int jlo = lo - 1;
         lo = -1; hi = n - 2;                     // last node q <= n - 2 with z_q <= zhi (-1: none)
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (uz[mid] <= zhi) lo = mid; else hi = mid - 1;
+            if (Z[mid] <= zhi) lo = mid; else hi = mid - 1;
         }
         const int jhi = lo;
         CmLay r;
@@ -458,7 +469,8 @@ static __device__ void cm_layer_records(const GridC &g, const Scratch<float> &sc
         }
         if (r.nseg > 0) {
             const float4 *N = sc.cmN + 4 * (long long)r.kfirst;
-            const float4 a0 = N[CM_P], a1 = N[4 * r.nseg + CM_P];
+            auto PN = [&](int t) { return st ? sP[jlo + t] : N[4 * t + CM_P]; };   // candidate t's position
+            const float4 a0 = PN(0), a1 = PN(r.nseg);
             const float ux = a1.x - a0.x, uy = a1.y - a0.y, uu = ux * ux + uy * uy;
             const float iuu = uu > 0.0f ? 1.0f / uu : 0.0f;
             // layers: cell centres z + 1/2 (brick-relative) within 3 eps (+0.02)
@@ -470,7 +482,7 @@ static __device__ void cm_layer_records(const GridC &g, const Scratch<float> &sc
             int j0 = 0;                          // last segment starting at or below the height of layer zf
 #pragma unroll 4
             for (int t = 0; t <= r.nseg; ++t) {
-                const float4 a = N[4 * t + CM_P];
+                const float4 a = PN(t);
                 const float qx = a.x - a0.x, qy = a.y - a0.y;
                 const float tt = __saturatef((qx * ux + qy * uy) * iuu);
                 const float ex = qx - tt * ux, ey = qy - tt * uy;

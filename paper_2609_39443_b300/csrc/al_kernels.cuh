@@ -44,7 +44,8 @@ constexpr int BX = 16, BY = 16;                  // projection brick footprint (
 constexpr int BZ_MIN = 4, BZ_MAX = 16;           // brick heights the kernels are built for
 constexpr int SPREAD_THREADS = BX * BY;          // one thread per column
 constexpr float BRICK_DIAG = 27.72f;             // diagonal of the tallest brick, 16 x 16 x 16
-constexpr int CM_NN = 640;                       // column march: nodes staged per batch of lines
+constexpr int CM_NN = 640;
+constexpr int CM_LN = 256;                        // column march: nodes of a line staged per warp in k_lines                       // column march: nodes staged per batch of lines
 constexpr double PI_D = 3.14159265358979323846;
 
 enum { ST_PA_OUTSIDE = 0, ST_PS_OUTSIDE = 1, ST_FALLBACK = 2, ST_FALLBACK_ZERO = 3,
@@ -848,11 +849,11 @@ __device__ void d_segments(const BeamsC &b, const Scratch<T> &sc, const int k) {
 //   closest segment whatever its start.
 // ---------------------------------------------------------------------------
 static __device__ void cm_layer_records(const GridC &g, const Scratch<float> &sc, long long np, int l, int off,
-                                        int n, float Rc, float Lmax, int lane, int *status);
+                                        int n, float Rc, float Lmax, int lane, int *status, float *sZ, float4 *sP);
 
 template <typename T>
 __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, const StepPtrs<T> &p, int *status,
-                        const int l, const int lane) {
+                        const int l, const int lane, float *sZ = nullptr, float4 *sP = nullptr) {
     const long long np = b.n_points;
     const int off = b.line_off[l], n = b.line_off[l + 1] - off;
     const double eps = b.eps[l];
@@ -1001,7 +1002,7 @@ __device__ void d_lines(const GridC &g, const BeamsC &b, const Scratch<T> &sc, c
     }
     if constexpr (std::is_same<T, float>::value) {
         // what the column march's entries of each brick layer share
-        if (okc && sc.cmlay && n >= 2) cm_layer_records(g, sc, np, l, off, n, Rc, Lmax, lane, status);
+        if (okc && sc.cmlay && n >= 2) cm_layer_records(g, sc, np, l, off, n, Rc, Lmax, lane, status, sZ, sP);
     }
 }
 
@@ -2968,7 +2969,15 @@ __global__ void __launch_bounds__(256) k_segments(BeamsC b, Scratch<T> sc) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_lines(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w < b.n_lines) d_lines(g, b, sc, p, status, w, threadIdx.x & 31);
+    if constexpr (std::is_same<T, float>::value) {
+        // per warp: its line's node heights and line-local positions, for the
+        // column march's layer records
+        __shared__ float sZ[8][CM_LN];
+        __shared__ float4 sP[8][CM_LN];
+        if (w < b.n_lines) d_lines(g, b, sc, p, status, w, threadIdx.x & 31, sZ[threadIdx.x >> 5], sP[threadIdx.x >> 5]);
+    } else {
+        if (w < b.n_lines) d_lines(g, b, sc, p, status, w, threadIdx.x & 31);
+    }
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_mask(GridC g, BeamsC b, Scratch<T> sc) {
