@@ -125,3 +125,27 @@ def test_dense_stems_several_batches_in_a_column_brick():
     compare(wl, g, o, label="dense column")
     assert g["status"][ST_COLUMN] > 0
     assert g["status"][8] == oracle.count_support(wl.grid, wl.beams, wl.step.P)
+
+
+def test_tile_stores_and_the_fallback_write_the_same_sources():
+    """The spread's S tile leaves by TMA tensor stores when S is 16-byte
+    aligned with rows of a multiple of 16 bytes, else by plain stores: an S
+    shifted by one float (no descriptor) gets the same bits, and the
+    totals agree to rounding."""
+    import torch
+    from paper_2609_39443_b300.al import Instance
+    wl = W.make_flume(2, nx=160, ny=48, nz=64, n_sx=14, n_sy=5, height=0.2)
+    a = Instance(wl)
+    a.step()
+    b = Instance(wl)
+    n = wl.grid.n_cells
+    raw = torch.empty(3 * n + 1, dtype=torch.float32, device="cuda")
+    S = raw[1:].view(3, n)                          # 4 bytes past an aligned start
+    b.grid.step(b.U, b.P, b.Pdot, S, b.F, alpha=b.alpha, totals=b.totals, status=b.status)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(S.cpu().numpy(), a.S.cpu().numpy())
+    np.testing.assert_array_equal(b.F.cpu().numpy(), a.F.cpu().numpy())
+    ta, tb = a.totals.cpu().numpy(), b.totals.cpu().numpy()
+    assert np.abs(ta - tb).max() <= 1e-6 * np.abs(ta).max()
+    a.close()
+    b.close()
