@@ -309,7 +309,7 @@ def run_ours(a):
         inst.grid.set_option(OPT_RECORD, 1 if tuned["records"] else 0)
         inst.grid.set_option(OPT_COLUMN, 1 if tuned["column_march"] else 0)
     elif not a.no_tune:
-        wmode, bz, rec, col = inst.autotune(trials=2)
+        wmode, bz, rec, col = inst.autotune(trials=4)
         tuned = {"weights": "segment" if wmode else "brick", "brick_z": bz, "records": bool(rec),
                  "column_march": bool(col), "autotuned": True}
     if a.reflect:                                    # the library takes the brick passes for it

@@ -329,12 +329,16 @@ int al_launches(al_grid g, long long *n);
 /* Autotuner: runs the caller's step (same in/out as al_sample_drag_spread)
  * under every combination of AL_OPT_WEIGHTS (with AL_WEIGHTS_SEGMENT: with
  * and without AL_OPT_RECORD), AL_OPT_BRICK_Z and, for instances that can take
- * it, AL_OPT_COLUMN on and off, `trials` timed steps each after one warm-up,
- * timed with CUDA events on `stream`, and keeps the fastest.  The relaxation
- * state and the status counters are restored afterwards; S, F and totals
- * hold the last trial's outputs.  *choice (optional) = 10000 * column march
- * + 1000 * records + 100 * weights mode + brick height.  Synchronises the
- * stream; allocates a temporary copy of the relaxation state. */
+ * it, AL_OPT_COLUMN on and off: one warm-up step, then `trials` steps each
+ * timed alone with CUDA events on `stream` after a write of twice the L2
+ * (the cold cache a coupled solver leaves between calls); a combination's
+ * time is its fastest step, and the fastest combination is kept.  The
+ * relaxation state and the status counters are restored afterwards; S, F
+ * and totals hold the last trial's outputs.  *choice (optional) = 10000 *
+ * column march + 1000 * records + 100 * weights mode + brick height.
+ * Synchronises the stream; allocates a temporary copy of the relaxation
+ * state and the L2-sized buffer (when that allocation fails, the steps are
+ * timed without it). */
 int al_autotune(al_grid g, const al_step_in *in, const al_step_out *out, int trials, void *stream, int *choice);
 
 /* Sizes of an instance: cells and points. */
