@@ -69,16 +69,23 @@ class Sim:
             P = np.asarray(self.wl.step.P, dtype=np.float64)
             Pd = np.asarray(self.wl.step.Pdot, dtype=np.float64)
             off = np.asarray(self.wl.beams.line_off, dtype=np.int64)
-            V = np.zeros_like(P)
-            for l in range(len(off) - 1):
-                a, b = int(off[l]), int(off[l + 1])
-                if b - a < 2:
-                    V[:, a:b] = Pd[:, a:b].mean(axis=1, keepdims=True)
-                    continue
-                ds = np.linalg.norm(np.diff(P[:, a:b], axis=1), axis=0)
-                s = np.concatenate([[0.0], np.cumsum(ds)])
-                V[:, a:b] = Pd[:, a:b].mean(axis=1, keepdims=True) * (s / max(s[-1], 1e-300))[None, :]
-            self._V = V
+            cnt = np.diff(off)
+            nl, n = len(cnt), P.shape[1]
+            line = np.repeat(np.arange(nl), cnt)                      # the line of every node
+            mean = np.stack([np.bincount(line, weights=Pd[c], minlength=nl) for c in range(3)])
+            mean /= np.maximum(cnt, 1)[None, :]
+            # arc length from the line's first node: a running sum over all
+            # nodes of the segment lengths inside lines, less its value there
+            ds = np.linalg.norm(np.diff(P, axis=1), axis=0) if n > 1 else np.zeros(0)
+            ds = ds * (line[1:] == line[:-1])
+            run = np.concatenate([[0.0], np.cumsum(ds)])
+            first = off[:-1][line]
+            s = run - run[first]
+            last = np.maximum(off[1:] - 1, off[:-1])
+            length = (run[np.minimum(last, max(n - 1, 0))] - run[np.minimum(off[:-1], max(n - 1, 0))])[line] \
+                if n else np.zeros(0)
+            frac = np.where(cnt[line] < 2, 1.0, s / np.maximum(length, 1e-300))
+            self._V = mean[:, line] * frac[None, :]
         return self._V
 
     def positions(self, k: int) -> np.ndarray:
@@ -328,6 +335,7 @@ class BatchServer:
                     break
                 slot[s], bufs[s] = q, b
                 st.admitted += 1
+                sims[s].positions(0)              # the client's motion, ready before the clock too
             st.peak_mem = srv.footprint()[0]
         t0 = time.perf_counter()
 
@@ -435,8 +443,10 @@ class PlainServer:
         stream = self.be.stream()
         if self.preadmit:
             for _, s, _ in arrivals:
-                if s not in self.res and not self._admit(s):
-                    break
+                if s not in self.res:
+                    if not self._admit(s):
+                        break
+                    self.sims[s].positions(0)     # the client's motion, ready before the clock too
         t0 = time.perf_counter()
         while st.completed < n_req:
             now = time.perf_counter() - t0

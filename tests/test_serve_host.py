@@ -234,3 +234,43 @@ def test_poisson_arrivals_keep_per_simulation_order():
     for s in range(5):
         ks = [k for _, ss, k in arr if ss == s]
         assert ks == list(range(7))
+
+
+def _motion_by_line(wl):
+    """The served motion written out line by line: V = the line's mean Pdot
+    times the node's arc length from the first node over the line's length
+    (a line of one node moves with its own Pdot)."""
+    P = np.asarray(wl.step.P, dtype=np.float64)
+    Pd = np.asarray(wl.step.Pdot, dtype=np.float64)
+    off = wl.beams.line_off
+    V = np.zeros_like(P)
+    for l in range(len(off) - 1):
+        a, b = int(off[l]), int(off[l + 1])
+        mean = Pd[:, a:b].mean(axis=1, keepdims=True) if b > a else None
+        if b - a == 1:
+            V[:, a:b] = mean
+        elif b - a > 1:
+            s = [0.0]
+            for i in range(a + 1, b):
+                s.append(s[-1] + float(np.linalg.norm(P[:, i] - P[:, i - 1])))
+            V[:, a:b] = mean * (np.array(s) / max(s[-1], 1e-300))[None, :]
+    return V
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_served_motion_matches_its_definition(seed):
+    # stems, arcs, random walks, single points and repeated nodes
+    wl = W.make_random(seed, 20, 16, 12, n_lines=7, kinds=("stem", "arc", "random", "point", "dup"))
+    sim = Sim(wl, 3)
+    V = sim.velocity()
+    ref = _motion_by_line(wl)
+    assert np.abs(V - ref).max() <= 1e-12 * max(np.abs(ref).max(), 1e-300)
+    # every line's first node stays put unless the line is a single point
+    off = wl.beams.line_off
+    for l in range(len(off) - 1):
+        if off[l + 1] - off[l] > 1:
+            assert np.all(V[:, off[l]] == 0.0)
+    # request k: P0 + k dt V in the simulation's precision
+    P2 = sim.positions(2)
+    assert P2.dtype == np.float32
+    np.testing.assert_allclose(P2, (wl.step.P + np.float32(2 * sim.dt) * V).astype(np.float32), rtol=1e-6, atol=1e-7)
