@@ -510,12 +510,18 @@ int al_server_submit(al_server s, int sim, const void *P_host, void *F_host, lon
  * requests' F_host), then launch a wave on each free stream.  Writes up to
  * max_done tags of completed requests (the rest are reported by later
  * polls).  wait != 0: if nothing has completed, wait for the oldest wave in
- * flight. */
+ * flight, polling its event for at most the server's wait limit; when the
+ * limit runs out, AL_ERR_TIMEOUT (*n_done = 0, the wave still in flight and
+ * retired by a later poll). */
 int al_server_poll(al_server s, long long *done_tags, int max_done, int *n_done, int wait);
-/* Evict: waits for the simulation's step in flight, unbinds and destroys its
- * instance, frees its slot and budget share.  AL_ERR_STATE while requests
- * are still queued. */
+/* Evict: waits (within the wait limit; AL_ERR_TIMEOUT otherwise, the
+ * simulation still resident) for the simulation's step in flight, unbinds
+ * and destroys its instance, frees its slot and budget share.  AL_ERR_STATE
+ * while requests are still queued. */
 int al_server_release(al_server s, int sim);
+/* The limit of the waits of al_server_poll and al_server_release, in seconds
+ * (0 <= seconds <= 1e6; 10 at creation).  AL_ERR_ARG outside that range. */
+int al_server_set_timeout(al_server s, double seconds);
 /* Device bytes held by the resident simulations (as counted at admission)
  * and how many are resident (optional). */
 int al_server_footprint(al_server s, unsigned long long *bytes, int *resident);

@@ -115,6 +115,7 @@ def lib():
         L.al_weights_set.argtypes = [_vp, _vp, _vp]
         L.al_slab_plan.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp]
         L.al_server_create.argtypes = [C.POINTER(ServerDesc), C.POINTER(_vp)]
+        L.al_server_set_timeout.argtypes = [_vp, C.c_double]
         L.al_server_admit.argtypes = [_vp, C.POINTER(GridDesc), C.POINTER(BeamDesc), C.POINTER(StepIn),
                                       C.POINTER(StepOut), C.c_ulonglong, C.POINTER(C.c_int)]
         L.al_server_submit.argtypes = [_vp, C.c_int, _vp, _vp, C.c_longlong]
@@ -520,6 +521,11 @@ class Server:
 
     def release(self, sim: int) -> None:
         check(lib().al_server_release(self.h, int(sim)), "al_server_release")
+
+    def set_timeout(self, seconds: float) -> None:
+        """Limit of the waits of poll(wait=True) and release(); past it they
+        raise with AL_ERR_TIMEOUT and the step stays in flight."""
+        check(lib().al_server_set_timeout(self.h, float(seconds)), "al_server_set_timeout")
 
     def footprint(self):
         """(device bytes held by the resident simulations, how many are resident)"""

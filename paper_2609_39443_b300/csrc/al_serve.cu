@@ -24,9 +24,11 @@
 #include "al.h"
 #include "al_kernels.cuh"
 
+#include <chrono>
 #include <cstring>
 #include <deque>
 #include <new>
+#include <thread>
 #include <vector>
 
 int al_detail_cuda_fail(cudaError_t e, const char *what);
@@ -114,7 +116,22 @@ struct al_server_s {
     int rr = 0;                       // round-robin start of wave formation
     std::vector<long long> done;      // tags completed, not yet reported
     long long n_waves = 0, n_wave_steps = 0;   // waves launched, steps they carried
+    double wait_s = 10.0;             // limit of a wait for a wave (al_server_set_timeout)
 };
+
+// wait for a wave's event, polling, for at most limit_s seconds: AL_ERR_TIMEOUT
+// when it runs out (the wave stays in flight)
+static int sv_wait(cudaEvent_t ev, double limit_s) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t q = cudaEventQuery(ev);
+        if (q == cudaSuccess) return AL_OK;
+        if (q != cudaErrorNotReady) return al_detail_cuda_fail(q, "cudaEventQuery");
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >= limit_s)
+            return AL_ERR_TIMEOUT;
+        std::this_thread::yield();
+    }
+}
 
 static size_t sv_stage_elems(const al_server_desc &d) { return 3 * (size_t)d.max_points; }
 
@@ -207,7 +224,8 @@ static int sv_retire(al_server s, int k, bool wait) {
     Wave &w = s->wave[k];
     if (!w.live) return AL_OK;
     if (wait) {
-        SV_CUDA(cudaEventSynchronize(w.ev));
+        const int rc = sv_wait(w.ev, s->wait_s);
+        if (rc != AL_OK) return rc;
     } else {
         const cudaError_t q = cudaEventQuery(w.ev);
         if (q == cudaErrorNotReady) return AL_OK;
@@ -327,7 +345,10 @@ extern "C" int al_server_release(al_server s, int sim) {
         for (int q : s->wave[k].sims) mine = mine || q == sim;
         if (mine) {
             const int rc = sv_retire(s, k, true);
-            if (rc != AL_OK) return rc;
+            if (rc != AL_OK) {
+                m.releasing = false;                // still resident; the caller may retry
+                return rc;
+            }
         }
     }
     if (!m.queue.empty()) {
@@ -358,6 +379,12 @@ extern "C" int al_server_stats(al_server s, long long *waves, long long *steps) 
     if (!s || !waves || !steps) return AL_ERR_ARG;
     *waves = s->n_waves;
     *steps = s->n_wave_steps;
+    return AL_OK;
+}
+
+extern "C" int al_server_set_timeout(al_server s, double seconds) {
+    if (!s || !(seconds >= 0.0) || !(seconds <= 1e6)) return AL_ERR_ARG;
+    s->wait_s = seconds;
     return AL_OK;
 }
 

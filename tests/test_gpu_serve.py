@@ -87,3 +87,45 @@ def test_admitted_memory_stays_within_the_budget():
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     assert abs(torch.cuda.mem_get_info()[0] - free0) <= 8 * 2 ** 20     # everything returned
+
+
+def test_a_wait_that_runs_out_returns_timeout_and_the_step_completes_later():
+    """A server wait bounded at 0 s returns AL_ERR_TIMEOUT while the wave
+    (a full canopy step, far longer than the launch) is still running; the
+    request stays in flight, a later poll with the default limit retires it,
+    and its forces are those of the same step run alone.  No GPU wait is
+    left unbounded and nothing is made to fault."""
+    import ctypes as C
+    import torch
+    from paper_2609_39443_b300.al import AL_ERR_ARG, AL_ERR_TIMEOUT, ALError, Instance, Server, lib
+    from paper_2609_39443_b300.serve import CudaBackend
+    wl = W.make_canopy(0)
+    sim = Sim(wl, 1)
+    be = CudaBackend()
+    srv = Server(sim.buffer_bytes() + instance_footprint(sim) + (1 << 30), 1, 1, sim.n_points, "fp32")
+    b = be.buffers(sim)
+    q = srv.admit(wl.grid, wl.beams, b.sin, b.sout, b.nbytes)
+    assert q is not None
+    with pytest.raises(ALError):
+        srv.set_timeout(-1.0)
+    assert lib().al_server_set_timeout(srv.h, float("nan")) == AL_ERR_ARG
+    srv.set_timeout(0.0)
+    P = sim.positions(0)
+    F = np.empty_like(P)
+    srv.submit(q, P, F, 7)
+    n = C.c_int(-1)
+    rc = lib().al_server_poll(srv.h, srv._done, len(srv._done), C.byref(n), 1)   # launches, waits 0 s
+    assert rc == AL_ERR_TIMEOUT and n.value == 0
+    srv.set_timeout(10.0)
+    tags = srv.poll(wait=True)
+    while not tags:
+        tags = srv.poll(wait=True)
+    assert tags == [7]
+    srv.release(q)
+    srv.close()
+    inst = Instance(wl, options=BRICK_PASSES)
+    inst.set_points(P=P)
+    inst.step()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(inst.F[:, :sim.n_points].cpu().numpy(), F)
+    inst.close()
