@@ -538,6 +538,7 @@ static __device__ void cm_make_entry(const GridC &g, const Scratch<float> &sc, i
 constexpr int CM_LIST = 256;
 template <typename T>
 __global__ void __launch_bounds__(256) k_cm_entries(GridC g, BeamsC b, Scratch<T> sc, int *status) {
+    pdl_enter();
 #define CHK(c, bit) if (!(c)) { atomicOr(&status[ST_GUARD], bit); } else
     __shared__ int lst[8][CM_LIST];
     const long long brl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -770,6 +771,7 @@ static __device__ __forceinline__ void d_cm_weights_entry(const GridC &g, const 
 template <typename T>
 __global__ void __launch_bounds__(CM_WTHREADS, 3) k_cm_weights(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
                                                                int *status) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CmWeightSmem &sm = *reinterpret_cast<CmWeightSmem *>(smem_raw);
     if (threadIdx.x == 0) cm_exact_init(sm.x, g, b, sc, p, status);
@@ -1159,6 +1161,7 @@ __device__ __forceinline__ void d_cm_spread(const GridC &g, const BeamsC &b, con
 template <int BZ>
 __global__ void __launch_bounds__(CM_STHREADS, 4) k_cm_spread(GridC g, BeamsC b, Scratch<float> sc, StepPtrs<float> p,
                                                               int *status, const __grid_constant__ CmStore tma) {
+    pdl_enter();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     CmSpreadSmem<BZ> &sm = *reinterpret_cast<CmSpreadSmem<BZ> *>(smem_raw);
     if (threadIdx.x == 0) cm_exact_init(sm.x, g, b, sc, p, status);
@@ -1179,6 +1182,7 @@ __global__ void __launch_bounds__(CM_STHREADS, 4) k_cm_spread(GridC g, BeamsC b,
 template <int BZ, bool FX>
 __global__ void __launch_bounds__(SPREAD_THREADS) k_spread_ls(GridC g, BeamsC b, Scratch<float> sc,
                                                               StepPtrs<float> p, int *status) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<float, BZ, FX> &sm = *reinterpret_cast<SpreadSmem<float, BZ, FX> *>(smem_raw);
     const int n = sc.cmcnt[1];
@@ -1190,6 +1194,7 @@ __global__ void __launch_bounds__(SPREAD_THREADS) k_spread_ls(GridC g, BeamsC b,
 template <int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) k_bweights_ls(GridC g, BeamsC b, Scratch<float> sc,
                                                                 StepPtrs<float> p, int *status) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<float, BZ, false> &sm = *reinterpret_cast<SpreadSmem<float, BZ, false> *>(smem_raw);
     const int n = sc.cmcnt[1];

@@ -48,6 +48,16 @@ constexpr int CM_NN = 640;
 constexpr int CM_LN = 256;                        // column march: nodes of a line staged per warp in k_lines                       // column march: nodes staged per batch of lines
 constexpr double PI_D = 3.14159265358979323846;
 
+// Programmatic dependent launch, first statement of every kernel of a step:
+// wait until the stream's previous kernel has completed and
+// its writes are visible.  Launched with the attribute, the kernel is set up
+// while its predecessor runs and starts as that one ends; launched without
+// it, the wait returns at once (stream order has already waited), so each
+// kernel sees what it saw with plain stream order.  No kernel triggers its
+// dependents early: dependents resident before their predecessor ended
+// slowed the latency-bound point pass.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 enum { ST_PA_OUTSIDE = 0, ST_PS_OUTSIDE = 1, ST_FALLBACK = 2, ST_FALLBACK_ZERO = 3,
        ST_ZERO_WEIGHT = 4, ST_DEPOSIT_LOST = 5, ST_REFINED = 6, ST_IRREGULAR = 7, ST_SUPPORT = 8,
        ST_REPLAYED = 9, ST_COLUMN = 10, ST_GUARD = 15 };
@@ -2952,22 +2962,26 @@ __device__ __noinline__ void d_points_nl(const GridC &g, const BeamsC &b, const 
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_points(GridC g, BeamsC b, StepPtrs<T> p, Scratch<T> sc, int *status) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < b.n_points) d_points_nl<T, 1>(g, b, p, sc, status, i);
 }
 // one warp per point (volume-average sampler)
 template <typename T>
 __global__ void __launch_bounds__(256) k_points_w(GridC g, BeamsC b, StepPtrs<T> p, Scratch<T> sc, int *status) {
+    pdl_enter();
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i < b.n_points) d_points_nl<T, 32>(g, b, p, sc, status, i);
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_segments(BeamsC b, Scratch<T> sc) {
+    pdl_enter();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < b.n_points) d_segments(b, sc, k);
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_lines(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
+    pdl_enter();
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if constexpr (std::is_same<T, float>::value) {
         // per warp: its line's node heights and line-local positions, for the
@@ -2981,11 +2995,13 @@ __global__ void __launch_bounds__(256) k_lines(GridC g, BeamsC b, Scratch<T> sc,
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_mask(GridC g, BeamsC b, Scratch<T> sc) {
+    pdl_enter();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < b.n_points) d_mask(g, b, sc, k);
 }
 template <typename T>
 __global__ void __launch_bounds__(128, 4) k_weights(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
+    pdl_enter();
     __shared__ RecStage<T> st;
     const bool stage = g.rmode != 0;
     if (stage) rec_init(st);
@@ -2996,11 +3012,13 @@ __global__ void __launch_bounds__(128, 4) k_weights(GridC g, BeamsC b, Scratch<T
 // scatter form of the projection: one warp per segment of a certified line
 template <typename T>
 __global__ void __launch_bounds__(128) k_scatter(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
+    pdl_enter();
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (k < b.n_points) d_weights<T, true>(g, b, sc, p, status, k, threadIdx.x & 31);
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_normalise(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p, int *status) {
+    pdl_enter();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned int m = k < b.n_points ? d_normalise(g, b, sc, p, status, k) : 0u;
     m = __reduce_max_sync(0xffffffffu, m);
@@ -3009,6 +3027,7 @@ __global__ void __launch_bounds__(256) k_normalise(GridC g, BeamsC b, Scratch<T>
 template <typename T, int BZ, bool FX>
 __global__ void __launch_bounds__(SPREAD_THREADS) k_spread(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
                                                            int *status) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T, BZ, FX> &sm = *reinterpret_cast<SpreadSmem<T, BZ, FX> *>(smem_raw);
     if (!brick_owned(g, blockIdx.x)) {                 // another slab's cells: no sources, no sum
@@ -3020,6 +3039,7 @@ __global__ void __launch_bounds__(SPREAD_THREADS) k_spread(GridC g, BeamsC b, Sc
 template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) k_bweights(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
                                                              int *status) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
     if (!brick_owned(g, blockIdx.x)) return;           // another slab's cells add nothing to the weights
@@ -3030,6 +3050,7 @@ __global__ void __launch_bounds__(SPREAD_THREADS) k_bweights(GridC g, BeamsC b, 
 template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) k_spread_refl(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
                                                                 int *status) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
     d_brick<T, false, BZ, false, true>(g, b, sc, p, status, (int)blockIdx.x, sm);
@@ -3037,6 +3058,7 @@ __global__ void __launch_bounds__(SPREAD_THREADS) k_spread_refl(GridC g, BeamsC 
 template <typename T, int BZ>
 __global__ void __launch_bounds__(SPREAD_THREADS) k_bweights_refl(GridC g, BeamsC b, Scratch<T> sc, StepPtrs<T> p,
                                                                   int *status) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T, BZ, false> &sm = *reinterpret_cast<SpreadSmem<T, BZ, false> *>(smem_raw);
     d_brick<T, true, BZ, false, true>(g, b, sc, p, status, (int)blockIdx.x, sm);
@@ -3044,6 +3066,7 @@ __global__ void __launch_bounds__(SPREAD_THREADS) k_bweights_refl(GridC g, Beams
 // the TOT_PARTS parts, one per CTA; the CTA that finishes last adds them
 template <typename T>
 __global__ void __launch_bounds__(256) k_totals(GridC g, BeamsC b, Scratch<T> sc, double *totals) {
+    pdl_enter();
     __shared__ double red[6][256];
     __shared__ int last;
     d_totals_part(g, b, sc, (int)blockIdx.x, red);
