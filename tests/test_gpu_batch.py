@@ -66,3 +66,25 @@ def test_batch_against_oracle():
     batch.close()
     for i in inst:
         i.close()
+
+
+def test_batch_with_a_full_size_instance_against_oracle():
+    """An instance at the batched workload's largest grid (256 x 128 x 128
+    cells, 600 stems of 60 CVs) run inside a batch beside smaller ones, its
+    S compared element by element with the FP64 oracle: the full size
+    reaches the oracle directly, not only through batch = alone."""
+    import torch
+    from paper_2609_39443_b300.al import Batch, Instance
+    big = W.random_canopy(123, 256, 128, 128, 0.005, 600, 60, 2.5, name="batch_full")
+    wls = [big] + W.make_batched(5, 3, max_cells=64 * 48 * 40)
+    inst = [Instance(w) for w in wls]
+    batch = Batch(inst, use_graph=True)
+    batch.run()
+    torch.cuda.synchronize()
+    for w, i in zip(wls, inst):
+        g = {"S": i.S.double().cpu().numpy(), "F": i.F[:, :w.beams.n_points].double().cpu().numpy(),
+             "totals": i.totals.cpu().numpy(), "status": i.status.cpu().numpy()}
+        compare(w, g, oracle.sample_drag_spread(w), label=w.name)    # downstream drag: the net criterion
+    batch.close()
+    for i in inst:
+        i.close()
